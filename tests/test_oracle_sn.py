@@ -1,0 +1,105 @@
+"""Pins of the full-rank S_N oracle against closed forms (no GPU).
+
+Each test fixes a part of oracle/sn.py by a value the mathematics determines
+independently of the code: an exact shift, a telescoping balance, a decay
+factor, a source increment.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import sn
+from paper_2602_14854_gb300 import inputs
+
+
+def axis_workload(nx=6, ny=5, dt=None, integrator="euler"):
+    """Four axis-aligned directions (+-1, 0), (0, +-1); weights pi/2."""
+    ox = np.array([1.0, -1.0, 0.0, 0.0])
+    oy = np.array([0.0, 0.0, 1.0, -1.0])
+    w = np.full(4, math.pi / 2)
+    nc = nx * ny
+    h = 1.0 / nx
+    return inputs.Workload(
+        name="axis", nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=ny * h, xcuts=[0, nx],
+        ycuts=[0, ny], omega_x=ox, omega_y=oy, w=w, sigma_s=np.zeros(nc),
+        sigma_a=np.zeros(nc), source=np.zeros(nc), g0=np.zeros(nc),
+        dt=h if dt is None else dt, nsteps=1, integrator=integrator)
+
+
+def test_unit_courant_is_exact_shift():
+    """Upwind at Courant number 1 moves every direction exactly one cell (zero inflow)."""
+    wl = axis_workload()
+    rng = np.random.default_rng(0)
+    f = rng.uniform(size=(wl.ny, wl.nx, 4))
+    fx = sn.step(f, wl)            # x-sweep, y-sweep (sigma = 0, Q = 0: collision is identity)
+    expect = np.zeros_like(f)
+    # x-sweep: +x shifts right, -x shifts left; then y-sweep: +y shifts up, -y shifts down
+    expect[:, 1:, 0] = f[:, :-1, 0]
+    expect[:, :-1, 1] = f[:, 1:, 1]
+    expect[1:, :, 2] = f[:-1, :, 2]
+    expect[:-1, :, 3] = f[1:, :, 3]
+    assert np.max(np.abs(fx - expect)) < 1e-15
+
+
+def test_mass_balance_telescopes():
+    """Euler x-sweep: change of mass = -dt * net outflow through the two x faces."""
+    wl = inputs.random_small_problem(3, nx=7, ny=5, tiles_x=1, tiles_y=1, n_mu=2, n_phi=8)
+    rng = np.random.default_rng(1)
+    f = rng.uniform(size=(wl.ny, wl.nx, wl.n))
+    dt = 0.3 * wl.hx
+    f1 = f + dt * sn.advection_rhs(f, wl.omega_x, 1, wl.hx)
+    mass = lambda g: wl.hx * wl.hy * np.sum(g @ wl.w)
+    ox = wl.omega_x
+    out_right = np.sum(wl.w * np.maximum(ox, 0) * f[:, -1, :].sum(axis=0)) * wl.hy
+    out_left = np.sum(wl.w * np.maximum(-ox, 0) * f[:, 0, :].sum(axis=0)) * wl.hy
+    assert abs((mass(f1) - mass(f)) + dt * (out_right + out_left)) < 1e-14 * mass(f)
+
+
+@pytest.mark.parametrize("integrator", ["euler", "rk4"])
+def test_isotropic_homogeneous_decay(integrator):
+    """Spatially uniform isotropic state: collision multiplies f by the stability
+    polynomial of the integrator at -dt*sigma_a (scattering conserves)."""
+    wl = inputs.random_small_problem(2, nx=4, ny=4).with_(integrator=integrator)
+    nc = wl.ncells
+    sa, ss = 0.7, 1.3
+    wl = wl.with_(sigma_a=np.full(nc, sa), sigma_s=np.full(nc, ss), source=np.zeros(nc))
+    f = np.full((wl.ny, wl.nx, wl.n), 2.5)
+    f1 = sn._integrate(f, lambda g: sn.collision_rhs(g, wl), wl.dt, integrator)
+    z = -wl.dt * sa
+    fac = 1 + z if integrator == "euler" else 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    assert np.max(np.abs(f1 - 2.5 * fac)) < 1e-14
+
+
+def test_decay_converges_to_exponential():
+    """Euler decay factor (1 - dt s)^{T/dt} -> exp(-s T) with first-order error."""
+    wl0 = inputs.random_small_problem(2, nx=2, ny=2)
+    nc = wl0.ncells
+    errs = []
+    for nst in (20, 40, 80):
+        wl = wl0.with_(sigma_a=np.full(nc, 1.0), sigma_s=np.zeros(nc), source=np.zeros(nc),
+                       dt=1.0 / nst)
+        f = np.ones((2, 2, wl.n))
+        for _ in range(nst):
+            f = sn._integrate(f, lambda g: sn.collision_rhs(g, wl), wl.dt, "euler")
+        errs.append(abs(f[0, 0, 0] - math.exp(-1.0)))
+    assert 1.8 < errs[0] / errs[1] < 2.2 and 1.8 < errs[1] / errs[2] < 2.2
+
+
+def test_source_increment():
+    """No material, zero data: one step adds exactly dt * |S| * Q to the density."""
+    wl = inputs.random_small_problem(5, nx=6, ny=6)
+    nc = wl.ncells
+    wl = wl.with_(sigma_s=np.zeros(nc), sigma_a=np.zeros(nc))
+    f = sn.step(np.zeros((wl.ny, wl.nx, wl.n)), wl)
+    rho = sn.scalar_flux(f, wl)
+    assert np.max(np.abs(rho - wl.dt * np.sum(wl.w) * wl.source)) < 1e-15
+
+
+def test_quadrature_weights_and_moments():
+    """Product set: weights sum to 4 pi, odd moments vanish, <Omega_x^2> = 4 pi / 3."""
+    ox, oy, w = inputs.product_quadrature(8, 16)
+    assert abs(np.sum(w) - 4 * math.pi) < 1e-13
+    assert abs(np.sum(w * ox)) < 1e-13 and abs(np.sum(w * oy)) < 1e-13
+    assert abs(np.sum(w * ox * ox) - 4 * math.pi / 3) < 1e-12
+    assert abs(np.sum(w * ox * oy)) < 1e-13
