@@ -1,0 +1,163 @@
+/*
+ * ddlra.h — C ABI of the GB300 (sm_103a) domain-decomposition dynamical low-rank
+ * (DD-DLRA) time step for the 2D-space x angle radiative transfer equation
+ * (Brunner, Einkemmer, Haut, arXiv 2602.14854).
+ *
+ * Model (Section 2, Eq. (rt)):
+ *     d_t f + c_adv Omega . grad f = sigma_s/|S| * rho - sigma_t f + Q,
+ *     sigma_t = sigma_s + sigma_a,   rho = sum_q w_q f_q,   |S| = sum_q w_q,
+ * discretised by cell-centred first-order upwind finite volumes on a uniform
+ * grid and a discrete direction table (Omega_x, Omega_y, w).
+ *
+ * On every subdomain k of a block tiling the solution is kept in low-rank form
+ * f = U_k S_k V_k^T (Section 3.4) with U orthonormal in the spatial product
+ * <u,v> = hx*hy*sum u v and V orthonormal in <a,b> = sum_q w_q a b.  One time
+ * step is Algorithm 6: x-augmentation (Algorithm 4), x-advection by the
+ * projector-splitting integrator (Algorithm 1) with inflow boundary data
+ * (Eq. (generate_Kboundary)) and eigen-upwinding (Appendix A), truncation
+ * (Algorithm 5), the same in y (Algorithm 2), then absorption/scattering/source
+ * (Algorithm 3).
+ *
+ * Conventions
+ *  - Every call returns a dd_status; DD_OK is 0.  On failure the call has no
+ *    effect on the solver state unless stated, and dd_last_error() returns a
+ *    thread-local message.  No call throws across the ABI.
+ *  - All host arrays passed in are copied; the caller keeps ownership.
+ *  - Cells are numbered x-fastest over the global grid: c = j*nx + i.
+ *    Within subdomain k cells are numbered x-fastest over the subdomain.
+ *  - Subdomain k = J*tx + I for tile column I and tile row J.
+ *  - Device memory is allocated by the library at create time and released by
+ *    dd_dlra_destroy.  All device work is issued on the stream given at create.
+ *  - Errors detected on the device (non-finite values, an exhausted basis
+ *    completion family) are recorded in a device status word and reported by
+ *    the next call that synchronises (dd_dlra_scalar_flux, dd_dlra_ranks,
+ *    dd_dlra_get_factors, dd_dlra_sync).
+ */
+#ifndef DDLRA_H
+#define DDLRA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dd_status {
+  DD_OK = 0,
+  DD_ERR_ARG = 1,        /* invalid argument (sizes, tiling, options)          */
+  DD_ERR_CUDA = 2,       /* a CUDA runtime call failed                           */
+  DD_ERR_RANK_CAP = 3,   /* a rank exceeds the capacity fixed at create time     */
+  DD_ERR_NONFINITE = 4,  /* a non-finite value appeared in the factors          */
+  DD_ERR_COMPLETION = 5, /* the fixed basis-completion family was exhausted      */
+  DD_ERR_STATE = 6       /* call not valid in the current state                 */
+} dd_status;
+
+typedef struct dd_grid {
+  int nx, ny;                 /* global cell counts                               */
+  double x0, x1, y0, y1;      /* domain [x0,x1] x [y0,y1], uniform cells           */
+} dd_grid;
+
+typedef struct dd_tiling {
+  int tx, ty;                 /* subdomain counts in x and y                      */
+  const int* xcuts;           /* host, tx+1 cell indices 0 = c_0 < ... < c_tx = nx */
+  const int* ycuts;           /* host, ty+1 cell indices 0 = c_0 < ... < c_ty = ny */
+} dd_tiling;
+
+typedef struct dd_quadrature {
+  int n;                      /* number of discrete directions                    */
+  const double* omega_x;      /* host, n: x velocity components                   */
+  const double* omega_y;      /* host, n: y velocity components                   */
+  const double* w;            /* host, n: positive quadrature weights, |S| = sum  */
+  int n_polar;                /* polar (mu) levels of a product set; 0 = circle    */
+  int n_azimuth;              /* azimuths per level (phi count)                   */
+} dd_quadrature;
+
+typedef struct dd_fields {
+  const double* sigma_s;      /* host, nx*ny: scattering coefficient  (>= 0)      */
+  const double* sigma_a;      /* host, nx*ny: absorption coefficient  (>= 0)      */
+  const double* source;       /* host, nx*ny: isotropic source Q                  */
+} dd_fields;
+
+enum { DD_RANK_FIXED = 0, DD_RANK_TOL = 1 };
+enum { DD_EULER = 0, DD_RK4 = 1 };
+enum { DD_FP64 = 0 };
+
+typedef struct dd_options {
+  int rank_mode;      /* DD_RANK_FIXED: stored rank <= rank; DD_RANK_TOL: tolerance tol   */
+  int rank;           /* fixed mode: stored rank r (also the augmentation floor)         */
+  double tol;         /* tolerance mode: absolute tail tolerance of Algorithms 4 and 5    */
+  int r_min, r_max;   /* tolerance mode: stored-rank clamp after truncation               */
+  int r_aug_max;      /* cap on the intermediate rank r_t (<= 64)                         */
+  int integrator;     /* DD_EULER or DD_RK4 for every sub-step ODE                        */
+  double c_adv;       /* advection speed                                                  */
+  double dt;          /* time step                                                        */
+  double tau;         /* relative numerical-rank threshold (sigma_j <= tau*sigma_1 -> 0)  */
+  int precision;      /* DD_FP64                                                          */
+} dd_options;
+
+typedef struct dd_dlra* dd_dlra_t;
+
+/*
+ * dd_dlra_create — plan, allocate and initialise a DD-DLRA solver.
+ *
+ * g0 (host, nx*ny) is the isotropic initial data f(0,x,y,Omega) = g0(x,y); it is
+ * stored at rank 1 per subdomain (rank 0 where g0 vanishes on a subdomain).
+ * Tilings are block-aligned (Section 3, Figure "block domain decomposition"):
+ * every subdomain in a tile row has the same height, in a tile column the same
+ * width.  stream is a cudaStream_t (NULL = the legacy default stream).
+ * Errors: DD_ERR_ARG for inconsistent sizes or options (r_aug_max > 64,
+ * 3*stored-rank cap > 64, a subdomain smaller than r_aug_max cells), DD_ERR_CUDA.
+ */
+dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling,
+                         const dd_quadrature* quad, const dd_fields* fields,
+                         const double* g0, const dd_options* opt, void* stream,
+                         dd_dlra_t* out);
+
+/*
+ * dd_dlra_step — advance every subdomain by nsteps time steps of Algorithm 6.
+ * Asynchronous on the solver's stream.  With use_graph != 0 the step is
+ * captured once into a CUDA graph and replayed.
+ */
+dd_status dd_dlra_step(dd_dlra_t h, int nsteps);
+dd_status dd_dlra_set_graph(dd_dlra_t h, int use_graph);
+
+/*
+ * dd_dlra_scalar_flux — rho = sum_q w_q f_q on all nx*ny cells, global x-fastest
+ * order (Section 2, density).  out has nx*ny doubles; out_on_device != 0 means
+ * a device pointer (written asynchronously on the solver's stream), else a host
+ * pointer (the call synchronises).
+ */
+dd_status dd_dlra_scalar_flux(dd_dlra_t h, double* out, int out_on_device);
+
+/* Stored ranks per subdomain after the last step (host, nsub ints), and the
+ * intermediate ranks r_t of the last x- and y-augmentation (host, 2*nsub ints,
+ * may be NULL).  Synchronises. */
+dd_status dd_dlra_ranks(dd_dlra_t h, int* stored, int* intermediate);
+
+/* Number of subdomains, directions and the rank capacity. */
+dd_status dd_dlra_info(dd_dlra_t h, int* nsub, int* n, int* r_cap);
+
+/*
+ * Factors of subdomain k in the paper's weighted form, host row-major:
+ * U (N_k x r), S (r x r), V (n x r), N_k = cells of subdomain k.  get: buffers
+ * sized for r_cap columns are enough; *r receives the rank.  set: r <= stored-
+ * rank cap; U must be orthonormal in hx*hy*sum and V in sum w (not checked).
+ * Both synchronise.
+ */
+dd_status dd_dlra_get_factors(dd_dlra_t h, int k, double* U, double* S, double* V, int* r);
+dd_status dd_dlra_set_factors(dd_dlra_t h, int k, int r, const double* U, const double* S,
+                              const double* V);
+
+/* Wait for the solver's stream and report any device-side error. */
+dd_status dd_dlra_sync(dd_dlra_t h);
+
+/* Release all device and host memory of the solver.  NULL is ignored. */
+void dd_dlra_destroy(dd_dlra_t h);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* dd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDLRA_H */

@@ -1,0 +1,200 @@
+"""Thin ctypes binding of libddlra.so (the C ABI declared in include/ddlra.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+The library is loaded from the package's ``lib/`` folder; when it is missing
+the binding raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libddlra.so")
+
+DD_OK = 0
+STATUS_NAMES = {0: "DD_OK", 1: "DD_ERR_ARG", 2: "DD_ERR_CUDA", 3: "DD_ERR_RANK_CAP",
+                4: "DD_ERR_NONFINITE", 5: "DD_ERR_COMPLETION", 6: "DD_ERR_STATE"}
+DD_RANK_FIXED, DD_RANK_TOL = 0, 1
+DD_EULER, DD_RK4 = 0, 1
+DD_FP64 = 0
+
+# every symbol include/ddlra.h declares
+EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scalar_flux",
+           "dd_dlra_ranks", "dd_dlra_info", "dd_dlra_get_factors", "dd_dlra_set_factors",
+           "dd_dlra_sync", "dd_dlra_destroy", "dd_last_error"]
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("x1", C.c_double),
+                ("y0", C.c_double), ("y1", C.c_double)]
+
+
+class Tiling(C.Structure):
+    _fields_ = [("tx", C.c_int), ("ty", C.c_int), ("xcuts", _ip), ("ycuts", _ip)]
+
+
+class Quadrature(C.Structure):
+    _fields_ = [("n", C.c_int), ("omega_x", _dp), ("omega_y", _dp), ("w", _dp),
+                ("n_polar", C.c_int), ("n_azimuth", C.c_int)]
+
+
+class Fields(C.Structure):
+    _fields_ = [("sigma_s", _dp), ("sigma_a", _dp), ("source", _dp)]
+
+
+class Options(C.Structure):
+    _fields_ = [("rank_mode", C.c_int), ("rank", C.c_int), ("tol", C.c_double),
+                ("r_min", C.c_int), ("r_max", C.c_int), ("r_aug_max", C.c_int),
+                ("integrator", C.c_int), ("c_adv", C.c_double), ("dt", C.c_double),
+                ("tau", C.c_double), ("precision", C.c_int)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libddlra.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"libddlra.so not built ({p}); run __graft_entry__.build()")
+    lib = C.CDLL(p)
+    vp = C.c_void_p
+    lib.dd_dlra_create.argtypes = [C.POINTER(Grid), C.POINTER(Tiling), C.POINTER(Quadrature),
+                                   C.POINTER(Fields), _dp, C.POINTER(Options), vp,
+                                   C.POINTER(vp)]
+    lib.dd_dlra_step.argtypes = [vp, C.c_int]
+    lib.dd_dlra_set_graph.argtypes = [vp, C.c_int]
+    lib.dd_dlra_scalar_flux.argtypes = [vp, vp, C.c_int]
+    lib.dd_dlra_ranks.argtypes = [vp, _ip, _ip]
+    lib.dd_dlra_info.argtypes = [vp, _ip, _ip, _ip]
+    lib.dd_dlra_get_factors.argtypes = [vp, C.c_int, _dp, _dp, _dp, _ip]
+    lib.dd_dlra_set_factors.argtypes = [vp, C.c_int, C.c_int, _dp, _dp, _dp]
+    lib.dd_dlra_sync.argtypes = [vp]
+    lib.dd_dlra_destroy.argtypes = [vp]
+    lib.dd_dlra_destroy.restype = None
+    lib.dd_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("dd_dlra_destroy", "dd_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class DDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(lib, st):
+    if st != DD_OK:
+        raise DDError(st, lib.dd_last_error().decode())
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+class Solver:
+    """DD-DLRA solver on one problem; wraps a dd_dlra_t handle."""
+
+    def __init__(self, wl, tau: float = 1e-5, stream: int = 0, use_graph: bool = False):
+        lib = load()
+        self.lib = lib
+        self.wl = wl
+        self._keep = []
+        xc = np.ascontiguousarray(wl.xcuts, dtype=np.int32)
+        yc = np.ascontiguousarray(wl.ycuts, dtype=np.int32)
+        ox, oy, w = _d(wl.omega_x), _d(wl.omega_y), _d(wl.w)
+        ss, sa, q, g0 = _d(wl.sigma_s), _d(wl.sigma_a), _d(wl.source), _d(wl.g0)
+        self._keep += [xc, yc, ox, oy, w, ss, sa, q, g0]
+        grid = Grid(wl.nx, wl.ny, wl.x0, wl.x1, wl.y0, wl.y1)
+        til = Tiling(len(xc) - 1, len(yc) - 1, xc.ctypes.data_as(_ip), yc.ctypes.data_as(_ip))
+        quad = Quadrature(wl.n, _ptr(ox), _ptr(oy), _ptr(w), wl.n_mu, wl.n_phi)
+        fld = Fields(_ptr(ss), _ptr(sa), _ptr(q))
+        fixed = wl.rank_mode == "fixed"
+        opt = Options(DD_RANK_FIXED if fixed else DD_RANK_TOL, wl.rank, wl.tol, wl.r_min,
+                      wl.r_max, wl.r_aug_max, DD_RK4 if wl.integrator == "rk4" else DD_EULER,
+                      wl.c_adv, wl.dt, tau, DD_FP64)
+        h = C.c_void_p()
+        _check(lib, lib.dd_dlra_create(C.byref(grid), C.byref(til), C.byref(quad),
+                                       C.byref(fld), _ptr(g0), C.byref(opt),
+                                       C.c_void_p(stream), C.byref(h)))
+        self.h = h
+        nsub, n, rc = C.c_int(), C.c_int(), C.c_int()
+        _check(lib, lib.dd_dlra_info(h, C.byref(nsub), C.byref(n), C.byref(rc)))
+        self.nsub, self.n, self.r_cap = nsub.value, n.value, rc.value
+        if use_graph:
+            _check(lib, lib.dd_dlra_set_graph(h, 1))
+
+    def step(self, nsteps: int = 1):
+        _check(self.lib, self.lib.dd_dlra_step(self.h, int(nsteps)))
+
+    def sync(self):
+        _check(self.lib, self.lib.dd_dlra_sync(self.h))
+
+    def scalar_flux(self, out=None):
+        """Host numpy array (synchronising), or write into a device pointer ``out``
+        (an int address, e.g. a torch tensor's data_ptr())."""
+        if out is not None:
+            _check(self.lib, self.lib.dd_dlra_scalar_flux(self.h, C.c_void_p(out), 1))
+            return None
+        rho = np.empty(self.wl.nx * self.wl.ny)
+        _check(self.lib, self.lib.dd_dlra_scalar_flux(self.h, rho.ctypes.data_as(C.c_void_p), 0))
+        return rho
+
+    def ranks(self):
+        st = np.empty(self.nsub, dtype=np.int32)
+        it = np.empty(2 * self.nsub, dtype=np.int32)
+        _check(self.lib, self.lib.dd_dlra_ranks(self.h, st.ctypes.data_as(_ip),
+                                                it.ctypes.data_as(_ip)))
+        return st, it.reshape(2, self.nsub)
+
+    def subdomain_cells(self, k):
+        wl = self.wl
+        TX = len(wl.xcuts) - 1
+        I, J = k % TX, k // TX
+        return (wl.xcuts[I + 1] - wl.xcuts[I]) * (wl.ycuts[J + 1] - wl.ycuts[J])
+
+    def get_factors(self, k):
+        N = self.subdomain_cells(k)
+        U = np.empty((N, self.r_cap))
+        S = np.empty((self.r_cap, self.r_cap))
+        V = np.empty((self.n, self.r_cap))
+        r = C.c_int()
+        _check(self.lib, self.lib.dd_dlra_get_factors(self.h, k, _ptr(U), _ptr(S), _ptr(V),
+                                                       C.byref(r)))
+        r = r.value
+        U = U.reshape(-1)[:N * r].reshape(N, r)
+        S = S.reshape(-1)[:r * r].reshape(r, r)
+        V = V.reshape(-1)[:self.n * r].reshape(self.n, r)
+        return U, S, V
+
+    def set_factors(self, k, U, S, V):
+        U, S, V = _d(U), _d(S), _d(V)
+        r = S.shape[0]
+        _check(self.lib, self.lib.dd_dlra_set_factors(self.h, k, r, _ptr(U), _ptr(S), _ptr(V)))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.dd_dlra_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,108 @@
+// Internal declarations of the DD-DLRA CUDA library (not part of the ABI).
+//
+// Storage convention on the device (the factors of the paper, rescaled so that
+// every orthonormality is Euclidean):
+//   X = sqrt(hx*hy) * U        (N_k x r, row-major, X^T X = I)
+//   Vt = diag(sqrt(w)) * V     (n x r,   row-major, Vt^T Vt = I)
+//   S                          (r x r,   the paper's S)
+// so f_{c,q} = X_c S Vt_q^T / (sqrt(hx*hy) sqrt(w_q)) and the singular values of S
+// are the paper's weighted L2 singular values (Section 3.4 matrix form).
+//
+// Spatial tall arrays hold all subdomains back to back: row rowoff[k] + c for
+// cell c (x-fastest inside subdomain k).  Angular tall arrays hold n rows per
+// subdomain: row k*n + q.  Small per-subdomain matrices are RC x RC blocks.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define DD_MAXC 64          // maximum columns of any tall or small matrix
+#define DD_THREADS 256
+
+namespace dd {
+
+enum OrthMode { ORTH_QR = 0, ORTH_AUG = 1, ORTH_COMPLETE = 2 };
+enum StatusBits { ST_NONFINITE = 1, ST_COMPLETION = 2, ST_RANKCAP = 4 };
+
+// Geometry of the tiling, device arrays (read-only inside kernels).
+struct Geo {
+  int nsub, n, RC, MC;
+  const int* N;      // cells of subdomain k
+  const int* nxk;    // width
+  const int* nyk;    // height
+  const int* rowoff; // first spatial row of subdomain k
+  const int* nb;     // 4 per subdomain: x-lo, x-hi, y-lo, y-hi neighbour, -1 = physical boundary
+  const int* cx0;    // global x offset of the subdomain
+  const int* cy0;    // global y offset
+};
+
+// Line geometry along an axis (0 = x, 1 = y) for subdomain k.
+struct Lines {
+  int nlines, len, stride_line, stride_pos;
+};
+__device__ __forceinline__ Lines lines_of(const Geo& g, int k, int axis) {
+  Lines L;
+  int nx = g.nxk[k], ny = g.nyk[k];
+  if (axis == 0) { L.nlines = ny; L.len = nx; L.stride_line = nx; L.stride_pos = 1; }
+  else           { L.nlines = nx; L.len = ny; L.stride_line = 1; L.stride_pos = nx; }
+  return L;
+}
+__device__ __forceinline__ int cell_of(const Lines& L, int line, int pos) {
+  return line * L.stride_line + pos * L.stride_pos;
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// Block-wide sum returned to every thread; red must hold >= 33 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double t = (lane < nw) ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+__device__ __forceinline__ double block_max(double v, double* red) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double t = (lane < nw) ? red[lane] : 0.0;
+    t = warp_max(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Round-robin (circle method) pairing for parallel Jacobi sweeps over mm
+// (even) indices: round r in [0, mm-1), pair i in [0, mm/2).
+__device__ __forceinline__ void rr_pair(int mm, int r, int i, int* p, int* q) {
+  int a0 = (mm > 1) ? 1 + (r % (mm - 1)) : 0;
+  if (i == 0) { *p = 0; *q = a0; }
+  else {
+    int ai = 1 + ((i + r) % (mm - 1));
+    int aj = 1 + ((mm - 1 - i + r) % (mm - 1));
+    *p = ai; *q = aj;
+  }
+}
+
+}  // namespace dd

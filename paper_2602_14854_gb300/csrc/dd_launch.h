@@ -1,0 +1,93 @@
+// Host-side launch interface between the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "dd_internal.cuh"
+
+namespace dd {
+
+struct OrthArgs {
+  Geo g;
+  int spatial;            // rows are cells (1) or directions (0)
+  int mode;               // OrthMode
+  const double* A; int lda;
+  const int* acols;       // input columns per subdomain
+  double* W; int ldw;     // Householder workspace (same row layout as A)
+  double* Q; int ldq;     // output basis
+  const int* rout;        // output columns per subdomain (QR, COMPLETE)
+  const int* r_own;       // AUG: current stored rank
+  int* rt_out;            // AUG: chosen intermediate rank
+  int rank_mode; double tol; int r_floor; int r_aug_max;
+  double tau; double accept;
+  const double* angcand; int n_angcand; int angcand_complete;
+  double* sig_out; int* p_out;
+  unsigned* status;
+};
+
+size_t orth_smem_bytes();
+cudaError_t orth_init();
+void launch_orth(const OrthArgs& a, cudaStream_t st);
+
+// Phase kernels (dd_phase.cu).  All buffers follow the layout described in
+// dd_internal.cuh; "small" matrices are RC x RC blocks, per subdomain stride RC*RC.
+struct PhaseBufs {
+  // state (read) and state (write)
+  const double* X; const double* V; const double* S; const int* r;
+  double* Xo; double* Vo; double* So; int* ro;
+  // workspace
+  double* L0;      // angular rows, ld MC
+  double* Hw;      // Householder workspace, spatial rows, ld MC
+  double* Hwa;     // Householder workspace, angular rows, ld MC
+  double* Vh;      // angular rows, ld RC (augmented basis)
+  double* K;       // spatial rows, ld RC
+  double* X1;      // spatial rows, ld RC
+  double* L;       // angular rows, ld RC
+  double* V1;      // angular rows, ld RC
+  double* Kb;      // ghosts: nsub x 2 sides x maxlines x RC
+  double* sm;      // small matrices: nsub x NSMALL x RC*RC
+  double* part;    // partial sums for chunked reductions
+  int* m;          // L0 columns per subdomain
+  int* rt;         // intermediate rank
+  int* rx;         // last r_t of x / y phases (2*nsub)
+  int* rc;         // collision rank
+  double* sig;     // diagnostics
+  int* p;          // diagnostics
+  unsigned* status;
+};
+
+// indices of small matrices inside a subdomain's block of NSMALL matrices
+enum Small {
+  SM_C = 0, SM_MOUT_LO, SM_MOUT_HI, SM_M, SM_MIN_LO, SM_MIN_HI,   // angular Galerkin coefficients
+  SM_B, SM_B_LO, SM_B_HI,                                          // S M, S_lo Min_lo, S_hi Min_hi
+  SM_CP, SM_CM, SM_CABS,                                           // C+, C-, |C|
+  SM_S1, SM_T, SM_G_LO, SM_G_HI,                                   // S-step coefficients
+  SM_S2, SM_AP, SM_AM,                                             // S-step result, L-step matrices
+  SM_S3T, SM_UB, SM_VB,                                            // S3^T, truncation rotations
+  SM_MS, SM_MT, SM_VEC,                                            // collision: Ms, Mt, vectors (a, q, b-stages)
+  NSMALL
+};
+
+struct Problem {
+  Geo g;
+  int maxlines;           // longest line (max subdomain width or height)
+  int maxN;               // most cells in a subdomain
+  const double* ox; const double* oy; const double* w; const double* sw;
+  const double* sig_s; const double* sig_t; const double* sQ;  // per cell (spatial row order); sQ = sqrt(hx hy) Q
+  double hx, hy, sh, dt, c_adv, ssum;
+  int integrator;         // 0 Euler, 1 RK4
+  int rank_mode; double tol; double tau; double accept;
+  int r_floor, r_aug_max, RS;
+  int WC;                 // leading dimension of the Householder workspaces, max(MC, RC)
+  const double* angcand; int n_angcand; int angcand_complete;
+  int nchunk_sp, nchunk_ang;   // chunks of the two-stage reductions
+};
+
+void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st);
+void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st);
+void scalar_flux(const Problem& P, const double* X, const double* V, const double* S, const int* r,
+                 double* work, double* rho, int nx, cudaStream_t st);
+cudaError_t phase_init(const Problem& P);
+size_t part_elems(const Problem& P);
+
+}  // namespace dd

@@ -1,0 +1,1177 @@
+// Phase kernels of the DD-DLRA time step (FP64).
+//
+// advection_phase() runs, for every subdomain at once, Algorithm 4 (augmentation)
+// -> Algorithm 1 or 2 (projector-splitting integrator for x- or y-advection with
+// the inflow boundary data of Eq. (generate_Kboundary) and the eigen-upwind
+// K-step of Appendix A) -> Algorithm 5 (truncation).  collision_phase() runs
+// Algorithm 3.  Storage is the Euclidean-rescaled form described in
+// dd_internal.cuh: X = sqrt(hx hy) U, Vt = sqrt(w) V, S unchanged.
+//
+// Discrete operators (per subdomain, along the advection axis, h = cell width):
+//   K-step  dK/dt = -(c/h) [K |C| - K_prev C+ + K_next C-],  C = Vh^T diag(Omega) Vh,
+//           C+- the positive / negative parts of C (Appendix A: each eigenvector of
+//           C upwinded by the sign of its eigenvalue); K_prev/K_next take the
+//           frozen ghost rows K^b at the line ends.
+//   S-step  dS/dt = (c/h) [S |C| - (T S + G_lo) C+ + (T^T S + G_hi) C-],
+//           T = X^T shift_prev(X), G_lo/hi = X_face^T K^b_lo/hi  (the K-step
+//           operator projected on the new basis, Eq. (advx_evolS)).
+//   L-step  per direction q:  dL_q/dt = -(c Omega_q/h) [(I - T) L_q - G_lo Vh_q]  (Omega_q > 0)
+//                              dL_q/dt = -(c Omega_q/h) [(T^T - I) L_q + G_hi Vh_q] (Omega_q < 0)
+//           (per-direction upwinding of f = U L^T with ghost f^b = K^b V^T, Eq. (advx_evolL)).
+#include "dd_internal.cuh"
+#include "dd_launch.h"
+
+namespace dd {
+
+#define SMB(B, P, k, idx) ((B).sm + ((long)(k) * NSMALL + (idx)) * (long)(P).g.RC * (P).g.RC)
+
+namespace {
+
+__constant__ double c_rk_a[4] = {0.0, 0.5, 0.5, 1.0};
+__constant__ double c_rk_b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+
+// out[i][j] (+)= alpha * sum_l A[i][l] B[l][j], block-wide, threads over (i, j)
+__device__ void bmm(double* out, int ldo, double alpha, const double* A, int lda, const double* Bm,
+                    int ldb, int ni, int nj, int nl, bool accumulate) {
+  for (int e = threadIdx.x; e < ni * nj; e += blockDim.x) {
+    int i = e / nj, j = e % nj;
+    double s = 0.0;
+    for (int l = 0; l < nl; ++l) s += A[i * lda + l] * Bm[l * ldb + j];
+    out[i * ldo + j] = accumulate ? out[i * ldo + j] + alpha * s : alpha * s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// augmentation input  L0 = [Vt S^T, Vt_lo S_lo^T, Vt_hi S_hi^T]
+// ---------------------------------------------------------------------------
+__global__ void k_aug_cols(Geo g, const int* r, int axis, int* m) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= g.nsub) return;
+  int lo = g.nb[k * 4 + 2 * axis], hi = g.nb[k * 4 + 2 * axis + 1];
+  m[k] = r[k] + (lo >= 0 ? r[lo] : 0) + (hi >= 0 ? r[hi] : 0);
+}
+
+__global__ void k_build_L0(Geo g, const double* V, const double* S, const int* r, int axis,
+                           double* L0) {
+  extern __shared__ double sh[];
+  const int k = blockIdx.y, RC = g.RC;
+  const int lo = g.nb[k * 4 + 2 * axis], hi = g.nb[k * 4 + 2 * axis + 1];
+  const int src[3] = {k, lo, hi};
+  int rr[3];
+  for (int b = 0; b < 3; ++b) rr[b] = src[b] >= 0 ? r[src[b]] : 0;
+  // stage the three S blocks
+  for (int b = 0; b < 3; ++b)
+    for (int e = threadIdx.x; e < RC * RC; e += blockDim.x)
+      sh[b * RC * RC + e] = src[b] >= 0 ? S[(long)src[b] * RC * RC + e] : 0.0;
+  __syncthreads();
+  const int m = rr[0] + rr[1] + rr[2];
+  const int q0 = blockIdx.x * 32;
+  for (int e = threadIdx.x; e < 32 * m; e += blockDim.x) {
+    int q = q0 + e / m, col = e % m;
+    if (q >= g.n) continue;
+    int b = 0, t = col;
+    while (t >= rr[b]) { t -= rr[b]; ++b; }
+    const double* Vq = V + ((long)src[b] * g.n + q) * RC;
+    const double* Sb = sh + b * RC * RC + t * RC;     // row t of S_b
+    double s = 0.0;
+    for (int l = 0; l < rr[b]; ++l) s += Vq[l] * Sb[l];
+    L0[((long)k * g.n + q) * g.MC + col] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// angular Galerkin coefficients (partial sums over direction chunks)
+//   C = Vh^T diag(Om) Vh, Mout_lo = Vh^T diag(Om<0) Vh, Mout_hi = Vh^T diag(Om>=0) Vh,
+//   M = Vt^T Vh, Min_lo = Vt_lo^T diag(Om>=0) Vh, Min_hi = Vt_hi^T diag(Om<0) Vh
+// ---------------------------------------------------------------------------
+__global__ void k_ang_coeffs(Geo g, const double* om, const double* Vh, const double* V,
+                             const int* r, const int* rt, int axis, int nchunk, double* part) {
+  const int k = blockIdx.y, c = blockIdx.x, RC = g.RC, n = g.n;
+  const int ch = (n + nchunk - 1) / nchunk;
+  const int q0 = c * ch, q1 = min(n, q0 + ch);
+  const int lo = g.nb[k * 4 + 2 * axis], hi = g.nb[k * 4 + 2 * axis + 1];
+  const int rtk = rt[k], rk = r[k], rlo = lo >= 0 ? r[lo] : 0, rhi = hi >= 0 ? r[hi] : 0;
+  const double* Vhk = Vh + (long)k * n * RC;
+  const double* Vk = V + (long)k * n * RC;
+  const double* Vlo = V + (long)(lo >= 0 ? lo : 0) * n * RC;
+  const double* Vhi = V + (long)(hi >= 0 ? hi : 0) * n * RC;
+  double* out = part + ((long)k * nchunk + c) * 6 * RC * RC;
+  for (int o = threadIdx.x; o < 6 * RC * RC; o += blockDim.x) {
+    const int blk = o / (RC * RC), e = o % (RC * RC), i = e / RC, j = e % RC;
+    double s = 0.0;
+    if (j < rtk) {
+      switch (blk) {
+        case 0: if (i < rtk) for (int q = q0; q < q1; ++q) s += om[q] * Vhk[q * RC + i] * Vhk[q * RC + j]; break;
+        case 1: if (i < rtk) for (int q = q0; q < q1; ++q) if (om[q] < 0.0) s += Vhk[q * RC + i] * Vhk[q * RC + j]; break;
+        case 2: if (i < rtk) for (int q = q0; q < q1; ++q) if (om[q] >= 0.0) s += Vhk[q * RC + i] * Vhk[q * RC + j]; break;
+        case 3: if (i < rk) for (int q = q0; q < q1; ++q) s += Vk[q * RC + i] * Vhk[q * RC + j]; break;
+        case 4: if (i < rlo) for (int q = q0; q < q1; ++q) if (om[q] >= 0.0) s += Vlo[q * RC + i] * Vhk[q * RC + j]; break;
+        case 5: if (i < rhi) for (int q = q0; q < q1; ++q) if (om[q] < 0.0) s += Vhi[q * RC + i] * Vhk[q * RC + j]; break;
+      }
+    }
+    out[o] = s;
+  }
+}
+
+struct Dst { int idx[6]; };
+
+// Sum the chunk partials in fixed order into the small matrices.
+__global__ void k_reduce(const double* part, int nchunk, int nblk, Dst dst, double* sm, int RC) {
+  const int k = blockIdx.x;
+  for (int o = threadIdx.x; o < nblk * RC * RC; o += blockDim.x) {
+    const int b = o / (RC * RC), e = o % (RC * RC);
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += part[(((long)k * nchunk + c) * nblk + b) * RC * RC + e];
+    sm[((long)k * NSMALL + dst.idx[b]) * RC * RC + e] = s;
+  }
+}
+
+// Generic chunked Gram  G = A^T diag(w) B  over the rows of one subdomain.
+// spatial != 0: rows are the subdomain's cells; else its directions.
+// B may be a per-row vector (ldb = 1, bcols = 1).
+struct GramArgs {
+  int spatial;
+  const double* A; int lda; const int* acnt; int afix;
+  const double* Bm; int ldb; const int* bcnt; int bfix; int b_per_sub;  // b_per_sub: B has per-subdomain rows
+  const double* wrow;   // row weights (indexed like a per-row vector of the same layout), or null
+  double* part; int nchunk;
+};
+__global__ void k_gram(Geo g, GramArgs a) {
+  const int k = blockIdx.y, c = blockIdx.x, RC = g.RC;
+  const int rows = a.spatial ? g.N[k] : g.n;
+  const long rb = a.spatial ? (long)g.rowoff[k] : (long)k * g.n;
+  const long rbB = a.b_per_sub ? rb : 0;
+  const int ch = (rows + a.nchunk - 1) / a.nchunk;
+  const int i0 = c * ch, i1 = min(rows, i0 + ch);
+  const int na = a.acnt ? a.acnt[k] : a.afix, nbc = a.bcnt ? a.bcnt[k] : a.bfix;
+  double* out = a.part + ((long)k * a.nchunk + c) * RC * RC;
+  for (int o = threadIdx.x; o < RC * RC; o += blockDim.x) {
+    const int i = o / RC, j = o % RC;
+    double s = 0.0;
+    if (i < na && j < nbc)
+      for (int row = i0; row < i1; ++row) {
+        double wv = a.wrow ? a.wrow[rb + row] : 1.0;
+        s += a.A[(rb + row) * a.lda + i] * wv * a.Bm[(rbB + row) * a.ldb + j];
+      }
+    out[o] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// small per-subdomain algebra: B = S M, B_lo = S_lo Min_lo, B_hi = S_hi Min_hi,
+// Jacobi eigendecomposition of C -> C+, C-, |C|  (Appendix A)
+// ---------------------------------------------------------------------------
+__global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
+  extern __shared__ double sh[];
+  const int k = blockIdx.x, RC = P.g.RC;
+  const int lo = P.g.nb[k * 4 + 2 * axis], hi = P.g.nb[k * 4 + 2 * axis + 1];
+  const int rk = B.r[k], rt = B.rt[k];
+  const int rlo = lo >= 0 ? B.r[lo] : 0, rhi = hi >= 0 ? B.r[hi] : 0;
+  const double* Sk = B.S + (long)k * RC * RC;
+  // products (inputs read from global; outputs to the small buffers)
+  bmm(SMB(B, P, k, SM_B), RC, 1.0, Sk, RC, SMB(B, P, k, SM_M), RC, rk, rt, rk, false);
+  if (lo >= 0)
+    bmm(SMB(B, P, k, SM_B_LO), RC, 1.0, B.S + (long)lo * RC * RC, RC, SMB(B, P, k, SM_MIN_LO), RC,
+        rlo, rt, rlo, false);
+  if (hi >= 0)
+    bmm(SMB(B, P, k, SM_B_HI), RC, 1.0, B.S + (long)hi * RC * RC, RC, SMB(B, P, k, SM_MIN_HI), RC,
+        rhi, rt, rhi, false);
+  // Jacobi eigendecomposition of the symmetric rt x rt matrix C
+  double* Cm = sh;                  // RC*RC
+  double* Pm = sh + RC * RC;        // RC*RC (eigenvectors, row-major: Pm[i*RC + j] = P_ij)
+  double* cs = sh + 2 * RC * RC;    // RC/2 cosines
+  double* sn = cs + RC;             // RC/2 sines
+  const double* Csrc = SMB(B, P, k, SM_C);
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    int i = e / RC, j = e % RC;
+    Cm[e] = (i < rt && j < rt) ? 0.5 * (Csrc[i * RC + j] + Csrc[j * RC + i]) : 0.0;
+    Pm[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int mm = rt + (rt & 1);
+  for (int sweep = 0; sweep < 60 && rt > 1; ++sweep) {
+    // convergence: off-diagonal mass relative to the whole matrix
+    double off = 0.0, tot = 0.0;
+    for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
+      int i = e / rt, j = e % rt;
+      double x = Cm[i * RC + j];
+      tot += x * x;
+      if (i != j) off += x * x;
+    }
+    __shared__ double red[40];
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (off <= 1e-32 * tot) break;
+    for (int rnd = 0; rnd < mm - 1; ++rnd) {
+      for (int pi = threadIdx.x; pi < mm / 2; pi += blockDim.x) {
+        int p, q;
+        rr_pair(mm, rnd, pi, &p, &q);
+        double c = 1.0, s = 0.0;
+        if (p < rt && q < rt) {
+          double apq = Cm[p * RC + q];
+          if (apq != 0.0) {
+            double zeta = (Cm[q * RC + q] - Cm[p * RC + p]) / (2.0 * apq);
+            double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = c * t;
+          }
+        }
+        cs[pi] = c; sn[pi] = s;
+      }
+      __syncthreads();
+      // columns: C <- C J, P <- P J
+      for (int e = threadIdx.x; e < rt * (mm / 2); e += blockDim.x) {
+        int row = e / (mm / 2), pi = e % (mm / 2);
+        int p, q;
+        rr_pair(mm, rnd, pi, &p, &q);
+        if (p >= rt || q >= rt) continue;
+        double c = cs[pi], s = sn[pi];
+        double x = Cm[row * RC + p], y = Cm[row * RC + q];
+        Cm[row * RC + p] = c * x - s * y;
+        Cm[row * RC + q] = s * x + c * y;
+        x = Pm[row * RC + p]; y = Pm[row * RC + q];
+        Pm[row * RC + p] = c * x - s * y;
+        Pm[row * RC + q] = s * x + c * y;
+      }
+      __syncthreads();
+      // rows: C <- J^T C
+      for (int e = threadIdx.x; e < rt * (mm / 2); e += blockDim.x) {
+        int col = e / (mm / 2), pi = e % (mm / 2);
+        int p, q;
+        rr_pair(mm, rnd, pi, &p, &q);
+        if (p >= rt || q >= rt) continue;
+        double c = cs[pi], s = sn[pi];
+        double x = Cm[p * RC + col], y = Cm[q * RC + col];
+        Cm[p * RC + col] = c * x - s * y;
+        Cm[q * RC + col] = s * x + c * y;
+      }
+      __syncthreads();
+    }
+  }
+  // C+ = P diag(max(l,0)) P^T, C- = P diag(min(l,0)) P^T
+  double* Cp = SMB(B, P, k, SM_CP);
+  double* Cn = SMB(B, P, k, SM_CM);
+  double* Ca = SMB(B, P, k, SM_CABS);
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    int i = e / RC, j = e % RC;
+    double sp = 0.0, sm = 0.0;
+    if (i < rt && j < rt)
+      for (int l = 0; l < rt; ++l) {
+        double lam = Cm[l * RC + l];
+        double pp = Pm[i * RC + l] * Pm[j * RC + l];
+        if (lam > 0.0) sp += lam * pp;
+        else if (lam < 0.0) sm += lam * pp;
+      }
+    Cp[e] = sp; Cn[e] = sm; Ca[e] = sp - sm;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tall x small product  Y = A Bm  (per subdomain counts), zero-filled to ldy
+// ---------------------------------------------------------------------------
+struct TallArgs {
+  int spatial;
+  const double* A; int lda; const int* ninner; int ninner_fix;
+  const double* Bm; int bsmall;     // small matrix index inside the subdomain block (or -1: Bm is per-k RC*RC stride)
+  const int* ncols; int ncols_fix;
+  double* Y; int ldy;
+};
+__global__ void k_tall(Geo g, TallArgs a, double* smbase) {
+  extern __shared__ double sh[];
+  const int k = blockIdx.y, RC = g.RC;
+  const int rows = a.spatial ? g.N[k] : g.n;
+  const long rb = a.spatial ? (long)g.rowoff[k] : (long)k * g.n;
+  const int ni = a.ninner ? a.ninner[k] : a.ninner_fix;
+  const int nc = a.ncols ? a.ncols[k] : a.ncols_fix;
+  const double* Bk = (a.bsmall >= 0) ? smbase + ((long)k * NSMALL + a.bsmall) * RC * RC
+                                     : a.Bm + (long)k * RC * RC;
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) sh[e] = Bk[e];
+  __syncthreads();
+  const int r0 = blockIdx.x * 64;
+  for (int e = threadIdx.x; e < 64 * a.ldy; e += blockDim.x) {
+    int row = r0 + e / a.ldy, j = e % a.ldy;
+    if (row >= rows) continue;
+    double s = 0.0;
+    if (j < nc) {
+      const double* Ar = a.A + (rb + row) * a.lda;
+      for (int l = 0; l < ni; ++l) s += Ar[l] * sh[l * RC + j];
+    }
+    a.Y[(rb + row) * a.ldy + j] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// ghost rows (Eq. (generate_Kboundary)): K^b_lo = (X_lo S_lo)|face Min_lo + K|own lo face Mout_lo
+// ---------------------------------------------------------------------------
+__global__ void k_ghost(Problem P, PhaseBufs B, int axis) {
+  const int k = blockIdx.x, RC = P.g.RC;
+  const Lines L = lines_of(P.g, k, axis);
+  const int rt = B.rt[k];
+  for (int e = threadIdx.x; e < 2 * L.nlines * RC; e += blockDim.x) {
+    const int side = e / (L.nlines * RC), line = (e / RC) % L.nlines, t = e % RC;
+    double s = 0.0;
+    if (t < rt) {
+      const int nbk = P.g.nb[k * 4 + 2 * axis + side];
+      const double* Mout = SMB(B, P, k, side == 0 ? SM_MOUT_LO : SM_MOUT_HI);
+      const int own = cell_of(L, line, side == 0 ? 0 : L.len - 1);
+      const double* Kr = B.K + ((long)P.g.rowoff[k] + own) * RC;
+      for (int u = 0; u < rt; ++u) s += Kr[u] * Mout[u * RC + t];
+      if (nbk >= 0) {
+        const Lines Ln = lines_of(P.g, nbk, axis);
+        const int cell = cell_of(Ln, line, side == 0 ? Ln.len - 1 : 0);
+        const double* Xr = B.X + ((long)P.g.rowoff[nbk] + cell) * RC;
+        const double* Bb = SMB(B, P, k, side == 0 ? SM_B_LO : SM_B_HI);
+        const int rn = B.r[nbk];
+        for (int u = 0; u < rn; ++u) s += Xr[u] * Bb[u * RC + t];
+      }
+    }
+    B.Kb[(((long)k * 2 + side) * P.maxlines + line) * RC + t] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K-step of the advection (Appendix A), all RK stages fused; a CTA owns whole lines
+// ---------------------------------------------------------------------------
+#define KS_EPT 24
+__global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B, int axis, int lpb) {
+  extern __shared__ double sh[];
+  const int k = blockIdx.y, RC = P.g.RC;
+  const Lines L = lines_of(P.g, k, axis);
+  const int l0 = blockIdx.x * lpb;
+  if (l0 >= L.nlines) return;
+  const int nl = min(lpb, L.nlines - l0);
+  const int rt = B.rt[k];
+  const int len = L.len;
+  double* Cp = sh;
+  double* Cn = Cp + RC * RC;
+  double* Ca = Cn + RC * RC;
+  double* Glo = Ca + RC * RC;          // lpb x RC
+  double* Ghi = Glo + lpb * RC;
+  double* Kst = Ghi + lpb * RC;        // lpb x len x rt
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    Cp[e] = SMB(B, P, k, SM_CP)[e];
+    Cn[e] = SMB(B, P, k, SM_CM)[e];
+    Ca[e] = SMB(B, P, k, SM_CABS)[e];
+  }
+  for (int e = threadIdx.x; e < nl * RC; e += blockDim.x) {
+    int li = e / RC, t = e % RC;
+    Glo[e] = B.Kb[(((long)k * 2 + 0) * P.maxlines + l0 + li) * RC + t];
+    Ghi[e] = B.Kb[(((long)k * 2 + 1) * P.maxlines + l0 + li) * RC + t];
+  }
+  const int tot = nl * len * rt;
+  double k0[KS_EPT], acc[KS_EPT];
+  for (int i = 0; i < KS_EPT; ++i) {
+    int e = threadIdx.x + i * blockDim.x;
+    k0[i] = 0.0; acc[i] = 0.0;
+    if (e < tot) {
+      int li = e / (len * rt), pos = (e / rt) % len, t = e % rt;
+      int cell = cell_of(L, l0 + li, pos);
+      k0[i] = B.K[((long)P.g.rowoff[k] + cell) * RC + t];
+      Kst[e] = k0[i];
+    }
+  }
+  __syncthreads();
+  const double coef = -P.c_adv / (axis == 0 ? P.hx : P.hy);
+  const int nst = P.integrator == 1 ? 4 : 1;
+  for (int s = 0; s < nst; ++s) {
+    double kv[KS_EPT];
+    for (int i = 0; i < KS_EPT; ++i) {
+      int e = threadIdx.x + i * blockDim.x;
+      kv[i] = 0.0;
+      if (e < tot) {
+        int li = e / (len * rt), pos = (e / rt) % len, t = e % rt;
+        const double* Kc = Kst + (li * len + pos) * rt;
+        const double* Kp = pos > 0 ? Kc - rt : Glo + li * RC;
+        const double* Kn = pos < len - 1 ? Kc + rt : Ghi + li * RC;
+        double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        for (int u = 0; u < rt; ++u) {
+          a1 += Kc[u] * Ca[u * RC + t];
+          a2 += Kp[u] * Cp[u * RC + t];
+          a3 += Kn[u] * Cn[u * RC + t];
+        }
+        kv[i] = coef * (a1 - a2 + a3);
+      }
+    }
+    __syncthreads();
+    const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
+    const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
+    for (int i = 0; i < KS_EPT; ++i) {
+      int e = threadIdx.x + i * blockDim.x;
+      if (e < tot) {
+        acc[i] += bs * kv[i];
+        if (s + 1 < nst) Kst[e] = k0[i] + an * P.dt * kv[i];
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < KS_EPT; ++i) {
+    int e = threadIdx.x + i * blockDim.x;
+    if (e < tot) {
+      int li = e / (len * rt), pos = (e / rt) % len, t = e % rt;
+      int cell = cell_of(L, l0 + li, pos);
+      B.K[((long)P.g.rowoff[k] + cell) * RC + t] = k0[i] + P.dt * acc[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// spatial coefficients of the S- and L-steps (partial sums over cell chunks)
+//   S1 = X1^T K1, T = X1^T shift_prev(X1), G_lo = X1_loface^T K^b_lo, G_hi = X1_hiface^T K^b_hi
+// ---------------------------------------------------------------------------
+__global__ void k_sp_coeffs(Problem P, PhaseBufs B, int axis) {
+  const int k = blockIdx.y, c = blockIdx.x, RC = P.g.RC, nchunk = P.nchunk_sp;
+  const Lines L = lines_of(P.g, k, axis);
+  const int N = P.g.N[k];
+  const int ch = (N + nchunk - 1) / nchunk;
+  const int c0 = c * ch, c1 = min(N, c0 + ch);
+  const int rt = B.rt[k];
+  const double* X1 = B.X1 + (long)P.g.rowoff[k] * RC;
+  const double* K = B.K + (long)P.g.rowoff[k] * RC;
+  const double* Kb = B.Kb + (long)k * 2 * P.maxlines * RC;
+  double* out = B.part + ((long)k * nchunk + c) * 4 * RC * RC;
+  for (int o = threadIdx.x; o < 4 * RC * RC; o += blockDim.x) {
+    const int blk = o / (RC * RC), e = o % (RC * RC), i = e / RC, j = e % RC;
+    double s = 0.0;
+    if (i < rt && j < rt) {
+      for (int cell = c0; cell < c1; ++cell) {
+        int line, pos;
+        if (axis == 0) { line = cell / L.len; pos = cell % L.len; }
+        else { pos = cell / L.nlines; line = cell % L.nlines; }
+        const double xi = X1[(long)cell * RC + i];
+        if (blk == 0) s += xi * K[(long)cell * RC + j];
+        else if (blk == 1) { if (pos > 0) s += xi * X1[(long)(cell - L.stride_pos) * RC + j]; }
+        else if (blk == 2) { if (pos == 0) s += xi * Kb[(long)line * RC + j]; }
+        else { if (pos == L.len - 1) s += xi * Kb[((long)P.maxlines + line) * RC + j]; }
+      }
+    }
+    out[o] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S-step of the advection (small, one CTA per subdomain), and the L-step matrices
+// ---------------------------------------------------------------------------
+__global__ void k_sstep_adv(Problem P, PhaseBufs B, int axis) {
+  extern __shared__ double sh[];
+  const int k = blockIdx.x, RC = P.g.RC;
+  const int rt = B.rt[k];
+  double* S0 = sh;
+  double* Ss = S0 + RC * RC;
+  double* Ac = Ss + RC * RC;
+  double* U1 = Ac + RC * RC;
+  double* U2 = U1 + RC * RC;
+  double* F = U2 + RC * RC;
+  const double* T = SMB(B, P, k, SM_T);
+  const double* Glo = SMB(B, P, k, SM_G_LO);
+  const double* Ghi = SMB(B, P, k, SM_G_HI);
+  const double* Cp = SMB(B, P, k, SM_CP);
+  const double* Cn = SMB(B, P, k, SM_CM);
+  const double* Ca = SMB(B, P, k, SM_CABS);
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    S0[e] = SMB(B, P, k, SM_S1)[e];
+    Ss[e] = S0[e];
+    Ac[e] = 0.0;
+  }
+  __syncthreads();
+  const double coef = P.c_adv / (axis == 0 ? P.hx : P.hy);
+  const int nst = P.integrator == 1 ? 4 : 1;
+  for (int s = 0; s < nst; ++s) {
+    // U1 = T S + G_lo ; U2 = T^T S + G_hi
+    for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
+      int i = e / rt, j = e % rt;
+      double a1 = Glo[i * RC + j], a2 = Ghi[i * RC + j];
+      for (int l = 0; l < rt; ++l) {
+        a1 += T[i * RC + l] * Ss[l * RC + j];
+        a2 += T[l * RC + i] * Ss[l * RC + j];
+      }
+      U1[i * RC + j] = a1; U2[i * RC + j] = a2;
+    }
+    __syncthreads();
+    // F = coef (S |C| - U1 C+ + U2 C-)
+    for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
+      int i = e / rt, j = e % rt;
+      double f = 0.0;
+      for (int l = 0; l < rt; ++l)
+        f += Ss[i * RC + l] * Ca[l * RC + j] - U1[i * RC + l] * Cp[l * RC + j] + U2[i * RC + l] * Cn[l * RC + j];
+      F[i * RC + j] = coef * f;
+    }
+    __syncthreads();
+    const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
+    const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
+    for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
+      int i = e / rt, j = e % rt;
+      Ac[i * RC + j] += bs * F[i * RC + j];
+      if (s + 1 < nst) Ss[i * RC + j] = S0[i * RC + j] + an * P.dt * F[i * RC + j];
+    }
+    __syncthreads();
+  }
+  double* S2 = SMB(B, P, k, SM_S2);
+  double* Ap = SMB(B, P, k, SM_AP);
+  double* Am = SMB(B, P, k, SM_AM);
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    int i = e / RC, j = e % RC;
+    bool in = i < rt && j < rt;
+    S2[e] = in ? S0[e] + P.dt * Ac[e] : 0.0;
+    Ap[e] = in ? ((i == j ? 1.0 : 0.0) - T[i * RC + j]) : 0.0;
+    Am[e] = in ? (T[j * RC + i] - (i == j ? 1.0 : 0.0)) : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// L-step of the advection: every direction is an independent r_t-dimensional
+// linear ODE; one warp per direction, all RK stages fused.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B, int axis) {
+  extern __shared__ double sh[];
+  const int k = blockIdx.y, RC = P.g.RC, n = P.g.n;
+  const int rt = B.rt[k];
+  double* S2 = sh;
+  double* Ap = S2 + RC * RC;
+  double* Am = Ap + RC * RC;
+  double* Glo = Am + RC * RC;
+  double* Ghi = Glo + RC * RC;
+  double* wsp = Ghi + RC * RC;          // per warp: vh, L0, Ls, g  (4*RC)
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    S2[e] = SMB(B, P, k, SM_S2)[e];
+    Ap[e] = SMB(B, P, k, SM_AP)[e];
+    Am[e] = SMB(B, P, k, SM_AM)[e];
+    Glo[e] = SMB(B, P, k, SM_G_LO)[e];
+    Ghi[e] = SMB(B, P, k, SM_G_HI)[e];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* vh = wsp + warp * 4 * RC;
+  double* L0 = vh + RC;
+  double* Ls = L0 + RC;
+  double* gv = Ls + RC;
+  const double* om = axis == 0 ? P.ox : P.oy;
+  const double hinv = 1.0 / (axis == 0 ? P.hx : P.hy);
+  const int nst = P.integrator == 1 ? 4 : 1;
+  for (int q = blockIdx.x * 32 + warp; q < min(n, (int)(blockIdx.x + 1) * 32); q += nw) {
+    const double* Vq = B.Vh + ((long)k * n + q) * RC;
+    for (int t = lane; t < RC; t += 32) vh[t] = t < rt ? Vq[t] : 0.0;
+    __syncwarp();
+    const double oq = om[q];
+    const double* A = oq > 0.0 ? Ap : Am;
+    const double kap = -P.c_adv * oq * hinv;
+    double accv[2] = {0.0, 0.0}, l0v[2] = {0.0, 0.0};
+    for (int h = 0; h < 2; ++h) {
+      int i = lane + 32 * h;
+      if (i < rt) {
+        double s = 0.0, gg = 0.0;
+        for (int j = 0; j < rt; ++j) {
+          s += S2[i * RC + j] * vh[j];
+          if (oq > 0.0) gg -= Glo[i * RC + j] * vh[j];
+          else if (oq < 0.0) gg += Ghi[i * RC + j] * vh[j];
+        }
+        L0[i] = s; Ls[i] = s; gv[i] = gg; l0v[h] = s;
+      }
+    }
+    __syncwarp();
+    if (oq != 0.0) {
+      for (int s = 0; s < nst; ++s) {
+        double kv[2] = {0.0, 0.0};
+        for (int h = 0; h < 2; ++h) {
+          int i = lane + 32 * h;
+          if (i < rt) {
+            double a = gv[i];
+            for (int j = 0; j < rt; ++j) a += A[i * RC + j] * Ls[j];
+            kv[h] = kap * a;
+          }
+        }
+        __syncwarp();
+        const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
+        const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
+        for (int h = 0; h < 2; ++h) {
+          int i = lane + 32 * h;
+          if (i < rt) {
+            accv[h] += bs * kv[h];
+            if (s + 1 < nst) Ls[i] = l0v[h] + an * P.dt * kv[h];
+          }
+        }
+        __syncwarp();
+      }
+    }
+    double* Lq = B.L + ((long)k * n + q) * RC;
+    for (int h = 0; h < 2; ++h) {
+      int i = lane + 32 * h;
+      if (i < RC) Lq[i] = i < rt ? l0v[h] + P.dt * accv[h] : 0.0;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// truncation (Algorithm 5): SVD of S3 by one-sided Jacobi on the columns of S3^T
+// ---------------------------------------------------------------------------
+__global__ void k_trunc(Problem P, PhaseBufs B, int rank_fixed, int r_min, int r_max) {
+  extern __shared__ double sh[];
+  const int k = blockIdx.x, RC = P.g.RC;
+  const int rt = B.rt[k];
+  double* Bc = sh;                 // column-major, column j = column j of S3^T = row j of S3
+  double* Jc = Bc + RC * RC;       // column-major rotations
+  double* sig = Jc + RC * RC;
+  int* perm = reinterpret_cast<int*>(sig + RC);
+  int* iv = perm + RC;
+  const double* S3T = SMB(B, P, k, SM_S3T);
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    int col = e / RC, row = e % RC;
+    // B = S3^T: B[row][col] = S3T[row][col]
+    Bc[col * RC + row] = (row < rt && col < rt) ? S3T[row * RC + col] : 0.0;
+    Jc[col * RC + row] = (row == col) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int mm = rt + (rt & 1);
+  for (int sweep = 0; sweep < 60 && rt > 1; ++sweep) {
+    if (threadIdx.x == 0) iv[0] = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < mm - 1; ++rnd) {
+      for (int pi = warp; pi < mm / 2; pi += nwarps) {
+        int p, q;
+        rr_pair(mm, rnd, pi, &p, &q);
+        if (p >= rt || q >= rt) continue;
+        double* bp = Bc + p * RC;
+        double* bq = Bc + q * RC;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int l = lane; l < rt; l += 32) {
+          double x = bp[l], y = bq[l];
+          al += x * x; be += y * y; ga += x * y;
+        }
+        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        if (ga != 0.0 && fabs(ga) > 2.220446049250313e-16 * sqrt(al * be)) {
+          double zeta = (be - al) / (2.0 * ga);
+          double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          double* jp = Jc + p * RC;
+          double* jq = Jc + q * RC;
+          for (int l = lane; l < rt; l += 32) {
+            double x = bp[l], y = bq[l];
+            bp[l] = c * x - s * y; bq[l] = s * x + c * y;
+            x = jp[l]; y = jq[l];
+            jp[l] = c * x - s * y; jq[l] = s * x + c * y;
+          }
+          if (lane == 0) iv[0] = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (iv[0] == 0) break;
+    __syncthreads();
+  }
+  for (int j = warp; j < rt; j += nwarps) {
+    double s = 0.0;
+    for (int l = lane; l < rt; l += 32) s += Bc[j * RC + l] * Bc[j * RC + l];
+    s = warp_sum(s);
+    if (lane == 0) sig[j] = sqrt(s);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < rt; ++t) perm[t] = t;
+    for (int t = 0; t < rt; ++t) {
+      int best = t;
+      for (int u = t + 1; u < rt; ++u)
+        if (sig[perm[u]] > sig[perm[best]]) best = u;
+      int tmp = perm[t]; perm[t] = perm[best]; perm[best] = tmp;
+    }
+    int p = 0;
+    double s1 = rt > 0 ? sig[perm[0]] : 0.0;
+    if (s1 > 0.0)
+      for (int t = 0; t < rt; ++t)
+        if (sig[perm[t]] > P.tau * s1) ++p;
+    int r1;
+    if (P.rank_mode == 1) {
+      int rtail = rt;
+      for (int rr = 0; rr <= rt; ++rr) {
+        double ss = 0.0;
+        for (int t = rr; t < rt; ++t) ss += sig[perm[t]] * sig[perm[t]];
+        if (sqrt(ss) <= P.tol) { rtail = rr; break; }
+      }
+      r1 = min(max(rtail, r_min), r_max);
+    } else {
+      r1 = rank_fixed;
+    }
+    r1 = min(r1, p);
+    iv[1] = r1;
+    B.ro[k] = r1;
+  }
+  __syncthreads();
+  const int r1 = iv[1];
+  // S3 = J diag(sig) W^T with W = B J / sig: U_bar = J, V_bar = (B J)/sig
+  double* Ub = SMB(B, P, k, SM_UB);
+  double* Vb = SMB(B, P, k, SM_VB);
+  double* So = B.So + (long)k * RC * RC;
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    int i = e / RC, t = e % RC;
+    double u = 0.0, v = 0.0;
+    if (i < rt && t < r1) {
+      int c = perm[t];
+      u = Jc[c * RC + i];
+      v = Bc[c * RC + i] / sig[c];
+    }
+    Ub[e] = u; Vb[e] = v;
+    So[e] = (i == t && t < r1) ? sig[perm[t]] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// collision (Algorithm 3)
+// ---------------------------------------------------------------------------
+__global__ void k_coll_rank(Problem P, const int* r, int* rc) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P.g.nsub) return;
+  rc[k] = min(min(max(r[k], P.r_floor), P.g.n), P.g.N[k]);
+}
+
+// a = Vh^T sqrt(w)  (the paper's <V_j>_phi)
+__global__ void k_coll_a(Problem P, PhaseBufs B) {
+  const int k = blockIdx.x, RC = P.g.RC, n = P.g.n;
+  const int rc = B.rc[k];
+  __shared__ double red[40];
+  double* vec = SMB(B, P, k, SM_VEC);
+  for (int t = 0; t < RC; ++t) {
+    double s = 0.0;
+    if (t < rc)
+      for (int q = threadIdx.x; q < n; q += blockDim.x) s += B.Vh[((long)k * n + q) * RC + t] * P.sw[q];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) vec[t] = s;
+  }
+}
+
+// row-local collision K-step: dK_c/dt = (sig_s/|S|)(K_c . a) a - sig_t K_c + sQ_c a
+__global__ void k_coll_kstep(Problem P, PhaseBufs B) {
+  const int k = blockIdx.y, RC = P.g.RC;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int N = P.g.N[k], rc = B.rc[k];
+  const double* a = SMB(B, P, k, SM_VEC);
+  const int nst = P.integrator == 1 ? 4 : 1;
+  for (int cell = blockIdx.x * nw + warp; cell < N; cell += gridDim.x * nw) {
+    const long row = (long)P.g.rowoff[k] + cell;
+    const double ss = P.sig_s[row] / P.ssum, st = P.sig_t[row], sq = P.sQ[row];
+    double k0[2], ks[2], acc[2] = {0.0, 0.0}, av[2];
+    for (int h = 0; h < 2; ++h) {
+      int t = lane + 32 * h;
+      k0[h] = t < rc ? B.K[row * RC + t] : 0.0;
+      av[h] = t < rc ? a[t] : 0.0;
+      ks[h] = k0[h];
+    }
+    for (int s = 0; s < nst; ++s) {
+      double d = warp_sum(ks[0] * av[0] + ks[1] * av[1]);
+      double kv[2];
+      for (int h = 0; h < 2; ++h) kv[h] = ss * d * av[h] - st * ks[h] + sq * av[h];
+      const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
+      const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
+      for (int h = 0; h < 2; ++h) {
+        acc[h] += bs * kv[h];
+        ks[h] = k0[h] + an * P.dt * kv[h];
+      }
+    }
+    for (int h = 0; h < 2; ++h) {
+      int t = lane + 32 * h;
+      if (t < RC) B.K[row * RC + t] = t < rc ? k0[h] + P.dt * acc[h] : 0.0;
+    }
+  }
+}
+
+// collision S-step and the stage values b_s of the L-step's direction mean
+__global__ void k_coll_small(Problem P, PhaseBufs B) {
+  extern __shared__ double sh[];
+  const int k = blockIdx.x, RC = P.g.RC;
+  const int rc = B.rc[k];
+  double* vec = SMB(B, P, k, SM_VEC);   // row 0: a, row 1: q, rows 2..5: b stages
+  const double* Ms = SMB(B, P, k, SM_MS);
+  const double* Mt = SMB(B, P, k, SM_MT);
+  double* S0 = sh;
+  double* Ss = S0 + RC * RC;
+  double* Ac = Ss + RC * RC;
+  double* F = Ac + RC * RC;
+  double* Wv = F + RC * RC;             // Ss a  (RC)
+  double* mv = Wv + RC;                 // m stage (RC)
+  double* m0 = mv + RC;
+  double* km = m0 + RC;
+  double* qv = km + RC;                 // q = X1^T sQ, column 0 of the scratch block
+  const double* av = vec;
+  const double iS = 1.0 / P.ssum;
+  for (int i = threadIdx.x; i < RC; i += blockDim.x) qv[i] = i < rc ? SMB(B, P, k, SM_UB)[i * RC] : 0.0;
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    S0[e] = SMB(B, P, k, SM_S1)[e];
+    Ss[e] = S0[e];
+    Ac[e] = 0.0;
+  }
+  __syncthreads();
+  const int nst = P.integrator == 1 ? 4 : 1;
+  // S-step:  dS/dt = -[(1/|S|) Ms S a a^T - Mt S + q a^T]
+  for (int s = 0; s < nst; ++s) {
+    for (int i = threadIdx.x; i < rc; i += blockDim.x) {
+      double w = 0.0;
+      for (int j = 0; j < rc; ++j) w += Ss[i * RC + j] * av[j];
+      Wv[i] = w;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rc * rc; e += blockDim.x) {
+      int i = e / rc, j = e % rc;
+      double msw = 0.0, mts = 0.0;
+      for (int l = 0; l < rc; ++l) {
+        msw += Ms[i * RC + l] * Wv[l];
+        mts += Mt[i * RC + l] * Ss[l * RC + j];
+      }
+      F[i * RC + j] = -(iS * msw * av[j] - mts + qv[i] * av[j]);
+    }
+    __syncthreads();
+    const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
+    const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
+    for (int e = threadIdx.x; e < rc * rc; e += blockDim.x) {
+      int i = e / rc, j = e % rc;
+      Ac[i * RC + j] += bs * F[i * RC + j];
+      if (s + 1 < nst) Ss[i * RC + j] = S0[i * RC + j] + an * P.dt * F[i * RC + j];
+    }
+    __syncthreads();
+  }
+  double* S2 = SMB(B, P, k, SM_S2);
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    int i = e / RC, j = e % RC;
+    S2[e] = (i < rc && j < rc) ? S0[e] + P.dt * Ac[e] : 0.0;
+  }
+  __syncthreads();
+  // m0 = S2 a ; dm/dt = (Ms - Mt) m + |S| q ; b_s = (1/|S|) Ms m_s + q
+  for (int i = threadIdx.x; i < rc; i += blockDim.x) {
+    double w = 0.0;
+    for (int j = 0; j < rc; ++j) w += S2[i * RC + j] * av[j];
+    m0[i] = w; mv[i] = w;
+  }
+  __syncthreads();
+  for (int s = 0; s < nst; ++s) {
+    for (int i = threadIdx.x; i < rc; i += blockDim.x) {
+      double bsv = qv[i], d = P.ssum * qv[i];
+      for (int j = 0; j < rc; ++j) {
+        bsv += iS * Ms[i * RC + j] * mv[j];
+        d += (Ms[i * RC + j] - Mt[i * RC + j]) * mv[j];
+      }
+      vec[(2 + s) * RC + i] = bsv;
+      km[i] = d;
+    }
+    __syncthreads();
+    const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
+    for (int i = threadIdx.x; i < rc; i += blockDim.x) mv[i] = m0[i] + an * P.dt * km[i];
+    __syncthreads();
+  }
+}
+
+// collision L-step per direction:  dL_q/dt = sqrt(w_q) b(t) - Mt L_q
+__global__ void __launch_bounds__(DD_THREADS) k_coll_lstep(Problem P, PhaseBufs B) {
+  extern __shared__ double sh[];
+  const int k = blockIdx.y, RC = P.g.RC, n = P.g.n;
+  const int rc = B.rc[k];
+  double* S2 = sh;
+  double* Mt = S2 + RC * RC;
+  double* bst = Mt + RC * RC;         // 4 x RC
+  double* wsp = bst + 4 * RC;         // per warp: vh, Ls (2*RC)
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    S2[e] = SMB(B, P, k, SM_S2)[e];
+    Mt[e] = SMB(B, P, k, SM_MT)[e];
+  }
+  for (int e = threadIdx.x; e < 4 * RC; e += blockDim.x) bst[e] = SMB(B, P, k, SM_VEC)[2 * RC + e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* vh = wsp + warp * 2 * RC;
+  double* Ls = vh + RC;
+  const int nst = P.integrator == 1 ? 4 : 1;
+  for (int q = blockIdx.x * 32 + warp; q < min(n, (int)(blockIdx.x + 1) * 32); q += nw) {
+    const double* Vq = B.Vh + ((long)k * n + q) * RC;
+    for (int t = lane; t < RC; t += 32) vh[t] = t < rc ? Vq[t] : 0.0;
+    __syncwarp();
+    const double swq = P.sw[q];
+    double l0v[2] = {0.0, 0.0}, accv[2] = {0.0, 0.0};
+    for (int h = 0; h < 2; ++h) {
+      int i = lane + 32 * h;
+      if (i < rc) {
+        double s = 0.0;
+        for (int j = 0; j < rc; ++j) s += S2[i * RC + j] * vh[j];
+        l0v[h] = s; Ls[i] = s;
+      }
+    }
+    __syncwarp();
+    for (int s = 0; s < nst; ++s) {
+      double kv[2] = {0.0, 0.0};
+      for (int h = 0; h < 2; ++h) {
+        int i = lane + 32 * h;
+        if (i < rc) {
+          double a = swq * bst[s * RC + i];
+          for (int j = 0; j < rc; ++j) a -= Mt[i * RC + j] * Ls[j];
+          kv[h] = a;
+        }
+      }
+      __syncwarp();
+      const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
+      const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
+      for (int h = 0; h < 2; ++h) {
+        int i = lane + 32 * h;
+        if (i < rc) {
+          accv[h] += bs * kv[h];
+          if (s + 1 < nst) Ls[i] = l0v[h] + an * P.dt * kv[h];
+        }
+      }
+      __syncwarp();
+    }
+    double* Lq = B.L + ((long)k * n + q) * RC;
+    for (int h = 0; h < 2; ++h) {
+      int i = lane + 32 * h;
+      if (i < RC) Lq[i] = i < rc ? l0v[h] + P.dt * accv[h] : 0.0;
+    }
+    __syncwarp();
+  }
+}
+
+// S_out = (S3^T)^T, rank = r_c
+__global__ void k_coll_final(Problem P, PhaseBufs B) {
+  const int k = blockIdx.x, RC = P.g.RC;
+  const int rc = B.rc[k];
+  const double* S3T = SMB(B, P, k, SM_S3T);
+  double* So = B.So + (long)k * RC * RC;
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    int i = e / RC, j = e % RC;
+    So[e] = (i < rc && j < rc) ? S3T[j * RC + i] : 0.0;
+  }
+  if (threadIdx.x == 0) B.ro[k] = rc;
+}
+
+// ---------------------------------------------------------------------------
+// scalar flux  rho_c = X_c (S a) / sqrt(hx hy),  a = Vt^T sqrt(w)
+// ---------------------------------------------------------------------------
+__global__ void k_flux_prep(Problem P, const double* V, const double* S, const int* r, double* work) {
+  const int k = blockIdx.x, RC = P.g.RC, n = P.g.n;
+  const int rk = r[k];
+  __shared__ double red[40];
+  __shared__ double av[DD_MAXC];
+  for (int t = 0; t < rk; ++t) {
+    double s = 0.0;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) s += V[((long)k * n + q) * RC + t] * P.sw[q];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) av[t] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < RC; i += blockDim.x) {
+    double s = 0.0;
+    if (i < rk)
+      for (int j = 0; j < rk; ++j) s += S[(long)k * RC * RC + i * RC + j] * av[j];
+    work[(long)k * RC + i] = s;
+  }
+}
+
+__global__ void k_flux(Problem P, const double* X, const int* r, const double* work, double* rho,
+                       int nx) {
+  const int k = blockIdx.y, RC = P.g.RC;
+  const int N = P.g.N[k], rk = r[k], nxk = P.g.nxk[k];
+  const double* sa = work + (long)k * RC;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < N; cell += gridDim.x * blockDim.x) {
+    const double* Xr = X + ((long)P.g.rowoff[k] + cell) * RC;
+    double s = 0.0;
+    for (int t = 0; t < rk; ++t) s += Xr[t] * sa[t];
+    int il = cell % nxk, jl = cell / nxk;
+    rho[(long)(P.g.cy0[k] + jl) * nx + P.g.cx0[k] + il] = s / P.sh;
+  }
+}
+
+size_t kstep_smem(const Problem& P, int lpb, int len) {
+  const int RC = P.g.RC;
+  return sizeof(double) * (3 * RC * RC + 2 * lpb * RC + (size_t)lpb * len * RC);
+}
+
+int kstep_lpb(const Problem& P, int len) {
+  // lines per CTA: bounded by the register tile (KS_EPT per thread) and shared memory
+  const int RC = P.g.RC;
+  int lpb = max(1, (DD_THREADS * KS_EPT) / (len * RC));
+  while (lpb > 1 && kstep_smem(P, lpb, len) > 200 * 1024) --lpb;
+  return lpb;
+}
+
+}  // namespace
+
+size_t part_elems(const Problem& P) {
+  const int nc = P.nchunk_sp > P.nchunk_ang ? P.nchunk_sp : P.nchunk_ang;
+  return (size_t)P.g.nsub * nc * 6 * P.g.RC * P.g.RC;
+}
+
+cudaError_t phase_init(const Problem& P) {
+  const int RC = P.g.RC;
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_kstep_adv, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_sstep_adv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * 6 * RC * RC));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_lstep_adv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * (5 * RC * RC + 8 * 4 * RC)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_small_adv1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * (2 * RC * RC + 2 * RC) + 64));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_trunc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * (2 * RC * RC + RC) + sizeof(int) * (RC + 8)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_coll_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * (4 * RC * RC + 5 * RC)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_coll_lstep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_build_L0, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * 3 * RC * RC));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tall, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * RC * RC));
+  return e;
+}
+
+static void gram(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spatial,
+                 const double* A, int lda, const int* acnt, int afix, const double* Bm, int ldb,
+                 const int* bcnt, int bfix, int b_per_sub, const double* wrow, int dst_small) {
+  GramArgs a;
+  a.spatial = spatial; a.A = A; a.lda = lda; a.acnt = acnt; a.afix = afix;
+  a.Bm = Bm; a.ldb = ldb; a.bcnt = bcnt; a.bfix = bfix; a.b_per_sub = b_per_sub;
+  a.wrow = wrow; a.part = B.part; a.nchunk = spatial ? P.nchunk_sp : P.nchunk_ang;
+  k_gram<<<dim3(a.nchunk, P.g.nsub), DD_THREADS, 0, st>>>(P.g, a);
+  Dst d;
+  d.idx[0] = dst_small;
+  k_reduce<<<P.g.nsub, DD_THREADS, 0, st>>>(B.part, a.nchunk, 1, d, B.sm, P.g.RC);
+}
+
+static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spatial,
+                 const double* A, int lda, const int* ninner, int ninner_fix, const double* Bm,
+                 int bsmall, const int* ncols, int ncols_fix, double* Y, int ldy) {
+  TallArgs a;
+  a.spatial = spatial; a.A = A; a.lda = lda; a.ninner = ninner; a.ninner_fix = ninner_fix;
+  a.Bm = Bm; a.bsmall = bsmall; a.ncols = ncols; a.ncols_fix = ncols_fix; a.Y = Y; a.ldy = ldy;
+  const int rows = spatial ? P.maxN : P.g.n;
+  dim3 grid((rows + 63) / 64, P.g.nsub);
+  k_tall<<<grid, DD_THREADS, sizeof(double) * P.g.RC * P.g.RC, st>>>(P.g, a, B.sm);
+}
+
+static OrthArgs orth_args(const Problem& P, const PhaseBufs& B, int spatial, int mode) {
+  OrthArgs a;
+  a.g = P.g; a.spatial = spatial; a.mode = mode;
+  a.rank_mode = P.rank_mode; a.tol = P.tol; a.r_floor = P.r_floor; a.r_aug_max = P.r_aug_max;
+  a.tau = P.tau; a.accept = P.accept;
+  a.angcand = P.angcand; a.n_angcand = P.n_angcand; a.angcand_complete = P.angcand_complete;
+  a.sig_out = B.sig; a.p_out = B.p; a.status = B.status;
+  a.r_own = B.r; a.rt_out = B.rt;
+  a.W = spatial ? B.Hw : B.Hwa; a.ldw = P.WC;
+  return a;
+}
+
+void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st) {
+  const Geo& g = P.g;
+  const int RC = g.RC, nsub = g.nsub;
+  // 1. augmentation (Algorithm 4)
+  k_aug_cols<<<(nsub + 127) / 128, 128, 0, st>>>(g, B.r, axis, B.m);
+  k_build_L0<<<dim3((g.n + 31) / 32, nsub), DD_THREADS, sizeof(double) * 3 * RC * RC, st>>>(
+      g, B.V, B.S, B.r, axis, B.L0);
+  {
+    OrthArgs a = orth_args(P, B, 0, ORTH_AUG);
+    a.A = B.L0; a.lda = g.MC; a.acols = B.m; a.Q = B.Vh; a.ldq = RC; a.rout = nullptr;
+    launch_orth(a, st);
+  }
+  cudaMemcpyAsync(B.rx + axis * nsub, B.rt, sizeof(int) * nsub, cudaMemcpyDeviceToDevice, st);
+  // 2. angular Galerkin coefficients, boundary masses
+  k_ang_coeffs<<<dim3(P.nchunk_ang, nsub), DD_THREADS, 0, st>>>(
+      g, axis == 0 ? P.ox : P.oy, B.Vh, B.V, B.r, B.rt, axis, P.nchunk_ang, B.part);
+  {
+    Dst d;
+    d.idx[0] = SM_C; d.idx[1] = SM_MOUT_LO; d.idx[2] = SM_MOUT_HI;
+    d.idx[3] = SM_M; d.idx[4] = SM_MIN_LO; d.idx[5] = SM_MIN_HI;
+    k_reduce<<<nsub, DD_THREADS, 0, st>>>(B.part, P.nchunk_ang, 6, d, B.sm, RC);
+  }
+  // 3. S M products, eigen-split of C
+  k_small_adv1<<<nsub, DD_THREADS, sizeof(double) * (2 * RC * RC + 2 * RC) + 64, st>>>(P, B, axis);
+  // 4. K^0 = X (S <V, Vh>)
+  tall(P, B, st, 1, B.X, RC, B.r, 0, nullptr, SM_B, B.rt, 0, B.K, RC);
+  // 5. boundary data
+  k_ghost<<<nsub, DD_THREADS, 0, st>>>(P, B, axis);
+  // 6. K-step
+  {
+    const int len = P.maxlines;
+    const int lpb = kstep_lpb(P, len);
+    dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
+    k_kstep_adv<<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+  }
+  // 7. QR of K
+  {
+    OrthArgs a = orth_args(P, B, 1, ORTH_QR);
+    a.A = B.K; a.lda = RC; a.acols = B.rt; a.Q = B.X1; a.ldq = RC; a.rout = B.rt;
+    launch_orth(a, st);
+  }
+  // 8. S-step coefficients and S-step
+  k_sp_coeffs<<<dim3(P.nchunk_sp, nsub), DD_THREADS, 0, st>>>(P, B, axis);
+  {
+    Dst d;
+    d.idx[0] = SM_S1; d.idx[1] = SM_T; d.idx[2] = SM_G_LO; d.idx[3] = SM_G_HI;
+    k_reduce<<<nsub, DD_THREADS, 0, st>>>(B.part, P.nchunk_sp, 4, d, B.sm, RC);
+  }
+  k_sstep_adv<<<nsub, DD_THREADS, sizeof(double) * 6 * RC * RC, st>>>(P, B, axis);
+  // 9. L-step
+  k_lstep_adv<<<dim3((g.n + 31) / 32, nsub), DD_THREADS, sizeof(double) * (5 * RC * RC + 8 * 4 * RC),
+                st>>>(P, B, axis);
+  // 10. QR of L
+  {
+    OrthArgs a = orth_args(P, B, 0, ORTH_QR);
+    a.A = B.L; a.lda = RC; a.acols = B.rt; a.Q = B.V1; a.ldq = RC; a.rout = B.rt;
+    launch_orth(a, st);
+  }
+  gram(P, B, st, 0, B.V1, RC, B.rt, 0, B.L, RC, B.rt, 0, 1, nullptr, SM_S3T);
+  // 11. truncation (Algorithm 5)
+  k_trunc<<<nsub, DD_THREADS, sizeof(double) * (2 * RC * RC + RC) + sizeof(int) * (RC + 8), st>>>(
+      P, B, P.RS, P.r_floor, P.RS);
+  tall(P, B, st, 1, B.X1, RC, B.rt, 0, nullptr, SM_UB, B.ro, 0, B.Xo, RC);
+  tall(P, B, st, 0, B.V1, RC, B.rt, 0, nullptr, SM_VB, B.ro, 0, B.Vo, RC);
+}
+
+void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
+  const Geo& g = P.g;
+  const int RC = g.RC, nsub = g.nsub;
+  k_coll_rank<<<(nsub + 127) / 128, 128, 0, st>>>(P, B.r, B.rc);
+  {
+    OrthArgs a = orth_args(P, B, 0, ORTH_COMPLETE);
+    a.A = B.V; a.lda = RC; a.acols = B.r; a.Q = B.Vh; a.ldq = RC; a.rout = B.rc;
+    launch_orth(a, st);
+  }
+  k_coll_a<<<nsub, DD_THREADS, 0, st>>>(P, B);
+  tall(P, B, st, 1, B.X, RC, B.r, 0, B.S, -1, B.rc, 0, B.K, RC);
+  k_coll_kstep<<<dim3(64, nsub), DD_THREADS, 0, st>>>(P, B);
+  {
+    OrthArgs a = orth_args(P, B, 1, ORTH_QR);
+    a.A = B.K; a.lda = RC; a.acols = B.rc; a.Q = B.Xo; a.ldq = RC; a.rout = B.rc;
+    launch_orth(a, st);
+  }
+  gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.K, RC, B.rc, 0, 1, nullptr, SM_S1);
+  gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.Xo, RC, B.rc, 0, 1, P.sig_s, SM_MS);
+  gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.Xo, RC, B.rc, 0, 1, P.sig_t, SM_MT);
+  // q = X1^T sQ  -> row 1 of the vector block (reduce into a scratch small, then copy)
+  {
+    GramArgs a;
+    a.spatial = 1; a.A = B.Xo; a.lda = RC; a.acnt = B.rc; a.afix = 0;
+    a.Bm = P.sQ; a.ldb = 1; a.bcnt = nullptr; a.bfix = 1; a.b_per_sub = 1;
+    a.wrow = nullptr; a.part = B.part; a.nchunk = P.nchunk_sp;
+    k_gram<<<dim3(a.nchunk, nsub), DD_THREADS, 0, st>>>(g, a);
+    Dst d;
+    d.idx[0] = SM_UB;   // scratch: column 0 holds q
+    k_reduce<<<nsub, DD_THREADS, 0, st>>>(B.part, a.nchunk, 1, d, B.sm, RC);
+  }
+  k_coll_small<<<nsub, DD_THREADS, sizeof(double) * (4 * RC * RC + 5 * RC), st>>>(P, B);
+  k_coll_lstep<<<dim3((g.n + 31) / 32, nsub), DD_THREADS,
+                 sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC), st>>>(P, B);
+  {
+    OrthArgs a = orth_args(P, B, 0, ORTH_QR);
+    a.A = B.L; a.lda = RC; a.acols = B.rc; a.Q = B.Vo; a.ldq = RC; a.rout = B.rc;
+    launch_orth(a, st);
+  }
+  gram(P, B, st, 0, B.Vo, RC, B.rc, 0, B.L, RC, B.rc, 0, 1, nullptr, SM_S3T);
+  k_coll_final<<<nsub, DD_THREADS, 0, st>>>(P, B);
+}
+
+void scalar_flux(const Problem& P, const double* X, const double* V, const double* S, const int* r,
+                 double* work, double* rho, int nx, cudaStream_t st) {
+  k_flux_prep<<<P.g.nsub, DD_THREADS, 0, st>>>(P, V, S, r, work);
+  k_flux<<<dim3(16, P.g.nsub), DD_THREADS, 0, st>>>(P, X, r, work, rho, nx);
+}
+
+}  // namespace dd

@@ -1,0 +1,167 @@
+"""Parity of the CUDA DD-DLRA step (through the C ABI) with the CPU oracle.
+
+FP64 throughout: the scalar flux must match the oracle to rel-L2 <= 1e-9 and
+the stored ranks exactly.  Full factor products f = U S V^T are compared where
+the problem is small enough to form them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dd_dlra
+from paper_2602_14854_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    from paper_2602_14854_gb300 import binding, build
+    assert torch.cuda.is_available()
+    build.build()
+    binding.load()
+    return binding
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def full_f(solver, wl):
+    subs = dd_dlra.make_subdomains(wl)
+    f = np.zeros((wl.ncells, wl.n))
+    for s in subs:
+        U, S, V = solver.get_factors(s.k)
+        if S.shape[0]:
+            f[dd_dlra.cell_index(wl, s)] = U @ S @ V.T
+    return f
+
+
+def run_both(B, wl, nsteps=None, state=None, use_graph=False):
+    nst = wl.nsteps if nsteps is None else nsteps
+    s = B.Solver(wl, use_graph=use_graph)
+    o = dd_dlra.DDDLRA(wl)
+    if state is not None:
+        o.set_state(state)
+        for k, (U, S, V) in enumerate(state):
+            s.set_factors(k, U, S, V)
+    s.step(nst)
+    o.run(nst)
+    return s, o
+
+
+@pytest.mark.parametrize("integrator", ["euler", "rk4"])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_small_random_problem(B, integrator, seed):
+    """8x8 cells, 2x2 subdomains, 16 directions, rank 3 (r_t <= 6), heterogeneous
+    random materials and source; several steps."""
+    wl = inputs.random_small_problem(seed, nx=8, ny=8, n_mu=2, n_phi=8, rank=3, r_aug_max=6,
+                                     integrator=integrator, nsteps=4)
+    s, o = run_both(B, wl)
+    st, _ = s.ranks()
+    assert list(st) == o.ranks()
+    f_gpu, f_ref = full_f(s, wl), o.full_f().reshape(wl.ncells, wl.n)
+    assert rel(f_gpu, f_ref) < TOL
+    assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+
+
+def test_ragged_tiling(B):
+    """Uneven block tiling (subdomains of 3, 5 and 8 cells per side)."""
+    wl = inputs.random_small_problem(3, nx=13, ny=11, n_mu=2, n_phi=8, rank=3, r_aug_max=6,
+                                     integrator="rk4", nsteps=3, xcuts=[0, 5, 13],
+                                     ycuts=[0, 3, 11])
+    s, o = run_both(B, wl)
+    assert list(s.ranks()[0]) == o.ranks()
+    assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+
+
+@pytest.mark.parametrize("integrator", ["euler", "rk4"])
+def test_gaussian_32(B, integrator):
+    """The small Gaussian workload: 32x32 cells, 2x2 subdomains, 128 directions,
+    rank 5, 50 steps (Euler as stated for it; RK4 as in the paper)."""
+    wl = inputs.config_c0(integrator=integrator)
+    s, o = run_both(B, wl)
+    assert list(s.ranks()[0]) == o.ranks()
+    assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+
+
+def test_graph_replay_matches_stream(B):
+    wl = inputs.config_c0(nsteps=6, integrator="rk4")
+    a = B.Solver(wl, use_graph=False)
+    g = B.Solver(wl, use_graph=True)
+    a.step(6)
+    g.step(6)
+    assert rel(g.scalar_flux(), a.scalar_flux()) < 1e-14
+    a.close()
+    g.close()
+
+
+def test_tolerance_mode_checkerboard(B):
+    """Rank-adaptive run (absolute tolerance) on a small checkerboard of absorbing
+    and scattering blocks with a central source."""
+    wl = inputs.checkerboard_problem(blocks=3, cells_per_block=8, n_mu=4, n_phi=8, t_end=0.5,
+                                     tol=1e-4, r_aug_max=16).with_(r_min=2, r_max=5)
+    s, o = run_both(B, wl)
+    assert list(s.ranks()[0]) == o.ranks()
+    assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+
+
+def test_source_enters_zero_state(B):
+    """No material, zero data: one step gives rho = dt |S| Q."""
+    wl = inputs.random_small_problem(6, nx=8, ny=8, n_mu=2, n_phi=8, rank=3, r_aug_max=6,
+                                     nsteps=1)
+    nc = wl.ncells
+    wl = wl.with_(sigma_s=np.zeros(nc), sigma_a=np.zeros(nc), g0=np.zeros(nc))
+    s = B.Solver(wl)
+    s.step(1)
+    expect = wl.dt * np.sum(wl.w) * wl.source
+    assert np.max(np.abs(s.scalar_flux() - expect)) < 1e-14
+    s.close()
+
+
+def test_set_factors_reparametrisation(B):
+    """Random rank-3 start set through the ABI; a rotated copy of the same factors
+    gives the same result; both match the oracle."""
+    wl = inputs.random_small_problem(7, nx=8, ny=8, n_mu=2, n_phi=8, rank=3, r_aug_max=6,
+                                     integrator="rk4", nsteps=2)
+    o = dd_dlra.DDDLRA(wl)
+    state = []
+    rng = np.random.default_rng(5)
+    for sub in o.subs:
+        U, S, V = inputs.random_factors(50 + sub.k, sub.N, wl.n, 3, wl.hx, wl.hy, wl.w)
+        state.append((U, S, V))
+    rot = []
+    for (U, S, V) in state:
+        Th = np.linalg.qr(rng.standard_normal((3, 3)))[0]
+        Ph = np.linalg.qr(rng.standard_normal((3, 3)))[0]
+        rot.append((U @ Th, Th.T @ S @ Ph, V @ Ph))
+    s1, o1 = run_both(B, wl, state=state)
+    s2, _ = run_both(B, wl, state=rot)
+    assert rel(s1.scalar_flux(), o1.scalar_flux()) < TOL
+    assert rel(s2.scalar_flux(), o1.scalar_flux()) < TOL
+    s1.close()
+    s2.close()
+
+
+def test_pointsource_full_size(B):
+    """The benchmarked workload at full size (128x128 cells, 4x4 subdomains, 512
+    directions, rank 10, RK4, 86 steps to t = 1), in the launch configuration the
+    benchmark times (graph replay), against the stored oracle result."""
+    gold = np.load(os.path.join(HERE, "golden", "pointsource_128_rk4_t1.npz"))
+    wl = inputs.config_c1()
+    assert int(gold["nsteps"]) == wl.nsteps
+    s = B.Solver(wl, use_graph=True)
+    s.step(wl.nsteps)
+    rho = s.scalar_flux()
+    assert list(s.ranks()[0]) == list(gold["ranks"])
+    assert rel(rho, gold["rho"]) < TOL
+    s.close()

@@ -1,0 +1,36 @@
+"""The C-ABI library builds, loads and exports every symbol include/ddlra.h declares
+(no GPU needed: nothing is computed)."""
+import os
+import re
+
+import pytest
+
+from paper_2602_14854_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "ddlra.h")).read()
+    return sorted(set(re.findall(r"\b(dd_\w+)\s*\(", txt)))
+
+
+def test_header_and_binding_agree():
+    assert header_symbols() == sorted(binding.EXPORTS)
+
+
+def test_library_exports_every_symbol():
+    path = build.build()
+    lib = binding.load(path)
+    for name in header_symbols():
+        assert hasattr(lib, name), name
+    assert lib.dd_last_error() == b""
+
+
+def test_create_rejects_bad_arguments():
+    """Argument checks run before any device call."""
+    import ctypes as C
+    lib = binding.load(build.build())
+    h = C.c_void_p()
+    st = lib.dd_dlra_create(None, None, None, None, None, None, None, C.byref(h))
+    assert st == 1 and b"null" in lib.dd_last_error()
