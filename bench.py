@@ -1,0 +1,345 @@
+"""Benchmark of the DD-DLRA time step on one GB300.
+
+A "step" is one time step of the domain-decomposition dynamical low-rank
+scheme (Algorithm 6: x-augmentation, x-advection, truncation, the same in y,
+then absorption/scattering/source) on every subdomain of the point-source
+workload: [-1.5,1.5]^2, 128x128 cells, 4x4 subdomains of 32x32, 512 directions
+(16 mu x 32 phi), rank 10 (intermediate rank <= 20), RK4, dt = 1/86.
+
+Metric: phase-space (cell x direction) updates per second =
+cells * directions * steps / time, FP64, with the scalar-flux rel-L2 error of
+a full run (86 steps to t = 1) against the stored CPU-oracle result.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The default arm times the CUDA library through the C ABI; ``--impl reference``
+times the CPU oracle (the plain FP64 restatement of the paper) on this
+machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "phase-space cell×direction updates/s; mixed vs FP64 at stated flux rel-L2 error"
+UNIT = "cell-direction updates/s"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "pointsource_128_rk4_t1.npz")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self._proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                          text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self._proc = None
+        return self
+
+    def _read(self):
+        for line in self._proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for nm, v in zip(names, s[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp64_gemm_peak(torch):
+    """Dense FP64 throughput of cuBLAS (torch.matmul, 8192^3) on this GPU, TFLOP/s."""
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def kernel_work(name, wl, rt, rs):
+    """Algorithmic FP64 flops of one launch of a kernel class on this workload
+    (rt: intermediate rank, rs: stored rank; uniform subdomains)."""
+    nsub = wl.nsub
+    N = wl.ncells // nsub
+    n = wl.n
+    st = 4 if wl.integrator == "rk4" else 1
+    if name == "k_kstep_adv":      # 3 r_t x r_t products per cell per stage
+        return nsub * N * 3 * 2 * rt * rt * st
+    if name == "k_lstep_adv":      # (r_t x r_t) matvec per direction per stage + S2 v
+        return nsub * n * (2 * rt * rt * st + 4 * rt * rt)
+    return None
+
+
+def run_ours(args, torch):
+    from paper_2602_14854_gb300 import binding, build
+    from paper_2602_14854_gb300 import inputs
+
+    ws, rank, local = dist_env()
+    build.build()
+    binding.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = inputs.config_c1()
+    units = wl.ncells * wl.n
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+
+    # ---- timed: graph-replayed steps, L2 flushed between steps -------------------------
+    s = binding.Solver(wl, stream=sptr, use_graph=True)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            s.step(1)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_ours = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([t_ours], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ours = float(t.item())
+    value = units * args.steps * ws / t_ours
+
+    # ---- per-kernel profile (event pair around every launch), 4 steps ------------------
+    prof = s.profile(4)
+    st_r, it_r = s.ranks()
+    s.close()
+    total = sum(v[0] for v in prof.values())
+    launches_per_step = sum(v[1] for v in prof.values()) / 4.0
+    top = max(prof.items(), key=lambda kv: kv[1][0])
+
+    # ---- accuracy of a full run against the stored oracle result ----------------------
+    err = None
+    if os.path.exists(GOLDEN):
+        g = np.load(GOLDEN)
+        s2 = binding.Solver(wl, stream=sptr, use_graph=True)
+        s2.step(wl.nsteps)
+        rho = s2.scalar_flux()
+        s2.close()
+        err = float(np.linalg.norm(rho - g["rho"]) / np.linalg.norm(g["rho"]))
+
+    # ---- end to end through the public API with host buffers ---------------------------
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s3 = binding.Solver(wl, stream=sptr, use_graph=True)
+    out = None
+    for _ in range(args.steps):
+        s3.step(1)
+        out = s3.scalar_flux()          # device -> host read of the step's result
+    s3.close()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    h2d = 8 * (3 * wl.ncells + wl.ncells + 3 * wl.n) + 4 * (len(wl.xcuts) + len(wl.ycuts))
+    e2e = {"value": units * args.steps * ws / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 8 * wl.ncells,
+           "note": "create (problem data upload) + per step: step + scalar flux to host + destroy"}
+    del out
+
+    # ---- roofline of the dominant kernel -----------------------------------------------
+    peaks = measured_peaks()
+    fp64_peak = fp64_gemm_peak(torch)
+    rt = int(np.max(it_r)) if it_r.size else wl.r_aug_max
+    rs = int(np.max(st_r)) if st_r.size else wl.rank
+    name, (ms, cnt) = top
+    work = kernel_work(name, wl, rt, rs)
+    roof = {"kernel": name, "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak,
+            "peak_source": "cuBLAS FP64 GEMM 8192^3 measured in this run",
+            "share_of_step": ms / total, "launch_ms": ms / cnt, "traffic": None}
+    if work is not None:
+        ach = work / (ms / cnt / 1e3) / 1e12
+        roof.update({"achieved": ach, "frac": ach / fp64_peak, "work_flops_per_launch": work})
+    else:
+        roof.update({"achieved": None, "frac": None,
+                     "note": "latency-bound one-CTA-per-subdomain kernel; no FLOP roofline"})
+    kstep = prof.get("k_kstep_adv")
+    if kstep:
+        w = kernel_work("k_kstep_adv", wl, rt, rs)
+        roof["k_kstep_adv"] = {"launch_ms": kstep[0] / kstep[1],
+                               "achieved_tflops": w / (kstep[0] / kstep[1] / 1e3) / 1e12,
+                               "frac": w / (kstep[0] / kstep[1] / 1e3) / 1e12 / fp64_peak}
+    roof["kernels_ms_per_step"] = {k: v[0] / 4.0 for k, v in sorted(prof.items(),
+                                                                      key=lambda kv: -kv[1][0])}
+
+    # ---- CPU baseline: the oracle on this machine's host cores ------------------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(wl, nsteps=args.cpu_steps)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ours / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "cells": wl.ncells, "directions": wl.n,
+                   "subdomains": wl.nsub, "rank": wl.rank, "r_aug_max": wl.r_aug_max,
+                   "integrator": wl.integrator, "dt": wl.dt, "parallelism": f"replicas{ws}",
+                   "l2": "flushed between timed steps (256 MiB write, outside the step events)",
+                   "launch": "one CUDA graph per step"},
+        "flux_rel_l2_vs_oracle": err,
+        "ranks": {"stored_max": rs, "intermediate_max": rt},
+        "e2e": e2e,
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops"),
+                  "fp64_gemm_tflops": fp64_peak},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    return line, rank
+
+
+def cpu_baseline(wl, nsteps=3):
+    from oracle import dd_dlra
+    o = dd_dlra.DDDLRA(wl)
+    o.step()                                # first step excluded (start-up)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        o.step()
+    t = time.perf_counter() - t0
+    return {"value": wl.ncells * wl.n * nsteps / t, "unit": UNIT,
+            "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{nsteps} time steps (steps 2..{nsteps + 1}) of the {wl.name} workload, "
+                      f"numpy FP64 with multithreaded BLAS, {t:.1f} s"}
+
+
+def run_reference(args):
+    """The CPU oracle timed as the reference arm (rank 0 only)."""
+    from paper_2602_14854_gb300 import inputs
+    from oracle import dd_dlra
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None, rank
+    wl = inputs.config_c1()
+    o = dd_dlra.DDDLRA(wl)
+    for _ in range(args.warmup):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step()
+    t = time.perf_counter() - t0
+    value = wl.ncells * wl.n * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "cells": wl.ncells, "directions": wl.n,
+                       "subdomains": wl.nsub, "rank": wl.rank, "integrator": wl.integrator},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"{args.steps} full time steps after {args.warmup} warm-up "
+                                       f"steps of {wl.name}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    return line, rank
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        if ws > 1 and rank != 0:
+            return
+        line, rank = run_reference(args)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    import torch
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    line, rank = run_ours(args, torch)
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -148,6 +148,19 @@ dd_status dd_dlra_get_factors(dd_dlra_t h, int k, double* U, double* S, double* 
 dd_status dd_dlra_set_factors(dd_dlra_t h, int k, int r, const double* U, const double* S,
                               const double* V);
 
+/*
+ * Instrumentation (no counterpart in the paper).  dd_dlra_profile runs nsteps
+ * time steps without the CUDA graph, with a CUDA event pair recorded around
+ * every kernel launch, and accumulates per kernel function (slot) the total
+ * device milliseconds (ms, dd_profile_slots() doubles) and the launch count
+ * (launches, dd_profile_slots() ints).  It advances the solver like
+ * dd_dlra_step and synchronises.  dd_profile_slot_name returns a static name,
+ * or NULL for an out-of-range slot.
+ */
+int dd_profile_slots(void);
+const char* dd_profile_slot_name(int slot);
+dd_status dd_dlra_profile(dd_dlra_t h, int nsteps, double* ms, int* launches);
+
 /* Wait for the solver's stream and report any device-side error. */
 dd_status dd_dlra_sync(dd_dlra_t h);
 

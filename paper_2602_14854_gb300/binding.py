@@ -24,7 +24,8 @@ DD_FP64 = 0
 # every symbol include/ddlra.h declares
 EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scalar_flux",
            "dd_dlra_ranks", "dd_dlra_info", "dd_dlra_get_factors", "dd_dlra_set_factors",
-           "dd_dlra_sync", "dd_dlra_destroy", "dd_last_error"]
+           "dd_dlra_sync", "dd_dlra_destroy", "dd_last_error", "dd_profile_slots",
+           "dd_profile_slot_name", "dd_dlra_profile"]
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -82,8 +83,12 @@ def load(path: str | None = None):
     lib.dd_dlra_destroy.argtypes = [vp]
     lib.dd_dlra_destroy.restype = None
     lib.dd_last_error.restype = C.c_char_p
+    lib.dd_profile_slots.argtypes = []
+    lib.dd_profile_slot_name.argtypes = [C.c_int]
+    lib.dd_profile_slot_name.restype = C.c_char_p
+    lib.dd_dlra_profile.argtypes = [vp, C.c_int, _dp, _ip]
     for name in EXPORTS:
-        if name not in ("dd_dlra_destroy", "dd_last_error"):
+        if name not in ("dd_dlra_destroy", "dd_last_error", "dd_profile_slot_name"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -187,6 +192,20 @@ class Solver:
         U, S, V = _d(U), _d(S), _d(V)
         r = S.shape[0]
         _check(self.lib, self.lib.dd_dlra_set_factors(self.h, k, r, _ptr(U), _ptr(S), _ptr(V)))
+
+    def profile(self, nsteps: int):
+        """Advance nsteps steps with a CUDA event pair around every kernel launch;
+        returns {kernel: (total_ms, launches)}."""
+        ns = self.lib.dd_profile_slots()
+        ms = np.zeros(ns)
+        cnt = np.zeros(ns, dtype=np.int32)
+        _check(self.lib, self.lib.dd_dlra_profile(self.h, int(nsteps), _ptr(ms),
+                                                   cnt.ctypes.data_as(_ip)))
+        out = {}
+        for i in range(ns):
+            if cnt[i]:
+                out[self.lib.dd_profile_slot_name(i).decode()] = (float(ms[i]), int(cnt[i]))
+        return out
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -396,11 +396,21 @@ dd_status dd_dlra_step(dd_dlra_t h, int nsteps) {
   if (!h || nsteps < 0) return fail(DD_ERR_ARG, "bad argument");
   if (h->use_graph) {
     if (!h->graph_ready) {
+      // capture on a private stream (the legacy default stream cannot be captured);
+      // the instantiated graph is then launched on the solver's stream
+      cudaStream_t user = h->stream, cap;
+      DD_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
       cudaGraph_t graph;
-      DD_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-      enqueue_step(h);
-      DD_CUDA(cudaStreamEndCapture(h->stream, &graph));
-      cudaError_t e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+      h->stream = cap;
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        enqueue_step(h);
+        e = cudaStreamEndCapture(cap, &graph);
+      }
+      h->stream = user;
+      cudaStreamDestroy(cap);
+      if (e != cudaSuccess) return fail(DD_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return fail(DD_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(e));
       h->graph_ready = true;
@@ -494,6 +504,47 @@ dd_status dd_dlra_set_factors(dd_dlra_t h, int k, int r, const double* U, const 
                      cudaMemcpyHostToDevice));
   DD_CUDA(cudaMemcpy(h->d_r[0] + k, &r, sizeof(int), cudaMemcpyHostToDevice));
   return DD_OK;
+}
+
+int dd_profile_slots(void) { return dd::NSLOT; }
+
+const char* dd_profile_slot_name(int slot) {
+  return (slot >= 0 && slot < dd::NSLOT) ? dd::kSlotNames[slot] : nullptr;
+}
+
+dd_status dd_dlra_profile(dd_dlra_t h, int nsteps, double* ms, int* launches) {
+  g_err.clear();
+  if (!h || nsteps < 0 || !ms || !launches) return fail(DD_ERR_ARG, "bad argument");
+  for (int i = 0; i < dd::NSLOT; ++i) { ms[i] = 0.0; launches[i] = 0; }
+  dd::Prof* prof = new dd::Prof();
+  prof->n = 0;
+  for (int i = 0; i < dd::Prof::MAXL; ++i) {
+    cudaEventCreate(&prof->b[i]);
+    cudaEventCreate(&prof->e[i]);
+  }
+  dd_status st = DD_OK;
+  for (int s = 0; s < nsteps && st == DD_OK; ++s) {
+    prof->n = 0;
+    dd::g_prof = prof;
+    enqueue_step(h);
+    dd::g_prof = nullptr;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { st = fail(DD_ERR_CUDA, cudaGetErrorString(e)); break; }
+    for (int i = 0; i < prof->n; ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, prof->b[i], prof->e[i]);
+      ms[prof->slot[i]] += t;
+      launches[prof->slot[i]] += 1;
+    }
+  }
+  dd::g_prof = nullptr;
+  for (int i = 0; i < dd::Prof::MAXL; ++i) {
+    cudaEventDestroy(prof->b[i]);
+    cudaEventDestroy(prof->e[i]);
+  }
+  delete prof;
+  if (st != DD_OK) return st;
+  return check_status(h);
 }
 
 dd_status dd_dlra_sync(dd_dlra_t h) {

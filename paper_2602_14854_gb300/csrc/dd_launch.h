@@ -7,6 +7,36 @@
 
 namespace dd {
 
+// Kernel classes timed by dd_dlra_profile (one slot per kernel function).
+enum KernelSlot {
+  KS_AUG_COLS = 0, KS_BUILD_L0, KS_ORTH, KS_ANG_COEFFS, KS_REDUCE, KS_SMALL_ADV1, KS_TALL,
+  KS_GHOST, KS_KSTEP_ADV, KS_SP_COEFFS, KS_SSTEP_ADV, KS_LSTEP_ADV, KS_GRAM, KS_TRUNC,
+  KS_COLL_RANK, KS_COLL_A, KS_COLL_KSTEP, KS_COLL_SMALL, KS_COLL_LSTEP, KS_COLL_FINAL,
+  KS_FLUX, KS_COPY, NSLOT
+};
+extern const char* const kSlotNames[NSLOT];
+
+// Event-pair recorder around kernel launches (active only inside dd_dlra_profile).
+struct Prof {
+  static const int MAXL = 256;
+  int n;
+  cudaEvent_t b[MAXL], e[MAXL];
+  int slot[MAXL];
+};
+extern thread_local Prof* g_prof;
+inline void pbeg(cudaStream_t st, int slot) {
+  if (g_prof && g_prof->n < Prof::MAXL) {
+    cudaEventRecord(g_prof->b[g_prof->n], st);
+    g_prof->slot[g_prof->n] = slot;
+  }
+}
+inline void pend(cudaStream_t st) {
+  if (g_prof && g_prof->n < Prof::MAXL) {
+    cudaEventRecord(g_prof->e[g_prof->n], st);
+    ++g_prof->n;
+  }
+}
+
 struct OrthArgs {
   Geo g;
   int spatial;            // rows are cells (1) or directions (0)

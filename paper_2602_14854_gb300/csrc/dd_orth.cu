@@ -376,7 +376,9 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a) {
 }
 
 void launch_orth(const OrthArgs& a, cudaStream_t st) {
+  pbeg(st, KS_ORTH);
   k_orth<<<a.g.nsub, DD_THREADS, orth_smem_bytes(), st>>>(a);
+  pend(st);
 }
 
 cudaError_t orth_init() {

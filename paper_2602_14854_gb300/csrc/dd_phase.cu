@@ -987,6 +987,13 @@ int kstep_lpb(const Problem& P, int len) {
 
 }  // namespace
 
+const char* const kSlotNames[NSLOT] = {
+    "k_aug_cols", "k_build_L0", "k_orth", "k_ang_coeffs", "k_reduce", "k_small_adv1", "k_tall",
+    "k_ghost", "k_kstep_adv", "k_sp_coeffs", "k_sstep_adv", "k_lstep_adv", "k_gram", "k_trunc",
+    "k_coll_rank", "k_coll_a", "k_coll_kstep", "k_coll_small", "k_coll_lstep", "k_coll_final",
+    "k_flux", "memcpy"};
+thread_local Prof* g_prof = nullptr;
+
 size_t part_elems(const Problem& P) {
   const int nc = P.nchunk_sp > P.nchunk_ang ? P.nchunk_sp : P.nchunk_ang;
   return (size_t)P.g.nsub * nc * 6 * P.g.RC * P.g.RC;
@@ -1030,10 +1037,14 @@ static void gram(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spat
   a.spatial = spatial; a.A = A; a.lda = lda; a.acnt = acnt; a.afix = afix;
   a.Bm = Bm; a.ldb = ldb; a.bcnt = bcnt; a.bfix = bfix; a.b_per_sub = b_per_sub;
   a.wrow = wrow; a.part = B.part; a.nchunk = spatial ? P.nchunk_sp : P.nchunk_ang;
+  pbeg(st, KS_GRAM);
   k_gram<<<dim3(a.nchunk, P.g.nsub), DD_THREADS, 0, st>>>(P.g, a);
+  pend(st);
   Dst d;
   d.idx[0] = dst_small;
+  pbeg(st, KS_REDUCE);
   k_reduce<<<P.g.nsub, DD_THREADS, 0, st>>>(B.part, a.nchunk, 1, d, B.sm, P.g.RC);
+  pend(st);
 }
 
 static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spatial,
@@ -1044,7 +1055,9 @@ static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spat
   a.Bm = Bm; a.bsmall = bsmall; a.ncols = ncols; a.ncols_fix = ncols_fix; a.Y = Y; a.ldy = ldy;
   const int rows = spatial ? P.maxN : P.g.n;
   dim3 grid((rows + 63) / 64, P.g.nsub);
+  pbeg(st, KS_TALL);
   k_tall<<<grid, DD_THREADS, sizeof(double) * P.g.RC * P.g.RC, st>>>(P.g, a, B.sm);
+  pend(st);
 }
 
 static OrthArgs orth_args(const Problem& P, const PhaseBufs& B, int spatial, int mode) {
@@ -1063,36 +1076,52 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   const Geo& g = P.g;
   const int RC = g.RC, nsub = g.nsub;
   // 1. augmentation (Algorithm 4)
+  pbeg(st, KS_AUG_COLS);
   k_aug_cols<<<(nsub + 127) / 128, 128, 0, st>>>(g, B.r, axis, B.m);
+  pend(st);
+  pbeg(st, KS_BUILD_L0);
   k_build_L0<<<dim3((g.n + 31) / 32, nsub), DD_THREADS, sizeof(double) * 3 * RC * RC, st>>>(
       g, B.V, B.S, B.r, axis, B.L0);
+  pend(st);
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_AUG);
     a.A = B.L0; a.lda = g.MC; a.acols = B.m; a.Q = B.Vh; a.ldq = RC; a.rout = nullptr;
     launch_orth(a, st);
   }
+  pbeg(st, KS_COPY);
   cudaMemcpyAsync(B.rx + axis * nsub, B.rt, sizeof(int) * nsub, cudaMemcpyDeviceToDevice, st);
+  pend(st);
   // 2. angular Galerkin coefficients, boundary masses
+  pbeg(st, KS_ANG_COEFFS);
   k_ang_coeffs<<<dim3(P.nchunk_ang, nsub), DD_THREADS, 0, st>>>(
       g, axis == 0 ? P.ox : P.oy, B.Vh, B.V, B.r, B.rt, axis, P.nchunk_ang, B.part);
+  pend(st);
   {
     Dst d;
     d.idx[0] = SM_C; d.idx[1] = SM_MOUT_LO; d.idx[2] = SM_MOUT_HI;
     d.idx[3] = SM_M; d.idx[4] = SM_MIN_LO; d.idx[5] = SM_MIN_HI;
+    pbeg(st, KS_REDUCE);
     k_reduce<<<nsub, DD_THREADS, 0, st>>>(B.part, P.nchunk_ang, 6, d, B.sm, RC);
+    pend(st);
   }
   // 3. S M products, eigen-split of C
+  pbeg(st, KS_SMALL_ADV1);
   k_small_adv1<<<nsub, DD_THREADS, sizeof(double) * (2 * RC * RC + 2 * RC) + 64, st>>>(P, B, axis);
+  pend(st);
   // 4. K^0 = X (S <V, Vh>)
   tall(P, B, st, 1, B.X, RC, B.r, 0, nullptr, SM_B, B.rt, 0, B.K, RC);
   // 5. boundary data
+  pbeg(st, KS_GHOST);
   k_ghost<<<nsub, DD_THREADS, 0, st>>>(P, B, axis);
+  pend(st);
   // 6. K-step
   {
     const int len = P.maxlines;
     const int lpb = kstep_lpb(P, len);
     dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
+    pbeg(st, KS_KSTEP_ADV);
     k_kstep_adv<<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+    pend(st);
   }
   // 7. QR of K
   {
@@ -1101,16 +1130,24 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
     launch_orth(a, st);
   }
   // 8. S-step coefficients and S-step
+  pbeg(st, KS_SP_COEFFS);
   k_sp_coeffs<<<dim3(P.nchunk_sp, nsub), DD_THREADS, 0, st>>>(P, B, axis);
+  pend(st);
   {
     Dst d;
     d.idx[0] = SM_S1; d.idx[1] = SM_T; d.idx[2] = SM_G_LO; d.idx[3] = SM_G_HI;
+    pbeg(st, KS_REDUCE);
     k_reduce<<<nsub, DD_THREADS, 0, st>>>(B.part, P.nchunk_sp, 4, d, B.sm, RC);
+    pend(st);
   }
+  pbeg(st, KS_SSTEP_ADV);
   k_sstep_adv<<<nsub, DD_THREADS, sizeof(double) * 6 * RC * RC, st>>>(P, B, axis);
+  pend(st);
   // 9. L-step
+  pbeg(st, KS_LSTEP_ADV);
   k_lstep_adv<<<dim3((g.n + 31) / 32, nsub), DD_THREADS, sizeof(double) * (5 * RC * RC + 8 * 4 * RC),
                 st>>>(P, B, axis);
+  pend(st);
   // 10. QR of L
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_QR);
@@ -1119,8 +1156,10 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   }
   gram(P, B, st, 0, B.V1, RC, B.rt, 0, B.L, RC, B.rt, 0, 1, nullptr, SM_S3T);
   // 11. truncation (Algorithm 5)
+  pbeg(st, KS_TRUNC);
   k_trunc<<<nsub, DD_THREADS, sizeof(double) * (2 * RC * RC + RC) + sizeof(int) * (RC + 8), st>>>(
       P, B, P.RS, P.r_floor, P.RS);
+  pend(st);
   tall(P, B, st, 1, B.X1, RC, B.rt, 0, nullptr, SM_UB, B.ro, 0, B.Xo, RC);
   tall(P, B, st, 0, B.V1, RC, B.rt, 0, nullptr, SM_VB, B.ro, 0, B.Vo, RC);
 }
@@ -1128,15 +1167,21 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
 void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   const Geo& g = P.g;
   const int RC = g.RC, nsub = g.nsub;
+  pbeg(st, KS_COLL_RANK);
   k_coll_rank<<<(nsub + 127) / 128, 128, 0, st>>>(P, B.r, B.rc);
+  pend(st);
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_COMPLETE);
     a.A = B.V; a.lda = RC; a.acols = B.r; a.Q = B.Vh; a.ldq = RC; a.rout = B.rc;
     launch_orth(a, st);
   }
+  pbeg(st, KS_COLL_A);
   k_coll_a<<<nsub, DD_THREADS, 0, st>>>(P, B);
+  pend(st);
   tall(P, B, st, 1, B.X, RC, B.r, 0, B.S, -1, B.rc, 0, B.K, RC);
+  pbeg(st, KS_COLL_KSTEP);
   k_coll_kstep<<<dim3(64, nsub), DD_THREADS, 0, st>>>(P, B);
+  pend(st);
   {
     OrthArgs a = orth_args(P, B, 1, ORTH_QR);
     a.A = B.K; a.lda = RC; a.acols = B.rc; a.Q = B.Xo; a.ldq = RC; a.rout = B.rc;
@@ -1151,27 +1196,41 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
     a.spatial = 1; a.A = B.Xo; a.lda = RC; a.acnt = B.rc; a.afix = 0;
     a.Bm = P.sQ; a.ldb = 1; a.bcnt = nullptr; a.bfix = 1; a.b_per_sub = 1;
     a.wrow = nullptr; a.part = B.part; a.nchunk = P.nchunk_sp;
+    pbeg(st, KS_GRAM);
     k_gram<<<dim3(a.nchunk, nsub), DD_THREADS, 0, st>>>(g, a);
+    pend(st);
     Dst d;
     d.idx[0] = SM_UB;   // scratch: column 0 holds q
+    pbeg(st, KS_REDUCE);
     k_reduce<<<nsub, DD_THREADS, 0, st>>>(B.part, a.nchunk, 1, d, B.sm, RC);
+    pend(st);
   }
+  pbeg(st, KS_COLL_SMALL);
   k_coll_small<<<nsub, DD_THREADS, sizeof(double) * (4 * RC * RC + 5 * RC), st>>>(P, B);
+  pend(st);
+  pbeg(st, KS_COLL_LSTEP);
   k_coll_lstep<<<dim3((g.n + 31) / 32, nsub), DD_THREADS,
                  sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC), st>>>(P, B);
+  pend(st);
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_QR);
     a.A = B.L; a.lda = RC; a.acols = B.rc; a.Q = B.Vo; a.ldq = RC; a.rout = B.rc;
     launch_orth(a, st);
   }
   gram(P, B, st, 0, B.Vo, RC, B.rc, 0, B.L, RC, B.rc, 0, 1, nullptr, SM_S3T);
+  pbeg(st, KS_COLL_FINAL);
   k_coll_final<<<nsub, DD_THREADS, 0, st>>>(P, B);
+  pend(st);
 }
 
 void scalar_flux(const Problem& P, const double* X, const double* V, const double* S, const int* r,
                  double* work, double* rho, int nx, cudaStream_t st) {
+  pbeg(st, KS_FLUX);
   k_flux_prep<<<P.g.nsub, DD_THREADS, 0, st>>>(P, V, S, r, work);
+  pend(st);
+  pbeg(st, KS_FLUX);
   k_flux<<<dim3(16, P.g.nsub), DD_THREADS, 0, st>>>(P, X, r, work, rho, nx);
+  pend(st);
 }
 
 }  // namespace dd
