@@ -104,11 +104,16 @@ def test_graph_replay_matches_stream(B):
     g.close()
 
 
+def tol_workload():
+    return inputs.checkerboard_problem(blocks=3, cells_per_block=8, n_mu=4, n_phi=8, t_end=0.5,
+                                       tol=1e-3, r_aug_max=16).with_(r_min=2, r_max=5,
+                                                                     integrator="rk4")
+
+
 def test_tolerance_mode_checkerboard(B):
     """Rank-adaptive run (absolute tolerance) on a small checkerboard of absorbing
     and scattering blocks with a central source."""
-    wl = inputs.checkerboard_problem(blocks=3, cells_per_block=8, n_mu=4, n_phi=8, t_end=0.5,
-                                     tol=1e-4, r_aug_max=16).with_(r_min=2, r_max=5)
+    wl = tol_workload()
     s, o = run_both(B, wl)
     assert list(s.ranks()[0]) == o.ranks()
     assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
