@@ -77,7 +77,8 @@ struct dd_dlra {
   // device: workspace
   double *d_L0, *d_Hw, *d_Hwa, *d_Vh, *d_K, *d_X1, *d_L, *d_V1, *d_Kb, *d_sm, *d_part;
   double *d_sig, *d_rho, *d_fluxw;
-  int *d_m, *d_rt, *d_rx, *d_rc, *d_p;
+  int *d_m, *d_rt, *d_rx, *d_rc, *d_p, *d_flag;
+  double* d_scale;
   unsigned* d_status;
   dd::Problem P;
 };
@@ -92,6 +93,7 @@ dd::PhaseBufs bufs(dd_dlra* h, int in, int out) {
   B.X1 = h->d_X1; B.L = h->d_L; B.V1 = h->d_V1; B.Kb = h->d_Kb; B.sm = h->d_sm;
   B.part = h->d_part; B.m = h->d_m; B.rt = h->d_rt; B.rx = h->d_rx; B.rc = h->d_rc;
   B.sig = h->d_sig; B.p = h->d_p; B.status = h->d_status;
+  B.flag = h->d_flag; B.scale = h->d_scale;
   return B;
 }
 
@@ -158,7 +160,8 @@ void free_all(dd_dlra* h) {
                   h->d_angcand, h->d_X[0], h->d_X[1], h->d_V[0], h->d_V[1], h->d_S[0],
                   h->d_S[1], h->d_r[0], h->d_r[1], h->d_L0, h->d_Hw, h->d_Hwa, h->d_Vh,
                   h->d_K, h->d_X1, h->d_L, h->d_V1, h->d_Kb, h->d_sm, h->d_part, h->d_sig,
-                  h->d_rho, h->d_fluxw, h->d_m, h->d_rt, h->d_rx, h->d_rc, h->d_p, h->d_status};
+                  h->d_rho, h->d_fluxw, h->d_m, h->d_rt, h->d_rx, h->d_rc, h->d_p, h->d_status,
+                  h->d_flag, h->d_scale};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->graph_ready) cudaGraphExecDestroy(h->graph_exec);
@@ -325,6 +328,8 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
   ok &= dalloc(&h->d_rx, 2 * nsub) == cudaSuccess;
   ok &= dalloc(&h->d_rc, nsub) == cudaSuccess;
   ok &= dalloc(&h->d_p, nsub) == cudaSuccess;
+  ok &= dalloc(&h->d_flag, nsub) == cudaSuccess;
+  ok &= dalloc(&h->d_scale, nsub) == cudaSuccess;
   ok &= dalloc(&h->d_status, 1) == cudaSuccess;
   if (!ok) return bail(DD_ERR_CUDA, "device allocation failed");
 

@@ -105,4 +105,51 @@ __device__ __forceinline__ void rr_pair(int mm, int r, int i, int* p, int* q) {
   }
 }
 
+#define JACOBI_TOL 1e-15
+
+// One-sided Jacobi (Hestenes) on the m columns (length m) of the column-major
+// matrix Bc (leading dimension ld), accumulating the rotations in Jc, until no
+// pair has |b_p . b_q| > 1e-15 |b_p| |b_q|.  Block-wide; flag is shared scratch.
+__device__ __forceinline__ void jacobi_columns(double* Bc, double* Jc, int m, int ld, int* flag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int mm = m + (m & 1);
+  for (int sweep = 0; sweep < 40 && m > 1; ++sweep) {
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    for (int r = 0; r < mm - 1; ++r) {
+      for (int pi = warp; pi < mm / 2; pi += nwarps) {
+        int p, q;
+        rr_pair(mm, r, pi, &p, &q);
+        if (p >= m || q >= m) continue;
+        double* bp = Bc + p * ld;
+        double* bq = Bc + q * ld;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int l = lane; l < m; l += 32) {
+          double x = bp[l], y = bq[l];
+          al += x * x; be += y * y; ga += x * y;
+        }
+        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        if (ga != 0.0 && fabs(ga) > JACOBI_TOL * sqrt(al * be)) {
+          double zeta = (be - al) / (2.0 * ga);
+          double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          double* jp = Jc + p * ld;
+          double* jq = Jc + q * ld;
+          for (int l = lane; l < m; l += 32) {
+            double x = bp[l], y = bq[l];
+            bp[l] = c * x - s * y; bq[l] = s * x + c * y;
+            x = jp[l]; y = jq[l];
+            jp[l] = c * x - s * y; jq[l] = s * x + c * y;
+          }
+          if (lane == 0) *flag = 1;
+        }
+      }
+      __syncthreads();
+    }
+    int f = *flag;
+    __syncthreads();
+    if (f == 0) break;
+  }
+}
+
 }  // namespace dd

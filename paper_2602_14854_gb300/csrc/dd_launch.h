@@ -12,7 +12,7 @@ enum KernelSlot {
   KS_AUG_COLS = 0, KS_BUILD_L0, KS_ORTH, KS_ANG_COEFFS, KS_REDUCE, KS_SMALL_ADV1, KS_TALL,
   KS_GHOST, KS_KSTEP_ADV, KS_SP_COEFFS, KS_SSTEP_ADV, KS_LSTEP_ADV, KS_GRAM, KS_TRUNC,
   KS_COLL_RANK, KS_COLL_A, KS_COLL_KSTEP, KS_COLL_SMALL, KS_COLL_LSTEP, KS_COLL_FINAL,
-  KS_FLUX, KS_COPY, NSLOT
+  KS_FLUX, KS_COPY, KS_CQR, NSLOT
 };
 extern const char* const kSlotNames[NSLOT];
 
@@ -55,9 +55,13 @@ struct OrthArgs {
   unsigned* status;
 };
 
-size_t orth_smem_bytes();
 cudaError_t orth_init();
-void launch_orth(const OrthArgs& a, cudaStream_t st);
+void launch_orth_fallback(const OrthArgs& a, int mcap, int maxrows, const int* flag,
+                          cudaStream_t st);
+void launch_cqr1(const OrthArgs& a, const double* sm, int sG, int sR, int sRi, double* smw,
+                 int* flag, double* scale, cudaStream_t st);
+void launch_cqr2(const OrthArgs& a, const double* sm, int sG2, int sR1, double* smw, int sM,
+                 int* flag, const double* scale, cudaStream_t st);
 
 // Phase kernels (dd_phase.cu).  All buffers follow the layout described in
 // dd_internal.cuh; "small" matrices are RC x RC blocks, per subdomain stride RC*RC.
@@ -83,6 +87,8 @@ struct PhaseBufs {
   int* rc;         // collision rank
   double* sig;     // diagnostics
   int* p;          // diagnostics
+  int* flag;       // per subdomain: 1 = the orthonormalisation needs the fallback
+  double* scale;   // per subdomain: Gram scaling of the fast path
   unsigned* status;
 };
 
@@ -95,6 +101,7 @@ enum Small {
   SM_S2, SM_AP, SM_AM,                                             // S-step result, L-step matrices
   SM_S3T, SM_UB, SM_VB,                                            // S3^T, truncation rotations
   SM_MS, SM_MT, SM_VEC,                                            // collision: Ms, Mt, vectors (a, q, b-stages)
+  SM_G1, SM_R1, SM_R1I, SM_G2, SM_QM,                              // CholeskyQR2 fast path
   NSMALL
 };
 

@@ -1,6 +1,6 @@
 // Rank-revealing orthonormalisation with deterministic basis completion.
 //
-// One CTA per subdomain.  Serves three steps of the scheme:
+// Serves three steps of the scheme:
 //   ORTH_QR       "perform a QR decomposition of K (of L)" (Algorithms 1-3, steps 2
 //                 and 5): an orthonormal basis of the numerically significant
 //                 column span of K (L), completed to r_out columns;
@@ -11,13 +11,22 @@
 //   ORTH_COMPLETE pad an orthonormal basis to r_out columns (collision step started
 //                 below the rank floor).
 //
-// Method: scale by a power of two (exact), Householder QR of the copy, one-sided
-// Jacobi SVD of R (Hestenes, on the rows of R, accumulating the rotations: the
-// accumulated orthogonal matrix is the left singular basis of R), a singular value
-// sigma_j counts as significant when sigma_j > tau * sigma_1, the significant left
-// singular vectors of the input are Q_H [U_R; 0], and missing columns come in order
-// from a fixed exactly-orthogonal candidate family, each Gram-Schmidt'd twice and
-// accepted when its residual norm is >= accept:
+// A singular value sigma_j counts as significant when sigma_j > tau * sigma_1.
+//
+// Fast path (all SMs): CholeskyQR2 of the tall input.  Gram G1 = A^T A (chunked
+// over rows), R1 = chol(G1), Q1 = A R1^-1, G2 = Q1^T Q1, R2 = chol(G2), R = R2 R1;
+// one-sided Jacobi SVD of R gives the singular values and the left singular basis
+// U_R; the output is Q1 (R2^-1 U_R).  It is taken only when every singular value
+// is significant and no completion is needed (then the span it returns is the
+// input's, to ~eps * cond <= 1e-11); otherwise the subdomain is flagged.
+//
+// Fallback (one CTA per flagged subdomain): exact power-of-two scaling of a copy,
+// Householder QR (in shared memory when it fits), explicit Q_H by backward
+// accumulation in place of the reflectors, one-sided Jacobi SVD of R (on the rows
+// of R, accumulating the rotations: the accumulated orthogonal matrix is the left
+// singular basis U_R), significant left singular vectors Q_H U_R, and missing
+// columns taken in order from a fixed exactly-orthogonal candidate family, each
+// Gram-Schmidt'd twice and accepted when its residual norm is >= accept:
 //   space: cos(pi a (i+1/2)/nx_k) cos(pi b (j+1/2)/ny_k), by a+b then a descending;
 //   angle: the table built at create time (P_2l(mu) x cos/sin(m phi), weighted by
 //          sqrt(w)), then the unit vectors.
@@ -28,25 +37,221 @@
 
 namespace dd {
 
-namespace {
+// Rank decision shared by both paths (one thread).  sig[] descending, scaled by
+// 2^-e; returns p, sets *keep and *r_out.
+__device__ int decide(const OrthArgs& a, int k, const double* sig, int nref, int e, int* keep,
+                      int* r_out) {
+  int p = 0;
+  double s1 = nref > 0 ? sig[0] : 0.0;
+  if (s1 > 0.0)
+    for (int t = 0; t < nref; ++t)
+      if (sig[t] > a.tau * s1) ++p;
+  const double unscale = ldexp(1.0, e);
+  if (a.sig_out)
+    for (int t = 0; t < DD_MAXC; ++t) a.sig_out[(long)k * DD_MAXC + t] = t < nref ? sig[t] * unscale : 0.0;
+  if (a.p_out) a.p_out[k] = p;
+  if (a.mode == ORTH_QR) {
+    *r_out = a.rout[k];
+    *keep = min(p, *r_out);
+  } else {  // ORTH_AUG
+    int r_tail = p;
+    if (a.rank_mode == 1) {
+      r_tail = nref;
+      for (int r = 0; r <= nref; ++r) {
+        double ss = 0.0;
+        for (int t = r; t < nref; ++t) {
+          double x = sig[t] * unscale;
+          ss += x * x;
+        }
+        if (sqrt(ss) <= a.tol) { r_tail = r; break; }
+      }
+    }
+    int r_sig = min(r_tail, p);
+    int cap = min(min(a.r_aug_max, a.g.n), a.g.N[k]);
+    int fl = max(a.r_own[k], a.r_floor);
+    int rt = min(max(r_sig, fl), cap);
+    *r_out = rt;
+    *keep = min(rt, p);
+  }
+  return p;
+}
 
+// ---------------------------------------------------------------------------
+// fast path, small kernels (one CTA per subdomain)
+// ---------------------------------------------------------------------------
+// Cholesky of the m x m matrix s*G (row-major, ld) into upper R (row-major);
+// returns 0 on a non-positive pivot.  Single thread (m <= 64).
+__device__ int chol_upper(const double* G, int ld, int m, double s, double* R) {
+  for (int j = 0; j < m; ++j) {
+    double d = G[j * ld + j] * s;
+    for (int l = 0; l < j; ++l) d -= R[l * ld + j] * R[l * ld + j];
+    if (!(d > 0.0)) return 0;
+    d = sqrt(d);
+    R[j * ld + j] = d;
+    for (int c = j + 1; c < m; ++c) {
+      double x = G[j * ld + c] * s;
+      for (int l = 0; l < j; ++l) x -= R[l * ld + j] * R[l * ld + c];
+      R[j * ld + c] = x / d;
+    }
+    for (int c = 0; c < j; ++c) R[j * ld + c] = 0.0;
+  }
+  return 1;
+}
+
+// Inverse of the upper-triangular R into Ri (block-wide: one column per thread).
+__device__ void tri_inv_upper(const double* R, int ld, int m, double* Ri) {
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+    for (int i = ld - 1; i >= 0; --i) {
+      double x = 0.0;
+      if (c < m && i <= c) {
+        x = (i == c) ? 1.0 : 0.0;
+        for (int l = i + 1; l <= c; ++l) x -= R[i * ld + l] * Ri[l * ld + c];
+        x /= R[i * ld + i];
+      }
+      Ri[i * ld + c] = x;
+    }
+  }
+}
+
+// pass 1: R1 = chol(s G1), R1^-1.  Flags the subdomain when the factorisation
+// fails or the diagonal ratio exceeds 1e7 (beyond CholeskyQR2's reach).
+__global__ void k_cqr1(OrthArgs a, const double* sm, int sG, int sR, int sRi, double* smw,
+                       int* flag, double* scale) {
+  const int k = blockIdx.x, RC = a.g.RC;
+  const int m = a.acols[k];
+  const double* G = sm + ((long)k * NSMALL + sG) * RC * RC;
+  double* R = smw + ((long)k * NSMALL + sR) * RC * RC;
+  double* Ri = smw + ((long)k * NSMALL + sRi) * RC * RC;
+  __shared__ int ok;
+  __shared__ double s;
+  if (threadIdx.x == 0) {
+    ok = 0;
+    s = 1.0;
+    if (m > 0) {
+      double dmax = 0.0;
+      bool fin = true;
+      for (int j = 0; j < m; ++j) {
+        dmax = fmax(dmax, G[j * RC + j]);
+        for (int c = 0; c < m; ++c) fin = fin && isfinite(G[j * RC + c]);
+      }
+      if (fin && dmax > 0.0 && isfinite(dmax)) {
+        s = ldexp(1.0, -ilogb(dmax));
+        ok = chol_upper(G, RC, m, s, R);
+        if (ok) {
+          double lo = R[0], hi = R[0];
+          for (int j = 1; j < m; ++j) { lo = fmin(lo, R[j * RC + j]); hi = fmax(hi, R[j * RC + j]); }
+          if (!(lo > 1e-7 * hi)) ok = 0;
+        }
+      }
+      if (!fin) atomicOr(a.status, (unsigned)ST_NONFINITE);
+    }
+    flag[k] = ok ? 0 : 1;
+    scale[k] = s;
+  }
+  __syncthreads();
+  if (ok) tri_inv_upper(R, RC, m, Ri);
+}
+
+// pass 2: R2 = chol(G2), R = R2 R1 / sqrt(s), SVD(R), rank decision; on success
+// the output transform M = R2^-1 U_R[:, :keep] is written to slot sM.
+__global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, double* smw, int sM,
+                       int* flag, const double* scale) {
+  extern __shared__ double shm[];
+  const int k = blockIdx.x, RC = a.g.RC;
+  if (flag[k]) return;
+  const int m = a.acols[k];
+  const double* G2 = sm + ((long)k * NSMALL + sG2) * RC * RC;
+  const double* R1 = smw + ((long)k * NSMALL + sR1) * RC * RC;
+  double* M = smw + ((long)k * NSMALL + sM) * RC * RC;
+  double* R2 = shm;                   // RC*RC row-major
+  double* R2i = R2 + RC * RC;
+  double* Bc = R2i + RC * RC;         // column-major B = R^T
+  double* Jc = Bc + RC * RC;
+  double* sig = Jc + RC * RC;
+  int* perm = reinterpret_cast<int*>(sig + RC);
+  int* iv = perm + RC;
+  if (threadIdx.x == 0) iv[0] = chol_upper(G2, RC, m, 1.0, R2);
+  __syncthreads();
+  if (!iv[0]) {
+    if (threadIdx.x == 0) flag[k] = 1;
+    return;
+  }
+  tri_inv_upper(R2, RC, m, R2i);
+  // B = R^T, R = R2 R1 (both upper); column j of B = row j of R
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    int col = e / RC, row = e % RC;
+    double x = 0.0;
+    if (col < m && row < m && row >= col)
+      for (int l = col; l <= row; ++l) x += R2[col * RC + l] * R1[l * RC + row];
+    Bc[col * RC + row] = x;
+    Jc[col * RC + row] = (row == col) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  jacobi_columns(Bc, Jc, m, RC, &iv[1]);
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double s = 0.0;
+    for (int l = 0; l < m; ++l) s += Bc[j * RC + l] * Bc[j * RC + l];
+    sig[j] = sqrt(s);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < m; ++t) perm[t] = t;
+    for (int t = 0; t < m; ++t) {
+      int best = t;
+      for (int u = t + 1; u < m; ++u)
+        if (sig[perm[u]] > sig[perm[best]]) best = u;
+      int tmp = perm[t]; perm[t] = perm[best]; perm[best] = tmp;
+    }
+    // singular values of the input: those of R divided by sqrt(s)
+    double ss[DD_MAXC];
+    const double us = 1.0 / sqrt(scale[k]);
+    for (int t = 0; t < m; ++t) ss[t] = sig[perm[t]] * us;
+    int keep, r_out;
+    int p = decide(a, k, ss, m, 0, &keep, &r_out);
+    int ok = (p == m) && (keep == r_out);
+    iv[2] = ok;
+    iv[3] = keep;
+    if (ok && a.mode == ORTH_AUG) a.rt_out[k] = r_out;
+    if (!ok) flag[k] = 1;
+  }
+  __syncthreads();
+  if (!iv[2]) return;
+  const int keep = iv[3];
+  // M = R2^-1 U_R[:, perm[:keep]] ; zero elsewhere
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    int i = e / RC, t = e % RC;
+    double x = 0.0;
+    if (i < m && t < keep)
+      for (int l = i; l < m; ++l) x += R2i[i * RC + l] * Jc[perm[t] * RC + l];
+    M[e] = x;
+  }
+}
+
+size_t cqr2_smem_bytes(int RC) {
+  return sizeof(double) * (4 * RC * RC + RC) + sizeof(int) * (RC + 8);
+}
+
+// ---------------------------------------------------------------------------
+// fallback (one CTA per flagged subdomain)
+// ---------------------------------------------------------------------------
 struct OrthSmem {
-  double* Bc;   // DD_MAXC x DD_MAXC, column-major: column j of B = R^T = row j of R
-  double* Jc;   // DD_MAXC x DD_MAXC, column-major accumulated rotations
+  double* Bc;   // mcap x mcap, column-major: column j of B = R^T = row j of R
+  double* Jc;   // mcap x mcap, column-major accumulated rotations
   double* tau;  // Householder scalars
   double* sig;  // singular values
   double* wv;   // dot products
   double* red;  // reduction scratch (40)
+  double* dv;   // double scalars
   int* perm;    // descending order of sig
   int* iv;      // integer scalars
-  double* dv;   // double scalars
+  double* W;    // staged matrix (shared-memory variant), column-major rows x m
 };
 
-__device__ OrthSmem carve(void* base) {
+__device__ OrthSmem carve(void* base, int mcap) {
   OrthSmem s;
   double* d = reinterpret_cast<double*>(base);
-  s.Bc = d; d += DD_MAXC * DD_MAXC;
-  s.Jc = d; d += DD_MAXC * DD_MAXC;
+  s.Bc = d; d += mcap * mcap;
+  s.Jc = d; d += mcap * mcap;
   s.tau = d; d += DD_MAXC;
   s.sig = d; d += DD_MAXC;
   s.wv = d; d += DD_MAXC;
@@ -54,34 +259,38 @@ __device__ OrthSmem carve(void* base) {
   s.dv = d; d += 8;
   s.perm = reinterpret_cast<int*>(d);
   s.iv = s.perm + DD_MAXC;
+  s.W = d + (DD_MAXC + 16) / 2;
   return s;
 }
 
-}  // namespace
-
-size_t orth_smem_bytes() {
-  return sizeof(double) * (2 * DD_MAXC * DD_MAXC + 3 * DD_MAXC + 48) + sizeof(int) * (DD_MAXC + 16);
+size_t orth_smem_base(int mcap) {
+  return sizeof(double) * (2 * mcap * mcap + 3 * DD_MAXC + 48) + sizeof(int) * (DD_MAXC + 16);
 }
 
-__global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a) {
+template <bool SMEM>
+__global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a, int mcap, const int* flag) {
   extern __shared__ double smem_raw[];
-  OrthSmem sm = carve(smem_raw);
   const int k = blockIdx.x;
+  if (flag && flag[k] == 0) return;
+  OrthSmem sm = carve(smem_raw, mcap);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const Geo& g = a.g;
   const int rows = a.spatial ? g.N[k] : g.n;
   const long rbase = a.spatial ? (long)g.rowoff[k] : (long)k * g.n;
   const double* A = a.A + rbase * a.lda;
-  double* W = a.W + rbase * a.ldw;
+  double* Wg = a.W + rbase * a.ldw;
   double* Q = a.Q + rbase * a.ldq;
   const int m = a.acols[k];
   int* iv = sm.iv;
   double* dv = sm.dv;
+  // element (i, j) of the working copy
+  auto Wp = [&](int i, int j) -> double& {
+    return SMEM ? sm.W[(long)j * rows + i] : Wg[(long)i * a.ldw + j];
+  };
 
   int keep = 0, r_out = 0;
 
   if (a.mode == ORTH_COMPLETE) {
-    // copy the orthonormal input columns, then pad below
     for (int i = tid; i < rows; i += blockDim.x)
       for (int t = 0; t < m; ++t) Q[(long)i * a.ldq + t] = A[(long)i * a.lda + t];
     keep = m;
@@ -102,8 +311,10 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a) {
     int e = 0;
     if (amax > 0.0 && isfinite(amax)) e = ilogb(amax) + 1;
     const double sc = ldexp(1.0, -e);
-    for (int i = tid; i < rows; i += blockDim.x)
-      for (int t = 0; t < m; ++t) W[(long)i * a.ldw + t] = A[(long)i * a.lda + t] * sc;
+    for (long idx = tid; idx < (long)rows * m; idx += blockDim.x) {
+      int i = (int)(idx / m), t = (int)(idx % m);
+      Wp(i, t) = A[(long)i * a.lda + t] * sc;
+    }
     __syncthreads();
 
     const bool zero = !(amax > 0.0) || !isfinite(amax);
@@ -113,12 +324,12 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a) {
     for (int j = 0; j < nref; ++j) {
       double s = 0.0;
       for (int i = j + 1 + tid; i < rows; i += blockDim.x) {
-        double x = W[(long)i * a.ldw + j];
+        double x = Wp(i, j);
         s += x * x;
       }
       double xn2 = block_sum(s, sm.red);
       if (tid == 0) {
-        double alpha = W[(long)j * a.ldw + j];
+        double alpha = Wp(j, j);
         if (xn2 == 0.0) {
           sm.tau[j] = 0.0;
           dv[0] = 0.0;
@@ -133,13 +344,12 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a) {
       const double tj = sm.tau[j];
       if (tj != 0.0) {
         const double vs = dv[0];
-        for (int i = j + 1 + tid; i < rows; i += blockDim.x) W[(long)i * a.ldw + j] *= vs;
+        for (int i = j + 1 + tid; i < rows; i += blockDim.x) Wp(i, j) *= vs;
         __syncthreads();
-        if (tid == 0) W[(long)j * a.ldw + j] = dv[1];
+        if (tid == 0) Wp(j, j) = dv[1];
         for (int c = j + 1 + warp; c < m; c += nwarps) {
-          double d = (lane == 0) ? W[(long)j * a.ldw + c] : 0.0;
-          for (int i = j + 1 + lane; i < rows; i += 32)
-            d += W[(long)i * a.ldw + j] * W[(long)i * a.ldw + c];
+          double d = (lane == 0) ? Wp(j, c) : 0.0;
+          for (int i = j + 1 + lane; i < rows; i += 32) d += Wp(i, j) * Wp(i, c);
           d = warp_sum(d);
           if (lane == 0) sm.wv[c] = d;
         }
@@ -148,71 +358,64 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a) {
         if (nc > 0) {
           const long tot = (long)(rows - j) * nc;
           for (long idx = tid; idx < tot; idx += blockDim.x) {
-            int i = j + (int)(idx / nc);
-            int c = j + 1 + (int)(idx % nc);
-            double v = (i == j) ? 1.0 : W[(long)i * a.ldw + j];
-            W[(long)i * a.ldw + c] -= tj * v * sm.wv[c];
+            int c = j + 1 + (int)(idx / (rows - j));
+            int i = j + (int)(idx % (rows - j));
+            double v = (i == j) ? 1.0 : Wp(i, j);
+            Wp(i, c) -= tj * v * sm.wv[c];
           }
         }
         __syncthreads();
       }
     }
 
-    // ---- 3. one-sided Jacobi SVD of R ------------------------------------------------
-    for (int idx = tid; idx < DD_MAXC * DD_MAXC; idx += blockDim.x) {
-      int col = idx / DD_MAXC, row = idx % DD_MAXC;
+    // ---- 3. R -> B = R^T (column-major); explicit Q_H in place (backward accumulation)
+    for (int idx = tid; idx < mcap * mcap; idx += blockDim.x) {
+      int col = idx / mcap, row = idx % mcap;
       double b = 0.0;
-      if (col < nref && row < nref && row >= col) b = W[(long)col * a.ldw + row];
+      if (col < nref && row < nref && row >= col) b = Wp(col, row);
       sm.Bc[idx] = b;
       sm.Jc[idx] = (row == col) ? 1.0 : 0.0;
     }
     __syncthreads();
-    const int mm = nref + (nref & 1);
-    for (int sweep = 0; sweep < 60 && nref > 1; ++sweep) {
-      if (tid == 0) iv[0] = 0;
-      __syncthreads();
-      for (int r = 0; r < mm - 1; ++r) {
-        for (int pi = warp; pi < mm / 2; pi += nwarps) {
-          int p, q;
-          rr_pair(mm, r, pi, &p, &q);
-          if (p >= nref || q >= nref) continue;
-          double* bp = sm.Bc + p * DD_MAXC;
-          double* bq = sm.Bc + q * DD_MAXC;
-          double al = 0.0, be = 0.0, ga = 0.0;
-          for (int l = lane; l < nref; l += 32) {
-            double x = bp[l], y = bq[l];
-            al += x * x; be += y * y; ga += x * y;
-          }
-          al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-          if (ga != 0.0 && fabs(ga) > 2.220446049250313e-16 * sqrt(al * be)) {
-            double zeta = (be - al) / (2.0 * ga);
-            double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-            double* jp = sm.Jc + p * DD_MAXC;
-            double* jq = sm.Jc + q * DD_MAXC;
-            for (int l = lane; l < nref; l += 32) {
-              double x = bp[l], y = bq[l];
-              bp[l] = c * x - s * y; bq[l] = s * x + c * y;
-              x = jp[l]; y = jq[l];
-              jp[l] = c * x - s * y; jq[l] = s * x + c * y;
-            }
-            if (lane == 0) iv[0] = 1;
-          }
+    for (int j = nref - 1; j >= 0; --j) {
+      const double tj = sm.tau[j];
+      if (tj != 0.0 && j < nref - 1) {
+        for (int c = j + 1 + warp; c < nref; c += nwarps) {
+          double d = 0.0;   // row j of the already formed columns is zero
+          for (int i = j + 1 + lane; i < rows; i += 32) d += Wp(i, j) * Wp(i, c);
+          d = warp_sum(d);
+          if (lane == 0) sm.wv[c] = d;
+        }
+        __syncthreads();
+        const int nc = nref - j - 1;
+        const long tot = (long)(rows - j) * nc;
+        for (long idx = tid; idx < tot; idx += blockDim.x) {
+          int c = j + 1 + (int)(idx / (rows - j));
+          int i = j + (int)(idx % (rows - j));
+          double v = (i == j) ? 1.0 : Wp(i, j);
+          Wp(i, c) -= tj * v * sm.wv[c];
         }
         __syncthreads();
       }
-      if (iv[0] == 0) break;
+      for (int i = tid; i < rows; i += blockDim.x) {
+        double x;
+        if (i < j) x = 0.0;
+        else if (i == j) x = 1.0 - tj;
+        else x = -tj * Wp(i, j);
+        Wp(i, j) = x;
+      }
       __syncthreads();
     }
+
+    // ---- 4. one-sided Jacobi SVD of R, rank decision --------------------------------
+    jacobi_columns(sm.Bc, sm.Jc, nref, mcap, &iv[0]);
     for (int j = warp; j < nref; j += nwarps) {
       double s = 0.0;
-      for (int l = lane; l < nref; l += 32) s += sm.Bc[j * DD_MAXC + l] * sm.Bc[j * DD_MAXC + l];
+      for (int l = lane; l < nref; l += 32) s += sm.Bc[j * mcap + l] * sm.Bc[j * mcap + l];
       s = warp_sum(s);
       if (lane == 0) sm.sig[j] = sqrt(s);
     }
     __syncthreads();
-
-    // ---- 4. rank decision (one thread) ----------------------------------------------
     if (tid == 0) {
       for (int t = 0; t < nref; ++t) sm.perm[t] = t;
       for (int t = 0; t < nref; ++t) {          // selection sort, descending, stable
@@ -221,40 +424,10 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a) {
           if (sm.sig[sm.perm[u]] > sm.sig[sm.perm[best]]) best = u;
         int tmp = sm.perm[t]; sm.perm[t] = sm.perm[best]; sm.perm[best] = tmp;
       }
-      int p = 0;
-      double s1 = nref > 0 ? sm.sig[sm.perm[0]] : 0.0;
-      if (s1 > 0.0)
-        for (int t = 0; t < nref; ++t)
-          if (sm.sig[sm.perm[t]] > a.tau * s1) ++p;
-      const double unscale = ldexp(1.0, e);
-      if (a.sig_out)
-        for (int t = 0; t < DD_MAXC; ++t)
-          a.sig_out[(long)k * DD_MAXC + t] = t < nref ? sm.sig[sm.perm[t]] * unscale : 0.0;
-      if (a.p_out) a.p_out[k] = p;
-      if (a.mode == ORTH_QR) {
-        r_out = a.rout[k];
-        keep = min(p, r_out);
-      } else {  // ORTH_AUG
-        int r_tail = p;
-        if (a.rank_mode == 1) {
-          r_tail = nref;
-          for (int r = 0; r <= nref; ++r) {
-            double ss = 0.0;
-            for (int t = r; t < nref; ++t) {
-              double x = sm.sig[sm.perm[t]] * unscale;
-              ss += x * x;
-            }
-            if (sqrt(ss) <= a.tol) { r_tail = r; break; }
-          }
-        }
-        int r_sig = min(r_tail, p);
-        int cap = min(min(a.r_aug_max, g.n), g.N[k]);
-        int fl = max(a.r_own[k], a.r_floor);
-        int rt = min(max(r_sig, fl), cap);
-        r_out = rt;
-        keep = min(rt, p);
-        a.rt_out[k] = rt;
-      }
+      double ss[DD_MAXC];
+      for (int t = 0; t < nref; ++t) ss[t] = sm.sig[sm.perm[t]];
+      decide(a, k, ss, nref, e, &keep, &r_out);
+      if (a.mode == ORTH_AUG) a.rt_out[k] = r_out;
       iv[1] = keep;
       iv[2] = r_out;
     }
@@ -262,30 +435,15 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a) {
     keep = iv[1];
     r_out = iv[2];
 
-    // ---- 5. significant left singular vectors: Q_H [U_R; 0] ----------------------------
+    // ---- 5. significant left singular vectors: Q_H U_R[:, :keep] -----------------------
     for (long idx = tid; idx < (long)rows * keep; idx += blockDim.x) {
       int i = (int)(idx / keep), t = (int)(idx % keep);
-      Q[(long)i * a.ldq + t] = (i < nref) ? sm.Jc[sm.perm[t] * DD_MAXC + i] : 0.0;
+      const double* u = sm.Jc + sm.perm[t] * mcap;
+      double x = 0.0;
+      for (int j = 0; j < nref; ++j) x += Wp(i, j) * u[j];
+      Q[(long)i * a.ldq + t] = x;
     }
     __syncthreads();
-    for (int j = nref - 1; j >= 0 && keep > 0; --j) {
-      const double tj = sm.tau[j];
-      if (tj == 0.0) continue;
-      for (int t = warp; t < keep; t += nwarps) {
-        double d = (lane == 0) ? Q[(long)j * a.ldq + t] : 0.0;
-        for (int i = j + 1 + lane; i < rows; i += 32) d += W[(long)i * a.ldw + j] * Q[(long)i * a.ldq + t];
-        d = warp_sum(d);
-        if (lane == 0) sm.wv[t] = d;
-      }
-      __syncthreads();
-      const long tot = (long)(rows - j) * keep;
-      for (long idx = tid; idx < tot; idx += blockDim.x) {
-        int i = j + (int)(idx / keep), t = (int)(idx % keep);
-        double v = (i == j) ? 1.0 : W[(long)i * a.ldw + j];
-        Q[(long)i * a.ldq + t] -= tj * v * sm.wv[t];
-      }
-      __syncthreads();
-    }
   }
 
   // ---- 6. completion from the fixed family ---------------------------------------------
@@ -375,15 +533,45 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a) {
   }
 }
 
-void launch_orth(const OrthArgs& a, cudaStream_t st) {
+static const size_t kSmemLimit = 220 * 1024;
+
+// Launch the fallback kernel: shared-memory staging when rows x mcap fits.
+void launch_orth_fallback(const OrthArgs& a, int mcap, int maxrows, const int* flag,
+                          cudaStream_t st) {
+  const size_t base = orth_smem_base(mcap);
+  const size_t need = base + sizeof(double) * ((size_t)maxrows * mcap + 8);
   pbeg(st, KS_ORTH);
-  k_orth<<<a.g.nsub, DD_THREADS, orth_smem_bytes(), st>>>(a);
+  if (need <= kSmemLimit)
+    k_orth<true><<<a.g.nsub, DD_THREADS, need, st>>>(a, mcap, flag);
+  else
+    k_orth<false><<<a.g.nsub, DD_THREADS, base, st>>>(a, mcap, flag);
+  pend(st);
+}
+
+void launch_cqr1(const OrthArgs& a, const double* sm, int sG, int sR, int sRi, double* smw,
+                 int* flag, double* scale, cudaStream_t st) {
+  pbeg(st, KS_CQR);
+  k_cqr1<<<a.g.nsub, 128, 0, st>>>(a, sm, sG, sR, sRi, smw, flag, scale);
+  pend(st);
+}
+
+void launch_cqr2(const OrthArgs& a, const double* sm, int sG2, int sR1, double* smw, int sM,
+                 int* flag, const double* scale, cudaStream_t st) {
+  pbeg(st, KS_CQR);
+  k_cqr2<<<a.g.nsub, DD_THREADS, cqr2_smem_bytes(a.g.RC), st>>>(a, sm, sG2, sR1, smw, sM, flag,
+                                                                 scale);
   pend(st);
 }
 
 cudaError_t orth_init() {
-  return cudaFuncSetAttribute(k_orth, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)orth_smem_bytes());
+  cudaError_t e = cudaFuncSetAttribute(k_orth<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kSmemLimit);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_orth<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)orth_smem_base(DD_MAXC));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_cqr2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)cqr2_smem_bytes(DD_MAXC));
 }
 
 }  // namespace dd

@@ -189,19 +189,17 @@ __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
   }
   __syncthreads();
   const int mm = rt + (rt & 1);
-  for (int sweep = 0; sweep < 60 && rt > 1; ++sweep) {
-    // convergence: off-diagonal mass relative to the whole matrix
-    double off = 0.0, tot = 0.0;
-    for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
-      int i = e / rt, j = e % rt;
-      double x = Cm[i * RC + j];
-      tot += x * x;
-      if (i != j) off += x * x;
-    }
-    __shared__ double red[40];
-    off = block_sum(off, red);
-    tot = block_sum(tot, red);
-    if (off <= 1e-32 * tot) break;
+  __shared__ double red[40];
+  __shared__ int rotated;
+  double nf = 0.0;
+  for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
+    double x = Cm[(e / rt) * RC + e % rt];
+    nf += x * x;
+  }
+  const double thr = JACOBI_TOL * sqrt(block_sum(nf, red));   // |C_pq| <= 1e-15 |C|_F is converged
+  for (int sweep = 0; sweep < 40 && rt > 1; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
     for (int rnd = 0; rnd < mm - 1; ++rnd) {
       for (int pi = threadIdx.x; pi < mm / 2; pi += blockDim.x) {
         int p, q;
@@ -209,11 +207,12 @@ __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
         double c = 1.0, s = 0.0;
         if (p < rt && q < rt) {
           double apq = Cm[p * RC + q];
-          if (apq != 0.0) {
+          if (fabs(apq) > thr) {
             double zeta = (Cm[q * RC + q] - Cm[p * RC + p]) / (2.0 * apq);
             double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             c = 1.0 / sqrt(1.0 + t * t);
             s = c * t;
+            rotated = 1;
           }
         }
         cs[pi] = c; sn[pi] = s;
@@ -247,6 +246,9 @@ __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
       }
       __syncthreads();
     }
+    int f = rotated;
+    __syncthreads();
+    if (!f) break;
   }
   // C+ = P diag(max(l,0)) P^T, C- = P diag(min(l,0)) P^T
   double* Cp = SMB(B, P, k, SM_CP);
@@ -622,43 +624,7 @@ __global__ void k_trunc(Problem P, PhaseBufs B, int rank_fixed, int r_min, int r
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int mm = rt + (rt & 1);
-  for (int sweep = 0; sweep < 60 && rt > 1; ++sweep) {
-    if (threadIdx.x == 0) iv[0] = 0;
-    __syncthreads();
-    for (int rnd = 0; rnd < mm - 1; ++rnd) {
-      for (int pi = warp; pi < mm / 2; pi += nwarps) {
-        int p, q;
-        rr_pair(mm, rnd, pi, &p, &q);
-        if (p >= rt || q >= rt) continue;
-        double* bp = Bc + p * RC;
-        double* bq = Bc + q * RC;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int l = lane; l < rt; l += 32) {
-          double x = bp[l], y = bq[l];
-          al += x * x; be += y * y; ga += x * y;
-        }
-        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-        if (ga != 0.0 && fabs(ga) > 2.220446049250313e-16 * sqrt(al * be)) {
-          double zeta = (be - al) / (2.0 * ga);
-          double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-          double* jp = Jc + p * RC;
-          double* jq = Jc + q * RC;
-          for (int l = lane; l < rt; l += 32) {
-            double x = bp[l], y = bq[l];
-            bp[l] = c * x - s * y; bq[l] = s * x + c * y;
-            x = jp[l]; y = jq[l];
-            jp[l] = c * x - s * y; jq[l] = s * x + c * y;
-          }
-          if (lane == 0) iv[0] = 1;
-        }
-      }
-      __syncthreads();
-    }
-    if (iv[0] == 0) break;
-    __syncthreads();
-  }
+  jacobi_columns(Bc, Jc, rt, RC, &iv[0]);
   for (int j = warp; j < rt; j += nwarps) {
     double s = 0.0;
     for (int l = lane; l < rt; l += 32) s += Bc[j * RC + l] * Bc[j * RC + l];
@@ -991,7 +957,7 @@ const char* const kSlotNames[NSLOT] = {
     "k_aug_cols", "k_build_L0", "k_orth", "k_ang_coeffs", "k_reduce", "k_small_adv1", "k_tall",
     "k_ghost", "k_kstep_adv", "k_sp_coeffs", "k_sstep_adv", "k_lstep_adv", "k_gram", "k_trunc",
     "k_coll_rank", "k_coll_a", "k_coll_kstep", "k_coll_small", "k_coll_lstep", "k_coll_final",
-    "k_flux", "memcpy"};
+    "k_flux", "memcpy", "k_cqr"};
 thread_local Prof* g_prof = nullptr;
 
 size_t part_elems(const Problem& P) {
@@ -1072,6 +1038,22 @@ static OrthArgs orth_args(const Problem& P, const PhaseBufs& B, int spatial, int
   return a;
 }
 
+// CholeskyQR2 on all SMs, then the one-CTA fallback for the subdomains it flagged.
+static void orthonormalize(const Problem& P, const PhaseBufs& B, cudaStream_t st, OrthArgs a,
+                           int mcap) {
+  const int sp = a.spatial;
+  const int maxrows = sp ? P.maxN : P.g.n;
+  double* W = sp ? B.Hw : B.Hwa;
+  gram(P, B, st, sp, a.A, a.lda, a.acols, 0, a.A, a.lda, a.acols, 0, 1, nullptr, SM_G1);
+  launch_cqr1(a, B.sm, SM_G1, SM_R1, SM_R1I, B.sm, B.flag, B.scale, st);
+  tall(P, B, st, sp, a.A, a.lda, a.acols, 0, nullptr, SM_R1I, a.acols, 0, W, P.WC);
+  gram(P, B, st, sp, W, P.WC, a.acols, 0, W, P.WC, a.acols, 0, 1, nullptr, SM_G2);
+  launch_cqr2(a, B.sm, SM_G2, SM_R1, B.sm, SM_QM, B.flag, B.scale, st);
+  tall(P, B, st, sp, W, P.WC, a.acols, 0, nullptr, SM_QM,
+       a.mode == ORTH_AUG ? a.rt_out : a.rout, 0, a.Q, a.ldq);
+  launch_orth_fallback(a, mcap, maxrows, B.flag, st);
+}
+
 void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st) {
   const Geo& g = P.g;
   const int RC = g.RC, nsub = g.nsub;
@@ -1086,7 +1068,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_AUG);
     a.A = B.L0; a.lda = g.MC; a.acols = B.m; a.Q = B.Vh; a.ldq = RC; a.rout = nullptr;
-    launch_orth(a, st);
+    orthonormalize(P, B, st, a, g.MC);
   }
   pbeg(st, KS_COPY);
   cudaMemcpyAsync(B.rx + axis * nsub, B.rt, sizeof(int) * nsub, cudaMemcpyDeviceToDevice, st);
@@ -1127,7 +1109,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   {
     OrthArgs a = orth_args(P, B, 1, ORTH_QR);
     a.A = B.K; a.lda = RC; a.acols = B.rt; a.Q = B.X1; a.ldq = RC; a.rout = B.rt;
-    launch_orth(a, st);
+    orthonormalize(P, B, st, a, RC);
   }
   // 8. S-step coefficients and S-step
   pbeg(st, KS_SP_COEFFS);
@@ -1152,7 +1134,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_QR);
     a.A = B.L; a.lda = RC; a.acols = B.rt; a.Q = B.V1; a.ldq = RC; a.rout = B.rt;
-    launch_orth(a, st);
+    orthonormalize(P, B, st, a, RC);
   }
   gram(P, B, st, 0, B.V1, RC, B.rt, 0, B.L, RC, B.rt, 0, 1, nullptr, SM_S3T);
   // 11. truncation (Algorithm 5)
@@ -1173,7 +1155,7 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_COMPLETE);
     a.A = B.V; a.lda = RC; a.acols = B.r; a.Q = B.Vh; a.ldq = RC; a.rout = B.rc;
-    launch_orth(a, st);
+    launch_orth_fallback(a, RC, g.n, nullptr, st);
   }
   pbeg(st, KS_COLL_A);
   k_coll_a<<<nsub, DD_THREADS, 0, st>>>(P, B);
@@ -1185,7 +1167,7 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   {
     OrthArgs a = orth_args(P, B, 1, ORTH_QR);
     a.A = B.K; a.lda = RC; a.acols = B.rc; a.Q = B.Xo; a.ldq = RC; a.rout = B.rc;
-    launch_orth(a, st);
+    orthonormalize(P, B, st, a, RC);
   }
   gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.K, RC, B.rc, 0, 1, nullptr, SM_S1);
   gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.Xo, RC, B.rc, 0, 1, P.sig_s, SM_MS);
@@ -1215,7 +1197,7 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_QR);
     a.A = B.L; a.lda = RC; a.acols = B.rc; a.Q = B.Vo; a.ldq = RC; a.rout = B.rc;
-    launch_orth(a, st);
+    orthonormalize(P, B, st, a, RC);
   }
   gram(P, B, st, 0, B.Vo, RC, B.rc, 0, B.L, RC, B.rc, 0, 1, nullptr, SM_S3T);
   pbeg(st, KS_COLL_FINAL);
