@@ -152,7 +152,7 @@ __global__ void k_cqr1(OrthArgs a, const double* sm, int sG, int sR, int sRi, do
   if (ok) tri_inv_upper(R, RC, m, Ri);
 }
 
-// pass 2: R2 = chol(G2), R = R2 R1 / sqrt(s), SVD(R), rank decision; on success
+// pass 2: R2 = chol(G2), R = R2 R1, SVD(R), rank decision; on success
 // the output transform M = R2^-1 U_R[:, :keep] is written to slot sM.
 __global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, double* smw, int sM,
                        int* flag, const double* scale) {
@@ -202,10 +202,9 @@ __global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, double* s
         if (sig[perm[u]] > sig[perm[best]]) best = u;
       int tmp = perm[t]; perm[t] = perm[best]; perm[best] = tmp;
     }
-    // singular values of the input: those of R divided by sqrt(s)
+    // A = (Q1 R2^-1)(R2 R1): the singular values of R = R2 R1 are those of the input
     double ss[DD_MAXC];
-    const double us = 1.0 / sqrt(scale[k]);
-    for (int t = 0; t < m; ++t) ss[t] = sig[perm[t]] * us;
+    for (int t = 0; t < m; ++t) ss[t] = sig[perm[t]];
     int keep, r_out;
     int p = decide(a, k, ss, m, 0, &keep, &r_out);
     int ok = (p == m) && (keep == r_out);
