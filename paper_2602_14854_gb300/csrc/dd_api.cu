@@ -212,17 +212,21 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->ssum = 0.0;
   for (int i = 0; i < quad->n; ++i) h->ssum += quad->w[i];
-  h->RC = opt->r_aug_max;
   h->RS = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_max;
   h->MC = 3 * h->RS;
+  // column capacity of every tall and small matrix: the intermediate rank and the
+  // augmentation input width both fit
+  h->RC = std::max(opt->r_aug_max, h->MC);
   h->r_floor = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_min;
   auto bail = [&](dd_status s, const std::string& m) {
     free_all(h);
     delete h;
     return fail(s, m);
   };
-  if (h->RC < 1 || h->RC > DD_MAXC) return bail(DD_ERR_ARG, "r_aug_max must be in [1, 64]");
-  if (h->RS < 1 || h->RS > h->RC) return bail(DD_ERR_ARG, "stored-rank cap must be in [1, r_aug_max]");
+  if (opt->r_aug_max < 1 || opt->r_aug_max > DD_MAXC)
+    return bail(DD_ERR_ARG, "r_aug_max must be in [1, 64]");
+  if (h->RS < 1 || h->RS > opt->r_aug_max)
+    return bail(DD_ERR_ARG, "stored-rank cap must be in [1, r_aug_max]");
   if (h->MC > DD_MAXC) return bail(DD_ERR_ARG, "3 * stored-rank cap must be <= 64");
   if (h->n < h->MC) return bail(DD_ERR_ARG, "need at least 3 * stored-rank cap directions");
   if (h->r_floor < 0 || h->r_floor > h->RS) return bail(DD_ERR_ARG, "rank floor");
@@ -249,7 +253,6 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
       s.nb[3] = J < h->ty - 1 ? k + h->tx : -1;
       h->maxlines = std::max(h->maxlines, std::max(s.nxk, s.nyk));
       h->maxN = std::max(h->maxN, s.N);
-      if (s.N < h->RC) return bail(DD_ERR_ARG, "every subdomain needs at least r_aug_max cells");
     }
   h->Ntot = rowoff;
   if (h->maxlines * h->RC > DD_THREADS * 24)
@@ -310,7 +313,7 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
     ok &= dalloc(&h->d_r[b], nsub) == cudaSuccess;
   }
   ok &= dalloc(&h->d_L0, (long)nsub * n * MC) == cudaSuccess;
-  const int WC = std::max(MC, RC);
+  const int WC = RC;
   ok &= dalloc(&h->d_Hw, Nt * WC) == cudaSuccess;
   ok &= dalloc(&h->d_Hwa, (long)nsub * n * WC) == cudaSuccess;
   ok &= dalloc(&h->d_Vh, (long)nsub * n * RC) == cudaSuccess;
