@@ -60,8 +60,8 @@ void launch_orth_fallback(const OrthArgs& a, int mcap, int maxrows, const int* f
                           cudaStream_t st);
 void launch_cqr1(const OrthArgs& a, const double* sm, int sG, int sR, int sRi, double* smw,
                  int* flag, double* scale, cudaStream_t st);
-void launch_cqr2(const OrthArgs& a, const double* sm, int sG2, int sR1, double* smw, int sM,
-                 int* flag, const double* scale, cudaStream_t st);
+void launch_cqr2(const OrthArgs& a, const double* sm, int sG2, int sR1, int sR1i, double* smw,
+                 int sM, int* flag, const double* scale, cudaStream_t st);
 
 // Phase kernels (dd_phase.cu).  All buffers follow the layout described in
 // dd_internal.cuh; "small" matrices are RC x RC blocks, per subdomain stride RC*RC.

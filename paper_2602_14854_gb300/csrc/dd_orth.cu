@@ -79,28 +79,35 @@ __device__ int decide(const OrthArgs& a, int k, const double* sig, int nref, int
 // ---------------------------------------------------------------------------
 // fast path, small kernels (one CTA per subdomain)
 // ---------------------------------------------------------------------------
-// Cholesky of the m x m matrix s*G (row-major, ld) into upper R (row-major);
-// returns 0 on a non-positive pivot.  Single thread (m <= 64).
-__device__ int chol_upper(const double* G, int ld, int m, double s, double* R) {
+// Cholesky s*G = R^T R of the m x m matrix G (row-major, ld) into upper R
+// (row-major, ld), by one warp (lanes over columns); Gw is m x ld scratch.
+// Returns 0 on a non-positive pivot.
+__device__ int chol_upper_warp(const double* G, int ld, int m, double s, double* R, double* Gw) {
+  const int lane = threadIdx.x & 31;
+  for (int e = lane; e < m * ld; e += 32) Gw[e] = G[e] * s;
+  __syncwarp();
   for (int j = 0; j < m; ++j) {
-    double d = G[j * ld + j] * s;
-    for (int l = 0; l < j; ++l) d -= R[l * ld + j] * R[l * ld + j];
+    const double d = Gw[j * ld + j];
     if (!(d > 0.0)) return 0;
-    d = sqrt(d);
-    R[j * ld + j] = d;
-    for (int c = j + 1; c < m; ++c) {
-      double x = G[j * ld + c] * s;
-      for (int l = 0; l < j; ++l) x -= R[l * ld + j] * R[l * ld + c];
-      R[j * ld + c] = x / d;
+    const double rd = sqrt(d);
+    for (int c = lane; c < ld; c += 32)
+      R[j * ld + c] = (c < j || c >= m) ? 0.0 : (c == j ? rd : Gw[j * ld + c] / rd);
+    __syncwarp();
+    for (int c = j + 1 + lane; c < m; c += 32) {
+      const double rc = R[j * ld + c];
+      for (int r = j + 1; r <= c; ++r) Gw[r * ld + c] -= R[j * ld + r] * rc;
     }
-    for (int c = 0; c < j; ++c) R[j * ld + c] = 0.0;
+    __syncwarp();
   }
+  for (int j = m; j < ld; ++j)
+    for (int c = lane; c < ld; c += 32) R[j * ld + c] = 0.0;
+  __syncwarp();
   return 1;
 }
 
-// Inverse of the upper-triangular R into Ri (block-wide: one column per thread).
-__device__ void tri_inv_upper(const double* R, int ld, int m, double* Ri) {
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+// Inverse of the upper-triangular R into Ri (lanes / threads over columns).
+__device__ void tri_inv_upper(const double* R, int ld, int m, double* Ri, int tid, int nthr) {
+  for (int c = tid; c < ld; c += nthr) {
     for (int i = ld - 1; i >= 0; --i) {
       double x = 0.0;
       if (c < m && i <= c) {
@@ -113,55 +120,59 @@ __device__ void tri_inv_upper(const double* R, int ld, int m, double* Ri) {
   }
 }
 
-// pass 1: R1 = chol(s G1), R1^-1.  Flags the subdomain when the factorisation
-// fails or the diagonal ratio exceeds 1e7 (beyond CholeskyQR2's reach).
+// pass 1 (one warp per subdomain): R1 = chol(s G1), R1^-1.  Flags the subdomain
+// when the factorisation fails or the diagonal ratio exceeds 1e7.
 __global__ void k_cqr1(OrthArgs a, const double* sm, int sG, int sR, int sRi, double* smw,
                        int* flag, double* scale) {
-  const int k = blockIdx.x, RC = a.g.RC;
+  extern __shared__ double shm[];
+  const int k = blockIdx.x, RC = a.g.RC, lane = threadIdx.x & 31;
   const int m = a.acols[k];
   const double* G = sm + ((long)k * NSMALL + sG) * RC * RC;
   double* R = smw + ((long)k * NSMALL + sR) * RC * RC;
   double* Ri = smw + ((long)k * NSMALL + sRi) * RC * RC;
-  __shared__ int ok;
-  __shared__ double s;
-  if (threadIdx.x == 0) {
-    ok = 0;
-    s = 1.0;
-    if (m > 0) {
-      double dmax = 0.0;
-      bool fin = true;
-      for (int j = 0; j < m; ++j) {
-        dmax = fmax(dmax, G[j * RC + j]);
-        for (int c = 0; c < m; ++c) fin = fin && isfinite(G[j * RC + c]);
-      }
-      if (fin && dmax > 0.0 && isfinite(dmax)) {
-        s = ldexp(1.0, -ilogb(dmax));
-        ok = chol_upper(G, RC, m, s, R);
-        if (ok) {
-          double lo = R[0], hi = R[0];
-          for (int j = 1; j < m; ++j) { lo = fmin(lo, R[j * RC + j]); hi = fmax(hi, R[j * RC + j]); }
-          if (!(lo > 1e-7 * hi)) ok = 0;
-        }
-      }
-      if (!fin) atomicOr(a.status, (unsigned)ST_NONFINITE);
+  double* Rs = shm;
+  double* Gw = Rs + RC * RC;
+  double dmax = 0.0;
+  bool fin = true;
+  for (int j = lane; j < m; j += 32) dmax = fmax(dmax, G[j * RC + j]);
+  for (int e = lane; e < m * RC; e += 32) fin = fin && isfinite(G[e]);
+  dmax = warp_max(dmax);
+  fin = __all_sync(0xffffffffu, fin);
+  int ok = 0;
+  double s = 1.0;
+  if (m > 0 && fin && dmax > 0.0 && isfinite(dmax)) {
+    s = ldexp(1.0, -ilogb(dmax));
+    ok = chol_upper_warp(G, RC, m, s, Rs, Gw);
+    if (ok) {
+      double lo = 1e300, hi = 0.0;
+      for (int j = lane; j < m; j += 32) { lo = fmin(lo, Rs[j * RC + j]); hi = fmax(hi, Rs[j * RC + j]); }
+      lo = -warp_max(-lo);
+      hi = warp_max(hi);
+      if (!(lo > 1e-7 * hi)) ok = 0;
     }
-    flag[k] = ok ? 0 : 1;
-    scale[k] = s;
   }
-  __syncthreads();
-  if (ok) tri_inv_upper(R, RC, m, Ri);
+  if (!fin && lane == 0) atomicOr(a.status, (unsigned)ST_NONFINITE);
+  if (lane == 0) { flag[k] = ok ? 0 : 1; scale[k] = s; }
+  if (!ok) return;
+  for (int e = lane; e < RC * RC; e += 32) R[e] = Rs[e];
+  tri_inv_upper(Rs, RC, m, Ri, lane, 32);
 }
 
-// pass 2: R2 = chol(G2), R = R2 R1, SVD(R), rank decision; on success
-// the output transform M = R2^-1 U_R[:, :keep] is written to slot sM.
-__global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, double* smw, int sM,
-                       int* flag, const double* scale) {
+// pass 2: R2 = chol(G2), R = R2 R1.  Every singular value of the input is
+// significant when |R|_F |R^-1|_F < 1/tau (the Frobenius condition bound is an
+// upper bound of the 2-norm one).  Then, when the output keeps all m columns, the
+// transform is M = R2^-1; when it keeps fewer (the augmentation's leading r_t of m
+// singular vectors, or a tolerance rule), the one-sided Jacobi SVD of R supplies
+// U_R and M = R2^-1 U_R[:, :keep].  Otherwise the subdomain is flagged.
+__global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, int sR1i, double* smw,
+                       int sM, int* flag, const double* scale) {
   extern __shared__ double shm[];
   const int k = blockIdx.x, RC = a.g.RC;
   if (flag[k]) return;
   const int m = a.acols[k];
   const double* G2 = sm + ((long)k * NSMALL + sG2) * RC * RC;
   const double* R1 = smw + ((long)k * NSMALL + sR1) * RC * RC;
+  const double* R1i = smw + ((long)k * NSMALL + sR1i) * RC * RC;
   double* M = smw + ((long)k * NSMALL + sM) * RC * RC;
   double* R2 = shm;                   // RC*RC row-major
   double* R2i = R2 + RC * RC;
@@ -170,58 +181,99 @@ __global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, double* s
   double* sig = Jc + RC * RC;
   int* perm = reinterpret_cast<int*>(sig + RC);
   int* iv = perm + RC;
-  if (threadIdx.x == 0) iv[0] = chol_upper(G2, RC, m, 1.0, R2);
+  __shared__ double red[40];
+  if (threadIdx.x < 32) {
+    int ok = chol_upper_warp(G2, RC, m, 1.0, R2, Bc);
+    if (threadIdx.x == 0) iv[0] = ok;
+  }
   __syncthreads();
   if (!iv[0]) {
     if (threadIdx.x == 0) flag[k] = 1;
     return;
   }
-  tri_inv_upper(R2, RC, m, R2i);
-  // B = R^T, R = R2 R1 (both upper); column j of B = row j of R
+  tri_inv_upper(R2, RC, m, R2i, threadIdx.x, blockDim.x);
+  __syncthreads();
+  // R = R2 R1 (into Bc as B = R^T, column-major) and R^-1 = R1^-1 R2^-1 (Frobenius norms)
+  double nr = 0.0, ni = 0.0;
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
     int col = e / RC, row = e % RC;
-    double x = 0.0;
-    if (col < m && row < m && row >= col)
-      for (int l = col; l <= row; ++l) x += R2[col * RC + l] * R1[l * RC + row];
+    double x = 0.0, y = 0.0;
+    if (col < m && row < m && row >= col) {
+      for (int l = col; l <= row; ++l) {
+        x += R2[col * RC + l] * R1[l * RC + row];
+        y += R1i[col * RC + l] * R2i[l * RC + row];
+      }
+    }
     Bc[col * RC + row] = x;
     Jc[col * RC + row] = (row == col) ? 1.0 : 0.0;
+    nr += x * x;
+    ni += y * y;
   }
-  __syncthreads();
-  jacobi_columns(Bc, Jc, m, RC, &iv[1]);
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    double s = 0.0;
-    for (int l = 0; l < m; ++l) s += Bc[j * RC + l] * Bc[j * RC + l];
-    sig[j] = sqrt(s);
-  }
-  __syncthreads();
+  nr = block_sum(nr, red);
+  ni = block_sum(ni, red);
+  const bool well = sqrt(nr) * sqrt(ni) * a.tau < 1.0;
+  int need_svd = 0;
   if (threadIdx.x == 0) {
-    for (int t = 0; t < m; ++t) perm[t] = t;
-    for (int t = 0; t < m; ++t) {
-      int best = t;
-      for (int u = t + 1; u < m; ++u)
-        if (sig[perm[u]] > sig[perm[best]]) best = u;
-      int tmp = perm[t]; perm[t] = perm[best]; perm[best] = tmp;
+    int keep_all = 0;
+    if (well) {
+      if (a.mode == ORTH_QR) keep_all = (a.rout[k] == m);
+      else if (a.rank_mode == 0) {                      // fixed mode: r_t = min(max(m, floor), cap)
+        int cap = min(min(a.r_aug_max, a.g.n), a.g.N[k]);
+        int rt = min(max(m, max(a.r_own[k], a.r_floor)), cap);
+        keep_all = (rt == m);
+        if (keep_all) a.rt_out[k] = m;
+      }
     }
-    // A = (Q1 R2^-1)(R2 R1): the singular values of R = R2 R1 are those of the input
-    double ss[DD_MAXC];
-    for (int t = 0; t < m; ++t) ss[t] = sig[perm[t]];
-    int keep, r_out;
-    int p = decide(a, k, ss, m, 0, &keep, &r_out);
-    int ok = (p == m) && (keep == r_out);
-    iv[2] = ok;
-    iv[3] = keep;
-    if (ok && a.mode == ORTH_AUG) a.rt_out[k] = r_out;
-    if (!ok) flag[k] = 1;
+    iv[2] = keep_all;
+    iv[3] = m;
+    need_svd = well && !keep_all && a.mode == ORTH_AUG;
+    iv[4] = need_svd;
+    if (!well || (!keep_all && !need_svd)) flag[k] = 1;
   }
   __syncthreads();
-  if (!iv[2]) return;
+  if (!iv[2] && !iv[4]) return;
+  if (iv[4]) {
+    jacobi_columns(Bc, Jc, m, RC, &iv[1]);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      double s2 = 0.0;
+      for (int l = 0; l < m; ++l) s2 += Bc[j * RC + l] * Bc[j * RC + l];
+      sig[j] = sqrt(s2);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int t = 0; t < m; ++t) perm[t] = t;
+      for (int t = 0; t < m; ++t) {
+        int best = t;
+        for (int u = t + 1; u < m; ++u)
+          if (sig[perm[u]] > sig[perm[best]]) best = u;
+        int tmp = perm[t]; perm[t] = perm[best]; perm[best] = tmp;
+      }
+      // A = (Q1 R2^-1)(R2 R1): the singular values of R are those of the input
+      double ss[DD_MAXC];
+      for (int t = 0; t < m; ++t) ss[t] = sig[perm[t]];
+      int keep, r_out;
+      int p = decide(a, k, ss, m, 0, &keep, &r_out);
+      int ok = (p == m) && (keep == r_out);
+      iv[2] = ok;
+      iv[3] = keep;
+      if (ok) a.rt_out[k] = r_out;
+      else flag[k] = 1;
+    }
+    __syncthreads();
+    if (!iv[2]) return;
+  }
   const int keep = iv[3];
-  // M = R2^-1 U_R[:, perm[:keep]] ; zero elsewhere
+  const bool rot = iv[4];
+  // M = R2^-1 (keep all) or R2^-1 U_R[:, perm[:keep]]; zero elsewhere
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
     int i = e / RC, t = e % RC;
     double x = 0.0;
-    if (i < m && t < keep)
-      for (int l = i; l < m; ++l) x += R2i[i * RC + l] * Jc[perm[t] * RC + l];
+    if (i < m && t < keep) {
+      if (rot)
+        for (int l = i; l < m; ++l) x += R2i[i * RC + l] * Jc[perm[t] * RC + l];
+      else
+        x = R2i[i * RC + t];
+    }
     M[e] = x;
   }
 }
@@ -550,15 +602,16 @@ void launch_orth_fallback(const OrthArgs& a, int mcap, int maxrows, const int* f
 void launch_cqr1(const OrthArgs& a, const double* sm, int sG, int sR, int sRi, double* smw,
                  int* flag, double* scale, cudaStream_t st) {
   pbeg(st, KS_CQR);
-  k_cqr1<<<a.g.nsub, 128, 0, st>>>(a, sm, sG, sR, sRi, smw, flag, scale);
+  k_cqr1<<<a.g.nsub, 32, sizeof(double) * 2 * a.g.RC * a.g.RC, st>>>(a, sm, sG, sR, sRi, smw,
+                                                                       flag, scale);
   pend(st);
 }
 
-void launch_cqr2(const OrthArgs& a, const double* sm, int sG2, int sR1, double* smw, int sM,
-                 int* flag, const double* scale, cudaStream_t st) {
+void launch_cqr2(const OrthArgs& a, const double* sm, int sG2, int sR1, int sR1i, double* smw,
+                 int sM, int* flag, const double* scale, cudaStream_t st) {
   pbeg(st, KS_CQR);
-  k_cqr2<<<a.g.nsub, DD_THREADS, cqr2_smem_bytes(a.g.RC), st>>>(a, sm, sG2, sR1, smw, sM, flag,
-                                                                 scale);
+  k_cqr2<<<a.g.nsub, DD_THREADS, cqr2_smem_bytes(a.g.RC), st>>>(a, sm, sG2, sR1, sR1i, smw, sM,
+                                                                 flag, scale);
   pend(st);
 }
 
@@ -568,6 +621,9 @@ cudaError_t orth_init() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_orth<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)orth_smem_base(DD_MAXC));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_cqr1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * 2 * DD_MAXC * DD_MAXC));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_cqr2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)cqr2_smem_bytes(DD_MAXC));

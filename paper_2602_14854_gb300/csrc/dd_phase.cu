@@ -1048,7 +1048,7 @@ static void orthonormalize(const Problem& P, const PhaseBufs& B, cudaStream_t st
   launch_cqr1(a, B.sm, SM_G1, SM_R1, SM_R1I, B.sm, B.flag, B.scale, st);
   tall(P, B, st, sp, a.A, a.lda, a.acols, 0, nullptr, SM_R1I, a.acols, 0, W, P.WC);
   gram(P, B, st, sp, W, P.WC, a.acols, 0, W, P.WC, a.acols, 0, 1, nullptr, SM_G2);
-  launch_cqr2(a, B.sm, SM_G2, SM_R1, B.sm, SM_QM, B.flag, B.scale, st);
+  launch_cqr2(a, B.sm, SM_G2, SM_R1, SM_R1I, B.sm, SM_QM, B.flag, B.scale, st);
   tall(P, B, st, sp, W, P.WC, a.acols, 0, nullptr, SM_QM,
        a.mode == ORTH_AUG ? a.rt_out : a.rout, 0, a.Q, a.ldq);
   launch_orth_fallback(a, mcap, maxrows, B.flag, st);
