@@ -109,10 +109,20 @@ __device__ __forceinline__ void rr_pair(int mm, int r, int i, int* p, int* q) {
 
 // One-sided Jacobi (Hestenes) on the m columns (length m) of the column-major
 // matrix Bc (leading dimension ld), accumulating the rotations in Jc, until no
-// pair has |b_p . b_q| > 1e-15 |b_p| |b_q|.  Block-wide; flag is shared scratch.
+// pair has |b_p . b_q| > 1e-15 |b_p| |b_q| and > 1e-30 |B|_F^2 (pairs of columns
+// that are negligible against the whole matrix are left alone: rotating rounding
+// noise never converges and cannot change the significant directions).
+// Block-wide; flag is shared scratch.
 __device__ __forceinline__ void jacobi_columns(double* Bc, double* Jc, int m, int ld, int* flag) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int mm = m + (m & 1);
+  __shared__ double jred[40];
+  double nf = 0.0;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    double x = Bc[(e / m) * ld + e % m];
+    nf += x * x;
+  }
+  const double abs_thr = 1e-30 * block_sum(nf, jred);
   for (int sweep = 0; sweep < 40 && m > 1; ++sweep) {
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
@@ -129,7 +139,7 @@ __device__ __forceinline__ void jacobi_columns(double* Bc, double* Jc, int m, in
           al += x * x; be += y * y; ga += x * y;
         }
         al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-        if (ga != 0.0 && fabs(ga) > JACOBI_TOL * sqrt(al * be)) {
+        if (fabs(ga) > abs_thr && fabs(ga) > JACOBI_TOL * sqrt(al * be)) {
           double zeta = (be - al) / (2.0 * ga);
           double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           double c = 1.0 / sqrt(1.0 + t * t), s = c * t;

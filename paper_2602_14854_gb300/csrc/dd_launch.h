@@ -12,7 +12,7 @@ enum KernelSlot {
   KS_AUG_COLS = 0, KS_BUILD_L0, KS_ORTH, KS_ANG_COEFFS, KS_REDUCE, KS_SMALL_ADV1, KS_TALL,
   KS_GHOST, KS_KSTEP_ADV, KS_SP_COEFFS, KS_SSTEP_ADV, KS_LSTEP_ADV, KS_GRAM, KS_TRUNC,
   KS_COLL_RANK, KS_COLL_A, KS_COLL_KSTEP, KS_COLL_SMALL, KS_COLL_LSTEP, KS_COLL_FINAL,
-  KS_FLUX, KS_COPY, KS_CQR, NSLOT
+  KS_FLUX, KS_COPY, KS_CQR1, KS_CQR2, NSLOT
 };
 extern const char* const kSlotNames[NSLOT];
 

@@ -601,7 +601,7 @@ void launch_orth_fallback(const OrthArgs& a, int mcap, int maxrows, const int* f
 
 void launch_cqr1(const OrthArgs& a, const double* sm, int sG, int sR, int sRi, double* smw,
                  int* flag, double* scale, cudaStream_t st) {
-  pbeg(st, KS_CQR);
+  pbeg(st, KS_CQR1);
   k_cqr1<<<a.g.nsub, 32, sizeof(double) * 2 * a.g.RC * a.g.RC, st>>>(a, sm, sG, sR, sRi, smw,
                                                                        flag, scale);
   pend(st);
@@ -609,7 +609,7 @@ void launch_cqr1(const OrthArgs& a, const double* sm, int sG, int sR, int sRi, d
 
 void launch_cqr2(const OrthArgs& a, const double* sm, int sG2, int sR1, int sR1i, double* smw,
                  int sM, int* flag, const double* scale, cudaStream_t st) {
-  pbeg(st, KS_CQR);
+  pbeg(st, KS_CQR2);
   k_cqr2<<<a.g.nsub, DD_THREADS, cqr2_smem_bytes(a.g.RC), st>>>(a, sm, sG2, sR1, sR1i, smw, sM,
                                                                  flag, scale);
   pend(st);

@@ -957,7 +957,7 @@ const char* const kSlotNames[NSLOT] = {
     "k_aug_cols", "k_build_L0", "k_orth", "k_ang_coeffs", "k_reduce", "k_small_adv1", "k_tall",
     "k_ghost", "k_kstep_adv", "k_sp_coeffs", "k_sstep_adv", "k_lstep_adv", "k_gram", "k_trunc",
     "k_coll_rank", "k_coll_a", "k_coll_kstep", "k_coll_small", "k_coll_lstep", "k_coll_final",
-    "k_flux", "memcpy", "k_cqr"};
+    "k_flux", "memcpy", "k_cqr1", "k_cqr2"};
 thread_local Prof* g_prof = nullptr;
 
 size_t part_elems(const Problem& P) {
