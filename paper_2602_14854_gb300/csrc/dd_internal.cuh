@@ -110,10 +110,15 @@ __device__ __forceinline__ void rr_pair(int mm, int r, int i, int* p, int* q) {
 // One-sided Jacobi (Hestenes) on the m columns (length m) of the column-major
 // matrix Bc (leading dimension ld), accumulating the rotations in Jc, until no
 // pair has |b_p . b_q| > 1e-15 |b_p| |b_q| and > 1e-30 |B|_F^2 (pairs of columns
-// that are negligible against the whole matrix are left alone: rotating rounding
-// noise never converges and cannot change the significant directions).
-// Block-wide; flag is shared scratch.
-__device__ __forceinline__ void jacobi_columns(double* Bc, double* Jc, int m, int ld, int* flag) {
+// negligible against the whole matrix are left alone: rotating rounding noise
+// never converges and cannot change the significant directions).
+// Column norms are recomputed at the start of every sweep and updated exactly in
+// between (a rotation with tangent t that annihilates gamma = b_p . b_q maps the
+// squared norms to alpha - t gamma and beta + t gamma), so each pair needs one
+// dot product.  The rotation is computed by lane 0 of the warp that owns the pair.
+// Block-wide; flag is shared scratch, nrm is m doubles of shared scratch.
+__device__ __forceinline__ void jacobi_columns(double* Bc, double* Jc, int m, int ld, int* flag,
+                                               double* nrm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int mm = m + (m & 1);
   __shared__ double jred[40];
@@ -124,6 +129,12 @@ __device__ __forceinline__ void jacobi_columns(double* Bc, double* Jc, int m, in
   }
   const double abs_thr = 1e-30 * block_sum(nf, jred);
   for (int sweep = 0; sweep < 40 && m > 1; ++sweep) {
+    for (int j = warp; j < m; j += nwarps) {
+      double s2 = 0.0;
+      for (int l = lane; l < m; l += 32) s2 += Bc[j * ld + l] * Bc[j * ld + l];
+      s2 = warp_sum(s2);
+      if (lane == 0) nrm[j] = s2;
+    }
     if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     for (int r = 0; r < mm - 1; ++r) {
@@ -133,25 +144,31 @@ __device__ __forceinline__ void jacobi_columns(double* Bc, double* Jc, int m, in
         if (p >= m || q >= m) continue;
         double* bp = Bc + p * ld;
         double* bq = Bc + q * ld;
-        double al = 0.0, be = 0.0, ga = 0.0;
+        double ga = 0.0;
+        for (int l = lane; l < m; l += 32) ga += bp[l] * bq[l];
+        ga = warp_sum(ga);
+        const double al = nrm[p], be = nrm[q];
+        if (!(fabs(ga) > abs_thr && fabs(ga) > JACOBI_TOL * sqrt(al * be))) continue;
+        double c = 0.0, s = 0.0, t = 0.0;
+        if (lane == 0) {
+          const double zeta = (be - al) / (2.0 * ga);
+          if (fabs(zeta) > 1e8) t = 0.5 / zeta;   // small angle: exact to rounding
+          else t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          c = rsqrt(1.0 + t * t);
+          s = c * t;
+          nrm[p] = al - t * ga;
+          nrm[q] = be + t * ga;
+          *flag = 1;
+        }
+        c = __shfl_sync(0xffffffffu, c, 0);
+        s = __shfl_sync(0xffffffffu, s, 0);
+        double* jp = Jc + p * ld;
+        double* jq = Jc + q * ld;
         for (int l = lane; l < m; l += 32) {
           double x = bp[l], y = bq[l];
-          al += x * x; be += y * y; ga += x * y;
-        }
-        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-        if (fabs(ga) > abs_thr && fabs(ga) > JACOBI_TOL * sqrt(al * be)) {
-          double zeta = (be - al) / (2.0 * ga);
-          double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-          double* jp = Jc + p * ld;
-          double* jq = Jc + q * ld;
-          for (int l = lane; l < m; l += 32) {
-            double x = bp[l], y = bq[l];
-            bp[l] = c * x - s * y; bq[l] = s * x + c * y;
-            x = jp[l]; y = jq[l];
-            jp[l] = c * x - s * y; jq[l] = s * x + c * y;
-          }
-          if (lane == 0) *flag = 1;
+          bp[l] = c * x - s * y; bq[l] = s * x + c * y;
+          x = jp[l]; y = jq[l];
+          jp[l] = c * x - s * y; jq[l] = s * x + c * y;
         }
       }
       __syncthreads();

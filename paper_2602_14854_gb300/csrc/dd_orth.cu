@@ -233,7 +233,7 @@ __global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, int sR1i,
   __syncthreads();
   if (!iv[2] && !iv[4]) return;
   if (iv[4]) {
-    jacobi_columns(Bc, Jc, m, RC, &iv[1]);
+    jacobi_columns(Bc, Jc, m, RC, &iv[1], sig);
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
       double s2 = 0.0;
       for (int l = 0; l < m; ++l) s2 += Bc[j * RC + l] * Bc[j * RC + l];
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a, int mcap, const
     }
 
     // ---- 4. one-sided Jacobi SVD of R, rank decision --------------------------------
-    jacobi_columns(sm.Bc, sm.Jc, nref, mcap, &iv[0]);
+    jacobi_columns(sm.Bc, sm.Jc, nref, mcap, &iv[0], sm.sig);
     for (int j = warp; j < nref; j += nwarps) {
       double s = 0.0;
       for (int l = lane; l < nref; l += 32) s += sm.Bc[j * mcap + l] * sm.Bc[j * mcap + l];

@@ -624,7 +624,7 @@ __global__ void k_trunc(Problem P, PhaseBufs B, int rank_fixed, int r_min, int r
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  jacobi_columns(Bc, Jc, rt, RC, &iv[0]);
+  jacobi_columns(Bc, Jc, rt, RC, &iv[0], sig);
   for (int j = warp; j < rt; j += nwarps) {
     double s = 0.0;
     for (int l = lane; l < rt; l += 32) s += Bc[j * RC + l] * Bc[j * RC + l];
