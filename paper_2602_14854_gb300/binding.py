@@ -25,7 +25,7 @@ DD_FP64 = 0
 EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scalar_flux",
            "dd_dlra_ranks", "dd_dlra_info", "dd_dlra_get_factors", "dd_dlra_set_factors",
            "dd_dlra_sync", "dd_dlra_destroy", "dd_last_error", "dd_profile_slots",
-           "dd_profile_slot_name", "dd_dlra_profile"]
+           "dd_profile_slot_name", "dd_dlra_profile", "dd_dlra_scalar_flux_noalloc"]
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -87,6 +87,7 @@ def load(path: str | None = None):
     lib.dd_profile_slot_name.argtypes = [C.c_int]
     lib.dd_profile_slot_name.restype = C.c_char_p
     lib.dd_dlra_profile.argtypes = [vp, C.c_int, _dp, _ip]
+    lib.dd_dlra_scalar_flux_noalloc.argtypes = [vp, vp]
     for name in EXPORTS:
         if name not in ("dd_dlra_destroy", "dd_last_error", "dd_profile_slot_name"):
             getattr(lib, name).restype = C.c_int
@@ -160,6 +161,11 @@ class Solver:
         rho = np.empty(self.wl.nx * self.wl.ny)
         _check(self.lib, self.lib.dd_dlra_scalar_flux(self.h, rho.ctypes.data_as(C.c_void_p), 0))
         return rho
+
+    def scalar_flux_noalloc(self, out):
+        """Density into the device pointer ``out`` without any allocation (see
+        dd_dlra_scalar_flux_noalloc in include/ddlra.h)."""
+        _check(self.lib, self.lib.dd_dlra_scalar_flux_noalloc(self.h, C.c_void_p(out)))
 
     def ranks(self):
         st = np.empty(self.nsub, dtype=np.int32)

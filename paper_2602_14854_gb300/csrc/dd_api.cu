@@ -55,6 +55,7 @@ double legendre(int l, double x) {
 
 struct dd_dlra {
   // problem
+  int device;
   int nx, ny, tx, ty, nsub, n;
   double hx, hy, sh, ssum;
   dd_options opt;
@@ -169,6 +170,27 @@ void free_all(dd_dlra* h) {
 
 }  // namespace
 
+namespace dd {
+
+dd_status set_error(dd_status s, const char* msg) { return fail(s, msg); }
+
+// Scalar flux with the per-subdomain scratch at a caller-supplied device address.
+dd_status noalloc_flux_impl(dd_dlra_t h, double* scratch, int scratch_doubles, double* out) {
+  g_err.clear();
+  int dev = -1;
+  DD_CUDA(cudaGetDevice(&dev));
+  if (dev != h->device) return fail(DD_ERR_ARG, "call on the device the solver was created on");
+  if ((long)h->nsub * h->RC > scratch_doubles)
+    return fail(DD_ERR_ARG, "nsub * r_cap = " + std::to_string((long)h->nsub * h->RC) +
+                                " exceeds the allocation-free scratch of " +
+                                std::to_string(scratch_doubles) + " doubles");
+  dd::scalar_flux(h->P, h->d_X[0], h->d_V[0], h->d_S[0], h->d_r[0], scratch, out, h->nx, h->stream);
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+}  // namespace dd
+
 extern "C" {
 
 const char* dd_last_error(void) { return g_err.c_str(); }
@@ -203,6 +225,7 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
   if (!(opt->dt > 0.0) || !(opt->tau >= 0.0)) return fail(DD_ERR_ARG, "dt / tau");
 
   dd_dlra* h = new dd_dlra();   // value-initialised: every device pointer starts null
+  cudaGetDevice(&h->device);
   h->nx = grid->nx; h->ny = grid->ny; h->tx = tiling->tx; h->ty = tiling->ty;
   h->nsub = h->tx * h->ty; h->n = quad->n;
   h->hx = (grid->x1 - grid->x0) / grid->nx;
