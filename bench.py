@@ -235,8 +235,9 @@ def run_ours(args, torch):
         roof["k_kstep_adv"] = {"launch_ms": kstep[0] / kstep[1],
                                "achieved_tflops": w / (kstep[0] / kstep[1] / 1e3) / 1e12,
                                "frac": w / (kstep[0] / kstep[1] / 1e3) / 1e12 / fp64_peak}
-    roof["kernels_ms_per_step"] = {k: v[0] / 4.0 for k, v in sorted(prof.items(),
-                                                                      key=lambda kv: -kv[1][0])}
+    roof["kernels_ms_per_step"] = {k: round(v[0] / 4.0, 4) for k, v in
+                                   sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    roof["launches_per_step"] = {k: v[1] / 4.0 for k, v in prof.items()}
 
     # ---- CPU baseline: the oracle on this machine's host cores ------------------------
     cpu = None

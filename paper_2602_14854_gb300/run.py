@@ -1,0 +1,56 @@
+"""Run the DD-DLRA time step on one of the synthetic workloads and print a JSON
+summary (scalar-flux statistics, ranks, wall time).
+
+    python -m paper_2602_14854_gb300.run --workload pointsource --steps 20 [--graph]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from paper_2602_14854_gb300 import binding, build, inputs
+
+WORKLOADS = {
+    "gaussian32": lambda: inputs.config_c0(),
+    "gaussian32-rk4": lambda: inputs.config_c0(integrator="rk4"),
+    "pointsource": lambda: inputs.config_c1(),
+    "checkerboard": lambda: inputs.checkerboard_problem(),
+    "lognormal": lambda: inputs.lognormal_problem(),
+}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="pointsource", choices=sorted(WORKLOADS))
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--graph", action="store_true")
+    ap.add_argument("--profile", type=int, default=0,
+                    help="additionally advance this many steps with per-kernel event timing")
+    args = ap.parse_args(argv)
+    build.build()
+    wl = WORKLOADS[args.workload]()
+    nsteps = wl.nsteps if args.steps is None else args.steps
+    s = binding.Solver(wl, use_graph=args.graph)
+    t0 = time.perf_counter()
+    s.step(nsteps)
+    s.sync()
+    t = time.perf_counter() - t0
+    prof = s.profile(args.profile) if args.profile else None
+    rho = s.scalar_flux()
+    stored, inter = s.ranks()
+    out = {"workload": wl.name, "steps": nsteps, "seconds": t,
+           "updates_per_s": wl.ncells * wl.n * nsteps / t,
+           "rho_sum": float(np.sum(rho)), "rho_max": float(np.max(rho)),
+           "ranks": stored.tolist(), "intermediate": inter.tolist()}
+    if prof:
+        out["profile_ms"] = {k: [round(v[0], 4), v[1]] for k, v in
+                             sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    s.close()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
