@@ -179,7 +179,8 @@ __global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, int sR1i,
   double* Bc = R2i + RC * RC;         // column-major B = R^T
   double* Jc = Bc + RC * RC;
   double* sig = Jc + RC * RC;
-  int* perm = reinterpret_cast<int*>(sig + RC);
+  double* pw = sig + RC;              // 2 x RC power-iteration vectors
+  int* perm = reinterpret_cast<int*>(pw + 2 * RC);
   int* iv = perm + RC;
   __shared__ double red[40];
   if (threadIdx.x < 32) {
@@ -211,7 +212,69 @@ __global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, int sR1i,
   }
   nr = block_sum(nr, red);
   ni = block_sum(ni, red);
-  const bool well = sqrt(nr) * sqrt(ni) * a.tau < 1.0;
+  bool well = sqrt(nr) * sqrt(ni) * a.tau < 1.0;
+  if (!well) {
+    // exact certificate: every singular value of R exceeds tau * sigma_max iff
+    // R^T R - tau^2 sigma_max^2 I is positive definite.  sigma_max^2 comes from a
+    // power iteration (a lower estimate, so the shift carries a 1% margin);
+    // cases within the margin go to the exact SVD / fallback.
+    double* GR = R2i;                 // scratch; R2^-1 is recomputed below
+    double* wv = pw;
+    double* wn = pw + RC;
+    __shared__ double lam;
+    __shared__ int cert;
+    // GR = R^T R from B (column c of B = row c of R)
+    __syncthreads();
+    double* G = Jc + 0;               // Jc is re-initialised before the SVD
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      int i = e / m, j = e % m;
+      double x = 0.0;
+      for (int l = 0; l < m; ++l) x += Bc[l * RC + i] * Bc[l * RC + j];
+      G[i * RC + j] = x;
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) wv[i] = 1.0 + 0.01 * i;
+    __syncthreads();
+    for (int it = 0; it < 40; ++it) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double x = 0.0;
+        for (int j = 0; j < m; ++j) x += G[i * RC + j] * wv[j];
+        wn[i] = x;
+      }
+      __syncthreads();
+      double nn = 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) nn += wn[i] * wn[i];
+      nn = block_sum(nn, red);
+      double dn = 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) dn += wn[i] * wv[i];
+      dn = block_sum(dn, red);
+      const double inv = nn > 0.0 ? rsqrt(nn) : 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) wv[i] = wn[i] * inv;
+      if (threadIdx.x == 0) lam = dn;   // Rayleigh quotient (w normalised after the first pass)
+      __syncthreads();
+    }
+    if (threadIdx.x < 32) {
+      const double shift = 1.01 * a.tau * a.tau * lam;
+      if (threadIdx.x == 0)
+        for (int i = 0; i < m; ++i) G[i * RC + i] -= shift;
+      __syncwarp();
+      int ok = lam > 0.0 ? chol_upper_warp(G, RC, m, 1.0, GR, Bc) : 0;
+      if (threadIdx.x == 0) cert = ok;
+    }
+    __syncthreads();
+    well = cert != 0;
+    // restore what the rest of the kernel reads: B = R^T, J = I, R2^-1
+    for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+      int col = e / RC, row = e % RC;
+      double x = 0.0;
+      if (col < m && row < m && row >= col)
+        for (int l = col; l <= row; ++l) x += R2[col * RC + l] * R1[l * RC + row];
+      Bc[col * RC + row] = x;
+      Jc[col * RC + row] = (row == col) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    tri_inv_upper(R2, RC, m, R2i, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
   int need_svd = 0;
   if (threadIdx.x == 0) {
     int keep_all = 0;
@@ -279,7 +342,7 @@ __global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, int sR1i,
 }
 
 size_t cqr2_smem_bytes(int RC) {
-  return sizeof(double) * (4 * RC * RC + RC) + sizeof(int) * (RC + 8);
+  return sizeof(double) * (4 * RC * RC + 3 * RC) + sizeof(int) * (RC + 8);
 }
 
 // ---------------------------------------------------------------------------
@@ -590,7 +653,9 @@ static const size_t kSmemLimit = 220 * 1024;
 void launch_orth_fallback(const OrthArgs& a, int mcap, int maxrows, const int* flag,
                           cudaStream_t st) {
   const size_t base = orth_smem_base(mcap);
-  const size_t need = base + sizeof(double) * ((size_t)maxrows * mcap + 8);
+  // the staged copy holds the input's columns: at most r_aug_max for a QR, mcap otherwise
+  const int wcols = a.mode == ORTH_QR ? min(mcap, a.r_aug_max) : mcap;
+  const size_t need = base + sizeof(double) * ((size_t)maxrows * wcols + 8);
   pbeg(st, KS_ORTH);
   if (need <= kSmemLimit)
     k_orth<true><<<a.g.nsub, DD_THREADS, need, st>>>(a, mcap, flag);
