@@ -57,7 +57,7 @@ struct OrthArgs {
 
 cudaError_t orth_init();
 void launch_orth_fallback(const OrthArgs& a, int mcap, int maxrows, const int* flag,
-                          cudaStream_t st);
+                          const double* sm_small, int sB, int sR2i, cudaStream_t st);
 void launch_cqr1(const OrthArgs& a, const double* sm, int sG, int sR, int sRi, double* smw,
                  int* flag, double* scale, cudaStream_t st);
 void launch_cqr2(const OrthArgs& a, const double* sm, int sG2, int sR1, int sR1i, double* smw,

@@ -294,50 +294,23 @@ __global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, int sR1i,
     if (!well || (!keep_all && !need_svd)) flag[k] = 1;
   }
   __syncthreads();
-  if (!iv[2] && !iv[4]) return;
   if (iv[4]) {
-    jacobi_columns(Bc, Jc, m, RC, &iv[1], sig);
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-      double s2 = 0.0;
-      for (int l = 0; l < m; ++l) s2 += Bc[j * RC + l] * Bc[j * RC + l];
-      sig[j] = sqrt(s2);
+    // leading singular vectors needed: leave B = R^T and R2^-1 for the SVD launch
+    double* Bo = smw + ((long)k * NSMALL + sG2) * RC * RC;
+    double* Ro = smw + ((long)k * NSMALL + sR1i) * RC * RC;
+    for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+      Bo[e] = Bc[e];
+      Ro[e] = R2i[e];
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int t = 0; t < m; ++t) perm[t] = t;
-      for (int t = 0; t < m; ++t) {
-        int best = t;
-        for (int u = t + 1; u < m; ++u)
-          if (sig[perm[u]] > sig[perm[best]]) best = u;
-        int tmp = perm[t]; perm[t] = perm[best]; perm[best] = tmp;
-      }
-      // A = (Q1 R2^-1)(R2 R1): the singular values of R are those of the input
-      double ss[DD_MAXC];
-      for (int t = 0; t < m; ++t) ss[t] = sig[perm[t]];
-      int keep, r_out;
-      int p = decide(a, k, ss, m, 0, &keep, &r_out);
-      int ok = (p == m) && (keep == r_out);
-      iv[2] = ok;
-      iv[3] = keep;
-      if (ok) a.rt_out[k] = r_out;
-      else flag[k] = 1;
-    }
-    __syncthreads();
-    if (!iv[2]) return;
+    if (threadIdx.x == 0) flag[k] = 2;
+    return;
   }
+  if (!iv[2]) return;
   const int keep = iv[3];
-  const bool rot = iv[4];
-  // M = R2^-1 (keep all) or R2^-1 U_R[:, perm[:keep]]; zero elsewhere
+  // M = R2^-1 (all columns kept); zero elsewhere
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
     int i = e / RC, t = e % RC;
-    double x = 0.0;
-    if (i < m && t < keep) {
-      if (rot)
-        for (int l = i; l < m; ++l) x += R2i[i * RC + l] * Jc[perm[t] * RC + l];
-      else
-        x = R2i[i * RC + t];
-    }
-    M[e] = x;
+    M[e] = (i < m && t < keep) ? R2i[i * RC + t] : 0.0;
   }
 }
 
@@ -358,6 +331,7 @@ struct OrthSmem {
   double* dv;   // double scalars
   int* perm;    // descending order of sig
   int* iv;      // integer scalars
+  double* X;    // scratch of the mixed-precision SVD (jacobi_mixed_scratch_bytes(mcap))
   double* W;    // staged matrix (shared-memory variant), column-major rows x m
 };
 
@@ -373,19 +347,25 @@ __device__ OrthSmem carve(void* base, int mcap) {
   s.dv = d; d += 8;
   s.perm = reinterpret_cast<int*>(d);
   s.iv = s.perm + DD_MAXC;
-  s.W = d + (DD_MAXC + 16) / 2;
+  d += (DD_MAXC + 16) / 2;
+  s.X = d;
+  d += (jacobi_mixed_scratch_bytes(mcap) + 7) / 8;
+  s.W = d;
   return s;
 }
 
 size_t orth_smem_base(int mcap) {
-  return sizeof(double) * (2 * mcap * mcap + 3 * DD_MAXC + 48) + sizeof(int) * (DD_MAXC + 16);
+  return sizeof(double) * (2 * mcap * mcap + 3 * DD_MAXC + 48) + sizeof(int) * (DD_MAXC + 16) +
+         8 * ((jacobi_mixed_scratch_bytes(mcap) + 7) / 8);
 }
 
 template <bool SMEM>
-__global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a, int mcap, const int* flag) {
+__global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a, int mcap, const int* flag,
+                                                      const double* sm_small, int sB, int sR2i) {
   extern __shared__ double smem_raw[];
   const int k = blockIdx.x;
   if (flag && flag[k] == 0) return;
+  const int how = flag ? flag[k] : 1;     // 1: full fallback, 2: SVD of the fast path's R
   OrthSmem sm = carve(smem_raw, mcap);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const Geo& g = a.g;
@@ -409,6 +389,62 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a, int mcap, const
       for (int t = 0; t < m; ++t) Q[(long)i * a.ldq + t] = A[(long)i * a.lda + t];
     keep = m;
     r_out = a.rout[k];
+    __syncthreads();
+  } else if (how == 2) {
+    // The fast path proved the input well conditioned and left B = R^T (A = Q1 R2^-1 R,
+    // Q1 in the workspace) and R2^-1: the left singular vectors of A are
+    // Q1 R2^-1 U_R, U_R from the SVD of R.
+    const int RC = g.RC;
+    const double* Bs = sm_small + ((long)k * NSMALL + sB) * RC * RC;
+    const double* R2i = sm_small + ((long)k * NSMALL + sR2i) * RC * RC;
+    for (int idx = tid; idx < mcap * mcap; idx += blockDim.x) {
+      int col = idx / mcap, row = idx % mcap;
+      sm.Bc[idx] = (col < m && row < m) ? Bs[col * RC + row] : 0.0;
+      sm.Jc[idx] = (row == col) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    jacobi_svd_mixed(sm.Bc, sm.Jc, m, mcap, &iv[0], sm.sig, sm.X);
+    for (int j = warp; j < m; j += nwarps) {
+      double s = 0.0;
+      for (int l = lane; l < m; l += 32) s += sm.Bc[j * mcap + l] * sm.Bc[j * mcap + l];
+      s = warp_sum(s);
+      if (lane == 0) sm.sig[j] = sqrt(s);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int t = 0; t < m; ++t) sm.perm[t] = t;
+      for (int t = 0; t < m; ++t) {
+        int best = t;
+        for (int u = t + 1; u < m; ++u)
+          if (sm.sig[sm.perm[u]] > sm.sig[sm.perm[best]]) best = u;
+        int tmp = sm.perm[t]; sm.perm[t] = sm.perm[best]; sm.perm[best] = tmp;
+      }
+      double ss[DD_MAXC];
+      for (int t = 0; t < m; ++t) ss[t] = sm.sig[sm.perm[t]];
+      decide(a, k, ss, m, 0, &keep, &r_out);
+      if (a.mode == ORTH_AUG) a.rt_out[k] = r_out;
+      iv[1] = keep;
+      iv[2] = r_out;
+    }
+    __syncthreads();
+    keep = iv[1];
+    r_out = iv[2];
+    // M = R2^-1 U_R[:, :keep] (column-major m x keep, in the mixed-SVD scratch)
+    double* M = sm.X;
+    for (int e = tid; e < m * keep; e += blockDim.x) {
+      int t = e / m, i = e % m;
+      double x = 0.0;
+      for (int l = i; l < m; ++l) x += R2i[i * RC + l] * sm.Jc[sm.perm[t] * mcap + l];
+      M[t * m + i] = x;
+    }
+    __syncthreads();
+    for (long idx = tid; idx < (long)rows * keep; idx += blockDim.x) {
+      int i = (int)(idx / keep), t = (int)(idx % keep);
+      const double* q1 = Wg + (long)i * a.ldw;
+      double x = 0.0;
+      for (int j = 0; j < m; ++j) x += q1[j] * M[t * m + j];
+      Q[(long)i * a.ldq + t] = x;
+    }
     __syncthreads();
   } else {
     // ---- 1. exact power-of-two scaling of a copy --------------------------------
@@ -522,7 +558,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a, int mcap, const
     }
 
     // ---- 4. one-sided Jacobi SVD of R, rank decision --------------------------------
-    jacobi_columns(sm.Bc, sm.Jc, nref, mcap, &iv[0], sm.sig);
+    jacobi_svd_mixed(sm.Bc, sm.Jc, nref, mcap, &iv[0], sm.sig, sm.X);
     for (int j = warp; j < nref; j += nwarps) {
       double s = 0.0;
       for (int l = lane; l < nref; l += 32) s += sm.Bc[j * mcap + l] * sm.Bc[j * mcap + l];
@@ -651,16 +687,16 @@ static const size_t kSmemLimit = 220 * 1024;
 
 // Launch the fallback kernel: shared-memory staging when rows x mcap fits.
 void launch_orth_fallback(const OrthArgs& a, int mcap, int maxrows, const int* flag,
-                          cudaStream_t st) {
+                          const double* sm_small, int sB, int sR2i, cudaStream_t st) {
   const size_t base = orth_smem_base(mcap);
   // the staged copy holds the input's columns: at most r_aug_max for a QR, mcap otherwise
   const int wcols = a.mode == ORTH_QR ? min(mcap, a.r_aug_max) : mcap;
   const size_t need = base + sizeof(double) * ((size_t)maxrows * wcols + 8);
   pbeg(st, KS_ORTH);
   if (need <= kSmemLimit)
-    k_orth<true><<<a.g.nsub, DD_THREADS, need, st>>>(a, mcap, flag);
+    k_orth<true><<<a.g.nsub, DD_THREADS, need, st>>>(a, mcap, flag, sm_small, sB, sR2i);
   else
-    k_orth<false><<<a.g.nsub, DD_THREADS, base, st>>>(a, mcap, flag);
+    k_orth<false><<<a.g.nsub, DD_THREADS, base, st>>>(a, mcap, flag, sm_small, sB, sR2i);
   pend(st);
 }
 
@@ -685,7 +721,7 @@ cudaError_t orth_init() {
                                        (int)kSmemLimit);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_orth<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)orth_smem_base(DD_MAXC));
+                           (int)orth_smem_base(DD_MAXC) + 64);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_cqr1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(double) * 2 * DD_MAXC * DD_MAXC));

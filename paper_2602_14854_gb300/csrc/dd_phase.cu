@@ -613,7 +613,8 @@ __global__ void k_trunc(Problem P, PhaseBufs B, int rank_fixed, int r_min, int r
   double* Bc = sh;                 // column-major, column j = column j of S3^T = row j of S3
   double* Jc = Bc + RC * RC;       // column-major rotations
   double* sig = Jc + RC * RC;
-  int* perm = reinterpret_cast<int*>(sig + RC);
+  double* X = sig + RC;            // scratch of the mixed-precision SVD
+  int* perm = reinterpret_cast<int*>(X + (jacobi_mixed_scratch_bytes(RC) + 7) / 8);
   int* iv = perm + RC;
   const double* S3T = SMB(B, P, k, SM_S3T);
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
@@ -624,7 +625,7 @@ __global__ void k_trunc(Problem P, PhaseBufs B, int rank_fixed, int r_min, int r
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  jacobi_columns(Bc, Jc, rt, RC, &iv[0], sig);
+  jacobi_svd_mixed(Bc, Jc, rt, RC, &iv[0], sig, X);
   for (int j = warp; j < rt; j += nwarps) {
     double s = 0.0;
     for (int l = lane; l < rt; l += 32) s += Bc[j * RC + l] * Bc[j * RC + l];
@@ -938,6 +939,11 @@ __global__ void k_flux(Problem P, const double* X, const int* r, const double* w
   }
 }
 
+size_t trunc_smem(int RC) {
+  return sizeof(double) * (2 * RC * RC + RC) + 8 * ((jacobi_mixed_scratch_bytes(RC) + 7) / 8) +
+         sizeof(int) * (RC + 8);
+}
+
 size_t kstep_smem(const Problem& P, int lpb, int len) {
   const int RC = P.g.RC;
   return sizeof(double) * (3 * RC * RC + 2 * lpb * RC + (size_t)lpb * len * RC);
@@ -980,7 +986,7 @@ cudaError_t phase_init(const Problem& P) {
                            (int)(sizeof(double) * (2 * RC * RC + 2 * RC) + 64));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_trunc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * (2 * RC * RC + RC) + sizeof(int) * (RC + 8)));
+                           (int)trunc_smem(RC));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_coll_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(double) * (4 * RC * RC + 5 * RC)));
@@ -1051,7 +1057,7 @@ static void orthonormalize(const Problem& P, const PhaseBufs& B, cudaStream_t st
   launch_cqr2(a, B.sm, SM_G2, SM_R1, SM_R1I, B.sm, SM_QM, B.flag, B.scale, st);
   tall(P, B, st, sp, W, P.WC, a.acols, 0, nullptr, SM_QM,
        a.mode == ORTH_AUG ? a.rt_out : a.rout, 0, a.Q, a.ldq);
-  launch_orth_fallback(a, mcap, maxrows, B.flag, st);
+  launch_orth_fallback(a, mcap, maxrows, B.flag, B.sm, SM_G2, SM_R1I, st);
 }
 
 void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st) {
@@ -1139,7 +1145,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   gram(P, B, st, 0, B.V1, RC, B.rt, 0, B.L, RC, B.rt, 0, 1, nullptr, SM_S3T);
   // 11. truncation (Algorithm 5)
   pbeg(st, KS_TRUNC);
-  k_trunc<<<nsub, DD_THREADS, sizeof(double) * (2 * RC * RC + RC) + sizeof(int) * (RC + 8), st>>>(
+  k_trunc<<<nsub, DD_THREADS, trunc_smem(RC), st>>>(
       P, B, P.RS, P.r_floor, P.RS);
   pend(st);
   tall(P, B, st, 1, B.X1, RC, B.rt, 0, nullptr, SM_UB, B.ro, 0, B.Xo, RC);
@@ -1155,7 +1161,7 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_COMPLETE);
     a.A = B.V; a.lda = RC; a.acols = B.r; a.Q = B.Vh; a.ldq = RC; a.rout = B.rc;
-    launch_orth_fallback(a, RC, g.n, nullptr, st);
+    launch_orth_fallback(a, RC, g.n, nullptr, B.sm, SM_G2, SM_R1I, st);
   }
   pbeg(st, KS_COLL_A);
   k_coll_a<<<nsub, DD_THREADS, 0, st>>>(P, B);
