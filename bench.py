@@ -239,6 +239,34 @@ def run_ours(args, torch):
                                    sorted(prof.items(), key=lambda kv: -kv[1][0])}
     roof["launches_per_step"] = {k: v[1] / 4.0 for k, v in prof.items()}
 
+    # ---- mixed precision: same workload, same timing, error of a full run ------------
+    mixed = None
+    if not args.no_mixed:
+        sm_ = binding.Solver(wl, stream=sptr, use_graph=True, precision="mixed")
+        sm_.step(args.warmup)
+        torch.cuda.synchronize()
+        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evm[i][0].record(stream)
+            sm_.step(1)
+            evm[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_m = sum(a.elapsed_time(b) for a, b in evm) / 1e3
+        sm_.close()
+        err_m = None
+        if os.path.exists(GOLDEN):
+            s4 = binding.Solver(wl, stream=sptr, use_graph=True, precision="mixed")
+            s4.step(wl.nsteps)
+            err_m = float(np.linalg.norm(s4.scalar_flux() - g["rho"]) / np.linalg.norm(g["rho"]))
+            s4.close()
+        mixed = {"value": units * args.steps * ws / t_m, "unit": UNIT,
+                 "ms_per_step": t_m / args.steps * 1e3, "flux_rel_l2_vs_oracle": err_m,
+                 "speedup_vs_fp64": t_ours / t_m,
+                 "arithmetic": "FP32: stencil, K/L/collision ODEs, eigen-split, augmentation "
+                               "SVD; FP64: CholeskyQR2, truncation SVD, reductions, storage"}
+
     # ---- CPU baseline: the oracle on this machine's host cores ------------------------
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -265,6 +293,8 @@ def run_ours(args, torch):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if mixed is not None:
+        line["mixed"] = mixed
     return line, rank
 
 
@@ -321,6 +351,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     ws, rank, local = dist_env()

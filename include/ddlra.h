@@ -80,7 +80,11 @@ typedef struct dd_fields {
 
 enum { DD_RANK_FIXED = 0, DD_RANK_TOL = 1 };
 enum { DD_EULER = 0, DD_RK4 = 1 };
-enum { DD_FP64 = 0 };
+/* Arithmetic of the step.  DD_FP64: FP64 throughout.  DD_MIXED: FP32 arithmetic for
+ * the eigen-upwind stencil and the K-, L- and collision-step ODEs, the eigen-split of
+ * C and the augmentation SVD; FP64 for CholeskyQR2 (Grams, factors), the truncation
+ * SVD of S, every reduction and the stored factors. */
+enum { DD_FP64 = 0, DD_MIXED = 1 };
 
 typedef struct dd_options {
   int rank_mode;      /* DD_RANK_FIXED: stored rank <= rank; DD_RANK_TOL: tolerance tol   */
@@ -92,7 +96,7 @@ typedef struct dd_options {
   double c_adv;       /* advection speed                                                  */
   double dt;          /* time step                                                        */
   double tau;         /* relative numerical-rank threshold (sigma_j <= tau*sigma_1 -> 0)  */
-  int precision;      /* DD_FP64                                                          */
+  int precision;      /* DD_FP64 or DD_MIXED                                              */
 } dd_options;
 
 typedef struct dd_dlra* dd_dlra_t;

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "DD_OK", 1: "DD_ERR_ARG", 2: "DD_ERR_CUDA", 3: "DD_ERR_RANK_C
                 4: "DD_ERR_NONFINITE", 5: "DD_ERR_COMPLETION", 6: "DD_ERR_STATE"}
 DD_RANK_FIXED, DD_RANK_TOL = 0, 1
 DD_EULER, DD_RK4 = 0, 1
-DD_FP64 = 0
+DD_FP64, DD_MIXED = 0, 1
 
 # every symbol include/ddlra.h declares
 EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scalar_flux",
@@ -117,7 +117,8 @@ def _ptr(a):
 class Solver:
     """DD-DLRA solver on one problem; wraps a dd_dlra_t handle."""
 
-    def __init__(self, wl, tau: float = 1e-5, stream: int = 0, use_graph: bool = False):
+    def __init__(self, wl, tau: float = 1e-5, stream: int = 0, use_graph: bool = False,
+                 precision: str = "fp64"):
         lib = load()
         self.lib = lib
         self.wl = wl
@@ -134,7 +135,7 @@ class Solver:
         fixed = wl.rank_mode == "fixed"
         opt = Options(DD_RANK_FIXED if fixed else DD_RANK_TOL, wl.rank, wl.tol, wl.r_min,
                       wl.r_max, wl.r_aug_max, DD_RK4 if wl.integrator == "rk4" else DD_EULER,
-                      wl.c_adv, wl.dt, tau, DD_FP64)
+                      wl.c_adv, wl.dt, tau, DD_MIXED if precision == "mixed" else DD_FP64)
         h = C.c_void_p()
         _check(lib, lib.dd_dlra_create(C.byref(grid), C.byref(til), C.byref(quad),
                                        C.byref(fld), _ptr(g0), C.byref(opt),

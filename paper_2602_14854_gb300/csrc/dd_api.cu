@@ -221,7 +221,8 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
     return fail(DD_ERR_ARG, "rank_mode");
   if (opt->integrator != DD_EULER && opt->integrator != DD_RK4)
     return fail(DD_ERR_ARG, "integrator");
-  if (opt->precision != DD_FP64) return fail(DD_ERR_ARG, "precision");
+  if (opt->precision != DD_FP64 && opt->precision != DD_MIXED)
+    return fail(DD_ERR_ARG, "precision");
   if (!(opt->dt > 0.0) || !(opt->tau >= 0.0)) return fail(DD_ERR_ARG, "dt / tau");
 
   dd_dlra* h = new dd_dlra();   // value-initialised: every device pointer starts null
@@ -369,6 +370,7 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
   P.sig_s = h->d_sig_s; P.sig_t = h->d_sig_t; P.sQ = h->d_sQ;
   P.hx = h->hx; P.hy = h->hy; P.sh = h->sh; P.dt = opt->dt; P.c_adv = opt->c_adv; P.ssum = h->ssum;
   P.integrator = opt->integrator; P.rank_mode = opt->rank_mode; P.tol = opt->tol;
+  P.prec = opt->precision == DD_MIXED ? 1 : 0;
   P.tau = opt->tau; P.accept = 0.5;
   P.r_floor = h->r_floor; P.r_aug_max = opt->r_aug_max; P.RS = h->RS; P.WC = WC;
   P.angcand = h->d_angcand; P.n_angcand = h->n_angcand; P.angcand_complete = h->angcand_complete;

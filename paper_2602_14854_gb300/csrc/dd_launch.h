@@ -53,6 +53,7 @@ struct OrthArgs {
   const double* angcand; int n_angcand; int angcand_complete;
   double* sig_out; int* p_out;
   unsigned* status;
+  int svd_fp32;           // mixed path: the SVD of the augmentation in FP32
 };
 
 cudaError_t orth_init();
@@ -113,6 +114,7 @@ struct Problem {
   const double* sig_s; const double* sig_t; const double* sQ;  // per cell (spatial row order); sQ = sqrt(hx hy) Q
   double hx, hy, sh, dt, c_adv, ssum;
   int integrator;         // 0 Euler, 1 RK4
+  int prec;               // 0 FP64 arithmetic throughout, 1 mixed (FP32 where allowed)
   int rank_mode; double tol; double tau; double accept;
   int r_floor, r_aug_max, RS;
   int WC;                 // leading dimension of the Householder workspaces, max(MC, RC)

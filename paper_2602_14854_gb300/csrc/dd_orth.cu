@@ -403,7 +403,8 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a, int mcap, const
       sm.Jc[idx] = (row == col) ? 1.0 : 0.0;
     }
     __syncthreads();
-    jacobi_svd_mixed(sm.Bc, sm.Jc, m, mcap, &iv[0], sm.sig, sm.X);
+    if (a.svd_fp32) jacobi_svd_fp32(sm.Bc, sm.Jc, m, mcap, &iv[0], sm.sig, sm.X);
+    else jacobi_svd_mixed(sm.Bc, sm.Jc, m, mcap, &iv[0], sm.sig, sm.X);
     for (int j = warp; j < m; j += nwarps) {
       double s = 0.0;
       for (int l = lane; l < m; l += 32) s += sm.Bc[j * mcap + l] * sm.Bc[j * mcap + l];
@@ -558,7 +559,8 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a, int mcap, const
     }
 
     // ---- 4. one-sided Jacobi SVD of R, rank decision --------------------------------
-    jacobi_svd_mixed(sm.Bc, sm.Jc, nref, mcap, &iv[0], sm.sig, sm.X);
+    if (a.svd_fp32) jacobi_svd_fp32(sm.Bc, sm.Jc, nref, mcap, &iv[0], sm.sig, sm.X);
+    else jacobi_svd_mixed(sm.Bc, sm.Jc, nref, mcap, &iv[0], sm.sig, sm.X);
     for (int j = warp; j < nref; j += nwarps) {
       double s = 0.0;
       for (int l = lane; l < nref; l += 32) s += sm.Bc[j * mcap + l] * sm.Bc[j * mcap + l];

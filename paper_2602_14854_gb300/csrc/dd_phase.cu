@@ -161,6 +161,7 @@ __global__ void k_gram(Geo g, GramArgs a) {
 // small per-subdomain algebra: B = S M, B_lo = S_lo Min_lo, B_hi = S_hi Min_hi,
 // Jacobi eigendecomposition of C -> C+, C-, |C|  (Appendix A)
 // ---------------------------------------------------------------------------
+template <typename TC>
 __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
   extern __shared__ double sh[];
   const int k = blockIdx.x, RC = P.g.RC;
@@ -176,16 +177,16 @@ __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
   if (hi >= 0)
     bmm(SMB(B, P, k, SM_B_HI), RC, 1.0, B.S + (long)hi * RC * RC, RC, SMB(B, P, k, SM_MIN_HI), RC,
         rhi, rt, rhi, false);
-  // Jacobi eigendecomposition of the symmetric rt x rt matrix C
-  double* Cm = sh;                  // RC*RC
-  double* Pm = sh + RC * RC;        // RC*RC (eigenvectors, row-major: Pm[i*RC + j] = P_ij)
-  double* cs = sh + 2 * RC * RC;    // RC/2 cosines
-  double* sn = cs + RC;             // RC/2 sines
+  // Jacobi eigendecomposition of the symmetric rt x rt matrix C (arithmetic TC)
+  TC* Cm = reinterpret_cast<TC*>(sh);   // RC*RC
+  TC* Pm = Cm + RC * RC;                // RC*RC (eigenvectors, row-major: Pm[i*RC + j] = P_ij)
+  TC* cs = Pm + RC * RC;                // RC/2 cosines
+  TC* sn = cs + RC;                     // RC/2 sines
   const double* Csrc = SMB(B, P, k, SM_C);
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
     int i = e / RC, j = e % RC;
-    Cm[e] = (i < rt && j < rt) ? 0.5 * (Csrc[i * RC + j] + Csrc[j * RC + i]) : 0.0;
-    Pm[e] = (i == j) ? 1.0 : 0.0;
+    Cm[e] = (TC)((i < rt && j < rt) ? 0.5 * (Csrc[i * RC + j] + Csrc[j * RC + i]) : 0.0);
+    Pm[e] = (i == j) ? (TC)1 : (TC)0;
   }
   __syncthreads();
   const int mm = rt + (rt & 1);
@@ -193,10 +194,11 @@ __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
   __shared__ int rotated;
   double nf = 0.0;
   for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
-    double x = Cm[(e / rt) * RC + e % rt];
+    double x = (double)Cm[(e / rt) * RC + e % rt];
     nf += x * x;
   }
-  const double thr = JACOBI_TOL * sqrt(block_sum(nf, red));   // |C_pq| <= 1e-15 |C|_F is converged
+  // |C_pq| <= tol |C|_F counts as converged (1e-15 in FP64, 1e-7 in FP32)
+  const TC thr = (TC)((sizeof(TC) == 8 ? JACOBI_TOL : 1e-7) * sqrt(block_sum(nf, red)));
   for (int sweep = 0; sweep < 40 && rt > 1; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
@@ -204,13 +206,13 @@ __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
       for (int pi = threadIdx.x; pi < mm / 2; pi += blockDim.x) {
         int p, q;
         rr_pair(mm, rnd, pi, &p, &q);
-        double c = 1.0, s = 0.0;
+        TC c = 1, s = 0;
         if (p < rt && q < rt) {
-          double apq = Cm[p * RC + q];
+          TC apq = Cm[p * RC + q];
           if (fabs(apq) > thr) {
-            double zeta = (Cm[q * RC + q] - Cm[p * RC + p]) / (2.0 * apq);
-            double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c = 1.0 / sqrt(1.0 + t * t);
+            TC zeta = (Cm[q * RC + q] - Cm[p * RC + p]) / (2 * apq);
+            TC t = (zeta >= 0 ? (TC)1 : (TC)-1) / (fabs(zeta) + sqrt((TC)1 + zeta * zeta));
+            c = rsqrt_t((TC)1 + t * t);
             s = c * t;
             rotated = 1;
           }
@@ -224,8 +226,8 @@ __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
         int p, q;
         rr_pair(mm, rnd, pi, &p, &q);
         if (p >= rt || q >= rt) continue;
-        double c = cs[pi], s = sn[pi];
-        double x = Cm[row * RC + p], y = Cm[row * RC + q];
+        TC c = cs[pi], s = sn[pi];
+        TC x = Cm[row * RC + p], y = Cm[row * RC + q];
         Cm[row * RC + p] = c * x - s * y;
         Cm[row * RC + q] = s * x + c * y;
         x = Pm[row * RC + p]; y = Pm[row * RC + q];
@@ -239,8 +241,8 @@ __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
         int p, q;
         rr_pair(mm, rnd, pi, &p, &q);
         if (p >= rt || q >= rt) continue;
-        double c = cs[pi], s = sn[pi];
-        double x = Cm[p * RC + col], y = Cm[q * RC + col];
+        TC c = cs[pi], s = sn[pi];
+        TC x = Cm[p * RC + col], y = Cm[q * RC + col];
         Cm[p * RC + col] = c * x - s * y;
         Cm[q * RC + col] = s * x + c * y;
       }
@@ -259,8 +261,8 @@ __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
     double sp = 0.0, sm = 0.0;
     if (i < rt && j < rt)
       for (int l = 0; l < rt; ++l) {
-        double lam = Cm[l * RC + l];
-        double pp = Pm[i * RC + l] * Pm[j * RC + l];
+        double lam = (double)Cm[l * RC + l];
+        double pp = (double)Pm[i * RC + l] * (double)Pm[j * RC + l];
         if (lam > 0.0) sp += lam * pp;
         else if (lam < 0.0) sm += lam * pp;
       }
@@ -335,8 +337,12 @@ __global__ void k_ghost(Problem P, PhaseBufs B, int axis) {
 // K-step of the advection (Appendix A), all RK stages fused; a CTA owns whole lines
 // ---------------------------------------------------------------------------
 #define KS_EPT 24
+// TC: arithmetic type (double for the FP64 path, float for the mixed path); the
+// factors stay FP64 in memory.
+template <typename TC>
 __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B, int axis, int lpb) {
-  extern __shared__ double sh[];
+  extern __shared__ double sh_raw[];
+  TC* sh = reinterpret_cast<TC*>(sh_raw);
   const int k = blockIdx.y, RC = P.g.RC;
   const Lines L = lines_of(P.g, k, axis);
   const int l0 = blockIdx.x * lpb;
@@ -344,48 +350,49 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
   const int nl = min(lpb, L.nlines - l0);
   const int rt = B.rt[k];
   const int len = L.len;
-  double* Cp = sh;
-  double* Cn = Cp + RC * RC;
-  double* Ca = Cn + RC * RC;
-  double* Glo = Ca + RC * RC;          // lpb x RC
-  double* Ghi = Glo + lpb * RC;
-  double* Kst = Ghi + lpb * RC;        // lpb x len x rt
+  TC* Cp = sh;
+  TC* Cn = Cp + RC * RC;
+  TC* Ca = Cn + RC * RC;
+  TC* Glo = Ca + RC * RC;          // lpb x RC
+  TC* Ghi = Glo + lpb * RC;
+  TC* Kst = Ghi + lpb * RC;        // lpb x len x rt
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
-    Cp[e] = SMB(B, P, k, SM_CP)[e];
-    Cn[e] = SMB(B, P, k, SM_CM)[e];
-    Ca[e] = SMB(B, P, k, SM_CABS)[e];
+    Cp[e] = (TC)SMB(B, P, k, SM_CP)[e];
+    Cn[e] = (TC)SMB(B, P, k, SM_CM)[e];
+    Ca[e] = (TC)SMB(B, P, k, SM_CABS)[e];
   }
   for (int e = threadIdx.x; e < nl * RC; e += blockDim.x) {
     int li = e / RC, t = e % RC;
-    Glo[e] = B.Kb[(((long)k * 2 + 0) * P.maxlines + l0 + li) * RC + t];
-    Ghi[e] = B.Kb[(((long)k * 2 + 1) * P.maxlines + l0 + li) * RC + t];
+    Glo[e] = (TC)B.Kb[(((long)k * 2 + 0) * P.maxlines + l0 + li) * RC + t];
+    Ghi[e] = (TC)B.Kb[(((long)k * 2 + 1) * P.maxlines + l0 + li) * RC + t];
   }
   const int tot = nl * len * rt;
-  double k0[KS_EPT], acc[KS_EPT];
+  TC k0[KS_EPT], acc[KS_EPT];
   for (int i = 0; i < KS_EPT; ++i) {
     int e = threadIdx.x + i * blockDim.x;
-    k0[i] = 0.0; acc[i] = 0.0;
+    k0[i] = 0; acc[i] = 0;
     if (e < tot) {
       int li = e / (len * rt), pos = (e / rt) % len, t = e % rt;
       int cell = cell_of(L, l0 + li, pos);
-      k0[i] = B.K[((long)P.g.rowoff[k] + cell) * RC + t];
+      k0[i] = (TC)B.K[((long)P.g.rowoff[k] + cell) * RC + t];
       Kst[e] = k0[i];
     }
   }
   __syncthreads();
-  const double coef = -P.c_adv / (axis == 0 ? P.hx : P.hy);
+  const TC coef = (TC)(-P.c_adv / (axis == 0 ? P.hx : P.hy));
+  const TC dt = (TC)P.dt;
   const int nst = P.integrator == 1 ? 4 : 1;
   for (int s = 0; s < nst; ++s) {
-    double kv[KS_EPT];
+    TC kv[KS_EPT];
     for (int i = 0; i < KS_EPT; ++i) {
       int e = threadIdx.x + i * blockDim.x;
-      kv[i] = 0.0;
+      kv[i] = 0;
       if (e < tot) {
         int li = e / (len * rt), pos = (e / rt) % len, t = e % rt;
-        const double* Kc = Kst + (li * len + pos) * rt;
-        const double* Kp = pos > 0 ? Kc - rt : Glo + li * RC;
-        const double* Kn = pos < len - 1 ? Kc + rt : Ghi + li * RC;
-        double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        const TC* Kc = Kst + (li * len + pos) * rt;
+        const TC* Kp = pos > 0 ? Kc - rt : Glo + li * RC;
+        const TC* Kn = pos < len - 1 ? Kc + rt : Ghi + li * RC;
+        TC a1 = 0, a2 = 0, a3 = 0;
         for (int u = 0; u < rt; ++u) {
           a1 += Kc[u] * Ca[u * RC + t];
           a2 += Kp[u] * Cp[u * RC + t];
@@ -395,13 +402,13 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
       }
     }
     __syncthreads();
-    const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
-    const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
+    const TC bs = (TC)((nst == 4) ? c_rk_b[s] : 1.0);
+    const TC an = (TC)((s + 1 < nst) ? c_rk_a[s + 1] : 0.0);
     for (int i = 0; i < KS_EPT; ++i) {
       int e = threadIdx.x + i * blockDim.x;
       if (e < tot) {
         acc[i] += bs * kv[i];
-        if (s + 1 < nst) Kst[e] = k0[i] + an * P.dt * kv[i];
+        if (s + 1 < nst) Kst[e] = k0[i] + an * dt * kv[i];
       }
     }
     __syncthreads();
@@ -411,7 +418,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
     if (e < tot) {
       int li = e / (len * rt), pos = (e / rt) % len, t = e % rt;
       int cell = cell_of(L, l0 + li, pos);
-      B.K[((long)P.g.rowoff[k] + cell) * RC + t] = k0[i] + P.dt * acc[i];
+      B.K[((long)P.g.rowoff[k] + cell) * RC + t] = (double)(k0[i] + dt * acc[i]);
     }
   }
 }
@@ -523,16 +530,18 @@ __global__ void k_sstep_adv(Problem P, PhaseBufs B, int axis) {
 // L-step of the advection: every direction is an independent r_t-dimensional
 // linear ODE; one warp per direction, all RK stages fused.
 // ---------------------------------------------------------------------------
+template <typename TC>
 __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B, int axis) {
-  extern __shared__ double sh[];
+  extern __shared__ double sh_raw[];
+  TC* sh = reinterpret_cast<TC*>(sh_raw);
   const int k = blockIdx.y, RC = P.g.RC, n = P.g.n;
   const int rt = B.rt[k];
-  double* S2 = sh;
-  double* Ap = S2 + RC * RC;
-  double* Am = Ap + RC * RC;
-  double* Glo = Am + RC * RC;
-  double* Ghi = Glo + RC * RC;
-  double* wsp = Ghi + RC * RC;          // per warp: vh, L0, Ls, g  (4*RC)
+  TC* S2 = sh;
+  TC* Ap = S2 + RC * RC;
+  TC* Am = Ap + RC * RC;
+  TC* Glo = Am + RC * RC;
+  TC* Ghi = Glo + RC * RC;
+  TC* wsp = Ghi + RC * RC;          // per warp: vh, L0, Ls, g  (4*RC)
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
     S2[e] = SMB(B, P, k, SM_S2)[e];
     Ap[e] = SMB(B, P, k, SM_AP)[e];
@@ -542,25 +551,26 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* vh = wsp + warp * 4 * RC;
-  double* L0 = vh + RC;
-  double* Ls = L0 + RC;
-  double* gv = Ls + RC;
+  TC* vh = wsp + warp * 4 * RC;
+  TC* L0 = vh + RC;
+  TC* Ls = L0 + RC;
+  TC* gv = Ls + RC;
   const double* om = axis == 0 ? P.ox : P.oy;
-  const double hinv = 1.0 / (axis == 0 ? P.hx : P.hy);
+  const TC dt = (TC)P.dt;
+  const TC hinv = (TC)(1.0 / (axis == 0 ? P.hx : P.hy));
   const int nst = P.integrator == 1 ? 4 : 1;
   for (int q = blockIdx.x * 32 + warp; q < min(n, (int)(blockIdx.x + 1) * 32); q += nw) {
     const double* Vq = B.Vh + ((long)k * n + q) * RC;
     for (int t = lane; t < RC; t += 32) vh[t] = t < rt ? Vq[t] : 0.0;
     __syncwarp();
-    const double oq = om[q];
-    const double* A = oq > 0.0 ? Ap : Am;
-    const double kap = -P.c_adv * oq * hinv;
-    double accv[2] = {0.0, 0.0}, l0v[2] = {0.0, 0.0};
+    const TC oq = om[q];
+    const TC* A = oq > 0.0 ? Ap : Am;
+    const TC kap = (TC)(-P.c_adv) * oq * hinv;
+    TC accv[2] = {0.0, 0.0}, l0v[2] = {0.0, 0.0};
     for (int h = 0; h < 2; ++h) {
       int i = lane + 32 * h;
       if (i < rt) {
-        double s = 0.0, gg = 0.0;
+        TC s = 0.0, gg = 0.0;
         for (int j = 0; j < rt; ++j) {
           s += S2[i * RC + j] * vh[j];
           if (oq > 0.0) gg -= Glo[i * RC + j] * vh[j];
@@ -572,23 +582,23 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
     __syncwarp();
     if (oq != 0.0) {
       for (int s = 0; s < nst; ++s) {
-        double kv[2] = {0.0, 0.0};
+        TC kv[2] = {0.0, 0.0};
         for (int h = 0; h < 2; ++h) {
           int i = lane + 32 * h;
           if (i < rt) {
-            double a = gv[i];
+            TC a = gv[i];
             for (int j = 0; j < rt; ++j) a += A[i * RC + j] * Ls[j];
             kv[h] = kap * a;
           }
         }
         __syncwarp();
-        const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
-        const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
+        const TC bs = (nst == 4) ? c_rk_b[s] : 1.0;
+        const TC an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
         for (int h = 0; h < 2; ++h) {
           int i = lane + 32 * h;
           if (i < rt) {
             accv[h] += bs * kv[h];
-            if (s + 1 < nst) Ls[i] = l0v[h] + an * P.dt * kv[h];
+            if (s + 1 < nst) Ls[i] = l0v[h] + an * dt * kv[h];
           }
         }
         __syncwarp();
@@ -597,7 +607,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
     double* Lq = B.L + ((long)k * n + q) * RC;
     for (int h = 0; h < 2; ++h) {
       int i = lane + 32 * h;
-      if (i < RC) Lq[i] = i < rt ? l0v[h] + P.dt * accv[h] : 0.0;
+      if (i < RC) Lq[i] = i < rt ? (double)(l0v[h] + dt * accv[h]) : 0.0;
     }
     __syncwarp();
   }
@@ -706,16 +716,18 @@ __global__ void k_coll_a(Problem P, PhaseBufs B) {
 }
 
 // row-local collision K-step: dK_c/dt = (sig_s/|S|)(K_c . a) a - sig_t K_c + sQ_c a
+template <typename TC>
 __global__ void k_coll_kstep(Problem P, PhaseBufs B) {
   const int k = blockIdx.y, RC = P.g.RC;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int N = P.g.N[k], rc = B.rc[k];
   const double* a = SMB(B, P, k, SM_VEC);
+  const TC dt = (TC)P.dt;
   const int nst = P.integrator == 1 ? 4 : 1;
   for (int cell = blockIdx.x * nw + warp; cell < N; cell += gridDim.x * nw) {
     const long row = (long)P.g.rowoff[k] + cell;
-    const double ss = P.sig_s[row] / P.ssum, st = P.sig_t[row], sq = P.sQ[row];
-    double k0[2], ks[2], acc[2] = {0.0, 0.0}, av[2];
+    const TC ss = (TC)(P.sig_s[row] / P.ssum), st = (TC)P.sig_t[row], sq = (TC)P.sQ[row];
+    TC k0[2], ks[2], acc[2] = {0.0, 0.0}, av[2];
     for (int h = 0; h < 2; ++h) {
       int t = lane + 32 * h;
       k0[h] = t < rc ? B.K[row * RC + t] : 0.0;
@@ -723,19 +735,19 @@ __global__ void k_coll_kstep(Problem P, PhaseBufs B) {
       ks[h] = k0[h];
     }
     for (int s = 0; s < nst; ++s) {
-      double d = warp_sum(ks[0] * av[0] + ks[1] * av[1]);
-      double kv[2];
+      TC d = warp_sum_t<TC>(ks[0] * av[0] + ks[1] * av[1]);
+      TC kv[2];
       for (int h = 0; h < 2; ++h) kv[h] = ss * d * av[h] - st * ks[h] + sq * av[h];
-      const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
-      const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
+      const TC bs = (nst == 4) ? c_rk_b[s] : 1.0;
+      const TC an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
       for (int h = 0; h < 2; ++h) {
         acc[h] += bs * kv[h];
-        ks[h] = k0[h] + an * P.dt * kv[h];
+        ks[h] = k0[h] + an * dt * kv[h];
       }
     }
     for (int h = 0; h < 2; ++h) {
       int t = lane + 32 * h;
-      if (t < RC) B.K[row * RC + t] = t < rc ? k0[h] + P.dt * acc[h] : 0.0;
+      if (t < RC) B.K[row * RC + t] = t < rc ? (double)(k0[h] + dt * acc[h]) : 0.0;
     }
   }
 }
@@ -825,14 +837,16 @@ __global__ void k_coll_small(Problem P, PhaseBufs B) {
 }
 
 // collision L-step per direction:  dL_q/dt = sqrt(w_q) b(t) - Mt L_q
+template <typename TC>
 __global__ void __launch_bounds__(DD_THREADS) k_coll_lstep(Problem P, PhaseBufs B) {
-  extern __shared__ double sh[];
+  extern __shared__ double sh_raw[];
+  TC* sh = reinterpret_cast<TC*>(sh_raw);
   const int k = blockIdx.y, RC = P.g.RC, n = P.g.n;
   const int rc = B.rc[k];
-  double* S2 = sh;
-  double* Mt = S2 + RC * RC;
-  double* bst = Mt + RC * RC;         // 4 x RC
-  double* wsp = bst + 4 * RC;         // per warp: vh, Ls (2*RC)
+  TC* S2 = sh;
+  TC* Mt = S2 + RC * RC;
+  TC* bst = Mt + RC * RC;         // 4 x RC
+  TC* wsp = bst + 4 * RC;         // per warp: vh, Ls (2*RC)
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
     S2[e] = SMB(B, P, k, SM_S2)[e];
     Mt[e] = SMB(B, P, k, SM_MT)[e];
@@ -840,42 +854,43 @@ __global__ void __launch_bounds__(DD_THREADS) k_coll_lstep(Problem P, PhaseBufs 
   for (int e = threadIdx.x; e < 4 * RC; e += blockDim.x) bst[e] = SMB(B, P, k, SM_VEC)[2 * RC + e];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double* vh = wsp + warp * 2 * RC;
-  double* Ls = vh + RC;
+  TC* vh = wsp + warp * 2 * RC;
+  TC* Ls = vh + RC;
   const int nst = P.integrator == 1 ? 4 : 1;
+  const TC dt = (TC)P.dt;
   for (int q = blockIdx.x * 32 + warp; q < min(n, (int)(blockIdx.x + 1) * 32); q += nw) {
     const double* Vq = B.Vh + ((long)k * n + q) * RC;
     for (int t = lane; t < RC; t += 32) vh[t] = t < rc ? Vq[t] : 0.0;
     __syncwarp();
-    const double swq = P.sw[q];
-    double l0v[2] = {0.0, 0.0}, accv[2] = {0.0, 0.0};
+    const TC swq = P.sw[q];
+    TC l0v[2] = {0.0, 0.0}, accv[2] = {0.0, 0.0};
     for (int h = 0; h < 2; ++h) {
       int i = lane + 32 * h;
       if (i < rc) {
-        double s = 0.0;
+        TC s = 0.0;
         for (int j = 0; j < rc; ++j) s += S2[i * RC + j] * vh[j];
         l0v[h] = s; Ls[i] = s;
       }
     }
     __syncwarp();
     for (int s = 0; s < nst; ++s) {
-      double kv[2] = {0.0, 0.0};
+      TC kv[2] = {0.0, 0.0};
       for (int h = 0; h < 2; ++h) {
         int i = lane + 32 * h;
         if (i < rc) {
-          double a = swq * bst[s * RC + i];
+          TC a = swq * bst[s * RC + i];
           for (int j = 0; j < rc; ++j) a -= Mt[i * RC + j] * Ls[j];
           kv[h] = a;
         }
       }
       __syncwarp();
-      const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
-      const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
+      const TC bs = (nst == 4) ? c_rk_b[s] : 1.0;
+      const TC an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
       for (int h = 0; h < 2; ++h) {
         int i = lane + 32 * h;
         if (i < rc) {
           accv[h] += bs * kv[h];
-          if (s + 1 < nst) Ls[i] = l0v[h] + an * P.dt * kv[h];
+          if (s + 1 < nst) Ls[i] = l0v[h] + an * dt * kv[h];
         }
       }
       __syncwarp();
@@ -883,7 +898,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_coll_lstep(Problem P, PhaseBufs 
     double* Lq = B.L + ((long)k * n + q) * RC;
     for (int h = 0; h < 2; ++h) {
       int i = lane + 32 * h;
-      if (i < RC) Lq[i] = i < rc ? l0v[h] + P.dt * accv[h] : 0.0;
+      if (i < RC) Lq[i] = i < rc ? (double)(l0v[h] + dt * accv[h]) : 0.0;
     }
     __syncwarp();
   }
@@ -974,15 +989,23 @@ size_t part_elems(const Problem& P) {
 cudaError_t phase_init(const Problem& P) {
   const int RC = P.g.RC;
   cudaError_t e;
-  e = cudaFuncSetAttribute(k_kstep_adv, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  e = cudaFuncSetAttribute(k_kstep_adv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_kstep_adv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_sstep_adv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(double) * 6 * RC * RC));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_lstep_adv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_lstep_adv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(double) * (5 * RC * RC + 8 * 4 * RC)));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_small_adv1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_lstep_adv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * (5 * RC * RC + 8 * 4 * RC)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_small_adv1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * (2 * RC * RC + 2 * RC) + 64));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_small_adv1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(double) * (2 * RC * RC + 2 * RC) + 64));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_trunc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -991,7 +1014,10 @@ cudaError_t phase_init(const Problem& P) {
   e = cudaFuncSetAttribute(k_coll_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(double) * (4 * RC * RC + 5 * RC)));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_coll_lstep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_coll_lstep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_coll_lstep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC)));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_build_L0, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1040,6 +1066,7 @@ static OrthArgs orth_args(const Problem& P, const PhaseBufs& B, int spatial, int
   a.angcand = P.angcand; a.n_angcand = P.n_angcand; a.angcand_complete = P.angcand_complete;
   a.sig_out = B.sig; a.p_out = B.p; a.status = B.status;
   a.r_own = B.r; a.rt_out = B.rt;
+  a.svd_fp32 = (P.prec == 1 && mode == ORTH_AUG) ? 1 : 0;
   a.W = spatial ? B.Hw : B.Hwa; a.ldw = P.WC;
   return a;
 }
@@ -1094,7 +1121,11 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   }
   // 3. S M products, eigen-split of C
   pbeg(st, KS_SMALL_ADV1);
-  k_small_adv1<<<nsub, DD_THREADS, sizeof(double) * (2 * RC * RC + 2 * RC) + 64, st>>>(P, B, axis);
+  if (P.prec == 1) {
+    k_small_adv1<float><<<nsub, DD_THREADS, sizeof(double) * (2 * RC * RC + 2 * RC) + 64, st>>>(P, B, axis);
+  } else {
+    k_small_adv1<double><<<nsub, DD_THREADS, sizeof(double) * (2 * RC * RC + 2 * RC) + 64, st>>>(P, B, axis);
+  }
   pend(st);
   // 4. K^0 = X (S <V, Vh>)
   tall(P, B, st, 1, B.X, RC, B.r, 0, nullptr, SM_B, B.rt, 0, B.K, RC);
@@ -1108,7 +1139,11 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
     const int lpb = kstep_lpb(P, len);
     dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
     pbeg(st, KS_KSTEP_ADV);
-    k_kstep_adv<<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+    if (P.prec == 1) {
+      k_kstep_adv<float><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+    } else {
+      k_kstep_adv<double><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+    }
     pend(st);
   }
   // 7. QR of K
@@ -1133,8 +1168,13 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   pend(st);
   // 9. L-step
   pbeg(st, KS_LSTEP_ADV);
-  k_lstep_adv<<<dim3((g.n + 31) / 32, nsub), DD_THREADS, sizeof(double) * (5 * RC * RC + 8 * 4 * RC),
-                st>>>(P, B, axis);
+  if (P.prec == 1) {
+    k_lstep_adv<float><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, sizeof(double) * (5 * RC * RC + 8 * 4 * RC),
+                  st>>>(P, B, axis);
+  } else {
+    k_lstep_adv<double><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, sizeof(double) * (5 * RC * RC + 8 * 4 * RC),
+                  st>>>(P, B, axis);
+  }
   pend(st);
   // 10. QR of L
   {
@@ -1168,7 +1208,11 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   pend(st);
   tall(P, B, st, 1, B.X, RC, B.r, 0, B.S, -1, B.rc, 0, B.K, RC);
   pbeg(st, KS_COLL_KSTEP);
-  k_coll_kstep<<<dim3(64, nsub), DD_THREADS, 0, st>>>(P, B);
+  if (P.prec == 1) {
+    k_coll_kstep<float><<<dim3(64, nsub), DD_THREADS, 0, st>>>(P, B);
+  } else {
+    k_coll_kstep<double><<<dim3(64, nsub), DD_THREADS, 0, st>>>(P, B);
+  }
   pend(st);
   {
     OrthArgs a = orth_args(P, B, 1, ORTH_QR);
@@ -1197,8 +1241,13 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   k_coll_small<<<nsub, DD_THREADS, sizeof(double) * (4 * RC * RC + 5 * RC), st>>>(P, B);
   pend(st);
   pbeg(st, KS_COLL_LSTEP);
-  k_coll_lstep<<<dim3((g.n + 31) / 32, nsub), DD_THREADS,
-                 sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC), st>>>(P, B);
+  if (P.prec == 1) {
+    k_coll_lstep<float><<<dim3((g.n + 31) / 32, nsub), DD_THREADS,
+                   sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC), st>>>(P, B);
+  } else {
+    k_coll_lstep<double><<<dim3((g.n + 31) / 32, nsub), DD_THREADS,
+                   sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC), st>>>(P, B);
+  }
   pend(st);
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_QR);
