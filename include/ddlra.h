@@ -118,6 +118,27 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling,
                          dd_dlra_t* out);
 
 /*
+ * dd_dlra_create_batch — one solver over ninst independent problems that share the
+ * direction table `quad`: grids, tilings, materials, initial data, dt, ranks and the
+ * intermediate-rank cap may differ per problem; rank_mode, tol, integrator,
+ * precision, c_adv and tau must agree (else DD_ERR_ARG).  Every problem's subdomains
+ * advance in the same kernel launches, so a batch is one CUDA graph per step.
+ * grids, tilings, fields, g0 and opts hold ninst entries (g0[i] = problem i's
+ * isotropic initial data).  Subdomains are numbered problem after problem; the
+ * density (dd_dlra_scalar_flux) holds the problems back to back.  (The batched
+ * form has no counterpart in the paper: independent problems are independent.)
+ */
+dd_status dd_dlra_create_batch(int ninst, const dd_grid* grids, const dd_tiling* tilings,
+                               const dd_quadrature* quad, const dd_fields* fields,
+                               const double* const* g0, const dd_options* opts, void* stream,
+                               dd_dlra_t* out);
+
+/* Layout of problem inst of a batch: its first subdomain index, subdomain count, the
+ * offset of its density in the dd_dlra_scalar_flux output and its grid size. */
+dd_status dd_dlra_instance(dd_dlra_t h, int inst, int* first_subdomain, int* nsub,
+                           int* flux_offset, int* nx, int* ny);
+
+/*
  * dd_dlra_step — advance every subdomain by nsteps time steps of Algorithm 6.
  * Asynchronous on the solver's stream.  With use_graph != 0 the step is
  * captured once into a CUDA graph and replayed.
@@ -127,7 +148,8 @@ dd_status dd_dlra_set_graph(dd_dlra_t h, int use_graph);
 
 /*
  * dd_dlra_scalar_flux — rho = sum_q w_q f_q on all nx*ny cells, global x-fastest
- * order (Section 2, density).  out has nx*ny doubles; out_on_device != 0 means
+ * order (Section 2, density); for a batch, the problems' densities back to back.
+ * out has nx*ny doubles (a batch: the sum over problems); out_on_device != 0 means
  * a device pointer (written asynchronously on the solver's stream), else a host
  * pointer (the call synchronises).
  */
@@ -167,7 +189,7 @@ dd_status dd_dlra_profile(dd_dlra_t h, int nsteps, double* ms, int* launches);
 
 /*
  * dd_dlra_scalar_flux_noalloc — the density of dd_dlra_scalar_flux written to the
- * device pointer out (nx*ny doubles), by a call that allocates nothing: no
+ * device pointer out (same size and layout), by a call that allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine.  It is for callers that
  * must not allocate at the moment they read the density, for instance while they
  * capture their own work into a CUDA graph or under a policy that forbids device

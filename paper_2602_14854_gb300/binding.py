@@ -25,7 +25,8 @@ DD_FP64, DD_MIXED = 0, 1
 EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scalar_flux",
            "dd_dlra_ranks", "dd_dlra_info", "dd_dlra_get_factors", "dd_dlra_set_factors",
            "dd_dlra_sync", "dd_dlra_destroy", "dd_last_error", "dd_profile_slots",
-           "dd_profile_slot_name", "dd_dlra_profile", "dd_dlra_scalar_flux_noalloc"]
+           "dd_profile_slot_name", "dd_dlra_profile", "dd_dlra_scalar_flux_noalloc",
+           "dd_dlra_create_batch", "dd_dlra_instance"]
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -88,6 +89,10 @@ def load(path: str | None = None):
     lib.dd_profile_slot_name.restype = C.c_char_p
     lib.dd_dlra_profile.argtypes = [vp, C.c_int, _dp, _ip]
     lib.dd_dlra_scalar_flux_noalloc.argtypes = [vp, vp]
+    lib.dd_dlra_create_batch.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Tiling),
+                                         C.POINTER(Quadrature), C.POINTER(Fields),
+                                         C.POINTER(_dp), C.POINTER(Options), vp, C.POINTER(vp)]
+    lib.dd_dlra_instance.argtypes = [vp, C.c_int, _ip, _ip, _ip, _ip, _ip]
     for name in EXPORTS:
         if name not in ("dd_dlra_destroy", "dd_last_error", "dd_profile_slot_name"):
             getattr(lib, name).restype = C.c_int
@@ -119,31 +124,57 @@ class Solver:
 
     def __init__(self, wl, tau: float = 1e-5, stream: int = 0, use_graph: bool = False,
                  precision: str = "fp64"):
+        """wl: one workload, or a list of workloads sharing the direction table (a batch)."""
         lib = load()
         self.lib = lib
-        self.wl = wl
+        wls = list(wl) if isinstance(wl, (list, tuple)) else [wl]
+        self.wls = wls
+        self.wl = wls[0]
         self._keep = []
-        xc = np.ascontiguousarray(wl.xcuts, dtype=np.int32)
-        yc = np.ascontiguousarray(wl.ycuts, dtype=np.int32)
-        ox, oy, w = _d(wl.omega_x), _d(wl.omega_y), _d(wl.w)
-        ss, sa, q, g0 = _d(wl.sigma_s), _d(wl.sigma_a), _d(wl.source), _d(wl.g0)
-        self._keep += [xc, yc, ox, oy, w, ss, sa, q, g0]
-        grid = Grid(wl.nx, wl.ny, wl.x0, wl.x1, wl.y0, wl.y1)
-        til = Tiling(len(xc) - 1, len(yc) - 1, xc.ctypes.data_as(_ip), yc.ctypes.data_as(_ip))
-        quad = Quadrature(wl.n, _ptr(ox), _ptr(oy), _ptr(w), wl.n_mu, wl.n_phi)
-        fld = Fields(_ptr(ss), _ptr(sa), _ptr(q))
-        fixed = wl.rank_mode == "fixed"
-        opt = Options(DD_RANK_FIXED if fixed else DD_RANK_TOL, wl.rank, wl.tol, wl.r_min,
-                      wl.r_max, wl.r_aug_max, DD_RK4 if wl.integrator == "rk4" else DD_EULER,
-                      wl.c_adv, wl.dt, tau, DD_MIXED if precision == "mixed" else DD_FP64)
+        n = len(wls)
+        grids = (Grid * n)()
+        tils = (Tiling * n)()
+        flds = (Fields * n)()
+        opts = (Options * n)()
+        g0s = (_dp * n)()
+        for i, w in enumerate(wls):
+            xc = np.ascontiguousarray(w.xcuts, dtype=np.int32)
+            yc = np.ascontiguousarray(w.ycuts, dtype=np.int32)
+            ss, sa, q, g0 = _d(w.sigma_s), _d(w.sigma_a), _d(w.source), _d(w.g0)
+            self._keep += [xc, yc, ss, sa, q, g0]
+            grids[i] = Grid(w.nx, w.ny, w.x0, w.x1, w.y0, w.y1)
+            tils[i] = Tiling(len(xc) - 1, len(yc) - 1, xc.ctypes.data_as(_ip),
+                             yc.ctypes.data_as(_ip))
+            flds[i] = Fields(_ptr(ss), _ptr(sa), _ptr(q))
+            fixed = w.rank_mode == "fixed"
+            opts[i] = Options(DD_RANK_FIXED if fixed else DD_RANK_TOL, w.rank, w.tol, w.r_min,
+                              w.r_max, w.r_aug_max, DD_RK4 if w.integrator == "rk4" else DD_EULER,
+                              w.c_adv, w.dt, tau, DD_MIXED if precision == "mixed" else DD_FP64)
+            g0s[i] = _ptr(g0)
+        w0 = wls[0]
+        ox, oy, w = _d(w0.omega_x), _d(w0.omega_y), _d(w0.w)
+        self._keep += [ox, oy, w, grids, tils, flds, opts, g0s]
+        quad = Quadrature(w0.n, _ptr(ox), _ptr(oy), _ptr(w), w0.n_mu, w0.n_phi)
         h = C.c_void_p()
-        _check(lib, lib.dd_dlra_create(C.byref(grid), C.byref(til), C.byref(quad),
-                                       C.byref(fld), _ptr(g0), C.byref(opt),
-                                       C.c_void_p(stream), C.byref(h)))
+        if n == 1:
+            st = lib.dd_dlra_create(C.byref(grids[0]), C.byref(tils[0]), C.byref(quad),
+                                    C.byref(flds[0]), g0s[0], C.byref(opts[0]),
+                                    C.c_void_p(stream), C.byref(h))
+        else:
+            st = lib.dd_dlra_create_batch(n, grids, tils, C.byref(quad), flds, g0s, opts,
+                                          C.c_void_p(stream), C.byref(h))
+        _check(lib, st)
         self.h = h
-        nsub, n, rc = C.c_int(), C.c_int(), C.c_int()
-        _check(lib, lib.dd_dlra_info(h, C.byref(nsub), C.byref(n), C.byref(rc)))
-        self.nsub, self.n, self.r_cap = nsub.value, n.value, rc.value
+        nsub, nd, rc = C.c_int(), C.c_int(), C.c_int()
+        _check(lib, lib.dd_dlra_info(h, C.byref(nsub), C.byref(nd), C.byref(rc)))
+        self.nsub, self.n, self.r_cap = nsub.value, nd.value, rc.value
+        self.layout = []
+        for i in range(n):
+            a, b, c, d, e = (C.c_int() for _ in range(5))
+            _check(lib, lib.dd_dlra_instance(h, i, C.byref(a), C.byref(b), C.byref(c), C.byref(d),
+                                             C.byref(e)))
+            self.layout.append((a.value, b.value, c.value, d.value, e.value))
+        self.ncells_out = sum(w.nx * w.ny for w in wls)
         if use_graph:
             _check(lib, lib.dd_dlra_set_graph(h, 1))
 
@@ -159,7 +190,7 @@ class Solver:
         if out is not None:
             _check(self.lib, self.lib.dd_dlra_scalar_flux(self.h, C.c_void_p(out), 1))
             return None
-        rho = np.empty(self.wl.nx * self.wl.ny)
+        rho = np.empty(self.ncells_out)
         _check(self.lib, self.lib.dd_dlra_scalar_flux(self.h, rho.ctypes.data_as(C.c_void_p), 0))
         return rho
 
@@ -175,11 +206,20 @@ class Solver:
                                                 it.ctypes.data_as(_ip)))
         return st, it.reshape(2, self.nsub)
 
+    def instance_flux(self, rho, i):
+        """Problem i's density out of the concatenated output of scalar_flux()."""
+        _, _, off, nx, ny = self.layout[i]
+        return rho[off:off + nx * ny]
+
     def subdomain_cells(self, k):
-        wl = self.wl
-        TX = len(wl.xcuts) - 1
-        I, J = k % TX, k // TX
-        return (wl.xcuts[I + 1] - wl.xcuts[I]) * (wl.ycuts[J + 1] - wl.ycuts[J])
+        for i, (k0, ns, _, _, _) in enumerate(self.layout):
+            if k0 <= k < k0 + ns:
+                wl = self.wls[i]
+                kk = k - k0
+                TX = len(wl.xcuts) - 1
+                I, J = kk % TX, kk // TX
+                return (wl.xcuts[I + 1] - wl.xcuts[I]) * (wl.ycuts[J + 1] - wl.ycuts[J])
+        raise IndexError(k)
 
     def get_factors(self, k):
         N = self.subdomain_cells(k)

@@ -33,6 +33,8 @@ dd_status fail(dd_status s, const std::string& msg) {
 struct SubGeo {
   int N, nxk, nyk, cx0, cy0, rowoff;
   int nb[4];
+  int inst, rlo, rhi, raug, fbase, fnx;
+  double hx, hy, dt, sh;
 };
 
 template <class T>
@@ -56,6 +58,9 @@ double legendre(int l, double x) {
 struct dd_dlra {
   // problem
   int device;
+  int ninst;
+  std::vector<int> inst_sub0, inst_nsub, inst_fbase, inst_nx, inst_ny;
+  long ncells_out;
   int nx, ny, tx, ty, nsub, n;
   double hx, hy, sh, ssum;
   dd_options opt;
@@ -69,6 +74,8 @@ struct dd_dlra {
   bool graph_ready;
   // device: geometry
   int *d_N, *d_nxk, *d_nyk, *d_rowoff, *d_nb, *d_cx0, *d_cy0;
+  int *d_rlo, *d_rhi, *d_raug, *d_fbase, *d_fnx;
+  double *d_hxk, *d_hyk, *d_dtk, *d_shk;
   // device: problem data
   double *d_ox, *d_oy, *d_w, *d_sw, *d_sig_s, *d_sig_t, *d_sQ, *d_angcand;
   int n_angcand, angcand_complete;
@@ -162,7 +169,8 @@ void free_all(dd_dlra* h) {
                   h->d_S[1], h->d_r[0], h->d_r[1], h->d_L0, h->d_Hw, h->d_Hwa, h->d_Vh,
                   h->d_K, h->d_X1, h->d_L, h->d_V1, h->d_Kb, h->d_sm, h->d_part, h->d_sig,
                   h->d_rho, h->d_fluxw, h->d_m, h->d_rt, h->d_rx, h->d_rc, h->d_p, h->d_status,
-                  h->d_flag, h->d_scale};
+                  h->d_flag, h->d_scale, h->d_rlo, h->d_rhi, h->d_raug, h->d_fbase,
+                  h->d_fnx, h->d_hxk, h->d_hyk, h->d_dtk, h->d_shk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->graph_ready) cudaGraphExecDestroy(h->graph_exec);
@@ -195,13 +203,10 @@ extern "C" {
 
 const char* dd_last_error(void) { return g_err.c_str(); }
 
-dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_quadrature* quad,
-                         const dd_fields* fields, const double* g0, const dd_options* opt,
-                         void* stream, dd_dlra_t* out) {
-  g_err.clear();
-  if (!grid || !tiling || !quad || !fields || !g0 || !opt || !out)
-    return fail(DD_ERR_ARG, "null argument");
-  *out = nullptr;
+static dd_status check_instance(const dd_grid* grid, const dd_tiling* tiling,
+                                const dd_fields* fields, const double* g0, const dd_options* opt) {
+  if (!grid || !tiling || !fields || !g0 || !opt) return fail(DD_ERR_ARG, "null argument");
+  if (!fields->sigma_s || !fields->sigma_a || !fields->source) return fail(DD_ERR_ARG, "null field");
   if (grid->nx <= 0 || grid->ny <= 0 || !(grid->x1 > grid->x0) || !(grid->y1 > grid->y0))
     return fail(DD_ERR_ARG, "bad grid");
   if (tiling->tx <= 0 || tiling->ty <= 0 || !tiling->xcuts || !tiling->ycuts)
@@ -213,10 +218,6 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
     if (tiling->xcuts[i + 1] <= tiling->xcuts[i]) return fail(DD_ERR_ARG, "xcuts not increasing");
   for (int j = 0; j < tiling->ty; ++j)
     if (tiling->ycuts[j + 1] <= tiling->ycuts[j]) return fail(DD_ERR_ARG, "ycuts not increasing");
-  if (quad->n <= 0 || !quad->omega_x || !quad->omega_y || !quad->w)
-    return fail(DD_ERR_ARG, "bad quadrature");
-  for (int i = 0; i < quad->n; ++i)
-    if (!(quad->w[i] > 0.0)) return fail(DD_ERR_ARG, "quadrature weights must be positive");
   if (opt->rank_mode != DD_RANK_FIXED && opt->rank_mode != DD_RANK_TOL)
     return fail(DD_ERR_ARG, "rank_mode");
   if (opt->integrator != DD_EULER && opt->integrator != DD_RK4)
@@ -224,60 +225,118 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
   if (opt->precision != DD_FP64 && opt->precision != DD_MIXED)
     return fail(DD_ERR_ARG, "precision");
   if (!(opt->dt > 0.0) || !(opt->tau >= 0.0)) return fail(DD_ERR_ARG, "dt / tau");
+  const int RS = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_max;
+  const int fl = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_min;
+  if (opt->r_aug_max < 1 || opt->r_aug_max > DD_MAXC)
+    return fail(DD_ERR_ARG, "r_aug_max must be in [1, 64]");
+  if (RS < 1 || RS > opt->r_aug_max) return fail(DD_ERR_ARG, "stored-rank cap must be in [1, r_aug_max]");
+  if (3 * RS > DD_MAXC) return fail(DD_ERR_ARG, "3 * stored-rank cap must be <= 64");
+  if (fl < 0 || fl > RS) return fail(DD_ERR_ARG, "rank floor");
+  return DD_OK;
+}
+
+// Plan, allocate and initialise a solver over ninst independent problems that
+// share the direction table; instance i's subdomains follow instance i-1's.
+static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* tilings,
+                             const dd_quadrature* quad, const dd_fields* fields,
+                             const double* const* g0s, const dd_options* opts, void* stream,
+                             dd_dlra_t* out) {
+  g_err.clear();
+  if (!out || !quad || !grids || !tilings || !fields || !g0s || !opts || ninst < 1)
+    return fail(DD_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (quad->n <= 0 || !quad->omega_x || !quad->omega_y || !quad->w)
+    return fail(DD_ERR_ARG, "bad quadrature");
+  for (int i = 0; i < quad->n; ++i)
+    if (!(quad->w[i] > 0.0)) return fail(DD_ERR_ARG, "quadrature weights must be positive");
+  for (int i = 0; i < ninst; ++i) {
+    dd_status st = check_instance(&grids[i], &tilings[i], &fields[i], g0s[i], &opts[i]);
+    if (st != DD_OK) return st;
+    const dd_options& a = opts[0];
+    const dd_options& b = opts[i];
+    if (b.rank_mode != a.rank_mode || b.integrator != a.integrator || b.precision != a.precision ||
+        b.c_adv != a.c_adv || b.tau != a.tau || b.tol != a.tol)
+      return fail(DD_ERR_ARG, "instances of a batch must share rank mode, tolerance, integrator, "
+                              "precision, c_adv and tau");
+  }
+  const dd_options* opt = &opts[0];
 
   dd_dlra* h = new dd_dlra();   // value-initialised: every device pointer starts null
   cudaGetDevice(&h->device);
-  h->nx = grid->nx; h->ny = grid->ny; h->tx = tiling->tx; h->ty = tiling->ty;
-  h->nsub = h->tx * h->ty; h->n = quad->n;
-  h->hx = (grid->x1 - grid->x0) / grid->nx;
-  h->hy = (grid->y1 - grid->y0) / grid->ny;
+  h->ninst = ninst;
+  h->nx = grids[0].nx; h->ny = grids[0].ny; h->tx = tilings[0].tx; h->ty = tilings[0].ty;
+  h->n = quad->n;
+  h->hx = (grids[0].x1 - grids[0].x0) / grids[0].nx;
+  h->hy = (grids[0].y1 - grids[0].y0) / grids[0].ny;
   h->sh = std::sqrt(h->hx * h->hy);
   h->opt = *opt;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->ssum = 0.0;
   for (int i = 0; i < quad->n; ++i) h->ssum += quad->w[i];
-  h->RS = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_max;
+  int RS = 0, raug_max = 0;
+  for (int i = 0; i < ninst; ++i) {
+    RS = std::max(RS, opts[i].rank_mode == DD_RANK_FIXED ? opts[i].rank : opts[i].r_max);
+    raug_max = std::max(raug_max, opts[i].r_aug_max);
+  }
+  h->RS = RS;
   h->MC = 3 * h->RS;
   // column capacity of every tall and small matrix: the intermediate rank and the
   // augmentation input width both fit
-  h->RC = std::max(opt->r_aug_max, h->MC);
+  h->RC = std::max(raug_max, h->MC);
   h->r_floor = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_min;
   auto bail = [&](dd_status s, const std::string& m) {
     free_all(h);
     delete h;
     return fail(s, m);
   };
-  if (opt->r_aug_max < 1 || opt->r_aug_max > DD_MAXC)
-    return bail(DD_ERR_ARG, "r_aug_max must be in [1, 64]");
-  if (h->RS < 1 || h->RS > opt->r_aug_max)
-    return bail(DD_ERR_ARG, "stored-rank cap must be in [1, r_aug_max]");
-  if (h->MC > DD_MAXC) return bail(DD_ERR_ARG, "3 * stored-rank cap must be <= 64");
   if (h->n < h->MC) return bail(DD_ERR_ARG, "need at least 3 * stored-rank cap directions");
-  if (h->r_floor < 0 || h->r_floor > h->RS) return bail(DD_ERR_ARG, "rank floor");
 
-  // geometry
-  h->geo.resize(h->nsub);
-  int rowoff = 0;
+  // geometry, instance after instance
+  int rowoff = 0, fbase = 0;
   h->maxlines = 0;
   h->maxN = 0;
-  for (int J = 0; J < h->ty; ++J)
-    for (int I = 0; I < h->tx; ++I) {
-      int k = J * h->tx + I;
-      SubGeo& s = h->geo[k];
-      s.cx0 = tiling->xcuts[I];
-      s.cy0 = tiling->ycuts[J];
-      s.nxk = tiling->xcuts[I + 1] - s.cx0;
-      s.nyk = tiling->ycuts[J + 1] - s.cy0;
-      s.N = s.nxk * s.nyk;
-      s.rowoff = rowoff;
-      rowoff += s.N;
-      s.nb[0] = I > 0 ? k - 1 : -1;
-      s.nb[1] = I < h->tx - 1 ? k + 1 : -1;
-      s.nb[2] = J > 0 ? k - h->tx : -1;
-      s.nb[3] = J < h->ty - 1 ? k + h->tx : -1;
-      h->maxlines = std::max(h->maxlines, std::max(s.nxk, s.nyk));
-      h->maxN = std::max(h->maxN, s.N);
-    }
+  for (int inst = 0; inst < ninst; ++inst) {
+    const dd_grid* grid = &grids[inst];
+    const dd_tiling* tiling = &tilings[inst];
+    const dd_options* o = &opts[inst];
+    const double hx = (grid->x1 - grid->x0) / grid->nx, hy = (grid->y1 - grid->y0) / grid->ny;
+    const int k0 = (int)h->geo.size();
+    const int tx = tiling->tx, ty = tiling->ty;
+    h->inst_sub0.push_back(k0);
+    h->inst_nsub.push_back(tx * ty);
+    h->inst_fbase.push_back(fbase);
+    h->inst_nx.push_back(grid->nx);
+    h->inst_ny.push_back(grid->ny);
+    for (int J = 0; J < ty; ++J)
+      for (int I = 0; I < tx; ++I) {
+        int k = k0 + J * tx + I;
+        SubGeo s;
+        s.cx0 = tiling->xcuts[I];
+        s.cy0 = tiling->ycuts[J];
+        s.nxk = tiling->xcuts[I + 1] - s.cx0;
+        s.nyk = tiling->ycuts[J + 1] - s.cy0;
+        s.N = s.nxk * s.nyk;
+        s.rowoff = rowoff;
+        rowoff += s.N;
+        s.nb[0] = I > 0 ? k - 1 : -1;
+        s.nb[1] = I < tx - 1 ? k + 1 : -1;
+        s.nb[2] = J > 0 ? k - tx : -1;
+        s.nb[3] = J < ty - 1 ? k + tx : -1;
+        s.inst = inst;
+        s.hx = hx; s.hy = hy; s.dt = o->dt; s.sh = std::sqrt(hx * hy);
+        s.rlo = o->rank_mode == DD_RANK_FIXED ? o->rank : o->r_min;
+        s.rhi = o->rank_mode == DD_RANK_FIXED ? o->rank : o->r_max;
+        s.raug = o->r_aug_max;
+        s.fbase = fbase;
+        s.fnx = grid->nx;
+        h->geo.push_back(s);
+        h->maxlines = std::max(h->maxlines, std::max(s.nxk, s.nyk));
+        h->maxN = std::max(h->maxN, s.N);
+      }
+    fbase += grid->nx * grid->ny;
+  }
+  h->nsub = (int)h->geo.size();
+  h->ncells_out = fbase;
   h->Ntot = rowoff;
   if (h->maxlines * h->RC > DD_THREADS * 24)
     return bail(DD_ERR_ARG, "subdomain side x r_aug_max exceeds the K-step tile (6144)");
@@ -285,19 +344,31 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
   const int RC = h->RC, n = h->n, nsub = h->nsub, MC = h->MC;
   const long Nt = h->Ntot;
   {
-    std::vector<int> vN(nsub), vnx(nsub), vny(nsub), vro(nsub), vnb(4 * nsub), vcx(nsub), vcy(nsub);
+    std::vector<int> vN(nsub), vnx(nsub), vny(nsub), vro(nsub), vnb(4 * nsub), vcx(nsub), vcy(nsub),
+        vlo(nsub), vhi(nsub), vaug(nsub), vfb(nsub), vfnx(nsub);
+    std::vector<double> vhx(nsub), vhy(nsub), vdt(nsub), vsh(nsub);
     for (int k = 0; k < nsub; ++k) {
-      vN[k] = h->geo[k].N; vnx[k] = h->geo[k].nxk; vny[k] = h->geo[k].nyk;
-      vro[k] = h->geo[k].rowoff; vcx[k] = h->geo[k].cx0; vcy[k] = h->geo[k].cy0;
-      for (int s = 0; s < 4; ++s) vnb[4 * k + s] = h->geo[k].nb[s];
+      const SubGeo& g = h->geo[k];
+      vN[k] = g.N; vnx[k] = g.nxk; vny[k] = g.nyk; vro[k] = g.rowoff; vcx[k] = g.cx0; vcy[k] = g.cy0;
+      for (int s = 0; s < 4; ++s) vnb[4 * k + s] = g.nb[s];
+      vlo[k] = g.rlo; vhi[k] = g.rhi; vaug[k] = g.raug; vfb[k] = g.fbase; vfnx[k] = g.fnx;
+      vhx[k] = g.hx; vhy[k] = g.hy; vdt[k] = g.dt; vsh[k] = g.sh;
     }
 #define UP_INT(dst, v)                                                                       \
   if (dalloc(&dst, v.size()) != cudaSuccess ||                                                \
       cudaMemcpy(dst, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) \
     return bail(DD_ERR_CUDA, "upload geometry");
+#define UP_DBLV(dst, v)                                                                         \
+  if (dalloc(&dst, v.size()) != cudaSuccess ||                                                   \
+      cudaMemcpy(dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) \
+    return bail(DD_ERR_CUDA, "upload geometry");
     UP_INT(h->d_N, vN); UP_INT(h->d_nxk, vnx); UP_INT(h->d_nyk, vny); UP_INT(h->d_rowoff, vro);
     UP_INT(h->d_nb, vnb); UP_INT(h->d_cx0, vcx); UP_INT(h->d_cy0, vcy);
+    UP_INT(h->d_rlo, vlo); UP_INT(h->d_rhi, vhi); UP_INT(h->d_raug, vaug); UP_INT(h->d_fbase, vfb);
+    UP_INT(h->d_fnx, vfnx);
+    UP_DBLV(h->d_hxk, vhx); UP_DBLV(h->d_hyk, vhy); UP_DBLV(h->d_dtk, vdt); UP_DBLV(h->d_shk, vsh);
 #undef UP_INT
+#undef UP_DBLV
   }
   // problem data
   std::vector<double> sw(n), sig_s(Nt), sig_t(Nt), sQ(Nt);
@@ -305,11 +376,12 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
   h->sw_host = sw;
   for (int k = 0; k < nsub; ++k) {
     const SubGeo& s = h->geo[k];
+    const dd_fields* f = &fields[s.inst];
     for (int c = 0; c < s.N; ++c) {
-      int gi = (s.cy0 + c / s.nxk) * h->nx + s.cx0 + c % s.nxk;
-      sig_s[s.rowoff + c] = fields->sigma_s[gi];
-      sig_t[s.rowoff + c] = fields->sigma_s[gi] + fields->sigma_a[gi];
-      sQ[s.rowoff + c] = h->sh * fields->source[gi];
+      int gi = (s.cy0 + c / s.nxk) * s.fnx + s.cx0 + c % s.nxk;
+      sig_s[s.rowoff + c] = f->sigma_s[gi];
+      sig_t[s.rowoff + c] = f->sigma_s[gi] + f->sigma_a[gi];
+      sQ[s.rowoff + c] = s.sh * f->source[gi];
     }
   }
   std::vector<double> tab;
@@ -348,7 +420,7 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
   ok &= dalloc(&h->d_Kb, (long)nsub * 2 * h->maxlines * RC) == cudaSuccess;
   ok &= dalloc(&h->d_sm, (long)nsub * dd::NSMALL * RC * RC) == cudaSuccess;
   ok &= dalloc(&h->d_sig, (long)nsub * DD_MAXC) == cudaSuccess;
-  ok &= dalloc(&h->d_rho, (long)h->nx * h->ny) == cudaSuccess;
+  ok &= dalloc(&h->d_rho, (long)h->ncells_out) == cudaSuccess;
   ok &= dalloc(&h->d_fluxw, (long)nsub * RC) == cudaSuccess;
   ok &= dalloc(&h->d_m, nsub) == cudaSuccess;
   ok &= dalloc(&h->d_rt, nsub) == cudaSuccess;
@@ -365,6 +437,9 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
   P.g.nsub = nsub; P.g.n = n; P.g.RC = RC; P.g.MC = MC;
   P.g.N = h->d_N; P.g.nxk = h->d_nxk; P.g.nyk = h->d_nyk; P.g.rowoff = h->d_rowoff;
   P.g.nb = h->d_nb; P.g.cx0 = h->d_cx0; P.g.cy0 = h->d_cy0;
+  P.g.hxk = h->d_hxk; P.g.hyk = h->d_hyk; P.g.dtk = h->d_dtk; P.g.shk = h->d_shk;
+  P.g.rlo = h->d_rlo; P.g.rhi = h->d_rhi; P.g.raug = h->d_raug; P.g.fbase = h->d_fbase;
+  P.g.fnx = h->d_fnx;
   P.maxlines = h->maxlines; P.maxN = h->maxN;
   P.ox = h->d_ox; P.oy = h->d_oy; P.w = h->d_w; P.sw = h->d_sw;
   P.sig_s = h->d_sig_s; P.sig_t = h->d_sig_t; P.sQ = h->d_sQ;
@@ -372,7 +447,7 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
   P.integrator = opt->integrator; P.rank_mode = opt->rank_mode; P.tol = opt->tol;
   P.prec = opt->precision == DD_MIXED ? 1 : 0;
   P.tau = opt->tau; P.accept = 0.5;
-  P.r_floor = h->r_floor; P.r_aug_max = opt->r_aug_max; P.RS = h->RS; P.WC = WC;
+  P.r_floor = h->r_floor; P.r_aug_max = raug_max; P.RS = h->RS; P.WC = WC;
   P.angcand = h->d_angcand; P.n_angcand = h->n_angcand; P.angcand_complete = h->angcand_complete;
   P.nchunk_sp = std::max(1, std::min(16, h->maxN / 64));
   P.nchunk_ang = std::max(1, std::min(16, n / 64));
@@ -388,18 +463,19 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
     std::vector<int> r(nsub, 0);
     for (int k = 0; k < nsub; ++k) {
       const SubGeo& s = h->geo[k];
+      const double* g0 = g0s[s.inst];
       double nn = 0.0;
       for (int c = 0; c < s.N; ++c) {
-        double gv = g0[(s.cy0 + c / s.nxk) * h->nx + s.cx0 + c % s.nxk];
+        double gv = g0[(s.cy0 + c / s.nxk) * s.fnx + s.cx0 + c % s.nxk];
         nn += gv * gv;
       }
       nn = std::sqrt(nn);
       if (!(nn > 0.0)) continue;
       r[k] = 1;
       for (int c = 0; c < s.N; ++c)
-        X[(size_t)(s.rowoff + c) * RC] = g0[(s.cy0 + c / s.nxk) * h->nx + s.cx0 + c % s.nxk] / nn;
+        X[(size_t)(s.rowoff + c) * RC] = g0[(s.cy0 + c / s.nxk) * s.fnx + s.cx0 + c % s.nxk] / nn;
       for (int q = 0; q < n; ++q) V[((size_t)k * n + q) * RC] = sw[q] / std::sqrt(h->ssum);
-      S[(size_t)k * RC * RC] = nn * h->sh * std::sqrt(h->ssum);
+      S[(size_t)k * RC * RC] = nn * s.sh * std::sqrt(h->ssum);
     }
     for (int b = 0; b < 2; ++b) {
       if (cudaMemcpy(h->d_X[b], X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -415,6 +491,35 @@ dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(DD_ERR_CUDA, "create: device error");
   *out = h;
+  return DD_OK;
+}
+
+dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling, const dd_quadrature* quad,
+                         const dd_fields* fields, const double* g0, const dd_options* opt,
+                         void* stream, dd_dlra_t* out) {
+  if (!grid || !tiling || !quad || !fields || !g0 || !opt || !out) {
+    g_err = "null argument";
+    return DD_ERR_ARG;
+  }
+  const double* g0s[1] = {g0};
+  return create_impl(1, grid, tiling, quad, fields, g0s, opt, stream, out);
+}
+
+dd_status dd_dlra_create_batch(int ninst, const dd_grid* grids, const dd_tiling* tilings,
+                               const dd_quadrature* quad, const dd_fields* fields,
+                               const double* const* g0, const dd_options* opts, void* stream,
+                               dd_dlra_t* out) {
+  return create_impl(ninst, grids, tilings, quad, fields, g0, opts, stream, out);
+}
+
+dd_status dd_dlra_instance(dd_dlra_t h, int inst, int* first_subdomain, int* nsub,
+                           int* flux_offset, int* nx, int* ny) {
+  if (!h || inst < 0 || inst >= h->ninst) return fail(DD_ERR_ARG, "bad instance");
+  if (first_subdomain) *first_subdomain = h->inst_sub0[inst];
+  if (nsub) *nsub = h->inst_nsub[inst];
+  if (flux_offset) *flux_offset = h->inst_fbase[inst];
+  if (nx) *nx = h->inst_nx[inst];
+  if (ny) *ny = h->inst_ny[inst];
   return DD_OK;
 }
 
@@ -463,7 +568,7 @@ dd_status dd_dlra_scalar_flux(dd_dlra_t h, double* out, int out_on_device) {
   dd::scalar_flux(h->P, h->d_X[0], h->d_V[0], h->d_S[0], h->d_r[0], h->d_fluxw, dst, h->nx, h->stream);
   DD_CUDA(cudaGetLastError());
   if (!out_on_device) {
-    DD_CUDA(cudaMemcpyAsync(out, h->d_rho, sizeof(double) * (size_t)h->nx * h->ny,
+    DD_CUDA(cudaMemcpyAsync(out, h->d_rho, sizeof(double) * (size_t)h->ncells_out,
                             cudaMemcpyDeviceToHost, h->stream));
     return check_status(h);
   }
@@ -505,7 +610,7 @@ dd_status dd_dlra_get_factors(dd_dlra_t h, int k, double* U, double* S, double* 
   dd_status st = check_status(h);
   if (st != DD_OK) return st;
   for (int c = 0; c < s.N; ++c)
-    for (int t = 0; t < rk; ++t) U[(size_t)c * rk + t] = X[(size_t)c * RC + t] / h->sh;
+    for (int t = 0; t < rk; ++t) U[(size_t)c * rk + t] = X[(size_t)c * RC + t] / s.sh;
   for (int q = 0; q < n; ++q)
     for (int t = 0; t < rk; ++t) V[(size_t)q * rk + t] = Vt[(size_t)q * RC + t] / h->sw_host[q];
   for (int i = 0; i < rk; ++i)
@@ -523,7 +628,7 @@ dd_status dd_dlra_set_factors(dd_dlra_t h, int k, int r, const double* U, const 
   const int RC = h->RC, n = h->n;
   std::vector<double> X((size_t)s.N * RC, 0.0), Vt((size_t)n * RC, 0.0), Sm((size_t)RC * RC, 0.0);
   for (int c = 0; c < s.N; ++c)
-    for (int t = 0; t < r; ++t) X[(size_t)c * RC + t] = U[(size_t)c * r + t] * h->sh;
+    for (int t = 0; t < r; ++t) X[(size_t)c * RC + t] = U[(size_t)c * r + t] * s.sh;
   for (int q = 0; q < n; ++q)
     for (int t = 0; t < r; ++t) Vt[(size_t)q * RC + t] = V[(size_t)q * r + t] * h->sw_host[q];
   for (int i = 0; i < r; ++i)

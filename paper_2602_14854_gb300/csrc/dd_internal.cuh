@@ -31,8 +31,19 @@ struct Geo {
   const int* nyk;    // height
   const int* rowoff; // first spatial row of subdomain k
   const int* nb;     // 4 per subdomain: x-lo, x-hi, y-lo, y-hi neighbour, -1 = physical boundary
-  const int* cx0;    // global x offset of the subdomain
-  const int* cy0;    // global y offset
+  const int* cx0;    // x offset of the subdomain inside its problem's grid
+  const int* cy0;    // y offset
+  // per-subdomain problem parameters (a batch holds several independent problems
+  // that share the direction table; every subdomain carries its problem's values)
+  const double* hxk;  // cell widths
+  const double* hyk;
+  const double* dtk;  // time step
+  const double* shk;  // sqrt(hx hy)
+  const int* rlo;     // rank floor / lower truncation clamp (fixed mode: the rank)
+  const int* rhi;     // upper truncation clamp (fixed mode: the rank)
+  const int* raug;    // cap of the intermediate rank
+  const int* fbase;   // first cell of the problem in the concatenated density output
+  const int* fnx;     // width of the problem's grid
 };
 
 // Line geometry along an axis (0 = x, 1 = y) for subdomain k.

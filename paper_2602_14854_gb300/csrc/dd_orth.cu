@@ -67,8 +67,8 @@ __device__ int decide(const OrthArgs& a, int k, const double* sig, int nref, int
       }
     }
     int r_sig = min(r_tail, p);
-    int cap = min(min(a.r_aug_max, a.g.n), a.g.N[k]);
-    int fl = max(a.r_own[k], a.r_floor);
+    int cap = min(min(a.g.raug[k], a.g.n), a.g.N[k]);
+    int fl = max(a.r_own[k], a.g.rlo[k]);
     int rt = min(max(r_sig, fl), cap);
     *r_out = rt;
     *keep = min(rt, p);
@@ -281,8 +281,8 @@ __global__ void k_cqr2(OrthArgs a, const double* sm, int sG2, int sR1, int sR1i,
     if (well) {
       if (a.mode == ORTH_QR) keep_all = (a.rout[k] == m);
       else if (a.rank_mode == 0) {                      // fixed mode: r_t = min(max(m, floor), cap)
-        int cap = min(min(a.r_aug_max, a.g.n), a.g.N[k]);
-        int rt = min(max(m, max(a.r_own[k], a.r_floor)), cap);
+        int cap = min(min(a.g.raug[k], a.g.n), a.g.N[k]);
+        int rt = min(max(m, max(a.r_own[k], a.g.rlo[k])), cap);
         keep_all = (rt == m);
         if (keep_all) a.rt_out[k] = m;
       }

@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
     }
   }
   __syncthreads();
-  const TC coef = (TC)(-P.c_adv / (axis == 0 ? P.hx : P.hy));
-  const TC dt = (TC)P.dt;
+  const TC coef = (TC)(-P.c_adv / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]));
+  const TC dt = (TC)P.g.dtk[k];
   const int nst = P.integrator == 1 ? 4 : 1;
   for (int s = 0; s < nst; ++s) {
     TC kv[KS_EPT];
@@ -482,7 +482,8 @@ __global__ void k_sstep_adv(Problem P, PhaseBufs B, int axis) {
     Ac[e] = 0.0;
   }
   __syncthreads();
-  const double coef = P.c_adv / (axis == 0 ? P.hx : P.hy);
+  const double coef = P.c_adv / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]);
+  const double dtk = P.g.dtk[k];
   const int nst = P.integrator == 1 ? 4 : 1;
   for (int s = 0; s < nst; ++s) {
     // U1 = T S + G_lo ; U2 = T^T S + G_hi
@@ -510,7 +511,7 @@ __global__ void k_sstep_adv(Problem P, PhaseBufs B, int axis) {
     for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
       int i = e / rt, j = e % rt;
       Ac[i * RC + j] += bs * F[i * RC + j];
-      if (s + 1 < nst) Ss[i * RC + j] = S0[i * RC + j] + an * P.dt * F[i * RC + j];
+      if (s + 1 < nst) Ss[i * RC + j] = S0[i * RC + j] + an * dtk * F[i * RC + j];
     }
     __syncthreads();
   }
@@ -520,7 +521,7 @@ __global__ void k_sstep_adv(Problem P, PhaseBufs B, int axis) {
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
     int i = e / RC, j = e % RC;
     bool in = i < rt && j < rt;
-    S2[e] = in ? S0[e] + P.dt * Ac[e] : 0.0;
+    S2[e] = in ? S0[e] + dtk * Ac[e] : 0.0;
     Ap[e] = in ? ((i == j ? 1.0 : 0.0) - T[i * RC + j]) : 0.0;
     Am[e] = in ? (T[j * RC + i] - (i == j ? 1.0 : 0.0)) : 0.0;
   }
@@ -556,8 +557,8 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
   TC* Ls = L0 + RC;
   TC* gv = Ls + RC;
   const double* om = axis == 0 ? P.ox : P.oy;
-  const TC dt = (TC)P.dt;
-  const TC hinv = (TC)(1.0 / (axis == 0 ? P.hx : P.hy));
+  const TC dt = (TC)P.g.dtk[k];
+  const TC hinv = (TC)(1.0 / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]));
   const int nst = P.integrator == 1 ? 4 : 1;
   for (int q = blockIdx.x * 32 + warp; q < min(n, (int)(blockIdx.x + 1) * 32); q += nw) {
     const double* Vq = B.Vh + ((long)k * n + q) * RC;
@@ -616,7 +617,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
 // ---------------------------------------------------------------------------
 // truncation (Algorithm 5): SVD of S3 by one-sided Jacobi on the columns of S3^T
 // ---------------------------------------------------------------------------
-__global__ void k_trunc(Problem P, PhaseBufs B, int rank_fixed, int r_min, int r_max) {
+__global__ void k_trunc(Problem P, PhaseBufs B) {
   extern __shared__ double sh[];
   const int k = blockIdx.x, RC = P.g.RC;
   const int rt = B.rt[k];
@@ -664,9 +665,9 @@ __global__ void k_trunc(Problem P, PhaseBufs B, int rank_fixed, int r_min, int r
         for (int t = rr; t < rt; ++t) ss += sig[perm[t]] * sig[perm[t]];
         if (sqrt(ss) <= P.tol) { rtail = rr; break; }
       }
-      r1 = min(max(rtail, r_min), r_max);
+      r1 = min(max(rtail, P.g.rlo[k]), P.g.rhi[k]);
     } else {
-      r1 = rank_fixed;
+      r1 = P.g.rhi[k];
     }
     r1 = min(r1, p);
     iv[1] = r1;
@@ -697,7 +698,7 @@ __global__ void k_trunc(Problem P, PhaseBufs B, int rank_fixed, int r_min, int r
 __global__ void k_coll_rank(Problem P, const int* r, int* rc) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= P.g.nsub) return;
-  rc[k] = min(min(max(r[k], P.r_floor), P.g.n), P.g.N[k]);
+  rc[k] = min(min(max(r[k], P.g.rlo[k]), P.g.n), P.g.N[k]);
 }
 
 // a = Vh^T sqrt(w)  (the paper's <V_j>_phi)
@@ -722,7 +723,7 @@ __global__ void k_coll_kstep(Problem P, PhaseBufs B) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int N = P.g.N[k], rc = B.rc[k];
   const double* a = SMB(B, P, k, SM_VEC);
-  const TC dt = (TC)P.dt;
+  const TC dt = (TC)P.g.dtk[k];
   const int nst = P.integrator == 1 ? 4 : 1;
   for (int cell = blockIdx.x * nw + warp; cell < N; cell += gridDim.x * nw) {
     const long row = (long)P.g.rowoff[k] + cell;
@@ -802,14 +803,14 @@ __global__ void k_coll_small(Problem P, PhaseBufs B) {
     for (int e = threadIdx.x; e < rc * rc; e += blockDim.x) {
       int i = e / rc, j = e % rc;
       Ac[i * RC + j] += bs * F[i * RC + j];
-      if (s + 1 < nst) Ss[i * RC + j] = S0[i * RC + j] + an * P.dt * F[i * RC + j];
+      if (s + 1 < nst) Ss[i * RC + j] = S0[i * RC + j] + an * P.g.dtk[k] * F[i * RC + j];
     }
     __syncthreads();
   }
   double* S2 = SMB(B, P, k, SM_S2);
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
     int i = e / RC, j = e % RC;
-    S2[e] = (i < rc && j < rc) ? S0[e] + P.dt * Ac[e] : 0.0;
+    S2[e] = (i < rc && j < rc) ? S0[e] + P.g.dtk[k] * Ac[e] : 0.0;
   }
   __syncthreads();
   // m0 = S2 a ; dm/dt = (Ms - Mt) m + |S| q ; b_s = (1/|S|) Ms m_s + q
@@ -831,7 +832,7 @@ __global__ void k_coll_small(Problem P, PhaseBufs B) {
     }
     __syncthreads();
     const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
-    for (int i = threadIdx.x; i < rc; i += blockDim.x) mv[i] = m0[i] + an * P.dt * km[i];
+    for (int i = threadIdx.x; i < rc; i += blockDim.x) mv[i] = m0[i] + an * P.g.dtk[k] * km[i];
     __syncthreads();
   }
 }
@@ -857,7 +858,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_coll_lstep(Problem P, PhaseBufs 
   TC* vh = wsp + warp * 2 * RC;
   TC* Ls = vh + RC;
   const int nst = P.integrator == 1 ? 4 : 1;
-  const TC dt = (TC)P.dt;
+  const TC dt = (TC)P.g.dtk[k];
   for (int q = blockIdx.x * 32 + warp; q < min(n, (int)(blockIdx.x + 1) * 32); q += nw) {
     const double* Vq = B.Vh + ((long)k * n + q) * RC;
     for (int t = lane; t < RC; t += 32) vh[t] = t < rc ? Vq[t] : 0.0;
@@ -950,7 +951,7 @@ __global__ void k_flux(Problem P, const double* X, const int* r, const double* w
     double s = 0.0;
     for (int t = 0; t < rk; ++t) s += Xr[t] * sa[t];
     int il = cell % nxk, jl = cell / nxk;
-    rho[(long)(P.g.cy0[k] + jl) * nx + P.g.cx0[k] + il] = s / P.sh;
+    rho[(long)P.g.fbase[k] + (long)(P.g.cy0[k] + jl) * P.g.fnx[k] + P.g.cx0[k] + il] = s / P.g.shk[k];
   }
 }
 
@@ -1186,7 +1187,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   // 11. truncation (Algorithm 5)
   pbeg(st, KS_TRUNC);
   k_trunc<<<nsub, DD_THREADS, trunc_smem(RC), st>>>(
-      P, B, P.RS, P.r_floor, P.RS);
+      P, B);
   pend(st);
   tall(P, B, st, 1, B.X1, RC, B.rt, 0, nullptr, SM_UB, B.ro, 0, B.Xo, RC);
   tall(P, B, st, 0, B.V1, RC, B.rt, 0, nullptr, SM_VB, B.ro, 0, B.Vo, RC);

@@ -273,3 +273,52 @@ def random_factors(seed: int, nrow: int, n: int, r: int, hx: float, hy: float, w
     Qr, _ = np.linalg.qr(rng.standard_normal((r, r)))
     S = P @ np.diag(decay ** np.arange(r)) @ Qr.T
     return U, S, V
+
+
+DIRECTION_SETS = {128: (8, 16), 512: (16, 32), 1024: (16, 64), 16: (2, 8), 32: (4, 8)}
+
+
+def batch_problems(count=64, seed0=0, grids=(64, 128, 256), tilings=(2, 4),
+                   directions=(128, 512, 1024), ranks=(4, 21), nsteps=100,
+                   integrator="rk4") -> dict:
+    """Independent seeded problems for the batched form, grouped by direction count
+    (a batch shares its direction table).  Problem i (seed seed0 + i): [0,1]^2 with a
+    grid from `grids`, a square tiling from `tilings`, a direction set from
+    `directions` (Gauss-Legendre mu x equidistant phi), a fixed rank drawn uniformly
+    from `ranks` (inclusive; 3 r <= 64), sigma_t per 4x4 block of the grid
+    log-uniform in [0.1, 100] with scattering ratio uniform in [0.5, 1], and initial
+    data either a centred Gaussian of width 0.05 or a narrow Gaussian (width 1.5 h)
+    at a random cell centre.  dt = h/2.  Returns {n: [Workload, ...]}."""
+    out = {}
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        nx = int(rng.choice(grids))
+        tiles = int(rng.choice(tilings))
+        n = int(rng.choice(directions))
+        n_mu, n_phi = DIRECTION_SETS[n]
+        rank = int(rng.integers(ranks[0], ranks[1] + 1))
+        ox, oy, w = product_quadrature(n_mu, n_phi)
+        X, Y = _cell_centres(nx, nx, 0.0, 1.0, 0.0, 1.0)
+        h = 1.0 / nx
+        blk = nx // 4
+        bs = 10.0 ** rng.uniform(-1.0, 2.0, (4, 4))
+        ratio = rng.uniform(0.5, 1.0, (4, 4))
+        sig_t = np.kron(bs, np.ones((blk, blk))).reshape(-1)
+        rat = np.kron(ratio, np.ones((blk, blk))).reshape(-1)
+        if rng.uniform() < 0.5:
+            g0 = np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2) / (2 * 0.05 ** 2))
+            kind = "gaussian"
+        else:
+            cx, cy = (rng.integers(0, nx, 2) + 0.5) * h
+            wd = 1.5 * h
+            g0 = np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * wd * wd))
+            kind = "point"
+        wl = Workload(
+            name=f"batch{i}-{nx}x{nx}-{tiles}x{tiles}-n{n}-r{rank}-{kind}", nx=nx, ny=nx,
+            x0=0.0, x1=1.0, y0=0.0, y1=1.0, xcuts=uniform_cuts(nx, tiles),
+            ycuts=uniform_cuts(nx, tiles), omega_x=ox, omega_y=oy, w=w,
+            sigma_s=rat * sig_t, sigma_a=(1.0 - rat) * sig_t, source=np.zeros(nx * nx), g0=g0,
+            dt=0.5 * h, nsteps=nsteps, rank_mode="fixed", rank=rank,
+            r_aug_max=min(2 * rank, 64), integrator=integrator, n_mu=n_mu, n_phi=n_phi)
+        out.setdefault(n, []).append(wl)
+    return out
