@@ -264,8 +264,14 @@ def run_ours(args, torch):
         mixed = {"value": units * args.steps * ws / t_m, "unit": UNIT,
                  "ms_per_step": t_m / args.steps * 1e3, "flux_rel_l2_vs_oracle": err_m,
                  "speedup_vs_fp64": t_ours / t_m,
-                 "arithmetic": "FP32: stencil, K/L/collision ODEs, eigen-split, augmentation "
-                               "SVD; FP64: CholeskyQR2, truncation SVD, reductions, storage"}
+                 "arithmetic": "FP32: stencil, K/L/collision ODE increments, eigen-split of C; "
+                               "FP64: updates, orthonormalisations, augmentation and "
+                               "truncation SVDs, reductions, storage"}
+
+    # ---- batched form ----------------------------------------------------------------
+    batch = None
+    if args.batch > 0:
+        batch = run_batch(args, torch, dev, flush)
 
     # ---- CPU baseline: the oracle on this machine's host cores ------------------------
     cpu = None
@@ -295,7 +301,96 @@ def run_ours(args, torch):
         line["cpu_baseline"] = cpu
     if mixed is not None:
         line["mixed"] = mixed
+    if batch is not None:
+        line["batch"] = batch
     return line, rank
+
+
+def run_batch(args, torch, dev, flush):
+    """The batched form: 64 seeded independent problems (grids 64^2/128^2/256^2, 2x2 or
+    4x4 tilings, 128/512/1024 directions, ranks 4..21, RK4), one solver per direction
+    count, the three solvers replayed concurrently on three streams.  Timed in FP64
+    and in mixed precision, beside the plain FP64 loop (one solver per problem, one
+    after another).  The mixed flux is compared with the FP64 flux of the same run."""
+    from paper_2602_14854_gb300 import binding, inputs
+    groups = sorted(inputs.batch_problems(count=args.batch).items())
+    units = sum(w.ncells * w.n for _, wls in groups for w in wls)
+    K = args.batch_steps
+    main = torch.cuda.current_stream(dev)
+
+    def timed(solvers, streams):
+        for sv in solvers:
+            sv.step(args.warmup)
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(main)
+        ends = []
+        for sv, st in zip(solvers, streams):
+            st.wait_event(t0)
+            sv.step(K)
+            e = torch.cuda.Event()
+            e.record(st)
+            ends.append(e)
+        for e in ends:
+            main.wait_event(e)
+        t1.record(main)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3
+
+    out = {"workload": f"batch{args.batch}: 64^2/128^2/256^2 grids, 2x2/4x4 tilings, "
+                       "128/512/1024 directions, ranks 4-21, RK4",
+           "problems": args.batch, "steps": K, "warmup": args.warmup,
+           "groups": [{"directions": n, "problems": len(wls),
+                       "cells": sum(w.ncells for w in wls)} for n, wls in groups],
+           "l2": "working set (tall factors of all problems) larger than L2"}
+    flux = {}
+    for prec in ("fp64", "mixed"):
+        streams = [torch.cuda.Stream(dev) for _ in groups]
+        solvers = [binding.Solver(wls, stream=st.cuda_stream, use_graph=True, precision=prec)
+                   for (n, wls), st in zip(groups, streams)]
+        t = timed(solvers, streams)
+        flux[prec] = [sv.scalar_flux() for sv in solvers]
+        launches = 0
+        if prec == "fp64":
+            launches = sum(c for sv in solvers for _, c in sv.profile(1).values())
+        for sv in solvers:
+            sv.close()
+        out[prec] = {"value": units * K / t, "unit": UNIT, "ms_per_step": t / K * 1e3}
+        if launches:
+            out[prec]["gpu_launches_per_step"] = launches
+    errs = []
+    for gi, (n, wls) in enumerate(groups):
+        for i in range(len(wls)):
+            a = flux["fp64"][gi]
+            m = flux["mixed"][gi]
+            lo = sum(w.ncells for w in wls[:i])
+            ref = a[lo:lo + wls[i].ncells]
+            got = m[lo:lo + wls[i].ncells]
+            errs.append(float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)))
+    out["mixed"]["flux_rel_l2_vs_fp64_max"] = max(errs)
+    out["mixed"]["flux_rel_l2_vs_fp64_median"] = float(np.median(errs))
+    out["mixed"]["speedup_vs_fp64_batched"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+
+    # plain FP64 loop: one solver per problem, replayed one after another
+    singles = [binding.Solver(w, stream=main.cuda_stream, use_graph=True)
+               for _, wls in groups for w in wls]
+    for sv in singles:
+        sv.step(args.warmup)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(main)
+    for _ in range(K):
+        for sv in singles:
+            sv.step(1)
+    t1.record(main)
+    torch.cuda.synchronize()
+    t = t0.elapsed_time(t1) / 1e3
+    for sv in singles:
+        sv.close()
+    out["fp64_loop"] = {"value": units * K / t, "unit": UNIT, "ms_per_step": t / K * 1e3}
+    out["mixed"]["speedup_vs_fp64_loop"] = out["fp64_loop"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    return out
 
 
 def cpu_baseline(wl, nsteps=3):
@@ -352,6 +447,9 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--batch", type=int, default=64,
+                    help="problems of the batched leg (0 skips it)")
+    ap.add_argument("--batch-steps", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     ws, rank, local = dist_env()

@@ -81,9 +81,10 @@ typedef struct dd_fields {
 enum { DD_RANK_FIXED = 0, DD_RANK_TOL = 1 };
 enum { DD_EULER = 0, DD_RK4 = 1 };
 /* Arithmetic of the step.  DD_FP64: FP64 throughout.  DD_MIXED: FP32 arithmetic for
- * the eigen-upwind stencil and the K-, L- and collision-step ODEs, the eigen-split of
- * C and the augmentation SVD; FP64 for CholeskyQR2 (Grams, factors), the truncation
- * SVD of S, every reduction and the stored factors. */
+ * the eigen-upwind stencil and the increments of the K-, L- and collision-step ODEs
+ * (each update itself is added in FP64) and the eigen-split of C; FP64 for the
+ * orthonormalisations and the augmentation SVD (FP32 sweeps, FP64 finish), the
+ * truncation SVD of S, every reduction and the stored factors. */
 enum { DD_FP64 = 0, DD_MIXED = 1 };
 
 typedef struct dd_options {

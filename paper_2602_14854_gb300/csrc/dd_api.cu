@@ -338,8 +338,10 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   h->nsub = (int)h->geo.size();
   h->ncells_out = fbase;
   h->Ntot = rowoff;
-  if (h->maxlines * h->RC > DD_THREADS * 24)
-    return bail(DD_ERR_ARG, "subdomain side x r_aug_max exceeds the K-step tile (6144)");
+  // the K-step holds one whole line of K (side x r_t <= side x r_aug_max values) per CTA
+  for (const SubGeo& s : h->geo)
+    if (std::max(s.nxk, s.nyk) * s.raug > DD_THREADS * 24)
+      return bail(DD_ERR_ARG, "subdomain side x r_aug_max exceeds the K-step tile (6144)");
 
   const int RC = h->RC, n = h->n, nsub = h->nsub, MC = h->MC;
   const long Nt = h->Ntot;

@@ -207,13 +207,6 @@ __device__ __forceinline__ void jacobi_columns(double* Bc, double* Jc, int m, in
   jacobi_columns_t<double>(Bc, Jc, m, ld, flag, nrm, JACOBI_TOL, 40);
 }
 
-// FP32 one-sided Jacobi on a scaled float copy (columns orthogonal to ~1e-6); the
-// accumulated rotation (orthogonal to FP32 rounding) is returned in Jc and
-// B <- B J in FP64.  Used by the mixed-precision path where FP32 accuracy is the
-// target.  Jc must hold the identity on entry.
-__device__ __forceinline__ void jacobi_svd_fp32(double* Bc, double* Jc, int m, int ld, int* flag,
-                                                double* nrm, void* scratch);
-
 // Shared scratch of jacobi_svd_mixed for leading dimension ld.
 __host__ __device__ __forceinline__ size_t jacobi_mixed_scratch_bytes(int ld) {
   return sizeof(float) * (2 * ld * ld + ld) + sizeof(double) * (2 * ld * ld);
@@ -285,42 +278,6 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
   }
   __syncthreads();
   jacobi_columns(Bc, Jc, m, ld, flag, nrm);
-}
-
-__device__ __forceinline__ void jacobi_svd_fp32(double* Bc, double* Jc, int m, int ld, int* flag,
-                                                double* nrm, void* scratch) {
-  float* B32 = reinterpret_cast<float*>(scratch);
-  float* J32 = B32 + ld * ld;
-  float* n32 = J32 + ld * ld;
-  double* T2 = reinterpret_cast<double*>(n32 + ld + (ld & 1)) + ld * ld;
-  if (m <= 1) return;
-  __shared__ double fred[40];
-  double mx = 0.0;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) mx = fmax(mx, fabs(Bc[(e / m) * ld + e % m]));
-  mx = block_max(mx, fred);
-  const double sc = (mx > 0.0 && isfinite(mx)) ? ldexp(1.0, -ilogb(mx)) : 1.0;
-  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
-    int c = e / ld, r = e % ld;
-    B32[e] = (c < m && r < m) ? (float)(Bc[e] * sc) : 0.f;
-    J32[e] = (c == r) ? 1.f : 0.f;
-  }
-  __syncthreads();
-  jacobi_columns_t<float>(B32, J32, m, ld, flag, n32, 1e-6f, 40);
-  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) Jc[e] = (double)J32[e];
-  __syncthreads();
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int c = e / m, r = e % m;
-    double x = 0.0;
-    for (int l = 0; l < m; ++l) x += Bc[l * ld + r] * Jc[c * ld + l];
-    T2[c * ld + r] = x;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int c = e / m, r = e % m;
-    Bc[c * ld + r] = T2[c * ld + r];
-  }
-  __syncthreads();
-  (void)nrm;
 }
 
 }  // namespace dd

@@ -12,7 +12,7 @@ enum KernelSlot {
   KS_AUG_COLS = 0, KS_BUILD_L0, KS_ORTH, KS_ANG_COEFFS, KS_REDUCE, KS_SMALL_ADV1, KS_TALL,
   KS_GHOST, KS_KSTEP_ADV, KS_SP_COEFFS, KS_SSTEP_ADV, KS_LSTEP_ADV, KS_GRAM, KS_TRUNC,
   KS_COLL_RANK, KS_COLL_A, KS_COLL_KSTEP, KS_COLL_SMALL, KS_COLL_LSTEP, KS_COLL_FINAL,
-  KS_FLUX, KS_COPY, KS_CQR1, KS_CQR2, NSLOT
+  KS_FLUX, KS_COPY, KS_CQR1, KS_CQR2, KS_ORTH_AUG, NSLOT
 };
 extern const char* const kSlotNames[NSLOT];
 
@@ -53,7 +53,6 @@ struct OrthArgs {
   const double* angcand; int n_angcand; int angcand_complete;
   double* sig_out; int* p_out;
   unsigned* status;
-  int svd_fp32;           // mixed path: the SVD of the augmentation in FP32
 };
 
 cudaError_t orth_init();

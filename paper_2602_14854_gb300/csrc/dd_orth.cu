@@ -403,8 +403,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a, int mcap, const
       sm.Jc[idx] = (row == col) ? 1.0 : 0.0;
     }
     __syncthreads();
-    if (a.svd_fp32) jacobi_svd_fp32(sm.Bc, sm.Jc, m, mcap, &iv[0], sm.sig, sm.X);
-    else jacobi_svd_mixed(sm.Bc, sm.Jc, m, mcap, &iv[0], sm.sig, sm.X);
+    jacobi_svd_mixed(sm.Bc, sm.Jc, m, mcap, &iv[0], sm.sig, sm.X);
     for (int j = warp; j < m; j += nwarps) {
       double s = 0.0;
       for (int l = lane; l < m; l += 32) s += sm.Bc[j * mcap + l] * sm.Bc[j * mcap + l];
@@ -559,8 +558,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_orth(OrthArgs a, int mcap, const
     }
 
     // ---- 4. one-sided Jacobi SVD of R, rank decision --------------------------------
-    if (a.svd_fp32) jacobi_svd_fp32(sm.Bc, sm.Jc, nref, mcap, &iv[0], sm.sig, sm.X);
-    else jacobi_svd_mixed(sm.Bc, sm.Jc, nref, mcap, &iv[0], sm.sig, sm.X);
+    jacobi_svd_mixed(sm.Bc, sm.Jc, nref, mcap, &iv[0], sm.sig, sm.X);
     for (int j = warp; j < nref; j += nwarps) {
       double s = 0.0;
       for (int l = lane; l < nref; l += 32) s += sm.Bc[j * mcap + l] * sm.Bc[j * mcap + l];
@@ -694,7 +692,7 @@ void launch_orth_fallback(const OrthArgs& a, int mcap, int maxrows, const int* f
   // the staged copy holds the input's columns: at most r_aug_max for a QR, mcap otherwise
   const int wcols = a.mode == ORTH_QR ? min(mcap, a.r_aug_max) : mcap;
   const size_t need = base + sizeof(double) * ((size_t)maxrows * wcols + 8);
-  pbeg(st, KS_ORTH);
+  pbeg(st, a.mode == ORTH_AUG ? KS_ORTH_AUG : KS_ORTH);
   if (need <= kSmemLimit)
     k_orth<true><<<a.g.nsub, DD_THREADS, need, st>>>(a, mcap, flag, sm_small, sB, sR2i);
   else

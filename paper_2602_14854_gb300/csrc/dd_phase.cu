@@ -418,7 +418,10 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
     if (e < tot) {
       int li = e / (len * rt), pos = (e / rt) % len, t = e % rt;
       int cell = cell_of(L, l0 + li, pos);
-      B.K[((long)P.g.rowoff[k] + cell) * RC + t] = (double)(k0[i] + dt * acc[i]);
+      double* Ke = B.K + ((long)P.g.rowoff[k] + cell) * RC + t;
+      // the increment is formed in TC, the update itself in FP64 (the start value is
+      // re-read, so FP32 arithmetic never rounds the state)
+      *Ke = *Ke + (double)(dt * acc[i]);
     }
   }
 }
@@ -543,7 +546,10 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
   TC* Glo = Am + RC * RC;
   TC* Ghi = Glo + RC * RC;
   TC* wsp = Ghi + RC * RC;          // per warp: vh, L0, Ls, g  (4*RC)
+  double* S2d = sh_raw + 5 * RC * RC + 8 * 4 * RC;   // FP64 copy for the start value
+  double* vhd = S2d + RC * RC;                         // per warp: FP64 vh (RC)
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    S2d[e] = SMB(B, P, k, SM_S2)[e];
     S2[e] = SMB(B, P, k, SM_S2)[e];
     Ap[e] = SMB(B, P, k, SM_AP)[e];
     Am[e] = SMB(B, P, k, SM_AM)[e];
@@ -556,28 +562,35 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
   TC* L0 = vh + RC;
   TC* Ls = L0 + RC;
   TC* gv = Ls + RC;
+  double* vw = vhd + warp * RC;
   const double* om = axis == 0 ? P.ox : P.oy;
   const TC dt = (TC)P.g.dtk[k];
   const TC hinv = (TC)(1.0 / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]));
   const int nst = P.integrator == 1 ? 4 : 1;
   for (int q = blockIdx.x * 32 + warp; q < min(n, (int)(blockIdx.x + 1) * 32); q += nw) {
     const double* Vq = B.Vh + ((long)k * n + q) * RC;
-    for (int t = lane; t < RC; t += 32) vh[t] = t < rt ? Vq[t] : 0.0;
+    for (int t = lane; t < RC; t += 32) {
+      vh[t] = t < rt ? Vq[t] : 0.0;
+      vw[t] = t < rt ? Vq[t] : 0.0;
+    }
     __syncwarp();
     const TC oq = om[q];
     const TC* A = oq > 0.0 ? Ap : Am;
     const TC kap = (TC)(-P.c_adv) * oq * hinv;
     TC accv[2] = {0.0, 0.0}, l0v[2] = {0.0, 0.0};
+    double l0d[2] = {0.0, 0.0};
     for (int h = 0; h < 2; ++h) {
       int i = lane + 32 * h;
       if (i < rt) {
-        TC s = 0.0, gg = 0.0;
+        TC gg = 0.0;
+        double sd = 0.0;
         for (int j = 0; j < rt; ++j) {
-          s += S2[i * RC + j] * vh[j];
+          sd += S2d[i * RC + j] * vw[j];
           if (oq > 0.0) gg -= Glo[i * RC + j] * vh[j];
           else if (oq < 0.0) gg += Ghi[i * RC + j] * vh[j];
         }
-        L0[i] = s; Ls[i] = s; gv[i] = gg; l0v[h] = s;
+        const TC s = (TC)sd;
+        L0[i] = s; Ls[i] = s; gv[i] = gg; l0v[h] = s; l0d[h] = sd;
       }
     }
     __syncwarp();
@@ -608,7 +621,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
     double* Lq = B.L + ((long)k * n + q) * RC;
     for (int h = 0; h < 2; ++h) {
       int i = lane + 32 * h;
-      if (i < RC) Lq[i] = i < rt ? (double)(l0v[h] + dt * accv[h]) : 0.0;
+      if (i < RC) Lq[i] = i < rt ? l0d[h] + (double)(dt * accv[h]) : 0.0;
     }
     __syncwarp();
   }
@@ -729,9 +742,11 @@ __global__ void k_coll_kstep(Problem P, PhaseBufs B) {
     const long row = (long)P.g.rowoff[k] + cell;
     const TC ss = (TC)(P.sig_s[row] / P.ssum), st = (TC)P.sig_t[row], sq = (TC)P.sQ[row];
     TC k0[2], ks[2], acc[2] = {0.0, 0.0}, av[2];
+    double k0d[2];
     for (int h = 0; h < 2; ++h) {
       int t = lane + 32 * h;
-      k0[h] = t < rc ? B.K[row * RC + t] : 0.0;
+      k0d[h] = t < rc ? B.K[row * RC + t] : 0.0;
+      k0[h] = (TC)k0d[h];
       av[h] = t < rc ? a[t] : 0.0;
       ks[h] = k0[h];
     }
@@ -748,7 +763,7 @@ __global__ void k_coll_kstep(Problem P, PhaseBufs B) {
     }
     for (int h = 0; h < 2; ++h) {
       int t = lane + 32 * h;
-      if (t < RC) B.K[row * RC + t] = t < rc ? (double)(k0[h] + dt * acc[h]) : 0.0;
+      if (t < RC) B.K[row * RC + t] = t < rc ? k0d[h] + (double)(dt * acc[h]) : 0.0;
     }
   }
 }
@@ -848,7 +863,10 @@ __global__ void __launch_bounds__(DD_THREADS) k_coll_lstep(Problem P, PhaseBufs 
   TC* Mt = S2 + RC * RC;
   TC* bst = Mt + RC * RC;         // 4 x RC
   TC* wsp = bst + 4 * RC;         // per warp: vh, Ls (2*RC)
+  double* S2d = sh_raw + 2 * RC * RC + 4 * RC + 8 * 2 * RC;   // FP64 copy for the start value
+  double* vhd = S2d + RC * RC;                                  // per warp: FP64 vh (RC)
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    S2d[e] = SMB(B, P, k, SM_S2)[e];
     S2[e] = SMB(B, P, k, SM_S2)[e];
     Mt[e] = SMB(B, P, k, SM_MT)[e];
   }
@@ -857,20 +875,25 @@ __global__ void __launch_bounds__(DD_THREADS) k_coll_lstep(Problem P, PhaseBufs 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   TC* vh = wsp + warp * 2 * RC;
   TC* Ls = vh + RC;
+  double* vw = vhd + warp * RC;
   const int nst = P.integrator == 1 ? 4 : 1;
   const TC dt = (TC)P.g.dtk[k];
   for (int q = blockIdx.x * 32 + warp; q < min(n, (int)(blockIdx.x + 1) * 32); q += nw) {
     const double* Vq = B.Vh + ((long)k * n + q) * RC;
-    for (int t = lane; t < RC; t += 32) vh[t] = t < rc ? Vq[t] : 0.0;
+    for (int t = lane; t < RC; t += 32) {
+      vh[t] = t < rc ? Vq[t] : 0.0;
+      vw[t] = t < rc ? Vq[t] : 0.0;
+    }
     __syncwarp();
     const TC swq = P.sw[q];
     TC l0v[2] = {0.0, 0.0}, accv[2] = {0.0, 0.0};
+    double l0d[2] = {0.0, 0.0};
     for (int h = 0; h < 2; ++h) {
       int i = lane + 32 * h;
       if (i < rc) {
-        TC s = 0.0;
-        for (int j = 0; j < rc; ++j) s += S2[i * RC + j] * vh[j];
-        l0v[h] = s; Ls[i] = s;
+        double sd = 0.0;
+        for (int j = 0; j < rc; ++j) sd += S2d[i * RC + j] * vw[j];
+        l0v[h] = (TC)sd; Ls[i] = (TC)sd; l0d[h] = sd;
       }
     }
     __syncwarp();
@@ -899,7 +922,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_coll_lstep(Problem P, PhaseBufs 
     double* Lq = B.L + ((long)k * n + q) * RC;
     for (int h = 0; h < 2; ++h) {
       int i = lane + 32 * h;
-      if (i < RC) Lq[i] = i < rc ? (double)(l0v[h] + dt * accv[h]) : 0.0;
+      if (i < RC) Lq[i] = i < rc ? l0d[h] + (double)(dt * accv[h]) : 0.0;
     }
     __syncwarp();
   }
@@ -955,6 +978,15 @@ __global__ void k_flux(Problem P, const double* X, const int* r, const double* w
   }
 }
 
+// TC working set plus an FP64 copy of S2 and one FP64 vh per warp
+size_t lstep_smem(int RC) {
+  return sizeof(double) * (5 * RC * RC + 8 * 4 * RC + RC * RC + 8 * RC);
+}
+
+size_t coll_lstep_smem(int RC) {
+  return sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC + RC * RC + 8 * RC);
+}
+
 size_t trunc_smem(int RC) {
   return sizeof(double) * (2 * RC * RC + RC) + 8 * ((jacobi_mixed_scratch_bytes(RC) + 7) / 8) +
          sizeof(int) * (RC + 8);
@@ -979,7 +1011,7 @@ const char* const kSlotNames[NSLOT] = {
     "k_aug_cols", "k_build_L0", "k_orth", "k_ang_coeffs", "k_reduce", "k_small_adv1", "k_tall",
     "k_ghost", "k_kstep_adv", "k_sp_coeffs", "k_sstep_adv", "k_lstep_adv", "k_gram", "k_trunc",
     "k_coll_rank", "k_coll_a", "k_coll_kstep", "k_coll_small", "k_coll_lstep", "k_coll_final",
-    "k_flux", "memcpy", "k_cqr1", "k_cqr2"};
+    "k_flux", "memcpy", "k_cqr1", "k_cqr2", "k_orth(aug)"};
 thread_local Prof* g_prof = nullptr;
 
 size_t part_elems(const Problem& P) {
@@ -998,10 +1030,10 @@ cudaError_t phase_init(const Problem& P) {
                            (int)(sizeof(double) * 6 * RC * RC));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_lstep_adv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * (5 * RC * RC + 8 * 4 * RC)));
+                           (int)(lstep_smem(RC)));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_lstep_adv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * (5 * RC * RC + 8 * 4 * RC)));
+                           (int)(lstep_smem(RC)));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_small_adv1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(double) * (2 * RC * RC + 2 * RC) + 64));
@@ -1016,10 +1048,10 @@ cudaError_t phase_init(const Problem& P) {
                            (int)(sizeof(double) * (4 * RC * RC + 5 * RC)));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_coll_lstep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC)));
+                           (int)(coll_lstep_smem(RC)));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_coll_lstep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC)));
+                           (int)(coll_lstep_smem(RC)));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_build_L0, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(double) * 3 * RC * RC));
@@ -1067,7 +1099,6 @@ static OrthArgs orth_args(const Problem& P, const PhaseBufs& B, int spatial, int
   a.angcand = P.angcand; a.n_angcand = P.n_angcand; a.angcand_complete = P.angcand_complete;
   a.sig_out = B.sig; a.p_out = B.p; a.status = B.status;
   a.r_own = B.r; a.rt_out = B.rt;
-  a.svd_fp32 = (P.prec == 1 && mode == ORTH_AUG) ? 1 : 0;
   a.W = spatial ? B.Hw : B.Hwa; a.ldw = P.WC;
   return a;
 }
@@ -1170,10 +1201,10 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   // 9. L-step
   pbeg(st, KS_LSTEP_ADV);
   if (P.prec == 1) {
-    k_lstep_adv<float><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, sizeof(double) * (5 * RC * RC + 8 * 4 * RC),
+    k_lstep_adv<float><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, lstep_smem(RC),
                   st>>>(P, B, axis);
   } else {
-    k_lstep_adv<double><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, sizeof(double) * (5 * RC * RC + 8 * 4 * RC),
+    k_lstep_adv<double><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, lstep_smem(RC),
                   st>>>(P, B, axis);
   }
   pend(st);
@@ -1244,10 +1275,10 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   pbeg(st, KS_COLL_LSTEP);
   if (P.prec == 1) {
     k_coll_lstep<float><<<dim3((g.n + 31) / 32, nsub), DD_THREADS,
-                   sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC), st>>>(P, B);
+                   coll_lstep_smem(RC), st>>>(P, B);
   } else {
     k_coll_lstep<double><<<dim3((g.n + 31) / 32, nsub), DD_THREADS,
-                   sizeof(double) * (2 * RC * RC + 4 * RC + 8 * 2 * RC), st>>>(P, B);
+                   coll_lstep_smem(RC), st>>>(P, B);
   }
   pend(st);
   {

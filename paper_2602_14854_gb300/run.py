@@ -22,6 +22,35 @@ WORKLOADS = {
 }
 
 
+def run_batch(args):
+    """The 64-problem batch, one solver per direction count."""
+    groups = inputs.batch_problems(count=args.batch, nsteps=args.steps or 100)
+    out = {"workload": f"batch{args.batch}", "groups": []}
+    total_units, total_t = 0.0, 0.0
+    for n, wls in sorted(groups.items()):
+        s = binding.Solver(wls, use_graph=args.graph, precision=args.precision)
+        s.step(args.warmup)
+        s.sync()
+        nsteps = args.steps or 100
+        t0 = time.perf_counter()
+        s.step(nsteps)
+        s.sync()
+        t = time.perf_counter() - t0
+        units = sum(w.ncells for w in wls) * n * nsteps
+        total_units += units
+        total_t += t
+        g = {"directions": n, "problems": len(wls), "subdomains": s.nsub, "seconds": t,
+             "updates_per_s": units / t}
+        if args.profile:
+            prof = s.profile(args.profile)
+            g["profile_ms"] = {k: [round(v[0], 3), v[1]] for k, v in
+                               sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}
+        out["groups"].append(g)
+        s.close()
+    out["updates_per_s"] = total_units / total_t
+    print(json.dumps(out))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="pointsource", choices=sorted(WORKLOADS))
@@ -29,11 +58,18 @@ def main(argv=None):
     ap.add_argument("--graph", action="store_true")
     ap.add_argument("--profile", type=int, default=0,
                     help="additionally advance this many steps with per-kernel event timing")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--batch", type=int, default=0,
+                    help="run the batched form on this many seeded problems instead")
+    ap.add_argument("--warmup", type=int, default=2)
     args = ap.parse_args(argv)
     build.build()
+    if args.batch:
+        run_batch(args)
+        return
     wl = WORKLOADS[args.workload]()
     nsteps = wl.nsteps if args.steps is None else args.steps
-    s = binding.Solver(wl, use_graph=args.graph)
+    s = binding.Solver(wl, use_graph=args.graph, precision=args.precision)
     t0 = time.perf_counter()
     s.step(nsteps)
     s.sync()

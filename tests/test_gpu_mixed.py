@@ -1,7 +1,8 @@
 """Mixed-precision form (DD_MIXED) against the FP64 CPU oracle.
 
-FP32 arithmetic for the stencil, the K-/L-/collision-step ODEs, the eigen-split of C
-and the augmentation SVD; FP64 for CholeskyQR2, the truncation SVD and reductions.
+FP32 arithmetic for the stencil, the increments of the K-/L-/collision-step ODEs and
+the eigen-split of C; FP64 for the updates, the orthonormalisations, the augmentation
+and truncation SVDs and reductions.
 Target: scalar-flux rel-L2 <= 1e-5 against the oracle (FP32 target of the task
 statement), on the same workloads as the FP64 parity tests.
 """
