@@ -80,11 +80,11 @@ typedef struct dd_fields {
 
 enum { DD_RANK_FIXED = 0, DD_RANK_TOL = 1 };
 enum { DD_EULER = 0, DD_RK4 = 1 };
-/* Arithmetic of the step.  DD_FP64: FP64 throughout.  DD_MIXED: FP32 arithmetic for
- * the eigen-upwind stencil and the increments of the K-, L- and collision-step ODEs
- * (each update itself is added in FP64) and the eigen-split of C; FP64 for the
- * orthonormalisations and the augmentation SVD (FP32 sweeps, FP64 finish), the
- * truncation SVD of S, every reduction and the stored factors. */
+/* Arithmetic of the step.  DD_FP64: FP64 throughout, except that the small
+ * eigen/singular value problems (m x m, m <= 64) run FP32 Jacobi sweeps finished in
+ * double-float arithmetic (~1e-13 relative).  DD_MIXED: in addition, FP32 arithmetic
+ * for the eigen-upwind stencil and for the increments of the K-, L- and
+ * collision-step ODEs (each update itself is added in FP64). */
 enum { DD_FP64 = 0, DD_MIXED = 1 };
 
 typedef struct dd_options {

@@ -85,8 +85,7 @@ struct dd_dlra {
   // device: workspace
   double *d_L0, *d_Hw, *d_Hwa, *d_Vh, *d_K, *d_X1, *d_L, *d_V1, *d_Kb, *d_sm, *d_part;
   double *d_sig, *d_rho, *d_fluxw;
-  int *d_m, *d_rt, *d_rx, *d_rc, *d_p, *d_flag;
-  double* d_scale;
+  int *d_m, *d_rt, *d_rx, *d_rc, *d_p, *d_keep, *d_cexp;
   unsigned* d_status;
   dd::Problem P;
 };
@@ -101,7 +100,7 @@ dd::PhaseBufs bufs(dd_dlra* h, int in, int out) {
   B.X1 = h->d_X1; B.L = h->d_L; B.V1 = h->d_V1; B.Kb = h->d_Kb; B.sm = h->d_sm;
   B.part = h->d_part; B.m = h->d_m; B.rt = h->d_rt; B.rx = h->d_rx; B.rc = h->d_rc;
   B.sig = h->d_sig; B.p = h->d_p; B.status = h->d_status;
-  B.flag = h->d_flag; B.scale = h->d_scale;
+  B.keep = h->d_keep; B.cexp = h->d_cexp;
   return B;
 }
 
@@ -169,7 +168,7 @@ void free_all(dd_dlra* h) {
                   h->d_S[1], h->d_r[0], h->d_r[1], h->d_L0, h->d_Hw, h->d_Hwa, h->d_Vh,
                   h->d_K, h->d_X1, h->d_L, h->d_V1, h->d_Kb, h->d_sm, h->d_part, h->d_sig,
                   h->d_rho, h->d_fluxw, h->d_m, h->d_rt, h->d_rx, h->d_rc, h->d_p, h->d_status,
-                  h->d_flag, h->d_scale, h->d_rlo, h->d_rhi, h->d_raug, h->d_fbase,
+                  h->d_keep, h->d_cexp, h->d_rlo, h->d_rhi, h->d_raug, h->d_fbase,
                   h->d_fnx, h->d_hxk, h->d_hyk, h->d_dtk, h->d_shk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -429,8 +428,8 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   ok &= dalloc(&h->d_rx, 2 * nsub) == cudaSuccess;
   ok &= dalloc(&h->d_rc, nsub) == cudaSuccess;
   ok &= dalloc(&h->d_p, nsub) == cudaSuccess;
-  ok &= dalloc(&h->d_flag, nsub) == cudaSuccess;
-  ok &= dalloc(&h->d_scale, nsub) == cudaSuccess;
+  ok &= dalloc(&h->d_keep, nsub) == cudaSuccess;
+  ok &= dalloc(&h->d_cexp, (long)nsub * 16) == cudaSuccess;
   ok &= dalloc(&h->d_status, 1) == cudaSuccess;
   if (!ok) return bail(DD_ERR_CUDA, "device allocation failed");
 
@@ -455,7 +454,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   P.nchunk_ang = std::max(1, std::min(16, n / 64));
   if (dalloc(&h->d_part, dd::part_elems(P)) != cudaSuccess)
     return bail(DD_ERR_CUDA, "device allocation failed");
-  if (dd::orth_init() != cudaSuccess || dd::phase_init(P) != cudaSuccess)
+  if (dd::orth_init() != cudaSuccess || dd::phase_init() != cudaSuccess)
     return bail(DD_ERR_CUDA, "kernel attribute setup failed");
 
   // isotropic initial data at rank 1 (rank 0 where g0 vanishes on the subdomain)

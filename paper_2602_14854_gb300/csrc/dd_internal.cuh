@@ -110,6 +110,22 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return red[32];
 }
 
+// Stable descending order of v[0..n) by ranks (block-wide, one thread per entry):
+// perm[t] is the index of the t-th largest value, ties by index.  NaN ranks as
+// -infinity, so perm is a permutation for any input.
+__device__ __forceinline__ double rank_key(double x) { return x == x ? x : -INFINITY; }
+__device__ __forceinline__ void rank_sort_desc(const double* v, int n, int* perm) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = rank_key(v[i]);
+    int r = 0;
+    for (int j = 0; j < n; ++j) {
+      const double y = rank_key(v[j]);
+      r += (y > x) || (y == x && j < i);
+    }
+    perm[r] = i;
+  }
+}
+
 // Round-robin (circle method) pairing for parallel Jacobi sweeps over mm
 // (even) indices: round r in [0, mm-1), pair i in [0, mm/2).
 __device__ __forceinline__ void rr_pair(int mm, int r, int i, int* p, int* q) {
@@ -124,23 +140,104 @@ __device__ __forceinline__ void rr_pair(int mm, int r, int i, int* p, int* q) {
 
 #define JACOBI_TOL 1e-15
 
-// One-sided Jacobi (Hestenes) on the m columns (length m) of the column-major
-// matrix Bc (leading dimension ld), accumulating the rotations in Jc, until no
-// pair has |b_p . b_q| > tol |b_p| |b_q| and > 1e-30 |B|_F^2 (pairs of columns
-// negligible against the whole matrix are left alone: rotating rounding noise
-// never converges and cannot change the significant directions).
-// Column norms are recomputed at the start of every sweep and updated exactly in
-// between (a rotation with tangent t that annihilates gamma = b_p . b_q maps the
-// squared norms to alpha - t gamma and beta + t gamma), so each pair needs one
-// dot product.  The rotation is computed by lane 0 of the warp that owns the pair.
-// Block-wide; flag is shared scratch, nrm is m values of shared scratch.
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
-template <typename T>
-__device__ __forceinline__ void jacobi_columns_t(T* Bc, T* Jc, int m, int ld, int* flag, T* nrm,
-                                                 T tol, int max_sweeps) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+// ---------------------------------------------------------------------------
+// Double-float ("float-float") arithmetic: a value is the unevaluated sum hi + lo of
+// two floats, |lo| <= ulp(hi)/2, about 48 significant bits.  Built from the exact
+// error-free transformations of Knuth (TwoSum) and Dekker (Fast2Sum), with the product
+// error taken by one FMA.  Explicit _rn intrinsics keep the compiler from contracting
+// or reassociating the compensated sequences.  On this GPU FP32 issues at 64x the
+// FP64 rate, so small sequential linear algebra runs several times faster this way
+// than in FP64 while keeping ~1e-14 relative accuracy.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+  return make_float2(s, e);
+}
+__device__ __forceinline__ float2 df_fast_sum(float a, float b) {   // needs |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float2 s = df_two_sum(a.x, b.x);
+  return df_fast_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return df_fast_sum(p, e);
+}
+__device__ __forceinline__ float2 df_mulf(float2 a, float b) {
+  const float p = __fmul_rn(a.x, b);
+  float e = __fmaf_rn(a.x, b, -p);
+  e = __fmaf_rn(a.y, b, e);
+  return df_fast_sum(p, e);
+}
+__device__ __forceinline__ float2 df_sqrt(float2 a) {          // a > 0
+  const float y = sqrtf(a.x);
+  const float p = __fmul_rn(y, y);
+  const float2 r = df_add(a, make_float2(-p, -__fmaf_rn(y, y, -p)));
+  return df_fast_sum(y, r.x / (2.f * y));
+}
+__device__ __forceinline__ float2 df_div(float2 a, float2 b) {
+  const float q1 = a.x / b.x;
+  const float2 r = df_add(a, df_neg(df_mulf(b, q1)));
+  return df_fast_sum(q1, r.x / b.x);
+}
+__device__ __forceinline__ float2 df_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ float2 df_shfl_xor(unsigned mask, float2 v, int o) {
+  return make_float2(__shfl_xor_sync(mask, v.x, o), __shfl_xor_sync(mask, v.y, o));
+}
+__device__ __forceinline__ float2 df_shfl(unsigned mask, float2 v, int src) {
+  return make_float2(__shfl_sync(mask, v.x, src), __shfl_sync(mask, v.y, src));
+}
+
+// ---------------------------------------------------------------------------
+// One-sided (Hestenes) Jacobi on the m columns (length m <= 64) of the column-major
+// matrix B (leading dimension ld), accumulating the rotations in J, until no pair
+// has |b_p . b_q| > tol |b_p| |b_q| and > 1e-30 |B|_F^2 (pairs negligible against
+// the whole matrix are left alone: rotating rounding noise never converges and
+// cannot change the significant directions).  Pairs follow the round-robin order;
+// a half-warp owns a pair (each of its 16 lanes holds up to 4 entries of a column),
+// so the 8 warps of a CTA rotate 16 disjoint pairs at once.  Squared column norms
+// are recomputed at the start of every sweep and updated in between (a rotation
+// with tangent t annihilating gamma = b_p . b_q maps them to alpha - t gamma and
+// beta + t gamma).  The rotation is computed by the first lane of the half-warp.
+// Block-wide; flag is two ints of shared scratch, nrm holds m values of shared scratch.
+// ---------------------------------------------------------------------------
+#define JAC_PER 4   // entries per lane: m <= 16 * JAC_PER
+
+__device__ __forceinline__ float half_sum(float v, unsigned hm) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(hm, v, o);
+  return v;
+}
+__device__ __forceinline__ float2 half_sum_df(float2 v, unsigned hm) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(hm, v, o));
+  return v;
+}
+
+// FP32 sweeps.  Besides the convergence test, a sweep whose largest relative
+// off-diagonal |b_p . b_q| / (|b_p| |b_q|) was below stop ends the iteration: in the
+// quadratic regime it leaves them at ~stop^2.
+__device__ __forceinline__ void jacobi_f32(float* Bc, float* Jc, int m, int ld, int* flag,
+                                           float* nrm, float tol, float stop, int max_sweeps) {
+  const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
+  const int slot0 = (threadIdx.x >> 5) * 2 + half, nslot = (blockDim.x >> 5) * 2;
+  const unsigned hm = half ? 0xffff0000u : 0x0000ffffu;
+  const int src = half * 16;
   const int mm = m + (m & 1);
   __shared__ double jred[40];
   double nf = 0.0;
@@ -148,136 +245,292 @@ __device__ __forceinline__ void jacobi_columns_t(T* Bc, T* Jc, int m, int ld, in
     double x = (double)Bc[(e / m) * ld + e % m];
     nf += x * x;
   }
-  const T abs_thr = (T)(1e-30 * block_sum(nf, jred));
+  const float abs_thr = (float)(1e-30 * block_sum(nf, jred));
   for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
-    for (int j = warp; j < m; j += nwarps) {
-      T s2 = 0;
-      for (int l = lane; l < m; l += 32) s2 += Bc[j * ld + l] * Bc[j * ld + l];
+    for (int j = slot0; j < m; j += nslot) {
+      float s2 = 0.f;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-      if (lane == 0) nrm[j] = s2;
+      for (int i = 0; i < JAC_PER; ++i) {
+        const int l = hl + 16 * i;
+        if (l < m) s2 = __fmaf_rn(Bc[j * ld + l], Bc[j * ld + l], s2);
+      }
+      s2 = half_sum(s2, hm);
+      if (hl == 0) nrm[j] = s2;
     }
-    if (threadIdx.x == 0) *flag = 0;
+    if (threadIdx.x == 0) { flag[0] = 0; flag[1] = 0; }
     __syncthreads();
     for (int r = 0; r < mm - 1; ++r) {
-      for (int pi = warp; pi < mm / 2; pi += nwarps) {
+      for (int pi = slot0; pi < mm / 2; pi += nslot) {
         int p, q;
         rr_pair(mm, r, pi, &p, &q);
         if (p >= m || q >= m) continue;
-        T* bp = Bc + p * ld;
-        T* bq = Bc + q * ld;
-        T ga = 0;
-        for (int l = lane; l < m; l += 32) ga += bp[l] * bq[l];
+        float* bp = Bc + p * ld;
+        float* bq = Bc + q * ld;
+        float ga = 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        const T al = nrm[p], be = nrm[q];
-        if (!(fabs(ga) > abs_thr && fabs(ga) > tol * sqrt(al * be))) continue;
-        T c = 0, s = 0, t = 0;
-        if (lane == 0) {
-          const T zeta = (be - al) / (2 * ga);
-          if (fabs(zeta) > (T)1e8) t = (T)0.5 / zeta;   // small angle: exact to rounding
-          else t = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-          c = rsqrt_t((T)1 + t * t);
-          s = c * t;
-          nrm[p] = al - t * ga;
-          nrm[q] = be + t * ga;
-          *flag = 1;
+        for (int i = 0; i < JAC_PER; ++i) {
+          const int l = hl + 16 * i;
+          if (l < m) ga = __fmaf_rn(bp[l], bq[l], ga);
         }
-        c = __shfl_sync(0xffffffffu, c, 0);
-        s = __shfl_sync(0xffffffffu, s, 0);
-        T* jp = Jc + p * ld;
-        T* jq = Jc + q * ld;
-        for (int l = lane; l < m; l += 32) {
-          T x = bp[l], y = bq[l];
-          bp[l] = c * x - s * y; bq[l] = s * x + c * y;
-          x = jp[l]; y = jq[l];
-          jp[l] = c * x - s * y; jq[l] = s * x + c * y;
+        ga = half_sum(ga, hm);
+        float c = 1.f, s = 0.f;
+        int rot = 0;
+        if (hl == 0) {
+          const float al = nrm[p], be = nrm[q];
+          const float den = sqrtf(al * be);
+          if (fabsf(ga) > abs_thr && den > 0.f) atomicMax(flag + 1, __float_as_int(fabsf(ga) / den));
+          if (fabsf(ga) > abs_thr && fabsf(ga) > tol * den) {
+            const float zeta = (be - al) / (2.f * ga);
+            float t;
+            if (fabsf(zeta) > 1e8f) t = 0.5f / zeta;
+            else t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+            c = rsqrtf(1.f + t * t);
+            s = c * t;
+            nrm[p] = al - t * ga;
+            nrm[q] = be + t * ga;
+            *flag = 1;
+            rot = 1;
+          }
+        }
+        rot = __shfl_sync(hm, rot, src);
+        if (!rot) continue;
+        c = __shfl_sync(hm, c, src);
+        s = __shfl_sync(hm, s, src);
+        float* jp = Jc + p * ld;
+        float* jq = Jc + q * ld;
+#pragma unroll
+        for (int i = 0; i < JAC_PER; ++i) {
+          const int l = hl + 16 * i;
+          if (l < m) {
+            float x = bp[l], y = bq[l];
+            bp[l] = c * x - s * y; bq[l] = s * x + c * y;
+            x = jp[l]; y = jq[l];
+            jp[l] = c * x - s * y; jq[l] = s * x + c * y;
+          }
         }
       }
       __syncthreads();
     }
-    int f = *flag;
+    const int f = flag[0];
+    const float mrel = __int_as_float(flag[1]);
     __syncthreads();
-    if (f == 0) break;
+    if (f == 0 || mrel < stop) break;
   }
 }
 
-__device__ __forceinline__ void jacobi_columns(double* Bc, double* Jc, int m, int ld, int* flag,
-                                               double* nrm) {
-  jacobi_columns_t<double>(Bc, Jc, m, ld, flag, nrm, JACOBI_TOL, 40);
+// double-float sweeps (same algorithm; the rotation's tangent comes from the hi parts
+// in FP32 and c = (1 + t^2)^-1/2 is refined by one Newton step in double-float, so
+// every rotation is orthogonal to double-float rounding)
+__device__ __forceinline__ void jacobi_df(float2* Bd, float2* Jd, int m, int ld, int* flag,
+                                          float2* nrm, float tol, float stop, int max_sweeps) {
+  const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
+  const int slot0 = (threadIdx.x >> 5) * 2 + half, nslot = (blockDim.x >> 5) * 2;
+  const unsigned hm = half ? 0xffff0000u : 0x0000ffffu;
+  const int src = half * 16;
+  const int mm = m + (m & 1);
+  __shared__ double jred[40];
+  double nf = 0.0;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    double x = (double)Bd[(e / m) * ld + e % m].x;
+    nf += x * x;
+  }
+  const float abs_thr = (float)(1e-30 * block_sum(nf, jred));
+  for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
+    for (int j = slot0; j < m; j += nslot) {
+      float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < JAC_PER; ++i) {
+        const int l = hl + 16 * i;
+        if (l < m) s2 = df_add(s2, df_mul(Bd[j * ld + l], Bd[j * ld + l]));
+      }
+      s2 = half_sum_df(s2, hm);
+      if (hl == 0) nrm[j] = s2;
+    }
+    if (threadIdx.x == 0) { flag[0] = 0; flag[1] = 0; }
+    __syncthreads();
+    for (int r = 0; r < mm - 1; ++r) {
+      for (int pi = slot0; pi < mm / 2; pi += nslot) {
+        int p, q;
+        rr_pair(mm, r, pi, &p, &q);
+        if (p >= m || q >= m) continue;
+        float2* bp = Bd + p * ld;
+        float2* bq = Bd + q * ld;
+        float2 ga = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < JAC_PER; ++i) {
+          const int l = hl + 16 * i;
+          if (l < m) ga = df_add(ga, df_mul(bp[l], bq[l]));
+        }
+        ga = half_sum_df(ga, hm);
+        float2 c = make_float2(1.f, 0.f), s = make_float2(0.f, 0.f);
+        int rot = 0;
+        if (hl == 0) {
+          const float2 al = nrm[p], be = nrm[q];
+          const float den = sqrtf(al.x * be.x);
+          if (fabsf(ga.x) > abs_thr && den > 0.f) atomicMax(flag + 1, __float_as_int(fabsf(ga.x) / den));
+          if (fabsf(ga.x) > abs_thr && fabsf(ga.x) > tol * den) {
+            const float zeta = df_add(be, df_neg(al)).x / (2.f * ga.x);
+            float t;
+            if (fabsf(zeta) > 1e8f) t = 0.5f / zeta;
+            else t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+            // w = 1 + t^2 exactly enough; c = w^-1/2 by one Newton step from rsqrtf
+            const float2 w = df_add(make_float2(1.f, 0.f), df_mulf(make_float2(t, 0.f), t));
+            const float y0 = rsqrtf(w.x);
+            const float2 h = df_add(make_float2(1.f, 0.f), df_neg(df_mulf(df_mulf(w, y0), y0)));
+            c = df_add(make_float2(y0, 0.f), df_mulf(h, 0.5f * y0));
+            s = df_mulf(c, t);
+            const float2 tg = df_mulf(ga, t);
+            nrm[p] = df_add(al, df_neg(tg));
+            nrm[q] = df_add(be, tg);
+            *flag = 1;
+            rot = 1;
+          }
+        }
+        rot = __shfl_sync(hm, rot, src);
+        if (!rot) continue;
+        c = df_shfl(hm, c, src);
+        s = df_shfl(hm, s, src);
+        const float2 ns = df_neg(s);
+        float2* jp = Jd + p * ld;
+        float2* jq = Jd + q * ld;
+#pragma unroll
+        for (int i = 0; i < JAC_PER; ++i) {
+          const int l = hl + 16 * i;
+          if (l < m) {
+            float2 x = bp[l], y = bq[l];
+            bp[l] = df_add(df_mul(c, x), df_mul(ns, y));
+            bq[l] = df_add(df_mul(s, x), df_mul(c, y));
+            x = jp[l]; y = jq[l];
+            jp[l] = df_add(df_mul(c, x), df_mul(ns, y));
+            jq[l] = df_add(df_mul(s, x), df_mul(c, y));
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const int f = flag[0];
+    const float mrel = __int_as_float(flag[1]);
+    __syncthreads();
+    if (f == 0 || mrel < stop) break;
+  }
 }
 
-// Shared scratch of jacobi_svd_mixed for leading dimension ld.
+// Shared scratch of jacobi_svd_mixed for leading dimension ld: the FP32 copies of B
+// and J (reused as a double-float temporary afterwards), m norms, and the
+// double-float B and J.
 __host__ __device__ __forceinline__ size_t jacobi_mixed_scratch_bytes(int ld) {
-  return sizeof(float) * (2 * ld * ld + ld) + sizeof(double) * (2 * ld * ld);
+  return sizeof(float) * (2 * ld * ld + 2 * ld) + sizeof(float2) * (2 * ld * ld);
 }
 
-// The same result as jacobi_columns (FP64 accuracy, Jc orthogonal to rounding),
-// with most of the sweeps on the FP32 pipe: FP32 sweeps on a float copy until the
-// columns are orthogonal to ~1e-6, two Newton-Schulz steps J <- J (3I - J^T J)/2
-// in FP64 make the accumulated rotation orthogonal to rounding, B <- B J in FP64,
-// then FP64 sweeps finish (typically two).  Jc must hold the identity on entry.
-__device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, int ld, int* flag,
-                                                 double* nrm, void* scratch) {
+// FP32 variant for the mixed-precision path: the sweeps alone (columns orthogonal to
+// ~1e-6, J orthogonal to ~1e-7); on return Bc = B J and Jc = J as with the FP64-accurate
+// version.  Same scratch.
+__device__ __forceinline__ void jacobi_svd_f32(double* Bc, double* Jc, int m, int ld, int* flag,
+                                               void* scratch) {
   float* B32 = reinterpret_cast<float*>(scratch);
   float* J32 = B32 + ld * ld;
   float* n32 = J32 + ld * ld;
-  double* T1 = reinterpret_cast<double*>(n32 + ld + (ld & 1));
-  double* T2 = T1 + ld * ld;
-  if (m <= 2) { jacobi_columns(Bc, Jc, m, ld, flag, nrm); return; }
-  // power-of-two scaling keeps the float copy clear of underflow and overflow
+  if (m <= 0) return;
+  __shared__ double fred[40];
+  double mx = 0.0;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) mx = fmax(mx, fabs(Bc[(e / m) * ld + e % m]));
+  mx = block_max(mx, fred);
+  if (!(mx > 0.0) || !isfinite(mx)) return;
+  const int ex = ilogb(mx);              // scalbn: 2^-ex itself may not be representable
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
+    int c = e / ld, r = e % ld;
+    B32[e] = (c < m && r < m) ? (float)scalbn(Bc[e], -ex) : 0.f;
+    J32[e] = (c == r) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  jacobi_f32(B32, J32, m, ld, flag, n32, 1e-6f, 1e-3f, 30);
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
+    int c = e / ld, r = e % ld;
+    if (c < m && r < m) {
+      Bc[e] = scalbn((double)B32[e], ex);
+      Jc[e] = (double)J32[e];
+    }
+  }
+  __syncthreads();
+}
+
+// SVD of the m x m (m <= 64) column-major B by one-sided Jacobi, accurate to about
+// 1e-13 relative to |B|: FP32 sweeps on a power-of-two scaled float copy until the
+// columns are orthogonal to ~1e-6; the accumulated rotation, converted to
+// double-float, is made orthogonal by two Newton-Schulz steps J <- J (3I - J^T J)/2;
+// B <- B J in double-float; double-float sweeps finish (typically two or three).
+// On return B J (in Bc, FP64) has orthogonal columns and Jc (FP64) is orthogonal.
+// Jc must hold the identity on entry; flag and nrm as for the sweeps.
+__device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, int ld, int* flag,
+                                                 double* nrm, void* scratch) {
+  (void)nrm;
+  float* B32 = reinterpret_cast<float*>(scratch);
+  float* J32 = B32 + ld * ld;
+  float* n32 = J32 + ld * ld;
+  float2* T = reinterpret_cast<float2*>(B32);           // after the FP32 sweeps
+  float2* Bd = reinterpret_cast<float2*>(n32 + 2 * ld);
+  float2* Jd = Bd + ld * ld;
+  if (m <= 0) return;
   __shared__ double mred[40];
   double mx = 0.0;
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) mx = fmax(mx, fabs(Bc[(e / m) * ld + e % m]));
   mx = block_max(mx, mred);
-  const double sc = (mx > 0.0 && isfinite(mx)) ? ldexp(1.0, -ilogb(mx)) : 1.0;
+  if (!(mx > 0.0) || !isfinite(mx)) return;
+  const int ex = ilogb(mx);              // scalbn: 2^-ex itself may not be representable
   for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
     int c = e / ld, r = e % ld;
-    B32[e] = (c < m && r < m) ? (float)(Bc[e] * sc) : 0.f;
+    B32[e] = (c < m && r < m) ? (float)scalbn(Bc[e], -ex) : 0.f;
     J32[e] = (c == r) ? 1.f : 0.f;
   }
   __syncthreads();
-  jacobi_columns_t<float>(B32, J32, m, ld, flag, n32, 1e-6f, 30);
-  // J = float -> double, two Newton-Schulz steps (column-major m x m)
-  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) Jc[e] = (double)J32[e];
+  jacobi_f32(B32, J32, m, ld, flag, n32, 1e-6f, 1e-3f, 30);
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) Jd[e] = make_float2(J32[e], 0.f);
   __syncthreads();
+  // two Newton-Schulz steps: T = 3I - J^T J, J <- J T / 2 (via Bd as the output)
   for (int it = 0; it < 2; ++it) {
-    // T1 = J^T J
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       int i = e / m, j = e % m;
-      double x = 0.0;
-      for (int l = 0; l < m; ++l) x += Jc[i * ld + l] * Jc[j * ld + l];
-      T1[i * ld + j] = (i == j ? 3.0 : 0.0) - x;
-    }
-    __syncthreads();
-    // T2 = J T1 / 2   (column j of T2 = J * column j of T1)
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      int c = e / m, r = e % m;
-      double x = 0.0;
-      for (int l = 0; l < m; ++l) x += Jc[l * ld + r] * T1[l * ld + c];
-      T2[c * ld + r] = 0.5 * x;
+      float2 x = make_float2(0.f, 0.f);
+      for (int l = 0; l < m; ++l) x = df_add(x, df_mul(Jd[i * ld + l], Jd[j * ld + l]));
+      T[i * ld + j] = df_add(make_float2(i == j ? 3.f : 0.f, 0.f), df_neg(x));
     }
     __syncthreads();
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       int c = e / m, r = e % m;
-      Jc[c * ld + r] = T2[c * ld + r];
+      float2 x = make_float2(0.f, 0.f);
+      for (int l = 0; l < m; ++l) x = df_add(x, df_mul(Jd[l * ld + r], T[c * ld + l]));
+      Bd[c * ld + r] = df_mulf(x, 0.5f);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      int c = e / m, r = e % m;
+      Jd[c * ld + r] = Bd[c * ld + r];
     }
     __syncthreads();
   }
-  // B <- B J
+  // B <- (sc B) J in double-float
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     int c = e / m, r = e % m;
-    double x = 0.0;
-    for (int l = 0; l < m; ++l) x += Bc[l * ld + r] * Jc[c * ld + l];
-    T2[c * ld + r] = x;
+    T[c * ld + r] = df_from_double(scalbn(Bc[c * ld + r], -ex));
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int c = e / m, r = e % m;
-    Bc[c * ld + r] = T2[c * ld + r];
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
+    int c = e / ld, r = e % ld;
+    float2 x = make_float2(0.f, 0.f);
+    if (c < m && r < m)
+      for (int l = 0; l < m; ++l) x = df_add(x, df_mul(T[l * ld + r], Jd[c * ld + l]));
+    Bd[e] = x;
   }
   __syncthreads();
-  jacobi_columns(Bc, Jc, m, ld, flag, nrm);
+  jacobi_df(Bd, Jd, m, ld, flag, T, 1e-13f, 3e-7f, 10);
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
+    int c = e / ld, r = e % ld;
+    if (c < m && r < m) {
+      Bc[e] = scalbn(df_to_double(Bd[e]), ex);
+      Jc[e] = df_to_double(Jd[e]);
+    }
+  }
+  __syncthreads();
 }
 
 }  // namespace dd

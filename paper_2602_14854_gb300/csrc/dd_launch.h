@@ -9,16 +9,16 @@ namespace dd {
 
 // Kernel classes timed by dd_dlra_profile (one slot per kernel function).
 enum KernelSlot {
-  KS_AUG_COLS = 0, KS_BUILD_L0, KS_ORTH, KS_ANG_COEFFS, KS_REDUCE, KS_SMALL_ADV1, KS_TALL,
+  KS_AUG_COLS = 0, KS_BUILD_L0, KS_GEIG_AUG, KS_ANG_COEFFS, KS_REDUCE, KS_SMALL_ADV1, KS_TALL,
   KS_GHOST, KS_KSTEP_ADV, KS_SP_COEFFS, KS_SSTEP_ADV, KS_LSTEP_ADV, KS_GRAM, KS_TRUNC,
   KS_COLL_RANK, KS_COLL_A, KS_COLL_KSTEP, KS_COLL_SMALL, KS_COLL_LSTEP, KS_COLL_FINAL,
-  KS_FLUX, KS_COPY, KS_CQR1, KS_CQR2, KS_ORTH_AUG, NSLOT
+  KS_FLUX, KS_COPY, KS_GEIG, KS_CHOL, KS_COMPLETE, NSLOT
 };
 extern const char* const kSlotNames[NSLOT];
 
 // Event-pair recorder around kernel launches (active only inside dd_dlra_profile).
 struct Prof {
-  static const int MAXL = 256;
+  static const int MAXL = 512;
   int n;
   cudaEvent_t b[MAXL], e[MAXL];
   int slot[MAXL];
@@ -43,7 +43,6 @@ struct OrthArgs {
   int mode;               // OrthMode
   const double* A; int lda;
   const int* acols;       // input columns per subdomain
-  double* W; int ldw;     // Householder workspace (same row layout as A)
   double* Q; int ldq;     // output basis
   const int* rout;        // output columns per subdomain (QR, COMPLETE)
   const int* r_own;       // AUG: current stored rank
@@ -56,12 +55,12 @@ struct OrthArgs {
 };
 
 cudaError_t orth_init();
-void launch_orth_fallback(const OrthArgs& a, int mcap, int maxrows, const int* flag,
-                          const double* sm_small, int sB, int sR2i, cudaStream_t st);
-void launch_cqr1(const OrthArgs& a, const double* sm, int sG, int sR, int sRi, double* smw,
-                 int* flag, double* scale, cudaStream_t st);
-void launch_cqr2(const OrthArgs& a, const double* sm, int sG2, int sR1, int sR1i, double* smw,
-                 int sM, int* flag, const double* scale, cudaStream_t st);
+// the per-subdomain steps of the orthonormalisation (dd_orth.cu)
+void launch_geig(const OrthArgs& a, const double* part, const int* cexp, int nchunk, double* sm,
+                 int sM, int* keep, cudaStream_t st);
+void launch_chol_inv(const OrthArgs& a, const double* part, int nchunk, double* sm, int sRi,
+                     const int* keep, cudaStream_t st);
+void launch_complete(const OrthArgs& a, const int* keep, cudaStream_t st);
 
 // Phase kernels (dd_phase.cu).  All buffers follow the layout described in
 // dd_internal.cuh; "small" matrices are RC x RC blocks, per subdomain stride RC*RC.
@@ -71,8 +70,8 @@ struct PhaseBufs {
   double* Xo; double* Vo; double* So; int* ro;
   // workspace
   double* L0;      // angular rows, ld MC
-  double* Hw;      // Householder workspace, spatial rows, ld MC
-  double* Hwa;     // Householder workspace, angular rows, ld MC
+  double* Hw;      // orthonormalisation workspace, spatial rows, ld WC
+  double* Hwa;     // orthonormalisation workspace, angular rows, ld WC
   double* Vh;      // angular rows, ld RC (augmented basis)
   double* K;       // spatial rows, ld RC
   double* X1;      // spatial rows, ld RC
@@ -87,8 +86,8 @@ struct PhaseBufs {
   int* rc;         // collision rank
   double* sig;     // diagnostics
   int* p;          // diagnostics
-  int* flag;       // per subdomain: 1 = the orthonormalisation needs the fallback
-  double* scale;   // per subdomain: Gram scaling of the fast path
+  int* keep;       // per subdomain: significant columns kept by the orthonormalisation
+  int* cexp;       // per subdomain and row chunk: power-of-two exponent of a scaled Gram
   unsigned* status;
 };
 
@@ -101,7 +100,7 @@ enum Small {
   SM_S2, SM_AP, SM_AM,                                             // S-step result, L-step matrices
   SM_S3T, SM_UB, SM_VB,                                            // S3^T, truncation rotations
   SM_MS, SM_MT, SM_VEC,                                            // collision: Ms, Mt, vectors (a, q, b-stages)
-  SM_G1, SM_R1, SM_R1I, SM_G2, SM_QM,                              // CholeskyQR2 fast path
+  SM_R1I, SM_QM,                                                   // orthonormalisation
   NSMALL
 };
 
@@ -116,7 +115,7 @@ struct Problem {
   int prec;               // 0 FP64 arithmetic throughout, 1 mixed (FP32 where allowed)
   int rank_mode; double tol; double tau; double accept;
   int r_floor, r_aug_max, RS;
-  int WC;                 // leading dimension of the Householder workspaces, max(MC, RC)
+  int WC;                 // leading dimension of the orthonormalisation workspaces
   const double* angcand; int n_angcand; int angcand_complete;
   int nchunk_sp, nchunk_ang;   // chunks of the two-stage reductions
 };
@@ -125,7 +124,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
 void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st);
 void scalar_flux(const Problem& P, const double* X, const double* V, const double* S, const int* r,
                  double* work, double* rho, int nx, cudaStream_t st);
-cudaError_t phase_init(const Problem& P);
+cudaError_t phase_init();   // kernel attributes for every capacity up to DD_MAXC
 size_t part_elems(const Problem& P);
 
 }  // namespace dd

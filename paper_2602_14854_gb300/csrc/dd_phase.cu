@@ -19,6 +19,8 @@
 //                              dL_q/dt = -(c Omega_q/h) [(T^T - I) L_q + G_hi Vh_q] (Omega_q < 0)
 //           (per-direction upwinding of f = U L^T with ghost f^b = K^b V^T, Eq. (advx_evolL)).
 #include "dd_internal.cuh"
+
+#include <climits>
 #include "dd_launch.h"
 
 namespace dd {
@@ -117,8 +119,8 @@ struct Dst { int idx[6]; };
 
 // Sum the chunk partials in fixed order into the small matrices.
 __global__ void k_reduce(const double* part, int nchunk, int nblk, Dst dst, double* sm, int RC) {
-  const int k = blockIdx.x;
-  for (int o = threadIdx.x; o < nblk * RC * RC; o += blockDim.x) {
+  const int k = blockIdx.y;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nblk * RC * RC; o += gridDim.x * blockDim.x) {
     const int b = o / (RC * RC), e = o % (RC * RC);
     double s = 0.0;
     for (int c = 0; c < nchunk; ++c) s += part[(((long)k * nchunk + c) * nblk + b) * RC * RC + e];
@@ -135,8 +137,10 @@ struct GramArgs {
   const double* Bm; int ldb; const int* bcnt; int bfix; int b_per_sub;  // b_per_sub: B has per-subdomain rows
   const double* wrow;   // row weights (indexed like a per-row vector of the same layout), or null
   double* part; int nchunk;
+  int* cexp;            // A^T A only (Bm == A): chunk exponents, see k_gram
 };
 __global__ void k_gram(Geo g, GramArgs a) {
+  __shared__ double red[40];
   const int k = blockIdx.y, c = blockIdx.x, RC = g.RC;
   const int rows = a.spatial ? g.N[k] : g.n;
   const long rb = a.spatial ? (long)g.rowoff[k] : (long)k * g.n;
@@ -145,14 +149,37 @@ __global__ void k_gram(Geo g, GramArgs a) {
   const int i0 = c * ch, i1 = min(rows, i0 + ch);
   const int na = a.acnt ? a.acnt[k] : a.afix, nbc = a.bcnt ? a.bcnt[k] : a.bfix;
   double* out = a.part + ((long)k * a.nchunk + c) * RC * RC;
+  // A^T A squares the entries: a chunk whose largest |entry| 2^e is far from 1
+  // (|e| > 400) is scaled by 2^-e first, so that tiny data keep their significant
+  // bits (e is stored; INT_MIN marks a chunk below 2^-1000, taken as zero)
+  int ex = 0;
+  bool scl = false, zero = false;
+  if (a.cexp) {
+    double mx = 0.0;
+    for (long e = threadIdx.x; e < (long)(i1 - i0) * na; e += blockDim.x)
+      mx = fmax(mx, fabs(a.A[(rb + i0 + e / na) * a.lda + e % na]));
+    mx = block_max(mx, red);
+    const int e0 = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) : 0;
+    zero = !(mx > 0.0) || e0 < -1000;
+    scl = !zero && (e0 < -400 || e0 > 400);
+    ex = scl ? e0 : 0;
+    if (threadIdx.x == 0) a.cexp[(long)k * a.nchunk + c] = zero ? INT_MIN : ex;
+  }
+  const double f = scl ? ldexp(1.0, -ex) : 1.0;
   for (int o = threadIdx.x; o < RC * RC; o += blockDim.x) {
     const int i = o / RC, j = o % RC;
     double s = 0.0;
-    if (i < na && j < nbc)
-      for (int row = i0; row < i1; ++row) {
-        double wv = a.wrow ? a.wrow[rb + row] : 1.0;
-        s += a.A[(rb + row) * a.lda + i] * wv * a.Bm[(rbB + row) * a.ldb + j];
+    if (i < na && j < nbc && !zero) {
+      if (scl) {
+        for (int row = i0; row < i1; ++row)
+          s += (a.A[(rb + row) * a.lda + i] * f) * (a.Bm[(rbB + row) * a.ldb + j] * f);
+      } else {
+        for (int row = i0; row < i1; ++row) {
+          double wv = a.wrow ? a.wrow[rb + row] : 1.0;
+          s += a.A[(rb + row) * a.lda + i] * wv * a.Bm[(rbB + row) * a.ldb + j];
+        }
       }
+    }
     out[o] = s;
   }
 }
@@ -161,8 +188,12 @@ __global__ void k_gram(Geo g, GramArgs a) {
 // small per-subdomain algebra: B = S M, B_lo = S_lo Min_lo, B_hi = S_hi Min_hi,
 // Jacobi eigendecomposition of C -> C+, C-, |C|  (Appendix A)
 // ---------------------------------------------------------------------------
-template <typename TC>
-__global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
+size_t small_adv1_smem(int RC) {
+  return sizeof(double) * (2 * RC * RC + RC) + 8 * ((jacobi_mixed_scratch_bytes(RC) + 7) / 8) +
+         sizeof(int) * 16;
+}
+
+__global__ void __launch_bounds__(DD_THREADS) k_small_adv1(Problem P, PhaseBufs B, int axis) {
   extern __shared__ double sh[];
   const int k = blockIdx.x, RC = P.g.RC;
   const int lo = P.g.nb[k * 4 + 2 * axis], hi = P.g.nb[k * 4 + 2 * axis + 1];
@@ -177,81 +208,44 @@ __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
   if (hi >= 0)
     bmm(SMB(B, P, k, SM_B_HI), RC, 1.0, B.S + (long)hi * RC * RC, RC, SMB(B, P, k, SM_MIN_HI), RC,
         rhi, rt, rhi, false);
-  // Jacobi eigendecomposition of the symmetric rt x rt matrix C (arithmetic TC)
-  TC* Cm = reinterpret_cast<TC*>(sh);   // RC*RC
-  TC* Pm = Cm + RC * RC;                // RC*RC (eigenvectors, row-major: Pm[i*RC + j] = P_ij)
-  TC* cs = Pm + RC * RC;                // RC/2 cosines
-  TC* sn = cs + RC;                     // RC/2 sines
-  const double* Csrc = SMB(B, P, k, SM_C);
-  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
-    int i = e / RC, j = e % RC;
-    Cm[e] = (TC)((i < rt && j < rt) ? 0.5 * (Csrc[i * RC + j] + Csrc[j * RC + i]) : 0.0);
-    Pm[e] = (i == j) ? (TC)1 : (TC)0;
-  }
-  __syncthreads();
-  const int mm = rt + (rt & 1);
+  // Eigendecomposition of the symmetric rt x rt matrix C: one-sided Jacobi of the
+  // positive semidefinite C + s I (s = |C|_F >= its spectral radius); the column
+  // norms of (C + s I) P are lambda + s.  FP32 sweeps and a double-float finish,
+  // accurate to ~1e-13 |C|, in both precisions: the upwind split feeds every stencil
+  // application, and FP32 errors here were the largest part of the mixed form's.
+  double* Bc = sh;                      // RC*RC column-major
+  double* Pm = Bc + RC * RC;            // RC*RC eigenvectors: column l = Pm[l*RC + i]
+  double* lam = Pm + RC * RC;           // RC
+  double* X = lam + RC;                 // SVD scratch
+  int* iv = reinterpret_cast<int*>(X + (jacobi_mixed_scratch_bytes(RC) + 7) / 8);
   __shared__ double red[40];
-  __shared__ int rotated;
+  const double* Csrc = SMB(B, P, k, SM_C);
   double nf = 0.0;
   for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
-    double x = (double)Cm[(e / rt) * RC + e % rt];
+    const int i = e / rt, j = e % rt;
+    const double x = 0.5 * (Csrc[i * RC + j] + Csrc[j * RC + i]);
     nf += x * x;
   }
-  // |C_pq| <= tol |C|_F counts as converged (1e-15 in FP64, 1e-7 in FP32)
-  const TC thr = (TC)((sizeof(TC) == 8 ? JACOBI_TOL : 1e-7) * sqrt(block_sum(nf, red)));
-  for (int sweep = 0; sweep < 40 && rt > 1; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
-    __syncthreads();
-    for (int rnd = 0; rnd < mm - 1; ++rnd) {
-      for (int pi = threadIdx.x; pi < mm / 2; pi += blockDim.x) {
-        int p, q;
-        rr_pair(mm, rnd, pi, &p, &q);
-        TC c = 1, s = 0;
-        if (p < rt && q < rt) {
-          TC apq = Cm[p * RC + q];
-          if (fabs(apq) > thr) {
-            TC zeta = (Cm[q * RC + q] - Cm[p * RC + p]) / (2 * apq);
-            TC t = (zeta >= 0 ? (TC)1 : (TC)-1) / (fabs(zeta) + sqrt((TC)1 + zeta * zeta));
-            c = rsqrt_t((TC)1 + t * t);
-            s = c * t;
-            rotated = 1;
-          }
-        }
-        cs[pi] = c; sn[pi] = s;
-      }
-      __syncthreads();
-      // columns: C <- C J, P <- P J
-      for (int e = threadIdx.x; e < rt * (mm / 2); e += blockDim.x) {
-        int row = e / (mm / 2), pi = e % (mm / 2);
-        int p, q;
-        rr_pair(mm, rnd, pi, &p, &q);
-        if (p >= rt || q >= rt) continue;
-        TC c = cs[pi], s = sn[pi];
-        TC x = Cm[row * RC + p], y = Cm[row * RC + q];
-        Cm[row * RC + p] = c * x - s * y;
-        Cm[row * RC + q] = s * x + c * y;
-        x = Pm[row * RC + p]; y = Pm[row * RC + q];
-        Pm[row * RC + p] = c * x - s * y;
-        Pm[row * RC + q] = s * x + c * y;
-      }
-      __syncthreads();
-      // rows: C <- J^T C
-      for (int e = threadIdx.x; e < rt * (mm / 2); e += blockDim.x) {
-        int col = e / (mm / 2), pi = e % (mm / 2);
-        int p, q;
-        rr_pair(mm, rnd, pi, &p, &q);
-        if (p >= rt || q >= rt) continue;
-        TC c = cs[pi], s = sn[pi];
-        TC x = Cm[p * RC + col], y = Cm[q * RC + col];
-        Cm[p * RC + col] = c * x - s * y;
-        Cm[q * RC + col] = s * x + c * y;
-      }
-      __syncthreads();
-    }
-    int f = rotated;
-    __syncthreads();
-    if (!f) break;
+  const double shift = sqrt(block_sum(nf, red));
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    const int col = e / RC, row = e % RC;
+    double x = 0.0;
+    if (row < rt && col < rt) x = 0.5 * (Csrc[row * RC + col] + Csrc[col * RC + row]) + (row == col ? shift : 0.0);
+    Bc[e] = x;
+    Pm[e] = (row == col) ? 1.0 : 0.0;
   }
+  __syncthreads();
+  jacobi_svd_mixed(Bc, Pm, rt, RC, &iv[0], lam, X);
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int j = warp; j < rt; j += nwarps) {
+      double s2 = 0.0;
+      for (int l = lane; l < rt; l += 32) s2 += Bc[j * RC + l] * Bc[j * RC + l];
+      s2 = warp_sum(s2);
+      if (lane == 0) lam[j] = sqrt(s2) - shift;
+    }
+  }
+  __syncthreads();
   // C+ = P diag(max(l,0)) P^T, C- = P diag(min(l,0)) P^T
   double* Cp = SMB(B, P, k, SM_CP);
   double* Cn = SMB(B, P, k, SM_CM);
@@ -261,10 +255,9 @@ __global__ void k_small_adv1(Problem P, PhaseBufs B, int axis) {
     double sp = 0.0, sm = 0.0;
     if (i < rt && j < rt)
       for (int l = 0; l < rt; ++l) {
-        double lam = (double)Cm[l * RC + l];
-        double pp = (double)Pm[i * RC + l] * (double)Pm[j * RC + l];
-        if (lam > 0.0) sp += lam * pp;
-        else if (lam < 0.0) sm += lam * pp;
+        const double pp = Pm[l * RC + i] * Pm[l * RC + j];
+        if (lam[l] > 0.0) sp += lam[l] * pp;
+        else if (lam[l] < 0.0) sm += lam[l] * pp;
       }
     Cp[e] = sp; Cn[e] = sm; Ca[e] = sp - sm;
   }
@@ -654,17 +647,15 @@ __global__ void k_trunc(Problem P, PhaseBufs B) {
     double s = 0.0;
     for (int l = lane; l < rt; l += 32) s += Bc[j * RC + l] * Bc[j * RC + l];
     s = warp_sum(s);
-    if (lane == 0) sig[j] = sqrt(s);
+    if (lane == 0) {
+      sig[j] = sqrt(s);
+      if (!isfinite(sig[j])) atomicOr(B.status, (unsigned)ST_NONFINITE);
+    }
   }
   __syncthreads();
+  rank_sort_desc(sig, rt, perm);
+  __syncthreads();
   if (threadIdx.x == 0) {
-    for (int t = 0; t < rt; ++t) perm[t] = t;
-    for (int t = 0; t < rt; ++t) {
-      int best = t;
-      for (int u = t + 1; u < rt; ++u)
-        if (sig[perm[u]] > sig[perm[best]]) best = u;
-      int tmp = perm[t]; perm[t] = perm[best]; perm[best] = tmp;
-    }
     int p = 0;
     double s1 = rt > 0 ? sig[perm[0]] : 0.0;
     if (s1 > 0.0)
@@ -1008,10 +999,10 @@ int kstep_lpb(const Problem& P, int len) {
 }  // namespace
 
 const char* const kSlotNames[NSLOT] = {
-    "k_aug_cols", "k_build_L0", "k_orth", "k_ang_coeffs", "k_reduce", "k_small_adv1", "k_tall",
+    "k_aug_cols", "k_build_L0", "k_geig(aug)", "k_ang_coeffs", "k_reduce", "k_small_adv1", "k_tall",
     "k_ghost", "k_kstep_adv", "k_sp_coeffs", "k_sstep_adv", "k_lstep_adv", "k_gram", "k_trunc",
     "k_coll_rank", "k_coll_a", "k_coll_kstep", "k_coll_small", "k_coll_lstep", "k_coll_final",
-    "k_flux", "memcpy", "k_cqr1", "k_cqr2", "k_orth(aug)"};
+    "k_flux", "memcpy", "k_geig", "k_chol_inv", "k_complete"};
 thread_local Prof* g_prof = nullptr;
 
 size_t part_elems(const Problem& P) {
@@ -1019,8 +1010,10 @@ size_t part_elems(const Problem& P) {
   return (size_t)P.g.nsub * nc * 6 * P.g.RC * P.g.RC;
 }
 
-cudaError_t phase_init(const Problem& P) {
-  const int RC = P.g.RC;
+// Kernel attributes are per process, not per solver: they are set for the largest
+// capacity (DD_MAXC) so that solvers of different widths can coexist.
+cudaError_t phase_init() {
+  const int RC = DD_MAXC;
   cudaError_t e;
   e = cudaFuncSetAttribute(k_kstep_adv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   if (e != cudaSuccess) return e;
@@ -1035,11 +1028,8 @@ cudaError_t phase_init(const Problem& P) {
   e = cudaFuncSetAttribute(k_lstep_adv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(lstep_smem(RC)));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_small_adv1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * (2 * RC * RC + 2 * RC) + 64));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_small_adv1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * (2 * RC * RC + 2 * RC) + 64));
+  e = cudaFuncSetAttribute(k_small_adv1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)small_adv1_smem(RC));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_trunc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trunc_smem(RC));
@@ -1061,6 +1051,11 @@ cudaError_t phase_init(const Problem& P) {
   return e;
 }
 
+// one thread per output element of the nblk small matrices of every subdomain
+static dim3 reduce_grid(const Geo& g, int nblk) {
+  return dim3((nblk * g.RC * g.RC + DD_THREADS - 1) / DD_THREADS, g.nsub);
+}
+
 static void gram(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spatial,
                  const double* A, int lda, const int* acnt, int afix, const double* Bm, int ldb,
                  const int* bcnt, int bfix, int b_per_sub, const double* wrow, int dst_small) {
@@ -1068,14 +1063,30 @@ static void gram(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spat
   a.spatial = spatial; a.A = A; a.lda = lda; a.acnt = acnt; a.afix = afix;
   a.Bm = Bm; a.ldb = ldb; a.bcnt = bcnt; a.bfix = bfix; a.b_per_sub = b_per_sub;
   a.wrow = wrow; a.part = B.part; a.nchunk = spatial ? P.nchunk_sp : P.nchunk_ang;
+  a.cexp = nullptr;
   pbeg(st, KS_GRAM);
   k_gram<<<dim3(a.nchunk, P.g.nsub), DD_THREADS, 0, st>>>(P.g, a);
   pend(st);
   Dst d;
   d.idx[0] = dst_small;
   pbeg(st, KS_REDUCE);
-  k_reduce<<<P.g.nsub, DD_THREADS, 0, st>>>(B.part, a.nchunk, 1, d, B.sm, P.g.RC);
+  k_reduce<<<reduce_grid(P.g, 1), DD_THREADS, 0, st>>>(B.part, a.nchunk, 1, d, B.sm, P.g.RC);
   pend(st);
+}
+
+// chunked Gram A^T A left as partial sums in B.part (summed by the consumer); returns
+// the number of chunks
+static int gram_partials(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spatial,
+                         const double* A, int lda, const int* acnt, int* cexp) {
+  GramArgs a;
+  a.spatial = spatial; a.A = A; a.lda = lda; a.acnt = acnt; a.afix = 0;
+  a.Bm = A; a.ldb = lda; a.bcnt = acnt; a.bfix = 0; a.b_per_sub = 1;
+  a.wrow = nullptr; a.part = B.part; a.nchunk = spatial ? P.nchunk_sp : P.nchunk_ang;
+  a.cexp = cexp;
+  pbeg(st, KS_GRAM);
+  k_gram<<<dim3(a.nchunk, P.g.nsub), DD_THREADS, 0, st>>>(P.g, a);
+  pend(st);
+  return a.nchunk;
 }
 
 static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spatial,
@@ -1099,24 +1110,22 @@ static OrthArgs orth_args(const Problem& P, const PhaseBufs& B, int spatial, int
   a.angcand = P.angcand; a.n_angcand = P.n_angcand; a.angcand_complete = P.angcand_complete;
   a.sig_out = B.sig; a.p_out = B.p; a.status = B.status;
   a.r_own = B.r; a.rt_out = B.rt;
-  a.W = spatial ? B.Hw : B.Hwa; a.ldw = P.WC;
   return a;
 }
 
-// CholeskyQR2 on all SMs, then the one-CTA fallback for the subdomains it flagged.
-static void orthonormalize(const Problem& P, const PhaseBufs& B, cudaStream_t st, OrthArgs a,
-                           int mcap) {
+// Orthonormal basis of the significant left singular span of A (per subdomain),
+// completed to the requested width: Gram, its eigendecomposition, U1 = A V S^-1,
+// one CholeskyQR pass on U1, completion (dd_orth.cu).
+static void orthonormalize(const Problem& P, const PhaseBufs& B, cudaStream_t st, OrthArgs a) {
   const int sp = a.spatial;
-  const int maxrows = sp ? P.maxN : P.g.n;
   double* W = sp ? B.Hw : B.Hwa;
-  gram(P, B, st, sp, a.A, a.lda, a.acols, 0, a.A, a.lda, a.acols, 0, 1, nullptr, SM_G1);
-  launch_cqr1(a, B.sm, SM_G1, SM_R1, SM_R1I, B.sm, B.flag, B.scale, st);
-  tall(P, B, st, sp, a.A, a.lda, a.acols, 0, nullptr, SM_R1I, a.acols, 0, W, P.WC);
-  gram(P, B, st, sp, W, P.WC, a.acols, 0, W, P.WC, a.acols, 0, 1, nullptr, SM_G2);
-  launch_cqr2(a, B.sm, SM_G2, SM_R1, SM_R1I, B.sm, SM_QM, B.flag, B.scale, st);
-  tall(P, B, st, sp, W, P.WC, a.acols, 0, nullptr, SM_QM,
-       a.mode == ORTH_AUG ? a.rt_out : a.rout, 0, a.Q, a.ldq);
-  launch_orth_fallback(a, mcap, maxrows, B.flag, B.sm, SM_G2, SM_R1I, st);
+  int nch = gram_partials(P, B, st, sp, a.A, a.lda, a.acols, B.cexp);
+  launch_geig(a, B.part, B.cexp, nch, B.sm, SM_QM, B.keep, st);
+  tall(P, B, st, sp, a.A, a.lda, a.acols, 0, nullptr, SM_QM, B.keep, 0, W, P.WC);
+  nch = gram_partials(P, B, st, sp, W, P.WC, B.keep, nullptr);
+  launch_chol_inv(a, B.part, nch, B.sm, SM_R1I, B.keep, st);
+  tall(P, B, st, sp, W, P.WC, B.keep, 0, nullptr, SM_R1I, B.keep, 0, a.Q, a.ldq);
+  launch_complete(a, B.keep, st);
 }
 
 void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st) {
@@ -1133,7 +1142,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_AUG);
     a.A = B.L0; a.lda = g.MC; a.acols = B.m; a.Q = B.Vh; a.ldq = RC; a.rout = nullptr;
-    orthonormalize(P, B, st, a, g.MC);
+    orthonormalize(P, B, st, a);
   }
   pbeg(st, KS_COPY);
   cudaMemcpyAsync(B.rx + axis * nsub, B.rt, sizeof(int) * nsub, cudaMemcpyDeviceToDevice, st);
@@ -1148,16 +1157,12 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
     d.idx[0] = SM_C; d.idx[1] = SM_MOUT_LO; d.idx[2] = SM_MOUT_HI;
     d.idx[3] = SM_M; d.idx[4] = SM_MIN_LO; d.idx[5] = SM_MIN_HI;
     pbeg(st, KS_REDUCE);
-    k_reduce<<<nsub, DD_THREADS, 0, st>>>(B.part, P.nchunk_ang, 6, d, B.sm, RC);
+    k_reduce<<<reduce_grid(g, 6), DD_THREADS, 0, st>>>(B.part, P.nchunk_ang, 6, d, B.sm, RC);
     pend(st);
   }
   // 3. S M products, eigen-split of C
   pbeg(st, KS_SMALL_ADV1);
-  if (P.prec == 1) {
-    k_small_adv1<float><<<nsub, DD_THREADS, sizeof(double) * (2 * RC * RC + 2 * RC) + 64, st>>>(P, B, axis);
-  } else {
-    k_small_adv1<double><<<nsub, DD_THREADS, sizeof(double) * (2 * RC * RC + 2 * RC) + 64, st>>>(P, B, axis);
-  }
+  k_small_adv1<<<nsub, DD_THREADS, small_adv1_smem(RC), st>>>(P, B, axis);
   pend(st);
   // 4. K^0 = X (S <V, Vh>)
   tall(P, B, st, 1, B.X, RC, B.r, 0, nullptr, SM_B, B.rt, 0, B.K, RC);
@@ -1182,7 +1187,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   {
     OrthArgs a = orth_args(P, B, 1, ORTH_QR);
     a.A = B.K; a.lda = RC; a.acols = B.rt; a.Q = B.X1; a.ldq = RC; a.rout = B.rt;
-    orthonormalize(P, B, st, a, RC);
+    orthonormalize(P, B, st, a);
   }
   // 8. S-step coefficients and S-step
   pbeg(st, KS_SP_COEFFS);
@@ -1192,7 +1197,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
     Dst d;
     d.idx[0] = SM_S1; d.idx[1] = SM_T; d.idx[2] = SM_G_LO; d.idx[3] = SM_G_HI;
     pbeg(st, KS_REDUCE);
-    k_reduce<<<nsub, DD_THREADS, 0, st>>>(B.part, P.nchunk_sp, 4, d, B.sm, RC);
+    k_reduce<<<reduce_grid(g, 4), DD_THREADS, 0, st>>>(B.part, P.nchunk_sp, 4, d, B.sm, RC);
     pend(st);
   }
   pbeg(st, KS_SSTEP_ADV);
@@ -1212,7 +1217,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_QR);
     a.A = B.L; a.lda = RC; a.acols = B.rt; a.Q = B.V1; a.ldq = RC; a.rout = B.rt;
-    orthonormalize(P, B, st, a, RC);
+    orthonormalize(P, B, st, a);
   }
   gram(P, B, st, 0, B.V1, RC, B.rt, 0, B.L, RC, B.rt, 0, 1, nullptr, SM_S3T);
   // 11. truncation (Algorithm 5)
@@ -1233,7 +1238,7 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_COMPLETE);
     a.A = B.V; a.lda = RC; a.acols = B.r; a.Q = B.Vh; a.ldq = RC; a.rout = B.rc;
-    launch_orth_fallback(a, RC, g.n, nullptr, B.sm, SM_G2, SM_R1I, st);
+    launch_complete(a, nullptr, st);
   }
   pbeg(st, KS_COLL_A);
   k_coll_a<<<nsub, DD_THREADS, 0, st>>>(P, B);
@@ -1249,7 +1254,7 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   {
     OrthArgs a = orth_args(P, B, 1, ORTH_QR);
     a.A = B.K; a.lda = RC; a.acols = B.rc; a.Q = B.Xo; a.ldq = RC; a.rout = B.rc;
-    orthonormalize(P, B, st, a, RC);
+    orthonormalize(P, B, st, a);
   }
   gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.K, RC, B.rc, 0, 1, nullptr, SM_S1);
   gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.Xo, RC, B.rc, 0, 1, P.sig_s, SM_MS);
@@ -1259,14 +1264,14 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
     GramArgs a;
     a.spatial = 1; a.A = B.Xo; a.lda = RC; a.acnt = B.rc; a.afix = 0;
     a.Bm = P.sQ; a.ldb = 1; a.bcnt = nullptr; a.bfix = 1; a.b_per_sub = 1;
-    a.wrow = nullptr; a.part = B.part; a.nchunk = P.nchunk_sp;
+    a.wrow = nullptr; a.part = B.part; a.nchunk = P.nchunk_sp; a.cexp = nullptr;
     pbeg(st, KS_GRAM);
     k_gram<<<dim3(a.nchunk, nsub), DD_THREADS, 0, st>>>(g, a);
     pend(st);
     Dst d;
     d.idx[0] = SM_UB;   // scratch: column 0 holds q
     pbeg(st, KS_REDUCE);
-    k_reduce<<<nsub, DD_THREADS, 0, st>>>(B.part, a.nchunk, 1, d, B.sm, RC);
+    k_reduce<<<reduce_grid(g, 1), DD_THREADS, 0, st>>>(B.part, a.nchunk, 1, d, B.sm, RC);
     pend(st);
   }
   pbeg(st, KS_COLL_SMALL);
@@ -1284,7 +1289,7 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_QR);
     a.A = B.L; a.lda = RC; a.acols = B.rc; a.Q = B.Vo; a.ldq = RC; a.rout = B.rc;
-    orthonormalize(P, B, st, a, RC);
+    orthonormalize(P, B, st, a);
   }
   gram(P, B, st, 0, B.Vo, RC, B.rc, 0, B.L, RC, B.rc, 0, 1, nullptr, SM_S3T);
   pbeg(st, KS_COLL_FINAL);

@@ -257,6 +257,18 @@ def random_small_problem(seed: int, nx=8, ny=8, tiles_x=2, tiles_y=2, n_mu=2, n_
     return wl
 
 
+def narrow_source_problem(seed: int = 13, nsteps: int = 3) -> Workload:
+    """A source of width 1.5 h centred on cell (2, 2) of a 64 x 64 grid in 4 x 4
+    subdomains (random heterogeneous materials, 32 directions, rank 4, RK4): the far
+    subdomains start with Gaussian tails of 1e-160 .. 1e-300."""
+    wl = random_small_problem(seed, nx=64, ny=64, tiles_x=4, tiles_y=4, n_mu=2, n_phi=16,
+                              rank=4, r_aug_max=8, integrator="rk4", nsteps=nsteps)
+    X, Y = _cell_centres(64, 64, 0.0, 1.0, 0.0, 1.0)
+    h = 1.0 / 64
+    g0 = np.exp(-((X - 2.5 * h) ** 2 + (Y - 2.5 * h) ** 2) / (2 * (1.5 * h) ** 2))
+    return wl.with_(name="narrow-source-64x64-4x4-n32-r4", g0=g0, source=np.zeros(64 * 64))
+
+
 def random_factors(seed: int, nrow: int, n: int, r: int, hx: float, hy: float, w: np.ndarray,
                    decay: float = 0.5):
     """Seeded random low-rank factors (U, S, V) with U orthonormal in the weighted

@@ -48,3 +48,20 @@ def test_batch_rejects_mismatched_options(B):
     b = a.with_(integrator="rk4")
     with pytest.raises(B.DDError):
         B.Solver([a, b])
+
+
+def test_solvers_of_different_width_coexist(B):
+    """Kernel attributes are per process: a wide solver (stored rank 12) created before a
+    narrow one (rank 2) must still step correctly after the narrow one exists."""
+    wide = inputs.random_small_problem(11, nx=16, ny=16, n_mu=4, n_phi=16, rank=12,
+                                       r_aug_max=24, integrator="rk4", nsteps=3)
+    narrow = inputs.random_small_problem(12, nx=8, ny=8, n_mu=2, n_phi=8, rank=2, r_aug_max=4,
+                                         integrator="rk4", nsteps=3)
+    sw = B.Solver(wide, use_graph=True)
+    sn = B.Solver(narrow, use_graph=True)
+    sn.step(3)
+    sw.step(3)
+    assert rel(sw.scalar_flux(), dd_dlra.DDDLRA(wide).run(3).scalar_flux()) < 1e-9
+    assert rel(sn.scalar_flux(), dd_dlra.DDDLRA(narrow).run(3).scalar_flux()) < 1e-9
+    sw.close()
+    sn.close()

@@ -1,8 +1,8 @@
 """Mixed-precision form (DD_MIXED) against the FP64 CPU oracle.
 
-FP32 arithmetic for the stencil, the increments of the K-/L-/collision-step ODEs and
-the eigen-split of C; FP64 for the updates, the orthonormalisations, the augmentation
-and truncation SVDs and reductions.
+FP32 arithmetic for the stencil and the increments of the K-/L-/collision-step ODEs;
+FP64 for the updates, the orthonormalisations, the small eigen/SVD problems and
+reductions.
 Target: scalar-flux rel-L2 <= 1e-5 against the oracle (FP32 target of the task
 statement), on the same workloads as the FP64 parity tests.
 """

@@ -172,9 +172,9 @@ def test_pointsource_full_size(B):
     s.close()
 
 
-def test_tall_subdomain_global_memory_qr(B):
-    """48x96-cell subdomains: the staged K of the Householder fallback (4608 rows) no
-    longer fits in shared memory, so the QR runs on the global-memory copy."""
+def test_tall_subdomain(B):
+    """48x96-cell subdomains (4608 rows per spatial basis, many row chunks per Gram
+    and per tall product)."""
     wl = inputs.random_small_problem(8, nx=96, ny=96, tiles_x=2, tiles_y=1, n_mu=2, n_phi=8,
                                      rank=3, r_aug_max=6, integrator="rk4", nsteps=3)
     s, o = run_both(B, wl)
@@ -183,12 +183,25 @@ def test_tall_subdomain_global_memory_qr(B):
     s.close()
 
 
-def test_many_directions_global_memory_augmentation(B):
-    """2048 directions at rank 7: the staged augmentation input (2048 x 21) and the
-    L factor exceed shared memory, so both run on the global-memory copy."""
+def test_many_directions(B):
+    """2048 directions at rank 7 (augmentation input 2048 x 21)."""
     wl = inputs.random_small_problem(9, nx=8, ny=8, n_mu=16, n_phi=128, rank=7, r_aug_max=14,
                                      integrator="rk4", nsteps=3)
     s, o = run_both(B, wl)
     assert list(s.ranks()[0]) == o.ranks()
     assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+
+
+def test_far_field_of_a_narrow_source(B):
+    """Tiny far-field data must not break the orthonormalisation (scaled Grams).  This
+    problem is ill-conditioned: 1e-15 relative noise in the initial data moves the
+    oracle's own result by ~6e-6 (pinned in the oracle conditioning tests), so the
+    bound is that sensitivity, not the 1e-9 parity bound."""
+    wl = inputs.narrow_source_problem()
+    s, o = run_both(B, wl)
+    rho = s.scalar_flux()
+    assert np.all(np.isfinite(rho))
+    assert list(s.ranks()[0]) == o.ranks()
+    assert rel(rho, o.scalar_flux()) < 1e-5
     s.close()
