@@ -125,7 +125,9 @@ def fp64_gemm_peak(torch):
 
 def kernel_work(name, wl, rt, rs):
     """Algorithmic FP64 flops of one launch of a kernel class on this workload
-    (rt: intermediate rank, rs: stored rank; uniform subdomains)."""
+    (rt: intermediate rank, rs: stored rank; uniform subdomains).  The symmetric
+    eigendecompositions count 9 m^3 per m x m problem (the textbook cost of a
+    tridiagonal-QR eigensolver with vectors), whatever the method that runs."""
     nsub = wl.nsub
     N = wl.ncells // nsub
     n = wl.n
@@ -134,7 +136,17 @@ def kernel_work(name, wl, rt, rs):
         return nsub * N * 3 * 2 * rt * rt * st
     if name == "k_lstep_adv":      # (r_t x r_t) matvec per direction per stage + S2 v
         return nsub * n * (2 * rt * rt * st + 4 * rt * rt)
+    if name == "k_geig":           # 4 advection QRs (m = r_t) and 2 collision QRs (m = r)
+        return nsub * 9 * (4 * rt ** 3 + 2 * rs ** 3) / 6.0
+    if name == "k_geig(aug)":      # augmentation input of 3 r columns
+        return nsub * 9 * (3 * rs) ** 3
     return None
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
+# capture summarised in profiles/k_geig_k_kstep_adv_pointsource_full.md; None where no
+# capture of the kernel as it stands exists.
+NCU_TRAFFIC = {"k_geig": 0.277e6, "k_kstep_adv": 3.88e6}
 
 
 def run_ours(args, torch):
@@ -221,20 +233,24 @@ def run_ours(args, torch):
     name, (ms, cnt) = top
     work = kernel_work(name, wl, rt, rs)
     roof = {"kernel": name, "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak,
-            "peak_source": "cuBLAS FP64 GEMM 8192^3 measured in this run",
-            "share_of_step": ms / total, "launch_ms": ms / cnt, "traffic": None}
+            "peak_source": "cuBLAS FP64 GEMM 8192^3 measured in this run (of measured)",
+            "share_of_step": ms / total, "launch_ms": ms / cnt,
+            "traffic": NCU_TRAFFIC.get(name)}
     if work is not None:
         ach = work / (ms / cnt / 1e3) / 1e12
         roof.update({"achieved": ach, "frac": ach / fp64_peak, "work_flops_per_launch": work})
     else:
-        roof.update({"achieved": None, "frac": None,
-                     "note": "latency-bound one-CTA-per-subdomain kernel; no FLOP roofline"})
+        roof.update({"achieved": None, "frac": None})
+    if name.startswith("k_geig"):
+        roof["note"] = ("one CTA per subdomain (16 of 152 SMs) running Jacobi sweeps: bound by "
+                        "barrier latency (ncu: 10% issue-active, barrier the top stall)")
     kstep = prof.get("k_kstep_adv")
     if kstep:
         w = kernel_work("k_kstep_adv", wl, rt, rs)
         roof["k_kstep_adv"] = {"launch_ms": kstep[0] / kstep[1],
                                "achieved_tflops": w / (kstep[0] / kstep[1] / 1e3) / 1e12,
-                               "frac": w / (kstep[0] / kstep[1] / 1e3) / 1e12 / fp64_peak}
+                               "frac": w / (kstep[0] / kstep[1] / 1e3) / 1e12 / fp64_peak,
+                               "traffic": NCU_TRAFFIC.get("k_kstep_adv")}
     roof["kernels_ms_per_step"] = {k: round(v[0] / 4.0, 4) for k, v in
                                    sorted(prof.items(), key=lambda kv: -kv[1][0])}
     roof["launches_per_step"] = {k: v[1] / 4.0 for k, v in prof.items()}
