@@ -214,7 +214,7 @@ __device__ __forceinline__ float2 df_shfl(unsigned mask, float2 v, int src) {
 // are recomputed at the start of every sweep and updated in between (a rotation
 // with tangent t annihilating gamma = b_p . b_q maps them to alpha - t gamma and
 // beta + t gamma).  The rotation is computed by the first lane of the half-warp.
-// Block-wide; flag is two ints of shared scratch, nrm holds m values of shared scratch.
+// Block-wide; nrm holds m values of shared scratch (flag is unused).
 // ---------------------------------------------------------------------------
 #define JAC_PER 4   // entries per lane: m <= 16 * JAC_PER
 
@@ -229,15 +229,19 @@ __device__ __forceinline__ float2 half_sum_df(float2 v, unsigned hm) {
   return v;
 }
 
-// FP32 sweeps.  Besides the convergence test, a sweep whose largest relative
-// off-diagonal |b_p . b_q| / (|b_p| |b_q|) was below stop ends the iteration: in the
-// quadratic regime it leaves them at ~stop^2.
+// FP32 sweeps.  Every lane of the half-warp computes the rotation itself (no
+// broadcasts) with the fast reciprocal / reciprocal-square-root units: any exactly
+// orthogonal rotation that reduces b_p . b_q will do, and c = (1 + t^2)^-1/2, s = c t
+// is orthogonal to FP32 rounding whatever t is.  Each thread keeps the largest
+// relative off-diagonal |b_p . b_q| / (|b_p| |b_q|) it saw; the sweep ends the
+// iteration when the block-wide largest is <= tol (nothing was rotated) or below stop
+// (in the quadratic regime that leaves them at ~stop^2).
 __device__ __forceinline__ void jacobi_f32(float* Bc, float* Jc, int m, int ld, int* flag,
                                            float* nrm, float tol, float stop, int max_sweeps) {
+  (void)flag;
   const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
   const int slot0 = (threadIdx.x >> 5) * 2 + half, nslot = (blockDim.x >> 5) * 2;
   const unsigned hm = half ? 0xffff0000u : 0x0000ffffu;
-  const int src = half * 16;
   const int mm = m + (m & 1);
   __shared__ double jred[40];
   double nf = 0.0;
@@ -257,8 +261,8 @@ __device__ __forceinline__ void jacobi_f32(float* Bc, float* Jc, int m, int ld, 
       s2 = half_sum(s2, hm);
       if (hl == 0) nrm[j] = s2;
     }
-    if (threadIdx.x == 0) { flag[0] = 0; flag[1] = 0; }
     __syncthreads();
+    float lmax = 0.f;
     for (int r = 0; r < mm - 1; ++r) {
       for (int pi = slot0; pi < mm / 2; pi += nslot) {
         int p, q;
@@ -266,6 +270,7 @@ __device__ __forceinline__ void jacobi_f32(float* Bc, float* Jc, int m, int ld, 
         if (p >= m || q >= m) continue;
         float* bp = Bc + p * ld;
         float* bq = Bc + q * ld;
+        const float al = nrm[p], be = nrm[q];      // read before this half-warp writes them
         float ga = 0.f;
 #pragma unroll
         for (int i = 0; i < JAC_PER; ++i) {
@@ -273,29 +278,25 @@ __device__ __forceinline__ void jacobi_f32(float* Bc, float* Jc, int m, int ld, 
           if (l < m) ga = __fmaf_rn(bp[l], bq[l], ga);
         }
         ga = half_sum(ga, hm);
-        float c = 1.f, s = 0.f;
-        int rot = 0;
-        if (hl == 0) {
-          const float al = nrm[p], be = nrm[q];
-          const float den = sqrtf(al * be);
-          if (fabsf(ga) > abs_thr && den > 0.f) atomicMax(flag + 1, __float_as_int(fabsf(ga) / den));
-          if (fabsf(ga) > abs_thr && fabsf(ga) > tol * den) {
-            const float zeta = (be - al) / (2.f * ga);
-            float t;
-            if (fabsf(zeta) > 1e8f) t = 0.5f / zeta;
-            else t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-            c = rsqrtf(1.f + t * t);
-            s = c * t;
-            nrm[p] = al - t * ga;
-            nrm[q] = be + t * ga;
-            *flag = 1;
-            rot = 1;
-          }
+        const float pr = al * be;
+        if (!(fabsf(ga) > abs_thr) || !(pr > 0.f)) continue;
+        const float rel = fabsf(ga) * rsqrtf(pr);
+        lmax = fmaxf(lmax, rel);
+        if (!(rel > tol)) continue;
+        const float zeta = __fdividef(be - al, 2.f * ga);
+        float t;
+        if (fabsf(zeta) > 1e8f) {
+          t = __fdividef(0.5f, zeta);
+        } else {
+          const float w = 1.f + zeta * zeta;
+          t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + w * rsqrtf(w));
         }
-        rot = __shfl_sync(hm, rot, src);
-        if (!rot) continue;
-        c = __shfl_sync(hm, c, src);
-        s = __shfl_sync(hm, s, src);
+        const float c = rsqrtf(1.f + t * t), s = c * t;
+        __syncwarp(hm);                              // every lane has read al, be
+        if (hl == 0) {
+          nrm[p] = al - t * ga;
+          nrm[q] = be + t * ga;
+        }
         float* jp = Jc + p * ld;
         float* jq = Jc + q * ld;
 #pragma unroll
@@ -311,10 +312,8 @@ __device__ __forceinline__ void jacobi_f32(float* Bc, float* Jc, int m, int ld, 
       }
       __syncthreads();
     }
-    const int f = flag[0];
-    const float mrel = __int_as_float(flag[1]);
-    __syncthreads();
-    if (f == 0 || mrel < stop) break;
+    const float mrel = (float)block_max((double)lmax, jred);
+    if (mrel <= tol || mrel < stop) break;
   }
 }
 
@@ -323,10 +322,10 @@ __device__ __forceinline__ void jacobi_f32(float* Bc, float* Jc, int m, int ld, 
 // every rotation is orthogonal to double-float rounding)
 __device__ __forceinline__ void jacobi_df(float2* Bd, float2* Jd, int m, int ld, int* flag,
                                           float2* nrm, float tol, float stop, int max_sweeps) {
+  (void)flag;
   const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
   const int slot0 = (threadIdx.x >> 5) * 2 + half, nslot = (blockDim.x >> 5) * 2;
   const unsigned hm = half ? 0xffff0000u : 0x0000ffffu;
-  const int src = half * 16;
   const int mm = m + (m & 1);
   __shared__ double jred[40];
   double nf = 0.0;
@@ -346,8 +345,8 @@ __device__ __forceinline__ void jacobi_df(float2* Bd, float2* Jd, int m, int ld,
       s2 = half_sum_df(s2, hm);
       if (hl == 0) nrm[j] = s2;
     }
-    if (threadIdx.x == 0) { flag[0] = 0; flag[1] = 0; }
     __syncthreads();
+    float lmax = 0.f;
     for (int r = 0; r < mm - 1; ++r) {
       for (int pi = slot0; pi < mm / 2; pi += nslot) {
         int p, q;
@@ -355,6 +354,7 @@ __device__ __forceinline__ void jacobi_df(float2* Bd, float2* Jd, int m, int ld,
         if (p >= m || q >= m) continue;
         float2* bp = Bd + p * ld;
         float2* bq = Bd + q * ld;
+        const float2 al = nrm[p], be = nrm[q];     // read before this half-warp writes them
         float2 ga = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < JAC_PER; ++i) {
@@ -362,34 +362,31 @@ __device__ __forceinline__ void jacobi_df(float2* Bd, float2* Jd, int m, int ld,
           if (l < m) ga = df_add(ga, df_mul(bp[l], bq[l]));
         }
         ga = half_sum_df(ga, hm);
-        float2 c = make_float2(1.f, 0.f), s = make_float2(0.f, 0.f);
-        int rot = 0;
-        if (hl == 0) {
-          const float2 al = nrm[p], be = nrm[q];
-          const float den = sqrtf(al.x * be.x);
-          if (fabsf(ga.x) > abs_thr && den > 0.f) atomicMax(flag + 1, __float_as_int(fabsf(ga.x) / den));
-          if (fabsf(ga.x) > abs_thr && fabsf(ga.x) > tol * den) {
-            const float zeta = df_add(be, df_neg(al)).x / (2.f * ga.x);
-            float t;
-            if (fabsf(zeta) > 1e8f) t = 0.5f / zeta;
-            else t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-            // w = 1 + t^2 exactly enough; c = w^-1/2 by one Newton step from rsqrtf
-            const float2 w = df_add(make_float2(1.f, 0.f), df_mulf(make_float2(t, 0.f), t));
-            const float y0 = rsqrtf(w.x);
-            const float2 h = df_add(make_float2(1.f, 0.f), df_neg(df_mulf(df_mulf(w, y0), y0)));
-            c = df_add(make_float2(y0, 0.f), df_mulf(h, 0.5f * y0));
-            s = df_mulf(c, t);
-            const float2 tg = df_mulf(ga, t);
-            nrm[p] = df_add(al, df_neg(tg));
-            nrm[q] = df_add(be, tg);
-            *flag = 1;
-            rot = 1;
-          }
+        const float pr = al.x * be.x;
+        if (!(fabsf(ga.x) > abs_thr) || !(pr > 0.f)) continue;
+        const float rel = fabsf(ga.x) * rsqrtf(pr);
+        lmax = fmaxf(lmax, rel);
+        if (!(rel > tol)) continue;
+        const float zeta = __fdividef(df_add(be, df_neg(al)).x, 2.f * ga.x);
+        float t;
+        if (fabsf(zeta) > 1e8f) {
+          t = __fdividef(0.5f, zeta);
+        } else {
+          const float w = 1.f + zeta * zeta;
+          t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + w * rsqrtf(w));
         }
-        rot = __shfl_sync(hm, rot, src);
-        if (!rot) continue;
-        c = df_shfl(hm, c, src);
-        s = df_shfl(hm, s, src);
+        // w = 1 + t^2 exactly enough; c = w^-1/2 by one Newton step from rsqrtf
+        const float2 w = df_add(make_float2(1.f, 0.f), df_mulf(make_float2(t, 0.f), t));
+        const float y0 = rsqrtf(w.x);
+        const float2 h = df_add(make_float2(1.f, 0.f), df_neg(df_mulf(df_mulf(w, y0), y0)));
+        const float2 c = df_add(make_float2(y0, 0.f), df_mulf(h, 0.5f * y0));
+        const float2 s = df_mulf(c, t);
+        __syncwarp(hm);                              // every lane has read al, be
+        if (hl == 0) {
+          const float2 tg = df_mulf(ga, t);
+          nrm[p] = df_add(al, df_neg(tg));
+          nrm[q] = df_add(be, tg);
+        }
         const float2 ns = df_neg(s);
         float2* jp = Jd + p * ld;
         float2* jq = Jd + q * ld;
@@ -408,10 +405,8 @@ __device__ __forceinline__ void jacobi_df(float2* Bd, float2* Jd, int m, int ld,
       }
       __syncthreads();
     }
-    const int f = flag[0];
-    const float mrel = __int_as_float(flag[1]);
-    __syncthreads();
-    if (f == 0 || mrel < stop) break;
+    const float mrel = (float)block_max((double)lmax, jred);
+    if (mrel <= tol || mrel < stop) break;
   }
 }
 

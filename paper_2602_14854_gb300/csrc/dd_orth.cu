@@ -21,8 +21,9 @@
 //                                   give the rank decision; M = V_keep diag(sigma)^-1
 //   U1 = A M                        k_tall: the leading left singular vectors, up to
 //                                   errors of order eps |A|^2 / sigma_j^2
-//   G2 = U1^T U1 = R2^T R2          k_gram + k_chol_inv (double-float Cholesky, R2^-1)
-//   Q  = U1 R2^-1                   k_tall: orthonormal to ~1e-14
+//   G2 = U1^T U1                    k_gram + k_chol_inv (G2^-1/2 by Newton-Schulz in
+//                                   double-float)
+//   Q  = U1 G2^-1/2                 k_tall: orthonormal to ~1e-14
 //   completion                      k_complete (subdomains with keep < r_out)
 // The span of Q is that of the leading left singular vectors of A.  The
 // eigenvector error eps |G1| / gap enters the result weighted by the discarded
@@ -104,18 +105,20 @@ __global__ void __launch_bounds__(DD_THREADS) k_geig(OrthArgs a, const double* p
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   // the chunk partials are Grams of 2^-e_c A: G1 of 2^-emax A is their sum with
   // weights 4^(e_c - emax)
+  __shared__ double fac[64];
   int emax = INT_MIN;
   for (int c = 0; c < nchunk; ++c) emax = max(emax, cexp[(long)k * nchunk + c]);
+  for (int c = tid; c < nchunk; c += blockDim.x) {
+    const int ec = cexp[(long)k * nchunk + c];
+    fac[c] = ec == INT_MIN ? 0.0 : ldexp(1.0, 2 * max(ec - emax, -600));
+  }
+  __syncthreads();
   bool fin = true;
   for (int e = tid; e < RC * RC; e += blockDim.x) {
     const int col = e / RC, row = e % RC;
     double x = 0.0;
     if (col < m && row < m && emax != INT_MIN)
-      for (int c = 0; c < nchunk; ++c) {
-        const int ec = cexp[(long)k * nchunk + c];
-        if (ec != INT_MIN)
-          x += G[(long)c * RC * RC + row * RC + col] * ldexp(1.0, 2 * max(ec - emax, -600));
-      }
+      for (int c = 0; c < nchunk; ++c) x += G[(long)c * RC * RC + row * RC + col] * fac[c];
     if (!isfinite(x)) { fin = false; x = 0.0; }
     Bc[e] = x;
     Jc[e] = (row == col) ? 1.0 : 0.0;
@@ -158,13 +161,17 @@ __global__ void __launch_bounds__(DD_THREADS) k_geig(OrthArgs a, const double* p
   }
 }
 
-size_t chol_smem_bytes(int RC) { return sizeof(float2) * 3 * RC * RC; }
+size_t chol_smem_bytes(int RC) { return sizeof(float2) * 5 * RC * RC; }
 
-// R2 = chol(G2) (q x q, q = keep) and R2^-1 (into slot sRi) in double-float.  G2,
-// summed here from its nchunk partial Grams, is the Gram of A V diag(sigma)^-1 and
-// close to the identity, so the factorisation is well conditioned; double-float
-// keeps Q = U1 R2^-1 orthonormal to ~1e-14.  A failed factorisation (only possible
-// through non-finite data) is reported and leaves the identity.
+// Z = G2^-1/2 (q x q, q = keep) into slot sRi, so that Q = U1 Z is orthonormal.  G2,
+// summed here from its nchunk partial Grams, is the Gram of U1 = A V diag(sigma)^-1,
+// the identity up to E = G2 - I (|E| <~ 1e-3, set by the eigensolver's accuracy
+// relative to the smallest kept sigma^2).  Coupled Newton-Schulz iteration in
+// double-float (Y <- Y T, Z <- T Z, T = (3I - Z Y)/2; Y -> G2^1/2, Z -> G2^-1/2, the
+// error e maps to ~3/4 e^2), iterated until the predicted error is below 1e-16: a few
+// parallel matrix products instead of a sequential factorisation.  |E|_F >= 0.9 (not
+// expected; only through non-finite or inconsistent data) is reported and leaves the
+// identity.
 __global__ void __launch_bounds__(DD_THREADS) k_chol_inv(OrthArgs a, const double* part,
                                                          int nchunk, double* sm, int sRi,
                                                          const int* keep) {
@@ -173,57 +180,56 @@ __global__ void __launch_bounds__(DD_THREADS) k_chol_inv(OrthArgs a, const doubl
   const int q = keep[k];
   const double* G = part + (long)k * nchunk * RC * RC;
   double* Ri = sm + ((long)k * NSMALL + sRi) * RC * RC;
-  float2* Gd = shc;
-  float2* Rd = Gd + RC * RC;
-  float2* Rid = Rd + RC * RC;
-  __shared__ int ok;
-  for (int e = tid; e < RC * RC; e += blockDim.x) {
+  float2* Y = shc;
+  float2* Z = Y + RC * RC;
+  float2* T = Z + RC * RC;
+  float2* W1 = T + RC * RC;
+  float2* W2 = W1 + RC * RC;
+  __shared__ double red[40];
+  double e2 = 0.0;
+  for (int e = tid; e < q * q; e += blockDim.x) {
+    const int i = e / q, j = e % q;
     double x = 0.0;
-    if (e / RC < q && e % RC < q)
-      for (int c = 0; c < nchunk; ++c) x += G[(long)c * RC * RC + e];
-    Gd[e] = df_from_double(x);
-    Rd[e] = make_float2(0.f, 0.f);
-    Rid[e] = make_float2(0.f, 0.f);
+    for (int c = 0; c < nchunk; ++c) x += G[(long)c * RC * RC + i * RC + j];
+    const double d = x - (i == j ? 1.0 : 0.0);
+    e2 += d * d;
+    Y[i * RC + j] = df_from_double(x);
+    Z[i * RC + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
   }
-  __shared__ float2 piv;
-  if (tid == 0) ok = 1;
-  __syncthreads();
-  // right-looking Cholesky, the whole CTA on each trailing update
-  for (int j = 0; j < q; ++j) {
-    if (tid == 0) {
-      const float2 d = Gd[j * RC + j];
-      if (!(d.x > 0.f) || !isfinite(d.x)) ok = 0;
-      else piv = df_sqrt(d);
-    }
-    __syncthreads();
-    if (!ok) break;
-    const float2 r = piv;
-    for (int c = j + tid; c < q; c += blockDim.x) Rd[j * RC + c] = (c == j) ? r : df_div(Gd[j * RC + c], r);
-    __syncthreads();
-    const int nt = q - j - 1;
-    for (int e = tid; e < nt * nt; e += blockDim.x) {
-      const int rr = j + 1 + e / nt, c = j + 1 + e % nt;
-      if (rr <= c) Gd[rr * RC + c] = df_add(Gd[rr * RC + c], df_neg(df_mul(Rd[j * RC + rr], Rd[j * RC + c])));
-    }
-    __syncthreads();
-  }
+  const double err = sqrt(block_sum(e2, red));
+  const bool ok = isfinite(err) && err < 0.9;
+  int iters = 0;
+  for (double e = err; e > 1e-16 && iters < 12; e = 0.75 * e * e) ++iters;
   if (ok) {
-    // R^-1 by rows from the bottom: row i of R^-1 needs the rows below it
-    for (int i = q - 1; i >= 0; --i) {
-      const float2 rii = Rd[i * RC + i];
-      for (int c = i + tid; c < q; c += blockDim.x) {
-        float2 x = make_float2(i == c ? 1.f : 0.f, 0.f);
-        for (int l = i + 1; l <= c; ++l) x = df_add(x, df_neg(df_mul(Rd[i * RC + l], Rid[l * RC + c])));
-        Rid[i * RC + c] = df_div(x, rii);
+    for (int it = 0; it < iters; ++it) {
+      for (int e = tid; e < q * q; e += blockDim.x) {          // T = (3I - Z Y) / 2
+        const int i = e / q, j = e % q;
+        float2 x = make_float2(0.f, 0.f);
+        for (int l = 0; l < q; ++l) x = df_add(x, df_mul(Z[i * RC + l], Y[l * RC + j]));
+        T[i * RC + j] = df_mulf(df_add(make_float2(i == j ? 3.f : 0.f, 0.f), df_neg(x)), 0.5f);
       }
       __syncthreads();
+      for (int e = tid; e < q * q; e += blockDim.x) {          // W1 = Y T, W2 = T Z
+        const int i = e / q, j = e % q;
+        float2 x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
+        for (int l = 0; l < q; ++l) {
+          x = df_add(x, df_mul(Y[i * RC + l], T[l * RC + j]));
+          y = df_add(y, df_mul(T[i * RC + l], Z[l * RC + j]));
+        }
+        W1[i * RC + j] = x;
+        W2[i * RC + j] = y;
+      }
+      __syncthreads();
+      float2* tmp = Y; Y = W1; W1 = tmp;
+      tmp = Z; Z = W2; W2 = tmp;
     }
   }
-  __syncthreads();
-  if (!ok && tid == 0) atomicOr(a.status, (unsigned)ST_NONFINITE);
+  if (!ok && tid == 0 && q > 0) atomicOr(a.status, (unsigned)ST_NONFINITE);
   for (int e = tid; e < RC * RC; e += blockDim.x) {
     const int i = e / RC, c = e % RC;
-    Ri[e] = ok ? df_to_double(Rid[e]) : ((i == c && i < q) ? 1.0 : 0.0);
+    double v = 0.0;
+    if (i < q && c < q) v = ok ? df_to_double(Z[i * RC + c]) : (i == c ? 1.0 : 0.0);
+    Ri[e] = v;
   }
 }
 
