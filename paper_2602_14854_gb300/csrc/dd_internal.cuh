@@ -127,15 +127,15 @@ __device__ __forceinline__ void rank_sort_desc(const double* v, int n, int* perm
 }
 
 // Round-robin (circle method) pairing for parallel Jacobi sweeps over mm
-// (even) indices: round r in [0, mm-1), pair i in [0, mm/2).
+// (even) indices: round r in [0, mm-1), pair i in [0, mm/2).  Both sums are below
+// 2 (mm - 1), so each reduction modulo mm - 1 is one compare-and-subtract.
 __device__ __forceinline__ void rr_pair(int mm, int r, int i, int* p, int* q) {
-  int a0 = (mm > 1) ? 1 + (r % (mm - 1)) : 0;
-  if (i == 0) { *p = 0; *q = a0; }
-  else {
-    int ai = 1 + ((i + r) % (mm - 1));
-    int aj = 1 + ((mm - 1 - i + r) % (mm - 1));
-    *p = ai; *q = aj;
-  }
+  const int M = mm - 1;
+  if (i == 0) { *p = 0; *q = (mm > 1) ? 1 + r : 0; return; }
+  int a = i + r, b = M - i + r;
+  a = a >= M ? a - M : a;
+  b = b >= M ? b - M : b;
+  *p = 1 + a; *q = 1 + b;
 }
 
 #define JACOBI_TOL 1e-15
