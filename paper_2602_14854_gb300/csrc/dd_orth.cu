@@ -79,14 +79,20 @@ __device__ int decide(const OrthArgs& a, int k, const double* sig, int nref, int
 }
 
 size_t geig_smem_bytes(int RC) {
-  return sizeof(double) * (2 * RC * RC + 2 * RC) + 8 * ((jacobi_mixed_scratch_bytes(RC) + 7) / 8) +
+  return sizeof(double) * (3 * RC * RC + 2 * RC) + 8 * ((jacobi_mixed_scratch_bytes(RC) + 7) / 8) +
          sizeof(int) * (RC + 16);
 }
 
-// Eigendecomposition of G1 (m x m, slot sG) by one-sided Jacobi: the columns of
-// G1 V are orthogonal with norms lambda_j (G1 is positive semidefinite), V holds
-// the eigenvectors.  Writes M = V_keep diag(sigma_keep)^-1 (row-major, slot sM),
-// keep (per subdomain) and, for the augmentation, r_t.
+// Eigendecomposition of G1 (m x m): one-sided Jacobi (FP32 sweeps, double-float
+// finish; the columns of G1 V are orthogonal with norms lambda_j, G1 being positive
+// semidefinite), then one FP64 refinement step of the eigenvectors (Ogita and
+// Aishima, 2018): with R = I - V^T V, S = V^T G1 V, lambda_i = s_ii / (1 - r_ii),
+// V <- V (I + E), e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for
+// separated pairs, r_ij / 2 within clusters and on the diagonal.  The double-float
+// solution is accurate to ~1e-14 |G1|; the step brings it to the FP64 level, which the
+// parity with an FP64 SVD needs for eigenvectors whose eigenvalues sit near the rank
+// threshold (tau^2 lambda_1).  Writes M = V_keep diag(sigma_keep)^-1 (row-major,
+// slot sM), keep (per subdomain) and, for the augmentation, r_t.
 __global__ void __launch_bounds__(DD_THREADS) k_geig(OrthArgs a, const double* part,
                                                      const int* cexp, int nchunk, double* sm,
                                                      int sM, int* keep_out) {
@@ -97,7 +103,8 @@ __global__ void __launch_bounds__(DD_THREADS) k_geig(OrthArgs a, const double* p
   double* M = sm + ((long)k * NSMALL + sM) * RC * RC;
   double* Bc = shg;                 // column-major working copy
   double* Jc = Bc + RC * RC;        // accumulated rotations
-  double* lam = Jc + RC * RC;       // eigenvalues
+  double* Gs = Jc + RC * RC;        // G1 (scaled), kept for the refinement
+  double* lam = Gs + RC * RC;       // eigenvalues
   double* sig = lam + RC;           // singular values of A, descending
   double* X = sig + RC;             // scratch of the SVD
   int* perm = reinterpret_cast<int*>(X + (jacobi_mixed_scratch_bytes(RC) + 7) / 8);
@@ -121,20 +128,72 @@ __global__ void __launch_bounds__(DD_THREADS) k_geig(OrthArgs a, const double* p
       for (int c = 0; c < nchunk; ++c) x += G[(long)c * RC * RC + row * RC + col] * fac[c];
     if (!isfinite(x)) { fin = false; x = 0.0; }
     Bc[e] = x;
+    Gs[e] = x;
     Jc[e] = (row == col) ? 1.0 : 0.0;
   }
   if (emax == INT_MIN) emax = 0;
   if (!fin) atomicOr(a.status, (unsigned)ST_NONFINITE);
   __syncthreads();
   jacobi_svd_mixed(Bc, Jc, m, RC, &iv[0], lam, X);
-  for (int j = warp; j < m; j += nwarps) {
-    double s = 0.0;
-    for (int l = lane; l < m; l += 32) s += Bc[j * RC + l] * Bc[j * RC + l];
-    s = warp_sum(s);
-    if (lane == 0) {
-      lam[j] = sqrt(s);
-      if (!isfinite(lam[j])) atomicOr(a.status, (unsigned)ST_NONFINITE);
+  // FP64 refinement (V is Jc: V_ij = Jc[j * RC + i]); T, S, R, E in the SVD scratch
+  double* T = X;
+  double* S = T + RC * RC;
+  double* R = S + RC * RC;
+  __shared__ double rred[40];
+  for (int e = tid; e < m * m; e += blockDim.x) {            // T = G1 V
+    const int i = e / m, j = e % m;
+    double x = 0.0;
+    for (int l = 0; l < m; ++l) x += Gs[i * RC + l] * Jc[j * RC + l];
+    T[i * RC + j] = x;
+  }
+  __syncthreads();
+  double offn = 0.0, rn = 0.0, gn = 0.0;
+  for (int e = tid; e < m * m; e += blockDim.x) {            // S = V^T T, R = I - V^T V
+    const int i = e / m, j = e % m;
+    double x = 0.0, y = 0.0;
+    for (int l = 0; l < m; ++l) {
+      x += Jc[i * RC + l] * T[l * RC + j];
+      y += Jc[i * RC + l] * Jc[j * RC + l];
     }
+    S[i * RC + j] = x;
+    R[i * RC + j] = (i == j ? 1.0 : 0.0) - y;
+    if (i != j) offn += x * x;
+    rn += R[i * RC + j] * R[i * RC + j];
+    gn += Gs[i * RC + j] * Gs[i * RC + j];
+  }
+  offn = block_sum(offn, rred);
+  rn = block_sum(rn, rred);
+  gn = block_sum(gn, rred);
+  const double delta = 2.0 * (sqrt(offn) + sqrt(gn) * sqrt(rn));   // cluster separation
+  for (int i = tid; i < m; i += blockDim.x) lam[i] = S[i * RC + i] / (1.0 - R[i * RC + i]);
+  __syncthreads();
+  for (int e = tid; e < m * m; e += blockDim.x) {            // E (into T)
+    const int i = e / m, j = e % m;
+    double x;
+    if (i == j) {
+      x = 0.5 * R[i * RC + i];
+    } else {
+      const double d = lam[j] - lam[i];
+      x = fabs(d) > delta ? (S[i * RC + j] + lam[j] * R[i * RC + j]) / d : 0.5 * R[i * RC + j];
+    }
+    T[i * RC + j] = x;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += blockDim.x) {            // V (I + E) into Bc
+    const int i = e / m, j = e % m;
+    double x = Jc[j * RC + i];
+    for (int l = 0; l < m; ++l) x += Jc[l * RC + i] * T[l * RC + j];
+    Bc[j * RC + i] = x;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    Jc[j * RC + i] = Bc[j * RC + i];
+  }
+  for (int j = tid; j < m; j += blockDim.x) {
+    const double l = lam[j];
+    if (!isfinite(l)) atomicOr(a.status, (unsigned)ST_NONFINITE);
+    lam[j] = l > 0.0 ? l : 0.0;       // G1 is positive semidefinite
   }
   __syncthreads();
   rank_sort_desc(lam, m, perm);

@@ -175,7 +175,7 @@ __global__ void k_gram(Geo g, GramArgs a) {
           s += (a.A[(rb + row) * a.lda + i] * f) * (a.Bm[(rbB + row) * a.ldb + j] * f);
       } else {
         for (int row = i0; row < i1; ++row) {
-          double wv = a.wrow ? a.wrow[rb + row] : 1.0;
+          const double wv = a.wrow ? a.wrow[rb + row] : 1.0;
           s += a.A[(rb + row) * a.lda + i] * wv * a.Bm[(rbB + row) * a.ldb + j];
         }
       }
@@ -426,9 +426,10 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
 __global__ void k_sp_coeffs(Problem P, PhaseBufs B, int axis) {
   const int k = blockIdx.y, c = blockIdx.x, RC = P.g.RC, nchunk = P.nchunk_sp;
   const Lines L = lines_of(P.g, k, axis);
-  const int N = P.g.N[k];
-  const int ch = (N + nchunk - 1) / nchunk;
-  const int c0 = c * ch, c1 = min(N, c0 + ch);
+  // chunks of whole lines: every cell's shift partner and the two face cells of a
+  // line are in the same chunk, and no index is divided inside the loops
+  const int lch = (L.nlines + nchunk - 1) / nchunk;
+  const int l0 = c * lch, l1 = min(L.nlines, l0 + lch);
   const int rt = B.rt[k];
   const double* X1 = B.X1 + (long)P.g.rowoff[k] * RC;
   const double* K = B.K + (long)P.g.rowoff[k] * RC;
@@ -438,15 +439,22 @@ __global__ void k_sp_coeffs(Problem P, PhaseBufs B, int axis) {
     const int blk = o / (RC * RC), e = o % (RC * RC), i = e / RC, j = e % RC;
     double s = 0.0;
     if (i < rt && j < rt) {
-      for (int cell = c0; cell < c1; ++cell) {
-        int line, pos;
-        if (axis == 0) { line = cell / L.len; pos = cell % L.len; }
-        else { pos = cell / L.nlines; line = cell % L.nlines; }
-        const double xi = X1[(long)cell * RC + i];
-        if (blk == 0) s += xi * K[(long)cell * RC + j];
-        else if (blk == 1) { if (pos > 0) s += xi * X1[(long)(cell - L.stride_pos) * RC + j]; }
-        else if (blk == 2) { if (pos == 0) s += xi * Kb[(long)line * RC + j]; }
-        else { if (pos == L.len - 1) s += xi * Kb[((long)P.maxlines + line) * RC + j]; }
+      if (blk == 0) {
+        for (int line = l0; line < l1; ++line)
+          for (int pos = 0, cell = line * L.stride_line; pos < L.len; ++pos, cell += L.stride_pos)
+            s += X1[(long)cell * RC + i] * K[(long)cell * RC + j];
+      } else if (blk == 1) {
+        for (int line = l0; line < l1; ++line)
+          for (int pos = 1, cell = line * L.stride_line + L.stride_pos; pos < L.len;
+               ++pos, cell += L.stride_pos)
+            s += X1[(long)cell * RC + i] * X1[(long)(cell - L.stride_pos) * RC + j];
+      } else if (blk == 2) {
+        for (int line = l0; line < l1; ++line)
+          s += X1[(long)(line * L.stride_line) * RC + i] * Kb[(long)line * RC + j];
+      } else {
+        for (int line = l0; line < l1; ++line)
+          s += X1[(long)(line * L.stride_line + (L.len - 1) * L.stride_pos) * RC + i] *
+               Kb[((long)P.maxlines + line) * RC + j];
       }
     }
     out[o] = s;
