@@ -451,6 +451,13 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   P.r_floor = h->r_floor; P.r_aug_max = raug_max; P.RS = h->RS; P.WC = WC;
   P.angcand = h->d_angcand; P.n_angcand = h->n_angcand; P.angcand_complete = h->angcand_complete;
   P.nchunk_sp = std::max(1, std::min(16, h->maxN / 64));
+  {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+        nsm <= 0)
+      nsm = 1;
+    P.nsm = nsm;
+  }
   P.nchunk_ang = std::max(1, std::min(16, n / 64));
   if (dalloc(&h->d_part, dd::part_elems(P)) != cudaSuccess)
     return bail(DD_ERR_CUDA, "device allocation failed");

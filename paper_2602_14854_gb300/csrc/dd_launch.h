@@ -118,6 +118,7 @@ struct Problem {
   int WC;                 // leading dimension of the orthonormalisation workspaces
   const double* angcand; int n_angcand; int angcand_complete;
   int nchunk_sp, nchunk_ang;   // chunks of the two-stage reductions
+  int nsm;                     // streaming multiprocessors of the device
 };
 
 void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st);

@@ -997,10 +997,14 @@ size_t kstep_smem(const Problem& P, int lpb, int len) {
 }
 
 int kstep_lpb(const Problem& P, int len) {
-  // lines per CTA: bounded by the register tile (KS_EPT per thread) and shared memory
+  // lines per CTA: bounded by the register tile (KS_EPT per thread) and shared memory,
+  // and small enough that the grid covers every SM about twice (the kernel is bound
+  // by the FP64 pipe of the SMs it occupies)
   const int RC = P.g.RC;
   int lpb = max(1, (DD_THREADS * KS_EPT) / (len * RC));
   while (lpb > 1 && kstep_smem(P, lpb, len) > 200 * 1024) --lpb;
+  const long lines = (long)P.maxlines * P.g.nsub;
+  while (lpb > 1 && (lines + lpb - 1) / lpb < 2L * P.nsm) --lpb;
   return lpb;
 }
 
