@@ -98,6 +98,10 @@ typedef struct dd_options {
   double dt;          /* time step                                                        */
   double tau;         /* relative numerical-rank threshold (sigma_j <= tau*sigma_1 -> 0)  */
   int precision;      /* DD_FP64 or DD_MIXED                                              */
+  int mass_fix;       /* 1: conserved-moment correction at the end of every step (not part */
+                      /* of the paper's scheme): the scalar-flux change of the S-, L-steps  */
+                      /* and truncations of the step is added back as the isotropic        */
+                      /* rank-one term delta(x) (x) 1/|S|, then Algorithm 5 truncates; 0: off */
 } dd_options;
 
 typedef struct dd_dlra* dd_dlra_t;

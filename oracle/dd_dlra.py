@@ -20,6 +20,8 @@ Factors are kept in the paper's form f = U S V^T with U orthonormal in
 primitives used as single steps: numpy SVD, symmetric eigendecomposition and
 matrix products.  No blocking, fusion or reordering beyond the paper's steps.
 
+Optional, not part of the paper's scheme: the conserved-moment correction (R18 below).
+
 Readings where the paper is silent or ambiguous (each also listed in the design doc):
   R1  general quadrature: scattering is sigma_s/|S| * sum_q w_q f_q, |S| = sum_q w_q.
   R2  inflow masks are the paper's inclusive ones: at the low side of an axis a
@@ -68,6 +70,14 @@ Readings where the paper is silent or ambiguous (each also listed in the design doc):
 
 Pins: tests/test_oracle_dd_dlra.py (full-rank identities, closed forms,
 invariances, brute force on tiny grids).
+  R18 conserved-moment correction (off unless the workload asks for it): the
+      K-steps move the scalar flux rho = sum_q w_q f_q conservatively, the S- and
+      L-steps and the truncation do not.  Over a step, delta = sum over its three
+      phases of [rho(K^1 V^T) - rho(end of the phase)] is the mass the
+      non-conservative parts changed; at the end of the step the isotropic
+      rank-one term delta(x) (x) 1/|S| is added to f and the result truncated by
+      Algorithm 5's rule.  Without truncation loss the step's rho is then the one
+      of the conservative K-step chain.
 """
 from __future__ import annotations
 
@@ -463,7 +473,8 @@ class DDDLRA:
         V1, pL = orthonormal_basis(L1, self.sw_phi, r_t, angular_candidates(wl),
                                    self.tau, self.accept)
         S3 = self._ip_phi(V1, L1).T
-        return U1, S3, V1, dict(pK=pK, pL=pL)
+        rho_k = K1 @ (Vhat.T @ self.w)                       # mass of the K-step (R18)
+        return U1, S3, V1, dict(pK=pK, pL=pL, rho_k=rho_k)
 
     # -- Algorithm 5 ------------------------------------------------------------
     def truncate(self, U, S, V):
@@ -527,7 +538,8 @@ class DDDLRA:
         V1, pL = orthonormal_basis(L1, self.sw_phi, r_c, angular_candidates(wl), self.tau,
                                    self.accept)
         S3 = self._ip_phi(V1, L1).T
-        return U1, S3, V1, dict(r_c=r_c, pK=pK, pL=pL)
+        rho_k = K1 @ a                                       # mass of the K-step (R18)
+        return U1, S3, V1, dict(r_c=r_c, pK=pK, pL=pL, rho_k=rho_k)
 
     # -- Algorithm 6 ------------------------------------------------------------
     def advection_phase(self, axis):
@@ -540,6 +552,7 @@ class DDDLRA:
             U1, S3, V1, ip = self.psi_advection(k, axis, K0, Vhat, Kb_lo, Kb_hi)
             Ut, St, Vt = self.truncate(U1, S3, V1)
             new.append((Ut, St, Vt))
+            ip["dmass"] = ip.pop("rho_k") - self._mass(Ut, St, Vt, k)
             info.append(dict(ia, **ip, r=St.shape[0]))
         self.state = new
         return info
@@ -551,14 +564,42 @@ class DDDLRA:
             U, S, V = self.state[k]
             U1, S3, V1, ic = self.psi_collision(k, U, S, V)
             new.append((U1, S3, V1))
+            ic["dmass"] = ic.pop("rho_k") - self._mass(U1, S3, V1, k)
             info.append(ic)
         self.state = new
         return info
+
+    def _mass(self, U, S, V, k):
+        """Per-cell scalar flux of one subdomain's factors."""
+        if S.shape[0] == 0:
+            return np.zeros(self.subs[k].N)
+        return U @ (S @ (V.T @ self.w))
+
+    def mass_correction(self, deltas):
+        """R18: add delta (x) 1/|S| to f on every subdomain and truncate (Algorithm 5's
+        rule).  The augmented factors are orthonormalised by weighted QR."""
+        new = []
+        for k, ((U, S, V), d) in enumerate(zip(self.state, deltas)):
+            if not np.any(d):
+                new.append((U, S, V))
+                continue
+            Ua = np.concatenate([U, d[:, None]], axis=1)
+            Va = np.concatenate([V, np.full((self.wl.n, 1), 1.0 / self.ssum)], axis=1)
+            Sa = np.zeros((S.shape[0] + 1, S.shape[0] + 1))
+            Sa[:S.shape[0], :S.shape[0]] = S
+            Sa[-1, -1] = 1.0
+            Qu, Ru = np.linalg.qr(self.sw_x * Ua)
+            Qv, Rv = np.linalg.qr(self.sw_phi[:, None] * Va)
+            new.append(self.truncate(Qu / self.sw_x, Ru @ Sa @ Rv.T, Qv / self.sw_phi[:, None]))
+        self.state = new
 
     def step(self):
         ix = self.advection_phase("x")
         iy = self.advection_phase("y")
         ic = self.collision_phase()
+        if self.wl.mass_fix:
+            self.mass_correction([a["dmass"] + b["dmass"] + c["dmass"]
+                                  for a, b, c in zip(ix, iy, ic)])
         self.log.append(dict(x=ix, y=iy, c=ic))
 
     def run(self, nsteps=None):

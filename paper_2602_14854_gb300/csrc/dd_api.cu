@@ -86,6 +86,7 @@ struct dd_dlra {
   double *d_L0, *d_Hw, *d_Hwa, *d_Vh, *d_K, *d_X1, *d_L, *d_V1, *d_Kb, *d_sm, *d_part;
   double *d_sig, *d_rho, *d_fluxw;
   int *d_m, *d_rt, *d_rx, *d_rc, *d_p, *d_keep, *d_cexp;
+  double *d_dm, *d_mvec;
   unsigned* d_status;
   dd::Problem P;
 };
@@ -100,7 +101,7 @@ dd::PhaseBufs bufs(dd_dlra* h, int in, int out) {
   B.X1 = h->d_X1; B.L = h->d_L; B.V1 = h->d_V1; B.Kb = h->d_Kb; B.sm = h->d_sm;
   B.part = h->d_part; B.m = h->d_m; B.rt = h->d_rt; B.rx = h->d_rx; B.rc = h->d_rc;
   B.sig = h->d_sig; B.p = h->d_p; B.status = h->d_status;
-  B.keep = h->d_keep; B.cexp = h->d_cexp;
+  B.keep = h->d_keep; B.cexp = h->d_cexp; B.dm = h->d_dm; B.mvec = h->d_mvec;
   return B;
 }
 
@@ -110,6 +111,17 @@ void enqueue_step(dd_dlra* h) {
   dd::advection_phase(h->P, bufs(h, 0, 1), 0, h->stream);
   dd::advection_phase(h->P, bufs(h, 1, 0), 1, h->stream);
   dd::collision_phase(h->P, bufs(h, 0, 0), h->stream);
+  if (h->P.mass_fix) {
+    // correction state 0 -> 1, then back to 0 (the state between steps)
+    dd::mass_fix_phase(h->P, bufs(h, 0, 1), h->stream);
+    const long Nt = h->Ntot, RC = h->RC;
+    cudaMemcpyAsync(h->d_X[0], h->d_X[1], sizeof(double) * Nt * RC, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(h->d_V[0], h->d_V[1], sizeof(double) * (long)h->nsub * h->n * RC,
+                    cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(h->d_S[0], h->d_S[1], sizeof(double) * (long)h->nsub * RC * RC,
+                    cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(h->d_r[0], h->d_r[1], sizeof(int) * h->nsub, cudaMemcpyDeviceToDevice, h->stream);
+  }
 }
 
 dd_status check_status(dd_dlra* h) {
@@ -168,7 +180,7 @@ void free_all(dd_dlra* h) {
                   h->d_S[1], h->d_r[0], h->d_r[1], h->d_L0, h->d_Hw, h->d_Hwa, h->d_Vh,
                   h->d_K, h->d_X1, h->d_L, h->d_V1, h->d_Kb, h->d_sm, h->d_part, h->d_sig,
                   h->d_rho, h->d_fluxw, h->d_m, h->d_rt, h->d_rx, h->d_rc, h->d_p, h->d_status,
-                  h->d_keep, h->d_cexp, h->d_rlo, h->d_rhi, h->d_raug, h->d_fbase,
+                  h->d_keep, h->d_cexp, h->d_dm, h->d_mvec, h->d_rlo, h->d_rhi, h->d_raug, h->d_fbase,
                   h->d_fnx, h->d_hxk, h->d_hyk, h->d_dtk, h->d_shk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -223,6 +235,7 @@ static dd_status check_instance(const dd_grid* grid, const dd_tiling* tiling,
     return fail(DD_ERR_ARG, "integrator");
   if (opt->precision != DD_FP64 && opt->precision != DD_MIXED)
     return fail(DD_ERR_ARG, "precision");
+  if (opt->mass_fix != 0 && opt->mass_fix != 1) return fail(DD_ERR_ARG, "mass_fix");
   if (!(opt->dt > 0.0) || !(opt->tau >= 0.0)) return fail(DD_ERR_ARG, "dt / tau");
   const int RS = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_max;
   const int fl = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_min;
@@ -254,9 +267,9 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     const dd_options& a = opts[0];
     const dd_options& b = opts[i];
     if (b.rank_mode != a.rank_mode || b.integrator != a.integrator || b.precision != a.precision ||
-        b.c_adv != a.c_adv || b.tau != a.tau || b.tol != a.tol)
+        b.c_adv != a.c_adv || b.tau != a.tau || b.tol != a.tol || b.mass_fix != a.mass_fix)
       return fail(DD_ERR_ARG, "instances of a batch must share rank mode, tolerance, integrator, "
-                              "precision, c_adv and tau");
+                              "precision, mass_fix, c_adv and tau");
   }
   const dd_options* opt = &opts[0];
 
@@ -430,6 +443,8 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   ok &= dalloc(&h->d_p, nsub) == cudaSuccess;
   ok &= dalloc(&h->d_keep, nsub) == cudaSuccess;
   ok &= dalloc(&h->d_cexp, (long)nsub * 16) == cudaSuccess;
+  ok &= dalloc(&h->d_dm, Nt) == cudaSuccess;
+  ok &= dalloc(&h->d_mvec, (long)nsub * RC) == cudaSuccess;
   ok &= dalloc(&h->d_status, 1) == cudaSuccess;
   if (!ok) return bail(DD_ERR_CUDA, "device allocation failed");
 
@@ -447,6 +462,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   P.hx = h->hx; P.hy = h->hy; P.sh = h->sh; P.dt = opt->dt; P.c_adv = opt->c_adv; P.ssum = h->ssum;
   P.integrator = opt->integrator; P.rank_mode = opt->rank_mode; P.tol = opt->tol;
   P.prec = opt->precision == DD_MIXED ? 1 : 0;
+  P.mass_fix = opt->mass_fix;
   P.tau = opt->tau; P.accept = 0.5;
   P.r_floor = h->r_floor; P.r_aug_max = raug_max; P.RS = h->RS; P.WC = WC;
   P.angcand = h->d_angcand; P.n_angcand = h->n_angcand; P.angcand_complete = h->angcand_complete;
@@ -494,7 +510,8 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     }
     if (cudaMemset(h->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(h->d_sm, 0, sizeof(double) * (size_t)nsub * dd::NSMALL * RC * RC) != cudaSuccess ||
-        cudaMemset(h->d_rx, 0, sizeof(int) * 2 * nsub) != cudaSuccess)
+        cudaMemset(h->d_rx, 0, sizeof(int) * 2 * nsub) != cudaSuccess ||
+        cudaMemset(h->d_dm, 0, sizeof(double) * (size_t)Nt) != cudaSuccess)
       return bail(DD_ERR_CUDA, "clear workspace");
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(DD_ERR_CUDA, "create: device error");

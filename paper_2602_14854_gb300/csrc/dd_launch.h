@@ -12,7 +12,7 @@ enum KernelSlot {
   KS_AUG_COLS = 0, KS_BUILD_L0, KS_GEIG_AUG, KS_ANG_COEFFS, KS_REDUCE, KS_SMALL_ADV1, KS_TALL,
   KS_GHOST, KS_KSTEP_ADV, KS_SP_COEFFS, KS_SSTEP_ADV, KS_LSTEP_ADV, KS_GRAM, KS_TRUNC,
   KS_COLL_RANK, KS_COLL_A, KS_COLL_KSTEP, KS_COLL_SMALL, KS_COLL_LSTEP, KS_COLL_FINAL,
-  KS_FLUX, KS_COPY, KS_GEIG, KS_CHOL, KS_COMPLETE, NSLOT
+  KS_FLUX, KS_COPY, KS_GEIG, KS_CHOL, KS_COMPLETE, KS_MASS, NSLOT
 };
 extern const char* const kSlotNames[NSLOT];
 
@@ -88,6 +88,8 @@ struct PhaseBufs {
   int* p;          // diagnostics
   int* keep;       // per subdomain: significant columns kept by the orthonormalisation
   int* cexp;       // per subdomain and row chunk: power-of-two exponent of a scaled Gram
+  double* dm;      // per cell: scalar-flux change of the non-conservative parts (mass fix)
+  double* mvec;    // per subdomain: RC-vector scratch of the mass bookkeeping
   unsigned* status;
 };
 
@@ -113,6 +115,7 @@ struct Problem {
   double hx, hy, sh, dt, c_adv, ssum;
   int integrator;         // 0 Euler, 1 RK4
   int prec;               // 0 FP64 arithmetic throughout, 1 mixed (FP32 where allowed)
+  int mass_fix;           // conserved-moment correction at the end of every step
   int rank_mode; double tol; double tau; double accept;
   int r_floor, r_aug_max, RS;
   int WC;                 // leading dimension of the orthonormalisation workspaces
@@ -123,6 +126,7 @@ struct Problem {
 
 void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st);
 void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st);
+void mass_fix_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st);
 void scalar_flux(const Problem& P, const double* X, const double* V, const double* S, const int* r,
                  double* work, double* rho, int nx, cudaStream_t st);
 cudaError_t phase_init();   // kernel attributes for every capacity up to DD_MAXC

@@ -705,6 +705,85 @@ __global__ void k_trunc(Problem P, PhaseBufs B) {
 }
 
 // ---------------------------------------------------------------------------
+// conserved-moment correction (optional; not part of the paper's scheme)
+// ---------------------------------------------------------------------------
+// mvec[k] = S (V^T sqrt(w)) over the first cnt[k] columns (S null: the identity):
+// with it, the scalar flux of X S V^T (or of K V^T) is X mvec / sqrt(hx hy).
+__global__ void k_mf_vec(Problem P, const double* V, const double* S, const int* cnt,
+                         double* mvec) {
+  __shared__ double a[DD_MAXC];
+  const int k = blockIdx.x, RC = P.g.RC, n = P.g.n, c = cnt[k];
+  const double* Vk = V + (long)k * n * RC;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = warp; t < RC; t += nw) {
+    double x = 0.0;
+    if (t < c)
+      for (int q = lane; q < n; q += 32) x += Vk[(long)q * RC + t] * P.sw[q];
+    x = warp_sum(x);
+    if (lane == 0) a[t] = x;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < RC; i += blockDim.x) {
+    double x = 0.0;
+    if (i < c) {
+      if (S) {
+        const double* Sk = S + (long)k * RC * RC;
+        for (int t = 0; t < c; ++t) x += Sk[i * RC + t] * a[t];
+      } else {
+        x = a[i];
+      }
+    }
+    mvec[(long)k * RC + i] = x;
+  }
+}
+
+// dm[cell] += sign * (A[cell, :cnt] . mvec[k]) / sqrt(hx hy)
+__global__ void k_mf_acc(Problem P, const double* A, const int* cnt, const double* mvec,
+                         double sign, double* dm) {
+  const int k = blockIdx.y, RC = P.g.RC, N = P.g.N[k], c = cnt[k];
+  const long rb = P.g.rowoff[k];
+  const double* v = mvec + (long)k * RC;
+  const double f = sign / P.g.shk[k];
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < N; row += gridDim.x * blockDim.x) {
+    double x = 0.0;
+    for (int t = 0; t < c; ++t) x += A[(rb + row) * RC + t] * v[t];
+    dm[rb + row] += f * x;
+  }
+}
+
+// K_a = [X S | sqrt(hx hy) dm] (the isotropic term's spatial factor), then dm = 0
+__global__ void k_mf_build_x(Problem P, const double* X, const double* S, const int* r,
+                             double* dm, double* Ka) {
+  const int k = blockIdx.y, RC = P.g.RC, N = P.g.N[k], rk = r[k];
+  const long rb = P.g.rowoff[k];
+  const double* Sk = S + (long)k * RC * RC;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < N; row += gridDim.x * blockDim.x) {
+    const double* Xr = X + (rb + row) * RC;
+    double* Kr = Ka + (rb + row) * RC;
+    for (int t = 0; t < RC; ++t) {
+      double x = 0.0;
+      if (t < rk) {
+        for (int u = 0; u < rk; ++u) x += Xr[u] * Sk[u * RC + t];
+      } else if (t == rk) {
+        x = P.g.shk[k] * dm[rb + row];
+      }
+      Kr[t] = x;
+    }
+    dm[rb + row] = 0.0;
+  }
+}
+
+// V_a = [V | sqrt(w) / |S|] (the isotropic term's angular factor), m = r + 1
+__global__ void k_mf_build_v(Problem P, const double* V, const int* r, double* Va, int* m) {
+  const int k = blockIdx.y, RC = P.g.RC, n = P.g.n, rk = r[k];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+    for (int t = 0; t < RC; ++t)
+      Va[((long)k * n + q) * RC + t] =
+          t < rk ? V[((long)k * n + q) * RC + t] : (t == rk ? P.sw[q] / P.ssum : 0.0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) m[k] = rk + 1;
+}
+
+// ---------------------------------------------------------------------------
 // collision (Algorithm 3)
 // ---------------------------------------------------------------------------
 __global__ void k_coll_rank(Problem P, const int* r, int* rc) {
@@ -1014,7 +1093,7 @@ const char* const kSlotNames[NSLOT] = {
     "k_aug_cols", "k_build_L0", "k_geig(aug)", "k_ang_coeffs", "k_reduce", "k_small_adv1", "k_tall",
     "k_ghost", "k_kstep_adv", "k_sp_coeffs", "k_sstep_adv", "k_lstep_adv", "k_gram", "k_trunc",
     "k_coll_rank", "k_coll_a", "k_coll_kstep", "k_coll_small", "k_coll_lstep", "k_coll_final",
-    "k_flux", "memcpy", "k_geig", "k_chol_inv", "k_complete"};
+    "k_flux", "memcpy", "k_geig", "k_chol_inv", "k_complete", "k_mass_fix"};
 thread_local Prof* g_prof = nullptr;
 
 size_t part_elems(const Problem& P) {
@@ -1114,6 +1193,17 @@ static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spat
   pend(st);
 }
 
+// dm += sign * scalar flux of A (spatial, cnt columns) in the angular basis V (with
+// core S when given); the conserved-moment correction's bookkeeping
+static void mass_acc(const Problem& P, const PhaseBufs& B, cudaStream_t st, const double* A,
+                     const double* V, const double* S, const int* cnt, double sign) {
+  pbeg(st, KS_MASS);
+  k_mf_vec<<<P.g.nsub, DD_THREADS, 0, st>>>(P, V, S, cnt, B.mvec);
+  k_mf_acc<<<dim3((P.maxN + DD_THREADS - 1) / DD_THREADS, P.g.nsub), DD_THREADS, 0, st>>>(
+      P, A, cnt, B.mvec, sign, B.dm);
+  pend(st);
+}
+
 static OrthArgs orth_args(const Problem& P, const PhaseBufs& B, int spatial, int mode) {
   OrthArgs a;
   a.g = P.g; a.spatial = spatial; a.mode = mode;
@@ -1195,6 +1285,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
     }
     pend(st);
   }
+  if (P.mass_fix) mass_acc(P, B, st, B.K, B.Vh, nullptr, B.rt, 1.0);
   // 7. QR of K
   {
     OrthArgs a = orth_args(P, B, 1, ORTH_QR);
@@ -1239,6 +1330,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   pend(st);
   tall(P, B, st, 1, B.X1, RC, B.rt, 0, nullptr, SM_UB, B.ro, 0, B.Xo, RC);
   tall(P, B, st, 0, B.V1, RC, B.rt, 0, nullptr, SM_VB, B.ro, 0, B.Vo, RC);
+  if (P.mass_fix) mass_acc(P, B, st, B.Xo, B.Vo, B.So, B.ro, -1.0);
 }
 
 void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
@@ -1263,6 +1355,7 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
     k_coll_kstep<double><<<dim3(64, nsub), DD_THREADS, 0, st>>>(P, B);
   }
   pend(st);
+  if (P.mass_fix) mass_acc(P, B, st, B.K, B.Vh, nullptr, B.rc, 1.0);
   {
     OrthArgs a = orth_args(P, B, 1, ORTH_QR);
     a.A = B.K; a.lda = RC; a.acols = B.rc; a.Q = B.Xo; a.ldq = RC; a.rout = B.rc;
@@ -1307,6 +1400,44 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   pbeg(st, KS_COLL_FINAL);
   k_coll_final<<<nsub, DD_THREADS, 0, st>>>(P, B);
   pend(st);
+  if (P.mass_fix) mass_acc(P, B, st, B.Xo, B.Vo, B.So, B.ro, -1.0);
+}
+
+// Conserved-moment correction at the end of a step (optional; not part of the
+// paper's scheme): f <- X S V^T + dm (x) 1/|S|, orthonormalised and truncated by
+// Algorithm 5's rule.  In the stored (Euclidean) form f = K_a V_a^T with
+// K_a = [X S | sqrt(hx hy) dm] and V_a = [V | sqrt(w)/|S|]; V_a = Q_v, K' = K_a (V_a^T Q_v),
+// K' = Q_x S', and the truncation of the (r+1) x (r+1) core S' as in the advection.
+void mass_fix_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
+  const Geo& g = P.g;
+  const int RC = g.RC, nsub = g.nsub;
+  pbeg(st, KS_MASS);
+  k_mf_build_x<<<dim3((P.maxN + DD_THREADS - 1) / DD_THREADS, nsub), DD_THREADS, 0, st>>>(
+      P, B.X, B.S, B.r, B.dm, B.K);
+  k_mf_build_v<<<dim3((g.n + DD_THREADS - 1) / DD_THREADS, nsub), DD_THREADS, 0, st>>>(
+      P, B.V, B.r, B.L, B.m);
+  pend(st);
+  {
+    OrthArgs a = orth_args(P, B, 0, ORTH_QR);
+    a.A = B.L; a.lda = RC; a.acols = B.m; a.Q = B.V1; a.ldq = RC; a.rout = B.m;
+    orthonormalize(P, B, st, a);
+  }
+  gram(P, B, st, 0, B.L, RC, B.m, 0, B.V1, RC, B.m, 0, 1, nullptr, SM_B);
+  tall(P, B, st, 1, B.K, RC, B.m, 0, nullptr, SM_B, B.m, 0, B.X1, RC);
+  {
+    OrthArgs a = orth_args(P, B, 1, ORTH_QR);
+    a.A = B.X1; a.lda = RC; a.acols = B.m; a.Q = B.K; a.ldq = RC; a.rout = B.m;
+    orthonormalize(P, B, st, a);
+  }
+  gram(P, B, st, 1, B.X1, RC, B.m, 0, B.K, RC, B.m, 0, 1, nullptr, SM_S3T);
+  pbeg(st, KS_COPY);
+  cudaMemcpyAsync(B.rt, B.m, sizeof(int) * nsub, cudaMemcpyDeviceToDevice, st);
+  pend(st);
+  pbeg(st, KS_TRUNC);
+  k_trunc<<<nsub, DD_THREADS, trunc_smem(RC), st>>>(P, B);
+  pend(st);
+  tall(P, B, st, 1, B.K, RC, B.rt, 0, nullptr, SM_UB, B.ro, 0, B.Xo, RC);
+  tall(P, B, st, 0, B.V1, RC, B.rt, 0, nullptr, SM_VB, B.ro, 0, B.Vo, RC);
 }
 
 void scalar_flux(const Problem& P, const double* X, const double* V, const double* S, const int* r,

@@ -55,6 +55,7 @@ class Workload:
     c_adv: float = 1.0
     n_mu: int = 0              # polar levels of the direction table (0: the paper's circle)
     n_phi: int = 0             # azimuths per level
+    mass_fix: bool = False     # conserved-moment correction at the end of every step
     meta: dict = field(default_factory=dict)
 
     @property
@@ -269,6 +270,21 @@ def narrow_source_problem(seed: int = 13, nsteps: int = 3) -> Workload:
     h = 1.0 / 64
     g0 = np.exp(-((X - 2.5 * h) ** 2 + (Y - 2.5 * h) ** 2) / (2 * (1.5 * h) ** 2))
     return wl.with_(name="narrow-source-64x64-4x4-n32-r4", g0=g0, source=np.zeros(64 * 64))
+
+
+def compact_transport_problem(tiles: int = 1, nx: int = 24, r_min: int = 4, r_max: int = 16,
+                              mass_fix: bool = False, nsteps: int = 4) -> Workload:
+    """Pure transport (sigma = 0, Q = 0) of a Gaussian of width 0.04 at the centre of
+    [0,1]^2, far from the boundary for the first steps; 16 directions, RK4, tolerance
+    mode with a tiny tolerance (1e-13) and ranks r_min..r_max."""
+    wl = random_small_problem(21, nx=nx, ny=nx, tiles_x=tiles, tiles_y=tiles, n_mu=2, n_phi=8,
+                              rank=2, r_aug_max=32, integrator="rk4", nsteps=nsteps)
+    X, Y = _cell_centres(nx, nx, 0.0, 1.0, 0.0, 1.0)
+    g0 = np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2) / (2 * 0.04 ** 2))
+    nc = nx * nx
+    return wl.with_(name=f"transport-{nx}x{nx}-{tiles}x{tiles}", sigma_s=np.zeros(nc),
+                    sigma_a=np.zeros(nc), source=np.zeros(nc), g0=g0, rank_mode="tol", tol=1e-13,
+                    r_min=r_min, r_max=r_max, mass_fix=mass_fix)
 
 
 def random_factors(seed: int, nrow: int, n: int, r: int, hx: float, hy: float, w: np.ndarray,

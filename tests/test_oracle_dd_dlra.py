@@ -288,3 +288,53 @@ def test_completion_families_orthogonal():
     assert np.all(np.diag(G) > 1e-3)
     # isotropic first, then the first azimuthal pair
     assert np.allclose(B[0], 1.0)
+
+
+def transport_only(tiles, fix, rmin=4):
+    return inputs.compact_transport_problem(tiles=tiles, r_min=rmin, mass_fix=fix)
+
+
+def mass_drift(wl):
+    o = dd_dlra.DDDLRA(wl)
+    m0 = o.scalar_flux().sum()
+    o.run()
+    return abs(o.scalar_flux().sum() - m0) / m0
+
+
+def test_mass_fix_conserves_mass_on_one_subdomain():
+    """R18: on one subdomain the K-steps conserve the total mass exactly (no interface,
+    nothing reaches the boundary); with the correction the step's mass is theirs.  At
+    rank 1 nothing is truncated away and the total mass is conserved to roundoff;
+    without the correction the S- and L-steps change it at O(dt^2)."""
+    assert mass_drift(transport_only(1, True, rmin=1)) < 1e-12
+    assert mass_drift(transport_only(1, False, rmin=1)) > 1e-2
+
+
+def test_mass_fix_reduces_mass_drift_at_rank_four():
+    """Rank floor 4: the truncation of the corrected state drops directions below the
+    rank threshold, so conservation is up to that loss, far below the drift without."""
+    fixed = mass_drift(transport_only(1, True, rmin=4))
+    plain = mass_drift(transport_only(1, False, rmin=4))
+    assert fixed < 1e-3 * plain
+
+
+def test_mass_correction_adds_exactly_delta():
+    """R18's correction term: adding delta (x) 1/|S| raises every cell's scalar flux by
+    delta (sum_q w_q / |S| = 1) and leaves the rest of f alone; with room under the rank
+    cap the truncation keeps it whole.  A zero delta leaves the factors untouched."""
+    o = dd_dlra.DDDLRA(transport_only(2, False)).run(1)
+    rng = np.random.default_rng(5)
+    before = [o._mass(U, S, V, k) for k, (U, S, V) in enumerate(o.state)]
+    f_before = [U @ S @ V.T for U, S, V in o.state]
+    deltas = [0.1 * np.max(np.abs(m)) * rng.standard_normal(m.shape) for m in before]
+    deltas[1] = np.zeros_like(deltas[1])
+    kept = o.state[1]
+    o.mass_correction(deltas)
+    assert all(a is b for a, b in zip(o.state[1], kept))
+    for k, (U, S, V) in enumerate(o.state):
+        after = o._mass(U, S, V, k)
+        scale = np.max(np.abs(before[k])) + np.max(np.abs(deltas[k]))
+        assert np.max(np.abs(after - before[k] - deltas[k])) < 1e-12 * scale
+        df = U @ S @ V.T - f_before[k]
+        iso = np.outer(deltas[k], np.full(V.shape[0], 1.0 / o.ssum))
+        assert np.max(np.abs(df - iso)) < 1e-12 * scale
