@@ -75,6 +75,12 @@ __device__ __forceinline__ T warp_sum_t(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+template <typename T>
+__device__ __forceinline__ T warp_max_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -410,6 +416,252 @@ __device__ __forceinline__ void jacobi_df(float2* Bd, float2* Jd, int m, int ld,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Column-per-lane one-sided Jacobi for m <= 32 (the same iteration, rotation and
+// stopping rules as jacobi_f32 / jacobi_df, laid out for latency): lane j of every
+// warp holds column j of B and of J in registers, the rows interleaved over the
+// block's JW_WARPS warps (row i in warp i % JW_WARPS).  In each round every column
+// meets its round-robin partner: the partner's entries arrive by shuffle, the dot
+// product's per-warp parts are summed in a fixed order through shared memory (one
+// barrier per round), and both lanes of a pair compute the same rotation from
+// bit-identical inputs, so no value is broadcast.  Every warp computes every
+// rotation, so the stopping test needs no block-wide reduction.
+// ---------------------------------------------------------------------------
+#define JW_WARPS (DD_THREADS / 32)
+#define JW_ROWS ((32 + JW_WARPS - 1) / JW_WARPS)   // rows per warp
+
+// Partner of index j in round r of the circle method over mm (even) indices: 0 is
+// fixed and meets 1 + r; otherwise a = j - 1 meets b with a + b = 2r (mod mm - 1).
+// Indices >= mm (lanes beyond the matrix) are their own partner.
+__device__ __forceinline__ int jw_partner(int j, int r, int mm) {
+  if (j >= mm) return j;
+  const int M = mm - 1;
+  if (j == 0) return 1 + r;
+  const int a = j - 1;
+  if (a == r) return 0;
+  int b = 2 * r - a;
+  b = b < 0 ? b + M : (b >= M ? b - M : b);
+  return 1 + b;
+}
+
+// Sum over the warps of the per-lane value x (fixed order, identical in every warp).
+// buf: 2 x JW_WARPS x 32 floats of shared memory, alternated by *ph.
+__device__ __forceinline__ float jw_sum(float x, float* buf, int* ph) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* b = buf + (*ph & 1) * JW_WARPS * 32;
+  ++*ph;
+  b[warp * 32 + lane] = x;
+  __syncthreads();
+  float t = 0.f;
+#pragma unroll
+  for (int w = 0; w < JW_WARPS; ++w) t += b[w * 32 + lane];
+  return t;
+}
+__device__ __forceinline__ float2 jw_sum_df(float2 x, float2* buf, int* ph) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2* b = buf + (*ph & 1) * JW_WARPS * 32;
+  ++*ph;
+  b[warp * 32 + lane] = x;
+  __syncthreads();
+  float2 u[JW_WARPS];
+#pragma unroll
+  for (int w = 0; w < JW_WARPS; ++w) u[w] = b[w * 32 + lane];
+#pragma unroll
+  for (int h = 1; h < JW_WARPS; h <<= 1)
+#pragma unroll
+    for (int w = 0; w + h < JW_WARPS; w += 2 * h) u[w] = df_add(u[w], u[w + h]);
+  return u[0];
+}
+
+// Double-float product whose rounding does not depend on the operand order (the two
+// lanes of a pair form their dot product with the operands swapped).
+__device__ __forceinline__ float2 df_mul_sym(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float e = __fadd_rn(__fmaf_rn(a.x, b.x, -p),
+                            __fadd_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+  return df_fast_sum(p, e);
+}
+
+// FP32 sweeps of the column-major m x m (m <= 32) Bf with J accumulated in Jf (both
+// shared memory, leading dimension ld; Jf holds the starting J).  Block-wide, blockDim
+// = DD_THREADS.  Same contract as jacobi_f32.
+__device__ __forceinline__ void jacobi_f32_cols(float* Bf, float* Jf, int m, int ld, float tol,
+                                                float stop, int max_sweeps) {
+  __shared__ float xb[2 * JW_WARPS * 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mm = m + (m & 1);
+  int ph = 0;
+  float b[JW_ROWS], v[JW_ROWS];
+#pragma unroll
+  for (int k = 0; k < JW_ROWS; ++k) {
+    const int i = warp + JW_WARPS * k;
+    const bool in = lane < m && i < m;
+    b[k] = in ? Bf[lane * ld + i] : 0.f;
+    v[k] = in ? Jf[lane * ld + i] : 0.f;
+  }
+  __syncthreads();                                 // Bf, Jf are rewritten at the end
+  float al;
+  {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < JW_ROWS; ++k) t = __fmaf_rn(b[k], b[k], t);
+    al = jw_sum(t, xb, &ph);
+  }
+  const float abs_thr = 1e-30f * warp_sum_t(al);
+  for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
+    if (sweep > 0) {                               // squared norms afresh every sweep
+      float t = 0.f;
+#pragma unroll
+      for (int k = 0; k < JW_ROWS; ++k) t = __fmaf_rn(b[k], b[k], t);
+      al = jw_sum(t, xb, &ph);
+    }
+    float lmax = 0.f;
+    for (int r = 0; r < mm - 1; ++r) {
+      const int p = jw_partner(lane, r, mm);
+      const float be = __shfl_sync(0xffffffffu, al, p);
+      float pb[JW_ROWS];
+#pragma unroll
+      for (int k = 0; k < JW_ROWS; ++k) pb[k] = __shfl_sync(0xffffffffu, b[k], p);
+      float g = 0.f;
+#pragma unroll
+      for (int k = 0; k < JW_ROWS; ++k) g = __fmaf_rn(b[k], pb[k], g);
+      g = jw_sum(g, xb, &ph);
+      float c = 1.f, sn = 0.f, tg = 0.f;
+      const float pr = al * be;
+      if (p != lane && p < m && lane < m && fabsf(g) > abs_thr && pr > 0.f) {
+        const float rel = fabsf(g) * rsqrtf(pr);
+        lmax = fmaxf(lmax, rel);
+        if (rel > tol) {
+          const bool lo = lane < p;
+          const float a_lo = lo ? al : be, a_hi = lo ? be : al;
+          const float zeta = __fdividef(a_hi - a_lo, 2.f * g);
+          float t;
+          if (fabsf(zeta) > 1e8f) {
+            t = __fdividef(0.5f, zeta);
+          } else {
+            const float w = 1.f + zeta * zeta;
+            t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + w * rsqrtf(w));
+          }
+          c = rsqrtf(1.f + t * t);
+          sn = lo ? -(c * t) : c * t;              // b_lo' = c b_lo - s b_hi, b_hi' = s b_lo + c b_hi
+          tg = lo ? -(t * g) : t * g;              // |b_lo'|^2 = al - t g, |b_hi'|^2 = al + t g
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < JW_ROWS; ++k) b[k] = c * b[k] + sn * pb[k];
+      al += tg;
+#pragma unroll
+      for (int k = 0; k < JW_ROWS; ++k) {
+        const float pv = __shfl_sync(0xffffffffu, v[k], p);
+        v[k] = c * v[k] + sn * pv;
+      }
+    }
+    const float mrel = warp_max_t(lmax);
+    if (mrel <= tol || mrel < stop) break;
+  }
+#pragma unroll
+  for (int k = 0; k < JW_ROWS; ++k) {
+    const int i = warp + JW_WARPS * k;
+    if (lane < m && i < m) {
+      Bf[lane * ld + i] = b[k];
+      Jf[lane * ld + i] = v[k];
+    }
+  }
+  __syncthreads();
+}
+
+// Double-float sweeps, column per lane (same contract as jacobi_df).
+__device__ __forceinline__ void jacobi_df_cols(float2* Bd, float2* Jd, int m, int ld, float tol,
+                                               float stop, int max_sweeps) {
+  __shared__ float2 xd[2 * JW_WARPS * 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mm = m + (m & 1);
+  int ph = 0;
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 b[JW_ROWS], v[JW_ROWS];
+#pragma unroll
+  for (int k = 0; k < JW_ROWS; ++k) {
+    const int i = warp + JW_WARPS * k;
+    const bool in = lane < m && i < m;
+    b[k] = in ? Bd[lane * ld + i] : z2;
+    v[k] = in ? Jd[lane * ld + i] : z2;
+  }
+  __syncthreads();
+  float2 al;
+  {
+    float2 t = z2;
+#pragma unroll
+    for (int k = 0; k < JW_ROWS; ++k) t = df_add(t, df_mul_sym(b[k], b[k]));
+    al = jw_sum_df(t, xd, &ph);
+  }
+  const float abs_thr = 1e-30f * warp_sum_t(al.x);
+  for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
+    if (sweep > 0) {
+      float2 t = z2;
+#pragma unroll
+      for (int k = 0; k < JW_ROWS; ++k) t = df_add(t, df_mul_sym(b[k], b[k]));
+      al = jw_sum_df(t, xd, &ph);
+    }
+    float lmax = 0.f;
+    for (int r = 0; r < mm - 1; ++r) {
+      const int p = jw_partner(lane, r, mm);
+      const float2 be = df_shfl(0xffffffffu, al, p);
+      float2 pb[JW_ROWS];
+#pragma unroll
+      for (int k = 0; k < JW_ROWS; ++k) pb[k] = df_shfl(0xffffffffu, b[k], p);
+      float2 g = z2;
+#pragma unroll
+      for (int k = 0; k < JW_ROWS; ++k) g = df_add(g, df_mul_sym(b[k], pb[k]));
+      g = jw_sum_df(g, xd, &ph);
+      float2 c = make_float2(1.f, 0.f), sn = z2, tg = z2;
+      const float pr = al.x * be.x;
+      if (p != lane && p < m && lane < m && fabsf(g.x) > abs_thr && pr > 0.f) {
+        const float rel = fabsf(g.x) * rsqrtf(pr);
+        lmax = fmaxf(lmax, rel);
+        if (rel > tol) {
+          const bool lo = lane < p;
+          const float2 a_lo = lo ? al : be, a_hi = lo ? be : al;
+          const float zeta = __fdividef(df_add(a_hi, df_neg(a_lo)).x, 2.f * g.x);
+          float t;
+          if (fabsf(zeta) > 1e8f) {
+            t = __fdividef(0.5f, zeta);
+          } else {
+            const float w = 1.f + zeta * zeta;
+            t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + w * rsqrtf(w));
+          }
+          // c = (1 + t^2)^-1/2 by one Newton step in double-float from rsqrtf
+          const float2 w = df_add(make_float2(1.f, 0.f), df_mulf(make_float2(t, 0.f), t));
+          const float y0 = rsqrtf(w.x);
+          const float2 h = df_add(make_float2(1.f, 0.f), df_neg(df_mulf(df_mulf(w, y0), y0)));
+          c = df_add(make_float2(y0, 0.f), df_mulf(h, 0.5f * y0));
+          const float2 s = df_mulf(c, t), gt = df_mulf(g, t);
+          sn = lo ? df_neg(s) : s;
+          tg = lo ? df_neg(gt) : gt;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < JW_ROWS; ++k) b[k] = df_add(df_mul(c, b[k]), df_mul(sn, pb[k]));
+      al = df_add(al, tg);
+#pragma unroll
+      for (int k = 0; k < JW_ROWS; ++k) {
+        const float2 pv = df_shfl(0xffffffffu, v[k], p);
+        v[k] = df_add(df_mul(c, v[k]), df_mul(sn, pv));
+      }
+    }
+    const float mrel = warp_max_t(lmax);
+    if (mrel <= tol || mrel < stop) break;
+  }
+#pragma unroll
+  for (int k = 0; k < JW_ROWS; ++k) {
+    const int i = warp + JW_WARPS * k;
+    if (lane < m && i < m) {
+      Bd[lane * ld + i] = b[k];
+      Jd[lane * ld + i] = v[k];
+    }
+  }
+  __syncthreads();
+}
+
 // Shared scratch of jacobi_svd_mixed for leading dimension ld: the FP32 copies of B
 // and J (reused as a double-float temporary afterwards), m norms, and the
 // double-float B and J.
@@ -478,7 +730,10 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
     J32[e] = (c == r) ? 1.f : 0.f;
   }
   __syncthreads();
-  jacobi_f32(B32, J32, m, ld, flag, n32, 1e-6f, 1e-3f, 30);
+  if (m <= 32 && blockDim.x == DD_THREADS)
+    jacobi_f32_cols(B32, J32, m, ld, 1e-6f, 1e-3f, 30);
+  else
+    jacobi_f32(B32, J32, m, ld, flag, n32, 1e-6f, 1e-3f, 30);
   for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) Jd[e] = make_float2(J32[e], 0.f);
   __syncthreads();
   // two Newton-Schulz steps: T = 3I - J^T J, J <- J T / 2 (via Bd as the output)
@@ -517,7 +772,10 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
     Bd[e] = x;
   }
   __syncthreads();
-  jacobi_df(Bd, Jd, m, ld, flag, T, 1e-13f, 3e-7f, 10);
+  if (m <= 32 && blockDim.x == DD_THREADS)
+    jacobi_df_cols(Bd, Jd, m, ld, 1e-13f, 3e-7f, 10);
+  else
+    jacobi_df(Bd, Jd, m, ld, flag, T, 1e-13f, 3e-7f, 10);
   for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
     int c = e / ld, r = e % ld;
     if (c < m && r < m) {
