@@ -417,61 +417,59 @@ __device__ __forceinline__ void jacobi_df(float2* Bd, float2* Jd, int m, int ld,
 }
 
 // ---------------------------------------------------------------------------
-// Column-per-lane one-sided Jacobi for m <= 32 (the same iteration, rotation and
+// Column-per-lane one-sided Jacobi for at most 32 columns (the same iteration and
 // stopping rules as jacobi_f32 / jacobi_df, laid out for latency): lane j of every
-// warp holds column j of B and of J in registers, the rows interleaved over the
+// warp holds column j of B (and of J) in registers, the rows interleaved over the
 // block's JW_WARPS warps (row i in warp i % JW_WARPS).  In each round every column
 // meets its round-robin partner: the partner's entries arrive by shuffle, the dot
 // product's per-warp parts are summed in a fixed order through shared memory (one
 // barrier per round), and both lanes of a pair compute the same rotation from
 // bit-identical inputs, so no value is broadcast.  Every warp computes every
-// rotation, so the stopping test needs no block-wide reduction.
+// rotation, so the stopping test needs no block-wide reduction.  B is nr x nc
+// (nr <= JW_WARPS * ROWS rows, nc <= 32 columns), J is nc x nc.
 // ---------------------------------------------------------------------------
 #define JW_WARPS (DD_THREADS / 32)
-#define JW_ROWS ((32 + JW_WARPS - 1) / JW_WARPS)   // rows per warp
+#define JW_JROWS ((32 + JW_WARPS - 1) / JW_WARPS)   // rows of J per warp (nc <= 32)
 
 // Partner of index j in round r of the circle method over mm (even) indices: 0 is
 // fixed and meets 1 + r; otherwise a = j - 1 meets b with a + b = 2r (mod mm - 1).
 // Indices >= mm (lanes beyond the matrix) are their own partner.
 __device__ __forceinline__ int jw_partner(int j, int r, int mm) {
-  if (j >= mm) return j;
-  const int M = mm - 1;
-  if (j == 0) return 1 + r;
-  const int a = j - 1;
-  if (a == r) return 0;
+  const int M = mm - 1, a = j - 1;
   int b = 2 * r - a;
-  b = b < 0 ? b + M : (b >= M ? b - M : b);
-  return 1 + b;
+  b = b < 0 ? b + M : b;
+  b = b >= M ? b - M : b;
+  int p = a == r ? 0 : 1 + b;
+  p = j == 0 ? 1 + r : p;
+  return j >= mm ? j : p;
 }
 
-// Sum over the warps of the per-lane value x (fixed order, identical in every warp).
-// buf: 2 x JW_WARPS x 32 floats of shared memory, alternated by *ph.
-__device__ __forceinline__ float jw_sum(float x, float* buf, int* ph) {
+// Sum over the warps of the per-lane value x (fixed pairwise order, identical in
+// every warp).  buf: 2 x JW_WARPS x 32 values of shared memory, alternated by *ph.
+template <typename T, typename Add>
+__device__ __forceinline__ T jw_sum(T x, T* buf, int* ph, Add add) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* b = buf + (*ph & 1) * JW_WARPS * 32;
+  T* b = buf + (*ph & 1) * JW_WARPS * 32;
   ++*ph;
   b[warp * 32 + lane] = x;
   __syncthreads();
-  float t = 0.f;
-#pragma unroll
-  for (int w = 0; w < JW_WARPS; ++w) t += b[w * 32 + lane];
-  return t;
-}
-__device__ __forceinline__ float2 jw_sum_df(float2 x, float2* buf, int* ph) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float2* b = buf + (*ph & 1) * JW_WARPS * 32;
-  ++*ph;
-  b[warp * 32 + lane] = x;
-  __syncthreads();
-  float2 u[JW_WARPS];
+  T u[JW_WARPS];
 #pragma unroll
   for (int w = 0; w < JW_WARPS; ++w) u[w] = b[w * 32 + lane];
 #pragma unroll
   for (int h = 1; h < JW_WARPS; h <<= 1)
 #pragma unroll
-    for (int w = 0; w + h < JW_WARPS; w += 2 * h) u[w] = df_add(u[w], u[w + h]);
+    for (int w = 0; w + h < JW_WARPS; w += 2 * h) u[w] = add(u[w], u[w + h]);
   return u[0];
 }
+// The exchange buffer of the column sweeps: one per kernel, shared by every
+// instantiation (2 x JW_WARPS x 32 double-float values).
+__device__ __forceinline__ float2* jw_buffer() {
+  __shared__ float2 jwb[2 * JW_WARPS * 32];
+  return jwb;
+}
+struct JwAddF { __device__ float operator()(float a, float b) const { return a + b; } };
+struct JwAddDF { __device__ float2 operator()(float2 a, float2 b) const { return df_add(a, b); } };
 
 // Double-float product whose rounding does not depend on the operand order (the two
 // lanes of a pair form their dot product with the operands swapped).
@@ -482,184 +480,228 @@ __device__ __forceinline__ float2 df_mul_sym(float2 a, float2 b) {
   return df_fast_sum(p, e);
 }
 
-// FP32 sweeps of the column-major m x m (m <= 32) Bf with J accumulated in Jf (both
+// Rotation of the pair (lo, hi) annihilating g = b_lo . b_hi, from a = |b_lo|^2 and
+// b = |b_hi|^2 (both lanes pass them in the same roles): t = sgn(z) / (|z| + (1 + z^2)^1/2),
+// z = (b - a) / (2g), c = (1 + t^2)^-1/2, s = c t, written without t: with
+// D = |z| + (1 + z^2)^1/2, s = sgn(z) (1 + D^2)^-1/2 and c = D |s| (three dependent
+// special-function operations); for |z| > 1e8, t = 1 / (2z) and c = 1.  Returns t in *t.
+__device__ __forceinline__ void jw_rotation(float a, float b, float g, float* c, float* s,
+                                            float* t) {
+  const float z = __fdividef(b - a, 2.f * g);
+  const float az = fabsf(z);
+  const float w = __fmaf_rn(z, z, 1.f);
+  const float D = az + w * rsqrtf(w);
+  const float q = rsqrtf(__fmaf_rn(D, D, 1.f));
+  const float iD = __fdividef(1.f, D);
+  const bool huge = az > 1e8f;
+  const float sg = z >= 0.f ? 1.f : -1.f;
+  const float th = __fdividef(0.5f, z);
+  *c = huge ? 1.f : D * q;
+  *s = huge ? th : sg * q;
+  *t = huge ? th : sg * iD;
+}
+
+// FP32 sweeps of the column-major nr x nc Bf with J accumulated in Jf when WJ (both
 // shared memory, leading dimension ld; Jf holds the starting J).  Block-wide, blockDim
 // = DD_THREADS.  Same contract as jacobi_f32.
-__device__ __forceinline__ void jacobi_f32_cols(float* Bf, float* Jf, int m, int ld, float tol,
-                                                float stop, int max_sweeps) {
-  __shared__ float xb[2 * JW_WARPS * 32];
+template <int ROWS, bool WJ>
+__device__ __forceinline__ void jacobi_f32_cols(float* Bf, float* Jf, int nr, int nc, int ld,
+                                                float tol, float stop, int max_sweeps) {
+  float* xb = reinterpret_cast<float*>(jw_buffer());
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int mm = m + (m & 1);
+  const int mm = nc + (nc & 1);
   int ph = 0;
-  float b[JW_ROWS], v[JW_ROWS];
+  float b[ROWS], v[JW_JROWS];
 #pragma unroll
-  for (int k = 0; k < JW_ROWS; ++k) {
+  for (int k = 0; k < ROWS; ++k) {
     const int i = warp + JW_WARPS * k;
-    const bool in = lane < m && i < m;
-    b[k] = in ? Bf[lane * ld + i] : 0.f;
-    v[k] = in ? Jf[lane * ld + i] : 0.f;
+    b[k] = (lane < nc && i < nr) ? Bf[lane * ld + i] : 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < JW_JROWS; ++k) {
+    const int i = warp + JW_WARPS * k;
+    v[k] = (WJ && lane < nc && i < nc) ? Jf[lane * ld + i] : 0.f;
   }
   __syncthreads();                                 // Bf, Jf are rewritten at the end
-  float al;
-  {
-    float t = 0.f;
-#pragma unroll
-    for (int k = 0; k < JW_ROWS; ++k) t = __fmaf_rn(b[k], b[k], t);
-    al = jw_sum(t, xb, &ph);
-  }
-  const float abs_thr = 1e-30f * warp_sum_t(al);
-  for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
-    if (sweep > 0) {                               // squared norms afresh every sweep
+  float al = 0.f, abs_thr = 0.f;
+  for (int sweep = 0; sweep < max_sweeps && nc > 1; ++sweep) {
+    {                                              // squared norms afresh every sweep
       float t = 0.f;
 #pragma unroll
-      for (int k = 0; k < JW_ROWS; ++k) t = __fmaf_rn(b[k], b[k], t);
-      al = jw_sum(t, xb, &ph);
+      for (int k = 0; k < ROWS; ++k) t = __fmaf_rn(b[k], b[k], t);
+      al = jw_sum(t, xb, &ph, JwAddF());
+      if (sweep == 0) abs_thr = 1e-30f * warp_sum_t(al);
     }
     float lmax = 0.f;
     for (int r = 0; r < mm - 1; ++r) {
       const int p = jw_partner(lane, r, mm);
       const float be = __shfl_sync(0xffffffffu, al, p);
-      float pb[JW_ROWS];
+      float pb[ROWS];
 #pragma unroll
-      for (int k = 0; k < JW_ROWS; ++k) pb[k] = __shfl_sync(0xffffffffu, b[k], p);
+      for (int k = 0; k < ROWS; ++k) pb[k] = __shfl_sync(0xffffffffu, b[k], p);
       float g = 0.f;
 #pragma unroll
-      for (int k = 0; k < JW_ROWS; ++k) g = __fmaf_rn(b[k], pb[k], g);
-      g = jw_sum(g, xb, &ph);
-      float c = 1.f, sn = 0.f, tg = 0.f;
+      for (int k = 0; k < ROWS; ++k) g = __fmaf_rn(b[k], pb[k], g);
+      g = jw_sum(g, xb, &ph, JwAddF());
       const float pr = al * be;
-      if (p != lane && p < m && lane < m && fabsf(g) > abs_thr && pr > 0.f) {
-        const float rel = fabsf(g) * rsqrtf(pr);
-        lmax = fmaxf(lmax, rel);
-        if (rel > tol) {
-          const bool lo = lane < p;
-          const float a_lo = lo ? al : be, a_hi = lo ? be : al;
-          const float zeta = __fdividef(a_hi - a_lo, 2.f * g);
-          float t;
-          if (fabsf(zeta) > 1e8f) {
-            t = __fdividef(0.5f, zeta);
-          } else {
-            const float w = 1.f + zeta * zeta;
-            t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + w * rsqrtf(w));
-          }
-          c = rsqrtf(1.f + t * t);
-          sn = lo ? -(c * t) : c * t;              // b_lo' = c b_lo - s b_hi, b_hi' = s b_lo + c b_hi
-          tg = lo ? -(t * g) : t * g;              // |b_lo'|^2 = al - t g, |b_hi'|^2 = al + t g
-        }
-      }
+      const bool ok = p != lane && p < nc && lane < nc && fabsf(g) > abs_thr && pr > 0.f;
+      const float rel = ok ? fabsf(g) * rsqrtf(pr) : 0.f;
+      lmax = fmaxf(lmax, rel);
+      const bool lo = lane < p;
+      float c, s, t;
+      jw_rotation(lo ? al : be, lo ? be : al, g, &c, &s, &t);
+      const bool rot = rel > tol;
+      // b_lo' = c b_lo - s b_hi, b_hi' = s b_lo + c b_hi; |b_lo'|^2 = a - t g, |b_hi'|^2 = b + t g
+      c = rot ? c : 1.f;
+      const float sn = rot ? (lo ? -s : s) : 0.f;
+      const float tg = rot ? (lo ? -(t * g) : t * g) : 0.f;
 #pragma unroll
-      for (int k = 0; k < JW_ROWS; ++k) b[k] = c * b[k] + sn * pb[k];
+      for (int k = 0; k < ROWS; ++k) b[k] = c * b[k] + sn * pb[k];
       al += tg;
+      if (WJ) {
 #pragma unroll
-      for (int k = 0; k < JW_ROWS; ++k) {
-        const float pv = __shfl_sync(0xffffffffu, v[k], p);
-        v[k] = c * v[k] + sn * pv;
+        for (int k = 0; k < JW_JROWS; ++k) {
+          const float pv = __shfl_sync(0xffffffffu, v[k], p);
+          v[k] = c * v[k] + sn * pv;
+        }
       }
     }
     const float mrel = warp_max_t(lmax);
     if (mrel <= tol || mrel < stop) break;
   }
 #pragma unroll
-  for (int k = 0; k < JW_ROWS; ++k) {
+  for (int k = 0; k < ROWS; ++k) {
     const int i = warp + JW_WARPS * k;
-    if (lane < m && i < m) {
-      Bf[lane * ld + i] = b[k];
-      Jf[lane * ld + i] = v[k];
+    if (lane < nc && i < nr) Bf[lane * ld + i] = b[k];
+  }
+  if (WJ) {
+#pragma unroll
+    for (int k = 0; k < JW_JROWS; ++k) {
+      const int i = warp + JW_WARPS * k;
+      if (lane < nc && i < nc) Jf[lane * ld + i] = v[k];
     }
   }
   __syncthreads();
 }
 
-// Double-float sweeps, column per lane (same contract as jacobi_df).
-__device__ __forceinline__ void jacobi_df_cols(float2* Bd, float2* Jd, int m, int ld, float tol,
-                                               float stop, int max_sweeps) {
-  __shared__ float2 xd[2 * JW_WARPS * 32];
+// Double-float sweeps, column per lane (same contract as jacobi_df; J accumulated in
+// Jd when WJ).  The tangent comes from the hi parts in FP32 and c = (1 + t^2)^-1/2 is
+// refined by one Newton step in double-float, so every rotation is orthogonal to
+// double-float rounding.
+template <int ROWS, bool WJ>
+__device__ __forceinline__ void jacobi_df_cols(float2* Bd, float2* Jd, int nr, int nc, int ld,
+                                               float tol, float stop, int max_sweeps) {
+  float2* xd = jw_buffer();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int mm = m + (m & 1);
+  const int mm = nc + (nc & 1);
   int ph = 0;
   const float2 z2 = make_float2(0.f, 0.f);
-  float2 b[JW_ROWS], v[JW_ROWS];
+  float2 b[ROWS], v[JW_JROWS];
 #pragma unroll
-  for (int k = 0; k < JW_ROWS; ++k) {
+  for (int k = 0; k < ROWS; ++k) {
     const int i = warp + JW_WARPS * k;
-    const bool in = lane < m && i < m;
-    b[k] = in ? Bd[lane * ld + i] : z2;
-    v[k] = in ? Jd[lane * ld + i] : z2;
+    b[k] = (lane < nc && i < nr) ? Bd[lane * ld + i] : z2;
+  }
+#pragma unroll
+  for (int k = 0; k < JW_JROWS; ++k) {
+    const int i = warp + JW_WARPS * k;
+    v[k] = (WJ && lane < nc && i < nc) ? Jd[lane * ld + i] : z2;
   }
   __syncthreads();
-  float2 al;
-  {
-    float2 t = z2;
-#pragma unroll
-    for (int k = 0; k < JW_ROWS; ++k) t = df_add(t, df_mul_sym(b[k], b[k]));
-    al = jw_sum_df(t, xd, &ph);
-  }
-  const float abs_thr = 1e-30f * warp_sum_t(al.x);
-  for (int sweep = 0; sweep < max_sweeps && m > 1; ++sweep) {
-    if (sweep > 0) {
+  float2 al = z2;
+  float abs_thr = 0.f;
+  for (int sweep = 0; sweep < max_sweeps && nc > 1; ++sweep) {
+    {
       float2 t = z2;
 #pragma unroll
-      for (int k = 0; k < JW_ROWS; ++k) t = df_add(t, df_mul_sym(b[k], b[k]));
-      al = jw_sum_df(t, xd, &ph);
+      for (int k = 0; k < ROWS; ++k) t = df_add(t, df_mul_sym(b[k], b[k]));
+      al = jw_sum(t, xd, &ph, JwAddDF());
+      if (sweep == 0) abs_thr = 1e-30f * warp_sum_t(al.x);
     }
     float lmax = 0.f;
     for (int r = 0; r < mm - 1; ++r) {
       const int p = jw_partner(lane, r, mm);
       const float2 be = df_shfl(0xffffffffu, al, p);
-      float2 pb[JW_ROWS];
+      float2 pb[ROWS];
 #pragma unroll
-      for (int k = 0; k < JW_ROWS; ++k) pb[k] = df_shfl(0xffffffffu, b[k], p);
+      for (int k = 0; k < ROWS; ++k) pb[k] = df_shfl(0xffffffffu, b[k], p);
       float2 g = z2;
 #pragma unroll
-      for (int k = 0; k < JW_ROWS; ++k) g = df_add(g, df_mul_sym(b[k], pb[k]));
-      g = jw_sum_df(g, xd, &ph);
-      float2 c = make_float2(1.f, 0.f), sn = z2, tg = z2;
+      for (int k = 0; k < ROWS; ++k) g = df_add(g, df_mul_sym(b[k], pb[k]));
+      g = jw_sum(g, xd, &ph, JwAddDF());
       const float pr = al.x * be.x;
-      if (p != lane && p < m && lane < m && fabsf(g.x) > abs_thr && pr > 0.f) {
-        const float rel = fabsf(g.x) * rsqrtf(pr);
-        lmax = fmaxf(lmax, rel);
-        if (rel > tol) {
-          const bool lo = lane < p;
-          const float2 a_lo = lo ? al : be, a_hi = lo ? be : al;
-          const float zeta = __fdividef(df_add(a_hi, df_neg(a_lo)).x, 2.f * g.x);
-          float t;
-          if (fabsf(zeta) > 1e8f) {
-            t = __fdividef(0.5f, zeta);
-          } else {
-            const float w = 1.f + zeta * zeta;
-            t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + w * rsqrtf(w));
-          }
-          // c = (1 + t^2)^-1/2 by one Newton step in double-float from rsqrtf
-          const float2 w = df_add(make_float2(1.f, 0.f), df_mulf(make_float2(t, 0.f), t));
-          const float y0 = rsqrtf(w.x);
-          const float2 h = df_add(make_float2(1.f, 0.f), df_neg(df_mulf(df_mulf(w, y0), y0)));
-          c = df_add(make_float2(y0, 0.f), df_mulf(h, 0.5f * y0));
-          const float2 s = df_mulf(c, t), gt = df_mulf(g, t);
-          sn = lo ? df_neg(s) : s;
-          tg = lo ? df_neg(gt) : gt;
-        }
-      }
+      const bool ok = p != lane && p < nc && lane < nc && fabsf(g.x) > abs_thr && pr > 0.f;
+      const float rel = ok ? fabsf(g.x) * rsqrtf(pr) : 0.f;
+      lmax = fmaxf(lmax, rel);
+      const bool lo = lane < p;
+      const float2 a_lo = lo ? al : be, a_hi = lo ? be : al;
+      float c32, s32, t;
+      jw_rotation(0.f, df_add(a_hi, df_neg(a_lo)).x, g.x, &c32, &s32, &t);
+      const bool rot = rel > tol;
+      // c = (1 + t^2)^-1/2 by one Newton step in double-float from rsqrtf
+      const float2 w = df_add(make_float2(1.f, 0.f), df_mulf(make_float2(t, 0.f), t));
+      const float y0 = rsqrtf(w.x);
+      const float2 h = df_add(make_float2(1.f, 0.f), df_neg(df_mulf(df_mulf(w, y0), y0)));
+      float2 c = df_add(make_float2(y0, 0.f), df_mulf(h, 0.5f * y0));
+      const float2 s = df_mulf(c, t), gt = df_mulf(g, t);
+      c = rot ? c : make_float2(1.f, 0.f);
+      const float2 sn = rot ? (lo ? df_neg(s) : s) : z2;
+      const float2 tg = rot ? (lo ? df_neg(gt) : gt) : z2;
 #pragma unroll
-      for (int k = 0; k < JW_ROWS; ++k) b[k] = df_add(df_mul(c, b[k]), df_mul(sn, pb[k]));
+      for (int k = 0; k < ROWS; ++k) b[k] = df_add(df_mul(c, b[k]), df_mul(sn, pb[k]));
       al = df_add(al, tg);
+      if (WJ) {
 #pragma unroll
-      for (int k = 0; k < JW_ROWS; ++k) {
-        const float2 pv = df_shfl(0xffffffffu, v[k], p);
-        v[k] = df_add(df_mul(c, v[k]), df_mul(sn, pv));
+        for (int k = 0; k < JW_JROWS; ++k) {
+          const float2 pv = df_shfl(0xffffffffu, v[k], p);
+          v[k] = df_add(df_mul(c, v[k]), df_mul(sn, pv));
+        }
       }
     }
     const float mrel = warp_max_t(lmax);
     if (mrel <= tol || mrel < stop) break;
   }
 #pragma unroll
-  for (int k = 0; k < JW_ROWS; ++k) {
+  for (int k = 0; k < ROWS; ++k) {
     const int i = warp + JW_WARPS * k;
-    if (lane < m && i < m) {
-      Bd[lane * ld + i] = b[k];
-      Jd[lane * ld + i] = v[k];
+    if (lane < nc && i < nr) Bd[lane * ld + i] = b[k];
+  }
+  if (WJ) {
+#pragma unroll
+    for (int k = 0; k < JW_JROWS; ++k) {
+      const int i = warp + JW_WARPS * k;
+      if (lane < nc && i < nc) Jd[lane * ld + i] = v[k];
     }
   }
   __syncthreads();
+}
+
+// Two Newton-Schulz steps J <- J (3I - J^T J) / 2 on the n x n column-major Jd in
+// double-float (T, W: n x n scratch), making a J orthogonal to ~1e-7 orthogonal to
+// double-float rounding.
+__device__ __forceinline__ void ns_orthogonalize_df(float2* Jd, float2* T, float2* W, int n,
+                                                    int ld) {
+  for (int it = 0; it < 2; ++it) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int i = e / n, j = e % n;
+      float2 x = make_float2(0.f, 0.f);
+      for (int l = 0; l < n; ++l) x = df_add(x, df_mul(Jd[i * ld + l], Jd[j * ld + l]));
+      T[i * ld + j] = df_add(make_float2(i == j ? 3.f : 0.f, 0.f), df_neg(x));
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int c = e / n, r = e % n;
+      float2 x = make_float2(0.f, 0.f);
+      for (int l = 0; l < n; ++l) x = df_add(x, df_mul(Jd[l * ld + r], T[c * ld + l]));
+      W[c * ld + r] = df_mulf(x, 0.5f);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int c = e / n, r = e % n;
+      Jd[c * ld + r] = W[c * ld + r];
+    }
+    __syncthreads();
+  }
 }
 
 // Shared scratch of jacobi_svd_mixed for leading dimension ld: the FP32 copies of B
@@ -731,33 +773,12 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
   }
   __syncthreads();
   if (m <= 32 && blockDim.x == DD_THREADS)
-    jacobi_f32_cols(B32, J32, m, ld, 1e-6f, 1e-3f, 30);
+    jacobi_f32_cols<JW_JROWS, true>(B32, J32, m, m, ld, 1e-6f, 1e-3f, 30);
   else
     jacobi_f32(B32, J32, m, ld, flag, n32, 1e-6f, 1e-3f, 30);
   for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) Jd[e] = make_float2(J32[e], 0.f);
   __syncthreads();
-  // two Newton-Schulz steps: T = 3I - J^T J, J <- J T / 2 (via Bd as the output)
-  for (int it = 0; it < 2; ++it) {
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      int i = e / m, j = e % m;
-      float2 x = make_float2(0.f, 0.f);
-      for (int l = 0; l < m; ++l) x = df_add(x, df_mul(Jd[i * ld + l], Jd[j * ld + l]));
-      T[i * ld + j] = df_add(make_float2(i == j ? 3.f : 0.f, 0.f), df_neg(x));
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      int c = e / m, r = e % m;
-      float2 x = make_float2(0.f, 0.f);
-      for (int l = 0; l < m; ++l) x = df_add(x, df_mul(Jd[l * ld + r], T[c * ld + l]));
-      Bd[c * ld + r] = df_mulf(x, 0.5f);
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      int c = e / m, r = e % m;
-      Jd[c * ld + r] = Bd[c * ld + r];
-    }
-    __syncthreads();
-  }
+  ns_orthogonalize_df(Jd, T, Bd, m, ld);
   // B <- (sc B) J in double-float
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     int c = e / m, r = e % m;
@@ -773,7 +794,7 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
   }
   __syncthreads();
   if (m <= 32 && blockDim.x == DD_THREADS)
-    jacobi_df_cols(Bd, Jd, m, ld, 1e-13f, 3e-7f, 10);
+    jacobi_df_cols<JW_JROWS, true>(Bd, Jd, m, m, ld, 1e-13f, 3e-7f, 10);
   else
     jacobi_df(Bd, Jd, m, ld, flag, T, 1e-13f, 3e-7f, 10);
   for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
@@ -783,6 +804,63 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
       Jc[e] = df_to_double(Jd[e]);
     }
   }
+  __syncthreads();
+}
+
+// Orthogonalisation of the columns of the nr x nc (nr <= 64, nc <= 32) column-major
+// FP64 X (leading dimension ld) by one-sided Jacobi: on return X <- X J with J
+// orthogonal and the columns of X J orthogonal to double-float accuracy (~1e-13
+// relative).  FP32 sweeps on a power-of-two scaled copy accumulate J; J is made
+// orthogonal by two Newton-Schulz steps and X J formed in double-float; double-float
+// sweeps finish on the rotated columns (J itself is not needed further).  Scratch as
+// for jacobi_svd_mixed.
+__device__ __forceinline__ void jacobi_rect_mixed(double* X, int nr, int nc, int ld,
+                                                  void* scratch) {
+  float* B32 = reinterpret_cast<float*>(scratch);
+  float* J32 = B32 + ld * ld;
+  float* n32 = J32 + ld * ld;
+  float2* T = reinterpret_cast<float2*>(B32);           // after the FP32 sweeps
+  float2* Bd = reinterpret_cast<float2*>(n32 + 2 * ld);
+  float2* Jd = Bd + ld * ld;
+  if (nr <= 0 || nc <= 0) return;
+  __shared__ double rred[40];
+  double mx = 0.0;
+  for (int c = 0; c < nc; ++c)
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) mx = fmax(mx, fabs(X[c * ld + r]));
+  mx = block_max(mx, rred);
+  if (!(mx > 0.0) || !isfinite(mx)) return;
+  const int ex = ilogb(mx);
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
+    int c = e / ld, r = e % ld;
+    B32[e] = (c < nc && r < nr) ? (float)scalbn(X[e], -ex) : 0.f;
+    J32[e] = (c == r) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  if (nr <= 32)
+    jacobi_f32_cols<32 / JW_WARPS, true>(B32, J32, nr, nc, ld, 1e-6f, 1e-3f, 30);
+  else
+    jacobi_f32_cols<64 / JW_WARPS, true>(B32, J32, nr, nc, ld, 1e-6f, 1e-3f, 30);
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) Jd[e] = make_float2(J32[e], 0.f);
+  __syncthreads();
+  ns_orthogonalize_df(Jd, T, Bd, nc, ld);
+  for (int c = 0; c < nc; ++c)
+    for (int r = threadIdx.x; r < nr; r += blockDim.x)
+      T[c * ld + r] = df_from_double(scalbn(X[c * ld + r], -ex));
+  __syncthreads();
+  for (int c = 0; c < nc; ++c)
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      float2 x = make_float2(0.f, 0.f);
+      for (int l = 0; l < nc; ++l) x = df_add(x, df_mul(T[l * ld + r], Jd[c * ld + l]));
+      Bd[c * ld + r] = x;
+    }
+  __syncthreads();
+  if (nr <= 32)
+    jacobi_df_cols<32 / JW_WARPS, false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10);
+  else
+    jacobi_df_cols<64 / JW_WARPS, false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10);
+  for (int c = 0; c < nc; ++c)
+    for (int r = threadIdx.x; r < nr; r += blockDim.x)
+      X[c * ld + r] = scalbn(df_to_double(Bd[c * ld + r]), ex);
   __syncthreads();
 }
 

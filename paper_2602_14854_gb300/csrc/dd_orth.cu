@@ -78,6 +78,95 @@ __device__ int decide(const OrthArgs& a, int k, const double* sig, int nref, int
   return p;
 }
 
+// Pivoted Cholesky of the m x m (m <= 64) positive semidefinite A (column-major,
+// leading dimension ld; overwritten by its Schur complements): A = X X^T up to a
+// remainder whose diagonal is <= thr_rel times the largest diagonal entry of A.  X is
+// m x k, written to the first k columns of X with the rows in the original order
+// (column t is row t of the triangular factor in pivot order).  The pivot is the
+// largest remaining diagonal entry (lowest index on ties), found by every warp alike;
+// *piv gets the pivoted indices as a bit mask.  Block-wide; returns k.
+__device__ int pchol_cols(double* A, double* X, int m, int ld, double thr_rel,
+                          unsigned long long* piv) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  unsigned long long done = 0ull;
+  double thr = 0.0;
+  int k = 0;
+  for (; k < m; ++k) {
+    double best = -1.0;
+    int bi = m;
+    for (int i = lane; i < m; i += 32) {
+      const double d = ((done >> i) & 1ull) ? -1.0 : A[i * ld + i];
+      if (d > best) { best = d; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (k == 0) thr = thr_rel * best;
+    if (!(best > 0.0) || !(best > thr)) break;
+    const double d = sqrt(best), id = 1.0 / d;
+    for (int i = tid; i < m; i += blockDim.x)
+      X[k * ld + i] = ((done >> i) & 1ull) ? 0.0 : (i == bi ? d : A[bi * ld + i] * id);
+    done |= 1ull << bi;
+    __syncthreads();
+    for (int j = warp; j < m; j += nw) {
+      if ((done >> j) & 1ull) continue;
+      const double xj = X[k * ld + j];
+      for (int i = lane; i < m; i += 32)
+        if (!((done >> i) & 1ull)) A[j * ld + i] -= X[k * ld + i] * xj;
+    }
+    __syncthreads();
+  }
+  *piv = done;
+  return k;
+}
+
+// Completes the orthonormal columns 0..cur-1 of the m x m column-major V (leading
+// dimension ld) to m columns with unit vectors, first those of the indices outside
+// mask (in index order), then the others: each candidate is Gram-Schmidt'd twice in
+// FP64 and accepted when its norm after that exceeds 0.1 (at every stage some unit
+// vector keeps at least m^-1/2).  coef: m doubles of shared scratch.
+__device__ void complete_unit(double* V, int m, int cur, int ld, unsigned long long mask,
+                              double* coef, unsigned* status) {
+  __shared__ double cred[40];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int cand = 0; cand < 2 * m && cur < m; ++cand) {
+    const int i = cand < m ? cand : cand - m;
+    const bool inmask = (mask >> i) & 1ull;
+    if ((cand < m) == inmask) continue;
+    double* x = V + (long)cur * ld;
+    for (int r = tid; r < m; r += blockDim.x) {
+      double s = r == i ? 1.0 : 0.0;
+      for (int l = 0; l < cur; ++l) s -= V[l * ld + i] * V[l * ld + r];
+      x[r] = s;
+    }
+    __syncthreads();
+    for (int l = warp; l < cur; l += nw) {
+      double s = 0.0;
+      for (int r = lane; r < m; r += 32) s += V[l * ld + r] * x[r];
+      s = warp_sum(s);
+      if (lane == 0) coef[l] = s;
+    }
+    __syncthreads();
+    double n2 = 0.0;
+    for (int r = tid; r < m; r += blockDim.x) {
+      double s = x[r];
+      for (int l = 0; l < cur; ++l) s -= coef[l] * V[l * ld + r];
+      x[r] = s;
+      n2 += s * s;
+    }
+    const double nrm = sqrt(block_sum(n2, cred));
+    if (nrm > 0.1) {
+      for (int r = tid; r < m; r += blockDim.x) x[r] /= nrm;
+      ++cur;
+    }
+    __syncthreads();
+  }
+  if (cur < m && threadIdx.x == 0) atomicOr(status, (unsigned)ST_COMPLETION);
+}
+
 size_t geig_smem_bytes(int RC) {
   return sizeof(double) * (3 * RC * RC + 2 * RC) + 8 * ((jacobi_mixed_scratch_bytes(RC) + 7) / 8) +
          sizeof(int) * (RC + 16);
@@ -93,7 +182,7 @@ size_t geig_smem_bytes(int RC) {
 // parity with an FP64 SVD needs for eigenvectors whose eigenvalues sit near the rank
 // threshold (tau^2 lambda_1).  Writes M = V_keep diag(sigma_keep)^-1 (row-major,
 // slot sM), keep (per subdomain) and, for the augmentation, r_t.
-__global__ void __launch_bounds__(DD_THREADS) k_geig(OrthArgs a, const double* part,
+__global__ void __launch_bounds__(DD_THREADS, 1) k_geig(OrthArgs a, const double* part,
                                                      const int* cexp, int nchunk, double* sm,
                                                      int sM, int* keep_out) {
   extern __shared__ double shg[];
@@ -134,7 +223,36 @@ __global__ void __launch_bounds__(DD_THREADS) k_geig(OrthArgs a, const double* p
   if (emax == INT_MIN) emax = 0;
   if (!fin) atomicOr(a.status, (unsigned)ST_NONFINITE);
   __syncthreads();
-  jacobi_svd_mixed(Bc, Jc, m, RC, &iv[0], lam, X);
+  // G1 = X X^T by pivoted Cholesky (X in Jc, its k columns ordered by decreasing pivot);
+  // one-sided Jacobi on X then gives X J = W with orthogonal columns, G1 = W W^T: the
+  // normalised columns of W are eigenvectors of G1 (eigenvalues |w_j|^2), completed
+  // by unit vectors for the null space below the Cholesky threshold (1e-13 of the
+  // largest diagonal entry, far below the rank threshold tau^2).  Jacobi on the
+  // triangular factor needs a fraction of the sweeps Jacobi on G1 does (the graded
+  // columns are nearly orthogonal from the start).  Numerical rank above 32: Jacobi on
+  // G1 itself.
+  unsigned long long pmask = 0ull;
+  const int kr = pchol_cols(Bc, Jc, m, RC, 1e-13, &pmask);
+  if (kr <= 32) {
+    jacobi_rect_mixed(Jc, m, kr, RC, X);
+    for (int t = warp; t < kr; t += nwarps) {
+      double s2 = 0.0;
+      for (int i = lane; i < m; i += 32) s2 += Jc[t * RC + i] * Jc[t * RC + i];
+      s2 = warp_sum(s2);
+      const double f = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+      for (int i = lane; i < m; i += 32) Jc[t * RC + i] *= f;
+    }
+    __syncthreads();
+    complete_unit(Jc, m, kr, RC, pmask, lam, a.status);
+  } else {
+    for (int e = tid; e < RC * RC; e += blockDim.x) {
+      const int col = e / RC, row = e % RC;
+      Bc[e] = Gs[e];
+      Jc[e] = (row == col) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    jacobi_svd_mixed(Bc, Jc, m, RC, &iv[0], lam, X);
+  }
   // FP64 refinement (V is Jc: V_ij = Jc[j * RC + i]); T, S, R, E in the SVD scratch
   double* T = X;
   double* S = T + RC * RC;
