@@ -202,6 +202,7 @@ __device__ __forceinline__ float2 df_from_double(double x) {
   return make_float2(h, __double2float_rn(x - (double)h));
 }
 __device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ float2 z2f() { return make_float2(0.f, 0.f); }
 __device__ __forceinline__ float2 df_shfl_xor(unsigned mask, float2 v, int o) {
   return make_float2(__shfl_xor_sync(mask, v.x, o), __shfl_xor_sync(mask, v.y, o));
 }
@@ -590,7 +591,8 @@ __device__ __forceinline__ void jacobi_f32_cols(float* Bf, float* Jf, int nr, in
 // double-float rounding.
 template <int ROWS, bool WJ>
 __device__ __forceinline__ void jacobi_df_cols(float2* Bd, float2* Jd, int nr, int nc, int ld,
-                                               float tol, float stop, int max_sweeps) {
+                                               float tol, float stop, int max_sweeps,
+                                               float2* nrm_out = nullptr) {
   float2* xd = jw_buffer();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mm = nc + (nc & 1);
@@ -660,6 +662,13 @@ __device__ __forceinline__ void jacobi_df_cols(float2* Bd, float2* Jd, int nr, i
     }
     const float mrel = warp_max_t(lmax);
     if (mrel <= tol || mrel < stop) break;
+  }
+  if (nrm_out) {                                   // squared column norms afresh
+    float2 t = z2;
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) t = df_add(t, df_mul_sym(b[k], b[k]));
+    t = jw_sum(t, xd, &ph, JwAddDF());
+    if (warp == 0 && lane < nc) nrm_out[lane] = t;
   }
 #pragma unroll
   for (int k = 0; k < ROWS; ++k) {
@@ -807,60 +816,77 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
   __syncthreads();
 }
 
-// Orthogonalisation of the columns of the nr x nc (nr <= 64, nc <= 32) column-major
-// FP64 X (leading dimension ld) by one-sided Jacobi: on return X <- X J with J
-// orthogonal and the columns of X J orthogonal to double-float accuracy (~1e-13
-// relative).  FP32 sweeps on a power-of-two scaled copy accumulate J; J is made
-// orthogonal by two Newton-Schulz steps and X J formed in double-float; double-float
-// sweeps finish on the rotated columns (J itself is not needed further).  Scratch as
-// for jacobi_svd_mixed.
-__device__ __forceinline__ void jacobi_rect_mixed(double* X, int nr, int nc, int ld,
-                                                  void* scratch) {
+// Orthonormal basis of the column span of the nr x nc (nr <= 64, nc <= 32) column-major
+// FP64 X of full column rank (leading dimension ld), by one-sided Jacobi: on return the
+// columns of X are those of X J / |X J| (J orthogonal, X J with orthogonal columns), to
+// double-float accuracy (~1e-13).  FP32 sweeps on a power-of-two scaled copy accumulate
+// J; J is made orthogonal by two Newton-Schulz steps and X J formed in double-float;
+// double-float sweeps finish on the rotated columns (J itself is not needed further),
+// whose norms give the normalisation.  Loops put whole warps on rows (warp per column,
+// lane per row).  Scratch as for jacobi_svd_mixed.
+__device__ __forceinline__ void orth_cols_mixed(double* X, int nr, int nc, int ld, void* scratch) {
   float* B32 = reinterpret_cast<float*>(scratch);
   float* J32 = B32 + ld * ld;
   float* n32 = J32 + ld * ld;
   float2* T = reinterpret_cast<float2*>(B32);           // after the FP32 sweeps
   float2* Bd = reinterpret_cast<float2*>(n32 + 2 * ld);
   float2* Jd = Bd + ld * ld;
+  float2* nd = reinterpret_cast<float2*>(n32);          // nc squared norms
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (nr <= 0 || nc <= 0) return;
-  __shared__ double rred[40];
-  double mx = 0.0;
-  for (int c = 0; c < nc; ++c)
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) mx = fmax(mx, fabs(X[c * ld + r]));
-  mx = block_max(mx, rred);
-  if (!(mx > 0.0) || !isfinite(mx)) return;
+  __shared__ long long rbits[JW_WARPS + 1];
+  long long mb = 0;                                     // largest |x| by its bit pattern
+  for (int c = warp; c < nc; c += nw)
+    for (int r = lane; r < nr; r += 32)
+      mb = max(mb, __double_as_longlong(X[c * ld + r]) & 0x7fffffffffffffffll);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  if (lane == 0) rbits[warp] = mb;
+  __syncthreads();
+  mb = 0;
+  for (int w = 0; w < nw; ++w) mb = max(mb, rbits[w]);
+  const double mx = __longlong_as_double(mb);
+  if (!(mx > 0.0) || mb >= 0x7ff0000000000000ll) return;
   const int ex = ilogb(mx);
-  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
-    int c = e / ld, r = e % ld;
-    B32[e] = (c < nc && r < nr) ? (float)scalbn(X[e], -ex) : 0.f;
-    J32[e] = (c == r) ? 1.f : 0.f;
+  const double f = ldexp(1.0, -ex);
+  for (int c = warp; c < nc; c += nw) {
+    for (int r = lane; r < nr; r += 32) B32[c * ld + r] = (float)(X[c * ld + r] * f);
+    for (int r = lane; r < nc; r += 32) J32[c * ld + r] = (c == r) ? 1.f : 0.f;
   }
   __syncthreads();
   if (nr <= 32)
     jacobi_f32_cols<32 / JW_WARPS, true>(B32, J32, nr, nc, ld, 1e-6f, 1e-3f, 30);
   else
     jacobi_f32_cols<64 / JW_WARPS, true>(B32, J32, nr, nc, ld, 1e-6f, 1e-3f, 30);
-  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) Jd[e] = make_float2(J32[e], 0.f);
+  for (int c = warp; c < nc; c += nw)
+    for (int r = lane; r < nc; r += 32) Jd[c * ld + r] = make_float2(J32[c * ld + r], 0.f);
   __syncthreads();
   ns_orthogonalize_df(Jd, T, Bd, nc, ld);
-  for (int c = 0; c < nc; ++c)
-    for (int r = threadIdx.x; r < nr; r += blockDim.x)
-      T[c * ld + r] = df_from_double(scalbn(X[c * ld + r], -ex));
+  for (int c = warp; c < nc; c += nw)
+    for (int r = lane; r < nr; r += 32) T[c * ld + r] = df_from_double(X[c * ld + r] * f);
   __syncthreads();
-  for (int c = 0; c < nc; ++c)
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+  for (int c = warp; c < nc; c += nw)
+    for (int r = lane; r < nr; r += 32) {
       float2 x = make_float2(0.f, 0.f);
       for (int l = 0; l < nc; ++l) x = df_add(x, df_mul(T[l * ld + r], Jd[c * ld + l]));
       Bd[c * ld + r] = x;
     }
   __syncthreads();
   if (nr <= 32)
-    jacobi_df_cols<32 / JW_WARPS, false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10);
+    jacobi_df_cols<32 / JW_WARPS, false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10, nd);
   else
-    jacobi_df_cols<64 / JW_WARPS, false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10);
-  for (int c = 0; c < nc; ++c)
-    for (int r = threadIdx.x; r < nr; r += blockDim.x)
-      X[c * ld + r] = scalbn(df_to_double(Bd[c * ld + r]), ex);
+    jacobi_df_cols<64 / JW_WARPS, false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10, nd);
+  for (int c = warp; c < nc; c += nw) {
+    // 1 / |w_c| in double-float: one Newton step from rsqrtf
+    const float2 n2 = nd[c];
+    float2 y = z2f();
+    if (n2.x > 0.f) {
+      const float y0 = rsqrtf(n2.x);
+      const float2 h = df_add(make_float2(1.f, 0.f), df_neg(df_mulf(df_mulf(n2, y0), y0)));
+      y = df_add(make_float2(y0, 0.f), df_mulf(h, 0.5f * y0));
+    }
+    for (int r = lane; r < nr; r += 32) X[c * ld + r] = df_to_double(df_mul(Bd[c * ld + r], y));
+  }
   __syncthreads();
 }
 

@@ -78,35 +78,57 @@ __device__ int decide(const OrthArgs& a, int k, const double* sig, int nref, int
   return p;
 }
 
+// On this GPU one FP64 warp instruction holds the SM's FP64 pipe for ~18 cycles
+// whatever the number of active lanes, so the small FP64 algebra below keeps its FP64
+// instructions few and full: scalar FP64 work is done by one lane and broadcast, loops
+// map whole warps onto rows, and comparisons use the integer order of the bit
+// patterns (positive doubles order as their bits).
+
 // Pivoted Cholesky of the m x m (m <= 64) positive semidefinite A (column-major,
 // leading dimension ld; overwritten by its Schur complements): A = X X^T up to a
 // remainder whose diagonal is <= thr_rel times the largest diagonal entry of A.  X is
 // m x k, written to the first k columns of X with the rows in the original order
 // (column t is row t of the triangular factor in pivot order).  The pivot is the
-// largest remaining diagonal entry (lowest index on ties), found by every warp alike;
-// *piv gets the pivoted indices as a bit mask.  Block-wide; returns k.
+// largest remaining positive finite diagonal entry (lowest index on ties); *piv gets
+// the pivoted indices as a bit mask.  Block-wide; returns k.
 __device__ int pchol_cols(double* A, double* X, int m, int ld, double thr_rel,
                           unsigned long long* piv) {
+  __shared__ double pc[2];
+  __shared__ int pi[1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   unsigned long long done = 0ull;
-  double thr = 0.0;
+  long long thr_bits = 0;                          // lane 0 of warp 0 only
   int k = 0;
   for (; k < m; ++k) {
-    double best = -1.0;
-    int bi = m;
-    for (int i = lane; i < m; i += 32) {
-      const double d = ((done >> i) & 1ull) ? -1.0 : A[i * ld + i];
-      if (d > best) { best = d; bi = i; }
-    }
+    if (warp == 0) {
+      long long best = 0;
+      int bi = m;
+      for (int i = lane; i < m; i += 32) {
+        const long long b = __double_as_longlong(A[i * ld + i]);
+        const bool ok = !((done >> i) & 1ull) && b > 0 && b < 0x7ff0000000000000ll;
+        if (ok && b > best) { best = b; bi = i; }
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        if (k == 0) thr_bits = __double_as_longlong(thr_rel * __longlong_as_double(best));
+        const bool go = bi < m && best > thr_bits;
+        if (go) {
+          const double dv = __longlong_as_double(best), id = rsqrt(dv);
+          pc[0] = dv * id;
+          pc[1] = id;
+        }
+        pi[0] = go ? bi : -1;
+      }
     }
-    if (k == 0) thr = thr_rel * best;
-    if (!(best > 0.0) || !(best > thr)) break;
-    const double d = sqrt(best), id = 1.0 / d;
+    __syncthreads();
+    const int bi = pi[0];
+    if (bi < 0) break;
+    const double d = pc[0], id = pc[1];
     for (int i = tid; i < m; i += blockDim.x)
       X[k * ld + i] = ((done >> i) & 1ull) ? 0.0 : (i == bi ? d : A[bi * ld + i] * id);
     done |= 1ull << bi;
@@ -126,8 +148,8 @@ __device__ int pchol_cols(double* A, double* X, int m, int ld, double thr_rel,
 // Completes the orthonormal columns 0..cur-1 of the m x m column-major V (leading
 // dimension ld) to m columns with unit vectors, first those of the indices outside
 // mask (in index order), then the others: each candidate is Gram-Schmidt'd twice in
-// FP64 and accepted when its norm after that exceeds 0.1 (at every stage some unit
-// vector keeps at least m^-1/2).  coef: m doubles of shared scratch.
+// FP64 and accepted when its squared norm after that exceeds 0.01 (at every stage some
+// unit vector keeps at least 1/m).  coef: m doubles of shared scratch.
 __device__ void complete_unit(double* V, int m, int cur, int ld, unsigned long long mask,
                               double* coef, unsigned* status) {
   __shared__ double cred[40];
@@ -157,9 +179,9 @@ __device__ void complete_unit(double* V, int m, int cur, int ld, unsigned long l
       x[r] = s;
       n2 += s * s;
     }
-    const double nrm = sqrt(block_sum(n2, cred));
-    if (nrm > 0.1) {
-      for (int r = tid; r < m; r += blockDim.x) x[r] /= nrm;
+    n2 = block_sum(n2, cred);
+    if (n2 > 0.01) {
+      for (int r = tid; r < m; r += blockDim.x) x[r] *= rsqrt(n2);
       ++cur;
     }
     __syncthreads();
@@ -234,15 +256,7 @@ __global__ void __launch_bounds__(DD_THREADS, 1) k_geig(OrthArgs a, const double
   unsigned long long pmask = 0ull;
   const int kr = pchol_cols(Bc, Jc, m, RC, 1e-13, &pmask);
   if (kr <= 32) {
-    jacobi_rect_mixed(Jc, m, kr, RC, X);
-    for (int t = warp; t < kr; t += nwarps) {
-      double s2 = 0.0;
-      for (int i = lane; i < m; i += 32) s2 += Jc[t * RC + i] * Jc[t * RC + i];
-      s2 = warp_sum(s2);
-      const double f = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
-      for (int i = lane; i < m; i += 32) Jc[t * RC + i] *= f;
-    }
-    __syncthreads();
+    orth_cols_mixed(Jc, m, kr, RC, X);
     complete_unit(Jc, m, kr, RC, pmask, lam, a.status);
   } else {
     for (int e = tid; e < RC * RC; e += blockDim.x) {
@@ -253,7 +267,10 @@ __global__ void __launch_bounds__(DD_THREADS, 1) k_geig(OrthArgs a, const double
     __syncthreads();
     jacobi_svd_mixed(Bc, Jc, m, RC, &iv[0], lam, X);
   }
-  // FP64 refinement (V is Jc: V_ij = Jc[j * RC + i]); T, S, R, E in the SVD scratch
+  // FP64 refinement (V is Jc: V_ij = Jc[j * RC + i]); T, S, R, E in the SVD scratch.
+  // S and R are symmetric (upper triangles computed, mirrored); the norms that set the
+  // cluster threshold and the quotients of E (a first-order correction) are taken in
+  // FP32.
   double* T = X;
   double* S = T + RC * RC;
   double* R = S + RC * RC;
@@ -265,34 +282,39 @@ __global__ void __launch_bounds__(DD_THREADS, 1) k_geig(OrthArgs a, const double
     T[i * RC + j] = x;
   }
   __syncthreads();
-  double offn = 0.0, rn = 0.0, gn = 0.0;
-  for (int e = tid; e < m * m; e += blockDim.x) {            // S = V^T T, R = I - V^T V
-    const int i = e / m, j = e % m;
+  float offn = 0.f, rn = 0.f, gn = 0.f;
+  const int ntri = m * (m + 1) / 2;
+  for (int e = tid; e < ntri; e += blockDim.x) {             // S = V^T T, R = I - V^T V
+    int j = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+    j += (j + 1) * (j + 2) / 2 <= e;
+    j -= j * (j + 1) / 2 > e;
+    const int i = e - j * (j + 1) / 2;                       // i <= j
     double x = 0.0, y = 0.0;
     for (int l = 0; l < m; ++l) {
       x += Jc[i * RC + l] * T[l * RC + j];
       y += Jc[i * RC + l] * Jc[j * RC + l];
     }
-    S[i * RC + j] = x;
-    R[i * RC + j] = (i == j ? 1.0 : 0.0) - y;
-    if (i != j) offn += x * x;
-    rn += R[i * RC + j] * R[i * RC + j];
-    gn += Gs[i * RC + j] * Gs[i * RC + j];
+    const double rr = (i == j ? 1.0 : 0.0) - y;
+    S[i * RC + j] = x; S[j * RC + i] = x;
+    R[i * RC + j] = rr; R[j * RC + i] = rr;
+    const float xf = (float)x, rf = (float)rr, gf = (float)Gs[i * RC + j];
+    const float wgt = i == j ? 1.f : 2.f;
+    if (i != j) offn += 2.f * xf * xf;
+    rn += wgt * rf * rf;
+    gn += wgt * gf * gf;
   }
-  offn = block_sum(offn, rred);
-  rn = block_sum(rn, rred);
-  gn = block_sum(gn, rred);
-  const double delta = 2.0 * (sqrt(offn) + sqrt(gn) * sqrt(rn));   // cluster separation
+  offn = (float)block_sum((double)offn, rred);
+  rn = (float)block_sum((double)rn, rred);
+  gn = (float)block_sum((double)gn, rred);
+  const float delta = 2.f * (sqrtf(offn) + sqrtf(gn) * sqrtf(rn));   // cluster separation
   for (int i = tid; i < m; i += blockDim.x) lam[i] = S[i * RC + i] / (1.0 - R[i * RC + i]);
   __syncthreads();
   for (int e = tid; e < m * m; e += blockDim.x) {            // E (into T)
     const int i = e / m, j = e % m;
-    double x;
-    if (i == j) {
-      x = 0.5 * R[i * RC + i];
-    } else {
-      const double d = lam[j] - lam[i];
-      x = fabs(d) > delta ? (S[i * RC + j] + lam[j] * R[i * RC + j]) / d : 0.5 * R[i * RC + j];
+    double x = 0.5 * R[i * RC + j];
+    if (i != j) {
+      const float d = (float)(lam[j] - lam[i]);
+      if (fabsf(d) > delta) x = (double)__fdividef((float)(S[i * RC + j] + lam[j] * R[i * RC + j]), d);
     }
     T[i * RC + j] = x;
   }
