@@ -138,10 +138,17 @@ struct GramArgs {
   const double* wrow;   // row weights (indexed like a per-row vector of the same layout), or null
   double* part; int nchunk;
   int* cexp;            // A^T A only (Bm == A): chunk exponents, see k_gram
+  int sym;              // A^T W A: the upper triangle is computed and mirrored
 };
-__global__ void k_gram(Geo g, GramArgs a) {
-  __shared__ double red[40];
+// Chunked Gram A^T diag(w) B: block (c, k) sums over row chunk c of subdomain k.  Each
+// thread owns whole (i, j) pairs, enumerated densely (the upper triangle only for a
+// symmetric product) so that every lane of an FP64 instruction does useful work; the
+// RC x RC partial is assembled in shared memory and stored whole (zeros outside).
+__global__ void __launch_bounds__(DD_THREADS) k_gram(Geo g, GramArgs a) {
+  extern __shared__ double gt[];
+  __shared__ long long mred[DD_THREADS / 32];
   const int k = blockIdx.y, c = blockIdx.x, RC = g.RC;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows = a.spatial ? g.N[k] : g.n;
   const long rb = a.spatial ? (long)g.rowoff[k] : (long)k * g.n;
   const long rbB = a.b_per_sub ? rb : 0;
@@ -151,37 +158,63 @@ __global__ void k_gram(Geo g, GramArgs a) {
   double* out = a.part + ((long)k * a.nchunk + c) * RC * RC;
   // A^T A squares the entries: a chunk whose largest |entry| 2^e is far from 1
   // (|e| > 400) is scaled by 2^-e first, so that tiny data keep their significant
-  // bits (e is stored; INT_MIN marks a chunk below 2^-1000, taken as zero)
+  // bits (e is stored; INT_MIN marks a chunk below 2^-1000, taken as zero).  The
+  // largest |entry| is found on the integer order of the bit patterns (NaN ignored).
   int ex = 0;
   bool scl = false, zero = false;
   if (a.cexp) {
-    double mx = 0.0;
-    for (long e = threadIdx.x; e < (long)(i1 - i0) * na; e += blockDim.x)
-      mx = fmax(mx, fabs(a.A[(rb + i0 + e / na) * a.lda + e % na]));
-    mx = block_max(mx, red);
+    long long mb = 0;
+    for (int row = i0 + warp; row < i1; row += DD_THREADS / 32)
+      for (int l = lane; l < na; l += 32) {
+        const long long b = __double_as_longlong(a.A[(rb + row) * a.lda + l]) & 0x7fffffffffffffffll;
+        if (b <= 0x7ff0000000000000ll) mb = max(mb, b);
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    if (lane == 0) mred[warp] = mb;
+    __syncthreads();
+    mb = 0;
+    for (int w = 0; w < DD_THREADS / 32; ++w) mb = max(mb, mred[w]);
+    const double mx = __longlong_as_double(mb);
     const int e0 = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) : 0;
     zero = !(mx > 0.0) || e0 < -1000;
     scl = !zero && (e0 < -400 || e0 > 400);
     ex = scl ? e0 : 0;
-    if (threadIdx.x == 0) a.cexp[(long)k * a.nchunk + c] = zero ? INT_MIN : ex;
+    if (tid == 0) a.cexp[(long)k * a.nchunk + c] = zero ? INT_MIN : ex;
   }
   const double f = scl ? ldexp(1.0, -ex) : 1.0;
-  for (int o = threadIdx.x; o < RC * RC; o += blockDim.x) {
-    const int i = o / RC, j = o % RC;
-    double s = 0.0;
-    if (i < na && j < nbc && !zero) {
-      if (scl) {
-        for (int row = i0; row < i1; ++row)
-          s += (a.A[(rb + row) * a.lda + i] * f) * (a.Bm[(rbB + row) * a.ldb + j] * f);
-      } else {
-        for (int row = i0; row < i1; ++row) {
-          const double wv = a.wrow ? a.wrow[rb + row] : 1.0;
-          s += a.A[(rb + row) * a.lda + i] * wv * a.Bm[(rbB + row) * a.ldb + j];
-        }
-      }
+  for (int e = tid; e < RC * RC; e += DD_THREADS) gt[e] = 0.0;
+  __syncthreads();
+  const int npair = zero ? 0 : (a.sym ? na * (na + 1) / 2 : na * nbc);
+  for (int p = tid; p < npair; p += DD_THREADS) {
+    int i, j;
+    if (a.sym) {                                   // p -> (i <= j)
+      j = (int)((sqrtf(8.f * p + 1.f) - 1.f) * 0.5f);
+      j += (j + 1) * (j + 2) / 2 <= p;
+      j -= j * (j + 1) / 2 > p;
+      i = p - j * (j + 1) / 2;
+    } else {
+      i = p / nbc;
+      j = p - i * nbc;
     }
-    out[o] = s;
+    const double* Ac = a.A + rb * a.lda + i;
+    const double* Bc = a.Bm + rbB * a.ldb + j;
+    double s0 = 0.0;
+    if (scl) {
+      for (int row = i0; row < i1; ++row)
+        s0 += (Ac[(long)row * a.lda] * f) * (Bc[(long)row * a.ldb] * f);
+    } else if (a.wrow) {
+      for (int row = i0; row < i1; ++row)
+        s0 += Ac[(long)row * a.lda] * a.wrow[rb + row] * Bc[(long)row * a.ldb];
+    } else {
+      for (int row = i0; row < i1; ++row) s0 += Ac[(long)row * a.lda] * Bc[(long)row * a.ldb];
+    }
+    const double sv = s0;
+    gt[i * RC + j] = sv;
+    if (a.sym) gt[j * RC + i] = sv;
   }
+  __syncthreads();
+  for (int e = tid; e < RC * RC; e += DD_THREADS) out[e] = gt[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -273,28 +306,58 @@ struct TallArgs {
   const int* ncols; int ncols_fix;
   double* Y; int ldy;
 };
-__global__ void k_tall(Geo g, TallArgs a, double* smbase) {
+#define TALL_ROWS 32
+size_t tall_smem(int RC, int ldy) {
+  return sizeof(double) * ((size_t)RC * RC + 4 + TALL_ROWS * (RC | 1) + TALL_ROWS * (ldy | 1));
+}
+// Y = A M (rows of subdomain k; columns nc..ldy-1 of Y set to zero).  A block takes
+// TALL_ROWS rows: the rows of A, M and the output tile live in shared memory (loads
+// and stores coalesced); lane = row, each warp takes tiles of 4 output columns, so
+// every lane of an FP64 instruction does useful work.
+__global__ void __launch_bounds__(DD_THREADS) k_tall(Geo g, TallArgs a, double* smbase) {
   extern __shared__ double sh[];
   const int k = blockIdx.y, RC = g.RC;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows = a.spatial ? g.N[k] : g.n;
   const long rb = a.spatial ? (long)g.rowoff[k] : (long)k * g.n;
   const int ni = a.ninner ? a.ninner[k] : a.ninner_fix;
   const int nc = a.ncols ? a.ncols[k] : a.ncols_fix;
+  const int r0 = blockIdx.x * TALL_ROWS;
+  const int nrow = min(TALL_ROWS, rows - r0);
+  if (nrow <= 0) return;
   const double* Bk = (a.bsmall >= 0) ? smbase + ((long)k * NSMALL + a.bsmall) * RC * RC
                                      : a.Bm + (long)k * RC * RC;
-  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) sh[e] = Bk[e];
+  const int SA = ni | 1, SY = a.ldy | 1;
+  double* Ms = sh;                                  // RC x RC (+4 so a tile never reads past it)
+  double* As = Ms + RC * RC + 4;                    // TALL_ROWS x SA
+  double* Ys = As + TALL_ROWS * (RC | 1);           // TALL_ROWS x SY
+  for (int e = tid; e < RC * RC + 4; e += DD_THREADS) Ms[e] = e < ni * RC ? Bk[e] : 0.0;
+  for (int r = warp; r < nrow; r += DD_THREADS / 32)
+    for (int l = lane; l < ni; l += 32) As[r * SA + l] = a.A[(rb + r0 + r) * a.lda + l];
   __syncthreads();
-  const int r0 = blockIdx.x * 64;
-  for (int e = threadIdx.x; e < 64 * a.ldy; e += blockDim.x) {
-    int row = r0 + e / a.ldy, j = e % a.ldy;
-    if (row >= rows) continue;
-    double s = 0.0;
-    if (j < nc) {
-      const double* Ar = a.A + (rb + row) * a.lda;
-      for (int l = 0; l < ni; ++l) s += Ar[l] * sh[l * RC + j];
+  const int ntile = (a.ldy + 3) >> 2;
+  for (int t = warp; t < ntile; t += DD_THREADS / 32) {
+    const int j0 = t * 4;
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    if (j0 < nc && lane < nrow) {
+      const double* ar = As + lane * SA;
+      for (int l = 0; l < ni; ++l) {
+        const double x = ar[l];
+        const double* mr = Ms + l * RC + j0;
+        c0 += x * mr[0]; c1 += x * mr[1]; c2 += x * mr[2]; c3 += x * mr[3];
+      }
     }
-    a.Y[(rb + row) * a.ldy + j] = s;
+    if (lane < nrow) {
+      double* yr = Ys + lane * SY + j0;
+      if (j0 < a.ldy) yr[0] = j0 < nc ? c0 : 0.0;
+      if (j0 + 1 < a.ldy) yr[1] = j0 + 1 < nc ? c1 : 0.0;
+      if (j0 + 2 < a.ldy) yr[2] = j0 + 2 < nc ? c2 : 0.0;
+      if (j0 + 3 < a.ldy) yr[3] = j0 + 3 < nc ? c3 : 0.0;
+    }
   }
+  __syncthreads();
+  for (int r = warp; r < nrow; r += DD_THREADS / 32)
+    for (int j = lane; j < a.ldy; j += 32) a.Y[(rb + r0 + r) * a.ldy + j] = Ys[r * SY + j];
 }
 
 // ---------------------------------------------------------------------------
@@ -1138,7 +1201,7 @@ cudaError_t phase_init() {
                            (int)(sizeof(double) * 3 * RC * RC));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_tall, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * RC * RC));
+                           (int)tall_smem(RC, RC));
   return e;
 }
 
@@ -1155,8 +1218,9 @@ static void gram(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spat
   a.Bm = Bm; a.ldb = ldb; a.bcnt = bcnt; a.bfix = bfix; a.b_per_sub = b_per_sub;
   a.wrow = wrow; a.part = B.part; a.nchunk = spatial ? P.nchunk_sp : P.nchunk_ang;
   a.cexp = nullptr;
+  a.sym = A == Bm && lda == ldb && acnt == bcnt && afix == bfix && b_per_sub;
   pbeg(st, KS_GRAM);
-  k_gram<<<dim3(a.nchunk, P.g.nsub), DD_THREADS, 0, st>>>(P.g, a);
+  k_gram<<<dim3(a.nchunk, P.g.nsub), DD_THREADS, sizeof(double) * P.g.RC * P.g.RC, st>>>(P.g, a);
   pend(st);
   Dst d;
   d.idx[0] = dst_small;
@@ -1174,8 +1238,9 @@ static int gram_partials(const Problem& P, const PhaseBufs& B, cudaStream_t st, 
   a.Bm = A; a.ldb = lda; a.bcnt = acnt; a.bfix = 0; a.b_per_sub = 1;
   a.wrow = nullptr; a.part = B.part; a.nchunk = spatial ? P.nchunk_sp : P.nchunk_ang;
   a.cexp = cexp;
+  a.sym = 1;
   pbeg(st, KS_GRAM);
-  k_gram<<<dim3(a.nchunk, P.g.nsub), DD_THREADS, 0, st>>>(P.g, a);
+  k_gram<<<dim3(a.nchunk, P.g.nsub), DD_THREADS, sizeof(double) * P.g.RC * P.g.RC, st>>>(P.g, a);
   pend(st);
   return a.nchunk;
 }
@@ -1187,9 +1252,9 @@ static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spat
   a.spatial = spatial; a.A = A; a.lda = lda; a.ninner = ninner; a.ninner_fix = ninner_fix;
   a.Bm = Bm; a.bsmall = bsmall; a.ncols = ncols; a.ncols_fix = ncols_fix; a.Y = Y; a.ldy = ldy;
   const int rows = spatial ? P.maxN : P.g.n;
-  dim3 grid((rows + 63) / 64, P.g.nsub);
+  dim3 grid((rows + TALL_ROWS - 1) / TALL_ROWS, P.g.nsub);
   pbeg(st, KS_TALL);
-  k_tall<<<grid, DD_THREADS, sizeof(double) * P.g.RC * P.g.RC, st>>>(P.g, a, B.sm);
+  k_tall<<<grid, DD_THREADS, tall_smem(P.g.RC, ldy), st>>>(P.g, a, B.sm);
   pend(st);
 }
 
@@ -1369,9 +1434,9 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
     GramArgs a;
     a.spatial = 1; a.A = B.Xo; a.lda = RC; a.acnt = B.rc; a.afix = 0;
     a.Bm = P.sQ; a.ldb = 1; a.bcnt = nullptr; a.bfix = 1; a.b_per_sub = 1;
-    a.wrow = nullptr; a.part = B.part; a.nchunk = P.nchunk_sp; a.cexp = nullptr;
+    a.wrow = nullptr; a.part = B.part; a.nchunk = P.nchunk_sp; a.cexp = nullptr; a.sym = 0;
     pbeg(st, KS_GRAM);
-    k_gram<<<dim3(a.nchunk, nsub), DD_THREADS, 0, st>>>(g, a);
+    k_gram<<<dim3(a.nchunk, nsub), DD_THREADS, sizeof(double) * RC * RC, st>>>(g, a);
     pend(st);
     Dst d;
     d.idx[0] = SM_UB;   // scratch: column 0 holds q
