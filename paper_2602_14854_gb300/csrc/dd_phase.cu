@@ -86,8 +86,14 @@ __global__ void k_build_L0(Geo g, const double* V, const double* S, const int* r
 //   C = Vh^T diag(Om) Vh, Mout_lo = Vh^T diag(Om<0) Vh, Mout_hi = Vh^T diag(Om>=0) Vh,
 //   M = Vt^T Vh, Min_lo = Vt_lo^T diag(Om>=0) Vh, Min_hi = Vt_hi^T diag(Om<0) Vh
 // ---------------------------------------------------------------------------
-__global__ void k_ang_coeffs(Geo g, const double* om, const double* Vh, const double* V,
-                             const int* r, const int* rt, int axis, int nchunk, double* part) {
+__global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* om,
+                                                            const double* Vh, const double* V,
+                                                            const int* r, const int* rt, int axis,
+                                                            int nchunk, double* part) {
+  // Work items, enumerated densely so that every lane of an FP64 instruction is used:
+  // the rt(rt+1)/2 pairs i <= j of the three symmetric blocks C, Mout_lo, Mout_hi (one
+  // product v_i v_j per direction feeds all three), then the pairs of M, Min_lo and
+  // Min_hi.  The sign of Om is taken from its bits (Om < 0 <=> sign bit set, not -0).
   const int k = blockIdx.y, c = blockIdx.x, RC = g.RC, n = g.n;
   const int ch = (n + nchunk - 1) / nchunk;
   const int q0 = c * ch, q1 = min(n, q0 + ch);
@@ -98,20 +104,44 @@ __global__ void k_ang_coeffs(Geo g, const double* om, const double* Vh, const do
   const double* Vlo = V + (long)(lo >= 0 ? lo : 0) * n * RC;
   const double* Vhi = V + (long)(hi >= 0 ? hi : 0) * n * RC;
   double* out = part + ((long)k * nchunk + c) * 6 * RC * RC;
-  for (int o = threadIdx.x; o < 6 * RC * RC; o += blockDim.x) {
-    const int blk = o / (RC * RC), e = o % (RC * RC), i = e / RC, j = e % RC;
-    double s = 0.0;
-    if (j < rtk) {
-      switch (blk) {
-        case 0: if (i < rtk) for (int q = q0; q < q1; ++q) s += om[q] * Vhk[q * RC + i] * Vhk[q * RC + j]; break;
-        case 1: if (i < rtk) for (int q = q0; q < q1; ++q) if (om[q] < 0.0) s += Vhk[q * RC + i] * Vhk[q * RC + j]; break;
-        case 2: if (i < rtk) for (int q = q0; q < q1; ++q) if (om[q] >= 0.0) s += Vhk[q * RC + i] * Vhk[q * RC + j]; break;
-        case 3: if (i < rk) for (int q = q0; q < q1; ++q) s += Vk[q * RC + i] * Vhk[q * RC + j]; break;
-        case 4: if (i < rlo) for (int q = q0; q < q1; ++q) if (om[q] >= 0.0) s += Vlo[q * RC + i] * Vhk[q * RC + j]; break;
-        case 5: if (i < rhi) for (int q = q0; q < q1; ++q) if (om[q] < 0.0) s += Vhi[q * RC + i] * Vhk[q * RC + j]; break;
+  for (int e = threadIdx.x; e < 6 * RC * RC; e += blockDim.x) out[e] = 0.0;
+  __syncthreads();
+  const int nsym = rtk * (rtk + 1) / 2;
+  const int n3 = rk * rtk, n4 = rlo * rtk, n5 = rhi * rtk;
+  const int nwork = nsym + n3 + n4 + n5;
+  for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+    if (w < nsym) {
+      int j = (int)((sqrtf(8.f * w + 1.f) - 1.f) * 0.5f);
+      j += (j + 1) * (j + 2) / 2 <= w;
+      j -= j * (j + 1) / 2 > w;
+      const int i = w - j * (j + 1) / 2;
+      double sc = 0.0, sl = 0.0, sh = 0.0;
+      for (int q = q0; q < q1; ++q) {
+        const double o = om[q];
+        const long long ob = __double_as_longlong(o);
+        const double t = Vhk[q * RC + i] * Vhk[q * RC + j];
+        sc += o * t;
+        if (ob < 0 && ob != (long long)0x8000000000000000ull) sl += t; else sh += t;
       }
+      out[i * RC + j] = sc; out[j * RC + i] = sc;
+      out[RC * RC + i * RC + j] = sl; out[RC * RC + j * RC + i] = sl;
+      out[2 * RC * RC + i * RC + j] = sh; out[2 * RC * RC + j * RC + i] = sh;
+    } else {
+      int u = w - nsym, blk;
+      const double* Va;
+      int sel;                                     // 0 all directions, 1 Om >= 0, 2 Om < 0
+      if (u < n3) { blk = 3; Va = Vk; sel = 0; }
+      else if ((u -= n3) < n4) { blk = 4; Va = Vlo; sel = 1; }
+      else { u -= n4; blk = 5; Va = Vhi; sel = 2; }
+      const int i = u / rtk, j = u - i * rtk;
+      double s = 0.0;
+      for (int q = q0; q < q1; ++q) {
+        const long long ob = __double_as_longlong(om[q]);
+        const bool ng = ob < 0 && ob != (long long)0x8000000000000000ull;
+        if (sel == 0 || (sel == 1 && !ng) || (sel == 2 && ng)) s += Va[q * RC + i] * Vhk[q * RC + j];
+      }
+      out[blk * RC * RC + i * RC + j] = s;
     }
-    out[o] = s;
   }
 }
 
@@ -498,10 +528,15 @@ __global__ void k_sp_coeffs(Problem P, PhaseBufs B, int axis) {
   const double* K = B.K + (long)P.g.rowoff[k] * RC;
   const double* Kb = B.Kb + (long)k * 2 * P.maxlines * RC;
   double* out = B.part + ((long)k * nchunk + c) * 4 * RC * RC;
-  for (int o = threadIdx.x; o < 4 * RC * RC; o += blockDim.x) {
-    const int blk = o / (RC * RC), e = o % (RC * RC), i = e / RC, j = e % RC;
+  // work items (block, i, j) enumerated densely over i, j < rt, so that every lane of
+  // an FP64 instruction is used; the partial is zeroed first
+  for (int o = threadIdx.x; o < 4 * RC * RC; o += blockDim.x) out[o] = 0.0;
+  __syncthreads();
+  const int rt2 = rt * rt;
+  for (int w = threadIdx.x; w < 4 * rt2; w += blockDim.x) {
+    const int blk = w / rt2, e = w - blk * rt2, i = e / rt, j = e - i * rt;
     double s = 0.0;
-    if (i < rt && j < rt) {
+    {
       if (blk == 0) {
         for (int line = l0; line < l1; ++line)
           for (int pos = 0, cell = line * L.stride_line; pos < L.len; ++pos, cell += L.stride_pos)
@@ -520,7 +555,7 @@ __global__ void k_sp_coeffs(Problem P, PhaseBufs B, int axis) {
                Kb[((long)P.maxlines + line) * RC + j];
       }
     }
-    out[o] = s;
+    out[blk * RC * RC + i * RC + j] = s;
   }
 }
 
@@ -1316,15 +1351,17 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   pend(st);
   // 2. angular Galerkin coefficients, boundary masses
   pbeg(st, KS_ANG_COEFFS);
-  k_ang_coeffs<<<dim3(P.nchunk_ang, nsub), DD_THREADS, 0, st>>>(
-      g, axis == 0 ? P.ox : P.oy, B.Vh, B.V, B.r, B.rt, axis, P.nchunk_ang, B.part);
+  // twice the angular chunks (more blocks than SMs), as far as the partial buffer holds
+  const int nch_ac = std::min(2 * P.nchunk_ang, std::max(P.nchunk_sp, P.nchunk_ang));
+  k_ang_coeffs<<<dim3(nch_ac, nsub), DD_THREADS, 0, st>>>(
+      g, axis == 0 ? P.ox : P.oy, B.Vh, B.V, B.r, B.rt, axis, nch_ac, B.part);
   pend(st);
   {
     Dst d;
     d.idx[0] = SM_C; d.idx[1] = SM_MOUT_LO; d.idx[2] = SM_MOUT_HI;
     d.idx[3] = SM_M; d.idx[4] = SM_MIN_LO; d.idx[5] = SM_MIN_HI;
     pbeg(st, KS_REDUCE);
-    k_reduce<<<reduce_grid(g, 6), DD_THREADS, 0, st>>>(B.part, P.nchunk_ang, 6, d, B.sm, RC);
+    k_reduce<<<reduce_grid(g, 6), DD_THREADS, 0, st>>>(B.part, nch_ac, 6, d, B.sm, RC);
     pend(st);
   }
   // 3. S M products, eigen-split of C
