@@ -144,9 +144,10 @@ def kernel_work(name, wl, rt, rs):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
-# capture summarised in profiles/k_geig_k_kstep_adv_pointsource_full.md; None where no
-# capture of the kernel as it stands exists.
-NCU_TRAFFIC = {"k_geig": 0.277e6, "k_kstep_adv": 3.88e6}
+# captures summarised in profiles/k_geig_k_gram_k_tall_pointsource_full.md and
+# profiles/k_kstep_adv_pointsource_full.md; None where no capture of the kernel as it
+# stands exists.
+NCU_TRAFFIC = {"k_geig": 0.660e6, "k_kstep_adv": 3.88e6, "k_gram": 3.18e6, "k_tall": 3.21e6}
 
 
 def run_ours(args, torch):
@@ -270,6 +271,7 @@ def run_ours(args, torch):
             evm[i][1].record(stream)
         torch.cuda.synchronize()
         t_m = sum(a.elapsed_time(b) for a, b in evm) / 1e3
+        prof_m = sm_.profile(4)
         sm_.close()
         err_m = None
         if os.path.exists(GOLDEN):
@@ -280,6 +282,8 @@ def run_ours(args, torch):
         mixed = {"value": units * args.steps * ws / t_m, "unit": UNIT,
                  "ms_per_step": t_m / args.steps * 1e3, "flux_rel_l2_vs_oracle": err_m,
                  "speedup_vs_fp64": t_ours / t_m,
+                 "kernels_ms_per_step": {k: round(v[0] / 4.0, 4) for k, v in
+                                         sorted(prof_m.items(), key=lambda kv: -kv[1][0])},
                  "arithmetic": "FP32: stencil, K/L/collision ODE increments; FP64: updates, "
                                "orthonormalisations, small eigen/SVD problems, reductions, "
                                "storage"}
