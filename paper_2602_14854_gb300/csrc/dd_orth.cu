@@ -399,24 +399,35 @@ __global__ void __launch_bounds__(DD_THREADS) k_chol_inv(OrthArgs a, const doubl
   const bool ok = isfinite(err) && err < 0.9;
   int iters = 0;
   for (double e = err; e > 1e-16 && iters < 12; e = 0.75 * e * e) ++iters;
+  // Y, Z and T are polynomials in G2: symmetric and commuting, so every product is
+  // symmetric; only its upper triangle is computed (pairs enumerated densely) and mirrored.
+  const int ntri = q * (q + 1) / 2;
   if (ok) {
     for (int it = 0; it < iters; ++it) {
-      for (int e = tid; e < q * q; e += blockDim.x) {          // T = (3I - Z Y) / 2
-        const int i = e / q, j = e % q;
+      for (int p = tid; p < ntri; p += blockDim.x) {            // T = (3I - Z Y) / 2
+        int j = (int)((sqrtf(8.f * p + 1.f) - 1.f) * 0.5f);
+        j += (j + 1) * (j + 2) / 2 <= p;
+        j -= j * (j + 1) / 2 > p;
+        const int i = p - j * (j + 1) / 2;
         float2 x = make_float2(0.f, 0.f);
         for (int l = 0; l < q; ++l) x = df_add(x, df_mul(Z[i * RC + l], Y[l * RC + j]));
-        T[i * RC + j] = df_mulf(df_add(make_float2(i == j ? 3.f : 0.f, 0.f), df_neg(x)), 0.5f);
+        const float2 t = df_mulf(df_add(make_float2(i == j ? 3.f : 0.f, 0.f), df_neg(x)), 0.5f);
+        T[i * RC + j] = t;
+        T[j * RC + i] = t;
       }
       __syncthreads();
-      for (int e = tid; e < q * q; e += blockDim.x) {          // W1 = Y T, W2 = T Z
-        const int i = e / q, j = e % q;
+      for (int p = tid; p < ntri; p += blockDim.x) {            // W1 = Y T, W2 = T Z
+        int j = (int)((sqrtf(8.f * p + 1.f) - 1.f) * 0.5f);
+        j += (j + 1) * (j + 2) / 2 <= p;
+        j -= j * (j + 1) / 2 > p;
+        const int i = p - j * (j + 1) / 2;
         float2 x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
         for (int l = 0; l < q; ++l) {
           x = df_add(x, df_mul(Y[i * RC + l], T[l * RC + j]));
           y = df_add(y, df_mul(T[i * RC + l], Z[l * RC + j]));
         }
-        W1[i * RC + j] = x;
-        W2[i * RC + j] = y;
+        W1[i * RC + j] = x; W1[j * RC + i] = x;
+        W2[i * RC + j] = y; W2[j * RC + i] = y;
       }
       __syncthreads();
       float2* tmp = Y; Y = W1; W1 = tmp;

@@ -393,29 +393,36 @@ __global__ void __launch_bounds__(DD_THREADS) k_tall(Geo g, TallArgs a, double* 
 // ---------------------------------------------------------------------------
 // ghost rows (Eq. (generate_Kboundary)): K^b_lo = (X_lo S_lo)|face Min_lo + K|own lo face Mout_lo
 // ---------------------------------------------------------------------------
-__global__ void k_ghost(Problem P, PhaseBufs B, int axis) {
-  const int k = blockIdx.x, RC = P.g.RC;
+// One warp per (side, line) ghost row, lane = output column t: the blocks of a
+// subdomain split its 2 * nlines rows, so every SM takes part.
+__global__ void __launch_bounds__(DD_THREADS) k_ghost(Problem P, PhaseBufs B, int axis) {
+  const int k = blockIdx.y, RC = P.g.RC;
   const Lines L = lines_of(P.g, k, axis);
   const int rt = B.rt[k];
-  for (int e = threadIdx.x; e < 2 * L.nlines * RC; e += blockDim.x) {
-    const int side = e / (L.nlines * RC), line = (e / RC) % L.nlines, t = e % RC;
+  const int row = blockIdx.x * (DD_THREADS / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= 2 * L.nlines) return;
+  const int side = row >= L.nlines, line = side ? row - L.nlines : row;
+  const int nbk = P.g.nb[k * 4 + 2 * axis + side];
+  const double* Mout = SMB(B, P, k, side == 0 ? SM_MOUT_LO : SM_MOUT_HI);
+  const int own = cell_of(L, line, side == 0 ? 0 : L.len - 1);
+  const double* Kr = B.K + ((long)P.g.rowoff[k] + own) * RC;
+  const double* Xr = nullptr;
+  const double* Bb = SMB(B, P, k, side == 0 ? SM_B_LO : SM_B_HI);
+  int rn = 0;
+  if (nbk >= 0) {
+    const Lines Ln = lines_of(P.g, nbk, axis);
+    const int cell = cell_of(Ln, line, side == 0 ? Ln.len - 1 : 0);
+    Xr = B.X + ((long)P.g.rowoff[nbk] + cell) * RC;
+    rn = B.r[nbk];
+  }
+  double* out = B.Kb + (((long)k * 2 + side) * P.maxlines + line) * RC;
+  for (int t = lane; t < RC; t += 32) {
     double s = 0.0;
     if (t < rt) {
-      const int nbk = P.g.nb[k * 4 + 2 * axis + side];
-      const double* Mout = SMB(B, P, k, side == 0 ? SM_MOUT_LO : SM_MOUT_HI);
-      const int own = cell_of(L, line, side == 0 ? 0 : L.len - 1);
-      const double* Kr = B.K + ((long)P.g.rowoff[k] + own) * RC;
       for (int u = 0; u < rt; ++u) s += Kr[u] * Mout[u * RC + t];
-      if (nbk >= 0) {
-        const Lines Ln = lines_of(P.g, nbk, axis);
-        const int cell = cell_of(Ln, line, side == 0 ? Ln.len - 1 : 0);
-        const double* Xr = B.X + ((long)P.g.rowoff[nbk] + cell) * RC;
-        const double* Bb = SMB(B, P, k, side == 0 ? SM_B_LO : SM_B_HI);
-        const int rn = B.r[nbk];
-        for (int u = 0; u < rn; ++u) s += Xr[u] * Bb[u * RC + t];
-      }
+      for (int u = 0; u < rn; ++u) s += Xr[u] * Bb[u * RC + t];
     }
-    B.Kb[(((long)k * 2 + side) * P.maxlines + line) * RC + t] = s;
+    out[t] = s;
   }
 }
 
@@ -1372,7 +1379,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   tall(P, B, st, 1, B.X, RC, B.r, 0, nullptr, SM_B, B.rt, 0, B.K, RC);
   // 5. boundary data
   pbeg(st, KS_GHOST);
-  k_ghost<<<nsub, DD_THREADS, 0, st>>>(P, B, axis);
+  k_ghost<<<dim3((2 * P.maxlines + DD_THREADS / 32 - 1) / (DD_THREADS / 32), nsub), DD_THREADS, 0, st>>>(P, B, axis);
   pend(st);
   // 6. K-step
   {
