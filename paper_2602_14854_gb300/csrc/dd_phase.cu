@@ -569,70 +569,83 @@ __global__ void k_sp_coeffs(Problem P, PhaseBufs B, int axis) {
 // ---------------------------------------------------------------------------
 // S-step of the advection (small, one CTA per subdomain), and the L-step matrices
 // ---------------------------------------------------------------------------
-__global__ void k_sstep_adv(Problem P, PhaseBufs B, int axis) {
+// One RK stage per launch, rows of each subdomain split over CL blocks: the FP64
+// products of this r_t x r_t ODE would otherwise run on one SM per subdomain.  Block
+// (k, c) takes rows [c*rpb, (c+1)*rpb): it reads the full stage value of S, computes its
+// rows of U1 = T S + G_lo, U2 = T^T S + G_hi and F = coef (S |C| - U1 C+ + U2 C-),
+// accumulates Ac = sum_s b_s F_s and writes its rows of the next stage value
+// S1 + a_{s+1} dt F (at the last stage S2 = S1 + dt Ac and the L-step matrices).  The
+// stage values alternate between the small slots S3T and UB, and Ac lives in VB: those
+// are free between the QR of K and the QR of L.  Every element is computed in the same
+// order as by a single block, so the result does not depend on CL.
+size_t sstep_smem(int RC) { return sizeof(double) * 3 * (size_t)RC * RC; }
+
+__global__ void __launch_bounds__(DD_THREADS) k_sstep_adv(Problem P, PhaseBufs B, int axis,
+                                                          int s, int CL) {
   extern __shared__ double sh[];
-  const int k = blockIdx.x, RC = P.g.RC;
+  const int k = blockIdx.x / CL, cr = blockIdx.x - k * CL, RC = P.g.RC;
   const int rt = B.rt[k];
-  double* S0 = sh;
-  double* Ss = S0 + RC * RC;
-  double* Ac = Ss + RC * RC;
-  double* U1 = Ac + RC * RC;
-  double* U2 = U1 + RC * RC;
-  double* F = U2 + RC * RC;
+  const int rpb = (rt + CL - 1) / CL;
+  const int i0 = min(rt, cr * rpb), i1 = min(rt, i0 + rpb), nr = i1 - i0;
+  const int nst = P.integrator == 1 ? 4 : 1;
+  double* Ss = sh;                                   // full stage value (rows < rt)
+  double* U1 = Ss + RC * RC;                         // rows i0..i1 (local index)
+  double* U2 = U1 + rpb * RC;
+  const double* S1 = SMB(B, P, k, SM_S1);
+  const double* Sin = s == 0 ? S1 : SMB(B, P, k, (s & 1) ? SM_S3T : SM_UB);
+  double* Sout = SMB(B, P, k, (s & 1) ? SM_UB : SM_S3T);
+  double* Ac = SMB(B, P, k, SM_VB);
   const double* T = SMB(B, P, k, SM_T);
   const double* Glo = SMB(B, P, k, SM_G_LO);
   const double* Ghi = SMB(B, P, k, SM_G_HI);
   const double* Cp = SMB(B, P, k, SM_CP);
   const double* Cn = SMB(B, P, k, SM_CM);
   const double* Ca = SMB(B, P, k, SM_CABS);
-  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
-    S0[e] = SMB(B, P, k, SM_S1)[e];
-    Ss[e] = S0[e];
-    Ac[e] = 0.0;
+  for (int e = threadIdx.x; e < rt * RC; e += blockDim.x) Ss[e] = Sin[e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * rt; e += blockDim.x) {
+    const int li = e / rt, j = e - li * rt, i = i0 + li;
+    double a1 = Glo[i * RC + j], a2 = Ghi[i * RC + j];
+    for (int l = 0; l < rt; ++l) {
+      a1 += T[i * RC + l] * Ss[l * RC + j];
+      a2 += T[l * RC + i] * Ss[l * RC + j];
+    }
+    U1[li * RC + j] = a1; U2[li * RC + j] = a2;
   }
   __syncthreads();
   const double coef = P.c_adv / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]);
   const double dtk = P.g.dtk[k];
-  const int nst = P.integrator == 1 ? 4 : 1;
-  for (int s = 0; s < nst; ++s) {
-    // U1 = T S + G_lo ; U2 = T^T S + G_hi
-    for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
-      int i = e / rt, j = e % rt;
-      double a1 = Glo[i * RC + j], a2 = Ghi[i * RC + j];
-      for (int l = 0; l < rt; ++l) {
-        a1 += T[i * RC + l] * Ss[l * RC + j];
-        a2 += T[l * RC + i] * Ss[l * RC + j];
-      }
-      U1[i * RC + j] = a1; U2[i * RC + j] = a2;
-    }
-    __syncthreads();
-    // F = coef (S |C| - U1 C+ + U2 C-)
-    for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
-      int i = e / rt, j = e % rt;
-      double f = 0.0;
-      for (int l = 0; l < rt; ++l)
-        f += Ss[i * RC + l] * Ca[l * RC + j] - U1[i * RC + l] * Cp[l * RC + j] + U2[i * RC + l] * Cn[l * RC + j];
-      F[i * RC + j] = coef * f;
-    }
-    __syncthreads();
-    const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
-    const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
-    for (int e = threadIdx.x; e < rt * rt; e += blockDim.x) {
-      int i = e / rt, j = e % rt;
-      Ac[i * RC + j] += bs * F[i * RC + j];
-      if (s + 1 < nst) Ss[i * RC + j] = S0[i * RC + j] + an * dtk * F[i * RC + j];
-    }
-    __syncthreads();
-  }
+  const double bs = (nst == 4) ? c_rk_b[s] : 1.0;
+  const double an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
   double* S2 = SMB(B, P, k, SM_S2);
-  double* Ap = SMB(B, P, k, SM_AP);
-  double* Am = SMB(B, P, k, SM_AM);
-  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
-    int i = e / RC, j = e % RC;
-    bool in = i < rt && j < rt;
-    S2[e] = in ? S0[e] + dtk * Ac[e] : 0.0;
-    Ap[e] = in ? ((i == j ? 1.0 : 0.0) - T[i * RC + j]) : 0.0;
-    Am[e] = in ? (T[j * RC + i] - (i == j ? 1.0 : 0.0)) : 0.0;
+  for (int e = threadIdx.x; e < nr * rt; e += blockDim.x) {
+    const int li = e / rt, j = e - li * rt, i = i0 + li;
+    double f = 0.0;
+    for (int l = 0; l < rt; ++l)
+      f += Ss[i * RC + l] * Ca[l * RC + j] - U1[li * RC + l] * Cp[l * RC + j] + U2[li * RC + l] * Cn[l * RC + j];
+    f = coef * f;
+    const double acc = (s == 0 ? 0.0 : Ac[i * RC + j]) + bs * f;
+    if (s + 1 < nst) {
+      Ac[i * RC + j] = acc;
+      Sout[i * RC + j] = S1[i * RC + j] + an * dtk * f;
+    } else {
+      S2[i * RC + j] = S1[i * RC + j] + dtk * acc;
+    }
+  }
+  if (s + 1 == nst) {                                // L-step matrices and zero padding
+    double* Ap = SMB(B, P, k, SM_AP);
+    double* Am = SMB(B, P, k, SM_AM);
+    for (int e = threadIdx.x; e < nr * RC; e += blockDim.x) {
+      const int li = e / RC, j = e - li * RC, i = i0 + li;
+      const bool in = j < rt;
+      if (!in) S2[i * RC + j] = 0.0;
+      Ap[i * RC + j] = in ? ((i == j ? 1.0 : 0.0) - T[i * RC + j]) : 0.0;
+      Am[i * RC + j] = in ? (T[j * RC + i] - (i == j ? 1.0 : 0.0)) : 0.0;
+    }
+    if (cr == 0)
+      for (int e = rt * RC + threadIdx.x; e < RC * RC; e += blockDim.x) {
+        S2[e] = 0.0; Ap[e] = 0.0; Am[e] = 0.0;
+      }
   }
 }
 
@@ -1216,7 +1229,7 @@ cudaError_t phase_init() {
   e = cudaFuncSetAttribute(k_kstep_adv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_sstep_adv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * 6 * RC * RC));
+                           (int)sstep_smem(RC));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_lstep_adv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(lstep_smem(RC)));
@@ -1413,7 +1426,13 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
     pend(st);
   }
   pbeg(st, KS_SSTEP_ADV);
-  k_sstep_adv<<<nsub, DD_THREADS, sizeof(double) * 6 * RC * RC, st>>>(P, B, axis);
+  {
+    // blocks per subdomain: enough to cover the SMs, at most 8
+    const int CL = std::max(1, std::min(8, P.nsm / std::max(1, nsub)));
+    const int nst = P.integrator == 1 ? 4 : 1;
+    for (int s = 0; s < nst; ++s)
+      k_sstep_adv<<<nsub * CL, DD_THREADS, sstep_smem(RC), st>>>(P, B, axis, s, CL);
+  }
   pend(st);
   // 9. L-step
   pbeg(st, KS_LSTEP_ADV);
