@@ -102,7 +102,13 @@ typedef struct dd_options {
                       /* of the paper's scheme): the scalar-flux change of the S-, L-steps  */
                       /* and truncations of the step is added back as the isotropic        */
                       /* rank-one term delta(x) (x) 1/|S|, then Algorithm 5 truncates; 0: off */
+  int splitting;      /* DD_SPLIT_LIE: x, y, collision (Algorithm 6); DD_SPLIT_STRANG:       */
+                      /* x(dt/2), y(dt/2), collision(dt), y(dt/2), x(dt/2), the second-order */
+                      /* splitting Section 3 refers to; every advection phase is a whole    */
+                      /* Algorithm 1/2 with the half step                                    */
 } dd_options;
+
+enum { DD_SPLIT_LIE = 0, DD_SPLIT_STRANG = 1 };
 
 typedef struct dd_dlra* dd_dlra_t;
 

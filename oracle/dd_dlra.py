@@ -21,6 +21,8 @@ primitives used as single steps: numpy SVD, symmetric eigendecomposition and
 matrix products.  No blocking, fusion or reordering beyond the paper's steps.
 
 Optional, not part of the paper's scheme: the conserved-moment correction (R18 below).
+Optional, the second-order splitting Section 3 points to: Strang splitting of the step
+(R20 below).
 
 Readings where the paper is silent or ambiguous (each also listed in the design doc):
   R1  general quadrature: scattering is sigma_s/|S| * sum_q w_q f_q, |S| = sum_q w_q.
@@ -78,6 +80,11 @@ invariances, brute force on tiny grids).
       rank-one term delta(x) (x) 1/|S| is added to f and the result truncated by
       Algorithm 5's rule.  Without truncation loss the step's rho is then the one
       of the conservative K-step chain.
+  R20 Strang splitting (off unless the workload asks for it): a step is x(dt/2),
+      y(dt/2), collision(dt), y(dt/2), x(dt/2), each advection phase a full
+      Algorithm 1/2 (augmentation, K-, S-, L-step, truncation) with the half step;
+      neighbour data come from the start of each phase (R7).  The Lie order of
+      Algorithm 6 is the default.
 """
 from __future__ import annotations
 
@@ -281,6 +288,7 @@ class DDDLRA:
 
     def __init__(self, wl, tau=1e-5, accept=0.5):
         self.wl = wl
+        self.dt_scale = 1.0          # fraction of dt the current phase advances (R20)
         self.tau = float(tau)
         self.accept = float(accept)
         self.subs = make_subdomains(wl)
@@ -440,7 +448,7 @@ class DDDLRA:
         wl = self.wl
         sub = self.subs[k]
         om = self._omega(axis)
-        dt = wl.dt
+        dt = wl.dt * self.dt_scale
         m = wl.integrator
         C = self._ip_phi(Vhat, om[:, None] * Vhat)       # <V_j, Omega V_k>_phi
         # 1: K-step, Eq. (advx_evolK)
@@ -498,7 +506,7 @@ class DDDLRA:
     def psi_collision(self, k, U, S, V):
         wl = self.wl
         sub = self.subs[k]
-        dt = wl.dt
+        dt = wl.dt * self.dt_scale
         m = wl.integrator
         r = S.shape[0]
         r_c = min(max(r, self.r_floor), wl.n, sub.N)
@@ -593,14 +601,26 @@ class DDDLRA:
             new.append(self.truncate(Qu / self.sw_x, Ru @ Sa @ Rv.T, Qv / self.sw_phi[:, None]))
         self.state = new
 
+    def _phase(self, kind, scale):
+        self.dt_scale = scale
+        try:
+            return self.collision_phase() if kind == "c" else self.advection_phase(kind)
+        finally:
+            self.dt_scale = 1.0
+
     def step(self):
-        ix = self.advection_phase("x")
-        iy = self.advection_phase("y")
-        ic = self.collision_phase()
+        if self.wl.splitting == "strang":                    # R20
+            order = [("x", 0.5), ("y", 0.5), ("c", 1.0), ("y", 0.5), ("x", 0.5)]
+        else:
+            order = [("x", 1.0), ("y", 1.0), ("c", 1.0)]
+        infos = [self._phase(kind, scale) for kind, scale in order]
         if self.wl.mass_fix:
-            self.mass_correction([a["dmass"] + b["dmass"] + c["dmass"]
-                                  for a, b, c in zip(ix, iy, ic)])
-        self.log.append(dict(x=ix, y=iy, c=ic))
+            self.mass_correction([sum(ph[k]["dmass"] for ph in infos)
+                                  for k in range(len(self.subs))])
+        entry = {"phases": [(kind, inf) for (kind, _), inf in zip(order, infos)]}
+        for (kind, _), inf in zip(order, infos):
+            entry.setdefault(kind, inf)                      # first phase of each kind
+        self.log.append(entry)
 
     def run(self, nsteps=None):
         for _ in range(self.wl.nsteps if nsteps is None else nsteps):

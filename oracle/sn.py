@@ -3,7 +3,9 @@
 Plain FP64 numpy restatement of the discretisation the low-rank scheme
 approximates:
   * Lie splitting x-advection -> y-advection -> absorption/scattering/source
-    (Section 3, the three sub-problems before Section 3.1),
+    (Section 3, the three sub-problems before Section 3.1), or its symmetric
+    (Strang) form x(dt/2), y(dt/2), collision(dt), y(dt/2), x(dt/2), the usual
+    second-order splitting the same section points to,
   * first-order upwind finite volumes on a uniform cell-centred grid
     (Section 4 introduction; Appendix A), each direction upwinded by the sign of
     its own velocity component, zero inflow at the physical boundary,
@@ -68,13 +70,23 @@ def initial_state(wl):
 
 
 def step(f, wl, dt=None):
-    """One split time step: x-advection, y-advection, collision."""
+    """One split time step: x-advection, y-advection, collision (Lie), or
+    x(dt/2), y(dt/2), collision(dt), y(dt/2), x(dt/2) (Strang)."""
     dt = wl.dt if dt is None else dt
     m = wl.integrator
-    f = _integrate(f, lambda g: advection_rhs(g, wl.omega_x, 1, wl.hx, wl.c_adv), dt, m)
-    f = _integrate(f, lambda g: advection_rhs(g, wl.omega_y, 0, wl.hy, wl.c_adv), dt, m)
-    f = _integrate(f, lambda g: collision_rhs(g, wl), dt, m)
-    return f
+    ax = lambda g, h: _integrate(g, lambda u: advection_rhs(u, wl.omega_x, 1, wl.hx, wl.c_adv), h, m)
+    ay = lambda g, h: _integrate(g, lambda u: advection_rhs(u, wl.omega_y, 0, wl.hy, wl.c_adv), h, m)
+    co = lambda g, h: _integrate(g, lambda u: collision_rhs(u, wl), h, m)
+    if wl.splitting == "strang":
+        return ax(ay(co(ay(ax(f, 0.5 * dt), 0.5 * dt), dt), 0.5 * dt), 0.5 * dt)
+    return co(ay(ax(f, dt), dt), dt)
+
+
+def unsplit_rhs(f, wl):
+    """The whole semi-discrete right-hand side (no splitting): the reference the
+    splittings converge to as dt -> 0."""
+    return (advection_rhs(f, wl.omega_x, 1, wl.hx, wl.c_adv)
+            + advection_rhs(f, wl.omega_y, 0, wl.hy, wl.c_adv) + collision_rhs(f, wl))
 
 
 def run(wl, nsteps=None, f=None):

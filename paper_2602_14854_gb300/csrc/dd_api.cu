@@ -76,6 +76,7 @@ struct dd_dlra {
   int *d_N, *d_nxk, *d_nyk, *d_rowoff, *d_nb, *d_cx0, *d_cy0;
   int *d_rlo, *d_rhi, *d_raug, *d_fbase, *d_fnx;
   double *d_hxk, *d_hyk, *d_dtk, *d_shk;
+  double* d_dth;   // dt / 2 per subdomain (the half steps of the Strang splitting)
   // device: problem data
   double *d_ox, *d_oy, *d_w, *d_sw, *d_sig_s, *d_sig_t, *d_sQ, *d_angcand;
   int n_angcand, angcand_complete;
@@ -108,9 +109,21 @@ dd::PhaseBufs bufs(dd_dlra* h, int in, int out) {
 // One time step of Algorithm 6: x-phase (state 0 -> 1), y-phase (1 -> 0),
 // collision in place on state 0.
 void enqueue_step(dd_dlra* h) {
-  dd::advection_phase(h->P, bufs(h, 0, 1), 0, h->stream);
-  dd::advection_phase(h->P, bufs(h, 1, 0), 1, h->stream);
-  dd::collision_phase(h->P, bufs(h, 0, 0), h->stream);
+  if (h->P.splitting == DD_SPLIT_STRANG) {
+    // x(dt/2), y(dt/2), collision(dt), y(dt/2), x(dt/2); the state alternates 0 -> 1 -> 0
+    // -> 0 -> 1 -> 0, so the step ends in state 0 as with the Lie order
+    dd::Problem Ph = h->P;
+    Ph.g.dtk = h->d_dth;
+    dd::advection_phase(Ph, bufs(h, 0, 1), 0, h->stream);
+    dd::advection_phase(Ph, bufs(h, 1, 0), 1, h->stream);
+    dd::collision_phase(h->P, bufs(h, 0, 0), h->stream);
+    dd::advection_phase(Ph, bufs(h, 0, 1), 1, h->stream);
+    dd::advection_phase(Ph, bufs(h, 1, 0), 0, h->stream);
+  } else {
+    dd::advection_phase(h->P, bufs(h, 0, 1), 0, h->stream);
+    dd::advection_phase(h->P, bufs(h, 1, 0), 1, h->stream);
+    dd::collision_phase(h->P, bufs(h, 0, 0), h->stream);
+  }
   if (h->P.mass_fix) {
     // correction state 0 -> 1, then back to 0 (the state between steps)
     dd::mass_fix_phase(h->P, bufs(h, 0, 1), h->stream);
@@ -181,7 +194,7 @@ void free_all(dd_dlra* h) {
                   h->d_K, h->d_X1, h->d_L, h->d_V1, h->d_Kb, h->d_sm, h->d_part, h->d_sig,
                   h->d_rho, h->d_fluxw, h->d_m, h->d_rt, h->d_rx, h->d_rc, h->d_p, h->d_status,
                   h->d_keep, h->d_cexp, h->d_dm, h->d_mvec, h->d_rlo, h->d_rhi, h->d_raug, h->d_fbase,
-                  h->d_fnx, h->d_hxk, h->d_hyk, h->d_dtk, h->d_shk};
+                  h->d_fnx, h->d_hxk, h->d_hyk, h->d_dtk, h->d_shk, h->d_dth};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->graph_ready) cudaGraphExecDestroy(h->graph_exec);
@@ -236,6 +249,8 @@ static dd_status check_instance(const dd_grid* grid, const dd_tiling* tiling,
   if (opt->precision != DD_FP64 && opt->precision != DD_MIXED)
     return fail(DD_ERR_ARG, "precision");
   if (opt->mass_fix != 0 && opt->mass_fix != 1) return fail(DD_ERR_ARG, "mass_fix");
+  if (opt->splitting != DD_SPLIT_LIE && opt->splitting != DD_SPLIT_STRANG)
+    return fail(DD_ERR_ARG, "splitting");
   if (!(opt->dt > 0.0) || !(opt->tau >= 0.0)) return fail(DD_ERR_ARG, "dt / tau");
   const int RS = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_max;
   const int fl = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_min;
@@ -267,9 +282,10 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     const dd_options& a = opts[0];
     const dd_options& b = opts[i];
     if (b.rank_mode != a.rank_mode || b.integrator != a.integrator || b.precision != a.precision ||
-        b.c_adv != a.c_adv || b.tau != a.tau || b.tol != a.tol || b.mass_fix != a.mass_fix)
+        b.c_adv != a.c_adv || b.tau != a.tau || b.tol != a.tol || b.mass_fix != a.mass_fix ||
+        b.splitting != a.splitting)
       return fail(DD_ERR_ARG, "instances of a batch must share rank mode, tolerance, integrator, "
-                              "precision, mass_fix, c_adv and tau");
+                              "precision, mass_fix, splitting, c_adv and tau");
   }
   const dd_options* opt = &opts[0];
 
@@ -380,7 +396,10 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     UP_INT(h->d_nb, vnb); UP_INT(h->d_cx0, vcx); UP_INT(h->d_cy0, vcy);
     UP_INT(h->d_rlo, vlo); UP_INT(h->d_rhi, vhi); UP_INT(h->d_raug, vaug); UP_INT(h->d_fbase, vfb);
     UP_INT(h->d_fnx, vfnx);
+    std::vector<double> vdth(nsub);
+    for (int k = 0; k < nsub; ++k) vdth[k] = 0.5 * vdt[k];
     UP_DBLV(h->d_hxk, vhx); UP_DBLV(h->d_hyk, vhy); UP_DBLV(h->d_dtk, vdt); UP_DBLV(h->d_shk, vsh);
+    UP_DBLV(h->d_dth, vdth);
 #undef UP_INT
 #undef UP_DBLV
   }
@@ -463,6 +482,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   P.integrator = opt->integrator; P.rank_mode = opt->rank_mode; P.tol = opt->tol;
   P.prec = opt->precision == DD_MIXED ? 1 : 0;
   P.mass_fix = opt->mass_fix;
+  P.splitting = opt->splitting;
   P.tau = opt->tau; P.accept = 0.5;
   P.r_floor = h->r_floor; P.r_aug_max = raug_max; P.RS = h->RS; P.WC = WC;
   P.angcand = h->d_angcand; P.n_angcand = h->n_angcand; P.angcand_complete = h->angcand_complete;

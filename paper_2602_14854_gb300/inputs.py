@@ -56,6 +56,7 @@ class Workload:
     n_mu: int = 0              # polar levels of the direction table (0: the paper's circle)
     n_phi: int = 0             # azimuths per level
     mass_fix: bool = False     # conserved-moment correction at the end of every step
+    splitting: str = "lie"     # "lie" (x, y, collision) or "strang" (x/2, y/2, collision, y/2, x/2)
     meta: dict = field(default_factory=dict)
 
     @property

@@ -233,6 +233,28 @@ def test_far_field_of_a_narrow_source(B):
     s.close()
 
 
+@pytest.mark.parametrize("integrator", ["euler", "rk4"])
+def test_strang_splitting_matches_oracle(B, integrator):
+    """Strang splitting (x/2, y/2, collision, y/2, x/2; R20): 2x2 tiling, heterogeneous
+    random materials and source, several steps, in the graph-replayed configuration."""
+    wl = inputs.random_small_problem(4, nx=12, ny=12, n_mu=2, n_phi=8, rank=3, r_aug_max=6,
+                                     integrator=integrator, nsteps=4).with_(splitting="strang")
+    s, o = run_both(B, wl, use_graph=True)
+    assert list(s.ranks()[0]) == o.ranks()
+    assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+
+
+def test_strang_splitting_gaussian_32(B):
+    """The small Gaussian workload (32x32, 2x2, 128 directions, rank 5) with Strang
+    splitting and the conserved-moment correction together, 20 steps."""
+    wl = inputs.config_c0(nsteps=20).with_(splitting="strang", mass_fix=True)
+    s, o = run_both(B, wl)
+    assert list(s.ranks()[0]) == o.ranks()
+    assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+
+
 def test_mass_fix_matches_oracle(B):
     """Conserved-moment correction on (not part of the paper's scheme): 2x2 tiling,
     heterogeneous materials, fixed rank."""
