@@ -106,9 +106,15 @@ typedef struct dd_options {
                       /* x(dt/2), y(dt/2), collision(dt), y(dt/2), x(dt/2), the second-order */
                       /* splitting Section 3 refers to; every advection phase is a whole    */
                       /* Algorithm 1/2 with the half step                                    */
+  int kstep_split;    /* DD_KSPLIT_EIGEN: the K-step's C+ and C- from the eigendecomposition */
+                      /* of C (Appendix A); DD_KSPLIT_FLUX: from the direction split,        */
+                      /* C+- = <V, max/min(Omega, 0) V> (the L-step's per-direction upwind   */
+                      /* flux projected on the angular basis; equal to Appendix A's at full  */
+                      /* rank; not the paper's scheme at low rank; no eigendecomposition)    */
 } dd_options;
 
 enum { DD_SPLIT_LIE = 0, DD_SPLIT_STRANG = 1 };
+enum { DD_KSPLIT_EIGEN = 0, DD_KSPLIT_FLUX = 1 };
 
 typedef struct dd_dlra* dd_dlra_t;
 

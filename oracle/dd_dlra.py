@@ -22,7 +22,8 @@ matrix products.  No blocking, fusion or reordering beyond the paper's steps.
 
 Optional, not part of the paper's scheme: the conserved-moment correction (R18 below).
 Optional, the second-order splitting Section 3 points to: Strang splitting of the step
-(R20 below).
+(R20 below).  Optional, not the paper's Appendix A: C+/C- of the advection K-step from
+the direction split instead of the eigen-split (R21 below).
 
 Readings where the paper is silent or ambiguous (each also listed in the design doc):
   R1  general quadrature: scattering is sigma_s/|S| * sum_q w_q f_q, |S| = sum_q w_q.
@@ -85,6 +86,12 @@ invariances, brute force on tiny grids).
       Algorithm 1/2 (augmentation, K-, S-, L-step, truncation) with the half step;
       neighbour data come from the start of each phase (R7).  The Lie order of
       Algorithm 6 is the default.
+  R21 flux-split K-step (off unless the workload asks for it): C+ = <V, Omega+ V>,
+      C- = <V, Omega- V> with Omega+- = max/min(Omega, 0), i.e. the per-direction
+      upwind flux of the L-step projected on the augmented angular basis, in place of
+      Appendix A's C+- = P Lambda+- P^T.  Both split C = C+ + C-; at full rank they
+      coincide (the eigenvectors of C are then the directions themselves); at low rank
+      the flux split needs no eigendecomposition.
 """
 from __future__ import annotations
 
@@ -443,6 +450,14 @@ class DDDLRA:
         D = np.where(lam[None, :] > 0, Dm, np.where(lam[None, :] < 0, Dp, 0.0))
         return -self.wl.c_adv * (D * lam[None, :]) @ P.T
 
+    def kstep_rhs_flux(self, K, Cp, Cm, Kb_lo, Kb_hi, sub, axis):
+        """-c_adv (D- K C+ + D+ K C-) with the direction split C+- (R21): backward
+        differences carry the part of the flux moving towards higher coordinates,
+        forward differences the rest."""
+        Dm = self._diff(K, sub, axis, Kb_lo, "minus")
+        Dp = self._diff(K, sub, axis, Kb_hi, "plus")
+        return -self.wl.c_adv * (Dm @ Cp + Dp @ Cm)
+
     # -- Algorithms 1 / 2 -------------------------------------------------------
     def psi_advection(self, k, axis, K0, Vhat, Kb_lo, Kb_hi):
         wl = self.wl
@@ -451,16 +466,21 @@ class DDDLRA:
         dt = wl.dt * self.dt_scale
         m = wl.integrator
         C = self._ip_phi(Vhat, om[:, None] * Vhat)       # <V_j, Omega V_k>_phi
+        if wl.kstep_split == "flux":                     # R21
+            Cp = self._ip_phi(Vhat, np.maximum(om, 0.0)[:, None] * Vhat)
+            Cm = self._ip_phi(Vhat, np.minimum(om, 0.0)[:, None] * Vhat)
+            rk = lambda K: self.kstep_rhs_flux(K, Cp, Cm, Kb_lo, Kb_hi, sub, axis)
+        else:
+            rk = lambda K: self.kstep_rhs_adv(K, C, Kb_lo, Kb_hi, sub, axis)
         # 1: K-step, Eq. (advx_evolK)
-        K1 = integrate(K0, lambda K: self.kstep_rhs_adv(K, C, Kb_lo, Kb_hi, sub, axis), dt, m)
+        K1 = integrate(K0, rk, dt, m)
         # 2: QR of K
         r_t = K0.shape[1]
         U1, pK = orthonormal_basis(K1, np.full(sub.N, self.sw_x), r_t,
                                    spatial_candidates(sub), self.tau, self.accept)
         S1 = self._ip_x(U1, K1)
         # 3: S-step, Eq. (advx_evolS): dS/dt = -<U1, R_K(U1 S)> (R4)
-        S2 = integrate(S1, lambda S: -self._ip_x(
-            U1, self.kstep_rhs_adv(U1 @ S, C, Kb_lo, Kb_hi, sub, axis)), dt, m)
+        S2 = integrate(S1, lambda S: -self._ip_x(U1, rk(U1 @ S)), dt, m)
         # 4: L-step, Eq. (advx_evolL), per-direction upwind, ghost f^b = K^b V^T (R4)
         fb_lo = Kb_lo @ Vhat.T
         fb_hi = Kb_hi @ Vhat.T

@@ -55,7 +55,7 @@ class Options(C.Structure):
                 ("r_min", C.c_int), ("r_max", C.c_int), ("r_aug_max", C.c_int),
                 ("integrator", C.c_int), ("c_adv", C.c_double), ("dt", C.c_double),
                 ("tau", C.c_double), ("precision", C.c_int), ("mass_fix", C.c_int),
-                ("splitting", C.c_int)]
+                ("splitting", C.c_int), ("kstep_split", C.c_int)]
 
 
 _lib = None
@@ -151,7 +151,8 @@ class Solver:
             opts[i] = Options(DD_RANK_FIXED if fixed else DD_RANK_TOL, w.rank, w.tol, w.r_min,
                               w.r_max, w.r_aug_max, DD_RK4 if w.integrator == "rk4" else DD_EULER,
                               w.c_adv, w.dt, tau, DD_MIXED if precision == "mixed" else DD_FP64,
-                              1 if w.mass_fix else 0, 1 if w.splitting == "strang" else 0)
+                              1 if w.mass_fix else 0, 1 if w.splitting == "strang" else 0,
+                              1 if w.kstep_split == "flux" else 0)
             g0s[i] = _ptr(g0)
         w0 = wls[0]
         ox, oy, w = _d(w0.omega_x), _d(w0.omega_y), _d(w0.w)

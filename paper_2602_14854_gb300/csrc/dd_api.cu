@@ -251,6 +251,8 @@ static dd_status check_instance(const dd_grid* grid, const dd_tiling* tiling,
   if (opt->mass_fix != 0 && opt->mass_fix != 1) return fail(DD_ERR_ARG, "mass_fix");
   if (opt->splitting != DD_SPLIT_LIE && opt->splitting != DD_SPLIT_STRANG)
     return fail(DD_ERR_ARG, "splitting");
+  if (opt->kstep_split != DD_KSPLIT_EIGEN && opt->kstep_split != DD_KSPLIT_FLUX)
+    return fail(DD_ERR_ARG, "kstep_split");
   if (!(opt->dt > 0.0) || !(opt->tau >= 0.0)) return fail(DD_ERR_ARG, "dt / tau");
   const int RS = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_max;
   const int fl = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_min;
@@ -283,9 +285,9 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     const dd_options& b = opts[i];
     if (b.rank_mode != a.rank_mode || b.integrator != a.integrator || b.precision != a.precision ||
         b.c_adv != a.c_adv || b.tau != a.tau || b.tol != a.tol || b.mass_fix != a.mass_fix ||
-        b.splitting != a.splitting)
+        b.splitting != a.splitting || b.kstep_split != a.kstep_split)
       return fail(DD_ERR_ARG, "instances of a batch must share rank mode, tolerance, integrator, "
-                              "precision, mass_fix, splitting, c_adv and tau");
+                              "precision, mass_fix, splitting, kstep_split, c_adv and tau");
   }
   const dd_options* opt = &opts[0];
 
@@ -483,6 +485,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   P.prec = opt->precision == DD_MIXED ? 1 : 0;
   P.mass_fix = opt->mass_fix;
   P.splitting = opt->splitting;
+  P.kstep_split = opt->kstep_split;
   P.tau = opt->tau; P.accept = 0.5;
   P.r_floor = h->r_floor; P.r_aug_max = raug_max; P.RS = h->RS; P.WC = WC;
   P.angcand = h->d_angcand; P.n_angcand = h->n_angcand; P.angcand_complete = h->angcand_complete;

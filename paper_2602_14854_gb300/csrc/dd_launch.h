@@ -117,6 +117,7 @@ struct Problem {
   int prec;               // 0 FP64 arithmetic throughout, 1 mixed (FP32 where allowed)
   int mass_fix;           // conserved-moment correction at the end of every step
   int splitting;          // 0 Lie (x, y, collision), 1 Strang (x/2, y/2, collision, y/2, x/2)
+  int kstep_split;        // C+/C- of the advection K-step: 0 eigen-split, 1 direction split
   int rank_mode; double tol; double tau; double accept;
   int r_floor, r_aug_max, RS;
   int WC;                 // leading dimension of the orthonormalisation workspaces

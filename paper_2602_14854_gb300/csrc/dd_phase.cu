@@ -89,11 +89,13 @@ __global__ void k_build_L0(Geo g, const double* V, const double* S, const int* r
 __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* om,
                                                             const double* Vh, const double* V,
                                                             const int* r, const int* rt, int axis,
-                                                            int nchunk, double* part) {
+                                                            int nchunk, int nblk, double* part) {
   // Work items, enumerated densely so that every lane of an FP64 instruction is used:
   // the rt(rt+1)/2 pairs i <= j of the three symmetric blocks C, Mout_lo, Mout_hi (one
   // product v_i v_j per direction feeds all three), then the pairs of M, Min_lo and
   // Min_hi.  The sign of Om is taken from its bits (Om < 0 <=> sign bit set, not -0).
+  // nblk = 8 adds the direction split C+ = <Vh, Om+ Vh>, C- = <Vh, Om- Vh> (flux-split
+  // K-step) as blocks 6 and 7, from the same products.
   const int k = blockIdx.y, c = blockIdx.x, RC = g.RC, n = g.n;
   const int ch = (n + nchunk - 1) / nchunk;
   const int q0 = c * ch, q1 = min(n, q0 + ch);
@@ -103,8 +105,8 @@ __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* 
   const double* Vk = V + (long)k * n * RC;
   const double* Vlo = V + (long)(lo >= 0 ? lo : 0) * n * RC;
   const double* Vhi = V + (long)(hi >= 0 ? hi : 0) * n * RC;
-  double* out = part + ((long)k * nchunk + c) * 6 * RC * RC;
-  for (int e = threadIdx.x; e < 6 * RC * RC; e += blockDim.x) out[e] = 0.0;
+  double* out = part + ((long)k * nchunk + c) * nblk * RC * RC;
+  for (int e = threadIdx.x; e < nblk * RC * RC; e += blockDim.x) out[e] = 0.0;
   __syncthreads();
   const int nsym = rtk * (rtk + 1) / 2;
   const int n3 = rk * rtk, n4 = rlo * rtk, n5 = rhi * rtk;
@@ -115,17 +117,22 @@ __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* 
       j += (j + 1) * (j + 2) / 2 <= w;
       j -= j * (j + 1) / 2 > w;
       const int i = w - j * (j + 1) / 2;
-      double sc = 0.0, sl = 0.0, sh = 0.0;
+      double sc = 0.0, sl = 0.0, sh = 0.0, sp = 0.0, sm = 0.0;
       for (int q = q0; q < q1; ++q) {
         const double o = om[q];
         const long long ob = __double_as_longlong(o);
         const double t = Vhk[q * RC + i] * Vhk[q * RC + j];
         sc += o * t;
-        if (ob < 0 && ob != (long long)0x8000000000000000ull) sl += t; else sh += t;
+        if (ob < 0 && ob != (long long)0x8000000000000000ull) { sl += t; sm += o * t; }
+        else { sh += t; sp += o * t; }
       }
       out[i * RC + j] = sc; out[j * RC + i] = sc;
       out[RC * RC + i * RC + j] = sl; out[RC * RC + j * RC + i] = sl;
       out[2 * RC * RC + i * RC + j] = sh; out[2 * RC * RC + j * RC + i] = sh;
+      if (nblk == 8) {
+        out[6 * RC * RC + i * RC + j] = sp; out[6 * RC * RC + j * RC + i] = sp;
+        out[7 * RC * RC + i * RC + j] = sm; out[7 * RC * RC + j * RC + i] = sm;
+      }
     } else {
       int u = w - nsym, blk;
       const double* Va;
@@ -145,7 +152,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* 
   }
 }
 
-struct Dst { int idx[6]; };
+struct Dst { int idx[8]; };
 
 // Sum the chunk partials in fixed order into the small matrices.
 __global__ void k_reduce(const double* part, int nchunk, int nblk, Dst dst, double* sm, int RC) {
@@ -271,6 +278,14 @@ __global__ void __launch_bounds__(DD_THREADS) k_small_adv1(Problem P, PhaseBufs 
   if (hi >= 0)
     bmm(SMB(B, P, k, SM_B_HI), RC, 1.0, B.S + (long)hi * RC * RC, RC, SMB(B, P, k, SM_MIN_HI), RC,
         rhi, rt, rhi, false);
+  if (P.kstep_split == 1) {
+    // flux split: C+ and C- came with the Galerkin coefficients; |C| = C+ - C-
+    const double* Cp = SMB(B, P, k, SM_CP);
+    const double* Cn = SMB(B, P, k, SM_CM);
+    double* Ca = SMB(B, P, k, SM_CABS);
+    for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) Ca[e] = Cp[e] - Cn[e];
+    return;
+  }
   // Eigendecomposition of the symmetric rt x rt matrix C: one-sided Jacobi of the
   // positive semidefinite C + s I (s = |C|_F >= its spectral radius); the column
   // norms of (C + s I) P are lambda + s.  FP32 sweeps and a double-float finish,
@@ -1216,7 +1231,7 @@ thread_local Prof* g_prof = nullptr;
 
 size_t part_elems(const Problem& P) {
   const int nc = P.nchunk_sp > P.nchunk_ang ? P.nchunk_sp : P.nchunk_ang;
-  return (size_t)P.g.nsub * nc * 6 * P.g.RC * P.g.RC;
+  return (size_t)P.g.nsub * nc * 8 * P.g.RC * P.g.RC;
 }
 
 // Kernel attributes are per process, not per solver: they are set for the largest
@@ -1373,15 +1388,17 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   pbeg(st, KS_ANG_COEFFS);
   // twice the angular chunks (more blocks than SMs), as far as the partial buffer holds
   const int nch_ac = std::min(2 * P.nchunk_ang, std::max(P.nchunk_sp, P.nchunk_ang));
+  const int nblk_ac = P.kstep_split == 1 ? 8 : 6;
   k_ang_coeffs<<<dim3(nch_ac, nsub), DD_THREADS, 0, st>>>(
-      g, axis == 0 ? P.ox : P.oy, B.Vh, B.V, B.r, B.rt, axis, nch_ac, B.part);
+      g, axis == 0 ? P.ox : P.oy, B.Vh, B.V, B.r, B.rt, axis, nch_ac, nblk_ac, B.part);
   pend(st);
   {
     Dst d;
     d.idx[0] = SM_C; d.idx[1] = SM_MOUT_LO; d.idx[2] = SM_MOUT_HI;
     d.idx[3] = SM_M; d.idx[4] = SM_MIN_LO; d.idx[5] = SM_MIN_HI;
+    d.idx[6] = SM_CP; d.idx[7] = SM_CM;
     pbeg(st, KS_REDUCE);
-    k_reduce<<<reduce_grid(g, 6), DD_THREADS, 0, st>>>(B.part, nch_ac, 6, d, B.sm, RC);
+    k_reduce<<<reduce_grid(g, nblk_ac), DD_THREADS, 0, st>>>(B.part, nch_ac, nblk_ac, d, B.sm, RC);
     pend(st);
   }
   // 3. S M products, eigen-split of C

@@ -57,6 +57,7 @@ class Workload:
     n_phi: int = 0             # azimuths per level
     mass_fix: bool = False     # conserved-moment correction at the end of every step
     splitting: str = "lie"     # "lie" (x, y, collision) or "strang" (x/2, y/2, collision, y/2, x/2)
+    kstep_split: str = "eigen" # C+/C- of the advection K-step: "eigen" (Appendix A) or "flux"
     meta: dict = field(default_factory=dict)
 
     @property

@@ -255,6 +255,29 @@ def test_strang_splitting_gaussian_32(B):
     s.close()
 
 
+@pytest.mark.parametrize("integrator", ["euler", "rk4"])
+def test_flux_split_matches_oracle(B, integrator):
+    """K-step with the direction split C+- = <V, Omega+- V> (R21): 2x2 tiling,
+    heterogeneous random materials and source, graph replay."""
+    wl = inputs.random_small_problem(5, nx=12, ny=12, n_mu=2, n_phi=8, rank=3, r_aug_max=6,
+                                     integrator=integrator, nsteps=4).with_(kstep_split="flux")
+    s, o = run_both(B, wl, use_graph=True)
+    assert list(s.ranks()[0]) == o.ranks()
+    assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+
+
+def test_flux_split_gaussian_32_strang(B):
+    """The small Gaussian workload with the flux-split K-step and Strang splitting, RK4,
+    20 steps."""
+    wl = inputs.config_c0(nsteps=20, integrator="rk4").with_(kstep_split="flux",
+                                                              splitting="strang")
+    s, o = run_both(B, wl)
+    assert list(s.ranks()[0]) == o.ranks()
+    assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+
+
 def test_mass_fix_matches_oracle(B):
     """Conserved-moment correction on (not part of the paper's scheme): 2x2 tiling,
     heterogeneous materials, fixed rank."""

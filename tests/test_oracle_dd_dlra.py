@@ -362,3 +362,54 @@ def test_strang_splitting_is_second_order_on_one_subdomain():
         orders[sp] = [math.log2(a / b) for a, b in zip(e, e[1:])]
     assert all(0.8 < p < 1.3 for p in orders["lie"]), orders
     assert all(1.8 < p < 2.3 for p in orders["strang"]), orders
+
+
+def test_flux_split_equals_eigen_split_at_full_rank():
+    """R21: at full angular rank the eigenvectors of C = <V, Omega V> are the directions
+    themselves, so the direction split and Appendix A's eigen-split give the same C+-
+    and the same steps (2x2 tiling, RK4)."""
+    wl = inputs.random_small_problem(6, nx=8, ny=8, n_mu=2, n_phi=8, rank=16, r_aug_max=16,
+                                     integrator="rk4", nsteps=2)
+    a = dd_dlra.DDDLRA(wl).run()
+    b = dd_dlra.DDDLRA(wl.with_(kstep_split="flux")).run()
+    assert a.ranks() == b.ranks()
+    ra, rb = a.scalar_flux(), b.scalar_flux()
+    assert np.linalg.norm(ra - rb) / np.linalg.norm(ra) < 1e-11
+
+
+def test_flux_split_kstep_is_energy_stable():
+    """R21: with C+ = <V, Omega+ V> positive and C- = <V, Omega- V> negative
+    semidefinite and zero inflow, the semi-discrete flux-split K-step cannot create
+    energy: <K, R(K)>_x <= 0 for any K.  Swapping the two differences (a plausible
+    mistake) creates energy for some K."""
+    wl = inputs.random_small_problem(7, nx=8, ny=8, tiles_x=1, tiles_y=1, n_mu=2, n_phi=8)
+    o = dd_dlra.DDDLRA(wl)
+    sub = o.subs[0]
+    rng = np.random.default_rng(0)
+    om = np.asarray(wl.omega_x)
+    V = np.linalg.qr(o.sw_phi[:, None] * rng.standard_normal((wl.n, 5)))[0] / o.sw_phi[:, None]
+    Cp = o._ip_phi(V, np.maximum(om, 0.0)[:, None] * V)
+    Cm = o._ip_phi(V, np.minimum(om, 0.0)[:, None] * V)
+    z = np.zeros((sub.N // sub.nxk, 5))                  # one ghost row per x-line
+    worst, swapped = -np.inf, -np.inf
+    for _ in range(20):
+        K = rng.standard_normal((sub.N, 5))
+        worst = max(worst, np.trace(o._ip_x(K, o.kstep_rhs_flux(K, Cp, Cm, z, z, sub, "x"))))
+        swapped = max(swapped, np.trace(o._ip_x(K, o.kstep_rhs_flux(K, Cm, Cp, z, z, sub, "x"))))
+    assert worst <= 1e-12
+    assert swapped > 1e-3
+
+
+def test_flux_split_rank_convergence_to_sn():
+    """R21: one subdomain, RK4: with the flux split too, the error against S_N falls as
+    the rank grows."""
+    base = inputs.config_c0(integrator="rk4", tiles_x=1, tiles_y=1,
+                            nsteps=12).with_(kstep_split="flux")
+    ref = sn.scalar_flux(sn.run(base), base)
+    errs = []
+    for r in (5, 10, 20, 40):
+        wl = base.with_(rank=r, r_aug_max=min(2 * r, base.n))
+        rho = dd_dlra.DDDLRA(wl).run().scalar_flux()
+        errs.append(np.linalg.norm(rho - ref) / np.linalg.norm(ref))
+    assert all(errs[i + 1] < errs[i] for i in range(3)), errs
+    assert errs[-1] < 1e-3, errs
