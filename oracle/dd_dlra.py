@@ -23,7 +23,8 @@ matrix products.  No blocking, fusion or reordering beyond the paper's steps.
 Optional, not part of the paper's scheme: the conserved-moment correction (R18 below).
 Optional, the second-order splitting Section 3 points to: Strang splitting of the step
 (R20 below).  Optional, not the paper's Appendix A: C+/C- of the advection K-step from
-the direction split instead of the eigen-split (R21 below).
+the direction split instead of the eigen-split (R21 below).  Physical inflow data
+(R22 below).
 
 Readings where the paper is silent or ambiguous (each also listed in the design doc):
   R1  general quadrature: scattering is sigma_s/|S| * sum_q w_q f_q, |S| = sum_q w_q.
@@ -92,6 +93,13 @@ invariances, brute force on tiny grids).
       Appendix A's C+- = P Lambda+- P^T.  Both split C = C+ + C-; at full rank they
       coincide (the eigenvectors of C are then the directions themselves); at low rank
       the flux split needs no eigendecomposition.
+  R22 physical inflow f(s, Omega) = g(s) h(Omega) on a side, for the directions that
+      enter through it (the masks of R2), acts as a virtual neighbour: its ghost term
+      is g(line) <m_in h, V_hat>_phi (as a neighbour's face row times M_in), and the
+      augmentation input L0 gets the column m_in h |g|_x with
+      |g|_x^2 = hx hy len sum_{face lines} g^2, the norm of the data extended across a
+      subdomain of the same size (Algorithm 4 takes a neighbour's whole V S^T), so that
+      V_hat can represent the inflow.
 """
 from __future__ import annotations
 
@@ -397,10 +405,14 @@ class DDDLRA:
         sub = self.subs[k]
         wl = self.wl
         blocks = [V @ S.T]
-        for nb in self._neighbours(sub, axis):
+        for side, nb in enumerate(self._neighbours(sub, axis)):
             if nb is not None:
                 _, Sn, Vn = snap[nb]
                 blocks.append(Vn @ Sn.T)
+            else:
+                col = self._inflow_column(sub, axis, side)        # R22
+                if col is not None:
+                    blocks.append(col[:, None])
         L0 = np.concatenate(blocks, axis=1)
         Lw = self.sw_phi[:, None] * L0
         if Lw.size and np.max(np.abs(Lw)) > 0.0:
@@ -435,8 +447,35 @@ class DDDLRA:
                 # the neighbour's cells adjacent to this face: its opposite face (R5)
                 Kn_face = self._face(Kn, self.subs[nb], axis, 1 - side)
                 own = own + Kn_face @ self._ip_phi(m_in[:, None] * Vn, Vhat)
+            else:
+                gh = self._inflow_face(sub, axis, side)           # R22
+                if gh is not None:
+                    g_face, hq = gh
+                    own = own + g_face[:, None] * self._ip_phi((m_in * hq)[:, None], Vhat)
             Kb.append(own)
         return Kb[0], Kb[1]
+
+    def _inflow_face(self, sub, axis, side):
+        """Physical inflow on the face of a boundary subdomain (R22): the values of g
+        on the face's lines and h, or None."""
+        key = axis + ("_lo" if side == 0 else "_hi")
+        if key not in self.wl.inflow:
+            return None
+        g, hq = self.wl.inflow[key]
+        g = np.asarray(g, dtype=np.float64)
+        g_face = g[sub.jy0:sub.jy1] if axis == "x" else g[sub.ix0:sub.ix1]
+        return g_face, np.asarray(hq, dtype=np.float64)
+
+    def _inflow_column(self, sub, axis, side):
+        """The augmentation column of a physical inflow side (R22), or None."""
+        gh = self._inflow_face(sub, axis, side)
+        if gh is None:
+            return None
+        g_face, hq = gh
+        om = self._omega(axis)
+        m_in = (om >= 0) if side == 0 else (om < 0)
+        ln = sub.nxk if axis == "x" else sub.nyk
+        return (m_in * hq) * math.sqrt(self.hx * self.hy * ln * float(np.sum(g_face ** 2)))
 
     # -- Appendix A: K-step right-hand side ------------------------------------
     def kstep_rhs_adv(self, K, C, Kb_lo, Kb_hi, sub, axis):

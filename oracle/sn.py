@@ -8,7 +8,9 @@ approximates:
     second-order splitting the same section points to,
   * first-order upwind finite volumes on a uniform cell-centred grid
     (Section 4 introduction; Appendix A), each direction upwinded by the sign of
-    its own velocity component, zero inflow at the physical boundary,
+    its own velocity component, zero inflow at the physical boundary unless
+    inflow data f = g(s) h(Omega) are given for a side (the Hohlraum and boundary
+    point-source inflow of Section 4),
   * explicit Euler or classic RK4 per sub-step (Section 4 introduction).
 Scattering is sigma_s/|S| * rho with rho = sum_q w_q f_q (Eq. (rt) with the
 circle's 1/(2 pi) replaced by 1/|S| for a general quadrature).
@@ -33,15 +35,17 @@ def _integrate(y, rhs, dt, method):
     raise ValueError(method)
 
 
-def advection_rhs(f, omega, axis, h, c_adv=1.0):
+def advection_rhs(f, omega, axis, h, c_adv=1.0, ghosts=None):
     """-c_adv * omega_q * d/d(axis) f with per-direction upwinding.
 
-    f has shape (ny, nx, n); axis 1 is x, axis 0 is y.  The ghost value outside
-    the physical domain is 0 (zero inflow).  omega_q = 0 gives no flux.
+    f has shape (ny, nx, n); axis 1 is x, axis 0 is y.  The ghost values outside the
+    physical domain are ghosts = (low side, high side), each shaped like one slice of f
+    along the axis; None means 0 (zero inflow).  omega_q = 0 gives no flux.
     """
     zero = np.zeros_like(np.take(f, [0], axis=axis))
-    lo = np.concatenate([zero, f], axis=axis)       # lo[c] = f[c-1]
-    hi = np.concatenate([f, zero], axis=axis)       # hi[c+1] = f[c+1]
+    g_lo, g_hi = ghosts if ghosts is not None else (zero, zero)
+    lo = np.concatenate([g_lo, f], axis=axis)       # lo[c] = f[c-1]
+    hi = np.concatenate([f, g_hi], axis=axis)       # hi[c+1] = f[c+1]
     n_ax = f.shape[axis]
     f_prev = np.take(lo, range(0, n_ax), axis=axis)
     f_next = np.take(hi, range(1, n_ax + 1), axis=axis)
@@ -53,6 +57,24 @@ def advection_rhs(f, omega, axis, h, c_adv=1.0):
     out[..., pos] = -c_adv * omega[pos] * back[..., pos]
     out[..., neg] = -c_adv * omega[neg] * fwd[..., neg]
     return out
+
+
+def inflow_ghosts(wl, axis):
+    """Ghost slices of the physical inflow f(s, Omega) = g(s) h(Omega) along the axis
+    (1 = x, 0 = y) for the directions entering through each side: Omega >= 0 at the
+    low side, Omega < 0 at the high side (the masks of the subdomain interfaces)."""
+    om = wl.omega_x if axis == 1 else wl.omega_y
+    out = []
+    for side, mask in (("lo", om >= 0), ("hi", om < 0)):
+        key = ("x_" if axis == 1 else "y_") + side
+        if key in wl.inflow:
+            g, hq = wl.inflow[key]
+            v = np.asarray(g, dtype=np.float64)[:, None] * (np.asarray(hq, dtype=np.float64) * mask)[None, :]
+            out.append(v[:, None, :] if axis == 1 else v[None, :, :])
+        else:
+            shape = (wl.ny, 1, wl.n) if axis == 1 else (1, wl.nx, wl.n)
+            out.append(np.zeros(shape))
+    return tuple(out)
 
 
 def collision_rhs(f, wl):
@@ -74,8 +96,9 @@ def step(f, wl, dt=None):
     x(dt/2), y(dt/2), collision(dt), y(dt/2), x(dt/2) (Strang)."""
     dt = wl.dt if dt is None else dt
     m = wl.integrator
-    ax = lambda g, h: _integrate(g, lambda u: advection_rhs(u, wl.omega_x, 1, wl.hx, wl.c_adv), h, m)
-    ay = lambda g, h: _integrate(g, lambda u: advection_rhs(u, wl.omega_y, 0, wl.hy, wl.c_adv), h, m)
+    gx, gy = inflow_ghosts(wl, 1), inflow_ghosts(wl, 0)
+    ax = lambda g, h: _integrate(g, lambda u: advection_rhs(u, wl.omega_x, 1, wl.hx, wl.c_adv, gx), h, m)
+    ay = lambda g, h: _integrate(g, lambda u: advection_rhs(u, wl.omega_y, 0, wl.hy, wl.c_adv, gy), h, m)
     co = lambda g, h: _integrate(g, lambda u: collision_rhs(u, wl), h, m)
     if wl.splitting == "strang":
         return ax(ay(co(ay(ax(f, 0.5 * dt), 0.5 * dt), dt), 0.5 * dt), 0.5 * dt)
@@ -85,8 +108,9 @@ def step(f, wl, dt=None):
 def unsplit_rhs(f, wl):
     """The whole semi-discrete right-hand side (no splitting): the reference the
     splittings converge to as dt -> 0."""
-    return (advection_rhs(f, wl.omega_x, 1, wl.hx, wl.c_adv)
-            + advection_rhs(f, wl.omega_y, 0, wl.hy, wl.c_adv) + collision_rhs(f, wl))
+    return (advection_rhs(f, wl.omega_x, 1, wl.hx, wl.c_adv, inflow_ghosts(wl, 1))
+            + advection_rhs(f, wl.omega_y, 0, wl.hy, wl.c_adv, inflow_ghosts(wl, 0))
+            + collision_rhs(f, wl))
 
 
 def run(wl, nsteps=None, f=None):

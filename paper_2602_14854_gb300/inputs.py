@@ -58,6 +58,10 @@ class Workload:
     mass_fix: bool = False     # conserved-moment correction at the end of every step
     splitting: str = "lie"     # "lie" (x, y, collision) or "strang" (x/2, y/2, collision, y/2, x/2)
     kstep_split: str = "eigen" # C+/C- of the advection K-step: "eigen" (Appendix A) or "flux"
+    # physical inflow f(s, Omega) = g(s) h(Omega) on a side ("x_lo", "x_hi", "y_lo", "y_hi")
+    # for the directions entering through it: side -> (g over the side's cells, h over the
+    # directions); absent sides have zero inflow
+    inflow: dict = field(default_factory=dict)
     meta: dict = field(default_factory=dict)
 
     @property

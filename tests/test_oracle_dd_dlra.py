@@ -78,6 +78,66 @@ def test_full_rank_kstep_equals_sn(axis, tiles, integrator):
     assert np.max(np.abs(f1.reshape(ref.shape) - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
+def with_random_inflow(wl, seed=11):
+    rng = np.random.default_rng(seed)
+    return wl.with_(inflow={"x_lo": (rng.uniform(size=wl.ny), rng.uniform(size=wl.n)),
+                            "x_hi": (rng.uniform(size=wl.ny), rng.uniform(size=wl.n)),
+                            "y_lo": (rng.uniform(size=wl.nx), rng.uniform(size=wl.n)),
+                            "y_hi": (rng.uniform(size=wl.nx), rng.uniform(size=wl.n))})
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+@pytest.mark.parametrize("tiles,integrator", [(2, "euler"), (1, "rk4")])
+def test_full_rank_kstep_with_inflow_equals_sn(axis, tiles, integrator):
+    """R22: with inflow data f = g(s) h(Omega) on all four physical sides, the
+    full-rank K-step (ghost = the inflow's projection for boundary faces, neighbour
+    data inside) reproduces the S_N sub-step with the same inflow ghosts."""
+    wl = with_random_inflow(circle_problem(tiles=tiles, integrator=integrator))
+    o = dd_dlra.DDDLRA(wl, tau=1e-12)
+    random_state(o, wl.n, 10)
+    f0 = o.full_f()
+    snap = o.state
+    f1 = np.zeros((wl.ncells, wl.n))
+    for k, sub in enumerate(o.subs):
+        K0, Vh, info = o.augment(k, axis, snap)
+        assert info["r_t"] == wl.n
+        lo, hi = o.boundary(k, axis, snap, K0, Vh)
+        om = wl.omega_x if axis == "x" else wl.omega_y
+        C = Vh.T @ (wl.w[:, None] * om[:, None] * Vh)
+        K1 = dd_dlra.integrate(K0, lambda K: o.kstep_rhs_adv(K, C, lo, hi, sub, axis),
+                               wl.dt, integrator)
+        f1[o.cells[k]] = K1 @ Vh.T
+    om, ax, h = (wl.omega_x, 1, wl.hx) if axis == "x" else (wl.omega_y, 0, wl.hy)
+    ref = sn._integrate(f0, lambda g: sn.advection_rhs(g, om, ax, h, 1.0,
+                                                        sn.inflow_ghosts(wl, ax)),
+                        wl.dt, integrator)
+    assert np.max(np.abs(f1.reshape(ref.shape) - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_inflow_enters_through_the_augmentation():
+    """R22: an inflow whose angular profile (peaked around Omega_x = 1) the completion
+    families represent poorly is carried into V_hat by its augmentation column: from a
+    zero state at rank 4, after three RK4 steps the scalar flux is 6x closer to S_N with
+    the column than without it, and the stored ranks stay at the floor."""
+    base = inputs.random_small_problem(8, nx=12, ny=12, tiles_x=2, tiles_y=2, n_mu=2,
+                                       n_phi=8, rank=4, r_aug_max=8, integrator="rk4",
+                                       nsteps=3)
+    nc = base.ncells
+    om = base.omega_x
+    h = np.where(om >= 0, np.exp(-20.0 * (1.0 - om) ** 2), 0.0)
+    wl = base.with_(sigma_s=np.zeros(nc), sigma_a=np.zeros(nc), source=np.zeros(nc),
+                    g0=np.zeros(nc), inflow={"x_lo": (np.ones(base.ny), h)})
+    ref = sn.scalar_flux(sn.run(wl), wl)
+    err = lambda o: np.linalg.norm(o.scalar_flux() - ref) / np.linalg.norm(ref)
+    with_col = dd_dlra.DDDLRA(wl).run()
+    without = dd_dlra.DDDLRA(wl)
+    without._inflow_column = lambda *args: None
+    without.run()
+    assert err(with_col) < 5e-3
+    assert err(with_col) < 0.3 * err(without)
+    assert all(r == 4 for r in with_col.ranks())
+
+
 @pytest.mark.parametrize("axis", ["x", "y"])
 def test_full_rank_psi_identity(axis):
     """At full rank, explicit Euler K-, S- and L-steps give

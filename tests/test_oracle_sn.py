@@ -133,3 +133,26 @@ def test_strang_splitting_is_second_order():
     assert all(0.8 < p < 1.3 for p in lie_order), lie_order
     assert all(1.8 < p < 2.3 for p in strang_order), strang_order
     assert strang[-1] < 0.2 * lie[-1]
+
+
+def test_mass_balance_with_inflow():
+    """Euler x-sweep with inflow data f = g(y) h(Omega) on both x sides: the change of
+    mass equals dt times (inflow through the faces - outflow through the faces), the
+    inflow being hy sum_j sum_q w_q |Omega_q| g_j h_q over the entering directions."""
+    wl = inputs.random_small_problem(3, nx=7, ny=5, tiles_x=1, tiles_y=1, n_mu=2, n_phi=8)
+    rng = np.random.default_rng(2)
+    g_lo, g_hi = rng.uniform(size=wl.ny), rng.uniform(size=wl.ny)
+    h_lo, h_hi = rng.uniform(size=wl.n), rng.uniform(size=wl.n)
+    wl = wl.with_(inflow={"x_lo": (g_lo, h_lo), "x_hi": (g_hi, h_hi)})
+    f = rng.uniform(size=(wl.ny, wl.nx, wl.n))
+    dt = 0.3 * wl.hx
+    f1 = f + dt * sn.advection_rhs(f, wl.omega_x, 1, wl.hx, 1.0, sn.inflow_ghosts(wl, 1))
+    mass = lambda u: wl.hx * wl.hy * np.sum(u @ wl.w)
+    ox = wl.omega_x
+    out_right = np.sum(wl.w * np.maximum(ox, 0) * f[:, -1, :].sum(axis=0)) * wl.hy
+    out_left = np.sum(wl.w * np.maximum(-ox, 0) * f[:, 0, :].sum(axis=0)) * wl.hy
+    in_left = np.sum(wl.w * np.maximum(ox, 0) * h_lo) * g_lo.sum() * wl.hy
+    in_right = np.sum(wl.w * np.maximum(-ox, 0) * h_hi) * g_hi.sum() * wl.hy
+    change = mass(f1) - mass(f)
+    assert abs(change - dt * (in_left + in_right - out_right - out_left)) < 1e-14 * mass(f)
+    assert dt * (in_left + in_right) > 1e-3 * mass(f)      # the inflow term matters
