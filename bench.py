@@ -350,6 +350,30 @@ def run_ours(args, torch):
                                  "discretisation at low rank (parity with the oracle's flux-split "
                                  "form is a GPU test)")
 
+    # ---- physical inflow: the Hohlraum-type problem in FP64 ---------------------------
+    infl = None
+    if not args.no_strang:
+        wh = inputs.hohlraum_problem()
+        sh_ = binding.Solver(wh, stream=sptr, use_graph=True)
+        sh_.step(args.warmup)
+        torch.cuda.synchronize()
+        evh = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evh[i][0].record(stream)
+            sh_.step(1)
+            evh[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_h = sum(a.elapsed_time(b) for a, b in evh) / 1e3
+        rk_, rt_ = sh_.ranks()
+        sh_.close()
+        infl = {"workload": wh.name, "value": wh.ncells * wh.n * args.steps * ws / t_h,
+                "unit": UNIT, "ms_per_step": t_h / args.steps * 1e3,
+                "ranks_after_warmup_and_steps": [int(x) for x in rk_],
+                "note": "inflow f = 1 through x = 0 for Omega_x >= 0, tolerance-adaptive "
+                        "ranks; parity with the oracle on inflow problems is a GPU test"}
+
     # ---- batched form ----------------------------------------------------------------
     batch = None
     if args.batch > 0:
@@ -387,6 +411,8 @@ def run_ours(args, torch):
         line["strang"] = strang
     if fsplit is not None:
         line["flux_split"] = fsplit
+    if infl is not None:
+        line["inflow"] = infl
     if batch is not None:
         line["batch"] = batch
     return line, rank

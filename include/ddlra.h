@@ -76,6 +76,15 @@ typedef struct dd_fields {
   const double* sigma_s;      /* host, nx*ny: scattering coefficient  (>= 0)      */
   const double* sigma_a;      /* host, nx*ny: absorption coefficient  (>= 0)      */
   const double* source;       /* host, nx*ny: isotropic source Q                  */
+  /* Physical inflow f(s, Omega) = g(s) h(Omega), constant in time, for the directions
+   * entering through a side (Omega_x >= 0 at x = x0, Omega_x < 0 at x = x1, likewise in
+   * y): the Hohlraum and boundary point-source inflow of Section 4.  Sides in the order
+   * x0, x1, y0, y1; a null g or h means zero inflow on that side.  In the scheme an
+   * inflow side acts as a neighbour: its data enter the ghost rows of the K-step and the
+   * augmentation of Algorithm 4 (one column m_in h |g|, |g|^2 = hx hy len sum g^2 over
+   * the subdomain's face, len its cell count along the axis). */
+  const double* inflow_g[4];  /* host: ny values (x sides) or nx values (y sides)  */
+  const double* inflow_h[4];  /* host: n values                                    */
 } dd_fields;
 
 enum { DD_RANK_FIXED = 0, DD_RANK_TOL = 1 };

@@ -47,7 +47,11 @@ class Quadrature(C.Structure):
 
 
 class Fields(C.Structure):
-    _fields_ = [("sigma_s", _dp), ("sigma_a", _dp), ("source", _dp)]
+    _fields_ = [("sigma_s", _dp), ("sigma_a", _dp), ("source", _dp),
+                ("inflow_g", _dp * 4), ("inflow_h", _dp * 4)]
+
+
+INFLOW_SIDES = ("x_lo", "x_hi", "y_lo", "y_hi")
 
 
 class Options(C.Structure):
@@ -146,7 +150,13 @@ class Solver:
             grids[i] = Grid(w.nx, w.ny, w.x0, w.x1, w.y0, w.y1)
             tils[i] = Tiling(len(xc) - 1, len(yc) - 1, xc.ctypes.data_as(_ip),
                              yc.ctypes.data_as(_ip))
-            flds[i] = Fields(_ptr(ss), _ptr(sa), _ptr(q))
+            ig, ih = (_dp * 4)(), (_dp * 4)()
+            for j, side in enumerate(INFLOW_SIDES):
+                if side in w.inflow:
+                    gs, hs = _d(w.inflow[side][0]), _d(w.inflow[side][1])
+                    self._keep += [gs, hs]
+                    ig[j], ih[j] = _ptr(gs), _ptr(hs)
+            flds[i] = Fields(_ptr(ss), _ptr(sa), _ptr(q), ig, ih)
             fixed = w.rank_mode == "fixed"
             opts[i] = Options(DD_RANK_FIXED if fixed else DD_RANK_TOL, w.rank, w.tol, w.r_min,
                               w.r_max, w.r_aug_max, DD_RK4 if w.integrator == "rk4" else DD_EULER,

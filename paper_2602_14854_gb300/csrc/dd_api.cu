@@ -77,6 +77,9 @@ struct dd_dlra {
   int *d_rlo, *d_rhi, *d_raug, *d_fbase, *d_fnx;
   double *d_hxk, *d_hyk, *d_dtk, *d_shk;
   double* d_dth;   // dt / 2 per subdomain (the half steps of the Strang splitting)
+  // physical inflow per subdomain and side (x-lo, x-hi, y-lo, y-hi), null without inflow
+  int* d_infl_on;
+  double *d_infl_g, *d_infl_hw, *d_infl_sc;
   // device: problem data
   double *d_ox, *d_oy, *d_w, *d_sw, *d_sig_s, *d_sig_t, *d_sQ, *d_angcand;
   int n_angcand, angcand_complete;
@@ -194,7 +197,8 @@ void free_all(dd_dlra* h) {
                   h->d_K, h->d_X1, h->d_L, h->d_V1, h->d_Kb, h->d_sm, h->d_part, h->d_sig,
                   h->d_rho, h->d_fluxw, h->d_m, h->d_rt, h->d_rx, h->d_rc, h->d_p, h->d_status,
                   h->d_keep, h->d_cexp, h->d_dm, h->d_mvec, h->d_rlo, h->d_rhi, h->d_raug, h->d_fbase,
-                  h->d_fnx, h->d_hxk, h->d_hyk, h->d_dtk, h->d_shk, h->d_dth};
+                  h->d_fnx, h->d_hxk, h->d_hyk, h->d_dtk, h->d_shk, h->d_dth, h->d_infl_on, h->d_infl_g,
+                  h->d_infl_hw, h->d_infl_sc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->graph_ready) cudaGraphExecDestroy(h->graph_exec);
@@ -231,6 +235,9 @@ static dd_status check_instance(const dd_grid* grid, const dd_tiling* tiling,
                                 const dd_fields* fields, const double* g0, const dd_options* opt) {
   if (!grid || !tiling || !fields || !g0 || !opt) return fail(DD_ERR_ARG, "null argument");
   if (!fields->sigma_s || !fields->sigma_a || !fields->source) return fail(DD_ERR_ARG, "null field");
+  for (int sd = 0; sd < 4; ++sd)
+    if ((fields->inflow_g[sd] == nullptr) != (fields->inflow_h[sd] == nullptr))
+      return fail(DD_ERR_ARG, "inflow needs both g and h on a side");
   if (grid->nx <= 0 || grid->ny <= 0 || !(grid->x1 > grid->x0) || !(grid->y1 > grid->y0))
     return fail(DD_ERR_ARG, "bad grid");
   if (tiling->tx <= 0 || tiling->ty <= 0 || !tiling->xcuts || !tiling->ycuts)
@@ -309,7 +316,11 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     raug_max = std::max(raug_max, opts[i].r_aug_max);
   }
   h->RS = RS;
-  h->MC = 3 * h->RS;
+  // inflow sides add up to two augmentation columns per axis (one per physical side)
+  bool any_inflow = false;
+  for (int i = 0; i < ninst; ++i)
+    for (int sd = 0; sd < 4; ++sd) any_inflow |= fields[i].inflow_g[sd] != nullptr;
+  h->MC = 3 * h->RS + (any_inflow ? 2 : 0);
   // column capacity of every tall and small matrix: the intermediate rank and the
   // augmentation input width both fit
   h->RC = std::max(raug_max, h->MC);
@@ -434,6 +445,43 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   UP_DBL(h->d_sig_t, sig_t.data(), Nt);
   UP_DBL(h->d_sQ, sQ.data(), Nt);
   UP_DBL(h->d_angcand, tab.data(), tab.size());
+  if (any_inflow) {
+    // per subdomain and side: on/off, face values sqrt(hx hy) g(line), angular column
+    // sqrt(w) m_in h and the augmentation scale |g|_x (the subdomain-sized virtual
+    // neighbour)
+    const int ML = h->maxlines;
+    std::vector<int> on(nsub * 4, 0);
+    std::vector<double> gf((size_t)nsub * 4 * ML, 0.0), hw((size_t)nsub * 4 * n, 0.0),
+        sc(nsub * 4, 0.0);
+    for (int k = 0; k < nsub; ++k) {
+      const SubGeo& sg = h->geo[k];
+      const dd_fields* f = &fields[sg.inst];
+      for (int sd = 0; sd < 4; ++sd) {
+        if (sg.nb[sd] >= 0 || !f->inflow_g[sd]) continue;
+        on[k * 4 + sd] = 1;
+        const bool xs = sd < 2;
+        const int lines = xs ? sg.nyk : sg.nxk, len = xs ? sg.nxk : sg.nyk;
+        double g2 = 0.0;
+        for (int l = 0; l < lines; ++l) {
+          const double gv = f->inflow_g[sd][xs ? sg.cy0 + l : sg.cx0 + l];
+          gf[((size_t)k * 4 + sd) * ML + l] = sg.sh * gv;
+          g2 += gv * gv;
+        }
+        sc[k * 4 + sd] = std::sqrt(sg.hx * sg.hy * len * g2);
+        const double* om = xs ? quad->omega_x : quad->omega_y;
+        for (int q = 0; q < n; ++q) {
+          const bool in = (sd % 2 == 0) ? om[q] >= 0.0 : om[q] < 0.0;
+          hw[((size_t)k * 4 + sd) * n + q] = in ? sw[q] * f->inflow_h[sd][q] : 0.0;
+        }
+      }
+    }
+    if (dalloc(&h->d_infl_on, on.size()) != cudaSuccess ||
+        cudaMemcpy(h->d_infl_on, on.data(), sizeof(int) * on.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(DD_ERR_CUDA, "upload inflow");
+    UP_DBL(h->d_infl_g, gf.data(), gf.size());
+    UP_DBL(h->d_infl_hw, hw.data(), hw.size());
+    UP_DBL(h->d_infl_sc, sc.data(), sc.size());
+  }
 #undef UP_DBL
   // state and workspace
   bool ok = true;
@@ -486,6 +534,8 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   P.mass_fix = opt->mass_fix;
   P.splitting = opt->splitting;
   P.kstep_split = opt->kstep_split;
+  P.infl_on = h->d_infl_on; P.infl_g = h->d_infl_g; P.infl_hw = h->d_infl_hw;
+  P.infl_sc = h->d_infl_sc;
   P.tau = opt->tau; P.accept = 0.5;
   P.r_floor = h->r_floor; P.r_aug_max = raug_max; P.RS = h->RS; P.WC = WC;
   P.angcand = h->d_angcand; P.n_angcand = h->n_angcand; P.angcand_complete = h->angcand_complete;

@@ -118,6 +118,10 @@ struct Problem {
   int mass_fix;           // conserved-moment correction at the end of every step
   int splitting;          // 0 Lie (x, y, collision), 1 Strang (x/2, y/2, collision, y/2, x/2)
   int kstep_split;        // C+/C- of the advection K-step: 0 eigen-split, 1 direction split
+  // physical inflow (null without): per subdomain and side (x-lo, x-hi, y-lo, y-hi) an
+  // on flag, face values sqrt(hx hy) g per line (maxlines), the angular column
+  // sqrt(w) m_in h (n) and its augmentation scale |g|_x
+  const int* infl_on; const double* infl_g; const double* infl_hw; const double* infl_sc;
   int rank_mode; double tol; double tau; double accept;
   int r_floor, r_aug_max, RS;
   int WC;                 // leading dimension of the orthonormalisation workspaces

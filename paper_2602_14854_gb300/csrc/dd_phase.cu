@@ -46,15 +46,20 @@ __device__ void bmm(double* out, int ldo, double alpha, const double* A, int lda
 // ---------------------------------------------------------------------------
 // augmentation input  L0 = [Vt S^T, Vt_lo S_lo^T, Vt_hi S_hi^T]
 // ---------------------------------------------------------------------------
-__global__ void k_aug_cols(Geo g, const int* r, int axis, int* m) {
+// Columns of L0: the own block, the neighbours' blocks and one column per physical
+// inflow side of the axis (the inflow's angular profile, a virtual neighbour).
+__global__ void k_aug_cols(Geo g, const int* r, int axis, int* m, const int* infl_on) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= g.nsub) return;
   int lo = g.nb[k * 4 + 2 * axis], hi = g.nb[k * 4 + 2 * axis + 1];
-  m[k] = r[k] + (lo >= 0 ? r[lo] : 0) + (hi >= 0 ? r[hi] : 0);
+  const int il = (lo < 0 && infl_on && infl_on[k * 4 + 2 * axis]) ? 1 : 0;
+  const int ih = (hi < 0 && infl_on && infl_on[k * 4 + 2 * axis + 1]) ? 1 : 0;
+  m[k] = r[k] + (lo >= 0 ? r[lo] : 0) + (hi >= 0 ? r[hi] : 0) + il + ih;
 }
 
 __global__ void k_build_L0(Geo g, const double* V, const double* S, const int* r, int axis,
-                           double* L0) {
+                           double* L0, const int* infl_on, const double* infl_hw,
+                           const double* infl_sc) {
   extern __shared__ double sh[];
   const int k = blockIdx.y, RC = g.RC;
   const int lo = g.nb[k * 4 + 2 * axis], hi = g.nb[k * 4 + 2 * axis + 1];
@@ -66,11 +71,20 @@ __global__ void k_build_L0(Geo g, const double* V, const double* S, const int* r
     for (int e = threadIdx.x; e < RC * RC; e += blockDim.x)
       sh[b * RC * RC + e] = src[b] >= 0 ? S[(long)src[b] * RC * RC + e] : 0.0;
   __syncthreads();
-  const int m = rr[0] + rr[1] + rr[2];
+  const int sl = 2 * axis, shi = 2 * axis + 1;
+  const int il = (lo < 0 && infl_on && infl_on[k * 4 + sl]) ? 1 : 0;
+  const int ih = (hi < 0 && infl_on && infl_on[k * 4 + shi]) ? 1 : 0;
+  const int mn = rr[0] + rr[1] + rr[2], m = mn + il + ih;
   const int q0 = blockIdx.x * 32;
   for (int e = threadIdx.x; e < 32 * m; e += blockDim.x) {
     int q = q0 + e / m, col = e % m;
     if (q >= g.n) continue;
+    if (col >= mn) {                               // inflow column: sqrt(w) m_in h |g|_x
+      const int side = (col == mn && il) ? sl : shi;
+      L0[((long)k * g.n + q) * g.MC + col] =
+          infl_hw[((long)k * 4 + side) * g.n + q] * infl_sc[k * 4 + side];
+      continue;
+    }
     int b = 0, t = col;
     while (t >= rr[b]) { t -= rr[b]; ++b; }
     const double* Vq = V + ((long)src[b] * g.n + q) * RC;
@@ -89,7 +103,9 @@ __global__ void k_build_L0(Geo g, const double* V, const double* S, const int* r
 __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* om,
                                                             const double* Vh, const double* V,
                                                             const int* r, const int* rt, int axis,
-                                                            int nchunk, int nblk, double* part) {
+                                                            int nchunk, int nblk, double* part,
+                                                            const int* infl_on,
+                                                            const double* infl_hw) {
   // Work items, enumerated densely so that every lane of an FP64 instruction is used:
   // the rt(rt+1)/2 pairs i <= j of the three symmetric blocks C, Mout_lo, Mout_hi (one
   // product v_i v_j per direction feeds all three), then the pairs of M, Min_lo and
@@ -100,11 +116,19 @@ __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* 
   const int ch = (n + nchunk - 1) / nchunk;
   const int q0 = c * ch, q1 = min(n, q0 + ch);
   const int lo = g.nb[k * 4 + 2 * axis], hi = g.nb[k * 4 + 2 * axis + 1];
-  const int rtk = rt[k], rk = r[k], rlo = lo >= 0 ? r[lo] : 0, rhi = hi >= 0 ? r[hi] : 0;
+  // a physical inflow side takes the neighbour's place with one row, the inflow's
+  // angular column sqrt(w) m_in h (already masked): Min = that column^T Vh
+  const bool il = lo < 0 && infl_on && infl_on[k * 4 + 2 * axis];
+  const bool ih = hi < 0 && infl_on && infl_on[k * 4 + 2 * axis + 1];
+  const int rtk = rt[k], rk = r[k];
+  const int rlo = lo >= 0 ? r[lo] : (il ? 1 : 0), rhi = hi >= 0 ? r[hi] : (ih ? 1 : 0);
   const double* Vhk = Vh + (long)k * n * RC;
   const double* Vk = V + (long)k * n * RC;
-  const double* Vlo = V + (long)(lo >= 0 ? lo : 0) * n * RC;
-  const double* Vhi = V + (long)(hi >= 0 ? hi : 0) * n * RC;
+  const double* Vlo = lo >= 0 ? V + (long)lo * n * RC
+                              : (il ? infl_hw + ((long)k * 4 + 2 * axis) * n : V);
+  const double* Vhi = hi >= 0 ? V + (long)hi * n * RC
+                              : (ih ? infl_hw + ((long)k * 4 + 2 * axis + 1) * n : V);
+  const int slo = lo >= 0 ? RC : 1, shi = hi >= 0 ? RC : 1;   // row strides
   double* out = part + ((long)k * nchunk + c) * nblk * RC * RC;
   for (int e = threadIdx.x; e < nblk * RC * RC; e += blockDim.x) out[e] = 0.0;
   __syncthreads();
@@ -136,16 +160,16 @@ __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* 
     } else {
       int u = w - nsym, blk;
       const double* Va;
-      int sel;                                     // 0 all directions, 1 Om >= 0, 2 Om < 0
-      if (u < n3) { blk = 3; Va = Vk; sel = 0; }
-      else if ((u -= n3) < n4) { blk = 4; Va = Vlo; sel = 1; }
-      else { u -= n4; blk = 5; Va = Vhi; sel = 2; }
+      int sel, sa;                                 // sel: 0 all directions, 1 Om >= 0, 2 Om < 0
+      if (u < n3) { blk = 3; Va = Vk; sel = 0; sa = RC; }
+      else if ((u -= n3) < n4) { blk = 4; Va = Vlo; sel = 1; sa = slo; }
+      else { u -= n4; blk = 5; Va = Vhi; sel = 2; sa = shi; }
       const int i = u / rtk, j = u - i * rtk;
       double s = 0.0;
       for (int q = q0; q < q1; ++q) {
         const long long ob = __double_as_longlong(om[q]);
         const bool ng = ob < 0 && ob != (long long)0x8000000000000000ull;
-        if (sel == 0 || (sel == 1 && !ng) || (sel == 2 && ng)) s += Va[q * RC + i] * Vhk[q * RC + j];
+        if (sel == 0 || (sel == 1 && !ng) || (sel == 2 && ng)) s += Va[q * sa + i] * Vhk[q * RC + j];
       }
       out[blk * RC * RC + i * RC + j] = s;
     }
@@ -278,6 +302,14 @@ __global__ void __launch_bounds__(DD_THREADS) k_small_adv1(Problem P, PhaseBufs 
   if (hi >= 0)
     bmm(SMB(B, P, k, SM_B_HI), RC, 1.0, B.S + (long)hi * RC * RC, RC, SMB(B, P, k, SM_MIN_HI), RC,
         rhi, rt, rhi, false);
+  // a physical inflow side: its face values carry the whole amplitude, B = Min (one row)
+  for (int side = 0; side < 2; ++side) {
+    const int nbs = side ? hi : lo;
+    if (nbs >= 0 || !P.infl_on || !P.infl_on[k * 4 + 2 * axis + side]) continue;
+    const double* Mi = SMB(B, P, k, side ? SM_MIN_HI : SM_MIN_LO);
+    double* Bs = SMB(B, P, k, side ? SM_B_HI : SM_B_LO);
+    for (int t = threadIdx.x; t < RC; t += blockDim.x) Bs[t] = t < rt ? Mi[t] : 0.0;
+  }
   if (P.kstep_split == 1) {
     // flux split: C+ and C- came with the Galerkin coefficients; |C| = C+ - C-
     const double* Cp = SMB(B, P, k, SM_CP);
@@ -429,6 +461,10 @@ __global__ void __launch_bounds__(DD_THREADS) k_ghost(Problem P, PhaseBufs B, in
     const int cell = cell_of(Ln, line, side == 0 ? Ln.len - 1 : 0);
     Xr = B.X + ((long)P.g.rowoff[nbk] + cell) * RC;
     rn = B.r[nbk];
+  } else if (P.infl_on && P.infl_on[k * 4 + 2 * axis + side]) {
+    // physical inflow: the face value sqrt(hx hy) g(line) times B = Min
+    Xr = P.infl_g + ((long)k * 4 + 2 * axis + side) * P.maxlines + line;
+    rn = 1;
   }
   double* out = B.Kb + (((long)k * 2 + side) * P.maxlines + line) * RC;
   for (int t = lane; t < RC; t += 32) {
@@ -1370,11 +1406,11 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   const int RC = g.RC, nsub = g.nsub;
   // 1. augmentation (Algorithm 4)
   pbeg(st, KS_AUG_COLS);
-  k_aug_cols<<<(nsub + 127) / 128, 128, 0, st>>>(g, B.r, axis, B.m);
+  k_aug_cols<<<(nsub + 127) / 128, 128, 0, st>>>(g, B.r, axis, B.m, P.infl_on);
   pend(st);
   pbeg(st, KS_BUILD_L0);
   k_build_L0<<<dim3((g.n + 31) / 32, nsub), DD_THREADS, sizeof(double) * 3 * RC * RC, st>>>(
-      g, B.V, B.S, B.r, axis, B.L0);
+      g, B.V, B.S, B.r, axis, B.L0, P.infl_on, P.infl_hw, P.infl_sc);
   pend(st);
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_AUG);
@@ -1390,7 +1426,8 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   const int nch_ac = std::min(2 * P.nchunk_ang, std::max(P.nchunk_sp, P.nchunk_ang));
   const int nblk_ac = P.kstep_split == 1 ? 8 : 6;
   k_ang_coeffs<<<dim3(nch_ac, nsub), DD_THREADS, 0, st>>>(
-      g, axis == 0 ? P.ox : P.oy, B.Vh, B.V, B.r, B.rt, axis, nch_ac, nblk_ac, B.part);
+      g, axis == 0 ? P.ox : P.oy, B.Vh, B.V, B.r, B.rt, axis, nch_ac, nblk_ac, B.part,
+      P.infl_on, P.infl_hw);
   pend(st);
   {
     Dst d;

@@ -216,6 +216,38 @@ def checkerboard_problem(**kw) -> Workload:
     return wl.with_(**kw) if kw else wl
 
 
+def hohlraum_problem(**kw) -> Workload:
+    """Hohlraum-type inflow problem: [0,1]^2, 128x128 cells, 4x4 subdomains, 512
+    directions (16 mu x 32 phi); radiation enters through x = 0 with f = 1 for
+    Omega_x >= 0 (the inflow of Section 4's Hohlraum test), zero inflow elsewhere;
+    vacuum except one absorbing block (sigma_a = 10) in the centre [0.4,0.6]^2, standing
+    in for the paper's block layout, which is given only as a figure; initial state
+    1e-9; tolerance-adaptive ranks (tol 1e-3, the paper's value for the domain
+    decomposition run), ranks 2..16, r_t <= 32; dt = h/2 up to t = 0.5."""
+    n_mu = kw.pop("n_mu", 16)
+    n_phi = kw.pop("n_phi", 32)
+    nx = ny = kw.pop("cells", 128)
+    tiles = kw.pop("tiles", 4)
+    t_end = kw.pop("t_end", 0.5)
+    ox, oy, w = product_quadrature(n_mu, n_phi)
+    X, Y = _cell_centres(nx, ny, 0.0, 1.0, 0.0, 1.0)
+    block = (np.abs(X - 0.5) < 0.1) & (np.abs(Y - 0.5) < 0.1)
+    h = 1.0 / nx
+    nsteps = int(math.ceil(t_end / (0.5 * h) - 1e-12))
+    wl = Workload(
+        name=f"hohlraum-{nx}x{ny}-{tiles}x{tiles}-n{ox.shape[0]}-tol",
+        nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0,
+        xcuts=uniform_cuts(nx, tiles), ycuts=uniform_cuts(ny, tiles),
+        omega_x=ox, omega_y=oy, w=w, sigma_s=np.zeros(nx * ny),
+        sigma_a=np.where(block, 10.0, 0.0), source=np.zeros(nx * ny),
+        g0=np.full(nx * ny, 1e-9), dt=t_end / nsteps, nsteps=nsteps,
+        rank_mode="tol", rank=2, tol=kw.pop("tol", 1e-3), r_min=2, r_max=kw.pop("r_max", 16),
+        r_aug_max=kw.pop("r_aug_max", 32), n_mu=n_mu, n_phi=n_phi, integrator="rk4",
+        inflow={"x_lo": (np.ones(ny), np.where(ox >= 0, 1.0, 0.0))},
+    )
+    return wl.with_(**kw) if kw else wl
+
+
 def lognormal_problem(seed: int = 2602, **kw) -> Workload:
     """Scale case: [0,1]^2, 512x512 cells, 8x8 subdomains of 64x64, 2048 directions
     (32 mu x 64 phi), fixed rank 20.  sigma_t lognormal per 16x16-cell patch
