@@ -371,6 +371,14 @@ __global__ void __launch_bounds__(DD_THREADS) k_small_adv1(Problem P, PhaseBufs 
       }
     Cp[e] = sp; Cn[e] = sm; Ca[e] = sp - sm;
   }
+  // P and lambda for the eigenbasis K-step (slots S3T and VB are free until the S-step)
+  double* Pout = SMB(B, P, k, SM_S3T);
+  double* lout = SMB(B, P, k, SM_VB);
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    const int u = e / RC, j = e % RC;
+    Pout[e] = (u < rt && j < rt) ? Pm[j * RC + u] : 0.0;
+  }
+  for (int j = threadIdx.x; j < RC; j += blockDim.x) lout[j] = j < rt ? lam[j] : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -566,6 +574,124 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
       // the increment is formed in TC, the update itself in FP64 (the start value is
       // re-read, so FP32 arithmetic never rounds the state)
       *Ke = *Ke + (double)(dt * acc[i]);
+    }
+  }
+}
+
+// K-step of the advection in the eigenbasis of C, where Appendix A's upwinding acts
+// column by column: with K~ = K P (ghost rows likewise) each RK stage is
+//   R~_ij = coef (lambda+_j (K~_ij - K~_(i-1)j) + lambda-_j (K~_(i+1)j - K~_ij)),
+// O(1) per entry instead of the 3 r_t products of the matrix stencil; the increment
+// dt sum_s b_s R~_s is rotated back with P^T and added to the FP64 state.  P and lambda
+// come from k_small_adv1 (small slots S3T and VB, free until the S-step).  Same lines-
+// per-CTA layout as k_kstep_adv; the entry indices are decoded once.
+#define KE_EPT 16
+template <typename TC>
+__global__ void __launch_bounds__(DD_THREADS) k_kstep_eig(Problem P, PhaseBufs B, int axis, int lpb) {
+  extern __shared__ double sh_raw[];
+  TC* sh = reinterpret_cast<TC*>(sh_raw);
+  const int k = blockIdx.y, RC = P.g.RC;
+  const Lines L = lines_of(P.g, k, axis);
+  const int l0 = blockIdx.x * lpb;
+  if (l0 >= L.nlines) return;
+  const int nl = min(lpb, L.nlines - l0);
+  const int rt = B.rt[k];
+  const int len = L.len;
+  TC* Pm = sh;                     // Pm[u * RC + j]: component u of eigenvector j
+  TC* lp = Pm + RC * RC;           // max(lambda, 0)
+  TC* ln = lp + RC;                // min(lambda, 0)
+  TC* Glo = ln + RC;               // lpb x RC ghost rows in the eigenbasis
+  TC* Ghi = Glo + lpb * RC;
+  TC* Kst = Ghi + lpb * RC;        // lpb x len x rt
+  const double* Pg = SMB(B, P, k, SM_S3T);
+  const double* lam = SMB(B, P, k, SM_VB);
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) Pm[e] = (TC)Pg[e];
+  for (int j = threadIdx.x; j < RC; j += blockDim.x) {
+    const double l = j < rt ? lam[j] : 0.0;
+    lp[j] = (TC)(l > 0.0 ? l : 0.0);
+    ln[j] = (TC)(l < 0.0 ? l : 0.0);
+  }
+  const int tot = nl * len * rt;
+  int code[KE_EPT];                // li << 20 | pos << 8 | t (li < 2^11, pos < 2^12, t < 2^8)
+#pragma unroll
+  for (int i = 0; i < KE_EPT; ++i) {
+    const int e = threadIdx.x + i * blockDim.x;
+    code[i] = 0;
+    if (e < tot) {
+      const int li = e / (len * rt), pos = (e / rt) % len, t = e % rt;
+      code[i] = (li << 20) | (pos << 8) | t;
+      Kst[e] = (TC)B.K[((long)P.g.rowoff[k] + cell_of(L, l0 + li, pos)) * RC + t];
+    }
+  }
+  __syncthreads();
+  // ghosts and K into the eigenbasis
+  for (int e = threadIdx.x; e < 2 * nl * rt; e += blockDim.x) {
+    const int side = e >= nl * rt, r = e - side * nl * rt, li = r / rt, j = r - li * rt;
+    const double* kb = B.Kb + (((long)k * 2 + side) * P.maxlines + l0 + li) * RC;
+    TC x = 0;
+    for (int u = 0; u < rt; ++u) x += (TC)kb[u] * Pm[u * RC + j];
+    (side ? Ghi : Glo)[li * RC + j] = x;
+  }
+  TC k0[KE_EPT], acc[KE_EPT];
+#pragma unroll
+  for (int i = 0; i < KE_EPT; ++i) {
+    const int e = threadIdx.x + i * blockDim.x;
+    k0[i] = 0; acc[i] = 0;
+    if (e < tot) {
+      const int t = code[i] & 255, rowe = e - t;   // entry of column 0 of this cell
+      TC x = 0;
+      for (int u = 0; u < rt; ++u) x += Kst[rowe + u] * Pm[u * RC + t];
+      k0[i] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < KE_EPT; ++i) {
+    const int e = threadIdx.x + i * blockDim.x;
+    if (e < tot) Kst[e] = k0[i];
+  }
+  __syncthreads();
+  const TC coef = (TC)(-P.c_adv / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]));
+  const TC dt = (TC)P.g.dtk[k];
+  const int nst = P.integrator == 1 ? 4 : 1;
+  for (int s = 0; s < nst; ++s) {
+    TC kv[KE_EPT];
+  #pragma unroll
+  for (int i = 0; i < KE_EPT; ++i) {
+      const int e = threadIdx.x + i * blockDim.x;
+      kv[i] = 0;
+      if (e < tot) {
+        const int li = code[i] >> 20, pos = (code[i] >> 8) & 4095, j = code[i] & 255;
+        const TC kc = Kst[e];
+        const TC kp = pos > 0 ? Kst[e - rt] : Glo[li * RC + j];
+        const TC kn = pos < len - 1 ? Kst[e + rt] : Ghi[li * RC + j];
+        kv[i] = coef * (lp[j] * (kc - kp) + ln[j] * (kn - kc));
+      }
+    }
+    __syncthreads();
+    const TC bs = (TC)((nst == 4) ? c_rk_b[s] : 1.0);
+    const TC an = (TC)((s + 1 < nst) ? c_rk_a[s + 1] : 0.0);
+  #pragma unroll
+  for (int i = 0; i < KE_EPT; ++i) {
+      const int e = threadIdx.x + i * blockDim.x;
+      if (e < tot) {
+        acc[i] += bs * kv[i];
+        Kst[e] = (s + 1 < nst) ? k0[i] + an * dt * kv[i] : acc[i];
+      }
+    }
+    __syncthreads();
+  }
+  // back to the original basis: increment_t = dt sum_j acc~_j P_tj, added in FP64
+#pragma unroll
+  for (int i = 0; i < KE_EPT; ++i) {
+    const int e = threadIdx.x + i * blockDim.x;
+    if (e < tot) {
+      const int li = code[i] >> 20, pos = (code[i] >> 8) & 4095, t = code[i] & 255;
+      const int rowe = e - t;
+      TC x = 0;
+      for (int j = 0; j < rt; ++j) x += Kst[rowe + j] * Pm[t * RC + j];
+      double* Ke = B.K + ((long)P.g.rowoff[k] + cell_of(L, l0 + li, pos)) * RC + t;
+      *Ke = *Ke + (double)(dt * x);
     }
   }
 }
@@ -1244,6 +1370,20 @@ size_t kstep_smem(const Problem& P, int lpb, int len) {
   return sizeof(double) * (3 * RC * RC + 2 * lpb * RC + (size_t)lpb * len * RC);
 }
 
+size_t kstep_eig_smem(const Problem& P, int lpb, int len) {
+  const int RC = P.g.RC;
+  return sizeof(double) * ((size_t)RC * RC + 2 * RC + 2 * lpb * RC + (size_t)lpb * len * RC);
+}
+
+int kstep_eig_lpb(const Problem& P, int len) {
+  const int RC = P.g.RC;
+  int lpb = max(1, (DD_THREADS * KE_EPT) / (len * RC));
+  while (lpb > 1 && kstep_eig_smem(P, lpb, len) > 200 * 1024) --lpb;
+  const long lines = (long)P.maxlines * P.g.nsub;
+  while (lpb > 1 && (lines + lpb - 1) / lpb < 2L * P.nsm) --lpb;
+  return lpb;
+}
+
 int kstep_lpb(const Problem& P, int len) {
   // lines per CTA: bounded by the register tile (KS_EPT per thread) and shared memory,
   // and small enough that the grid covers every SM about twice (the kernel is bound
@@ -1278,6 +1418,8 @@ cudaError_t phase_init() {
   e = cudaFuncSetAttribute(k_kstep_adv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_kstep_adv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_kstep_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_sstep_adv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sstep_smem(RC));
@@ -1451,13 +1593,20 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   // 6. K-step
   {
     const int len = P.maxlines;
-    const int lpb = kstep_lpb(P, len);
-    dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
     pbeg(st, KS_KSTEP_ADV);
-    if (P.prec == 1) {
-      k_kstep_adv<float><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+    if (P.kstep_split == 0 && P.prec == 0 && len < 4096) {
+      // FP64 eigen-split: in the eigenbasis (the mixed form keeps the FP32 matrix
+      // stencil, whose rounding does not pass through the two basis changes)
+      const int lpb = kstep_eig_lpb(P, len);
+      dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
+      k_kstep_eig<double><<<grid, DD_THREADS, kstep_eig_smem(P, lpb, len), st>>>(P, B, axis, lpb);
     } else {
-      k_kstep_adv<double><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+      const int lpb = kstep_lpb(P, len);
+      dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
+      if (P.prec == 1)
+        k_kstep_adv<float><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+      else
+        k_kstep_adv<double><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb);
     }
     pend(st);
   }
