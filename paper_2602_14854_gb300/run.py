@@ -19,6 +19,7 @@ WORKLOADS = {
     "pointsource": lambda: inputs.config_c1(),
     "checkerboard": lambda: inputs.checkerboard_problem(),
     "lognormal": lambda: inputs.lognormal_problem(),
+    "hohlraum": lambda: inputs.hohlraum_problem(),
 }
 
 
