@@ -685,6 +685,296 @@ __device__ __forceinline__ void jacobi_df_cols(float2* Bd, float2* Jd, int nr, i
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Column-per-lane sweeps for 33..64 columns: lane j holds columns j and j + 32 (slots 0
+// and 1), rows interleaved over the warps as above.  A sweep is 63 rounds: 31 rounds pair
+// the columns of each slot among themselves by the circle method (both slots at once, the
+// same partner lane), then 32 rounds pair column j of slot 0 with column (j + r) mod 32 of
+// slot 1.  Every column meets every other once per sweep; each round costs one shuffle per
+// held entry, as with one column per lane, and both lanes of a pair again form their dot
+// product from the same operands.
+// ---------------------------------------------------------------------------
+#define JW_JROWS2 ((64 + JW_WARPS - 1) / JW_WARPS)   // rows of J per warp (nc <= 64)
+
+__device__ __forceinline__ float4* jw_buffer4() {
+  __shared__ float4 jwb4[2 * JW_WARPS * 32];
+  return jwb4;
+}
+struct JwAddF2 {
+  __device__ float2 operator()(float2 a, float2 b) const { return make_float2(a.x + b.x, a.y + b.y); }
+};
+struct JwAddDF2 {
+  __device__ float4 operator()(float4 a, float4 b) const {
+    const float2 x = df_add(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    const float2 y = df_add(make_float2(a.z, a.w), make_float2(b.z, b.w));
+    return make_float4(x.x, x.y, y.x, y.y);
+  }
+};
+
+// Partner lane of the round: within-slot rounds (r < 31) by the circle method over the 32
+// lanes (same partner for both slots); cross rounds: slot 0 meets lane (lane + c) & 31 in
+// slot 1, slot 1 meets lane (lane - c) & 31 in slot 0, c = r - 31.
+__device__ __forceinline__ void jw2_partners(int lane, int r, int* p0, int* p1, bool* cross) {
+  if (r < 31) {
+    const int p = jw_partner(lane, r, 32);
+    *p0 = p; *p1 = p; *cross = false;
+  } else {
+    const int c = r - 31;
+    *p0 = (lane + c) & 31; *p1 = (lane - c) & 31; *cross = true;
+  }
+}
+
+template <int ROWS, bool WJ>
+__device__ __forceinline__ void jacobi_f32_cols2(float* Bf, float* Jf, int nr, int nc, int ld,
+                                                 float tol, float stop, int max_sweeps) {
+  float2* xb = jw_buffer();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int ph = 0;
+  float b[2][ROWS], v[2][JW_JROWS2];
+#pragma unroll
+  for (int sl = 0; sl < 2; ++sl) {
+    const int c = lane + 32 * sl;
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+      const int i = warp + JW_WARPS * k;
+      b[sl][k] = (c < nc && i < nr) ? Bf[c * ld + i] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < JW_JROWS2; ++k) {
+      const int i = warp + JW_WARPS * k;
+      v[sl][k] = (WJ && c < nc && i < nc) ? Jf[c * ld + i] : 0.f;
+    }
+  }
+  __syncthreads();
+  float al[2] = {0.f, 0.f};
+  float abs_thr = 0.f;
+  for (int sweep = 0; sweep < max_sweeps && nc > 1; ++sweep) {
+    {
+      float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < ROWS; ++k) {
+        t.x = __fmaf_rn(b[0][k], b[0][k], t.x);
+        t.y = __fmaf_rn(b[1][k], b[1][k], t.y);
+      }
+      t = jw_sum(t, xb, &ph, JwAddF2());
+      al[0] = t.x; al[1] = t.y;
+      if (sweep == 0) abs_thr = 1e-30f * warp_sum_t(al[0] + al[1]);
+    }
+    float lmax = 0.f;
+    for (int r = 0; r < 63; ++r) {
+      int p0, p1;
+      bool cross;
+      jw2_partners(lane, r, &p0, &p1, &cross);
+      // partner entries: slot 0 takes slot (cross ? 1 : 0) of lane p0, slot 1 takes slot
+      // (cross ? 0 : 1) of lane p1
+      float pb[2][ROWS], be[2];
+#pragma unroll
+      for (int k = 0; k < ROWS; ++k) {
+        pb[0][k] = __shfl_sync(0xffffffffu, cross ? b[1][k] : b[0][k], p0);
+        pb[1][k] = __shfl_sync(0xffffffffu, cross ? b[0][k] : b[1][k], p1);
+      }
+      be[0] = __shfl_sync(0xffffffffu, cross ? al[1] : al[0], p0);
+      be[1] = __shfl_sync(0xffffffffu, cross ? al[0] : al[1], p1);
+      float2 g = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < ROWS; ++k) {
+        g.x = __fmaf_rn(b[0][k], pb[0][k], g.x);
+        g.y = __fmaf_rn(b[1][k], pb[1][k], g.y);
+      }
+      g = jw_sum(g, xb, &ph, JwAddF2());
+      float c[2], sn[2], tg[2];
+#pragma unroll
+      for (int sl = 0; sl < 2; ++sl) {
+        const int col = lane + 32 * sl;
+        const int pcol = cross ? (sl ? p1 : p0 + 32) : ((sl ? p1 : p0) + 32 * sl);
+        const float gg = sl ? g.y : g.x;
+        const float pr = al[sl] * be[sl];
+        const bool ok = pcol != col && pcol < nc && col < nc && fabsf(gg) > abs_thr && pr > 0.f;
+        const float rel = ok ? fabsf(gg) * rsqrtf(pr) : 0.f;
+        lmax = fmaxf(lmax, rel);
+        const bool lo = col < pcol;
+        float cc, ss, tt;
+        jw_rotation(lo ? al[sl] : be[sl], lo ? be[sl] : al[sl], gg, &cc, &ss, &tt);
+        const bool rot = rel > tol;
+        c[sl] = rot ? cc : 1.f;
+        sn[sl] = rot ? (lo ? -ss : ss) : 0.f;
+        tg[sl] = rot ? (lo ? -(tt * gg) : tt * gg) : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < ROWS; ++k) {
+        b[0][k] = c[0] * b[0][k] + sn[0] * pb[0][k];
+        b[1][k] = c[1] * b[1][k] + sn[1] * pb[1][k];
+      }
+      al[0] += tg[0];
+      al[1] += tg[1];
+      if (WJ) {
+#pragma unroll
+        for (int k = 0; k < JW_JROWS2; ++k) {
+          const float q0 = __shfl_sync(0xffffffffu, cross ? v[1][k] : v[0][k], p0);
+          const float q1 = __shfl_sync(0xffffffffu, cross ? v[0][k] : v[1][k], p1);
+          v[0][k] = c[0] * v[0][k] + sn[0] * q0;
+          v[1][k] = c[1] * v[1][k] + sn[1] * q1;
+        }
+      }
+    }
+    const float mrel = warp_max_t(lmax);
+    if (mrel <= tol || mrel < stop) break;
+  }
+#pragma unroll
+  for (int sl = 0; sl < 2; ++sl) {
+    const int c = lane + 32 * sl;
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+      const int i = warp + JW_WARPS * k;
+      if (c < nc && i < nr) Bf[c * ld + i] = b[sl][k];
+    }
+    if (WJ) {
+#pragma unroll
+      for (int k = 0; k < JW_JROWS2; ++k) {
+        const int i = warp + JW_WARPS * k;
+        if (c < nc && i < nc) Jf[c * ld + i] = v[sl][k];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int ROWS, bool WJ>
+__device__ __forceinline__ void jacobi_df_cols2(float2* Bd, float2* Jd, int nr, int nc, int ld,
+                                                float tol, float stop, int max_sweeps,
+                                                float2* nrm_out = nullptr) {
+  float4* xd = jw_buffer4();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int ph = 0;
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 b[2][ROWS], v[2][WJ ? JW_JROWS2 : 1];
+#pragma unroll
+  for (int sl = 0; sl < 2; ++sl) {
+    const int c = lane + 32 * sl;
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+      const int i = warp + JW_WARPS * k;
+      b[sl][k] = (c < nc && i < nr) ? Bd[c * ld + i] : z2;
+    }
+    if (WJ) {
+#pragma unroll
+      for (int k = 0; k < (WJ ? JW_JROWS2 : 1); ++k) {
+        const int i = warp + JW_WARPS * k;
+        v[sl][k] = (c < nc && i < nc) ? Jd[c * ld + i] : z2;
+      }
+    }
+  }
+  __syncthreads();
+  float2 al[2] = {z2, z2};
+  float abs_thr = 0.f;
+  for (int sweep = 0; sweep < max_sweeps && nc > 1; ++sweep) {
+    {
+      float2 t0 = z2, t1 = z2;
+#pragma unroll
+      for (int k = 0; k < ROWS; ++k) {
+        t0 = df_add(t0, df_mul_sym(b[0][k], b[0][k]));
+        t1 = df_add(t1, df_mul_sym(b[1][k], b[1][k]));
+      }
+      const float4 t = jw_sum(make_float4(t0.x, t0.y, t1.x, t1.y), xd, &ph, JwAddDF2());
+      al[0] = make_float2(t.x, t.y); al[1] = make_float2(t.z, t.w);
+      if (sweep == 0) abs_thr = 1e-30f * warp_sum_t(al[0].x + al[1].x);
+    }
+    float lmax = 0.f;
+    for (int r = 0; r < 63; ++r) {
+      int p0, p1;
+      bool cross;
+      jw2_partners(lane, r, &p0, &p1, &cross);
+      float2 pb[2][ROWS], be[2];
+#pragma unroll
+      for (int k = 0; k < ROWS; ++k) {
+        pb[0][k] = df_shfl(0xffffffffu, cross ? b[1][k] : b[0][k], p0);
+        pb[1][k] = df_shfl(0xffffffffu, cross ? b[0][k] : b[1][k], p1);
+      }
+      be[0] = df_shfl(0xffffffffu, cross ? al[1] : al[0], p0);
+      be[1] = df_shfl(0xffffffffu, cross ? al[0] : al[1], p1);
+      float2 g0 = z2, g1 = z2;
+#pragma unroll
+      for (int k = 0; k < ROWS; ++k) {
+        g0 = df_add(g0, df_mul_sym(b[0][k], pb[0][k]));
+        g1 = df_add(g1, df_mul_sym(b[1][k], pb[1][k]));
+      }
+      const float4 gs = jw_sum(make_float4(g0.x, g0.y, g1.x, g1.y), xd, &ph, JwAddDF2());
+      const float2 g[2] = {make_float2(gs.x, gs.y), make_float2(gs.z, gs.w)};
+      float2 c[2], sn[2], tg[2];
+#pragma unroll
+      for (int sl = 0; sl < 2; ++sl) {
+        const int col = lane + 32 * sl;
+        const int pcol = cross ? (sl ? p1 : p0 + 32) : ((sl ? p1 : p0) + 32 * sl);
+        const float pr = al[sl].x * be[sl].x;
+        const bool ok = pcol != col && pcol < nc && col < nc && fabsf(g[sl].x) > abs_thr && pr > 0.f;
+        const float rel = ok ? fabsf(g[sl].x) * rsqrtf(pr) : 0.f;
+        lmax = fmaxf(lmax, rel);
+        const bool lo = col < pcol;
+        const float2 a_lo = lo ? al[sl] : be[sl], a_hi = lo ? be[sl] : al[sl];
+        float c32, s32, t;
+        jw_rotation(0.f, df_add(a_hi, df_neg(a_lo)).x, g[sl].x, &c32, &s32, &t);
+        const bool rot = rel > tol;
+        const float2 w = df_add(make_float2(1.f, 0.f), df_mulf(make_float2(t, 0.f), t));
+        const float y0 = rsqrtf(w.x);
+        const float2 h = df_add(make_float2(1.f, 0.f), df_neg(df_mulf(df_mulf(w, y0), y0)));
+        float2 cc = df_add(make_float2(y0, 0.f), df_mulf(h, 0.5f * y0));
+        const float2 ss = df_mulf(cc, t), gt = df_mulf(g[sl], t);
+        c[sl] = rot ? cc : make_float2(1.f, 0.f);
+        sn[sl] = rot ? (lo ? df_neg(ss) : ss) : z2;
+        tg[sl] = rot ? (lo ? df_neg(gt) : gt) : z2;
+      }
+#pragma unroll
+      for (int k = 0; k < ROWS; ++k) {
+        b[0][k] = df_add(df_mul(c[0], b[0][k]), df_mul(sn[0], pb[0][k]));
+        b[1][k] = df_add(df_mul(c[1], b[1][k]), df_mul(sn[1], pb[1][k]));
+      }
+      al[0] = df_add(al[0], tg[0]);
+      al[1] = df_add(al[1], tg[1]);
+      if (WJ) {
+#pragma unroll
+        for (int k = 0; k < (WJ ? JW_JROWS2 : 1); ++k) {
+          const float2 q0 = df_shfl(0xffffffffu, cross ? v[1][k] : v[0][k], p0);
+          const float2 q1 = df_shfl(0xffffffffu, cross ? v[0][k] : v[1][k], p1);
+          v[0][k] = df_add(df_mul(c[0], v[0][k]), df_mul(sn[0], q0));
+          v[1][k] = df_add(df_mul(c[1], v[1][k]), df_mul(sn[1], q1));
+        }
+      }
+    }
+    const float mrel = warp_max_t(lmax);
+    if (mrel <= tol || mrel < stop) break;
+  }
+  if (nrm_out) {
+    float2 t0 = z2, t1 = z2;
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+      t0 = df_add(t0, df_mul_sym(b[0][k], b[0][k]));
+      t1 = df_add(t1, df_mul_sym(b[1][k], b[1][k]));
+    }
+    const float4 t = jw_sum(make_float4(t0.x, t0.y, t1.x, t1.y), xd, &ph, JwAddDF2());
+    if (warp == 0) {
+      if (lane < nc) nrm_out[lane] = make_float2(t.x, t.y);
+      if (lane + 32 < nc) nrm_out[lane + 32] = make_float2(t.z, t.w);
+    }
+  }
+#pragma unroll
+  for (int sl = 0; sl < 2; ++sl) {
+    const int c = lane + 32 * sl;
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+      const int i = warp + JW_WARPS * k;
+      if (c < nc && i < nr) Bd[c * ld + i] = b[sl][k];
+    }
+    if (WJ) {
+#pragma unroll
+      for (int k = 0; k < (WJ ? JW_JROWS2 : 1); ++k) {
+        const int i = warp + JW_WARPS * k;
+        if (c < nc && i < nc) Jd[c * ld + i] = v[sl][k];
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // Two Newton-Schulz steps J <- J (3I - J^T J) / 2 on the n x n column-major Jd in
 // double-float (T, W: n x n scratch), making a J orthogonal to ~1e-7 orthogonal to
 // double-float rounding.
@@ -783,6 +1073,8 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
   __syncthreads();
   if (m <= 32 && blockDim.x == DD_THREADS)
     jacobi_f32_cols<JW_JROWS, true>(B32, J32, m, m, ld, 1e-6f, 1e-3f, 30);
+  else if (m <= 64 && blockDim.x == DD_THREADS)
+    jacobi_f32_cols2<64 / JW_WARPS, true>(B32, J32, m, m, ld, 1e-6f, 1e-3f, 30);
   else
     jacobi_f32(B32, J32, m, ld, flag, n32, 1e-6f, 1e-3f, 30);
   for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) Jd[e] = make_float2(J32[e], 0.f);
@@ -804,6 +1096,8 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
   __syncthreads();
   if (m <= 32 && blockDim.x == DD_THREADS)
     jacobi_df_cols<JW_JROWS, true>(Bd, Jd, m, m, ld, 1e-13f, 3e-7f, 10);
+  else if (m <= 64 && blockDim.x == DD_THREADS)
+    jacobi_df_cols2<64 / JW_WARPS, true>(Bd, Jd, m, m, ld, 1e-13f, 3e-7f, 10);
   else
     jacobi_df(Bd, Jd, m, ld, flag, T, 1e-13f, 3e-7f, 10);
   for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
@@ -816,7 +1110,7 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
   __syncthreads();
 }
 
-// Orthonormal basis of the column span of the nr x nc (nr <= 64, nc <= 32) column-major
+// Orthonormal basis of the column span of the nr x nc (nc <= nr <= 64) column-major
 // FP64 X of full column rank (leading dimension ld), by one-sided Jacobi: on return the
 // columns of X are those of X J / |X J| (J orthogonal, X J with orthogonal columns), to
 // double-float accuracy (~1e-13).  FP32 sweeps on a power-of-two scaled copy accumulate
@@ -854,7 +1148,9 @@ __device__ __forceinline__ void orth_cols_mixed(double* X, int nr, int nc, int l
     for (int r = lane; r < nc; r += 32) J32[c * ld + r] = (c == r) ? 1.f : 0.f;
   }
   __syncthreads();
-  if (nr <= 32)
+  if (nc > 32)                                          // then nr >= nc > 32
+    jacobi_f32_cols2<64 / JW_WARPS, true>(B32, J32, nr, nc, ld, 1e-6f, 1e-3f, 30);
+  else if (nr <= 32)
     jacobi_f32_cols<32 / JW_WARPS, true>(B32, J32, nr, nc, ld, 1e-6f, 1e-3f, 30);
   else
     jacobi_f32_cols<64 / JW_WARPS, true>(B32, J32, nr, nc, ld, 1e-6f, 1e-3f, 30);
@@ -872,7 +1168,9 @@ __device__ __forceinline__ void orth_cols_mixed(double* X, int nr, int nc, int l
       Bd[c * ld + r] = x;
     }
   __syncthreads();
-  if (nr <= 32)
+  if (nc > 32)
+    jacobi_df_cols2<64 / JW_WARPS, false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10, nd);
+  else if (nr <= 32)
     jacobi_df_cols<32 / JW_WARPS, false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10, nd);
   else
     jacobi_df_cols<64 / JW_WARPS, false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10, nd);

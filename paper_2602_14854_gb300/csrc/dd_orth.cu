@@ -251,11 +251,11 @@ __global__ void __launch_bounds__(DD_THREADS, 1) k_geig(OrthArgs a, const double
   // by unit vectors for the null space below the Cholesky threshold (1e-13 of the
   // largest diagonal entry, far below the rank threshold tau^2).  Jacobi on the
   // triangular factor needs a fraction of the sweeps Jacobi on G1 does (the graded
-  // columns are nearly orthogonal from the start).  Numerical rank above 32: Jacobi on
-  // G1 itself.
+  // columns are nearly orthogonal from the start).  (The Jacobi of G1 itself remains
+  // only for a rank beyond the 64-column capacity, which does not occur.)
   unsigned long long pmask = 0ull;
   const int kr = pchol_cols(Bc, Jc, m, RC, 1e-13, &pmask);
-  if (kr <= 32) {
+  if (kr <= 64) {
     orth_cols_mixed(Jc, m, kr, RC, X);
     complete_unit(Jc, m, kr, RC, pmask, lam, a.status);
   } else {
