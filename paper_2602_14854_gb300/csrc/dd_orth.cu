@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(DD_THREADS, 1) k_geig(OrthArgs a, const double
   double* X = sig + RC;             // scratch of the SVD
   int* perm = reinterpret_cast<int*>(X + (jacobi_mixed_scratch_bytes(RC) + 7) / 8);
   int* iv = perm + RC;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int tid = threadIdx.x;
   // the chunk partials are Grams of 2^-e_c A: G1 of 2^-emax A is their sum with
   // weights 4^(e_c - emax)
   __shared__ double fac[64];
@@ -446,7 +446,9 @@ __global__ void __launch_bounds__(DD_THREADS) k_chol_inv(OrthArgs a, const doubl
 // Completion to r_out columns (one CTA per subdomain; idle where keep >= r_out).
 // ORTH_COMPLETE first copies the input's columns.  Columns from the last accepted
 // one up to ldq are zero on return.
+#define KC_TAB 512
 __global__ void __launch_bounds__(DD_THREADS) k_complete(OrthArgs a, const int* keep_in) {
+  __shared__ double cxy[2 * KC_TAB];   // the two cosine vectors of a spatial candidate
   __shared__ double red[40];
   __shared__ double wv[DD_MAXC];
   __shared__ int iv[12];
@@ -501,10 +503,20 @@ __global__ void __launch_bounds__(DD_THREADS) k_complete(OrthArgs a, const int* 
     }
     double s = 0.0;
     if (a.spatial) {
+      // the candidate is a product of two cosine vectors: evaluate each once (the same
+      // expressions as per cell, so the candidate is bitwise the same)
       const int ca = iv[6], cb = iv[7];
+      const bool tab = nxk + nyk <= 2 * KC_TAB;
+      if (tab) {
+        for (int i = tid; i < nxk + nyk; i += blockDim.x)
+          cxy[i] = i < nxk ? cos(CUDART_PI * ca * (i + 0.5) / nxk)
+                           : cos(CUDART_PI * cb * (i - nxk + 0.5) / nyk);
+        __syncthreads();
+      }
       for (int i = tid; i < rows; i += blockDim.x) {
         int il = i % nxk, jl = i / nxk;
-        double v = cos(CUDART_PI * ca * (il + 0.5) / nxk) * cos(CUDART_PI * cb * (jl + 0.5) / nyk);
+        double v = tab ? cxy[il] * cxy[nxk + jl]
+                       : cos(CUDART_PI * ca * (il + 0.5) / nxk) * cos(CUDART_PI * cb * (jl + 0.5) / nyk);
         Q[(long)i * a.ldq + cur] = v;
         s += v * v;
       }
@@ -516,11 +528,19 @@ __global__ void __launch_bounds__(DD_THREADS) k_complete(OrthArgs a, const int* 
         s += v * v;
       }
     }
+    // scalar FP64 work (square roots, reciprocals) by one lane, broadcast through red[34]
     double n2 = block_sum(s, red);
     if (n2 == 0.0) { __syncthreads(); continue; }
-    const double inv = 1.0 / sqrt(n2);
+    if (tid == 0) red[34] = rsqrt(n2);
+    __syncthreads();
+    const double inv = red[34];
     for (int i = tid; i < rows; i += blockDim.x) Q[(long)i * a.ldq + cur] *= inv;
     __syncthreads();
+    // Gram-Schmidt against the accepted columns, a second pass only when the first one
+    // cancelled more than half of the squared norm (with at least 1/sqrt(2) of the unit
+    // candidate left, one pass already leaves it orthogonal to ~sqrt(2) eps: "twice is
+    // enough"); the squared norm after the last pass decides acceptance
+    double rn2 = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
       for (int t = warp; t < cur; t += nwarps) {
         double d = 0.0;
@@ -529,21 +549,20 @@ __global__ void __launch_bounds__(DD_THREADS) k_complete(OrthArgs a, const int* 
         if (lane == 0) wv[t] = d;
       }
       __syncthreads();
+      s = 0.0;
       for (int i = tid; i < rows; i += blockDim.x) {
         double v = Q[(long)i * a.ldq + cur];
         for (int t = 0; t < cur; ++t) v -= wv[t] * Q[(long)i * a.ldq + t];
         Q[(long)i * a.ldq + cur] = v;
+        s += v * v;
       }
+      rn2 = block_sum(s, red);
+      if (rn2 >= 0.5) break;
+    }
+    if (rn2 >= a.accept * a.accept) {
+      if (tid == 0) red[34] = rsqrt(rn2);
       __syncthreads();
-    }
-    s = 0.0;
-    for (int i = tid; i < rows; i += blockDim.x) {
-      double v = Q[(long)i * a.ldq + cur];
-      s += v * v;
-    }
-    double rn = sqrt(block_sum(s, red));
-    if (rn >= a.accept) {
-      const double ir = 1.0 / rn;
+      const double ir = red[34];
       for (int i = tid; i < rows; i += blockDim.x) Q[(long)i * a.ldq + cur] *= ir;
       ++cur;
     }
