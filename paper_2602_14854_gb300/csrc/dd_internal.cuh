@@ -101,6 +101,35 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   __syncthreads();
   return red[32];
 }
+// Three block-wide FP32 sums in one reduction, returned to every thread; red must hold
+// >= 99 floats.
+__device__ __forceinline__ void block_sum3f(float* a, float* b, float* c, float* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  float x = *a, y = *b, z = *c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
+    z += __shfl_xor_sync(0xffffffffu, z, o);
+  }
+  __syncthreads();
+  if (lane == 0) { red[wid] = x; red[32 + wid] = y; red[64 + wid] = z; }
+  __syncthreads();
+  if (wid == 0) {
+    x = lane < nw ? red[lane] : 0.f;
+    y = lane < nw ? red[32 + lane] : 0.f;
+    z = lane < nw ? red[64 + lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+      z += __shfl_xor_sync(0xffffffffu, z, o);
+    }
+    if (lane == 0) { red[96] = x; red[97] = y; red[98] = z; }
+  }
+  __syncthreads();
+  *a = red[96]; *b = red[97]; *c = red[98];
+}
 __device__ __forceinline__ double block_max(double v, double* red) {
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   v = warp_max(v);
@@ -126,6 +155,20 @@ __device__ __forceinline__ void rank_sort_desc(const double* v, int n, int* perm
     int r = 0;
     for (int j = 0; j < n; ++j) {
       const double y = rank_key(v[j]);
+      r += (y > x) || (y == x && j < i);
+    }
+    perm[r] = i;
+  }
+}
+
+// The same order for non-negative, non-NaN values, compared by their bit patterns
+// (which order as the values).
+__device__ __forceinline__ void rank_sort_desc_nonneg(const double* v, int n, int* perm) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const long long x = __double_as_longlong(v[i]);
+    int r = 0;
+    for (int j = 0; j < n; ++j) {
+      const long long y = __double_as_longlong(v[j]);
       r += (y > x) || (y == x && j < i);
     }
     perm[r] = i;

@@ -129,15 +129,17 @@ __device__ int pchol_cols(double* A, double* X, int m, int ld, double thr_rel,
     const int bi = pi[0];
     if (bi < 0) break;
     const double d = pc[0], id = pc[1];
-    for (int i = tid; i < m; i += blockDim.x)
-      X[k * ld + i] = ((done >> i) & 1ull) ? 0.0 : (i == bi ? d : A[bi * ld + i] * id);
+    // column k of X (warp 0) and the Schur update (every warp) both read the pivot
+    // column of A, which no thread writes in this step (bi is done)
+    if (warp == 0)
+      for (int i = lane; i < m; i += 32)
+        X[k * ld + i] = ((done >> i) & 1ull) ? 0.0 : (i == bi ? d : A[bi * ld + i] * id);
     done |= 1ull << bi;
-    __syncthreads();
     for (int j = warp; j < m; j += nw) {
       if ((done >> j) & 1ull) continue;
-      const double xj = X[k * ld + j];
+      const double xj = A[bi * ld + j] * id;
       for (int i = lane; i < m; i += 32)
-        if (!((done >> i) & 1ull)) A[j * ld + i] -= X[k * ld + i] * xj;
+        if (!((done >> i) & 1ull)) A[j * ld + i] -= (A[bi * ld + i] * id) * xj;
     }
     __syncthreads();
   }
@@ -147,14 +149,72 @@ __device__ int pchol_cols(double* A, double* X, int m, int ld, double thr_rel,
 
 // Completes the orthonormal columns 0..cur-1 of the m x m column-major V (leading
 // dimension ld) to m columns with unit vectors, first those of the indices outside
-// mask (in index order), then the others: each candidate is Gram-Schmidt'd twice in
-// FP64 and accepted when its squared norm after that exceeds 0.01 (at every stage some
-// unit vector keeps at least 1/m).  coef: m doubles of shared scratch.
+// mask (in index order), then the others, each accepted when its squared norm after
+// Gram-Schmidt exceeds 0.01 (at every stage some unit vector keeps at least 1/m).
+// The candidates outside mask are taken as a block: the span of the first cur columns
+// is removed from all of them at once (twice), then each is Gram-Schmidt'd against the
+// block columns accepted before it; the rest, when needed, one by one against
+// everything (twice).  coef: m doubles, W: 2 ld^2 doubles of shared scratch.
 __device__ void complete_unit(double* V, int m, int cur, int ld, unsigned long long mask,
-                              double* coef, unsigned* status) {
+                              double* coef, double* W, unsigned* status) {
   __shared__ double cred[40];
+  __shared__ int cidx[64];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int cand = 0; cand < 2 * m && cur < m; ++cand) {
+  if (cur >= m) return;
+  // indices outside mask, ascending
+  const unsigned long long out = ~mask & (m >= 64 ? ~0ull : ((1ull << m) - 1ull));
+  const int q = __popcll(out);
+  for (int t = tid; t < m; t += blockDim.x)
+    if ((out >> t) & 1ull) cidx[__popcll(out & ((1ull << t) - 1ull))] = t;
+  __syncthreads();
+  const int c0 = cur;
+  double* C = W + (long)ld * ld;
+  for (int e = tid; e < m * q; e += blockDim.x) {          // W = E - V V^T E
+    const int r = e % m, t = e / m, i = cidx[t];
+    double s = r == i ? 1.0 : 0.0;
+    for (int l = 0; l < c0; ++l) s -= V[l * ld + i] * V[l * ld + r];
+    W[t * ld + r] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < c0 * q; e += blockDim.x) {         // C = V^T W
+    const int l = e % c0, t = e / c0;
+    double s = 0.0;
+    for (int r = 0; r < m; ++r) s += V[l * ld + r] * W[t * ld + r];
+    C[t * ld + l] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * q; e += blockDim.x) {          // W -= V C
+    const int r = e % m, t = e / m;
+    double s = W[t * ld + r];
+    for (int l = 0; l < c0; ++l) s -= C[t * ld + l] * V[l * ld + r];
+    W[t * ld + r] = s;
+  }
+  __syncthreads();
+  for (int t = 0; t < q && cur < m; ++t) {
+    const int na = cur - c0;
+    for (int l = warp; l < na; l += nw) {
+      double s = 0.0;
+      for (int r = lane; r < m; r += 32) s += V[(c0 + l) * ld + r] * W[t * ld + r];
+      s = warp_sum(s);
+      if (lane == 0) coef[l] = s;
+    }
+    __syncthreads();
+    double* x = V + (long)cur * ld;
+    double n2 = 0.0;
+    for (int r = tid; r < m; r += blockDim.x) {
+      double s = W[t * ld + r];
+      for (int l = 0; l < na; ++l) s -= coef[l] * V[(c0 + l) * ld + r];
+      x[r] = s;
+      n2 += s * s;
+    }
+    n2 = block_sum(n2, cred);
+    if (n2 > 0.01) {
+      for (int r = tid; r < m; r += blockDim.x) x[r] *= rsqrt(n2);
+      ++cur;
+    }
+    __syncthreads();
+  }
+  for (int cand = 0; cand < 2 * m && cur < m; ++cand) {    // not expected: one by one
     const int i = cand < m ? cand : cand - m;
     const bool inmask = (mask >> i) & 1ull;
     if ((cand < m) == inmask) continue;
@@ -257,7 +317,7 @@ __global__ void __launch_bounds__(DD_THREADS, 1) k_geig(OrthArgs a, const double
   const int kr = pchol_cols(Bc, Jc, m, RC, 1e-13, &pmask);
   if (kr <= 64) {
     orth_cols_mixed(Jc, m, kr, RC, X);
-    complete_unit(Jc, m, kr, RC, pmask, lam, a.status);
+    complete_unit(Jc, m, kr, RC, pmask, lam, X, a.status);
   } else {
     for (int e = tid; e < RC * RC; e += blockDim.x) {
       const int col = e / RC, row = e % RC;
@@ -274,7 +334,7 @@ __global__ void __launch_bounds__(DD_THREADS, 1) k_geig(OrthArgs a, const double
   double* T = X;
   double* S = T + RC * RC;
   double* R = S + RC * RC;
-  __shared__ double rred[40];
+  __shared__ double rred[50];            // >= 99 floats for block_sum3f
   for (int e = tid; e < m * m; e += blockDim.x) {            // T = G1 V
     const int i = e / m, j = e % m;
     double x = 0.0;
@@ -303,9 +363,7 @@ __global__ void __launch_bounds__(DD_THREADS, 1) k_geig(OrthArgs a, const double
     rn += wgt * rf * rf;
     gn += wgt * gf * gf;
   }
-  offn = (float)block_sum((double)offn, rred);
-  rn = (float)block_sum((double)rn, rred);
-  gn = (float)block_sum((double)gn, rred);
+  block_sum3f(&offn, &rn, &gn, reinterpret_cast<float*>(rred));
   const float delta = 2.f * (sqrtf(offn) + sqrtf(gn) * sqrtf(rn));   // cluster separation
   for (int i = tid; i < m; i += blockDim.x) lam[i] = S[i * RC + i] / (1.0 - R[i * RC + i]);
   __syncthreads();
@@ -336,7 +394,7 @@ __global__ void __launch_bounds__(DD_THREADS, 1) k_geig(OrthArgs a, const double
     lam[j] = l > 0.0 ? l : 0.0;       // G1 is positive semidefinite
   }
   __syncthreads();
-  rank_sort_desc(lam, m, perm);
+  rank_sort_desc_nonneg(lam, m, perm);
   __syncthreads();
   for (int t = tid; t < m; t += blockDim.x) sig[t] = sqrt(lam[perm[t]]);   // of 2^-emax A
   __syncthreads();
