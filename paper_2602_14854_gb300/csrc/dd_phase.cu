@@ -828,7 +828,11 @@ __global__ void __launch_bounds__(DD_THREADS) k_sstep_adv(Problem P, PhaseBufs B
 
 // ---------------------------------------------------------------------------
 // L-step of the advection: every direction is an independent r_t-dimensional
-// linear ODE; one warp per direction, all RK stages fused.
+// linear ODE; one warp per direction, all RK stages fused.  In FP32 (TC = float) the
+// first-stage right-hand side a0 = g + A L0 is formed in FP64 (the interior and ghost
+// terms are large and cancel where a direction's flux through the subdomain is nearly
+// balanced) and the later stages add only A times the stage increment, so FP32 rounds
+// no term larger than the result it contributes to.
 // ---------------------------------------------------------------------------
 template <typename TC>
 __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B, int axis) {
@@ -844,6 +848,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
   TC* wsp = Ghi + RC * RC;          // per warp: vh, L0, Ls, g  (4*RC)
   double* S2d = sh_raw + 5 * RC * RC + 8 * 4 * RC;   // FP64 copy for the start value
   double* vhd = S2d + RC * RC;                         // per warp: FP64 vh (RC)
+  constexpr bool f32 = sizeof(TC) == sizeof(float);
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
     S2d[e] = SMB(B, P, k, SM_S2)[e];
     S2[e] = SMB(B, P, k, SM_S2)[e];
@@ -859,6 +864,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
   TC* Ls = L0 + RC;
   TC* gv = Ls + RC;
   double* vw = vhd + warp * RC;
+  double* l0w = vhd + (8 + warp) * RC;                 // per warp: FP64 L0 (FP32 form)
   const double* om = axis == 0 ? P.ox : P.oy;
   const TC dt = (TC)P.g.dtk[k];
   const TC hinv = (TC)(1.0 / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]));
@@ -887,9 +893,29 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
         }
         const TC s = (TC)sd;
         L0[i] = s; Ls[i] = s; gv[i] = gg; l0v[h] = s; l0d[h] = sd;
+        if (f32) l0w[i] = sd;
       }
     }
     __syncwarp();
+    if (f32 && oq != 0.0) {
+      // a0 = g + A L0 in FP64 into gv; Ls holds the stage increment (0 at stage 0)
+      const double* A64 = SMB(B, P, k, oq > 0.0 ? SM_AP : SM_AM);
+      const double* G64 = SMB(B, P, k, oq > 0.0 ? SM_G_LO : SM_G_HI);
+      const double gs = oq > 0.0 ? -1.0 : 1.0;
+      for (int h = 0; h < 2; ++h) {
+        int i = lane + 32 * h;
+        if (i < rt) {
+          double g64 = 0.0, a64 = 0.0;
+          for (int j = 0; j < rt; ++j) {
+            g64 += G64[i * RC + j] * vw[j];
+            a64 += A64[i * RC + j] * l0w[j];
+          }
+          gv[i] = (TC)(gs * g64 + a64);
+          Ls[i] = 0;
+        }
+      }
+      __syncwarp();
+    }
     if (oq != 0.0) {
       for (int s = 0; s < nst; ++s) {
         TC kv[2] = {0.0, 0.0};
@@ -908,7 +934,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
           int i = lane + 32 * h;
           if (i < rt) {
             accv[h] += bs * kv[h];
-            if (s + 1 < nst) Ls[i] = l0v[h] + an * dt * kv[h];
+            if (s + 1 < nst) Ls[i] = f32 ? an * dt * kv[h] : l0v[h] + an * dt * kv[h];
           }
         }
         __syncwarp();
@@ -1353,7 +1379,7 @@ __global__ void k_flux(Problem P, const double* X, const int* r, const double* w
 
 // TC working set plus an FP64 copy of S2 and one FP64 vh per warp
 size_t lstep_smem(int RC) {
-  return sizeof(double) * (5 * RC * RC + 8 * 4 * RC + RC * RC + 8 * RC);
+  return sizeof(double) * (5 * RC * RC + 8 * 4 * RC + RC * RC + 2 * 8 * RC);
 }
 
 size_t coll_lstep_smem(int RC) {
@@ -1594,9 +1620,10 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   {
     const int len = P.maxlines;
     pbeg(st, KS_KSTEP_ADV);
-    if (P.kstep_split == 0 && P.prec == 0 && len < 4096) {
-      // FP64 eigen-split: in the eigenbasis (the mixed form keeps the FP32 matrix
-      // stencil, whose rounding does not pass through the two basis changes)
+    if (P.kstep_split == 0 && len < 4096) {
+      // FP64 eigen-split in the eigenbasis, in the mixed form too: the FP32 matrix
+      // stencil rounds |C| K_i, C+ K_i-1 and C- K_i+1, which cancel to the much smaller
+      // increment, and its error grew to 1e-4..1e-3 of the flux on narrow sources
       const int lpb = kstep_eig_lpb(P, len);
       dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
       k_kstep_eig<double><<<grid, DD_THREADS, kstep_eig_smem(P, lpb, len), st>>>(P, B, axis, lpb);
