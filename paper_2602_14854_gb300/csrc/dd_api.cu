@@ -89,7 +89,11 @@ struct dd_dlra {
   // device: workspace
   double *d_L0, *d_Hw, *d_Hwa, *d_Vh, *d_K, *d_X1, *d_L, *d_V1, *d_Kb, *d_sm, *d_part;
   double *d_sig, *d_rho, *d_fluxw;
-  int *d_m, *d_rt, *d_rx, *d_rc, *d_p, *d_keep, *d_cexp;
+  int *d_m, *d_rt, *d_rx, *d_rc, *d_p, *d_keep, *d_cexp, *d_kcn, *d_kcur;
+  // spatial completion family: cosine tables per subdomain
+  double* d_sptab;
+  long long* d_spoff;
+  int* d_spnf;
   double *d_dm, *d_mvec;
   unsigned* d_status;
   dd::Problem P;
@@ -105,7 +109,7 @@ dd::PhaseBufs bufs(dd_dlra* h, int in, int out) {
   B.X1 = h->d_X1; B.L = h->d_L; B.V1 = h->d_V1; B.Kb = h->d_Kb; B.sm = h->d_sm;
   B.part = h->d_part; B.m = h->d_m; B.rt = h->d_rt; B.rx = h->d_rx; B.rc = h->d_rc;
   B.sig = h->d_sig; B.p = h->d_p; B.status = h->d_status;
-  B.keep = h->d_keep; B.cexp = h->d_cexp; B.dm = h->d_dm; B.mvec = h->d_mvec;
+  B.keep = h->d_keep; B.kcn = h->d_kcn; B.kcur = h->d_kcur; B.cexp = h->d_cexp; B.dm = h->d_dm; B.mvec = h->d_mvec;
   return B;
 }
 
@@ -198,7 +202,8 @@ void free_all(dd_dlra* h) {
                   h->d_rho, h->d_fluxw, h->d_m, h->d_rt, h->d_rx, h->d_rc, h->d_p, h->d_status,
                   h->d_keep, h->d_cexp, h->d_dm, h->d_mvec, h->d_rlo, h->d_rhi, h->d_raug, h->d_fbase,
                   h->d_fnx, h->d_hxk, h->d_hyk, h->d_dtk, h->d_shk, h->d_dth, h->d_infl_on, h->d_infl_g,
-                  h->d_infl_hw, h->d_infl_sc};
+                  h->d_infl_hw, h->d_infl_sc, h->d_kcn, h->d_kcur, h->d_sptab, h->d_spoff,
+                  h->d_spnf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->graph_ready) cudaGraphExecDestroy(h->graph_exec);
@@ -445,6 +450,39 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   UP_DBL(h->d_sig_t, sig_t.data(), Nt);
   UP_DBL(h->d_sQ, sQ.data(), Nt);
   UP_DBL(h->d_angcand, tab.data(), tab.size());
+  {
+    // spatial completion family (R11): per subdomain the cosines cos(pi f (i + 1/2) / n)
+    // of the x and y frequencies that its first kc_bmax(RC) candidates use
+    const int bm = dd::kc_bmax(RC);
+    std::vector<double> sptab;
+    std::vector<long long> spoff(nsub);
+    std::vector<int> spnf(2 * nsub);
+    for (int k = 0; k < nsub; ++k) {
+      const int nx = h->geo[k].nxk, ny = h->geo[k].nyk;
+      int dmax = nx + ny - 2, cum = 0;
+      for (int d = 0; d <= nx + ny - 2; ++d) {
+        cum += std::min(d, nx - 1) - std::max(0, d - (ny - 1)) + 1;
+        if (cum >= bm) { dmax = d; break; }
+      }
+      const int nfx = std::min(dmax, nx - 1) + 1, nfy = std::min(dmax, ny - 1) + 1;
+      spoff[k] = (long long)sptab.size();
+      spnf[2 * k] = nfx;
+      spnf[2 * k + 1] = nfy;
+      const double pi = 3.141592653589793;
+      for (int f = 0; f < nfx; ++f)
+        for (int i = 0; i < nx; ++i) sptab.push_back(std::cos(pi * f * (i + 0.5) / nx));
+      for (int f = 0; f < nfy; ++f)
+        for (int j = 0; j < ny; ++j) sptab.push_back(std::cos(pi * f * (j + 0.5) / ny));
+    }
+    UP_DBL(h->d_sptab, sptab.data(), sptab.size());
+    if (dalloc(&h->d_spoff, spoff.size()) != cudaSuccess ||
+        cudaMemcpy(h->d_spoff, spoff.data(), sizeof(long long) * spoff.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        dalloc(&h->d_spnf, spnf.size()) != cudaSuccess ||
+        cudaMemcpy(h->d_spnf, spnf.data(), sizeof(int) * spnf.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+      return bail(DD_ERR_CUDA, "upload problem data");
+  }
   if (any_inflow) {
     // per subdomain and side: on/off, face values sqrt(hx hy) g(line), angular column
     // sqrt(w) m_in h and the augmentation scale |g|_x (the subdomain-sized virtual
@@ -511,6 +549,8 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   ok &= dalloc(&h->d_rc, nsub) == cudaSuccess;
   ok &= dalloc(&h->d_p, nsub) == cudaSuccess;
   ok &= dalloc(&h->d_keep, nsub) == cudaSuccess;
+  ok &= dalloc(&h->d_kcn, nsub) == cudaSuccess;
+  ok &= dalloc(&h->d_kcur, nsub) == cudaSuccess;
   ok &= dalloc(&h->d_cexp, (long)nsub * 16) == cudaSuccess;
   ok &= dalloc(&h->d_dm, Nt) == cudaSuccess;
   ok &= dalloc(&h->d_mvec, (long)nsub * RC) == cudaSuccess;
@@ -539,6 +579,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   P.tau = opt->tau; P.accept = 0.5;
   P.r_floor = h->r_floor; P.r_aug_max = raug_max; P.RS = h->RS; P.WC = WC;
   P.angcand = h->d_angcand; P.n_angcand = h->n_angcand; P.angcand_complete = h->angcand_complete;
+  P.sptab = h->d_sptab; P.spoff = h->d_spoff; P.spnf = h->d_spnf;
   P.nchunk_sp = std::max(1, std::min(16, h->maxN / 64));
   {
     int nsm = 0;

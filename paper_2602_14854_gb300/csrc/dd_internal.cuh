@@ -175,6 +175,39 @@ __device__ __forceinline__ void rank_sort_desc_nonneg(const double* v, int n, in
   }
 }
 
+// Spatial completion candidates (the cosine products of the completion family, by
+// a + b, then a descending): at most kc_bmax(RC) of them are examined at once.
+__host__ __device__ __forceinline__ int kc_bmax(int RC) { return RC + (4 * RC + 2) / 3 + 1; }
+// doubles of scratch per subdomain: coefficients A (bmax x RC), B (RC x RC), then
+// W = Q0^T C ((RC + 1) x bmax, the candidates' squared norms in row RC)
+__host__ __device__ __forceinline__ size_t kc_region(int RC) {
+  return (size_t)(kc_bmax(RC) + RC) * RC + (size_t)(RC + 1) * kc_bmax(RC);
+}
+// Candidate j of an nxk x nyk subdomain: frequencies (a, b); false past the family.
+__host__ __device__ __forceinline__ bool kc_cand(int j, int nxk, int nyk, int* ca, int* cb) {
+  for (int d = 0; d <= nxk + nyk - 2; ++d) {
+    const int ahi = d < nxk - 1 ? d : nxk - 1;
+    const int alo = d - (nyk - 1) > 0 ? d - (nyk - 1) : 0;
+    const int cnt = ahi - alo + 1;
+    if (j < cnt) { *ca = ahi - j; *cb = d - *ca; return true; }
+    j -= cnt;
+  }
+  return false;
+}
+// Candidates examined for cur0 columns done out of r_out: the missing ones plus 4 cur0 / 3
+// for rejections.  The unit candidates are orthonormal, so their squared projections
+// onto the span of the cur0 first columns sum to at most cur0, and a candidate rejected
+// for that projection alone carries more than 3/4 of it; when the block still falls
+// short, the sequential completion adds the rest.
+__host__ __device__ __forceinline__ int kc_b(int nxk, int nyk, int cur0, int r_out, int RC) {
+  const int need = r_out - cur0;
+  if (need <= 0) return 0;
+  int b = need + (4 * cur0 + 2) / 3 + 1;
+  if (b > nxk * nyk) b = nxk * nyk;
+  if (b > kc_bmax(RC)) b = kc_bmax(RC);
+  return b;
+}
+
 // Round-robin (circle method) pairing for parallel Jacobi sweeps over mm
 // (even) indices: round r in [0, mm-1), pair i in [0, mm/2).  Both sums are below
 // 2 (mm - 1), so each reduction modulo mm - 1 is one compare-and-subtract.

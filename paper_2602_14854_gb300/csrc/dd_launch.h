@@ -12,7 +12,8 @@ enum KernelSlot {
   KS_AUG_COLS = 0, KS_BUILD_L0, KS_GEIG_AUG, KS_ANG_COEFFS, KS_REDUCE, KS_SMALL_ADV1, KS_TALL,
   KS_GHOST, KS_KSTEP_ADV, KS_SP_COEFFS, KS_SSTEP_ADV, KS_LSTEP_ADV, KS_GRAM, KS_TRUNC,
   KS_COLL_RANK, KS_COLL_A, KS_COLL_KSTEP, KS_COLL_SMALL, KS_COLL_LSTEP, KS_COLL_FINAL,
-  KS_FLUX, KS_COPY, KS_GEIG, KS_CHOL, KS_COMPLETE, KS_MASS, NSLOT
+  KS_FLUX, KS_COPY, KS_GEIG, KS_CHOL, KS_COMPLETE, KS_MASS, KS_KC_W, KS_KC_SEL, KS_KC_APPLY,
+  NSLOT
 };
 extern const char* const kSlotNames[NSLOT];
 
@@ -61,6 +62,11 @@ void launch_geig(const OrthArgs& a, const double* part, const int* cexp, int nch
 void launch_chol_inv(const OrthArgs& a, const double* part, int nchunk, double* sm, int sRi,
                      const int* keep, cudaStream_t st);
 void launch_complete(const OrthArgs& a, const int* keep, cudaStream_t st);
+// Spatial completion of a QR basis by Gram-Schmidt in coefficient space (dd_orth.cu):
+// tab/off/nf are the cosine tables of the candidate family, part the scratch region
+// (kc_region doubles per subdomain), kcn the accepted count, kcur the columns done.
+void launch_kc(const OrthArgs& a, const double* tab, const long long* off, const int* nf,
+               const int* keep, double* part, int* kcn, int* kcur, int maxN, cudaStream_t st);
 
 // Phase kernels (dd_phase.cu).  All buffers follow the layout described in
 // dd_internal.cuh; "small" matrices are RC x RC blocks, per subdomain stride RC*RC.
@@ -87,6 +93,8 @@ struct PhaseBufs {
   double* sig;     // diagnostics
   int* p;          // diagnostics
   int* keep;       // per subdomain: significant columns kept by the orthonormalisation
+  int* kcn;        // per subdomain: candidates accepted by the coefficient-space completion
+  int* kcur;       // per subdomain: columns done before the sequential completion
   int* cexp;       // per subdomain and row chunk: power-of-two exponent of a scaled Gram
   double* dm;      // per cell: scalar-flux change of the non-conservative parts (mass fix)
   double* mvec;    // per subdomain: RC-vector scratch of the mass bookkeeping
@@ -126,6 +134,9 @@ struct Problem {
   int r_floor, r_aug_max, RS;
   int WC;                 // leading dimension of the orthonormalisation workspaces
   const double* angcand; int n_angcand; int angcand_complete;
+  // spatial candidate family: per subdomain the cosines cos(pi f (i + 1/2) / n_x) for
+  // f < nf[2k] and cos(pi f (j + 1/2) / n_y) for f < nf[2k + 1], from offset spoff[k]
+  const double* sptab; const long long* spoff; const int* spnf;
   int nchunk_sp, nchunk_ang;   // chunks of the two-stage reductions
   int nsm;                     // streaming multiprocessors of the device
 };

@@ -647,6 +647,250 @@ void launch_chol_inv(const OrthArgs& a, const double* part, int nchunk, double* 
   pend(st);
 }
 
+// ---------------------------------------------------------------------------------------
+// Spatial completion in coefficient space.  The cosine candidates c_j are mutually
+// orthogonal, so Gram-Schmidt of c_j against the first cur0 columns Q0 and the columns
+// q_k = C a_k + Q0 b_k accepted before it needs only w_j = Q0^T c_j / |c_j|:
+//   q_k^T c_j / |c_j| = b_k^T w_j =: g_k,   |residual|^2 = 1 - |w_j|^2 - |g|^2,
+//   accepted (|residual| >= accept):  a = (e_j / |c_j| - sum g_k a_k) / |residual|,
+//                                     b = (-w_j - sum g_k b_k) / |residual|.
+// The same candidates in the same order with the same acceptance rule as the one-by-one
+// completion (and R11's definition), equal to it up to rounding; the passes over the
+// rows (W and the new columns) run on all SMs instead of one CTA per subdomain.
+// ---------------------------------------------------------------------------------------
+#define KC_TR3 32    // rows per CTA of k_kc_apply
+#define KC_JB 32     // grid rows per block of k_kc_w
+static_assert(DD_THREADS >= 160, "k_kc_w gives each of up to kc_bmax(DD_MAXC) candidates a thread");
+
+size_t kc_w_smem(int RC) { return sizeof(double) * KC_JB * kc_bmax(RC); }   // nfa <= b <= bmax
+size_t kc_sel_smem(int RC) { return sizeof(double) * ((size_t)(kc_bmax(RC) + RC) * RC + 2 * RC); }
+size_t kc_apply_smem(int RC) { return sizeof(double) * KC_TR3 * ((kc_bmax(RC) | 1) + (RC | 1)); }
+
+// W = Q0^T C and the candidates' squared norms.  A candidate is the product of an
+// x-cosine cx_a and a y-cosine cy_b, so W[l][j] = sum_jl cy_b(jl) sum_il Q0[jl nx + il][l]
+// cx_a(il): one CTA per (column l, subdomain) contracts x first for the nfa frequencies
+// in use (N nfa FMAs instead of N b) in blocks of KC_JB grid rows, then y per candidate;
+// CTA l = RC writes |c_j|^2 = |cx_a|^2 |cy_b|^2.
+__global__ void __launch_bounds__(DD_THREADS) k_kc_w(OrthArgs a, const double* tab,
+                                                     const long long* off, const int* nf,
+                                                     const int* keep, double* part) {
+  extern __shared__ double kq[];
+  __shared__ int cab[2 * 160];
+  const int k = blockIdx.y, l = blockIdx.x, RC = a.g.RC, bm = kc_bmax(RC), tid = threadIdx.x;
+  const int cur0 = keep[k], nxk = a.g.nxk[k], nyk = a.g.nyk[k];
+  const int b = kc_b(nxk, nyk, cur0, a.rout[k], RC);
+  if (b <= 0 || (l >= cur0 && l != RC)) return;
+  // candidate frequencies (all inside the tables, else k_kc_sel leaves it all to the
+  // sequential completion and nothing here is read)
+  __shared__ int nfa_s, okc;
+  if (tid == 0) { nfa_s = 0; okc = 1; }
+  __syncthreads();
+  for (int j = tid; j < b; j += blockDim.x) {
+    int ca = 0, cb = 0;
+    const bool ok = kc_cand(j, nxk, nyk, &ca, &cb) && ca < nf[2 * k] && cb < nf[2 * k + 1];
+    if (!ok) okc = 0;
+    cab[2 * j] = ok ? ca : 0;
+    cab[2 * j + 1] = ok ? cb : 0;
+    atomicMax(&nfa_s, ca + 1);
+  }
+  __syncthreads();
+  if (!okc) return;
+  const int nfa = nfa_s;
+  const double* tx = tab + off[k];
+  const double* ty = tx + (size_t)nf[2 * k] * nxk;
+  double* W = part + (size_t)k * kc_region(RC) + (size_t)(bm + RC) * RC;
+  if (l == RC) {
+    for (int j = tid; j < b; j += blockDim.x) {
+      const double* cx = tx + (size_t)cab[2 * j] * nxk;
+      const double* cy = ty + (size_t)cab[2 * j + 1] * nyk;
+      double sx = 0.0, sy = 0.0;
+      for (int i = 0; i < nxk; ++i) sx += cx[i] * cx[i];
+      for (int i = 0; i < nyk; ++i) sy += cy[i] * cy[i];
+      W[(size_t)RC * bm + j] = sx * sy;
+    }
+    return;
+  }
+  const double* Q = a.Q + (size_t)a.g.rowoff[k] * a.ldq + l;
+  double* T = kq;                                  // KC_JB x nfa
+  double acc = 0.0;                                // thread j < b: W[l][j]
+  for (int j0 = 0; j0 < nyk; j0 += KC_JB) {
+    const int nj = min(KC_JB, nyk - j0);
+    for (int e = tid; e < nj * nfa; e += blockDim.x) {
+      const int jl = e / nfa, fa = e - jl * nfa;
+      const double* row = Q + (size_t)(j0 + jl) * nxk * a.ldq;
+      const double* cx = tx + (size_t)fa * nxk;
+      double x = 0.0;
+      for (int i = 0; i < nxk; ++i) x += row[(size_t)i * a.ldq] * cx[i];
+      T[jl * nfa + fa] = x;
+    }
+    __syncthreads();
+    if (tid < b) {
+      const int ca = cab[2 * tid];
+      const double* cy = ty + (size_t)cab[2 * tid + 1] * nyk + j0;
+      for (int jl = 0; jl < nj; ++jl) acc += T[jl * nfa + ca] * cy[jl];
+    }
+    __syncthreads();
+  }
+  if (tid < b) W[(size_t)l * bm + tid] = acc;
+}
+
+// The selection in coefficient space (one CTA per subdomain): kcn = accepted count,
+// kcur = cur0 + kcn (cur0 when the tables do not cover the candidates: the sequential
+// completion then does all of it); the coefficients a_t (rows of A, b x kcn) and b_t
+// (rows of B, cur0 x kcn) go to the subdomain's scratch.
+__global__ void __launch_bounds__(DD_THREADS) k_kc_sel(OrthArgs a, const int* nf, const int* keep,
+                                                       double* part, int* kcn, int* kcur) {
+  extern __shared__ double ks[];
+  __shared__ int okf;
+  __shared__ double sc[2];
+  const int k = blockIdx.x, RC = a.g.RC, bm = kc_bmax(RC), tid = threadIdx.x;
+  const int cur0 = keep[k], r_out = a.rout[k], nxk = a.g.nxk[k], nyk = a.g.nyk[k];
+  const int b = kc_b(nxk, nyk, cur0, r_out, RC);
+  if (tid == 0) {
+    int ok = b > 0;
+    for (int j = 0; j < b && ok; ++j) {
+      int ca = 0, cb = 0;
+      ok = kc_cand(j, nxk, nyk, &ca, &cb) && ca < nf[2 * k] && cb < nf[2 * k + 1];
+    }
+    okf = ok;
+  }
+  __syncthreads();
+  if (!okf) {
+    if (tid == 0) { kcn[k] = 0; kcur[k] = cur0; }
+    return;
+  }
+  double* R = part + (size_t)k * kc_region(RC);
+  double* Ac = R;                                   // bm x RC
+  double* Bc = R + (size_t)bm * RC;                 // RC x RC
+  const double* W = R + (size_t)(bm + RC) * RC;     // (RC + 1) x bm
+  double* As = ks;                                  // b x RC
+  double* Bs = As + (size_t)bm * RC;                // cur0 x RC
+  double* wt = Bs + (size_t)RC * RC;                // cur0
+  double* g = wt + RC;                              // accepted count
+  const int need = r_out - cur0;
+  int nacc = 0;
+  for (int j = 0; j < b && nacc < need; ++j) {
+    // scalar FP64 work on one lane, broadcast through sc
+    if (tid == 0) {
+      const double n2 = W[(size_t)RC * bm + j];
+      sc[0] = n2 > 0.0 ? rsqrt(n2) : 0.0;
+    }
+    __syncthreads();
+    const double inv = sc[0];
+    if (inv != 0.0) {
+      for (int l = tid; l < cur0; l += blockDim.x) wt[l] = W[(size_t)l * bm + j] * inv;
+      __syncthreads();
+      for (int t = tid; t < nacc; t += blockDim.x) {
+        double x = 0.0;
+        for (int l = 0; l < cur0; ++l) x += Bs[l * RC + t] * wt[l];
+        g[t] = x;
+      }
+      __syncthreads();
+      if (tid < 32) {
+        double x = 0.0;
+        for (int i = tid; i < cur0; i += 32) x += wt[i] * wt[i];
+        for (int i = tid; i < nacc; i += 32) x += g[i] * g[i];
+        x = warp_sum(x);
+        if (tid == 0) {
+          const double rn2 = 1.0 - x;
+          sc[1] = rn2 >= a.accept * a.accept ? rsqrt(rn2) : 0.0;
+        }
+      }
+      __syncthreads();
+      const double ir = sc[1];
+      if (ir != 0.0) {
+        for (int i = tid; i < b + cur0; i += blockDim.x) {
+          if (i < b) {
+            double x = i == j ? inv : 0.0;
+            for (int t = 0; t < nacc; ++t) x -= g[t] * As[i * RC + t];
+            As[i * RC + nacc] = x * ir;
+          } else {
+            const int l = i - b;
+            double x = -wt[l];
+            for (int t = 0; t < nacc; ++t) x -= g[t] * Bs[l * RC + t];
+            Bs[l * RC + nacc] = x * ir;
+          }
+        }
+        ++nacc;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < b * nacc; e += blockDim.x) {
+    const int i = e / nacc, t = e - i * nacc;
+    Ac[i * RC + t] = As[i * RC + t];
+  }
+  for (int e = tid; e < cur0 * nacc; e += blockDim.x) {
+    const int l = e / nacc, t = e - l * nacc;
+    Bc[l * RC + t] = Bs[l * RC + t];
+  }
+  if (tid == 0) { kcn[k] = nacc; kcur[k] = cur0 + nacc; }
+}
+
+// The accepted columns Q[:, cur0 + t] = C a_t + Q0 b_t, 32 rows per CTA (candidate
+// values and Q0 rows staged in shared memory).
+__global__ void __launch_bounds__(DD_THREADS) k_kc_apply(OrthArgs a, const double* tab,
+                                                         const long long* off, const int* nf,
+                                                         const int* keep, const int* kcn,
+                                                         const double* part) {
+  extern __shared__ double kt[];
+  __shared__ int cab[2 * 160];
+  const int k = blockIdx.y, RC = a.g.RC, bm = kc_bmax(RC), tid = threadIdx.x;
+  const int nacc = kcn[k];
+  if (nacc <= 0) return;
+  const int rows = a.g.N[k], r0 = blockIdx.x * KC_TR3;
+  if (r0 >= rows) return;
+  const int cur0 = keep[k], nxk = a.g.nxk[k], nyk = a.g.nyk[k];
+  const int b = kc_b(nxk, nyk, cur0, a.rout[k], RC);
+  const int nr = min(KC_TR3, rows - r0);
+  const int cp = b | 1, qp = cur0 | 1;
+  double* Ct = kt;                                  // KC_TR3 x cp
+  double* Qt = Ct + KC_TR3 * (bm | 1);              // KC_TR3 x qp
+  double* Q = a.Q + (size_t)a.g.rowoff[k] * a.ldq;
+  for (int j = tid; j < b; j += blockDim.x) {
+    int ca = 0, cb = 0;
+    kc_cand(j, nxk, nyk, &ca, &cb);
+    cab[2 * j] = ca;
+    cab[2 * j + 1] = cb;
+  }
+  for (int e = tid; e < nr * cur0; e += blockDim.x) {
+    const int r = e / cur0, l = e - r * cur0;
+    Qt[r * qp + l] = Q[(size_t)(r0 + r) * a.ldq + l];
+  }
+  __syncthreads();
+  const double* tx = tab + off[k];
+  const double* ty = tx + (size_t)nf[2 * k] * nxk;
+  for (int e = tid; e < nr * b; e += blockDim.x) {
+    const int r = e / b, j = e - r * b, i = r0 + r;
+    Ct[r * cp + j] = tx[(size_t)cab[2 * j] * nxk + i % nxk] * ty[(size_t)cab[2 * j + 1] * nyk + i / nxk];
+  }
+  __syncthreads();
+  const double* Ac = part + (size_t)k * kc_region(RC);
+  const double* Bc = Ac + (size_t)bm * RC;
+  for (int e = tid; e < nr * nacc; e += blockDim.x) {
+    const int r = e / nacc, t = e - r * nacc;
+    double x = 0.0;
+    for (int j = 0; j < b; ++j) x += Ct[r * cp + j] * Ac[j * RC + t];
+    for (int l = 0; l < cur0; ++l) x += Qt[r * qp + l] * Bc[l * RC + t];
+    Q[(size_t)(r0 + r) * a.ldq + cur0 + t] = x;
+  }
+}
+
+void launch_kc(const OrthArgs& a, const double* tab, const long long* off, const int* nf,
+               const int* keep, double* part, int* kcn, int* kcur, int maxN, cudaStream_t st) {
+  const int RC = a.g.RC, nsub = a.g.nsub;
+  pbeg(st, KS_KC_W);
+  k_kc_w<<<dim3(RC + 1, nsub), DD_THREADS, kc_w_smem(RC), st>>>(a, tab, off, nf, keep, part);
+  pend(st);
+  pbeg(st, KS_KC_SEL);
+  k_kc_sel<<<nsub, DD_THREADS, kc_sel_smem(RC), st>>>(a, nf, keep, part, kcn, kcur);
+  pend(st);
+  pbeg(st, KS_KC_APPLY);
+  k_kc_apply<<<dim3((maxN + KC_TR3 - 1) / KC_TR3, nsub), DD_THREADS, kc_apply_smem(RC), st>>>(
+      a, tab, off, nf, keep, kcn, part);
+  pend(st);
+}
+
 void launch_complete(const OrthArgs& a, const int* keep, cudaStream_t st) {
   pbeg(st, KS_COMPLETE);
   k_complete<<<a.g.nsub, DD_THREADS, 0, st>>>(a, keep);
@@ -656,6 +900,15 @@ void launch_complete(const OrthArgs& a, const int* keep, cudaStream_t st) {
 cudaError_t orth_init() {
   cudaError_t e = cudaFuncSetAttribute(k_geig, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)geig_smem_bytes(DD_MAXC));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_kc_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kc_w_smem(DD_MAXC));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_kc_sel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kc_sel_smem(DD_MAXC));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_kc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kc_apply_smem(DD_MAXC));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)chol_smem_bytes(DD_MAXC));

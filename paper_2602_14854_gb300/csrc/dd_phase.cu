@@ -1428,12 +1428,15 @@ const char* const kSlotNames[NSLOT] = {
     "k_aug_cols", "k_build_L0", "k_geig(aug)", "k_ang_coeffs", "k_reduce", "k_small_adv1", "k_tall",
     "k_ghost", "k_kstep_adv", "k_sp_coeffs", "k_sstep_adv", "k_lstep_adv", "k_gram", "k_trunc",
     "k_coll_rank", "k_coll_a", "k_coll_kstep", "k_coll_small", "k_coll_lstep", "k_coll_final",
-    "k_flux", "memcpy", "k_geig", "k_chol_inv", "k_complete", "k_mass_fix"};
+    "k_flux", "memcpy", "k_geig", "k_chol_inv", "k_complete", "k_mass_fix", "k_kc_w", "k_kc_sel",
+    "k_kc_apply"};
 thread_local Prof* g_prof = nullptr;
 
 size_t part_elems(const Problem& P) {
   const int nc = P.nchunk_sp > P.nchunk_ang ? P.nchunk_sp : P.nchunk_ang;
-  return (size_t)P.g.nsub * nc * 8 * P.g.RC * P.g.RC;
+  const size_t grams = (size_t)P.g.nsub * nc * 8 * P.g.RC * P.g.RC;
+  const size_t kc = (size_t)P.g.nsub * kc_region(P.g.RC);   // the spatial completion's scratch
+  return grams > kc ? grams : kc;
 }
 
 // Kernel attributes are per process, not per solver: they are set for the largest
@@ -1566,7 +1569,14 @@ static void orthonormalize(const Problem& P, const PhaseBufs& B, cudaStream_t st
   nch = gram_partials(P, B, st, sp, W, P.WC, B.keep, nullptr);
   launch_chol_inv(a, B.part, nch, B.sm, SM_R1I, B.keep, st);
   tall(P, B, st, sp, W, P.WC, B.keep, 0, nullptr, SM_R1I, B.keep, 0, a.Q, a.ldq);
-  launch_complete(a, B.keep, st);
+  if (sp && a.mode == ORTH_QR) {
+    // cosine candidates: coefficient-space Gram-Schmidt on all SMs, then the one-by-one
+    // completion for whatever that leaves (normally nothing)
+    launch_kc(a, P.sptab, P.spoff, P.spnf, B.keep, B.part, B.kcn, B.kcur, P.maxN, st);
+    launch_complete(a, B.kcur, st);
+  } else {
+    launch_complete(a, B.keep, st);
+  }
 }
 
 void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st) {
