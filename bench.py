@@ -145,10 +145,12 @@ def kernel_work(name, wl, rt, rs):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
-# captures summarised in profiles/k_geig_k_gram_k_tall_pointsource_full.md and
-# profiles/k_kstep_adv_pointsource_full.md; None where no capture of the kernel as it
-# stands exists.
-NCU_TRAFFIC = {"k_geig": 0.660e6, "k_kstep_adv": None, "k_gram": 3.18e6, "k_tall": 3.21e6}
+# captures summarised in profiles/k_geig_k_gram_k_tall_k_kc_pointsource_full.md and
+# profiles/k_kstep_eig_k_lstep_adv_pointsource_full.md (k_kstep_adv is the profile name of
+# the FP64 K-step, the eigenbasis kernel k_kstep_eig); one captured launch each (k_geig: a
+# QR with m = 20 over 8 chunk partials; k_gram, k_tall: the 16-chunk / 512-CTA launch over
+# the spatial K).  None where no capture of the kernel as it stands exists.
+NCU_TRAFFIC = {"k_geig": 0.419e6, "k_kstep_adv": 3.57e6, "k_gram": 2.40e6, "k_tall": 2.40e6}
 
 
 def run_ours(args, torch):
@@ -244,8 +246,9 @@ def run_ours(args, torch):
     else:
         roof.update({"achieved": None, "frac": None})
     if name.startswith("k_geig"):
-        roof["note"] = ("one CTA per subdomain (16 of 152 SMs) running Jacobi sweeps: bound by "
-                        "barrier latency (ncu: 10% issue-active, barrier the top stall)")
+        roof["note"] = ("one CTA per subdomain (16 of 152 SMs) running Jacobi sweeps: latency-"
+                        "bound (ncu: 14% issue-active, 15% FP64 pipe on its SMs, 0.09% of DRAM "
+                        "bandwidth; Jacobi sweeps 56%, pivoted Cholesky 23% of its cycles)")
     kstep = prof.get("k_kstep_adv")
     if kstep:
         w = kernel_work("k_kstep_adv", wl, rt, rs)
