@@ -488,11 +488,14 @@ __global__ void __launch_bounds__(DD_THREADS) k_ghost(Problem P, PhaseBufs B, in
 // ---------------------------------------------------------------------------
 // K-step of the advection (Appendix A), all RK stages fused; a CTA owns whole lines
 // ---------------------------------------------------------------------------
-#define KS_EPT 24
+#define KS_EPT 24    // entries per thread of k_kstep_adv (lines x cells x r_t <= 256 x 24)
+#define KE_EPT 16    // entries per thread of k_kstep_eig (<= 256 x 16)
 // TC: arithmetic type (double for the FP64 path, float for the mixed path); the
-// factors stay FP64 in memory.
+// factors stay FP64 in memory.  big_only: only the subdomains whose line does not fit
+// k_kstep_eig's tile (len r_t > 256 KE_EPT; that kernel skips them).
 template <typename TC>
-__global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B, int axis, int lpb) {
+__global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B, int axis, int lpb,
+                                                          int big_only) {
   extern __shared__ double sh_raw[];
   TC* sh = reinterpret_cast<TC*>(sh_raw);
   const int k = blockIdx.y, RC = P.g.RC;
@@ -502,6 +505,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
   const int nl = min(lpb, L.nlines - l0);
   const int rt = B.rt[k];
   const int len = L.len;
+  if (big_only && (long)len * rt <= (long)DD_THREADS * KE_EPT) return;
   TC* Cp = sh;
   TC* Cn = Cp + RC * RC;
   TC* Ca = Cn + RC * RC;
@@ -585,7 +589,6 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
 // dt sum_s b_s R~_s is rotated back with P^T and added to the FP64 state.  P and lambda
 // come from k_small_adv1 (small slots S3T and VB, free until the S-step).  Same lines-
 // per-CTA layout as k_kstep_adv; the entry indices are decoded once.
-#define KE_EPT 16
 template <typename TC>
 __global__ void __launch_bounds__(DD_THREADS) k_kstep_eig(Problem P, PhaseBufs B, int axis, int lpb) {
   extern __shared__ double sh_raw[];
@@ -597,6 +600,9 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_eig(Problem P, PhaseBufs B
   const int nl = min(lpb, L.nlines - l0);
   const int rt = B.rt[k];
   const int len = L.len;
+  // a tile larger than the register tile (only with lpb = 1: a line longer than
+  // 256 KE_EPT / r_t) is left to k_kstep_adv, launched after this kernel for exactly these
+  if ((long)nl * len * rt > (long)DD_THREADS * KE_EPT) return;
   TC* Pm = sh;                     // Pm[u * RC + j]: component u of eigenvector j
   TC* lp = Pm + RC * RC;           // max(lambda, 0)
   TC* ln = lp + RC;                // min(lambda, 0)
@@ -1637,13 +1643,20 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
       const int lpb = kstep_eig_lpb(P, len);
       dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
       k_kstep_eig<double><<<grid, DD_THREADS, kstep_eig_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+      if ((long)len * g.RC > (long)DD_THREADS * KE_EPT) {
+        // subdomains whose line exceeds the eigenbasis kernel's tile: the FP64 matrix
+        // stencil (the same discrete operator)
+        const int lpb2 = kstep_lpb(P, len);
+        dim3 grid2((P.maxlines + lpb2 - 1) / lpb2, nsub);
+        k_kstep_adv<double><<<grid2, DD_THREADS, kstep_smem(P, lpb2, len), st>>>(P, B, axis, lpb2, 1);
+      }
     } else {
       const int lpb = kstep_lpb(P, len);
       dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
       if (P.prec == 1)
-        k_kstep_adv<float><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+        k_kstep_adv<float><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb, 0);
       else
-        k_kstep_adv<double><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+        k_kstep_adv<double><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb, 0);
     }
     pend(st);
   }

@@ -206,6 +206,23 @@ def test_tall_subdomain(B):
     s.close()
 
 
+def test_line_longer_than_the_eigenbasis_tile(B):
+    """256-cell x-lines at r_t = 17: 4352 entries per line, more than the eigenbasis
+    K-step's register tile (4096), so those lines take the FP64 matrix stencil while the
+    64-cell y-lines stay in the eigenbasis; FP64 to the parity bound, mixed to 1e-5."""
+    wl = inputs.random_small_problem(10, nx=512, ny=64, tiles_x=2, tiles_y=1, n_mu=4, n_phi=16,
+                                     rank=17, r_aug_max=24, integrator="rk4", nsteps=3)
+    s, o = run_both(B, wl)
+    assert int(s.ranks()[1][0].min()) * 256 > 4096       # every x-line beyond the tile
+    assert list(s.ranks()[0]) == o.ranks()
+    assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+    m = B.Solver(wl, precision="mixed")
+    m.step(wl.nsteps)
+    assert rel(m.scalar_flux(), o.scalar_flux()) < 1e-5
+    m.close()
+
+
 def test_many_directions(B):
     """2048 directions at rank 7 (augmentation input 2048 x 21)."""
     wl = inputs.random_small_problem(9, nx=8, ny=8, n_mu=16, n_phi=128, rank=7, r_aug_max=14,
