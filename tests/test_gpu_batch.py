@@ -65,3 +65,38 @@ def test_solvers_of_different_width_coexist(B):
     assert rel(sn.scalar_flux(), dd_dlra.DDDLRA(narrow).run(3).scalar_flux()) < 1e-9
     sw.close()
     sn.close()
+
+
+def test_full_size_batch_sampled_against_oracle(B):
+    """The 64-problem batch at full size (64^2/128^2/256^2 grids, 2x2/4x4 tilings,
+    128/512/1024 directions, ranks 4..21, RK4) in the benchmark's launch configuration:
+    one graph-replayed solver per direction group, 2 steps.  Three problems, sampled, are
+    checked against the oracle run on each alone: the 256^2, 2x2, rank-21 Gaussian (128-cell
+    lines at r_t up to 42, beyond the eigenbasis K-step's tile: the FP64 matrix stencil
+    takes them, in the mixed form too), a 512- and a 1024-direction narrow point source."""
+    groups = sorted(inputs.batch_problems(count=64, nsteps=2).items())
+    sample = ("batch8-", "batch19-", "batch1-")
+    checked = 0
+    for n, wls in groups:
+        picks = [(i, wl) for i, wl in enumerate(wls) if wl.name.startswith(sample)]
+        if not picks:
+            continue
+        s = B.Solver(wls, use_graph=True)
+        s.step(2)
+        rho = s.scalar_flux()
+        got = {i: s.instance_flux(rho, i) for i, _ in picks}
+        s.close()
+        got_mixed = {}
+        if any(wl.name.startswith("batch8-") for _, wl in picks):
+            m = B.Solver(wls, use_graph=True, precision="mixed")
+            m.step(2)
+            rm = m.scalar_flux()
+            got_mixed = {i: m.instance_flux(rm, i) for i, wl in picks if wl.name.startswith("batch8-")}
+            m.close()
+        for i, wl in picks:
+            ref = dd_dlra.DDDLRA(wl).run(2).scalar_flux()
+            assert rel(got[i], ref) < 1e-9, (wl.name, rel(got[i], ref))
+            if i in got_mixed:
+                assert rel(got_mixed[i], ref) < 1e-5, (wl.name, rel(got_mixed[i], ref))
+            checked += 1
+    assert checked == 3
