@@ -223,6 +223,26 @@ def test_line_longer_than_the_eigenbasis_tile(B):
     m.close()
 
 
+def test_checkerboard_full_size(B):
+    """The checkerboard at full size (224^2 cells, 7x7 subdomains, 1024 directions,
+    tolerance-adaptive ranks), 2 steps: flux and ranks against the oracle."""
+    wl = inputs.checkerboard_problem()
+    s, o = run_both(B, wl, nsteps=2, use_graph=True)
+    assert list(s.ranks()[0]) == o.ranks()
+    assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+
+
+def test_lognormal_full_size(B):
+    """The lognormal medium at full size (512^2 cells, 8x8 subdomains of 64^2, 2048
+    directions, rank 20, r_t <= 40), 1 step against the oracle."""
+    wl = inputs.lognormal_problem()
+    s, o = run_both(B, wl, nsteps=1, use_graph=True)
+    assert list(s.ranks()[0]) == o.ranks()
+    assert rel(s.scalar_flux(), o.scalar_flux()) < TOL
+    s.close()
+
+
 def test_many_directions(B):
     """2048 directions at rank 7 (augmentation input 2048 x 21)."""
     wl = inputs.random_small_problem(9, nx=8, ny=8, n_mu=16, n_phi=128, rank=7, r_aug_max=14,
