@@ -82,7 +82,7 @@ struct dd_dlra {
   double *d_infl_g, *d_infl_hw, *d_infl_sc;
   // device: problem data
   double *d_ox, *d_oy, *d_w, *d_sw, *d_sig_s, *d_sig_t, *d_sQ, *d_angcand;
-  int n_angcand, angcand_complete;
+  int n_angcand, angcand_complete, n_angorth;
   // device: state, double buffered
   double *d_X[2], *d_V[2], *d_S[2];
   int* d_r[2];
@@ -438,6 +438,29 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   std::vector<double> tab;
   angular_family(quad, h->ssum, tab, 4 * RC + 16, &h->angcand_complete);
   h->n_angcand = (int)(tab.size() / n);
+  {
+    // the longest leading part of the table whose candidates are mutually orthogonal
+    // (to 1e-12 in cosine; a product quadrature makes the whole table so): only those
+    // enter the coefficient-space completion
+    const int nc = h->n_angcand;
+    std::vector<double> nrm(nc);
+    for (int i = 0; i < nc; ++i) {
+      double x = 0.0;
+      for (int q = 0; q < n; ++q) x += tab[(size_t)i * n + q] * tab[(size_t)i * n + q];
+      nrm[i] = std::sqrt(x);
+    }
+    int po = 0;
+    for (; po < nc; ++po) {
+      bool ok = nrm[po] > 0.0;
+      for (int i = 0; i < po && ok; ++i) {
+        double x = 0.0;
+        for (int q = 0; q < n; ++q) x += tab[(size_t)i * n + q] * tab[(size_t)po * n + q];
+        ok = std::fabs(x) <= 1e-12 * nrm[i] * nrm[po];
+      }
+      if (!ok) break;
+    }
+    h->n_angorth = po;
+  }
 #define UP_DBL(dst, ptr, count)                                                                 \
   if (dalloc(&dst, count) != cudaSuccess ||                                                      \
       cudaMemcpy(dst, ptr, sizeof(double) * (count), cudaMemcpyHostToDevice) != cudaSuccess)     \
@@ -579,6 +602,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   P.tau = opt->tau; P.accept = 0.5;
   P.r_floor = h->r_floor; P.r_aug_max = raug_max; P.RS = h->RS; P.WC = WC;
   P.angcand = h->d_angcand; P.n_angcand = h->n_angcand; P.angcand_complete = h->angcand_complete;
+  P.n_angorth = h->n_angorth;
   P.sptab = h->d_sptab; P.spoff = h->d_spoff; P.spnf = h->d_spnf;
   P.nchunk_sp = std::max(1, std::min(16, h->maxN / 64));
   {

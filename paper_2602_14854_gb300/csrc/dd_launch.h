@@ -51,6 +51,7 @@ struct OrthArgs {
   int rank_mode; double tol; int r_floor; int r_aug_max;
   double tau; double accept;
   const double* angcand; int n_angcand; int angcand_complete;
+  int n_angorth;          // leading table candidates that are mutually orthogonal
   double* sig_out; int* p_out;
   unsigned* status;
 };
@@ -134,6 +135,7 @@ struct Problem {
   int r_floor, r_aug_max, RS;
   int WC;                 // leading dimension of the orthonormalisation workspaces
   const double* angcand; int n_angcand; int angcand_complete;
+  int n_angorth;          // leading table candidates mutually orthogonal to 1e-12
   // spatial candidate family: per subdomain the cosines cos(pi f (i + 1/2) / n_x) for
   // f < nf[2k] and cos(pi f (j + 1/2) / n_y) for f < nf[2k + 1], from offset spoff[k]
   const double* sptab; const long long* spoff; const int* spnf;

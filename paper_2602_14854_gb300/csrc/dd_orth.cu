@@ -658,10 +658,33 @@ void launch_chol_inv(const OrthArgs& a, const double* part, int nchunk, double* 
 // completion (and R11's definition), equal to it up to rounding; the passes over the
 // rows (W and the new columns) run on all SMs instead of one CTA per subdomain.
 // ---------------------------------------------------------------------------------------
+#define KC_TR 128    // rows per tile of k_kca_w
 #define KC_TR3 32    // rows per CTA of k_kc_apply
 #define KC_JB 32     // grid rows per block of k_kc_w
 static_assert(DD_THREADS >= 160, "k_kc_w gives each of up to kc_bmax(DD_MAXC) candidates a thread");
 
+// Subdomain k's completion: columns done (cur0), target (r_out), rows, and the number of
+// candidates examined at once (0: nothing to add).  Angle: the leading table candidates
+// that are mutually orthogonal (all of them under a product quadrature); the rest and the
+// unit vectors after them are left to the one-by-one completion.
+__device__ __forceinline__ int kc_plan(const OrthArgs& a, const int* keep, int k, int* cur0,
+                                       int* r_out, int* rows) {
+  const int RC = a.g.RC;
+  *cur0 = keep[k];
+  *r_out = a.mode == ORTH_AUG ? a.rt_out[k] : a.rout[k];
+  if (a.spatial) {
+    *rows = a.g.N[k];
+    return kc_b(a.g.nxk[k], a.g.nyk[k], *cur0, *r_out, RC);
+  }
+  *rows = a.g.n;
+  const int need = *r_out - *cur0;
+  if (need <= 0) return 0;
+  int b = need + (4 * *cur0 + 2) / 3 + 1;
+  b = min(b, a.n_angorth);
+  return min(b, kc_bmax(RC));
+}
+
+size_t kca_w_smem(int RC) { return sizeof(double) * (KC_TR * (RC | 1) + KC_TR); }
 size_t kc_w_smem(int RC) { return sizeof(double) * KC_JB * kc_bmax(RC); }   // nfa <= b <= bmax
 size_t kc_sel_smem(int RC) { return sizeof(double) * ((size_t)(kc_bmax(RC) + RC) * RC + 2 * RC); }
 size_t kc_apply_smem(int RC) { return sizeof(double) * KC_TR3 * ((kc_bmax(RC) | 1) + (RC | 1)); }
@@ -734,6 +757,54 @@ __global__ void __launch_bounds__(DD_THREADS) k_kc_w(OrthArgs a, const double* t
   if (tid < b) W[(size_t)l * bm + tid] = acc;
 }
 
+// W for the angular table candidates: one CTA per (candidate j, subdomain), 128-row tiles
+// of Q0 staged in shared memory (odd pitch), lane = row, warp w accumulating columns
+// w + 8 q; warp 0 also sums |c_j|^2.
+__global__ void __launch_bounds__(DD_THREADS) k_kca_w(OrthArgs a, const int* keep, double* part) {
+  extern __shared__ double kq[];
+  const int k = blockIdx.y, j = blockIdx.x, RC = a.g.RC, bm = kc_bmax(RC);
+  int cur0 = 0, r_out = 0, rows = 0;
+  const int b = kc_plan(a, keep, k, &cur0, &r_out, &rows);
+  if (j >= b) return;
+  const double* c = a.angcand + (size_t)j * a.g.n;
+  const double* Q = a.Q + (size_t)k * a.g.n * a.ldq;
+  const int pitch = cur0 | 1;
+  double* cv = kq + KC_TR * pitch;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  double nn = 0.0;
+  for (int r0 = 0; r0 < rows; r0 += KC_TR) {
+    const int nr = min(KC_TR, rows - r0);
+    for (int e = tid; e < nr * cur0; e += blockDim.x) {
+      const int r = e / cur0, l = e - r * cur0;
+      kq[r * pitch + l] = Q[(size_t)(r0 + r) * a.ldq + l];
+    }
+    for (int r = tid; r < nr; r += blockDim.x) cv[r] = c[r0 + r];
+    __syncthreads();
+    for (int r = lane; r < nr; r += 32) {
+      const double x = cv[r];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int l = warp + 8 * q;
+        if (l < cur0) acc[q] += kq[r * pitch + l] * x;
+      }
+      if (warp == 0) nn += x * x;
+    }
+    __syncthreads();
+  }
+  double* W = part + (size_t)k * kc_region(RC) + (size_t)(bm + RC) * RC;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double x = warp_sum(acc[q]);
+    const int l = warp + 8 * q;
+    if (lane == 0 && l < cur0) W[(size_t)l * bm + j] = x;
+  }
+  const double x = warp_sum(nn);
+  if (tid == 0) W[(size_t)RC * bm + j] = x;
+}
+
 // The selection in coefficient space (one CTA per subdomain): kcn = accepted count,
 // kcur = cur0 + kcn (cur0 when the tables do not cover the candidates: the sequential
 // completion then does all of it); the coefficients a_t (rows of A, b x kcn) and b_t
@@ -744,13 +815,16 @@ __global__ void __launch_bounds__(DD_THREADS) k_kc_sel(OrthArgs a, const int* nf
   __shared__ int okf;
   __shared__ double sc[2];
   const int k = blockIdx.x, RC = a.g.RC, bm = kc_bmax(RC), tid = threadIdx.x;
-  const int cur0 = keep[k], r_out = a.rout[k], nxk = a.g.nxk[k], nyk = a.g.nyk[k];
-  const int b = kc_b(nxk, nyk, cur0, r_out, RC);
+  int cur0 = 0, r_out = 0, rows = 0;
+  const int b = kc_plan(a, keep, k, &cur0, &r_out, &rows);
   if (tid == 0) {
     int ok = b > 0;
-    for (int j = 0; j < b && ok; ++j) {
-      int ca = 0, cb = 0;
-      ok = kc_cand(j, nxk, nyk, &ca, &cb) && ca < nf[2 * k] && cb < nf[2 * k + 1];
+    if (a.spatial) {
+      const int nxk = a.g.nxk[k], nyk = a.g.nyk[k];
+      for (int j = 0; j < b && ok; ++j) {
+        int ca = 0, cb = 0;
+        ok = kc_cand(j, nxk, nyk, &ca, &cb) && ca < nf[2 * k] && cb < nf[2 * k + 1];
+      }
     }
     okf = ok;
   }
@@ -838,31 +912,40 @@ __global__ void __launch_bounds__(DD_THREADS) k_kc_apply(OrthArgs a, const doubl
   const int k = blockIdx.y, RC = a.g.RC, bm = kc_bmax(RC), tid = threadIdx.x;
   const int nacc = kcn[k];
   if (nacc <= 0) return;
-  const int rows = a.g.N[k], r0 = blockIdx.x * KC_TR3;
+  int cur0 = 0, r_out = 0, rows = 0;
+  const int b = kc_plan(a, keep, k, &cur0, &r_out, &rows);
+  const int r0 = blockIdx.x * KC_TR3;
   if (r0 >= rows) return;
-  const int cur0 = keep[k], nxk = a.g.nxk[k], nyk = a.g.nyk[k];
-  const int b = kc_b(nxk, nyk, cur0, a.rout[k], RC);
+  const int nxk = a.spatial ? a.g.nxk[k] : 1, nyk = a.spatial ? a.g.nyk[k] : 1;
   const int nr = min(KC_TR3, rows - r0);
   const int cp = b | 1, qp = cur0 | 1;
   double* Ct = kt;                                  // KC_TR3 x cp
   double* Qt = Ct + KC_TR3 * (bm | 1);              // KC_TR3 x qp
-  double* Q = a.Q + (size_t)a.g.rowoff[k] * a.ldq;
-  for (int j = tid; j < b; j += blockDim.x) {
-    int ca = 0, cb = 0;
-    kc_cand(j, nxk, nyk, &ca, &cb);
-    cab[2 * j] = ca;
-    cab[2 * j + 1] = cb;
-  }
+  double* Q = a.Q + (a.spatial ? (size_t)a.g.rowoff[k] : (size_t)k * a.g.n) * a.ldq;
+  if (a.spatial)
+    for (int j = tid; j < b; j += blockDim.x) {
+      int ca = 0, cb = 0;
+      kc_cand(j, nxk, nyk, &ca, &cb);
+      cab[2 * j] = ca;
+      cab[2 * j + 1] = cb;
+    }
   for (int e = tid; e < nr * cur0; e += blockDim.x) {
     const int r = e / cur0, l = e - r * cur0;
     Qt[r * qp + l] = Q[(size_t)(r0 + r) * a.ldq + l];
   }
   __syncthreads();
-  const double* tx = tab + off[k];
-  const double* ty = tx + (size_t)nf[2 * k] * nxk;
-  for (int e = tid; e < nr * b; e += blockDim.x) {
-    const int r = e / b, j = e - r * b, i = r0 + r;
-    Ct[r * cp + j] = tx[(size_t)cab[2 * j] * nxk + i % nxk] * ty[(size_t)cab[2 * j + 1] * nyk + i / nxk];
+  if (a.spatial) {
+    const double* tx = tab + off[k];
+    const double* ty = tx + (size_t)nf[2 * k] * nxk;
+    for (int e = tid; e < nr * b; e += blockDim.x) {
+      const int r = e / b, j = e - r * b, i = r0 + r;
+      Ct[r * cp + j] = tx[(size_t)cab[2 * j] * nxk + i % nxk] * ty[(size_t)cab[2 * j + 1] * nyk + i / nxk];
+    }
+  } else {
+    for (int e = tid; e < nr * b; e += blockDim.x) {
+      const int r = e / b, j = e - r * b;
+      Ct[r * cp + j] = a.angcand[(size_t)j * a.g.n + r0 + r];
+    }
   }
   __syncthreads();
   const double* Ac = part + (size_t)k * kc_region(RC);
@@ -880,13 +963,17 @@ void launch_kc(const OrthArgs& a, const double* tab, const long long* off, const
                const int* keep, double* part, int* kcn, int* kcur, int maxN, cudaStream_t st) {
   const int RC = a.g.RC, nsub = a.g.nsub;
   pbeg(st, KS_KC_W);
-  k_kc_w<<<dim3(RC + 1, nsub), DD_THREADS, kc_w_smem(RC), st>>>(a, tab, off, nf, keep, part);
+  if (a.spatial)
+    k_kc_w<<<dim3(RC + 1, nsub), DD_THREADS, kc_w_smem(RC), st>>>(a, tab, off, nf, keep, part);
+  else
+    k_kca_w<<<dim3(kc_bmax(RC), nsub), DD_THREADS, kca_w_smem(RC), st>>>(a, keep, part);
   pend(st);
   pbeg(st, KS_KC_SEL);
   k_kc_sel<<<nsub, DD_THREADS, kc_sel_smem(RC), st>>>(a, nf, keep, part, kcn, kcur);
   pend(st);
   pbeg(st, KS_KC_APPLY);
-  k_kc_apply<<<dim3((maxN + KC_TR3 - 1) / KC_TR3, nsub), DD_THREADS, kc_apply_smem(RC), st>>>(
+  const int rows_max = a.spatial ? maxN : a.g.n;
+  k_kc_apply<<<dim3((rows_max + KC_TR3 - 1) / KC_TR3, nsub), DD_THREADS, kc_apply_smem(RC), st>>>(
       a, tab, off, nf, keep, kcn, part);
   pend(st);
 }
@@ -903,6 +990,9 @@ cudaError_t orth_init() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_kc_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kc_w_smem(DD_MAXC));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_kca_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kca_w_smem(DD_MAXC));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_kc_sel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kc_sel_smem(DD_MAXC));

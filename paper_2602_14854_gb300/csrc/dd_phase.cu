@@ -1558,6 +1558,7 @@ static OrthArgs orth_args(const Problem& P, const PhaseBufs& B, int spatial, int
   a.rank_mode = P.rank_mode; a.tol = P.tol; a.r_floor = P.r_floor; a.r_aug_max = P.r_aug_max;
   a.tau = P.tau; a.accept = P.accept;
   a.angcand = P.angcand; a.n_angcand = P.n_angcand; a.angcand_complete = P.angcand_complete;
+  a.n_angorth = P.n_angorth;
   a.sig_out = B.sig; a.p_out = B.p; a.status = B.status;
   a.r_own = B.r; a.rt_out = B.rt;
   return a;
@@ -1575,9 +1576,10 @@ static void orthonormalize(const Problem& P, const PhaseBufs& B, cudaStream_t st
   nch = gram_partials(P, B, st, sp, W, P.WC, B.keep, nullptr);
   launch_chol_inv(a, B.part, nch, B.sm, SM_R1I, B.keep, st);
   tall(P, B, st, sp, W, P.WC, B.keep, 0, nullptr, SM_R1I, B.keep, 0, a.Q, a.ldq);
-  if (sp && a.mode == ORTH_QR) {
-    // cosine candidates: coefficient-space Gram-Schmidt on all SMs, then the one-by-one
-    // completion for whatever that leaves (normally nothing)
+  if (a.mode == ORTH_QR || (!sp && a.mode == ORTH_AUG)) {
+    // mutually orthogonal candidates (the cosines; the angular table): coefficient-space
+    // Gram-Schmidt on all SMs, then the one-by-one completion for whatever that leaves
+    // (normally nothing; in angle the unit vectors after the table)
     launch_kc(a, P.sptab, P.spoff, P.spnf, B.keep, B.part, B.kcn, B.kcur, P.maxN, st);
     launch_complete(a, B.kcur, st);
   } else {
