@@ -16,23 +16,27 @@
 // Method (every pass over the rows runs on all SMs; only m x m work is per
 // subdomain):
 //   G1 = A^T A                      chunked Gram (k_gram; partials summed by k_geig)
-//   G1 = V diag(lambda) V^T         k_geig: one-sided Jacobi of G1 (FP32 sweeps,
-//                                   double-float finish); sigma_j = lambda_j^1/2
-//                                   give the rank decision; M = V_keep diag(sigma)^-1
+//   G1 = V diag(lambda) V^T         k_geig: pivoted Cholesky G1 = X X^T, one-sided
+//                                   Jacobi on X (FP32 sweeps, double-float finish),
+//                                   one FP64 refinement; sigma_j = lambda_j^1/2 give
+//                                   the rank decision; M = V_keep diag(sigma)^-1
 //   U1 = A M                        k_tall: the leading left singular vectors, up to
 //                                   errors of order eps |A|^2 / sigma_j^2
 //   G2 = U1^T U1                    k_gram + k_chol_inv (G2^-1/2 by Newton-Schulz in
 //                                   double-float)
 //   Q  = U1 G2^-1/2                 k_tall: orthonormal to ~1e-14
-//   completion                      k_complete (subdomains with keep < r_out)
+//   completion                      k_kc_w / k_kca_w, k_kc_sel, k_kc_apply (QR and
+//                                   augmentation: Gram-Schmidt in coefficient space),
+//                                   then k_complete (what that leaves; the collision's
+//                                   padding)
 // The span of Q is that of the leading left singular vectors of A.  The
 // eigenvector error eps |G1| / gap enters the result weighted by the discarded
 // sigma_j, orders of magnitude below the FP64 parity bound (the CPU oracle takes
 // the SVD of A itself).
 //
 // Completion: missing columns are taken in order from a fixed exactly-orthogonal
-// candidate family, each Gram-Schmidt'd twice and accepted when its residual norm
-// is >= accept:
+// candidate family, each Gram-Schmidt'd against the columns so far and accepted when
+// its residual norm is >= accept:
 //   space: cos(pi a (i+1/2)/nx_k) cos(pi b (j+1/2)/ny_k), by a+b then a descending;
 //   angle: the table built at create time (P_2l(mu) x cos/sin(m phi), weighted by
 //          sqrt(w)), then the unit vectors.
