@@ -91,9 +91,12 @@ enum { DD_RANK_FIXED = 0, DD_RANK_TOL = 1 };
 enum { DD_EULER = 0, DD_RK4 = 1 };
 /* Arithmetic of the step.  DD_FP64: FP64 throughout, except that the small
  * eigen/singular value problems (m x m, m <= 64) run FP32 Jacobi sweeps finished in
- * double-float arithmetic (~1e-13 relative).  DD_MIXED: in addition, FP32 arithmetic
- * for the eigen-upwind stencil and for the increments of the K-, L- and
- * collision-step ODEs (each update itself is added in FP64). */
+ * double-float arithmetic (~1e-13 relative; the eigensolver of the orthonormalisation adds
+ * one FP64 refinement).  DD_MIXED: in addition, FP32 arithmetic for the increments of the
+ * collision-step ODEs and for the L-step's stage corrections (its first-stage right-hand
+ * side is formed in FP64); each update itself is added in FP64.  The advection K-step is
+ * FP64 in both (Appendix A's eigenbasis form), and so is the matrix stencil of the
+ * flux-split form except in DD_MIXED. */
 enum { DD_FP64 = 0, DD_MIXED = 1 };
 
 typedef struct dd_options {
