@@ -43,6 +43,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(t_local, ws, device):
+    """The timed region's seconds, maximum over the ranks (each rank runs an independent
+    replica of the workload; the caller brackets the region with barriers)."""
+    if ws <= 1:
+        return t_local
+    import torch
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_step, steps, ws, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_step * steps * ws / seconds
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples while the timed region runs."""
 
@@ -187,12 +203,8 @@ def run_ours(args, torch):
     if ws > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_ours = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([t_ours], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ours = float(t.item())
-    value = units * args.steps * ws / t_ours
+    t_ours = max_over_ranks(sum(step_ms) / 1e3, ws, dev)
+    value = job_value(units, args.steps, ws, t_ours)
 
     # ---- per-kernel profile (event pair around every launch), 4 steps ------------------
     prof = s.profile(4)
