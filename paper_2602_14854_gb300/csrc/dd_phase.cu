@@ -390,6 +390,9 @@ struct TallArgs {
   const double* Bm; int bsmall;     // small matrix index inside the subdomain block (or -1: Bm is per-k RC*RC stride)
   const int* ncols; int ncols_fix;
   double* Y; int ldy;
+  // optional: the Gram Y^T Y of each row tile (nc x nc, RC x RC stride) to
+  // gpart[k * gridDim.x + tile], the chunk partials of the next orthonormalisation step
+  double* gpart;
 };
 #define TALL_ROWS 32
 size_t tall_smem(int RC, int ldy) {
@@ -409,7 +412,12 @@ __global__ void __launch_bounds__(DD_THREADS) k_tall(Geo g, TallArgs a, double* 
   const int nc = a.ncols ? a.ncols[k] : a.ncols_fix;
   const int r0 = blockIdx.x * TALL_ROWS;
   const int nrow = min(TALL_ROWS, rows - r0);
-  if (nrow <= 0) return;
+  double* gp = a.gpart ? a.gpart + ((long)k * gridDim.x + blockIdx.x) * RC * RC : nullptr;
+  if (nrow <= 0) {
+    if (gp)
+      for (int e = tid; e < nc * nc; e += DD_THREADS) gp[(e / nc) * RC + e % nc] = 0.0;
+    return;
+  }
   const double* Bk = (a.bsmall >= 0) ? smbase + ((long)k * NSMALL + a.bsmall) * RC * RC
                                      : a.Bm + (long)k * RC * RC;
   const int SA = ni | 1, SY = a.ldy | 1;
@@ -443,6 +451,20 @@ __global__ void __launch_bounds__(DD_THREADS) k_tall(Geo g, TallArgs a, double* 
   __syncthreads();
   for (int r = warp; r < nrow; r += DD_THREADS / 32)
     for (int j = lane; j < a.ldy; j += 32) a.Y[(rb + r0 + r) * a.ldy + j] = Ys[r * SY + j];
+  if (gp) {
+    // the tile's Gram, pairs (i <= j) enumerated densely, rows in order
+    const int npair = nc * (nc + 1) / 2;
+    for (int p = tid; p < npair; p += DD_THREADS) {
+      int j = (int)((sqrtf(8.f * p + 1.f) - 1.f) * 0.5f);
+      j += (j + 1) * (j + 2) / 2 <= p;
+      j -= j * (j + 1) / 2 > p;
+      const int i = p - j * (j + 1) / 2;
+      double x = 0.0;
+      for (int r = 0; r < nrow; ++r) x += Ys[r * SY + i] * Ys[r * SY + j];
+      gp[i * RC + j] = x;
+      gp[j * RC + i] = x;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1530,10 +1552,12 @@ static int gram_partials(const Problem& P, const PhaseBufs& B, cudaStream_t st, 
 
 static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spatial,
                  const double* A, int lda, const int* ninner, int ninner_fix, const double* Bm,
-                 int bsmall, const int* ncols, int ncols_fix, double* Y, int ldy) {
+                 int bsmall, const int* ncols, int ncols_fix, double* Y, int ldy,
+                 double* gpart = nullptr) {
   TallArgs a;
   a.spatial = spatial; a.A = A; a.lda = lda; a.ninner = ninner; a.ninner_fix = ninner_fix;
   a.Bm = Bm; a.bsmall = bsmall; a.ncols = ncols; a.ncols_fix = ncols_fix; a.Y = Y; a.ldy = ldy;
+  a.gpart = gpart;
   const int rows = spatial ? P.maxN : P.g.n;
   dim3 grid((rows + TALL_ROWS - 1) / TALL_ROWS, P.g.nsub);
   pbeg(st, KS_TALL);
@@ -1572,8 +1596,13 @@ static void orthonormalize(const Problem& P, const PhaseBufs& B, cudaStream_t st
   double* W = sp ? B.Hw : B.Hwa;
   int nch = gram_partials(P, B, st, sp, a.A, a.lda, a.acols, B.cexp);
   launch_geig(a, B.part, B.cexp, nch, B.sm, SM_QM, B.keep, st);
-  tall(P, B, st, sp, a.A, a.lda, a.acols, 0, nullptr, SM_QM, B.keep, 0, W, P.WC);
-  nch = gram_partials(P, B, st, sp, W, P.WC, B.keep, nullptr);
+  // U1 = A M; its Gram from the same tiles when their partials fit the buffer (one partial
+  // per 32-row tile, counted from each subdomain's first row), else by k_gram
+  const int ntile = ((sp ? P.maxN : P.g.n) + TALL_ROWS - 1) / TALL_ROWS;
+  const bool fuse = ntile <= 8 * std::max(P.nchunk_sp, P.nchunk_ang);
+  tall(P, B, st, sp, a.A, a.lda, a.acols, 0, nullptr, SM_QM, B.keep, 0, W, P.WC,
+       fuse ? B.part : nullptr);
+  nch = fuse ? ntile : gram_partials(P, B, st, sp, W, P.WC, B.keep, nullptr);
   launch_chol_inv(a, B.part, nch, B.sm, SM_R1I, B.keep, st);
   tall(P, B, st, sp, W, P.WC, B.keep, 0, nullptr, SM_R1I, B.keep, 0, a.Q, a.ldq);
   if (a.mode == ORTH_QR || (!sp && a.mode == ORTH_AUG)) {
