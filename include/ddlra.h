@@ -139,7 +139,8 @@ typedef struct dd_dlra* dd_dlra_t;
  * every subdomain in a tile row has the same height, in a tile column the same
  * width.  stream is a cudaStream_t (NULL = the legacy default stream).
  * Errors: DD_ERR_ARG for inconsistent sizes or options (r_aug_max > 64,
- * 3*stored-rank cap > 64, fewer directions than 3*stored-rank cap), DD_ERR_CUDA.
+ * 3*stored-rank cap > 64, fewer directions than 3*stored-rank cap, a subdomain side
+ * times r_aug_max above 6144: the K-step keeps a whole line of K in one CTA), DD_ERR_CUDA.
  */
 dd_status dd_dlra_create(const dd_grid* grid, const dd_tiling* tiling,
                          const dd_quadrature* quad, const dd_fields* fields,
