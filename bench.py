@@ -164,10 +164,10 @@ def kernel_work(name, wl, rt, rs):
 # captures summarised in profiles/k_geig_k_gram_k_tall_k_kc_pointsource_full.md and
 # profiles/k_kstep_eig_k_lstep_adv_pointsource_full.md (k_kstep_adv is the profile name of
 # the FP64 K-step, the eigenbasis kernel k_kstep_eig); one captured launch each (k_geig: a
-# QR with m = 20 over 8 chunk partials; k_gram: the 16-chunk launch over the spatial K).
-# None where no capture of the kernel as it stands exists (k_tall has since taken over the
-# second Gram of the orthonormalisation).
-NCU_TRAFFIC = {"k_geig": 0.419e6, "k_kstep_adv": 3.57e6, "k_gram": 2.40e6, "k_tall": None}
+# QR with m = 20 over 8 chunk partials; k_gram: the 16-chunk launch over the spatial K;
+# k_tall: the 512-CTA launch over the spatial rows, from profiles/k_tall_pointsource_full.md).
+# None where no capture of the kernel as it stands exists.
+NCU_TRAFFIC = {"k_geig": 0.419e6, "k_kstep_adv": 3.57e6, "k_gram": 2.40e6, "k_tall": 3.21e6}
 
 
 def run_ours(args, torch):
