@@ -438,29 +438,9 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   std::vector<double> tab;
   angular_family(quad, h->ssum, tab, 4 * RC + 16, &h->angcand_complete);
   h->n_angcand = (int)(tab.size() / n);
-  {
-    // the longest leading part of the table whose candidates are mutually orthogonal
-    // (to 1e-12 in cosine; a product quadrature makes the whole table so): only those
-    // enter the coefficient-space completion
-    const int nc = h->n_angcand;
-    std::vector<double> nrm(nc);
-    for (int i = 0; i < nc; ++i) {
-      double x = 0.0;
-      for (int q = 0; q < n; ++q) x += tab[(size_t)i * n + q] * tab[(size_t)i * n + q];
-      nrm[i] = std::sqrt(x);
-    }
-    int po = 0;
-    for (; po < nc; ++po) {
-      bool ok = nrm[po] > 0.0;
-      for (int i = 0; i < po && ok; ++i) {
-        double x = 0.0;
-        for (int q = 0; q < n; ++q) x += tab[(size_t)i * n + q] * tab[(size_t)po * n + q];
-        ok = std::fabs(x) <= 1e-12 * nrm[i] * nrm[po];
-      }
-      if (!ok) break;
-    }
-    h->n_angorth = po;
-  }
+  // the longest leading part of the table whose candidates are mutually orthogonal (to
+  // 1e-12 in cosine): only those enter the coefficient-space completion
+  h->n_angorth = dd::orthogonal_prefix(tab.data(), h->n_angcand, n, 1e-12);
 #define UP_DBL(dst, ptr, count)                                                                 \
   if (dalloc(&dst, count) != cudaSuccess ||                                                      \
       cudaMemcpy(dst, ptr, sizeof(double) * (count), cudaMemcpyHostToDevice) != cudaSuccess)     \

@@ -183,6 +183,28 @@ __host__ __device__ __forceinline__ int kc_bmax(int RC) { return RC + (4 * RC + 
 __host__ __device__ __forceinline__ size_t kc_region(int RC) {
   return (size_t)(kc_bmax(RC) + RC) * RC + (size_t)(RC + 1) * kc_bmax(RC);
 }
+// Length of the longest leading run of the nc candidates tab[i * n .. i * n + n) (host
+// memory) that are mutually orthogonal to rel_tol in cosine and non-zero: only those take
+// the coefficient-space completion (a product quadrature makes the whole angular table so).
+inline int orthogonal_prefix(const double* tab, int nc, int n, double rel_tol) {
+  double* nrm = new double[nc > 0 ? nc : 1];
+  int po = 0;
+  for (; po < nc; ++po) {
+    double x = 0.0;
+    for (int q = 0; q < n; ++q) x += tab[(size_t)po * n + q] * tab[(size_t)po * n + q];
+    nrm[po] = __builtin_sqrt(x);
+    bool ok = nrm[po] > 0.0;
+    for (int i = 0; i < po && ok; ++i) {
+      double y = 0.0;
+      for (int q = 0; q < n; ++q) y += tab[(size_t)i * n + q] * tab[(size_t)po * n + q];
+      ok = __builtin_fabs(y) <= rel_tol * nrm[i] * nrm[po];
+    }
+    if (!ok) break;
+  }
+  delete[] nrm;
+  return po;
+}
+
 // Candidate j of an nxk x nyk subdomain: frequencies (a, b); false past the family.
 __host__ __device__ __forceinline__ bool kc_cand(int j, int nxk, int nyk, int* ca, int* cb) {
   for (int d = 0; d <= nxk + nyk - 2; ++d) {
