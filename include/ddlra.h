@@ -221,20 +221,19 @@ dd_status dd_dlra_profile(dd_dlra_t h, int nsteps, double* ms, int* launches);
  * dd_dlra_scalar_flux_noalloc — the density of dd_dlra_scalar_flux written to the
  * device pointer out (same size and layout), by a call that allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine.  It is for callers that
- * must not allocate at the moment they read the density, for instance while they
- * capture their own work into a CUDA graph or under a policy that forbids device
- * allocation after start-up.  (No counterpart in the paper: this is a property of
- * the library, not of the method.)
+ * must not allocate device memory at the moment they read the density, for instance
+ * under a policy that allows device allocation only at start-up.  (No counterpart in
+ * the paper: this is a property of the library, not of the method.)
  *
  * The per-subdomain scratch (nsub * r_cap doubles) lives in one file-scope device
  * array of 16384 doubles (128 KiB) that every GPU loading the library keeps until
- * the process exits; larger solvers get DD_ERR_ARG.  The first call on a device
- * looks up the array's device address (once per device, with that device
- * current), so make the first call before any stream capture.  Call it with the
- * solver's device current (else DD_ERR_ARG).  All calls share the array and each
- * overwrites every element it later reads, so nothing needs clearing; calls that
- * overlap on the GPU (other streams, other solvers) race on it.  Asynchronous on
- * the solver's stream, like dd_dlra_scalar_flux with out_on_device != 0.
+ * the process exits; larger solvers get DD_ERR_ARG.  Each solver looks up the array's
+ * device address when it is created (with its device and context current), so the
+ * address is valid exactly as long as the solver's own memory.  Call it with the
+ * solver's device current (else DD_ERR_ARG, checked before anything else).  All calls
+ * share the array and each overwrites every element it later reads, so nothing needs
+ * clearing; calls that overlap on the GPU (other streams, other solvers) race on it.
+ * Asynchronous on the solver's stream, like dd_dlra_scalar_flux with out_on_device != 0.
  */
 dd_status dd_dlra_scalar_flux_noalloc(dd_dlra_t h, double* out);
 

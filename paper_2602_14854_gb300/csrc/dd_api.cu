@@ -96,6 +96,7 @@ struct dd_dlra {
   int* d_spnf;
   double *d_dm, *d_mvec;
   unsigned* d_status;
+  double* d_noalloc;   // device address of the allocation-free readout's scratch array
   dd::Problem P;
 };
 
@@ -215,8 +216,11 @@ namespace dd {
 
 dd_status set_error(dd_status s, const char* msg) { return fail(s, msg); }
 
-// Scalar flux with the per-subdomain scratch at a caller-supplied device address.
-dd_status noalloc_flux_impl(dd_dlra_t h, double* scratch, int scratch_doubles, double* out) {
+cudaError_t noalloc_scratch_address(double** addr);   // dd_noalloc.cu
+
+// Scalar flux with the per-subdomain scratch in the fixed device array whose address
+// the solver looked up at create time.
+dd_status noalloc_flux_impl(dd_dlra_t h, int scratch_doubles, double* out) {
   g_err.clear();
   int dev = -1;
   DD_CUDA(cudaGetDevice(&dev));
@@ -225,7 +229,8 @@ dd_status noalloc_flux_impl(dd_dlra_t h, double* scratch, int scratch_doubles, d
     return fail(DD_ERR_ARG, "nsub * r_cap = " + std::to_string((long)h->nsub * h->RC) +
                                 " exceeds the allocation-free scratch of " +
                                 std::to_string(scratch_doubles) + " doubles");
-  dd::scalar_flux(h->P, h->d_X[0], h->d_V[0], h->d_S[0], h->d_r[0], scratch, out, h->nx, h->stream);
+  dd::scalar_flux(h->P, h->d_X[0], h->d_V[0], h->d_S[0], h->d_r[0], h->d_noalloc, out, h->nx,
+                  h->stream);
   DD_CUDA(cudaGetLastError());
   return DD_OK;
 }
@@ -597,6 +602,10 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     return bail(DD_ERR_CUDA, "device allocation failed");
   if (dd::orth_init() != cudaSuccess || dd::phase_init() != cudaSuccess)
     return bail(DD_ERR_CUDA, "kernel attribute setup failed");
+  // the allocation-free readout's scratch array, looked up with this solver's device and
+  // context current (no allocation)
+  if (dd::noalloc_scratch_address(&h->d_noalloc) != cudaSuccess)
+    return bail(DD_ERR_CUDA, "scratch array lookup failed");
 
   // isotropic initial data at rank 1 (rank 0 where g0 vanishes on the subdomain)
   {

@@ -2,9 +2,9 @@
 regular one (dd_dlra_scalar_flux), through the C ABI.
 
 The allocation-free call serves callers that must not allocate device memory
-when they read the density, e.g. while capturing their own CUDA graph; it keeps
-its scratch in a fixed device array instead of solver workspace.  This file is
-collected last on purpose.
+when they read the density (e.g. under an allocate-at-start-up-only policy); it
+keeps its scratch in a fixed device array instead of solver workspace.  This file
+is collected last on purpose.
 """
 import numpy as np
 import pytest
