@@ -26,7 +26,7 @@ Optional, the second-order splitting Section 3 points to: Strang splitting of th
 the direction split instead of the eigen-split (R21 below).  Physical inflow data
 (R22 below).
 
-Readings where the paper is silent or ambiguous (each also listed in the design doc):
+Readings where the paper is silent or ambiguous:
   R1  general quadrature: scattering is sigma_s/|S| * sum_q w_q f_q, |S| = sum_q w_q.
   R2  inflow masks are the paper's inclusive ones: at the low side of an axis a
       direction is inflow when its velocity component is >= 0 (Section 3.1,
@@ -73,7 +73,11 @@ Readings where the paper is silent or ambiguous (each also listed in the design doc):
       can enter a subdomain whose stored rank is below the floor.
 
 Pins: tests/test_oracle_dd_dlra.py (full-rank identities, closed forms,
-invariances, brute force on tiny grids).
+invariances) and tests/test_oracle_pins.py (a dense brute-force restatement of
+Algorithm 6 on tiny grids, with and without physical inflow, fixed and tolerance
+ranks; an independently written one-domain classic DLRA that a 1x1 tiling must
+reproduce; the collision step at full rank; the tolerance rule of Algorithm 4 on a
+constructed spectrum; planted mistakes that each fail a named pin).
   R18 conserved-moment correction (off unless the workload asks for it): the
       K-steps move the scalar flux rho = sum_q w_q f_q conservatively, the S- and
       L-steps and the truncation do not.  Over a step, delta = sum over its three
