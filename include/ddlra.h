@@ -49,7 +49,9 @@ typedef enum dd_status {
   DD_ERR_RANK_CAP = 3,   /* a rank exceeds the capacity fixed at create time     */
   DD_ERR_NONFINITE = 4,  /* a non-finite value appeared in the factors          */
   DD_ERR_COMPLETION = 5, /* the fixed basis-completion family was exhausted      */
-  DD_ERR_STATE = 6       /* call not valid in the current state                 */
+  DD_ERR_STATE = 6,      /* call not valid in the current state                 */
+  DD_ERR_TIMEOUT = 7     /* a kernel's bounded wait (tile load, tensor-core      */
+                         /* product) ran out; the step's results are not valid  */
 } dd_status;
 
 typedef struct dd_grid {
@@ -89,15 +91,23 @@ typedef struct dd_fields {
 
 enum { DD_RANK_FIXED = 0, DD_RANK_TOL = 1 };
 enum { DD_EULER = 0, DD_RK4 = 1 };
-/* Arithmetic of the step.  DD_FP64: FP64 throughout, except that the small
- * eigen/singular value problems (m x m, m <= 64) run FP32 Jacobi sweeps finished in
- * double-float arithmetic (~1e-13 relative; the eigensolver of the orthonormalisation adds
- * one FP64 refinement).  DD_MIXED: in addition, FP32 arithmetic for the increments of the
- * collision-step ODEs and for the L-step's stage corrections (its first-stage right-hand
- * side is formed in FP64); each update itself is added in FP64.  The advection K-step is
- * FP64 in both (Appendix A's eigenbasis form), and so is the matrix stencil of the
- * flux-split form except in DD_MIXED. */
-enum { DD_FP64 = 0, DD_MIXED = 1 };
+/* Arithmetic of the step (the paper fixes none).  DD_FP64: FP64 throughout, except that
+ * the small eigen/singular value problems (m x m, m <= 64) run FP32 Jacobi sweeps finished
+ * in double-float arithmetic (~1e-13 relative; the eigensolver of the orthonormalisation
+ * adds one FP64 refinement).  DD_MIXED: in addition, FP32 arithmetic for the increments of
+ * the collision-step ODEs and for the L-step's stage corrections (its first-stage
+ * right-hand side is formed in FP64); each update itself is added in FP64.  DD_TF32 /
+ * DD_BF16: DD_MIXED plus the Galerkin contractions on the tensor cores (tcgen05) in TF32 /
+ * BF16 with FP32 accumulation, each FP64 operand split into a high and a low part of that
+ * type and multiplied hi*hi + hi*lo + lo*hi (FP32-level error per product): the angular
+ * coefficients <V, Omega V> and boundary masses, the spatial coefficients X^T K and
+ * X^T shift(X), the collision's X^T diag(sigma) X and X^T K, the projection V^T L, and the
+ * products K0 = X (S <V, V_hat>), the truncation's rotations and the collision's X S.
+ * The orthonormalisations, the small SVDs and eigendecompositions, the advection K-step
+ * (Appendix A's eigenbasis form) and the storage stay FP64.  With physical inflow the
+ * angular coefficients stay FP64.  The advection K-step is FP64 in every form except the
+ * matrix stencil of the flux-split form outside DD_FP64. */
+enum { DD_FP64 = 0, DD_MIXED = 1, DD_TF32 = 2, DD_BF16 = 3 };
 
 typedef struct dd_options {
   int rank_mode;      /* DD_RANK_FIXED: stored rank <= rank; DD_RANK_TOL: tolerance tol   */
@@ -109,7 +119,7 @@ typedef struct dd_options {
   double c_adv;       /* advection speed                                                  */
   double dt;          /* time step                                                        */
   double tau;         /* relative numerical-rank threshold (sigma_j <= tau*sigma_1 -> 0)  */
-  int precision;      /* DD_FP64 or DD_MIXED                                              */
+  int precision;      /* DD_FP64, DD_MIXED, DD_TF32 or DD_BF16                            */
   int mass_fix;       /* 1: conserved-moment correction at the end of every step (not part */
                       /* of the paper's scheme): the scalar-flux change of the S-, L-steps  */
                       /* and truncations of the step is added back as the isotropic        */

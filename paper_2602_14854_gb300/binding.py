@@ -16,10 +16,12 @@ LIB_PATH = os.path.join(PKG, "lib", "libddlra.so")
 
 DD_OK = 0
 STATUS_NAMES = {0: "DD_OK", 1: "DD_ERR_ARG", 2: "DD_ERR_CUDA", 3: "DD_ERR_RANK_CAP",
-                4: "DD_ERR_NONFINITE", 5: "DD_ERR_COMPLETION", 6: "DD_ERR_STATE"}
+                4: "DD_ERR_NONFINITE", 5: "DD_ERR_COMPLETION", 6: "DD_ERR_STATE",
+                7: "DD_ERR_TIMEOUT"}
 DD_RANK_FIXED, DD_RANK_TOL = 0, 1
 DD_EULER, DD_RK4 = 0, 1
-DD_FP64, DD_MIXED = 0, 1
+DD_FP64, DD_MIXED, DD_TF32, DD_BF16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": DD_FP64, "mixed": DD_MIXED, "tf32": DD_TF32, "bf16": DD_BF16}
 
 # every symbol include/ddlra.h declares
 EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scalar_flux",
@@ -160,7 +162,7 @@ class Solver:
             fixed = w.rank_mode == "fixed"
             opts[i] = Options(DD_RANK_FIXED if fixed else DD_RANK_TOL, w.rank, w.tol, w.r_min,
                               w.r_max, w.r_aug_max, DD_RK4 if w.integrator == "rk4" else DD_EULER,
-                              w.c_adv, w.dt, tau, DD_MIXED if precision == "mixed" else DD_FP64,
+                              w.c_adv, w.dt, tau, PRECISIONS[precision],
                               1 if w.mass_fix else 0, 1 if w.splitting == "strang" else 0,
                               1 if w.kstep_split == "flux" else 0)
             g0s[i] = _ptr(g0)

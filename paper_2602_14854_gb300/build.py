@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libddlra.so")
-SOURCES = ["dd_api.cu", "dd_orth.cu", "dd_phase.cu", "dd_noalloc.cu"]
+SOURCES = ["dd_api.cu", "dd_orth.cu", "dd_phase.cu", "dd_noalloc.cu", "dd_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

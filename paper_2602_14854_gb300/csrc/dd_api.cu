@@ -152,6 +152,9 @@ dd_status check_status(dd_dlra* h) {
   if (st & dd::ST_NONFINITE) return fail(DD_ERR_NONFINITE, "non-finite value in the factors");
   if (st & dd::ST_COMPLETION) return fail(DD_ERR_COMPLETION, "basis completion family exhausted");
   if (st & dd::ST_RANKCAP) return fail(DD_ERR_RANK_CAP, "rank capacity exceeded");
+  if (st & dd::ST_TIMEOUT)
+    return fail(DD_ERR_TIMEOUT, "a kernel's bounded wait for its tile loads or tensor-core "
+                                "products ran out");
   return DD_OK;
 }
 
@@ -263,7 +266,8 @@ static dd_status check_instance(const dd_grid* grid, const dd_tiling* tiling,
     return fail(DD_ERR_ARG, "rank_mode");
   if (opt->integrator != DD_EULER && opt->integrator != DD_RK4)
     return fail(DD_ERR_ARG, "integrator");
-  if (opt->precision != DD_FP64 && opt->precision != DD_MIXED)
+  if (opt->precision != DD_FP64 && opt->precision != DD_MIXED && opt->precision != DD_TF32 &&
+      opt->precision != DD_BF16)
     return fail(DD_ERR_ARG, "precision");
   if (opt->mass_fix != 0 && opt->mass_fix != 1) return fail(DD_ERR_ARG, "mass_fix");
   if (opt->splitting != DD_SPLIT_LIE && opt->splitting != DD_SPLIT_STRANG)
@@ -334,6 +338,8 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   // column capacity of every tall and small matrix: the intermediate rank and the
   // augmentation input width both fit
   h->RC = std::max(raug_max, h->MC);
+  // the tensor-core forms stage rows with TMA, which needs rows on 16-byte boundaries
+  if (opt->precision == DD_TF32 || opt->precision == DD_BF16) h->RC += h->RC & 1;
   h->r_floor = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_min;
   auto bail = [&](dd_status s, const std::string& m) {
     free_all(h);
@@ -578,7 +584,11 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   P.sig_s = h->d_sig_s; P.sig_t = h->d_sig_t; P.sQ = h->d_sQ;
   P.hx = h->hx; P.hy = h->hy; P.sh = h->sh; P.dt = opt->dt; P.c_adv = opt->c_adv; P.ssum = h->ssum;
   P.integrator = opt->integrator; P.rank_mode = opt->rank_mode; P.tol = opt->tol;
-  P.prec = opt->precision == DD_MIXED ? 1 : 0;
+  P.prec = opt->precision == DD_MIXED  ? dd::PREC_MIXED
+           : opt->precision == DD_TF32 ? dd::PREC_TF32
+           : opt->precision == DD_BF16 ? dd::PREC_BF16
+                                       : dd::PREC_FP64;
+  P.Ntot = Nt;
   P.mass_fix = opt->mass_fix;
   P.splitting = opt->splitting;
   P.kstep_split = opt->kstep_split;
@@ -602,6 +612,8 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     return bail(DD_ERR_CUDA, "device allocation failed");
   if (dd::orth_init() != cudaSuccess || dd::phase_init() != cudaSuccess)
     return bail(DD_ERR_CUDA, "kernel attribute setup failed");
+  if (P.prec >= dd::PREC_TF32 && dd::tc_init() != cudaSuccess)
+    return bail(DD_ERR_CUDA, "tensor-core setup failed (tensor-map encoder or kernel attributes)");
   // the allocation-free readout's scratch array, looked up with this solver's device and
   // context current (no allocation)
   if (dd::noalloc_scratch_address(&h->d_noalloc) != cudaSuccess)

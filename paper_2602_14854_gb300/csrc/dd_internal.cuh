@@ -21,7 +21,9 @@
 namespace dd {
 
 enum OrthMode { ORTH_QR = 0, ORTH_AUG = 1, ORTH_COMPLETE = 2 };
-enum StatusBits { ST_NONFINITE = 1, ST_COMPLETION = 2, ST_RANKCAP = 4 };
+enum StatusBits { ST_NONFINITE = 1, ST_COMPLETION = 2, ST_RANKCAP = 4, ST_TIMEOUT = 8 };
+// arithmetic of the step (dd_options.precision)
+enum Prec { PREC_FP64 = 0, PREC_MIXED = 1, PREC_TF32 = 2, PREC_BF16 = 3 };
 
 // Geometry of the tiling, device arrays (read-only inside kernels).
 struct Geo {

@@ -13,7 +13,7 @@ enum KernelSlot {
   KS_GHOST, KS_KSTEP_ADV, KS_SP_COEFFS, KS_SSTEP_ADV, KS_LSTEP_ADV, KS_GRAM, KS_TRUNC,
   KS_COLL_RANK, KS_COLL_A, KS_COLL_KSTEP, KS_COLL_SMALL, KS_COLL_LSTEP, KS_COLL_FINAL,
   KS_FLUX, KS_COPY, KS_GEIG, KS_CHOL, KS_COMPLETE, KS_MASS, KS_KC_W, KS_KC_SEL, KS_KC_APPLY,
-  NSLOT
+  KS_TC_TALL, KS_TC_GRAM, KS_TC_LSTEP, NSLOT
 };
 extern const char* const kSlotNames[NSLOT];
 
@@ -123,7 +123,8 @@ struct Problem {
   const double* sig_s; const double* sig_t; const double* sQ;  // per cell (spatial row order); sQ = sqrt(hx hy) Q
   double hx, hy, sh, dt, c_adv, ssum;
   int integrator;         // 0 Euler, 1 RK4
-  int prec;               // 0 FP64 arithmetic throughout, 1 mixed (FP32 where allowed)
+  int prec;               // Prec: FP64 throughout; FP32 increments (MIXED); in addition the
+                          // Galerkin contractions on tensor cores (TF32, BF16)
   int mass_fix;           // conserved-moment correction at the end of every step
   int splitting;          // 0 Lie (x, y, collision), 1 Strang (x/2, y/2, collision, y/2, x/2)
   int kstep_split;        // C+/C- of the advection K-step: 0 eigen-split, 1 direction split
@@ -141,7 +142,46 @@ struct Problem {
   const double* sptab; const long long* spoff; const int* spnf;
   int nchunk_sp, nchunk_ang;   // chunks of the two-stage reductions
   int nsm;                     // streaming multiprocessors of the device
+  long Ntot;                   // spatial rows of all subdomains
 };
+
+// ---- tensor-core contractions (dd_tc.cu), DD_TF32 / DD_BF16 --------------------------
+// Row weights of a Gram source: none, the advection axis' velocity Omega, its sign masks
+// (Omega < 0 / Omega >= 0, -0 counting as >= 0), Omega+ = max(Omega, 0), Omega- =
+// min(Omega, 0), or a per-row array (spatial rows).
+enum GramWeight { W_NONE = 0, W_OMEGA, W_NEG, W_NONNEG, W_OMEGA_POS, W_OMEGA_NEG, W_ROW };
+struct TcGramSrc {
+  const double* ptr; int ld;   // the tall array (ignored when same_as_b)
+  const int* cnt; int fix;     // columns per subdomain (cnt[k'] or fix)
+  int nbside;                  // -1: the subdomain's own rows; 0 / 1: the low / high
+                               // neighbour's along the axis (absent neighbour: no product)
+  int same_as_b;               // the rows of the common operand B (no separate load)
+  int shift;                   // the difference B - shift(B): each row of the common operand
+                               // minus the row one cell earlier along the axis (0 before a
+                               // line start); ptr must be B
+  int wsel; const double* wrow;
+  int blk;                     // partial block written
+  int transpose;               // write D^T
+};
+#define TC_MAXSRC 8
+struct TcGram {
+  Geo g;
+  int spatial, axis;
+  const double* B; int ldb; const int* bcnt; int bfix;   // the common operand
+  int nsrc; TcGramSrc src[TC_MAXSRC];  // sources 2j and 2j + 1 share a CTA; the sources
+                                       // of one slot (even / odd) not same_as_b share ptr, ld
+  double* part; int nchunk, nblk;
+  const double* ox; const double* oy;
+  unsigned* status;
+};
+cudaError_t tc_init();
+// Y = alpha A M (accumulate: Y += alpha A M); false when the operands do not suit TMA
+// (odd leading dimension), then nothing is launched
+bool tc_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
+             int lda, const int* ninner, int ninner_fix, const double* Bm, int bsmall,
+             const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy,
+             double alpha, int accumulate);
+bool tc_gram(const Problem& P, cudaStream_t st, const TcGram& a);
 
 void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st);
 void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st);

@@ -176,7 +176,10 @@ __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* 
   }
 }
 
-struct Dst { int idx[8]; };
+struct Dst {
+  int idx[8];
+  int ident = 0;   // bit b: block b holds E and the slot receives I - E
+};
 
 // Sum the chunk partials in fixed order into the small matrices.
 __global__ void k_reduce(const double* part, int nchunk, int nblk, Dst dst, double* sm, int RC) {
@@ -185,6 +188,7 @@ __global__ void k_reduce(const double* part, int nchunk, int nblk, Dst dst, doub
     const int b = o / (RC * RC), e = o % (RC * RC);
     double s = 0.0;
     for (int c = 0; c < nchunk; ++c) s += part[(((long)k * nchunk + c) * nblk + b) * RC * RC + e];
+    if ((dst.ident >> b) & 1) s = (e / RC == e % RC ? 1.0 : 0.0) - s;
     sm[((long)k * NSMALL + dst.idx[b]) * RC * RC + e] = s;
   }
 }
@@ -728,7 +732,9 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_eig(Problem P, PhaseBufs B
 // spatial coefficients of the S- and L-steps (partial sums over cell chunks)
 //   S1 = X1^T K1, T = X1^T shift_prev(X1), G_lo = X1_loface^T K^b_lo, G_hi = X1_hiface^T K^b_hi
 // ---------------------------------------------------------------------------
-__global__ void k_sp_coeffs(Problem P, PhaseBufs B, int axis) {
+// skip_t: every block but T (block 1), which the tensor-core Gram writes in its
+// difference form E = I - T.
+__global__ void k_sp_coeffs(Problem P, PhaseBufs B, int axis, int skip_t) {
   const int k = blockIdx.y, c = blockIdx.x, RC = P.g.RC, nchunk = P.nchunk_sp;
   const Lines L = lines_of(P.g, k, axis);
   // chunks of whole lines: every cell's shift partner and the two face cells of a
@@ -742,11 +748,13 @@ __global__ void k_sp_coeffs(Problem P, PhaseBufs B, int axis) {
   double* out = B.part + ((long)k * nchunk + c) * 4 * RC * RC;
   // work items (block, i, j) enumerated densely over i, j < rt, so that every lane of
   // an FP64 instruction is used; the partial is zeroed first
-  for (int o = threadIdx.x; o < 4 * RC * RC; o += blockDim.x) out[o] = 0.0;
+  for (int o = threadIdx.x; o < 4 * RC * RC; o += blockDim.x)
+    if (!(skip_t && o / (RC * RC) == 1)) out[o] = 0.0;
   __syncthreads();
   const int rt2 = rt * rt;
   for (int w = threadIdx.x; w < 4 * rt2; w += blockDim.x) {
     const int blk = w / rt2, e = w - blk * rt2, i = e / rt, j = e - i * rt;
+    if (skip_t && blk == 1) continue;
     double s = 0.0;
     {
       if (blk == 0) {
@@ -1457,7 +1465,7 @@ const char* const kSlotNames[NSLOT] = {
     "k_ghost", "k_kstep_adv", "k_sp_coeffs", "k_sstep_adv", "k_lstep_adv", "k_gram", "k_trunc",
     "k_coll_rank", "k_coll_a", "k_coll_kstep", "k_coll_small", "k_coll_lstep", "k_coll_final",
     "k_flux", "memcpy", "k_geig", "k_chol_inv", "k_complete", "k_mass_fix", "k_kc_w", "k_kc_sel",
-    "k_kc_apply"};
+    "k_kc_apply", "k_tc_tall", "k_tc_gram", "k_tc_lstep"};
 thread_local Prof* g_prof = nullptr;
 
 size_t part_elems(const Problem& P) {
@@ -1550,10 +1558,26 @@ static int gram_partials(const Problem& P, const PhaseBufs& B, cudaStream_t st, 
   return a.nchunk;
 }
 
+// The same product on the tensor cores in the DD_TF32 / DD_BF16 forms (the Galerkin
+// products: K0, the truncation's rotations, the collision's X S); FP64 otherwise, and for
+// the orthonormalisation's products, which call tall() directly.
 static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spatial,
                  const double* A, int lda, const int* ninner, int ninner_fix, const double* Bm,
                  int bsmall, const int* ncols, int ncols_fix, double* Y, int ldy,
-                 double* gpart = nullptr) {
+                 double* gpart = nullptr);
+static void galerkin_tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spatial,
+                          const double* A, int lda, const int* ninner, const double* Bm,
+                          int bsmall, const int* ncols, double* Y, int ldy) {
+  if (P.prec >= PREC_TF32 && tc_tall(P, B.status, st, spatial, A, lda, ninner, 0, Bm, bsmall,
+                                     B.sm, ncols, 0, Y, ldy, 1.0, 0))
+    return;
+  tall(P, B, st, spatial, A, lda, ninner, 0, Bm, bsmall, ncols, 0, Y, ldy);
+}
+
+static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spatial,
+                 const double* A, int lda, const int* ninner, int ninner_fix, const double* Bm,
+                 int bsmall, const int* ncols, int ncols_fix, double* Y, int ldy,
+                 double* gpart) {
   TallArgs a;
   a.spatial = spatial; a.A = A; a.lda = lda; a.ninner = ninner; a.ninner_fix = ninner_fix;
   a.Bm = Bm; a.bsmall = bsmall; a.ncols = ncols; a.ncols_fix = ncols_fix; a.Y = Y; a.ldy = ldy;
@@ -1562,6 +1586,28 @@ static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spat
   dim3 grid((rows + TALL_ROWS - 1) / TALL_ROWS, P.g.nsub);
   pbeg(st, KS_TALL);
   k_tall<<<grid, DD_THREADS, tall_smem(P.g.RC, ldy), st>>>(P.g, a, B.sm);
+  pend(st);
+}
+
+static TcGramSrc gsrc(const double* ptr, int ld, const int* cnt, int blk, int wsel = W_NONE,
+                      const double* wrow = nullptr, int transpose = 0) {
+  TcGramSrc s;
+  s.ptr = ptr; s.ld = ld; s.cnt = cnt; s.fix = 0; s.nbside = -1; s.same_as_b = 0; s.shift = 0;
+  s.wsel = wsel; s.wrow = wrow; s.blk = blk; s.transpose = transpose;
+  return s;
+}
+static TcGram tgram(const Problem& P, const PhaseBufs& B, int spatial, int axis, const double* Bop,
+                    const int* bcnt, int nchunk, int nblk) {
+  TcGram a;
+  a.g = P.g; a.spatial = spatial; a.axis = axis; a.B = Bop; a.ldb = P.g.RC; a.bcnt = bcnt;
+  a.bfix = 0; a.nsrc = 0; a.part = B.part; a.nchunk = nchunk; a.nblk = nblk;
+  a.ox = P.ox; a.oy = P.oy; a.status = B.status;
+  return a;
+}
+static void reduce_to(const Problem& P, const PhaseBufs& B, cudaStream_t st, int nchunk, int nblk,
+                      const Dst& d) {
+  pbeg(st, KS_REDUCE);
+  k_reduce<<<reduce_grid(P.g, nblk), DD_THREADS, 0, st>>>(B.part, nchunk, nblk, d, B.sm, P.g.RC);
   pend(st);
 }
 
@@ -1636,14 +1682,38 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   cudaMemcpyAsync(B.rx + axis * nsub, B.rt, sizeof(int) * nsub, cudaMemcpyDeviceToDevice, st);
   pend(st);
   // 2. angular Galerkin coefficients, boundary masses
-  pbeg(st, KS_ANG_COEFFS);
   // twice the angular chunks (more blocks than SMs), as far as the partial buffer holds
   const int nch_ac = std::min(2 * P.nchunk_ang, std::max(P.nchunk_sp, P.nchunk_ang));
   const int nblk_ac = P.kstep_split == 1 ? 8 : 6;
-  k_ang_coeffs<<<dim3(nch_ac, nsub), DD_THREADS, 0, st>>>(
-      g, axis == 0 ? P.ox : P.oy, B.Vh, B.V, B.r, B.rt, axis, nch_ac, nblk_ac, B.part,
-      P.infl_on, P.infl_hw);
-  pend(st);
+  bool tc_done = false;
+  if (P.prec >= PREC_TF32 && !P.infl_on) {
+    // the six (eight) blocks as weighted Grams against Vh; the sources that read Vh itself
+    // take the even slots, the own and neighbour V the odd ones
+    TcGram a = tgram(P, B, 0, axis, B.Vh, B.rt, nch_ac, nblk_ac);
+    TcGramSrc vh = gsrc(nullptr, RC, B.rt, 0, W_OMEGA);
+    vh.same_as_b = 1;
+    TcGramSrc v = gsrc(B.V, RC, B.r, 3);
+    a.src[0] = vh;                                   // C
+    a.src[1] = v;                                    // M
+    a.src[2] = vh; a.src[2].blk = 1; a.src[2].wsel = W_NEG;      // Mout_lo
+    a.src[3] = v; a.src[3].blk = 4; a.src[3].nbside = 0; a.src[3].wsel = W_NONNEG;  // Min_lo
+    a.src[4] = vh; a.src[4].blk = 2; a.src[4].wsel = W_NONNEG;   // Mout_hi
+    a.src[5] = v; a.src[5].blk = 5; a.src[5].nbside = 1; a.src[5].wsel = W_NEG;     // Min_hi
+    a.nsrc = 6;
+    if (nblk_ac == 8) {
+      a.src[6] = vh; a.src[6].blk = 6; a.src[6].wsel = W_OMEGA_POS;                  // C+
+      a.src[7] = vh; a.src[7].blk = 7; a.src[7].wsel = W_OMEGA_NEG;                  // C-
+      a.nsrc = 8;
+    }
+    tc_done = tc_gram(P, st, a);
+  }
+  if (!tc_done) {
+    pbeg(st, KS_ANG_COEFFS);
+    k_ang_coeffs<<<dim3(nch_ac, nsub), DD_THREADS, 0, st>>>(
+        g, axis == 0 ? P.ox : P.oy, B.Vh, B.V, B.r, B.rt, axis, nch_ac, nblk_ac, B.part,
+        P.infl_on, P.infl_hw);
+    pend(st);
+  }
   {
     Dst d;
     d.idx[0] = SM_C; d.idx[1] = SM_MOUT_LO; d.idx[2] = SM_MOUT_HI;
@@ -1658,7 +1728,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   k_small_adv1<<<nsub, DD_THREADS, small_adv1_smem(RC), st>>>(P, B, axis);
   pend(st);
   // 4. K^0 = X (S <V, Vh>)
-  tall(P, B, st, 1, B.X, RC, B.r, 0, nullptr, SM_B, B.rt, 0, B.K, RC);
+  galerkin_tall(P, B, st, 1, B.X, RC, B.r, nullptr, SM_B, B.rt, B.K, RC);
   // 5. boundary data
   pbeg(st, KS_GHOST);
   k_ghost<<<dim3((2 * P.maxlines + DD_THREADS / 32 - 1) / (DD_THREADS / 32), nsub), DD_THREADS, 0, st>>>(P, B, axis);
@@ -1684,7 +1754,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
     } else {
       const int lpb = kstep_lpb(P, len);
       dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
-      if (P.prec == 1)
+      if (P.prec >= PREC_MIXED)
         k_kstep_adv<float><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb, 0);
       else
         k_kstep_adv<double><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb, 0);
@@ -1699,12 +1769,28 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
     orthonormalize(P, B, st, a);
   }
   // 8. S-step coefficients and S-step
-  pbeg(st, KS_SP_COEFFS);
-  k_sp_coeffs<<<dim3(P.nchunk_sp, nsub), DD_THREADS, 0, st>>>(P, B, axis);
-  pend(st);
+  bool sp_tc = false;
+  {
+    // the spatial coefficient T = X1^T shift(X1) on the tensor cores in its difference form
+    // E = X1^T (X1 - shift(X1)) = I - T (a Gram against X1, written transposed; the
+    // reduction forms T = I - E); S1 = X1^T K (the R factor of the QR of K) and the face
+    // products G_lo, G_hi in FP64
+    bool& tcd = sp_tc;
+    if (P.prec >= PREC_TF32) {
+      TcGram a = tgram(P, B, 1, axis, B.X1, B.rt, P.nchunk_sp, 4);
+      a.src[0] = gsrc(B.X1, RC, B.rt, 1, W_NONE, nullptr, 1);
+      a.src[0].shift = 1;
+      a.nsrc = 1;
+      tcd = tc_gram(P, st, a);
+    }
+    pbeg(st, KS_SP_COEFFS);
+    k_sp_coeffs<<<dim3(P.nchunk_sp, nsub), DD_THREADS, 0, st>>>(P, B, axis, tcd ? 1 : 0);
+    pend(st);
+  }
   {
     Dst d;
     d.idx[0] = SM_S1; d.idx[1] = SM_T; d.idx[2] = SM_G_LO; d.idx[3] = SM_G_HI;
+    d.ident = sp_tc ? 2 : 0;
     pbeg(st, KS_REDUCE);
     k_reduce<<<reduce_grid(g, 4), DD_THREADS, 0, st>>>(B.part, P.nchunk_sp, 4, d, B.sm, RC);
     pend(st);
@@ -1720,7 +1806,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   pend(st);
   // 9. L-step
   pbeg(st, KS_LSTEP_ADV);
-  if (P.prec == 1) {
+  if (P.prec >= PREC_MIXED) {
     k_lstep_adv<float><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, lstep_smem(RC),
                   st>>>(P, B, axis);
   } else {
@@ -1740,8 +1826,8 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   k_trunc<<<nsub, DD_THREADS, trunc_smem(RC), st>>>(
       P, B);
   pend(st);
-  tall(P, B, st, 1, B.X1, RC, B.rt, 0, nullptr, SM_UB, B.ro, 0, B.Xo, RC);
-  tall(P, B, st, 0, B.V1, RC, B.rt, 0, nullptr, SM_VB, B.ro, 0, B.Vo, RC);
+  galerkin_tall(P, B, st, 1, B.X1, RC, B.rt, nullptr, SM_UB, B.ro, B.Xo, RC);
+  galerkin_tall(P, B, st, 0, B.V1, RC, B.rt, nullptr, SM_VB, B.ro, B.Vo, RC);
   if (P.mass_fix) mass_acc(P, B, st, B.Xo, B.Vo, B.So, B.ro, -1.0);
 }
 
@@ -1759,9 +1845,9 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   pbeg(st, KS_COLL_A);
   k_coll_a<<<nsub, DD_THREADS, 0, st>>>(P, B);
   pend(st);
-  tall(P, B, st, 1, B.X, RC, B.r, 0, B.S, -1, B.rc, 0, B.K, RC);
+  galerkin_tall(P, B, st, 1, B.X, RC, B.r, B.S, -1, B.rc, B.K, RC);
   pbeg(st, KS_COLL_KSTEP);
-  if (P.prec == 1) {
+  if (P.prec >= PREC_MIXED) {
     k_coll_kstep<float><<<dim3(64, nsub), DD_THREADS, 0, st>>>(P, B);
   } else {
     k_coll_kstep<double><<<dim3(64, nsub), DD_THREADS, 0, st>>>(P, B);
@@ -1773,9 +1859,31 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
     a.A = B.K; a.lda = RC; a.acols = B.rc; a.Q = B.Xo; a.ldq = RC; a.rout = B.rc;
     orthonormalize(P, B, st, a);
   }
+  // S1 = Xo^T K (the R factor of the QR of K) in FP64; the Galerkin contractions
+  // Ms = Xo^T diag(sigma_s) Xo, Mt = Xo^T diag(sigma_t) Xo on the tensor cores in the
+  // DD_TF32 / DD_BF16 forms
   gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.K, RC, B.rc, 0, 1, nullptr, SM_S1);
-  gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.Xo, RC, B.rc, 0, 1, P.sig_s, SM_MS);
-  gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.Xo, RC, B.rc, 0, 1, P.sig_t, SM_MT);
+  {
+    bool tcd = false;
+    if (P.prec >= PREC_TF32) {
+      TcGram a = tgram(P, B, 1, 0, B.Xo, B.rc, P.nchunk_sp, 2);
+      a.src[0] = gsrc(nullptr, RC, B.rc, 0, W_ROW, P.sig_s);
+      a.src[0].same_as_b = 1;
+      a.src[1] = a.src[0];
+      a.src[1].blk = 1;
+      a.src[1].wrow = P.sig_t;
+      a.nsrc = 2;
+      if ((tcd = tc_gram(P, st, a))) {
+        Dst d;
+        d.idx[0] = SM_MS; d.idx[1] = SM_MT;
+        reduce_to(P, B, st, P.nchunk_sp, 2, d);
+      }
+    }
+    if (!tcd) {
+      gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.Xo, RC, B.rc, 0, 1, P.sig_s, SM_MS);
+      gram(P, B, st, 1, B.Xo, RC, B.rc, 0, B.Xo, RC, B.rc, 0, 1, P.sig_t, SM_MT);
+    }
+  }
   // q = X1^T sQ  -> row 1 of the vector block (reduce into a scratch small, then copy)
   {
     GramArgs a;
@@ -1795,7 +1903,7 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   k_coll_small<<<nsub, DD_THREADS, sizeof(double) * (4 * RC * RC + 5 * RC), st>>>(P, B);
   pend(st);
   pbeg(st, KS_COLL_LSTEP);
-  if (P.prec == 1) {
+  if (P.prec >= PREC_MIXED) {
     k_coll_lstep<float><<<dim3((g.n + 31) / 32, nsub), DD_THREADS,
                    coll_lstep_smem(RC), st>>>(P, B);
   } else {
