@@ -226,6 +226,14 @@ dd_status dd_dlra_set_factors(dd_dlra_t h, int k, int r, const double* U, const 
 int dd_profile_slots(void);
 const char* dd_profile_slot_name(int slot);
 dd_status dd_dlra_profile(dd_dlra_t h, int nsteps, double* ms, int* launches);
+/* dd_dlra_profile, and (flops != NULL, dd_profile_slots() doubles) the algorithmic
+ * floating-point operations of every kernel slot over the nsteps steps, counted by the
+ * kernels themselves from the sizes they process (the method's operation count for the
+ * ranks actually used: 2 per multiply-add of the products, per stage of the fused
+ * integrators; the tensor-core slots count the products once, not their three partial
+ * products).  The latency-bound slots (small eigen/singular-value problems, completions,
+ * reductions) count nothing.  Allocates a small device buffer for the counters. */
+dd_status dd_dlra_profile_work(dd_dlra_t h, int nsteps, double* ms, int* launches, double* flops);
 
 /*
  * dd_dlra_scalar_flux_noalloc — the density of dd_dlra_scalar_flux written to the

@@ -27,7 +27,8 @@ PRECISIONS = {"fp64": DD_FP64, "mixed": DD_MIXED, "tf32": DD_TF32, "bf16": DD_BF
 EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scalar_flux",
            "dd_dlra_ranks", "dd_dlra_info", "dd_dlra_get_factors", "dd_dlra_set_factors",
            "dd_dlra_sync", "dd_dlra_destroy", "dd_last_error", "dd_profile_slots",
-           "dd_profile_slot_name", "dd_dlra_profile", "dd_dlra_scalar_flux_noalloc",
+           "dd_profile_slot_name", "dd_dlra_profile", "dd_dlra_profile_work",
+           "dd_dlra_scalar_flux_noalloc",
            "dd_dlra_create_batch", "dd_dlra_instance"]
 
 _dp = C.POINTER(C.c_double)
@@ -95,6 +96,7 @@ def load(path: str | None = None):
     lib.dd_profile_slot_name.argtypes = [C.c_int]
     lib.dd_profile_slot_name.restype = C.c_char_p
     lib.dd_dlra_profile.argtypes = [vp, C.c_int, _dp, _ip]
+    lib.dd_dlra_profile_work.argtypes = [vp, C.c_int, _dp, _ip, _dp]
     lib.dd_dlra_scalar_flux_noalloc.argtypes = [vp, vp]
     lib.dd_dlra_create_batch.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Tiling),
                                          C.POINTER(Quadrature), C.POINTER(Fields),
@@ -255,18 +257,26 @@ class Solver:
         r = S.shape[0]
         _check(self.lib, self.lib.dd_dlra_set_factors(self.h, k, r, _ptr(U), _ptr(S), _ptr(V)))
 
-    def profile(self, nsteps: int):
+    def profile(self, nsteps: int, work: bool = False):
         """Advance nsteps steps with a CUDA event pair around every kernel launch;
-        returns {kernel: (total_ms, launches)}."""
+        returns {kernel: (total_ms, launches)}, or with work=True {kernel: (total_ms,
+        launches, algorithmic_flops)}."""
         ns = self.lib.dd_profile_slots()
         ms = np.zeros(ns)
         cnt = np.zeros(ns, dtype=np.int32)
-        _check(self.lib, self.lib.dd_dlra_profile(self.h, int(nsteps), _ptr(ms),
-                                                   cnt.ctypes.data_as(_ip)))
+        fl = np.zeros(ns)
+        if work:
+            _check(self.lib, self.lib.dd_dlra_profile_work(self.h, int(nsteps), _ptr(ms),
+                                                            cnt.ctypes.data_as(_ip), _ptr(fl)))
+        else:
+            _check(self.lib, self.lib.dd_dlra_profile(self.h, int(nsteps), _ptr(ms),
+                                                       cnt.ctypes.data_as(_ip)))
         out = {}
         for i in range(ns):
             if cnt[i]:
-                out[self.lib.dd_profile_slot_name(i).decode()] = (float(ms[i]), int(cnt[i]))
+                name = self.lib.dd_profile_slot_name(i).decode()
+                out[name] = (float(ms[i]), int(cnt[i]), float(fl[i])) if work else \
+                    (float(ms[i]), int(cnt[i]))
         return out
 
     def close(self):

@@ -815,9 +815,20 @@ const char* dd_profile_slot_name(int slot) {
 }
 
 dd_status dd_dlra_profile(dd_dlra_t h, int nsteps, double* ms, int* launches) {
+  return dd_dlra_profile_work(h, nsteps, ms, launches, nullptr);
+}
+
+dd_status dd_dlra_profile_work(dd_dlra_t h, int nsteps, double* ms, int* launches, double* flops) {
   g_err.clear();
   if (!h || nsteps < 0 || !ms || !launches) return fail(DD_ERR_ARG, "bad argument");
   for (int i = 0; i < dd::NSLOT; ++i) { ms[i] = 0.0; launches[i] = 0; }
+  unsigned long long* d_work = nullptr;
+  if (flops) {
+    // the kernels add their algorithmic flops to these counters while this call runs
+    DD_CUDA(cudaMalloc(&d_work, sizeof(unsigned long long) * dd::NSLOT));
+    DD_CUDA(cudaMemsetAsync(d_work, 0, sizeof(unsigned long long) * dd::NSLOT, h->stream));
+    h->P.g.work = d_work;
+  }
   dd::Prof* prof = new dd::Prof();
   prof->n = 0;
   for (int i = 0; i < dd::Prof::MAXL; ++i) {
@@ -845,6 +856,14 @@ dd_status dd_dlra_profile(dd_dlra_t h, int nsteps, double* ms, int* launches) {
     cudaEventDestroy(prof->e[i]);
   }
   delete prof;
+  if (d_work) {
+    h->P.g.work = nullptr;
+    unsigned long long w[dd::NSLOT];
+    cudaError_t e = cudaMemcpy(w, d_work, sizeof(w), cudaMemcpyDeviceToHost);
+    cudaFree(d_work);
+    if (e != cudaSuccess && st == DD_OK) st = fail(DD_ERR_CUDA, cudaGetErrorString(e));
+    for (int i = 0; i < dd::NSLOT; ++i) flops[i] = e == cudaSuccess ? (double)w[i] : 0.0;
+  }
   if (st != DD_OK) return st;
   return check_status(h);
 }

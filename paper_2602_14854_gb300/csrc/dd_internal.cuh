@@ -46,7 +46,16 @@ struct Geo {
   const int* raug;    // cap of the intermediate rank
   const int* fbase;   // first cell of the problem in the concatenated density output
   const int* fnx;     // width of the problem's grid
+  // algorithmic flops per kernel slot, counted by the kernels while dd_dlra_profile_work
+  // runs (null otherwise: nothing is counted)
+  unsigned long long* work;
 };
+
+// Adds one CTA's algorithmic flops to the slot's counter (profiling only).
+__device__ __forceinline__ void count_work(const Geo& g, int slot, double flops) {
+  if (g.work && threadIdx.x == 0 && flops > 0.0)
+    atomicAdd(&g.work[slot], (unsigned long long)flops);
+}
 
 // Line geometry along an axis (0 = x, 1 = y) for subdomain k.
 struct Lines {

@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* 
   const int nsym = rtk * (rtk + 1) / 2;
   const int n3 = rk * rtk, n4 = rlo * rtk, n5 = rhi * rtk;
   const int nwork = nsym + n3 + n4 + n5;
+  count_work(g, KS_ANG_COEFFS, (double)(q1 - q0) * (nsym * (nblk == 8 ? 8.0 : 5.0) + 2.0 * (n3 + n4 + n5)));
   for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
     if (w < nsym) {
       int j = (int)((sqrtf(8.f * w + 1.f) - 1.f) * 0.5f);
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_gram(Geo g, GramArgs a) {
   for (int e = tid; e < RC * RC; e += DD_THREADS) gt[e] = 0.0;
   __syncthreads();
   const int npair = zero ? 0 : (a.sym ? na * (na + 1) / 2 : na * nbc);
+  count_work(g, KS_GRAM, 2.0 * (i1 - i0) * npair * (a.wrow ? 1.5 : 1.0));
   for (int p = tid; p < npair; p += DD_THREADS) {
     int i, j;
     if (a.sym) {                                   // p -> (i <= j)
@@ -425,6 +427,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_tall(Geo g, TallArgs a, double* 
   const double* Bk = (a.bsmall >= 0) ? smbase + ((long)k * NSMALL + a.bsmall) * RC * RC
                                      : a.Bm + (long)k * RC * RC;
   const int SA = ni | 1, SY = a.ldy | 1;
+  count_work(g, KS_TALL, 2.0 * nrow * ni * nc + (gp ? (double)nrow * nc * (nc + 1) : 0.0));
   double* Ms = sh;                                  // RC x RC (+4 so a tile never reads past it)
   double* As = Ms + RC * RC + 4;                    // TALL_ROWS x SA
   double* Ys = As + TALL_ROWS * (RC | 1);           // TALL_ROWS x SY
@@ -532,6 +535,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
   const int rt = B.rt[k];
   const int len = L.len;
   if (big_only && (long)len * rt <= (long)DD_THREADS * KE_EPT) return;
+  count_work(P.g, KS_KSTEP_ADV, (double)nl * len * rt * (6.0 * rt + 4.0) * (P.integrator == 1 ? 4 : 1));
   TC* Cp = sh;
   TC* Cn = Cp + RC * RC;
   TC* Ca = Cn + RC * RC;
@@ -629,6 +633,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_eig(Problem P, PhaseBufs B
   // a tile larger than the register tile (only with lpb = 1: a line longer than
   // 256 KE_EPT / r_t) is left to k_kstep_adv, launched after this kernel for exactly these
   if ((long)nl * len * rt > (long)DD_THREADS * KE_EPT) return;
+  count_work(P.g, KS_KSTEP_ADV, (double)nl * len * rt * (4.0 * rt + 8.0 * (P.integrator == 1 ? 4 : 1)));
   TC* Pm = sh;                     // Pm[u * RC + j]: component u of eigenvector j
   TC* lp = Pm + RC * RC;           // max(lambda, 0)
   TC* ln = lp + RC;                // min(lambda, 0)
@@ -742,6 +747,8 @@ __global__ void k_sp_coeffs(Problem P, PhaseBufs B, int axis, int skip_t) {
   const int lch = (L.nlines + nchunk - 1) / nchunk;
   const int l0 = c * lch, l1 = min(L.nlines, l0 + lch);
   const int rt = B.rt[k];
+  count_work(P.g, KS_SP_COEFFS, 2.0 * rt * rt * (max(0, l1 - l0) * (double)L.len * (skip_t ? 1 : 2) +
+                                                 2.0 * max(0, l1 - l0)));
   const double* X1 = B.X1 + (long)P.g.rowoff[k] * RC;
   const double* K = B.K + (long)P.g.rowoff[k] * RC;
   const double* Kb = B.Kb + (long)k * 2 * P.maxlines * RC;
@@ -905,6 +912,8 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_adv(Problem P, PhaseBufs B
   const TC dt = (TC)P.g.dtk[k];
   const TC hinv = (TC)(1.0 / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]));
   const int nst = P.integrator == 1 ? 4 : 1;
+  count_work(P.g, KS_LSTEP_ADV, (double)max(0, min(n, (int)(blockIdx.x + 1) * 32) - (int)blockIdx.x * 32) *
+                                    rt * rt * (4.0 + 2.0 * nst));
   for (int q = blockIdx.x * 32 + warp; q < min(n, (int)(blockIdx.x + 1) * 32); q += nw) {
     const double* Vq = B.Vh + ((long)k * n + q) * RC;
     for (int t = lane; t < RC; t += 32) {
@@ -1173,6 +1182,10 @@ __global__ void k_coll_kstep(Problem P, PhaseBufs B) {
   const double* a = SMB(B, P, k, SM_VEC);
   const TC dt = (TC)P.g.dtk[k];
   const int nst = P.integrator == 1 ? 4 : 1;
+  {
+    const int cells = (N > (int)blockIdx.x * nw) ? ((N - (int)blockIdx.x * nw - 1) / ((int)gridDim.x * nw) + 1) * nw : 0;
+    count_work(P.g, KS_COLL_KSTEP, (double)min(cells, N) * rc * 6.0 * nst);
+  }
   for (int cell = blockIdx.x * nw + warp; cell < N; cell += gridDim.x * nw) {
     const long row = (long)P.g.rowoff[k] + cell;
     const TC ss = (TC)(P.sig_s[row] / P.ssum), st = (TC)P.sig_t[row], sq = (TC)P.sQ[row];
@@ -1313,6 +1326,8 @@ __global__ void __launch_bounds__(DD_THREADS) k_coll_lstep(Problem P, PhaseBufs 
   double* vw = vhd + warp * RC;
   const int nst = P.integrator == 1 ? 4 : 1;
   const TC dt = (TC)P.g.dtk[k];
+  count_work(P.g, KS_COLL_LSTEP, (double)max(0, min(n, (int)(blockIdx.x + 1) * 32) - (int)blockIdx.x * 32) *
+                                     rc * rc * (2.0 + 2.0 * nst));
   for (int q = blockIdx.x * 32 + warp; q < min(n, (int)(blockIdx.x + 1) * 32); q += nw) {
     const double* Vq = B.Vh + ((long)k * n + q) * RC;
     for (int t = lane; t < RC; t += 32) {

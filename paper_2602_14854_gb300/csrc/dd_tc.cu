@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_tc_tall(const __grid_constant
     const int Kp = ni <= kq ? kq : (ni + kq - 1) / kq * kq;
     const int KB = Kp * es;
     const int N = nc <= 16 ? 16 : (nc + 15) / 16 * 16;
+    count_work(a.g, KS_TC_TALL, 2.0 * min(TT_ROWS, rows - r0) * ni * nc);
     if (k != kB) {                                     // M^T as the B operand (N x Kp)
       const double* Mk = a.bsmall >= 0 ? a.smbase + ((long)k * NSMALL + a.bsmall) * RC * RC
                                        : a.Bm + (long)k * RC * RC;
@@ -315,6 +316,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_tc_gram(const __grid_constant
       }
     return;
   }
+  count_work(a.g, KS_TC_GRAM, 2.0 * (i1 - i0) * nb * (ma[0] + ma[1]));
   if (tid == 0) {
     tc::mbar_init(&bar_tma[0], 1);
     tc::mbar_init(&bar_tma[1], 1);
