@@ -133,10 +133,17 @@ typedef struct dd_options {
                       /* C+- = <V, max/min(Omega, 0) V> (the L-step's per-direction upwind   */
                       /* flux projected on the angular basis; equal to Appendix A's at full  */
                       /* rank; not the paper's scheme at low rank; no eigendecomposition)    */
+  int products;       /* the FP64 tall x small products (orthonormalisations, truncation,     */
+                      /* K0 = X S <V, V_hat>): DD_PRODUCTS_FP64: FP64 CUDA-core arithmetic;    */
+                      /* DD_PRODUCTS_TENSOR: on the BF16 tensor cores with the error-free      */
+                      /* splitting of Ozaki et al. (seven 8-bit digits per value, exact FP32   */
+                      /* accumulation, FP64-level error).  Results agree to FP64 rounding, not */
+                      /* bits.                                                                  */
 } dd_options;
 
 enum { DD_SPLIT_LIE = 0, DD_SPLIT_STRANG = 1 };
 enum { DD_KSPLIT_EIGEN = 0, DD_KSPLIT_FLUX = 1 };
+enum { DD_PRODUCTS_FP64 = 0, DD_PRODUCTS_TENSOR = 1 };
 
 typedef struct dd_dlra* dd_dlra_t;
 

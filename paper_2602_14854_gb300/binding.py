@@ -22,6 +22,7 @@ DD_RANK_FIXED, DD_RANK_TOL = 0, 1
 DD_EULER, DD_RK4 = 0, 1
 DD_FP64, DD_MIXED, DD_TF32, DD_BF16 = 0, 1, 2, 3
 PRECISIONS = {"fp64": DD_FP64, "mixed": DD_MIXED, "tf32": DD_TF32, "bf16": DD_BF16}
+PRODUCTS = {"fp64": 0, "tensor": 1}
 
 # every symbol include/ddlra.h declares
 EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scalar_flux",
@@ -62,7 +63,7 @@ class Options(C.Structure):
                 ("r_min", C.c_int), ("r_max", C.c_int), ("r_aug_max", C.c_int),
                 ("integrator", C.c_int), ("c_adv", C.c_double), ("dt", C.c_double),
                 ("tau", C.c_double), ("precision", C.c_int), ("mass_fix", C.c_int),
-                ("splitting", C.c_int), ("kstep_split", C.c_int)]
+                ("splitting", C.c_int), ("kstep_split", C.c_int), ("products", C.c_int)]
 
 
 _lib = None
@@ -132,7 +133,7 @@ class Solver:
     """DD-DLRA solver on one problem; wraps a dd_dlra_t handle."""
 
     def __init__(self, wl, tau: float = 1e-5, stream: int = 0, use_graph: bool = False,
-                 precision: str = "fp64"):
+                 precision: str = "fp64", products: str = "fp64"):
         """wl: one workload, or a list of workloads sharing the direction table (a batch)."""
         lib = load()
         self.lib = lib
@@ -166,7 +167,7 @@ class Solver:
                               w.r_max, w.r_aug_max, DD_RK4 if w.integrator == "rk4" else DD_EULER,
                               w.c_adv, w.dt, tau, PRECISIONS[precision],
                               1 if w.mass_fix else 0, 1 if w.splitting == "strang" else 0,
-                              1 if w.kstep_split == "flux" else 0)
+                              1 if w.kstep_split == "flux" else 0, PRODUCTS[products])
             g0s[i] = _ptr(g0)
         w0 = wls[0]
         ox, oy, w = _d(w0.omega_x), _d(w0.omega_y), _d(w0.w)

@@ -274,6 +274,8 @@ static dd_status check_instance(const dd_grid* grid, const dd_tiling* tiling,
     return fail(DD_ERR_ARG, "splitting");
   if (opt->kstep_split != DD_KSPLIT_EIGEN && opt->kstep_split != DD_KSPLIT_FLUX)
     return fail(DD_ERR_ARG, "kstep_split");
+  if (opt->products != DD_PRODUCTS_TENSOR && opt->products != DD_PRODUCTS_FP64)
+    return fail(DD_ERR_ARG, "products");
   if (!(opt->dt > 0.0) || !(opt->tau >= 0.0)) return fail(DD_ERR_ARG, "dt / tau");
   const int RS = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_max;
   const int fl = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_min;
@@ -306,9 +308,9 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     const dd_options& b = opts[i];
     if (b.rank_mode != a.rank_mode || b.integrator != a.integrator || b.precision != a.precision ||
         b.c_adv != a.c_adv || b.tau != a.tau || b.tol != a.tol || b.mass_fix != a.mass_fix ||
-        b.splitting != a.splitting || b.kstep_split != a.kstep_split)
+        b.splitting != a.splitting || b.kstep_split != a.kstep_split || b.products != a.products)
       return fail(DD_ERR_ARG, "instances of a batch must share rank mode, tolerance, integrator, "
-                              "precision, mass_fix, splitting, kstep_split, c_adv and tau");
+                              "precision, mass_fix, splitting, kstep_split, products, c_adv and tau");
   }
   const dd_options* opt = &opts[0];
 
@@ -339,7 +341,8 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   // augmentation input width both fit
   h->RC = std::max(raug_max, h->MC);
   // the tensor-core forms stage rows with TMA, which needs rows on 16-byte boundaries
-  if (opt->precision == DD_TF32 || opt->precision == DD_BF16) h->RC += h->RC & 1;
+  if (opt->precision == DD_TF32 || opt->precision == DD_BF16 || opt->products == DD_PRODUCTS_TENSOR)
+    h->RC += h->RC & 1;
   h->r_floor = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_min;
   auto bail = [&](dd_status s, const std::string& m) {
     free_all(h);
@@ -589,6 +592,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
            : opt->precision == DD_BF16 ? dd::PREC_BF16
                                        : dd::PREC_FP64;
   P.Ntot = Nt;
+  P.oz = opt->products == DD_PRODUCTS_TENSOR ? 1 : 0;
   P.mass_fix = opt->mass_fix;
   P.splitting = opt->splitting;
   P.kstep_split = opt->kstep_split;
@@ -612,7 +616,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     return bail(DD_ERR_CUDA, "device allocation failed");
   if (dd::orth_init() != cudaSuccess || dd::phase_init() != cudaSuccess)
     return bail(DD_ERR_CUDA, "kernel attribute setup failed");
-  if (P.prec >= dd::PREC_TF32 && dd::tc_init() != cudaSuccess)
+  if ((P.prec >= dd::PREC_TF32 || P.oz) && dd::tc_init() != cudaSuccess)
     return bail(DD_ERR_CUDA, "tensor-core setup failed (tensor-map encoder or kernel attributes)");
   // the allocation-free readout's scratch array, looked up with this solver's device and
   // context current (no allocation)

@@ -13,7 +13,7 @@ enum KernelSlot {
   KS_GHOST, KS_KSTEP_ADV, KS_SP_COEFFS, KS_SSTEP_ADV, KS_LSTEP_ADV, KS_GRAM, KS_TRUNC,
   KS_COLL_RANK, KS_COLL_A, KS_COLL_KSTEP, KS_COLL_SMALL, KS_COLL_LSTEP, KS_COLL_FINAL,
   KS_FLUX, KS_COPY, KS_GEIG, KS_CHOL, KS_COMPLETE, KS_MASS, KS_KC_W, KS_KC_SEL, KS_KC_APPLY,
-  KS_TC_TALL, KS_TC_GRAM, KS_TC_LSTEP, NSLOT
+  KS_TC_TALL, KS_TC_GRAM, KS_TC_LSTEP, KS_OZ_TALL, NSLOT
 };
 extern const char* const kSlotNames[NSLOT];
 
@@ -128,6 +128,7 @@ struct Problem {
   int mass_fix;           // conserved-moment correction at the end of every step
   int splitting;          // 0 Lie (x, y, collision), 1 Strang (x/2, y/2, collision, y/2, x/2)
   int kstep_split;        // C+/C- of the advection K-step: 0 eigen-split, 1 direction split
+  int oz;                 // FP64 tall products on the tensor cores (Ozaki splitting)
   // physical inflow (null without): per subdomain and side (x-lo, x-hi, y-lo, y-hi) an
   // on flag, face values sqrt(hx hy) g per line (maxlines), the angular column
   // sqrt(w) m_in h (n) and its augmentation scale |g|_x
@@ -182,6 +183,11 @@ bool tc_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, c
              const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy,
              double alpha, int accumulate);
 bool tc_gram(const Problem& P, cudaStream_t st, const TcGram& a);
+// Y = A M to FP64 accuracy on the BF16 tensor cores (Ozaki splitting); false when the
+// operands do not suit TMA, then nothing is launched
+bool oz_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
+             int lda, const int* ninner, int ninner_fix, const double* Bm, int bsmall,
+             const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy);
 
 void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st);
 void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st);

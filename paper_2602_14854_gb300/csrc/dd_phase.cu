@@ -1480,7 +1480,7 @@ const char* const kSlotNames[NSLOT] = {
     "k_ghost", "k_kstep_adv", "k_sp_coeffs", "k_sstep_adv", "k_lstep_adv", "k_gram", "k_trunc",
     "k_coll_rank", "k_coll_a", "k_coll_kstep", "k_coll_small", "k_coll_lstep", "k_coll_final",
     "k_flux", "memcpy", "k_geig", "k_chol_inv", "k_complete", "k_mass_fix", "k_kc_w", "k_kc_sel",
-    "k_kc_apply", "k_tc_tall", "k_tc_gram", "k_tc_lstep"};
+    "k_kc_apply", "k_tc_tall", "k_tc_gram", "k_tc_lstep", "k_oz_tall"};
 thread_local Prof* g_prof = nullptr;
 
 size_t part_elems(const Problem& P) {
@@ -1593,6 +1593,9 @@ static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spat
                  const double* A, int lda, const int* ninner, int ninner_fix, const double* Bm,
                  int bsmall, const int* ncols, int ncols_fix, double* Y, int ldy,
                  double* gpart) {
+  if (P.oz && !gpart && oz_tall(P, B.status, st, spatial, A, lda, ninner, ninner_fix, Bm, bsmall,
+                                B.sm, ncols, ncols_fix, Y, ldy))
+    return;
   TallArgs a;
   a.spatial = spatial; a.A = A; a.lda = lda; a.ninner = ninner; a.ninner_fix = ninner_fix;
   a.Bm = Bm; a.bsmall = bsmall; a.ncols = ncols; a.ncols_fix = ncols_fix; a.Y = Y; a.ldy = ldy;
@@ -1660,7 +1663,7 @@ static void orthonormalize(const Problem& P, const PhaseBufs& B, cudaStream_t st
   // U1 = A M; its Gram from the same tiles when their partials fit the buffer (one partial
   // per 32-row tile, counted from each subdomain's first row), else by k_gram
   const int ntile = ((sp ? P.maxN : P.g.n) + TALL_ROWS - 1) / TALL_ROWS;
-  const bool fuse = ntile <= 8 * std::max(P.nchunk_sp, P.nchunk_ang);
+  const bool fuse = !P.oz && ntile <= 8 * std::max(P.nchunk_sp, P.nchunk_ang);
   tall(P, B, st, sp, a.A, a.lda, a.acols, 0, nullptr, SM_QM, B.keep, 0, W, P.WC,
        fuse ? B.part : nullptr);
   nch = fuse ? ntile : gram_partials(P, B, st, sp, W, P.WC, B.keep, nullptr);

@@ -473,6 +473,257 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_tc_gram(const __grid_constant
 }
 
 // ---------------------------------------------------------------------------------------
+// FP64-accurate tall x small products on the BF16 tensor cores (Ozaki scheme)
+// ---------------------------------------------------------------------------------------
+// Y = A M with the error-free splitting of Ozaki, Ogita, Oishi and Rump (2012, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix multiplication
+// and its applications"): per 128-row tile the columns of A are equalised by powers of two
+// 2^-c_k (folded into the rows of M), each row of A and each column of M get a power-of-two
+// scale, and every value becomes a fixed-point integer with 56 fraction bits, split into 7
+// balanced base-256 digits (|digit| <= 256: exact in BF16).  Digit products of orders s, t
+// go to the TMEM accumulator of g = s + t (pairs with g <= 6; 28 of 49): every partial sum is
+// an integer below 2^23, so the FP32 accumulation is exact.  The epilogue combines the seven
+// sums in 64-bit integers and builds the FP64 result from bits.  Error: a few units of 2^-56
+// of max|A row| max|M column| per entry (FP64 rounding of the products is 2^-53 each).  No
+// FP64 instruction runs anywhere in the kernel.
+#define OZ_DIG 7
+#define OZ_ASL (TT_ROWS * 32 * 2)            // 8 KiB: one digit plane of 128 rows x 32 k
+#define OZ_MSL (DD_MAXC * DD_MAXC * 2)       // 8 KiB: one digit plane of M^T (64 x 64)
+size_t oz_tall_smem() { return 1024 + TT_STAGE + OZ_DIG * OZ_ASL + OZ_DIG * OZ_MSL; }
+
+// biased FP64 exponent of x (0 for zero and subnormals)
+__device__ __forceinline__ int f64_bexp(double x) {
+  return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
+}
+// x * 2^(56 - e) rounded to an integer (|x| < 2^e), by integer operations
+__device__ __forceinline__ long long oz_fixed(double x, int e) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((u >> 52) & 0x7ff);
+  if (E == 0) return 0;
+  const long long m = (long long)((u & 0xfffffffffffffull) | 0x10000000000000ull);
+  const int sh = E - 1019 - e;
+  long long T = 0;
+  if (sh >= 0) T = m << sh;
+  else if (sh > -62) T = (m + (1ll << (-sh - 1))) >> (-sh);
+  return (u >> 63) ? -T : T;
+}
+// the 7 balanced base-256 digits of T (T = sum_s d_s 2^(48 - 8 s), |T| < 2^56) as BF16 bit
+// patterns: the bytes of |T| by 32-bit operations, balanced from the lowest up (a byte
+// >= 128 becomes byte - 256 with a carry into the next), then the sign
+__device__ __forceinline__ void oz_digits(long long T, uint16_t* d) {
+  const bool neg = T < 0;
+  const unsigned long long U = neg ? (unsigned long long)(-T) : (unsigned long long)T;
+  const unsigned tl = (unsigned)U, th = (unsigned)(U >> 32);
+  int b[OZ_DIG] = {(int)(th >> 16), (int)((th >> 8) & 255u), (int)(th & 255u), (int)(tl >> 24),
+                   (int)((tl >> 16) & 255u), (int)((tl >> 8) & 255u), (int)(tl & 255u)};
+#pragma unroll
+  for (int s = OZ_DIG - 1; s > 0; --s) {
+    const int c = b[s] >= 128;
+    b[s] -= c << 8;
+    b[s - 1] += c;
+  }
+#pragma unroll
+  for (int s = 0; s < OZ_DIG; ++s)
+    d[s] = __bfloat16_as_ushort(__float2bfloat16_rn((float)(neg ? -b[s] : b[s])));
+}
+// J * 2^sc as an FP64 (round to nearest even), by integer operations
+__device__ __forceinline__ double oz_to_f64(long long J, int sc) {
+  if (J == 0) return 0.0;
+  const unsigned long long sg = J < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long u = J < 0 ? (unsigned long long)(-J) : (unsigned long long)J;
+  int msb = 63 - __clzll((long long)u);
+  unsigned long long r;
+  if (msb > 52) {
+    const int sh = msb - 52;
+    r = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (r & 1ull))) ++r;
+    if (r >> 53) { r >>= 1; ++msb; }
+  } else {
+    r = u << (52 - msb);
+  }
+  const int be = 1023 + msb + sc;
+  if (be <= 0) return __longlong_as_double((long long)sg);
+  if (be >= 2047) return __longlong_as_double((long long)(sg | 0x7ff0000000000000ull));
+  return __longlong_as_double((long long)(sg | ((unsigned long long)be << 52) | (r & 0xfffffffffffffull)));
+}
+
+__global__ void __launch_bounds__(TT_THREADS, 1) k_oz_tall(const __grid_constant__ CUtensorMap mapA,
+                                                           TcTall a) {
+  extern __shared__ uint8_t raw_oz[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw_oz) + 1023) &
+                                             ~uintptr_t(1023));
+  const double* st = reinterpret_cast<const double*>(base);
+  uint8_t* asl = base + TT_STAGE;                      // OZ_DIG planes of 128 x 32 (K-major)
+  uint8_t* msl = asl + OZ_DIG * OZ_ASL;                // OZ_DIG planes of 64 x 64
+  __shared__ uint64_t bar_tma, bar_mma;
+  __shared__ uint32_t tmem_s;
+  __shared__ int cmax[DD_MAXC], rexp[TT_ROWS], fexp[DD_MAXC];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int RC = a.g.RC;
+  const long ntot = (long)a.g.nsub * a.tps;
+  const long f0 = blockIdx.x * ntot / gridDim.x, f1 = (blockIdx.x + 1) * ntot / gridDim.x;
+  auto rows_of = [&](int k) { return a.spatial ? a.g.N[k] : a.g.n; };
+  auto valid = [&](long f) { return (int)(f % a.tps) * TT_ROWS < rows_of((int)(f / a.tps)); };
+  auto next_valid = [&](long f) {
+    while (f < f1 && !valid(f)) ++f;
+    return f;
+  };
+  auto row0 = [&](long f) {
+    const int k = (int)(f / a.tps);
+    return (a.spatial ? (long)a.g.rowoff[k] : (long)k * a.g.n) + (long)(f % a.tps) * TT_ROWS;
+  };
+  long f = next_valid(f0);
+  if (f >= f1) return;
+  if (tid == 0) {
+    tc::mbar_init(&bar_tma, 1);
+    tc::mbar_init(&bar_mma, 1);
+    tc::mbar_init_fence();
+  }
+  if (warp == 0) tc::tmem_alloc(&tmem_s, 512);          // OZ_DIG accumulators of 64 columns
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_s;
+  const uint32_t box_bytes = (uint32_t)TT_ROWS * a.lda * 8;
+  if (tid == 0) {
+    tc::mbar_arrive_expect_tx(&bar_tma, box_bytes);
+    tc::tma_load_2d(base, &mapA, 0, (int)row0(f), &bar_tma);
+  }
+  bool alive = true;
+  int it = 0, nmma = 0;
+  for (; f < f1 && alive; f = next_valid(f + 1), ++it) {
+    const long fn = next_valid(f + 1);
+    const int k = (int)(f / a.tps), rows = rows_of(k);
+    const int r0 = (int)(f % a.tps) * TT_ROWS, nrow = min(TT_ROWS, rows - r0);
+    const int ni = a.ninner ? a.ninner[k] : a.ninner_fix;
+    const int nc = a.ncols ? a.ncols[k] : a.ncols_fix;
+    const int N = nc <= 16 ? 16 : (nc + 15) / 16 * 16;
+    count_work(a.g, KS_OZ_TALL, 2.0 * nrow * ni * nc);
+    const double* Mk = a.bsmall >= 0 ? a.smbase + ((long)k * NSMALL + a.bsmall) * RC * RC
+                                     : a.Bm + (long)k * RC * RC;
+    if (tid < DD_MAXC) cmax[tid] = 0;
+    const bool got = tc::mbar_wait(&bar_tma, it & 1, kWait);
+    __syncthreads();
+    // column exponents of the tile: c_k = max_r E(A[r][k]) - 1022
+    for (int e = tid; e < TT_ROWS * DD_MAXC; e += TT_THREADS) {
+      const int kk = e & (DD_MAXC - 1), r = e >> 6;
+      if (kk < ni && r < nrow) atomicMax(&cmax[kk], f64_bexp(st[r * a.lda + kk]));
+    }
+    __syncthreads();
+    // row exponents of A 2^-c: e_r = max_k (E(A[r][k]) - c_k) - 1022 (2 threads per row)
+    {
+      const int r = tid >> 1, h = tid & 1;
+      int mx = -100000;
+      if (r < nrow)
+        for (int kk = h; kk < ni; kk += 2) {
+          const int E = f64_bexp(st[r * a.lda + kk]);
+          if (E) mx = max(mx, E - (cmax[kk] - 1022));
+        }
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      if (h == 0) rexp[r] = mx - 1022;
+    }
+    // column exponents of 2^c M: f_n = max_k (E(M[k][n]) + c_k) - 1022
+    if (tid < DD_MAXC) {
+      int mx = -100000;
+      if (tid < nc)
+        for (int kk = 0; kk < ni; ++kk) {
+          const int E = f64_bexp(Mk[kk * RC + tid]);
+          if (E && cmax[kk]) mx = max(mx, E + (cmax[kk] - 1022));
+        }
+      fexp[tid] = mx - 1022;
+    }
+    __syncthreads();
+    // digit planes of (2^c M)^T: element (n, k) relative to 2^(f_n - c_k) (the N rows and
+    // K halves the products read)
+    const int kw = ni > 32 ? 64 : 32;
+    for (int e = tid; e < N * kw; e += TT_THREADS) {
+      const int n = e / kw, kk = e - n * kw;
+      uint16_t d[OZ_DIG];
+      const long long T = (n < nc && kk < ni && cmax[kk])
+                              ? oz_fixed(Mk[kk * RC + n], fexp[n] - (cmax[kk] - 1022)) : 0;
+      oz_digits(T, d);
+      const uint32_t off = tc::op_off(n, kk * 2, 128);
+#pragma unroll
+      for (int s2 = 0; s2 < OZ_DIG; ++s2) *reinterpret_cast<uint16_t*>(msl + s2 * OZ_MSL + off) = d[s2];
+    }
+    const int nh = ni > 32 ? 2 : 1;
+    for (int h = 0; h < nh; ++h) {
+      if (h > 0) alive = tc::mbar_wait(&bar_mma, nmma++ & 1, kWait) && alive;   // planes free
+      // digit planes of the tile's columns 32 h .. 32 h + 31: element (r, k) of A 2^-c
+      // relative to 2^(e_r + c_k)
+      for (int e = tid; e < TT_ROWS * 32; e += TT_THREADS) {
+        const int r = e >> 5, kk = 32 * h + (e & 31);
+        uint16_t d[OZ_DIG];
+        const long long T = (got && r < nrow && kk < ni && cmax[kk])
+                                ? oz_fixed(st[r * a.lda + kk], rexp[r] + (cmax[kk] - 1022)) : 0;
+        oz_digits(T, d);
+        const uint32_t off = tc::op_off(r, (e & 31) * 2, 64);
+#pragma unroll
+        for (int s2 = 0; s2 < OZ_DIG; ++s2) *reinterpret_cast<uint16_t*>(asl + s2 * OZ_ASL + off) = d[s2];
+      }
+      tc::fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+        if (h == nh - 1 && fn < f1) {                  // the stage is no longer read
+          tc::mbar_arrive_expect_tx(&bar_tma, box_bytes);
+          tc::tma_load_2d(base, &mapA, 0, (int)row0(fn), &bar_tma);
+        }
+        const uint32_t id = tc::idesc(tc::FMT_BF16, 128, N);
+        const uint32_t sa = tc::smem_u32(asl), sb = tc::smem_u32(msl);
+        for (int g = 0; g < OZ_DIG; ++g)
+          for (int s1 = 0; s1 <= g; ++s1)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const uint64_t ad = tc::sdesc(sa + s1 * OZ_ASL + 256 * j, 128, 512);
+              const uint64_t bd = tc::sdesc(sb + (g - s1) * OZ_MSL + 256 * (2 * h + j), 128, 1024);
+              tc::mma_bf16(tmem + (uint32_t)(g * 64), ad, bd, id,
+                           (h > 0 || s1 > 0 || j > 0) ? 1u : 0u);
+            }
+        tc::mma_commit(&bar_mma);
+      }
+      __syncwarp();
+    }
+    alive = tc::mbar_wait(&bar_mma, nmma++ & 1, kWait) && alive && got;
+    tc::fence_after_sync();
+    // epilogue: row m of the tile, the 16-column groups of parity w / 4
+    const int m = (warp & 3) * 32 + lane, r = r0 + m;
+    double* y = a.Y + (row0(f) + m) * a.ldy;
+    const int er = m < nrow ? rexp[m] : 0;
+    for (int c0 = (warp >> 2) * 16; c0 < N; c0 += 32) {
+      float D[OZ_DIG][16];
+#pragma unroll
+      for (int g = 0; g < OZ_DIG; ++g)
+        tc::tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * 64 + c0), D[g]);
+      if (r < rows) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = c0 + j;
+          if (c < nc) {
+            long long J = 0;
+#pragma unroll
+            for (int g = 0; g < OZ_DIG - 1; ++g) J += (long long)__float2int_rn(D[g][j]) << (40 - 8 * g);
+            J += (long long)(__float2int_rn(D[OZ_DIG - 1][j]) >> 8);
+            y[c] = oz_to_f64(J, er + fexp[c] - 56);
+          } else if (c < a.ldy) {
+            y[c] = 0.0;
+          }
+        }
+      }
+    }
+    if (r < rows && warp < 4)
+      for (int c = N; c < a.ldy; ++c) y[c] = 0.0;
+    tc::fence_before_sync();
+    alive = __syncthreads_and(alive) != 0;
+    if (!alive && tid == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
+  }
+  if (!alive && tid == 0 && f < f1) tc::mbar_wait(&bar_tma, it & 1, kWait);   // load in flight
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
 cudaError_t tc_init() {
@@ -494,6 +745,9 @@ cudaError_t tc_init() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_tc_gram<tc::FMT_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc_gram_smem());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_oz_tall, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)oz_tall_smem());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_tc_gram<tc::FMT_BF16>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_gram_smem());
@@ -518,6 +772,25 @@ bool tc_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, c
     k_tc_tall<tc::FMT_BF16><<<grid, TT_THREADS, tc_tall_smem(), st>>>(map, a);
   else
     k_tc_tall<tc::FMT_TF32><<<grid, TT_THREADS, tc_tall_smem(), st>>>(map, a);
+  pend(st);
+  return true;
+}
+
+bool oz_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
+             int lda, const int* ninner, int ninner_fix, const double* Bm, int bsmall,
+             const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy) {
+  const long rows_all = spatial ? P.Ntot : (long)P.g.nsub * P.g.n;
+  CUtensorMap map;
+  if (!make_map(&map, A, lda, rows_all, TT_ROWS)) return false;
+  TcTall a;
+  a.g = P.g; a.spatial = spatial; a.lda = lda; a.ninner = ninner; a.ninner_fix = ninner_fix;
+  a.Bm = Bm; a.bsmall = bsmall; a.smbase = smbase; a.ncols = ncols; a.ncols_fix = ncols_fix;
+  a.Y = Y; a.ldy = ldy; a.alpha = 1.0; a.accumulate = 0; a.status = status;
+  a.tps = ((spatial ? P.maxN : P.g.n) + TT_ROWS - 1) / TT_ROWS;
+  const long ntot = (long)P.g.nsub * a.tps;
+  const int grid = (int)std::min<long>(ntot, P.nsm);
+  pbeg(st, KS_OZ_TALL);
+  k_oz_tall<<<grid, TT_THREADS, oz_tall_smem(), st>>>(map, a);
   pend(st);
   return true;
 }
