@@ -138,12 +138,21 @@ typedef struct dd_options {
                       /* DD_PRODUCTS_TENSOR: on the BF16 tensor cores with the error-free      */
                       /* splitting of Ozaki et al. (seven 8-bit digits per value, exact FP32   */
                       /* accumulation, FP64-level error).  Results agree to FP64 rounding, not */
-                      /* bits.                                                                  */
+                      /* bits.  DD_PRODUCTS_AUTO: per row family (spatial rows, angular rows)  */
+                      /* the faster of the two: timed when the solver is created if autotune  */
+                      /* is set, else the tensor cores where the family has at least two      */
+                      /* 128-row tiles per SM.                                                 */
+  int autotune;       /* 1: when the solver is created, time the launch choices on its own    */
+                      /* workspace and keep the fastest: the products' engine per row family  */
+                      /* (with DD_PRODUCTS_AUTO) and the chunk counts of the chunked Gram     */
+                      /* reductions (the heuristic's, a half and a quarter of it; every count */
+                      /* keeps a fixed summation order).  Cached per problem shape in the     */
+                      /* process.  0: fixed heuristics.  See dd_dlra_tuning.                   */
 } dd_options;
 
 enum { DD_SPLIT_LIE = 0, DD_SPLIT_STRANG = 1 };
 enum { DD_KSPLIT_EIGEN = 0, DD_KSPLIT_FLUX = 1 };
-enum { DD_PRODUCTS_FP64 = 0, DD_PRODUCTS_TENSOR = 1 };
+enum { DD_PRODUCTS_FP64 = 0, DD_PRODUCTS_TENSOR = 1, DD_PRODUCTS_AUTO = 2 };
 
 typedef struct dd_dlra* dd_dlra_t;
 
@@ -241,6 +250,16 @@ dd_status dd_dlra_profile(dd_dlra_t h, int nsteps, double* ms, int* launches);
  * products).  The latency-bound slots (small eigen/singular-value problems, completions,
  * reductions) count nothing.  Allocates a small device buffer for the counters. */
 dd_status dd_dlra_profile_work(dd_dlra_t h, int nsteps, double* ms, int* launches, double* flops);
+
+/*
+ * dd_dlra_tuning — the launch choices the solver runs with (host outputs, either may be
+ * NULL): choice[4] = {tensor-core products for spatial rows (0/1), for angular rows (0/1),
+ * Gram chunks per subdomain for spatial rows, for angular rows}; ms[8] = the autotuner's
+ * timings per family (spatial, then angular): FP64 products, tensor-core products, the
+ * best and the worst chunk count (ms for one trial Gram and reduction); -1 where nothing
+ * was timed (autotune off, or a choice fixed by the options).
+ */
+dd_status dd_dlra_tuning(dd_dlra_t h, int* choice, double* ms);
 
 /*
  * dd_dlra_scalar_flux_noalloc — the density of dd_dlra_scalar_flux written to the

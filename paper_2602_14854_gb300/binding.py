@@ -22,14 +22,14 @@ DD_RANK_FIXED, DD_RANK_TOL = 0, 1
 DD_EULER, DD_RK4 = 0, 1
 DD_FP64, DD_MIXED, DD_TF32, DD_BF16 = 0, 1, 2, 3
 PRECISIONS = {"fp64": DD_FP64, "mixed": DD_MIXED, "tf32": DD_TF32, "bf16": DD_BF16}
-PRODUCTS = {"fp64": 0, "tensor": 1}
+PRODUCTS = {"fp64": 0, "tensor": 1, "auto": 2}
 
 # every symbol include/ddlra.h declares
 EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scalar_flux",
            "dd_dlra_ranks", "dd_dlra_info", "dd_dlra_get_factors", "dd_dlra_set_factors",
            "dd_dlra_sync", "dd_dlra_destroy", "dd_last_error", "dd_profile_slots",
            "dd_profile_slot_name", "dd_dlra_profile", "dd_dlra_profile_work",
-           "dd_dlra_scalar_flux_noalloc",
+           "dd_dlra_scalar_flux_noalloc", "dd_dlra_tuning",
            "dd_dlra_create_batch", "dd_dlra_instance"]
 
 _dp = C.POINTER(C.c_double)
@@ -63,7 +63,8 @@ class Options(C.Structure):
                 ("r_min", C.c_int), ("r_max", C.c_int), ("r_aug_max", C.c_int),
                 ("integrator", C.c_int), ("c_adv", C.c_double), ("dt", C.c_double),
                 ("tau", C.c_double), ("precision", C.c_int), ("mass_fix", C.c_int),
-                ("splitting", C.c_int), ("kstep_split", C.c_int), ("products", C.c_int)]
+                ("splitting", C.c_int), ("kstep_split", C.c_int), ("products", C.c_int),
+                ("autotune", C.c_int)]
 
 
 _lib = None
@@ -99,6 +100,7 @@ def load(path: str | None = None):
     lib.dd_dlra_profile.argtypes = [vp, C.c_int, _dp, _ip]
     lib.dd_dlra_profile_work.argtypes = [vp, C.c_int, _dp, _ip, _dp]
     lib.dd_dlra_scalar_flux_noalloc.argtypes = [vp, vp]
+    lib.dd_dlra_tuning.argtypes = [vp, _ip, _dp]
     lib.dd_dlra_create_batch.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Tiling),
                                          C.POINTER(Quadrature), C.POINTER(Fields),
                                          C.POINTER(_dp), C.POINTER(Options), vp, C.POINTER(vp)]
@@ -133,8 +135,10 @@ class Solver:
     """DD-DLRA solver on one problem; wraps a dd_dlra_t handle."""
 
     def __init__(self, wl, tau: float = 1e-5, stream: int = 0, use_graph: bool = False,
-                 precision: str = "fp64", products: str = "fp64"):
-        """wl: one workload, or a list of workloads sharing the direction table (a batch)."""
+                 precision: str = "fp64", products: str = "fp64", autotune: bool = False):
+        """wl: one workload, or a list of workloads sharing the direction table (a batch).
+        products: "fp64", "tensor" or "auto" (dd_options.products); autotune: time the
+        launch choices at creation (dd_options.autotune)."""
         lib = load()
         self.lib = lib
         wls = list(wl) if isinstance(wl, (list, tuple)) else [wl]
@@ -167,7 +171,8 @@ class Solver:
                               w.r_max, w.r_aug_max, DD_RK4 if w.integrator == "rk4" else DD_EULER,
                               w.c_adv, w.dt, tau, PRECISIONS[precision],
                               1 if w.mass_fix else 0, 1 if w.splitting == "strang" else 0,
-                              1 if w.kstep_split == "flux" else 0, PRODUCTS[products])
+                              1 if w.kstep_split == "flux" else 0, PRODUCTS[products],
+                              1 if autotune else 0)
             g0s[i] = _ptr(g0)
         w0 = wls[0]
         ox, oy, w = _d(w0.omega_x), _d(w0.omega_y), _d(w0.w)
@@ -195,6 +200,15 @@ class Solver:
         self.ncells_out = sum(w.nx * w.ny for w in wls)
         if use_graph:
             _check(lib, lib.dd_dlra_set_graph(h, 1))
+
+    def tuning(self):
+        """The launch choices in use and the autotuner's timings (dd_dlra_tuning):
+        ({"oz_spatial", "oz_angular", "chunks_spatial", "chunks_angular"}, ms[8])."""
+        ch = np.zeros(4, dtype=np.int32)
+        ms = np.zeros(8)
+        _check(self.lib, self.lib.dd_dlra_tuning(self.h, ch.ctypes.data_as(_ip), _ptr(ms)))
+        return ({"oz_spatial": int(ch[0]), "oz_angular": int(ch[1]),
+                 "chunks_spatial": int(ch[2]), "chunks_angular": int(ch[3])}, ms.tolist())
 
     def step(self, nsteps: int = 1):
         _check(self.lib, self.lib.dd_dlra_step(self.h, int(nsteps)))

@@ -97,6 +97,7 @@ struct dd_dlra {
   double *d_dm, *d_mvec;
   unsigned* d_status;
   double* d_noalloc;   // device address of the allocation-free readout's scratch array
+  double tune_ms[8];   // the autotuner's timings (dd_dlra_tuning)
   dd::Problem P;
 };
 
@@ -274,8 +275,10 @@ static dd_status check_instance(const dd_grid* grid, const dd_tiling* tiling,
     return fail(DD_ERR_ARG, "splitting");
   if (opt->kstep_split != DD_KSPLIT_EIGEN && opt->kstep_split != DD_KSPLIT_FLUX)
     return fail(DD_ERR_ARG, "kstep_split");
-  if (opt->products != DD_PRODUCTS_TENSOR && opt->products != DD_PRODUCTS_FP64)
+  if (opt->products != DD_PRODUCTS_TENSOR && opt->products != DD_PRODUCTS_FP64 &&
+      opt->products != DD_PRODUCTS_AUTO)
     return fail(DD_ERR_ARG, "products");
+  if (opt->autotune != 0 && opt->autotune != 1) return fail(DD_ERR_ARG, "autotune");
   if (!(opt->dt > 0.0) || !(opt->tau >= 0.0)) return fail(DD_ERR_ARG, "dt / tau");
   const int RS = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_max;
   const int fl = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_min;
@@ -308,9 +311,10 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     const dd_options& b = opts[i];
     if (b.rank_mode != a.rank_mode || b.integrator != a.integrator || b.precision != a.precision ||
         b.c_adv != a.c_adv || b.tau != a.tau || b.tol != a.tol || b.mass_fix != a.mass_fix ||
-        b.splitting != a.splitting || b.kstep_split != a.kstep_split || b.products != a.products)
+        b.splitting != a.splitting || b.kstep_split != a.kstep_split || b.products != a.products ||
+        b.autotune != a.autotune)
       return fail(DD_ERR_ARG, "instances of a batch must share rank mode, tolerance, integrator, "
-                              "precision, mass_fix, splitting, kstep_split, products, c_adv and tau");
+                              "precision, mass_fix, splitting, kstep_split, products, autotune, c_adv and tau");
   }
   const dd_options* opt = &opts[0];
 
@@ -341,7 +345,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   // augmentation input width both fit
   h->RC = std::max(raug_max, h->MC);
   // the tensor-core forms stage rows with TMA, which needs rows on 16-byte boundaries
-  if (opt->precision == DD_TF32 || opt->precision == DD_BF16 || opt->products == DD_PRODUCTS_TENSOR)
+  if (opt->precision == DD_TF32 || opt->precision == DD_BF16 || opt->products != DD_PRODUCTS_FP64)
     h->RC += h->RC & 1;
   h->r_floor = opt->rank_mode == DD_RANK_FIXED ? opt->rank : opt->r_min;
   auto bail = [&](dd_status s, const std::string& m) {
@@ -592,7 +596,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
            : opt->precision == DD_BF16 ? dd::PREC_BF16
                                        : dd::PREC_FP64;
   P.Ntot = Nt;
-  P.oz = opt->products == DD_PRODUCTS_TENSOR ? 1 : 0;
+  P.oz_sp = P.oz_ang = opt->products == DD_PRODUCTS_TENSOR ? 1 : 0;
   P.mass_fix = opt->mass_fix;
   P.splitting = opt->splitting;
   P.kstep_split = opt->kstep_split;
@@ -616,7 +620,12 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     return bail(DD_ERR_CUDA, "device allocation failed");
   if (dd::orth_init() != cudaSuccess || dd::phase_init() != cudaSuccess)
     return bail(DD_ERR_CUDA, "kernel attribute setup failed");
-  if ((P.prec >= dd::PREC_TF32 || P.oz) && dd::tc_init() != cudaSuccess)
+  if (opt->products == DD_PRODUCTS_AUTO) {      // the heuristic; the autotuner may revise it
+    const long tiles_sp = (long)nsub * ((h->maxN + 127) / 128), tiles_ang = (long)nsub * ((n + 127) / 128);
+    P.oz_sp = tiles_sp >= 2L * P.nsm;
+    P.oz_ang = tiles_ang >= 2L * P.nsm;
+  }
+  if ((P.prec >= dd::PREC_TF32 || opt->products != DD_PRODUCTS_FP64) && dd::tc_init() != cudaSuccess)
     return bail(DD_ERR_CUDA, "tensor-core setup failed (tensor-map encoder or kernel attributes)");
   // the allocation-free readout's scratch array, looked up with this solver's device and
   // context current (no allocation)
@@ -657,6 +666,11 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
         cudaMemset(h->d_dm, 0, sizeof(double) * (size_t)Nt) != cudaSuccess)
       return bail(DD_ERR_CUDA, "clear workspace");
   }
+  for (int i = 0; i < 8; ++i) h->tune_ms[i] = -1.0;
+  if (opt->autotune &&
+      dd::autotune(P, bufs(h, 0, 1), h->stream, opt->products == DD_PRODUCTS_AUTO, 1, h->tune_ms) !=
+          cudaSuccess)
+    return bail(DD_ERR_CUDA, "autotuner");
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(DD_ERR_CUDA, "create: device error");
   *out = h;
   return DD_OK;
@@ -820,6 +834,20 @@ const char* dd_profile_slot_name(int slot) {
 
 dd_status dd_dlra_profile(dd_dlra_t h, int nsteps, double* ms, int* launches) {
   return dd_dlra_profile_work(h, nsteps, ms, launches, nullptr);
+}
+
+dd_status dd_dlra_tuning(dd_dlra_t h, int* choice, double* ms) {
+  g_err.clear();
+  if (!h) return fail(DD_ERR_ARG, "null handle");
+  if (choice) {
+    choice[0] = h->P.oz_sp;
+    choice[1] = h->P.oz_ang;
+    choice[2] = h->P.nchunk_sp;
+    choice[3] = h->P.nchunk_ang;
+  }
+  if (ms)
+    for (int i = 0; i < 8; ++i) ms[i] = h->tune_ms[i];
+  return DD_OK;
 }
 
 dd_status dd_dlra_profile_work(dd_dlra_t h, int nsteps, double* ms, int* launches, double* flops) {

@@ -128,7 +128,8 @@ struct Problem {
   int mass_fix;           // conserved-moment correction at the end of every step
   int splitting;          // 0 Lie (x, y, collision), 1 Strang (x/2, y/2, collision, y/2, x/2)
   int kstep_split;        // C+/C- of the advection K-step: 0 eigen-split, 1 direction split
-  int oz;                 // FP64 tall products on the tensor cores (Ozaki splitting)
+  int oz_sp, oz_ang;      // FP64 tall products on the tensor cores (Ozaki splitting), for
+                          // the spatial / the angular row family
   // physical inflow (null without): per subdomain and side (x-lo, x-hi, y-lo, y-hi) an
   // on flag, face values sqrt(hx hy) g per line (maxlines), the angular column
   // sqrt(w) m_in h (n) and its augmentation scale |g|_x
@@ -196,5 +197,14 @@ void scalar_flux(const Problem& P, const double* X, const double* V, const doubl
                  double* work, double* rho, int nx, cudaStream_t st);
 cudaError_t phase_init();   // kernel attributes for every capacity up to DD_MAXC
 size_t part_elems(const Problem& P);
+// Launch choices timed on the solver's own workspace (called once, when a solver is
+// created): the engine of the FP64 tall x small products per row family (when
+// tune_products) and the chunk counts of the chunked Gram reductions (when tune_chunks).
+// The winners are written to P; each family's times are reported in ms[8] (FP64 products,
+// tensor-core products, then the chunk candidates' best and worst), -1 where not timed.
+// Choices are cached per shape (subdomains, cells, directions, column capacity,
+// precision): a later solver of the same shape reuses them without timing.
+cudaError_t autotune(Problem& P, const PhaseBufs& B, cudaStream_t st, int tune_products,
+                     int tune_chunks, double* ms);
 
 }  // namespace dd

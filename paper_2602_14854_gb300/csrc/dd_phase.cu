@@ -18,6 +18,10 @@
 //   L-step  per direction q:  dL_q/dt = -(c Omega_q/h) [(I - T) L_q - G_lo Vh_q]  (Omega_q > 0)
 //                              dL_q/dt = -(c Omega_q/h) [(T^T - I) L_q + G_hi Vh_q] (Omega_q < 0)
 //           (per-direction upwinding of f = U L^T with ghost f^b = K^b V^T, Eq. (advx_evolL)).
+#include <map>
+#include <mutex>
+#include <vector>
+
 #include "dd_internal.cuh"
 
 #include <climits>
@@ -1593,7 +1597,8 @@ static void tall(const Problem& P, const PhaseBufs& B, cudaStream_t st, int spat
                  const double* A, int lda, const int* ninner, int ninner_fix, const double* Bm,
                  int bsmall, const int* ncols, int ncols_fix, double* Y, int ldy,
                  double* gpart) {
-  if (P.oz && !gpart && oz_tall(P, B.status, st, spatial, A, lda, ninner, ninner_fix, Bm, bsmall,
+  if ((spatial ? P.oz_sp : P.oz_ang) && !gpart &&
+      oz_tall(P, B.status, st, spatial, A, lda, ninner, ninner_fix, Bm, bsmall,
                                 B.sm, ncols, ncols_fix, Y, ldy))
     return;
   TallArgs a;
@@ -1627,6 +1632,145 @@ static void reduce_to(const Problem& P, const PhaseBufs& B, cudaStream_t st, int
   pbeg(st, KS_REDUCE);
   k_reduce<<<reduce_grid(P.g, nblk), DD_THREADS, 0, st>>>(B.part, nchunk, nblk, d, B.sm, P.g.RC);
   pend(st);
+}
+
+// ---------------------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------------------
+// deterministic trial values in [-1, 1) (a multiplicative hash of the index)
+__global__ void k_trial_fill(double* a, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    a[i] = (double)((unsigned)(i * 2654435761ull) >> 8) * (1.0 / 8388608.0) - 1.0;
+}
+
+namespace {
+struct TuneChoice {
+  int oz_sp, oz_ang, nch_sp, nch_ang;
+  double ms[8];
+};
+std::mutex g_tune_mu;
+std::map<std::vector<long>, TuneChoice> g_tune_cache;
+
+// average time of fn() on st over reps launches after one untimed call (ms; -1 on error)
+template <class F>
+double time_on(cudaStream_t st, int reps, F fn) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return -1.0;
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1.0; }
+  fn();
+  cudaEventRecord(a, st);
+  for (int i = 0; i < reps; ++i) fn();
+  cudaEventRecord(b, st);
+  float t = -1.0f;
+  const bool ok = cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&t, a, b) == cudaSuccess;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ok ? (double)t / reps : -1.0;
+}
+}  // namespace
+
+cudaError_t autotune(Problem& P, const PhaseBufs& B, cudaStream_t st, int tune_products,
+                     int tune_chunks, double* ms) {
+  for (int i = 0; i < 8; ++i) ms[i] = -1.0;
+  if (!tune_products && !tune_chunks) return cudaSuccess;
+  const int RC = P.g.RC, nsub = P.g.nsub;
+  const std::vector<long> key = {nsub, P.maxN, P.g.n, RC, P.prec, P.Ntot, tune_products,
+                                 tune_chunks, P.nchunk_sp, P.nchunk_ang};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      const TuneChoice& c = it->second;
+      if (tune_products) { P.oz_sp = c.oz_sp; P.oz_ang = c.oz_ang; }
+      if (tune_chunks) { P.nchunk_sp = c.nch_sp; P.nchunk_ang = c.nch_ang; }
+      for (int i = 0; i < 8; ++i) ms[i] = c.ms[i];
+      return cudaSuccess;
+    }
+  }
+  // trial operands in the workspace: A = K (spatial) / L (angular), Y = Hw / Hwa, the
+  // small matrices filled with trial values, every column count = RC (in keep)
+  const long nsm_elems = (long)nsub * NSMALL * RC * RC;
+  k_trial_fill<<<P.nsm * 4, 256, 0, st>>>(B.K, P.Ntot * RC);
+  k_trial_fill<<<P.nsm * 4, 256, 0, st>>>(B.L, (long)nsub * P.g.n * RC);
+  k_trial_fill<<<P.nsm * 4, 256, 0, st>>>(B.sm, nsm_elems);
+  {
+    std::vector<int> cnt(nsub, RC);
+    cudaError_t e = cudaMemcpyAsync(B.keep, cnt.data(), sizeof(int) * nsub, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+  }
+  const int REPS = 3;
+  for (int sp = 1; sp >= 0; --sp) {
+    const double* A = sp ? B.K : B.L;
+    double* Y = sp ? B.Hw : B.Hwa;
+    const int f = sp ? 0 : 1;
+    if (tune_products) {
+      // both engines at two column counts (half and full capacity).  The FP64 kernel also
+      // forms the Gram of its output from the same tiles in the orthonormalisation (one of
+      // its two products there): the tensor-core side is charged half a separate Gram
+      // reduction per product.
+      const int half = std::max(2, (RC / 2) & ~1);
+      Problem Q = P;
+      Q.oz_sp = Q.oz_ang = 0;
+      const double tg = time_on(st, REPS, [&] {
+        const int n = gram_partials(P, B, st, sp, A, RC, B.keep, nullptr);
+        Dst d;
+        for (int i = 0; i < 8; ++i) d.idx[i] = SM_QM;
+        reduce_to(P, B, st, n, 1, d);
+      });
+      double t64 = 0.0, toz = tg > 0.0 ? tg : 0.0;
+      bool oz_ok = true;
+      for (int c : {half, RC}) {
+        t64 += time_on(st, REPS, [&] {
+          tall(Q, B, st, sp, A, RC, nullptr, c, nullptr, SM_QM, nullptr, c, Y, P.WC);
+        });
+        toz += time_on(st, REPS, [&] {
+          oz_ok = oz_ok && oz_tall(P, B.status, st, sp, A, RC, nullptr, c, nullptr, SM_QM, B.sm,
+                                   nullptr, c, Y, P.WC);
+        });
+      }
+      ms[4 * f + 0] = t64;
+      ms[4 * f + 1] = oz_ok ? toz : -1.0;
+      const int pick = oz_ok && toz > 0.0 && toz < t64 ? 1 : 0;
+      if (sp) P.oz_sp = pick; else P.oz_ang = pick;
+    }
+    if (tune_chunks) {
+      // the Gram A^T A with its fixed-order reduction, at the heuristic's chunk count and
+      // at a half and a quarter of it (the partials buffer is sized for the heuristic's)
+      int& nch = sp ? P.nchunk_sp : P.nchunk_ang;
+      const int h = nch;
+      double best = -1.0, worst = -1.0;
+      int pick = h;
+      for (int cand : {h, h / 2, h / 4}) {
+        if (cand < 1 || (cand != h && cand == pick)) continue;
+        Problem Q = P;
+        (sp ? Q.nchunk_sp : Q.nchunk_ang) = cand;
+        const double t = time_on(st, REPS, [&] {
+          const int n = gram_partials(Q, B, st, sp, A, RC, B.keep, nullptr);
+          Dst d;
+          for (int i = 0; i < 8; ++i) d.idx[i] = SM_QM;
+          reduce_to(Q, B, st, n, 1, d);
+        });
+        if (t > 0.0 && (best < 0.0 || t < 0.97 * best)) { best = t; pick = cand; }
+        worst = std::max(worst, t);
+      }
+      nch = pick;
+      ms[4 * f + 2] = best;
+      ms[4 * f + 3] = worst;
+    }
+  }
+  // leave the workspace as a new solver has it
+  cudaError_t e = cudaMemsetAsync(B.sm, 0, sizeof(double) * nsm_elems, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneChoice c;
+    c.oz_sp = P.oz_sp; c.oz_ang = P.oz_ang; c.nch_sp = P.nchunk_sp; c.nch_ang = P.nchunk_ang;
+    for (int i = 0; i < 8; ++i) c.ms[i] = ms[i];
+    g_tune_cache[key] = c;
+  }
+  return cudaSuccess;
 }
 
 // dm += sign * scalar flux of A (spatial, cnt columns) in the angular basis V (with
@@ -1663,7 +1807,7 @@ static void orthonormalize(const Problem& P, const PhaseBufs& B, cudaStream_t st
   // U1 = A M; its Gram from the same tiles when their partials fit the buffer (one partial
   // per 32-row tile, counted from each subdomain's first row), else by k_gram
   const int ntile = ((sp ? P.maxN : P.g.n) + TALL_ROWS - 1) / TALL_ROWS;
-  const bool fuse = !P.oz && ntile <= 8 * std::max(P.nchunk_sp, P.nchunk_ang);
+  const bool fuse = !(sp ? P.oz_sp : P.oz_ang) && ntile <= 8 * std::max(P.nchunk_sp, P.nchunk_ang);
   tall(P, B, st, sp, a.A, a.lda, a.acols, 0, nullptr, SM_QM, B.keep, 0, W, P.WC,
        fuse ? B.part : nullptr);
   nch = fuse ? ntile : gram_partials(P, B, st, sp, W, P.WC, B.keep, nullptr);

@@ -18,6 +18,7 @@
 //              k_reduce sums in FP64 (the same layout as the FP64 Gram kernels).
 #include <cuda.h>
 
+#include <algorithm>
 #include <climits>
 
 #include "dd_internal.cuh"
@@ -101,6 +102,7 @@ struct TcTall {
   double alpha; int accumulate;     // accumulate: Y += alpha A M on columns < nc only
   int tps;                          // 128-row tiles per subdomain (of the largest)
   unsigned* status;
+  const double* A;                  // A itself (the kernels that load it without a tensor map)
 };
 
 #define TT_ROWS 128
@@ -477,54 +479,91 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_tc_gram(const __grid_constant
 // ---------------------------------------------------------------------------------------
 // Y = A M with the error-free splitting of Ozaki, Ogita, Oishi and Rump (2012, "Error-free
 // transformations of matrix multiplication by using fast routines of matrix multiplication
-// and its applications"): per 128-row tile the columns of A are equalised by powers of two
-// 2^-c_k (folded into the rows of M), each row of A and each column of M get a power-of-two
-// scale, and every value becomes a fixed-point integer with 56 fraction bits, split into 7
-// balanced base-256 digits (|digit| <= 256: exact in BF16).  Digit products of orders s, t
-// go to the TMEM accumulator of g = s + t (pairs with g <= 6; 28 of 49): every partial sum is
-// an integer below 2^23, so the FP32 accumulation is exact.  The epilogue combines the seven
-// sums in 64-bit integers and builds the FP64 result from bits.  Error: a few units of 2^-56
-// of max|A row| max|M column| per entry (FP64 rounding of the products is 2^-53 each).  No
-// FP64 instruction runs anywhere in the kernel.
+// and its applications").  The rows of M are equalised by powers of two, M' = diag(2^-mu) M
+// with mu_k the exponent of row k's largest entry, the inverse scale folded into the columns
+// of A (A' = A diag(2^mu)); each row r of A' gets the power-of-two bound 2^e_r and each column
+// n of M' the bound 2^f_n, and every value becomes a fixed-point integer with 56 fraction bits
+// relative to its bound (truncated), split into 7 balanced base-256 digits (the top digit is at
+// most 256, the others at most 128 in magnitude: exact in BF16).  Digit products of
+// orders s, t go to the TMEM accumulator of g = s + t (pairs with g <= 6; 28 of 49): with at
+// most 64 terms of at most 7 pairs every partial sum is an integer below 2^24, so the FP32
+// accumulation is exact.  The epilogue combines the seven sums in 64-bit integers and builds
+// the FP64 result from bits.  Error: a few units of 2^-56 of max_k |A'[r][k]| max_k
+// |M'[k][n]| per entry (the FP64 rounding of each product is 2^-53 of the product).  No FP64
+// arithmetic runs in the kernel.
+//
+// A CTA (one per SM: 16 worker warps and one warp that issues the MMAs) walks a contiguous
+// range of 128-row tiles.  M's digit planes
+// are formed once per subdomain.  Per tile, each warp loads 8 rows straight into registers
+// (16-byte loads, 8 rows x 64 bytes per instruction), takes the row bounds by shuffles and
+// writes the digit planes (two digits per 32-bit shared store); one thread then issues the
+// 28 x (K / 16) MMAs.  The planes are double-buffered: tile i's MMAs run while the warps
+// convert tile i + 1, and tile i's epilogue (TMEM -> registers -> FP64 -> a per-warp
+// transposition buffer -> whole-row stores) follows.  When two buffers of a whole row's
+// planes do not fit beside M's (lda > 48), K runs in two passes of 32 on one buffer.
 #define OZ_DIG 7
-#define OZ_ASL (TT_ROWS * 32 * 2)            // 8 KiB: one digit plane of 128 rows x 32 k
-#define OZ_MSL (DD_MAXC * DD_MAXC * 2)       // 8 KiB: one digit plane of M^T (64 x 64)
-size_t oz_tall_smem() { return 1024 + TT_STAGE + OZ_DIG * OZ_ASL + OZ_DIG * OZ_MSL; }
+#define OZ_WORKERS 512                       // 16 warps: loads, digits, epilogue
+#define OZ_THREADS (OZ_WORKERS + 32)         // + one warp that issues the MMAs
+#define OZ_WARPS (OZ_WORKERS / 32)
+#define OZ_NONE (-(1 << 20))                 // exponent of an all-zero row / column
+#define OZ_EPI (OZ_WARPS * 32 * 5 * 8)       // epilogue buffers: 32 rows x 4 (+1) per warp
+#define OZ_SMEM_LIMIT (227 * 1024 - 4096)    // dynamic shared memory (the static part is < 4 KiB)
+
+struct OzPlan {
+  int KP, KA, npass, nbuf;                   // K extent of M's planes, of a pass; passes; buffers
+  size_t mpl, apl, abuf, total;              // bytes: one M plane, one A plane, one A buffer, all
+};
+// the shared-memory plan for inner dimensions up to lda (even, <= 64)
+OzPlan oz_plan(int lda, size_t limit) {
+  OzPlan p;
+  p.KP = (lda + 15) / 16 * 16;
+  p.mpl = (size_t)DD_MAXC * 2 * p.KP;
+  for (int mode = 0; mode < 2; ++mode) {
+    p.KA = mode ? 32 : p.KP;
+    p.nbuf = mode ? 1 : 2;
+    p.npass = (p.KP + p.KA - 1) / p.KA;
+    p.apl = (size_t)TT_ROWS * 2 * p.KA;
+    p.abuf = std::max((size_t)OZ_DIG * p.apl, (size_t)OZ_EPI);
+    p.total = 128 + OZ_DIG * p.mpl + p.nbuf * p.abuf;
+    if (p.total <= limit) break;
+  }
+  return p;
+}
 
 // biased FP64 exponent of x (0 for zero and subnormals)
 __device__ __forceinline__ int f64_bexp(double x) {
-  return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
+  return (int)((unsigned)(__double_as_longlong(x) >> 52) & 0x7ffu);
 }
-// x * 2^(56 - e) rounded to an integer (|x| < 2^e), by integer operations
-__device__ __forceinline__ long long oz_fixed(double x, int e) {
+// The 7 digits of T = trunc(x 2^(56 - e)) (|x| < 2^e, so |T| < 2^56), T = sum_s d_s 2^(48 - 8 s),
+// as exact FP32 values, by integer operations: with the mantissa left-aligned (implicit bit
+// at bit 63) T is one right shift; adding 128 at each of the six low byte positions makes
+// every low byte of V = T + 0x808080808080 equal to d_s + 128 with the borrows and carries
+// of a balanced representation (d_s in [-128, 127] for s >= 1, and d_0 = V >> 48 in
+// [-256, 256]); byte b becomes the FP32 (0x4B4000bb = 1.5 2^23 + b) minus 1.5 2^23 + 128.
+// Signed T needs nothing more: the identity is modular.
+__device__ __forceinline__ void oz_digits(double x, int e, float* d) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const int E = (int)((u >> 52) & 0x7ff);
-  if (E == 0) return 0;
-  const long long m = (long long)((u & 0xfffffffffffffull) | 0x10000000000000ull);
-  const int sh = E - 1019 - e;
-  long long T = 0;
-  if (sh >= 0) T = m << sh;
-  else if (sh > -62) T = (m + (1ll << (-sh - 1))) >> (-sh);
-  return (u >> 63) ? -T : T;
+  const unsigned hi = (unsigned)(u >> 32);
+  const int E = (int)((hi >> 20) & 0x7ffu);
+  const int sh = 1030 + e - E;                       // >= 8
+  const unsigned long long m = (u << 11) | 0x8000000000000000ull;
+  long long T = (E != 0 && sh < 64) ? (long long)(m >> sh) : 0ll;
+  if (hi >> 31) T = -T;
+  const unsigned long long V = (unsigned long long)T + 0x808080808080ull;
+  const unsigned vl = (unsigned)V, vh = (unsigned)(V >> 32);
+  const float c = 12583040.0f;                       // 1.5 2^23 + 128
+  d[6] = __int_as_float((int)__byte_perm(vl, 0x4B400000u, 0x7650)) - c;
+  d[5] = __int_as_float((int)__byte_perm(vl, 0x4B400000u, 0x7651)) - c;
+  d[4] = __int_as_float((int)__byte_perm(vl, 0x4B400000u, 0x7652)) - c;
+  d[3] = __int_as_float((int)__byte_perm(vl, 0x4B400000u, 0x7653)) - c;
+  d[2] = __int_as_float((int)__byte_perm(vh, 0x4B400000u, 0x7650)) - c;
+  d[1] = __int_as_float((int)__byte_perm(vh, 0x4B400000u, 0x7651)) - c;
+  d[0] = __int_as_float(0x4B400000 + ((int)vh >> 16)) - 12582912.0f;
 }
-// the 7 balanced base-256 digits of T (T = sum_s d_s 2^(48 - 8 s), |T| < 2^56) as BF16 bit
-// patterns: the bytes of |T| by 32-bit operations, balanced from the lowest up (a byte
-// >= 128 becomes byte - 256 with a carry into the next), then the sign
-__device__ __forceinline__ void oz_digits(long long T, uint16_t* d) {
-  const bool neg = T < 0;
-  const unsigned long long U = neg ? (unsigned long long)(-T) : (unsigned long long)T;
-  const unsigned tl = (unsigned)U, th = (unsigned)(U >> 32);
-  int b[OZ_DIG] = {(int)(th >> 16), (int)((th >> 8) & 255u), (int)(th & 255u), (int)(tl >> 24),
-                   (int)((tl >> 16) & 255u), (int)((tl >> 8) & 255u), (int)(tl & 255u)};
-#pragma unroll
-  for (int s = OZ_DIG - 1; s > 0; --s) {
-    const int c = b[s] >= 128;
-    b[s] -= c << 8;
-    b[s - 1] += c;
-  }
-#pragma unroll
-  for (int s = 0; s < OZ_DIG; ++s)
-    d[s] = __bfloat16_as_ushort(__float2bfloat16_rn((float)(neg ? -b[s] : b[s])));
+// the BF16 digits of two values packed in one word (each digit has <= 8 significant bits:
+// its BF16 is the top half of its FP32)
+__device__ __forceinline__ uint32_t oz_pack(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 // J * 2^sc as an FP64 (round to nearest even), by integer operations
 __device__ __forceinline__ double oz_to_f64(long long J, int sc) {
@@ -547,36 +586,67 @@ __device__ __forceinline__ double oz_to_f64(long long J, int sc) {
   if (be >= 2047) return __longlong_as_double((long long)(sg | 0x7ff0000000000000ull));
   return __longlong_as_double((long long)(sg | ((unsigned long long)be << 52) | (r & 0xfffffffffffffull)));
 }
+// tcgen05.ld of 4 columns without the wait (the caller waits once for several)
+__device__ __forceinline__ void oz_tmem_ld4(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
 
-__global__ void __launch_bounds__(TT_THREADS, 1) k_oz_tall(const __grid_constant__ CUtensorMap mapA,
-                                                           TcTall a) {
+// one tile's shape
+struct OzTile {
+  int k, nrow, ni, nc, N;
+  long row0;
+};
+// a warp's 8 rows of the tile: lane (rho, q) loads row 8 w + rho, columns 8 c + 2 q and
+// 8 c + 2 q + 1 (c < KP / 8) with 16-byte loads (8 rows x 64 bytes per instruction)
+__device__ __forceinline__ void oz_load_rows(double2 (&x)[8], const double* A, int lda,
+                                             const OzTile& t, int r, int q, int KP) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int kk = 8 * c + 2 * q;
+    x[c] = make_double2(0.0, 0.0);
+    if (c < KP / 8 && r < t.nrow && kk < t.ni)
+      x[c] = __ldg(reinterpret_cast<const double2*>(A + (t.row0 + r) * lda + kk));
+  }
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int KA, int npass,
+                                                           int nbuf) {
   extern __shared__ uint8_t raw_oz[];
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw_oz) + 1023) &
-                                             ~uintptr_t(1023));
-  const double* st = reinterpret_cast<const double*>(base);
-  uint8_t* asl = base + TT_STAGE;                      // OZ_DIG planes of 128 x 32 (K-major)
-  uint8_t* msl = asl + OZ_DIG * OZ_ASL;                // OZ_DIG planes of 64 x 64
-  __shared__ uint64_t bar_tma, bar_mma;
+  uint8_t* msl = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw_oz) + 127) &
+                                            ~uintptr_t(127));   // OZ_DIG planes DD_MAXC x KP
+  const uint32_t MPL = DD_MAXC * 2 * KP, APL = TT_ROWS * 2 * KA;
+  const uint32_t ABUF = max(OZ_DIG * APL, (uint32_t)OZ_EPI);
+  uint8_t* asl0 = msl + OZ_DIG * MPL;                          // nbuf x (OZ_DIG planes 128 x KA)
+  __shared__ uint64_t bar_mma;
   __shared__ uint32_t tmem_s;
-  __shared__ int cmax[DD_MAXC], rexp[TT_ROWS], fexp[DD_MAXC];
+  __shared__ int mexp[DD_MAXC], fexp[DD_MAXC], rexp[2][TT_ROWS], red[8][DD_MAXC];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int RC = a.g.RC;
-  const long ntot = (long)a.g.nsub * a.tps;
-  const long f0 = blockIdx.x * ntot / gridDim.x, f1 = (blockIdx.x + 1) * ntot / gridDim.x;
+  const bool worker = warp < OZ_WARPS;
+  const int RC = a.g.RC, tps = a.tps;
+  const int ntot = a.g.nsub * tps;
+  const int f0 = (int)((long)blockIdx.x * ntot / gridDim.x);
+  const int f1 = (int)((long)(blockIdx.x + 1) * ntot / gridDim.x);
   auto rows_of = [&](int k) { return a.spatial ? a.g.N[k] : a.g.n; };
-  auto valid = [&](long f) { return (int)(f % a.tps) * TT_ROWS < rows_of((int)(f / a.tps)); };
-  auto next_valid = [&](long f) {
-    while (f < f1 && !valid(f)) ++f;
+  auto next_valid = [&](int f) {
+    while (f < f1 && (f % tps) * TT_ROWS >= rows_of(f / tps)) ++f;
     return f;
   };
-  auto row0 = [&](long f) {
-    const int k = (int)(f / a.tps);
-    return (a.spatial ? (long)a.g.rowoff[k] : (long)k * a.g.n) + (long)(f % a.tps) * TT_ROWS;
+  auto shape = [&](int f) {
+    OzTile t;
+    t.k = f / tps;
+    const int r0 = (f - t.k * tps) * TT_ROWS;
+    t.nrow = min(TT_ROWS, rows_of(t.k) - r0);
+    t.row0 = (a.spatial ? (long)a.g.rowoff[t.k] : (long)t.k * a.g.n) + r0;
+    t.ni = a.ninner ? a.ninner[t.k] : a.ninner_fix;
+    t.nc = a.ncols ? a.ncols[t.k] : a.ncols_fix;
+    t.N = t.nc <= 16 ? 16 : (t.nc + 15) / 16 * 16;
+    return t;
   };
-  long f = next_valid(f0);
+  int f = next_valid(f0);
   if (f >= f1) return;
   if (tid == 0) {
-    tc::mbar_init(&bar_tma, 1);
     tc::mbar_init(&bar_mma, 1);
     tc::mbar_init_fence();
   }
@@ -585,140 +655,217 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_oz_tall(const __grid_constant
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_s;
-  const uint32_t box_bytes = (uint32_t)TT_ROWS * a.lda * 8;
-  if (tid == 0) {
-    tc::mbar_arrive_expect_tx(&bar_tma, box_bytes);
-    tc::tma_load_2d(base, &mapA, 0, (int)row0(f), &bar_tma);
-  }
   bool alive = true;
-  int it = 0, nmma = 0;
-  for (; f < f1 && alive; f = next_valid(f + 1), ++it) {
-    const long fn = next_valid(f + 1);
-    const int k = (int)(f / a.tps), rows = rows_of(k);
-    const int r0 = (int)(f % a.tps) * TT_ROWS, nrow = min(TT_ROWS, rows - r0);
-    const int ni = a.ninner ? a.ninner[k] : a.ninner_fix;
-    const int nc = a.ncols ? a.ncols[k] : a.ncols_fix;
-    const int N = nc <= 16 ? 16 : (nc + 15) / 16 * 16;
-    count_work(a.g, KS_OZ_TALL, 2.0 * nrow * ni * nc);
-    const double* Mk = a.bsmall >= 0 ? a.smbase + ((long)k * NSMALL + a.bsmall) * RC * RC
-                                     : a.Bm + (long)k * RC * RC;
-    if (tid < DD_MAXC) cmax[tid] = 0;
-    const bool got = tc::mbar_wait(&bar_tma, it & 1, kWait);
-    __syncthreads();
-    // column exponents of the tile: c_k = max_r E(A[r][k]) - 1022
-    for (int e = tid; e < TT_ROWS * DD_MAXC; e += TT_THREADS) {
-      const int kk = e & (DD_MAXC - 1), r = e >> 6;
-      if (kk < ni && r < nrow) atomicMax(&cmax[kk], f64_bexp(st[r * a.lda + kk]));
-    }
-    __syncthreads();
-    // row exponents of A 2^-c: e_r = max_k (E(A[r][k]) - c_k) - 1022 (2 threads per row)
-    {
-      const int r = tid >> 1, h = tid & 1;
-      int mx = -100000;
-      if (r < nrow)
-        for (int kk = h; kk < ni; kk += 2) {
-          const int E = f64_bexp(st[r * a.lda + kk]);
-          if (E) mx = max(mx, E - (cmax[kk] - 1022));
-        }
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-      if (h == 0) rexp[r] = mx - 1022;
-    }
-    // column exponents of 2^c M: f_n = max_k (E(M[k][n]) + c_k) - 1022
-    if (tid < DD_MAXC) {
-      int mx = -100000;
-      if (tid < nc)
-        for (int kk = 0; kk < ni; ++kk) {
-          const int E = f64_bexp(Mk[kk * RC + tid]);
-          if (E && cmax[kk]) mx = max(mx, E + (cmax[kk] - 1022));
-        }
-      fexp[tid] = mx - 1022;
-    }
-    __syncthreads();
-    // digit planes of (2^c M)^T: element (n, k) relative to 2^(f_n - c_k) (the N rows and
-    // K halves the products read)
-    const int kw = ni > 32 ? 64 : 32;
-    for (int e = tid; e < N * kw; e += TT_THREADS) {
-      const int n = e / kw, kk = e - n * kw;
-      uint16_t d[OZ_DIG];
-      const long long T = (n < nc && kk < ni && cmax[kk])
-                              ? oz_fixed(Mk[kk * RC + n], fexp[n] - (cmax[kk] - 1022)) : 0;
-      oz_digits(T, d);
-      const uint32_t off = tc::op_off(n, kk * 2, 128);
+  int nmma = 0, ncommit = 0, kcur = -1, buf = 0;
+  bool pending = false;                                 // a tile's MMAs issued, epilogue not done
+  OzTile prev{};
+  int prevbuf = 0;
+
+  // epilogue of tile t (its MMAs complete), planes buffer b as scratch; worker warp w: TMEM
+  // lanes 32 (w % 4) .., 4-column groups w / 4, w / 4 + 4, ...
+  auto epilogue = [&](const OzTile& t, int b) {
+    const int q4 = warp & 3, m = q4 * 32 + lane;
+    const int er = rexp[b][m];
+    double* ebuf = reinterpret_cast<double*>(asl0 + (size_t)b * ABUF) + warp * (32 * 5);
+    double* ybase = a.Y + t.row0 * a.ldy;
+    for (int c0 = (warp >> 2) * 4; c0 < t.N; c0 += 16) {
+      uint32_t D[OZ_DIG][4];
 #pragma unroll
-      for (int s2 = 0; s2 < OZ_DIG; ++s2) *reinterpret_cast<uint16_t*>(msl + s2 * OZ_MSL + off) = d[s2];
-    }
-    const int nh = ni > 32 ? 2 : 1;
-    for (int h = 0; h < nh; ++h) {
-      if (h > 0) alive = tc::mbar_wait(&bar_mma, nmma++ & 1, kWait) && alive;   // planes free
-      // digit planes of the tile's columns 32 h .. 32 h + 31: element (r, k) of A 2^-c
-      // relative to 2^(e_r + c_k)
-      for (int e = tid; e < TT_ROWS * 32; e += TT_THREADS) {
-        const int r = e >> 5, kk = 32 * h + (e & 31);
-        uint16_t d[OZ_DIG];
-        const long long T = (got && r < nrow && kk < ni && cmax[kk])
-                                ? oz_fixed(st[r * a.lda + kk], rexp[r] + (cmax[kk] - 1022)) : 0;
-        oz_digits(T, d);
-        const uint32_t off = tc::op_off(r, (e & 31) * 2, 64);
+      for (int g = 0; g < OZ_DIG; ++g)
+        oz_tmem_ld4(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * t.N + c0), D[g]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int s2 = 0; s2 < OZ_DIG; ++s2) *reinterpret_cast<uint16_t*>(asl + s2 * OZ_ASL + off) = d[s2];
+      for (int g = 0; g < OZ_DIG; ++g)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) asm volatile("" : "+r"(D[g][j]));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = c0 + j;
+        double v = 0.0;
+        if (c < t.nc && m < t.nrow && alive) {
+          long long J = 0;
+#pragma unroll
+          for (int g = 0; g < OZ_DIG - 1; ++g)
+            J += (long long)__float2int_rn(__uint_as_float(D[g][j])) << (40 - 8 * g);
+          J += (long long)(__float2int_rn(__uint_as_float(D[OZ_DIG - 1][j])) >> 8);
+          v = oz_to_f64(J, er + fexp[c] - 56);
+        }
+        ebuf[lane * 5 + j] = v;
       }
-      tc::fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after_sync();
-        if (h == nh - 1 && fn < f1) {                  // the stage is no longer read
-          tc::mbar_arrive_expect_tx(&bar_tma, box_bytes);
-          tc::tma_load_2d(base, &mapA, 0, (int)row0(fn), &bar_tma);
-        }
-        const uint32_t id = tc::idesc(tc::FMT_BF16, 128, N);
-        const uint32_t sa = tc::smem_u32(asl), sb = tc::smem_u32(msl);
-        for (int g = 0; g < OZ_DIG; ++g)
-          for (int s1 = 0; s1 <= g; ++s1)
+      __syncwarp();
+      const int cc = c0 + (lane & 3);
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              const uint64_t ad = tc::sdesc(sa + s1 * OZ_ASL + 256 * j, 128, 512);
-              const uint64_t bd = tc::sdesc(sb + (g - s1) * OZ_MSL + 256 * (2 * h + j), 128, 1024);
-              tc::mma_bf16(tmem + (uint32_t)(g * 64), ad, bd, id,
-                           (h > 0 || s1 > 0 || j > 0) ? 1u : 0u);
-            }
-        tc::mma_commit(&bar_mma);
+      for (int i = 0; i < 4; ++i) {
+        const int rl = 8 * i + (lane >> 2), rr = q4 * 32 + rl;
+        if (rr < t.nrow && cc < a.ldy) ybase[(long)rr * a.ldy + cc] = ebuf[rl * 5 + (lane & 3)];
       }
       __syncwarp();
     }
-    alive = tc::mbar_wait(&bar_mma, nmma++ & 1, kWait) && alive && got;
-    tc::fence_after_sync();
-    // epilogue: row m of the tile, the 16-column groups of parity w / 4
-    const int m = (warp & 3) * 32 + lane, r = r0 + m;
-    double* y = a.Y + (row0(f) + m) * a.ldy;
-    const int er = m < nrow ? rexp[m] : 0;
-    for (int c0 = (warp >> 2) * 16; c0 < N; c0 += 32) {
-      float D[OZ_DIG][16];
-#pragma unroll
-      for (int g = 0; g < OZ_DIG; ++g)
-        tc::tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(g * 64 + c0), D[g]);
-      if (r < rows) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int c = c0 + j;
-          if (c < nc) {
-            long long J = 0;
-#pragma unroll
-            for (int g = 0; g < OZ_DIG - 1; ++g) J += (long long)__float2int_rn(D[g][j]) << (40 - 8 * g);
-            J += (long long)(__float2int_rn(D[OZ_DIG - 1][j]) >> 8);
-            y[c] = oz_to_f64(J, er + fexp[c] - 56);
-          } else if (c < a.ldy) {
-            y[c] = 0.0;
-          }
-        }
+    if (warp < 4 && a.ldy > t.N)                        // columns N .. ldy - 1
+      for (int e = lane; e < 32 * (a.ldy - t.N); e += 32) {
+        const int rr = q4 * 32 + e / (a.ldy - t.N), c = t.N + e % (a.ldy - t.N);
+        if (rr < t.nrow) ybase[(long)rr * a.ldy + c] = 0.0;
       }
-    }
-    if (r < rows && warp < 4)
-      for (int c = N; c < a.ldy; ++c) y[c] = 0.0;
+  };
+  auto finish_prev = [&]() {                            // wait for prev's MMAs, its epilogue
+    alive = tc::mbar_wait(&bar_mma, nmma++ & 1, kWait) && alive;
+    tc::fence_after_sync();
+    if (worker) epilogue(prev, prevbuf);
     tc::fence_before_sync();
     alive = __syncthreads_and(alive) != 0;
-    if (!alive && tid == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
+    pending = false;
+  };
+  // MMAs of tile t, K range k0 .. k0 + KA - 1 of its planes in buffer b.  M's planes are
+  // stacked along N (plane u = rows u N .. u N + N - 1) and accumulator g sits at TMEM
+  // columns g N .., so one MMA of A's plane s with planes u0 .. u0 + nu - 1 adds the pairs
+  // (s, u) into accumulators s + u0 .. s + u0 + nu - 1: at most 256 / N planes an MMA
+  auto issue = [&](const OzTile& t, int b, int k0, int acc0) {
+    tc::fence_after_sync();
+    const int ns = max(k0 == 0 ? 1 : 0, (min(t.ni, k0 + KA) - k0 + 15) >> 4);
+    const int nper = 256 / t.N;
+    const uint32_t MPLt = (uint32_t)t.N * 2 * KP;
+    const uint64_t ad0 = tc::sdesc(tc::smem_u32(asl0 + (size_t)b * ABUF), 128, 16 * KA);
+    const uint64_t bd0 = tc::sdesc(tc::smem_u32(msl) + 256 * (k0 / 16), 128, 16 * KP);
+    for (int j = 0; j < ns; ++j)
+      for (int s1 = 0; s1 < OZ_DIG; ++s1)
+        for (int u0 = 0; u0 < OZ_DIG - s1; u0 += nper) {
+          const int nu = min(nper, OZ_DIG - s1 - u0);
+          tc::mma_bf16(tmem + (uint32_t)((s1 + u0) * t.N), ad0 + ((s1 * APL + 256 * j) >> 4),
+                       bd0 + ((u0 * MPLt + 256 * j) >> 4), tc::idesc(tc::FMT_BF16, 128, nu * t.N),
+                       (acc0 || j > 0 || s1 > 0) ? 1u : 0u);
+        }
+    tc::mma_commit(&bar_mma);
+  };
+
+  const int rho = lane & 7, q = lane >> 3, r = 8 * warp + rho;
+  double2 x[8];                                          // the warp's rows of the tile
+  OzTile t = shape(f);
+  if (worker) oz_load_rows(x, a.A, a.lda, t, r, q, KP);
+  while (alive) {
+    count_work(a.g, KS_OZ_TALL, 2.0 * t.nrow * t.ni * t.nc);
+    if (t.k != kcur) {
+      if (pending) finish_prev();                       // its MMAs read the old M planes
+      if (!alive) break;
+      // ---- M's digit planes, once per subdomain: M staged as FP64 [kk][DD_MAXC] in the
+      // (free) first planes buffer by coalesced loads, then bounds and digits from there
+      kcur = t.k;
+      const double* Mk = a.bsmall >= 0 ? a.smbase + ((long)t.k * NSMALL + a.bsmall) * RC * RC
+                                       : a.Bm + (long)t.k * RC * RC;
+      double* Ms = reinterpret_cast<double*>(asl0);
+#pragma unroll
+      for (int i = 0; i < DD_MAXC * DD_MAXC / OZ_WORKERS; ++i) {
+        const int e = tid + OZ_WORKERS * i, kk = e >> 6, n = e & (DD_MAXC - 1);
+        if (worker && kk < KP) Ms[e] = (kk < t.ni && n < t.nc) ? __ldg(Mk + (long)kk * RC + n) : 0.0;
+      }
+      __syncthreads();
+      for (int kk = worker ? warp : KP; kk < KP; kk += OZ_WARPS) {   // mu_k: warp per row
+        int mx = OZ_NONE;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int E = f64_bexp(Ms[kk * DD_MAXC + lane + 32 * h]);
+          if (E) mx = max(mx, E - 1022);
+        }
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) mexp[kk] = mx;
+      }
+      __syncthreads();
+      if (worker) {                                     // f_n: 8 threads per column
+        const int n = tid & (DD_MAXC - 1), q = tid >> 6;
+        int mx = OZ_NONE;
+        for (int kk = q; kk < t.ni; kk += 8) {
+          const int E = f64_bexp(Ms[kk * DD_MAXC + n]);
+          if (E) mx = max(mx, E - 1022 - mexp[kk]);
+        }
+        red[q][n] = mx;
+      }
+      __syncthreads();
+      if (tid < DD_MAXC) {
+        int mx = red[0][tid];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) mx = max(mx, red[q][tid]);
+        fexp[tid] = mx;
+      }
+      __syncthreads();
+      // digits of M'[kk][n] relative to 2^f_n, two adjacent kk per thread; plane u holds
+      // rows u N + n
+      const uint32_t MPLt = (uint32_t)t.N * 2 * KP;
+      for (int e = worker ? tid : t.N * (KP / 2); e < t.N * (KP / 2); e += OZ_WORKERS) {
+        const int n = e / (KP / 2), kk = 2 * (e - n * (KP / 2));
+        const double m0 = Ms[kk * DD_MAXC + n], m1 = Ms[(kk + 1) * DD_MAXC + n];
+        float d0[OZ_DIG], d1[OZ_DIG];
+        oz_digits(m0, fexp[n] + mexp[kk], d0);
+        oz_digits(m1, fexp[n] + mexp[kk + 1], d1);
+        const uint32_t off = tc::op_off(n, kk * 2, 2 * KP);
+#pragma unroll
+        for (int u = 0; u < OZ_DIG; ++u)
+          *reinterpret_cast<uint32_t*>(msl + u * MPLt + off) = oz_pack(d0[u], d1[u]);
+      }
+      __syncthreads();
+    }
+    // ---- the tile's rows (loaded during the previous tile): row bounds, digit planes
+    if (pending && nbuf == 1) {                         // one buffer: prev's planes, rexp
+      finish_prev();
+      if (!alive) break;
+    }
+    int mx = OZ_NONE;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int kk = 8 * c + 2 * q;
+      if (worker && c < KP / 8 && kk < t.ni) {
+        const int E0 = f64_bexp(x[c].x), E1 = f64_bexp(x[c].y);
+        if (E0 && mexp[kk] != OZ_NONE) mx = max(mx, E0 - 1022 + mexp[kk]);
+        if (E1 && kk + 1 < t.ni && mexp[kk + 1] != OZ_NONE) mx = max(mx, E1 - 1022 + mexp[kk + 1]);
+      }
+    }
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+    if (worker && q == 0) rexp[buf][r] = mx;
+    const int fn = next_valid(f + 1);
+    const OzTile tn = fn < f1 ? shape(fn) : t;
+    for (int p = 0; p < npass; ++p) {
+      const int k0 = p * KA;
+      if (p > 0)                                        // one buffer: the previous pass is read
+        alive = tc::mbar_wait(&bar_mma, nmma++ & 1, kWait) && alive;
+      uint8_t* asl = asl0 + (size_t)buf * ABUF;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int kk = 8 * c + 2 * q;
+        if (worker && c < KP / 8 && kk >= k0 && kk < k0 + KA) {
+          // entries past ni, or whose row of M is zero, are zero (their digits too)
+          const double x0 = (kk < t.ni && mexp[kk] != OZ_NONE) ? x[c].x : 0.0;
+          const double x1 = (kk + 1 < t.ni && mexp[kk + 1] != OZ_NONE) ? x[c].y : 0.0;
+          float d0[OZ_DIG], d1[OZ_DIG];
+          oz_digits(x0, mx - mexp[kk], d0);
+          oz_digits(x1, mx - mexp[min(kk + 1, DD_MAXC - 1)], d1);
+          const uint32_t off = tc::op_off(r, (kk - k0) * 2, 2 * KA);
+#pragma unroll
+          for (int s = 0; s < OZ_DIG; ++s)
+            *reinterpret_cast<uint32_t*>(asl + s * APL + off) = oz_pack(d0[s], d1[s]);
+        }
+      }
+      if (worker && p == npass - 1 && fn < f1) oz_load_rows(x, a.A, a.lda, tn, r, q, KP);
+      tc::fence_async_smem();
+      alive = __syncthreads_and(alive) != 0;
+      if (alive && p == 0 && pending) finish_prev();    // two buffers: overlapped with the MMAs
+      if (!alive) break;
+      if (tid == OZ_WORKERS) issue(t, buf, k0, p > 0);   // the issuing warp
+      ++ncommit;
+      __syncwarp();
+    }
+    if (!alive) break;
+    pending = true;
+    prev = t;
+    prevbuf = buf;
+    buf = (buf + 1) % nbuf;
+    if (fn >= f1) break;
+    f = fn;
+    t = tn;
   }
-  if (!alive && tid == 0 && f < f1) tc::mbar_wait(&bar_tma, it & 1, kWait);   // load in flight
+  if (pending && alive) finish_prev();
+  if (!alive) {
+    if (tid == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
+    if (ncommit > 0) tc::mbar_wait(&bar_mma, (ncommit - 1) & 1, kWait);   // MMAs in flight
+  }
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
@@ -747,7 +894,7 @@ cudaError_t tc_init() {
                            (int)tc_gram_smem());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_oz_tall, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)oz_tall_smem());
+                           (int)OZ_SMEM_LIMIT);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_tc_gram<tc::FMT_BF16>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_gram_smem());
@@ -779,18 +926,19 @@ bool tc_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, c
 bool oz_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
              int lda, const int* ninner, int ninner_fix, const double* Bm, int bsmall,
              const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy) {
-  const long rows_all = spatial ? P.Ntot : (long)P.g.nsub * P.g.n;
-  CUtensorMap map;
-  if (!make_map(&map, A, lda, rows_all, TT_ROWS)) return false;
+  if (lda > DD_MAXC || (lda & 1)) return false;
+  const OzPlan pl = oz_plan(lda, OZ_SMEM_LIMIT);
+  if (pl.total > OZ_SMEM_LIMIT) return false;
   TcTall a;
   a.g = P.g; a.spatial = spatial; a.lda = lda; a.ninner = ninner; a.ninner_fix = ninner_fix;
   a.Bm = Bm; a.bsmall = bsmall; a.smbase = smbase; a.ncols = ncols; a.ncols_fix = ncols_fix;
   a.Y = Y; a.ldy = ldy; a.alpha = 1.0; a.accumulate = 0; a.status = status;
+  a.A = A;
   a.tps = ((spatial ? P.maxN : P.g.n) + TT_ROWS - 1) / TT_ROWS;
   const long ntot = (long)P.g.nsub * a.tps;
   const int grid = (int)std::min<long>(ntot, P.nsm);
   pbeg(st, KS_OZ_TALL);
-  k_oz_tall<<<grid, TT_THREADS, oz_tall_smem(), st>>>(map, a);
+  k_oz_tall<<<grid, OZ_THREADS, pl.total, st>>>(a, pl.KP, pl.KA, pl.npass, pl.nbuf);
   pend(st);
   return true;
 }
