@@ -156,22 +156,31 @@ def fp64_gemm_peak(torch):
 FP64_SLOTS = ["k_tall", "k_gram", "k_ang_coeffs", "k_sp_coeffs", "k_kstep_adv", "k_lstep_adv",
               "k_coll_kstep", "k_coll_lstep"]
 TC_SLOTS = ["k_tc_tall", "k_tc_gram"]
+OZ_SLOTS = ["k_oz_tall"]          # FP64-accurate products on the BF16 tensor cores (Ozaki)
+OZ_PAIRS = 28                     # digit-pair products per FP64 product (7 digits, order <= 6)
 LATENCY = ["k_geig", "k_geig(aug)", "k_trunc", "k_small_adv1", "k_chol_inv", "k_sstep_adv",
            "k_coll_small", "k_kc_w", "k_kc_sel", "k_kc_apply", "k_complete", "k_reduce"]
 
 
-def per_kernel_roofline(prof, nsteps, fp64_peak, fp32_peak, tc_peak):
+def per_kernel_roofline(prof, nsteps, fp64_peak, fp32_peak, tc_peak, bf16_peak=None):
     """Achieved rate and fraction of each counting kernel class: the FP64 classes against
     the FP64 peak (FP32 when the form computes the class in FP32), the tensor-core classes
     against the tensor peak of their type (their three partial products counted, since the
     split is what runs); the latency classes by time."""
     out = {}
-    for slot in FP64_SLOTS + TC_SLOTS:
+    for slot in FP64_SLOTS + TC_SLOTS + OZ_SLOTS:
         if slot not in prof or prof[slot][2] <= 0:
             continue
         ms, cnt, fl = prof[slot]
         ach = fl / (ms / 1e3) / 1e12
-        if slot in TC_SLOTS:
+        if slot in OZ_SLOTS:
+            out[slot] = {"ms_per_step": round(ms / nsteps, 4), "launches_per_step": cnt / nsteps,
+                         "bound": "alu (integer/FP32 issue: digit conversion and recombination)",
+                         "achieved_fp64_equivalent_tflops": ach,
+                         "frac_of_fp64": ach / fp64_peak,
+                         "achieved_bf16_tflops_28_pair_products": OZ_PAIRS * ach,
+                         "frac_of_bf16_peak": OZ_PAIRS * ach / bf16_peak if bf16_peak else None}
+        elif slot in TC_SLOTS:
             out[slot] = {"ms_per_step": round(ms / nsteps, 4), "launches_per_step": cnt / nsteps,
                          "bound": "tensor", "achieved_tflops_3products": 3 * ach,
                          "frac_of_tensor_peak": 3 * ach / tc_peak}
@@ -227,8 +236,11 @@ def run_ours(args, torch):
     sptr = stream.cuda_stream
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    # ---- timed: the headline workload, FP64, graph-replayed steps ------------------------
-    s = binding.Solver(wl, stream=sptr, use_graph=True)
+    # ---- timed: the headline workload, FP64, graph-replayed steps, the launch choices
+    # (tall-product engine per row family, Gram chunk counts) picked by the autotuner -------
+    OPT = {"products": "auto", "autotune": True}
+    s = binding.Solver(wl, stream=sptr, use_graph=True, **OPT)
+    tuning, tune_ms = s.tuning()
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -247,19 +259,28 @@ def run_ours(args, torch):
     gold = np.load(os.path.join(GOLD, "lognormal_512_prefix20.npz"))
     g_steps = int(gold["nsteps"])
 
-    def prefix_err(prec):
-        sv = binding.Solver(wl, stream=sptr, use_graph=True, precision=prec)
+    def prefix_err(prec, **opt):
+        sv = binding.Solver(wl, stream=sptr, use_graph=True, precision=prec, **opt)
         sv.step(g_steps)
         rho = sv.scalar_flux()
         sv.close()
         return rel(rho[gold["idx"]], gold["rho"]), rho
 
-    err64, rho64 = prefix_err("fp64")
+    err64, rho64 = prefix_err("fp64", **OPT)
+
+    # ---- the same with the FP64 CUDA-core products throughout (no tensor cores) ------------
+    sv = binding.Solver(wl, stream=sptr, use_graph=True, products="fp64")
+    t_cc = timed_steps(sv, args.steps, args.warmup, flush, stream, torch)
+    sv.close()
+    err_cc, _ = prefix_err("fp64", products="fp64")
+    cuda_core = {"ms_per_step": t_cc / args.steps * 1e3, "value": units * args.steps * ws / t_cc,
+                 "unit": UNIT, "flux_rel_l2_vs_oracle_%dsteps" % g_steps: err_cc,
+                 "speedup_of_headline": t_cc / t_ours}
 
     # ---- end to end through the public API with host buffers -------------------------------
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s3 = binding.Solver(wl, stream=sptr, use_graph=True)
+    s3 = binding.Solver(wl, stream=sptr, use_graph=True, **OPT)
     for _ in range(args.steps):
         s3.step(1)
         s3.scalar_flux()                 # device -> host read of the step's result
@@ -269,21 +290,29 @@ def run_ours(args, torch):
     h2d = 8 * (4 * wl.ncells + 3 * wl.n) + 4 * (len(wl.xcuts) + len(wl.ycuts))
     e2e = {"value": units * args.steps * ws / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 8 * wl.ncells,
-           "note": "create (problem data from host memory) + per step: step + scalar flux "
-                   "to host + destroy, wall clock"}
+           "note": "create (problem data from host memory; the autotuner's choices cached "
+                   "from the first solver of this shape) + per step: step + scalar flux to "
+                   "host + destroy, wall clock"}
 
     # ---- roofline ------------------------------------------------------------------------
     peaks = measured_peaks()
     fp64_peak = fp64_gemm_peak(torch)
     bf16_peak = peaks.get("bf16_tflops") or 1900.0
-    kernels = per_kernel_roofline(prof, 2, fp64_peak, None, bf16_peak / 2.0)
+    kernels = per_kernel_roofline(prof, 2, fp64_peak, None, bf16_peak / 2.0, bf16_peak)
     total = sum(v[0] for v in prof.values())
     top = max(prof.items(), key=lambda kv: kv[1][0])
     roof = {"kernel": top[0], "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak,
             "peak_source": "cuBLAS FP64 GEMM 8192^3 measured in this run (of measured)",
             "share_of_step": top[1][0] / total, "launch_ms": top[1][0] / top[1][1],
             "launches_per_step": top[1][1] / 2.0, "traffic": NCU_TRAFFIC.get(top[0])}
-    if top[1][2] > 0:
+    if top[0] in OZ_SLOTS and top[1][2] > 0:
+        ach = top[1][2] / (top[1][0] / 1e3) / 1e12
+        roof.update({"achieved": ach, "frac": ach / fp64_peak,
+                     "note": "FP64-accurate products on the BF16 tensor cores: achieved is the "
+                             "FP64 work per second, against the FP64 roofline",
+                     "work_flops_per_launch": top[1][2] / top[1][1],
+                     "work_source": "counted by the kernels (dd_dlra_profile_work)"})
+    elif top[1][2] > 0:
         ach = top[1][2] / (top[1][0] / 1e3) / 1e12
         roof.update({"achieved": ach, "frac": ach / fp64_peak,
                      "work_flops_per_launch": top[1][2] / top[1][1],
@@ -298,11 +327,11 @@ def run_ours(args, torch):
     forms = {}
     if not args.no_mixed:
         for prec in ("tf32", "bf16", "mixed"):
-            sv = binding.Solver(wl, stream=sptr, use_graph=True, precision=prec)
+            sv = binding.Solver(wl, stream=sptr, use_graph=True, precision=prec, **OPT)
             t_p = timed_steps(sv, args.steps, args.warmup, flush, stream, torch)
             pp = sv.profile(1, work=True)
             sv.close()
-            e_or, rho_p = prefix_err(prec)
+            e_or, rho_p = prefix_err(prec, **OPT)
             forms[prec] = {"value": units * args.steps * ws / t_p, "unit": UNIT,
                            "ms_per_step": t_p / args.steps * 1e3, "speedup_vs_fp64": t_ours / t_p,
                            "flux_rel_l2_vs_oracle_%dsteps" % g_steps: e_or,
@@ -310,11 +339,14 @@ def run_ours(args, torch):
                            "kernels_ms_per_step": {k: round(v[0], 4) for k, v in
                                                    sorted(pp.items(), key=lambda kv: -kv[1][0])[:8]},
                            "kernels": per_kernel_roofline(pp, 1, fp64_peak, None,
-                                                          bf16_peak / (2.0 if prec == "tf32" else 1.0))}
+                                                          bf16_peak / (2.0 if prec == "tf32" else 1.0),
+                                                          bf16_peak)}
         forms["note"] = ("tf32/bf16: Galerkin contractions as tcgen05 MMAs (operands split "
                          "hi + lo, FP32 accumulation), FP32 increments; mixed: FP32 "
                          "increments only; orthonormalisations, QR R factors, SVDs, eigen-"
-                         "splits and the K-step FP64 in every form")
+                         "splits and the K-step FP64-accurate in every form (the tall "
+                         "products of the orthonormalisations on the Ozaki kernel where the "
+                         "autotuner picks it)")
 
     # ---- the point source: oracle, one-subdomain DLRA, full-rank S_N ---------------------
     point = None
@@ -389,7 +421,10 @@ def run_ours(args, torch):
                    "integrator": wl.integrator, "dt": wl.dt, "parallelism": f"replicas{ws}",
                    "l2": "flushed between timed steps (256 MiB write, outside the step events); "
                          "the factors alone (~250 MB) exceed L2",
-                   "launch": "one CUDA graph per step"},
+                   "launch": "one CUDA graph per step",
+                   "options": "products=auto, autotune=1 (the choices in 'tuning')"},
+        "tuning": {"choices": tuning, "trial_ms": tune_ms},
+        "fp64_cuda_core_products": cuda_core,
         "flux_rel_l2_vs_oracle_%dsteps" % g_steps: err64,
         "ranks": {"stored_max": int(np.max(st_r)), "intermediate_max": int(np.max(it_r))},
         "e2e": e2e,
