@@ -500,7 +500,8 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_tc_gram(const __grid_constant
 // 28 x (K / 16) MMAs.  The planes are double-buffered: tile i's MMAs run while the warps
 // convert tile i + 1, and tile i's epilogue (TMEM -> registers -> FP64 -> a per-warp
 // transposition buffer -> whole-row stores) follows.  When two buffers of a whole row's
-// planes do not fit beside M's (lda > 48), K runs in two passes of 32 on one buffer.
+// planes do not fit beside M's (lda > 48), K runs in two passes of 32: the stages (one pass
+// of one tile each) alternate between the two buffers all the same.
 #define OZ_DIG 7
 #define OZ_WORKERS 512                       // 16 warps: loads, digits, epilogue
 #define OZ_THREADS (OZ_WORKERS + 32)         // + one warp that issues the MMAs
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_tc_gram(const __grid_constant
 #define OZ_SMEM_LIMIT (227 * 1024 - 4096)    // dynamic shared memory (the static part is < 4 KiB)
 
 struct OzPlan {
-  int KP, KA, npass, nbuf;                   // K extent of M's planes, of a pass; passes; buffers
+  int KP, KA, npass, nbuf;                   // K extent of M's planes, of a pass; passes; buffers (2)
   size_t mpl, apl, abuf, total;              // bytes: one M plane, one A plane, one A buffer, all
 };
 // the shared-memory plan for inner dimensions up to lda (even, <= 64)
@@ -520,7 +521,7 @@ OzPlan oz_plan(int lda, size_t limit) {
   p.mpl = (size_t)DD_MAXC * 2 * p.KP;
   for (int mode = 0; mode < 2; ++mode) {
     p.KA = mode ? 32 : p.KP;
-    p.nbuf = mode ? 1 : 2;
+    p.nbuf = 2;
     p.npass = (p.KP + p.KA - 1) / p.KA;
     p.apl = (size_t)TT_ROWS * 2 * p.KA;
     p.abuf = std::max((size_t)OZ_DIG * p.apl, (size_t)OZ_EPI);
@@ -618,8 +619,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
                                             ~uintptr_t(127));   // OZ_DIG planes DD_MAXC x KP
   const uint32_t MPL = DD_MAXC * 2 * KP, APL = TT_ROWS * 2 * KA;
   const uint32_t ABUF = max(OZ_DIG * APL, (uint32_t)OZ_EPI);
-  uint8_t* asl0 = msl + OZ_DIG * MPL;                          // nbuf x (OZ_DIG planes 128 x KA)
-  __shared__ uint64_t bar_mma;
+  uint8_t* asl0 = msl + OZ_DIG * MPL;                          // 2 x (OZ_DIG planes 128 x KA)
+  __shared__ uint64_t bar_mma[2];                              // MMAs of the stages in buffer 0 / 1
   __shared__ uint32_t tmem_s;
   __shared__ int mexp[DD_MAXC], fexp[DD_MAXC], rexp[2][TT_ROWS], red[8][DD_MAXC];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -647,7 +648,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
   int f = next_valid(f0);
   if (f >= f1) return;
   if (tid == 0) {
-    tc::mbar_init(&bar_mma, 1);
+    tc::mbar_init(&bar_mma[0], 1);
+    tc::mbar_init(&bar_mma[1], 1);
     tc::mbar_init_fence();
   }
   if (warp == 0) tc::tmem_alloc(&tmem_s, 512);          // OZ_DIG accumulators of 64 columns
@@ -656,16 +658,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
   tc::fence_after_sync();
   const uint32_t tmem = tmem_s;
   bool alive = true;
-  int nmma = 0, ncommit = 0, kcur = -1, buf = 0;
+  // A stage is one pass of one tile: its digit planes go to buffer (stage & 1) and its MMAs
+  // commit to that buffer's barrier, completing that barrier's phase (stage >> 1).
+  int ns = 0, kcur = -1, tb = 0, prev_tb = 0;           // stages issued, tile parity (rexp)
   bool pending = false;                                 // a tile's MMAs issued, epilogue not done
   OzTile prev{};
-  int prevbuf = 0;
+  auto wait_stage = [&](int j) {
+    alive = tc::mbar_wait(&bar_mma[j & 1], (j >> 1) & 1, kWait) && alive;
+  };
 
-  // epilogue of tile t (its MMAs complete), planes buffer b as scratch; worker warp w: TMEM
-  // lanes 32 (w % 4) .., 4-column groups w / 4, w / 4 + 4, ...
-  auto epilogue = [&](const OzTile& t, int b) {
+  // epilogue of tile t (its MMAs complete; row bounds rexp[rb]), planes buffer b as scratch;
+  // worker warp w: TMEM lanes 32 (w % 4) .., 4-column groups w / 4, w / 4 + 4, ...
+  auto epilogue = [&](const OzTile& t, int rb, int b) {
     const int q4 = warp & 3, m = q4 * 32 + lane;
-    const int er = rexp[b][m];
+    const int er = rexp[rb][m];
     double* ebuf = reinterpret_cast<double*>(asl0 + (size_t)b * ABUF) + warp * (32 * 5);
     double* ybase = a.Y + t.row0 * a.ldy;
     for (int c0 = (warp >> 2) * 4; c0 < t.N; c0 += 16) {
@@ -707,10 +713,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
         if (rr < t.nrow) ybase[(long)rr * a.ldy + c] = 0.0;
       }
   };
-  auto finish_prev = [&]() {                            // wait for prev's MMAs, its epilogue
-    alive = tc::mbar_wait(&bar_mma, nmma++ & 1, kWait) && alive;
+  auto finish_prev = [&]() {          // wait for prev's MMAs (its last stage), its epilogue
+    wait_stage(ns - 1);
     tc::fence_after_sync();
-    if (worker) epilogue(prev, prevbuf);
+    if (worker) epilogue(prev, prev_tb, (ns - 1) & 1);
     tc::fence_before_sync();
     alive = __syncthreads_and(alive) != 0;
     pending = false;
@@ -734,7 +740,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
                        bd0 + ((u0 * MPLt + 256 * j) >> 4), tc::idesc(tc::FMT_BF16, 128, nu * t.N),
                        (acc0 || j > 0 || s1 > 0) ? 1u : 0u);
         }
-    tc::mma_commit(&bar_mma);
+    tc::mma_commit(&bar_mma[b]);
   };
 
   const int rho = lane & 7, q = lane >> 3, r = 8 * warp + rho;
@@ -803,10 +809,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
       __syncthreads();
     }
     // ---- the tile's rows (loaded during the previous tile): row bounds, digit planes
-    if (pending && nbuf == 1) {                         // one buffer: prev's planes, rexp
-      finish_prev();
-      if (!alive) break;
-    }
     int mx = OZ_NONE;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -819,13 +821,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
     }
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
-    if (worker && q == 0) rexp[buf][r] = mx;
+    if (worker && q == 0) rexp[tb][r] = mx;
     const int fn = next_valid(f + 1);
     const OzTile tn = fn < f1 ? shape(fn) : t;
     for (int p = 0; p < npass; ++p) {
-      const int k0 = p * KA;
-      if (p > 0)                                        // one buffer: the previous pass is read
-        alive = tc::mbar_wait(&bar_mma, nmma++ & 1, kWait) && alive;
+      const int k0 = p * KA, buf = ns & 1;
+      if (ns >= 2) wait_stage(ns - 2);                  // the buffer's previous stage is read
       uint8_t* asl = asl0 + (size_t)buf * ABUF;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
@@ -846,17 +847,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
       if (worker && p == npass - 1 && fn < f1) oz_load_rows(x, a.A, a.lda, tn, r, q, KP);
       tc::fence_async_smem();
       alive = __syncthreads_and(alive) != 0;
-      if (alive && p == 0 && pending) finish_prev();    // two buffers: overlapped with the MMAs
+      if (alive && p == 0 && pending) finish_prev();    // overlapped with the previous MMAs
       if (!alive) break;
       if (tid == OZ_WORKERS) issue(t, buf, k0, p > 0);   // the issuing warp
-      ++ncommit;
+      ++ns;
       __syncwarp();
     }
     if (!alive) break;
     pending = true;
     prev = t;
-    prevbuf = buf;
-    buf = (buf + 1) % nbuf;
+    prev_tb = tb;
+    tb ^= 1;
     if (fn >= f1) break;
     f = fn;
     t = tn;
@@ -864,7 +865,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
   if (pending && alive) finish_prev();
   if (!alive) {
     if (tid == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
-    if (ncommit > 0) tc::mbar_wait(&bar_mma, (ncommit - 1) & 1, kWait);   // MMAs in flight
+    if (ns > 0) tc::mbar_wait(&bar_mma[(ns - 1) & 1], ((ns - 1) >> 1) & 1, kWait);   // in flight
   }
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 512);

@@ -2,6 +2,7 @@
 summary (scalar-flux statistics, ranks, wall time).
 
     python -m paper_2602_14854_gb300.run --workload pointsource --steps 20 [--graph]
+        [--precision fp64|mixed|tf32|bf16] [--products fp64|tensor|auto] [--autotune]
 """
 from __future__ import annotations
 
@@ -29,7 +30,8 @@ def run_batch(args):
     out = {"workload": f"batch{args.batch}", "groups": []}
     total_units, total_t = 0.0, 0.0
     for n, wls in sorted(groups.items()):
-        s = binding.Solver(wls, use_graph=args.graph, precision=args.precision)
+        s = binding.Solver(wls, use_graph=args.graph, precision=args.precision,
+                           products=args.products, autotune=args.autotune)
         s.step(args.warmup)
         s.sync()
         nsteps = args.steps or 100
@@ -59,7 +61,11 @@ def main(argv=None):
     ap.add_argument("--graph", action="store_true")
     ap.add_argument("--profile", type=int, default=0,
                     help="additionally advance this many steps with per-kernel event timing")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "tf32", "bf16"])
+    ap.add_argument("--products", default="fp64", choices=["fp64", "tensor", "auto"],
+                    help="engine of the FP64 tall products (dd_options.products)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the launch choices when the solver is created")
     ap.add_argument("--batch", type=int, default=0,
                     help="run the batched form on this many seeded problems instead")
     ap.add_argument("--warmup", type=int, default=2)
@@ -70,7 +76,8 @@ def main(argv=None):
         return
     wl = WORKLOADS[args.workload]()
     nsteps = wl.nsteps if args.steps is None else args.steps
-    s = binding.Solver(wl, use_graph=args.graph, precision=args.precision)
+    s = binding.Solver(wl, use_graph=args.graph, precision=args.precision,
+                       products=args.products, autotune=args.autotune)
     t0 = time.perf_counter()
     s.step(nsteps)
     s.sync()
@@ -81,7 +88,8 @@ def main(argv=None):
     out = {"workload": wl.name, "steps": nsteps, "seconds": t,
            "updates_per_s": wl.ncells * wl.n * nsteps / t,
            "rho_sum": float(np.sum(rho)), "rho_max": float(np.max(rho)),
-           "ranks": stored.tolist(), "intermediate": inter.tolist()}
+           "ranks": stored.tolist(), "intermediate": inter.tolist(),
+           "tuning": s.tuning()[0]}
     if prof:
         out["profile_ms"] = {k: [round(v[0], 4), v[1]] for k, v in
                              sorted(prof.items(), key=lambda kv: -kv[1][0])}
