@@ -1115,6 +1115,79 @@ __device__ __forceinline__ void ns_orthogonalize_df(float2* Jd, float2* T, float
 // Shared scratch of jacobi_svd_mixed for leading dimension ld: the FP32 copies of B
 // and J (reused as a double-float temporary afterwards), m norms, and the
 // double-float B and J.
+// One FP64 refinement step of approximate eigenvectors of a symmetric matrix (Ogita and
+// Aishima, 2018): with R = I - V^T V, S = V^T G V, lambda_i = s_ii / (1 - r_ii),
+// V <- V (I + E), e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for separated pairs,
+// r_ij / 2 within clusters and on the diagonal; the error of V maps to about its square.
+// G: m x m, row-major with stride RC; V: V_ij = V[j * RC + i] (refined in place); lam: the
+// refined eigenvalues (not sorted).  S and R are symmetric (upper triangles computed,
+// mirrored); the norms that set the cluster threshold and the quotients of E (a
+// first-order correction) are taken in FP32.  Scratch X: 3 RC^2 doubles.  Block-wide.
+static __device__ __noinline__ void refine_sym_eig(const double* G, double* V, double* lam, int m,
+                                                   int RC, double* X) {
+  // S and R are symmetric (upper triangles computed, mirrored); the norms that set the
+  // cluster threshold and the quotients of E (a first-order correction) are taken in
+  // FP32.
+  double* T = X;
+  double* S = T + RC * RC;
+  double* R = S + RC * RC;
+  __shared__ double rred[50];            // >= 99 floats for block_sum3f
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {            // T = G1 V
+    const int i = e / m, j = e % m;
+    double x = 0.0;
+    for (int l = 0; l < m; ++l) x += G[i * RC + l] * V[j * RC + l];
+    T[i * RC + j] = x;
+  }
+  __syncthreads();
+  float offn = 0.f, rn = 0.f, gn = 0.f;
+  const int ntri = m * (m + 1) / 2;
+  for (int e = threadIdx.x; e < ntri; e += blockDim.x) {             // S = V^T T, R = I - V^T V
+    int j = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+    j += (j + 1) * (j + 2) / 2 <= e;
+    j -= j * (j + 1) / 2 > e;
+    const int i = e - j * (j + 1) / 2;                       // i <= j
+    double x = 0.0, y = 0.0;
+    for (int l = 0; l < m; ++l) {
+      x += V[i * RC + l] * T[l * RC + j];
+      y += V[i * RC + l] * V[j * RC + l];
+    }
+    const double rr = (i == j ? 1.0 : 0.0) - y;
+    S[i * RC + j] = x; S[j * RC + i] = x;
+    R[i * RC + j] = rr; R[j * RC + i] = rr;
+    const float xf = (float)x, rf = (float)rr, gf = (float)G[i * RC + j];
+    const float wgt = i == j ? 1.f : 2.f;
+    if (i != j) offn += 2.f * xf * xf;
+    rn += wgt * rf * rf;
+    gn += wgt * gf * gf;
+  }
+  block_sum3f(&offn, &rn, &gn, reinterpret_cast<float*>(rred));
+  const float delta = 2.f * (sqrtf(offn) + sqrtf(gn) * sqrtf(rn));   // cluster separation
+  for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = S[i * RC + i] / (1.0 - R[i * RC + i]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {            // E (into T)
+    const int i = e / m, j = e % m;
+    double x = 0.5 * R[i * RC + j];
+    if (i != j) {
+      const float d = (float)(lam[j] - lam[i]);
+      if (fabsf(d) > delta) x = (double)__fdividef((float)(S[i * RC + j] + lam[j] * R[i * RC + j]), d);
+    }
+    T[i * RC + j] = x;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {     // V (I + E) into S (dead)
+    const int i = e / m, j = e % m;
+    double x = V[j * RC + i];
+    for (int l = 0; l < m; ++l) x += V[l * RC + i] * T[l * RC + j];
+    S[j * RC + i] = x;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    V[j * RC + i] = S[j * RC + i];
+  }
+  __syncthreads();
+}
+
 __host__ __device__ __forceinline__ size_t jacobi_mixed_scratch_bytes(int ld) {
   return sizeof(float) * (2 * ld * ld + 2 * ld) + sizeof(float2) * (2 * ld * ld);
 }

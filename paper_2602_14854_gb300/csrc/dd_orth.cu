@@ -331,67 +331,8 @@ __global__ void __launch_bounds__(DD_THREADS, 1) k_geig(OrthArgs a, const double
     __syncthreads();
     jacobi_svd_mixed(Bc, Jc, m, RC, &iv[0], lam, X);
   }
-  // FP64 refinement (V is Jc: V_ij = Jc[j * RC + i]); T, S, R, E in the SVD scratch.
-  // S and R are symmetric (upper triangles computed, mirrored); the norms that set the
-  // cluster threshold and the quotients of E (a first-order correction) are taken in
-  // FP32.
-  double* T = X;
-  double* S = T + RC * RC;
-  double* R = S + RC * RC;
-  __shared__ double rred[50];            // >= 99 floats for block_sum3f
-  for (int e = tid; e < m * m; e += blockDim.x) {            // T = G1 V
-    const int i = e / m, j = e % m;
-    double x = 0.0;
-    for (int l = 0; l < m; ++l) x += Gs[i * RC + l] * Jc[j * RC + l];
-    T[i * RC + j] = x;
-  }
-  __syncthreads();
-  float offn = 0.f, rn = 0.f, gn = 0.f;
-  const int ntri = m * (m + 1) / 2;
-  for (int e = tid; e < ntri; e += blockDim.x) {             // S = V^T T, R = I - V^T V
-    int j = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
-    j += (j + 1) * (j + 2) / 2 <= e;
-    j -= j * (j + 1) / 2 > e;
-    const int i = e - j * (j + 1) / 2;                       // i <= j
-    double x = 0.0, y = 0.0;
-    for (int l = 0; l < m; ++l) {
-      x += Jc[i * RC + l] * T[l * RC + j];
-      y += Jc[i * RC + l] * Jc[j * RC + l];
-    }
-    const double rr = (i == j ? 1.0 : 0.0) - y;
-    S[i * RC + j] = x; S[j * RC + i] = x;
-    R[i * RC + j] = rr; R[j * RC + i] = rr;
-    const float xf = (float)x, rf = (float)rr, gf = (float)Gs[i * RC + j];
-    const float wgt = i == j ? 1.f : 2.f;
-    if (i != j) offn += 2.f * xf * xf;
-    rn += wgt * rf * rf;
-    gn += wgt * gf * gf;
-  }
-  block_sum3f(&offn, &rn, &gn, reinterpret_cast<float*>(rred));
-  const float delta = 2.f * (sqrtf(offn) + sqrtf(gn) * sqrtf(rn));   // cluster separation
-  for (int i = tid; i < m; i += blockDim.x) lam[i] = S[i * RC + i] / (1.0 - R[i * RC + i]);
-  __syncthreads();
-  for (int e = tid; e < m * m; e += blockDim.x) {            // E (into T)
-    const int i = e / m, j = e % m;
-    double x = 0.5 * R[i * RC + j];
-    if (i != j) {
-      const float d = (float)(lam[j] - lam[i]);
-      if (fabsf(d) > delta) x = (double)__fdividef((float)(S[i * RC + j] + lam[j] * R[i * RC + j]), d);
-    }
-    T[i * RC + j] = x;
-  }
-  __syncthreads();
-  for (int e = tid; e < m * m; e += blockDim.x) {            // V (I + E) into Bc
-    const int i = e / m, j = e % m;
-    double x = Jc[j * RC + i];
-    for (int l = 0; l < m; ++l) x += Jc[l * RC + i] * T[l * RC + j];
-    Bc[j * RC + i] = x;
-  }
-  __syncthreads();
-  for (int e = tid; e < m * m; e += blockDim.x) {
-    const int i = e / m, j = e % m;
-    Jc[j * RC + i] = Bc[j * RC + i];
-  }
+  // FP64 refinement of the eigenvectors (V is Jc: V_ij = Jc[j * RC + i])
+  refine_sym_eig(Gs, Jc, lam, m, RC, X);
   for (int j = tid; j < m; j += blockDim.x) {
     const double l = lam[j];
     if (!isfinite(l)) atomicOr(a.status, (unsigned)ST_NONFINITE);

@@ -331,8 +331,10 @@ __global__ void __launch_bounds__(DD_THREADS) k_small_adv1(Problem P, PhaseBufs 
   // Eigendecomposition of the symmetric rt x rt matrix C: one-sided Jacobi of the
   // positive semidefinite C + s I (s = |C|_F >= its spectral radius); the column
   // norms of (C + s I) P are lambda + s.  FP32 sweeps and a double-float finish,
-  // accurate to ~1e-13 |C|, in both precisions: the upwind split feeds every stencil
-  // application, and FP32 errors here were the largest part of the mixed form's.
+  // accurate to ~1e-13 |C|, then one FP64 refinement step, in every precision: the upwind
+  // split feeds every stencil application (FP32 errors here were the largest part of the
+  // mixed form's; the double-float level still put single steps of narrow sources 1e-10
+  // off the oracle).
   double* Bc = sh;                      // RC*RC column-major
   double* Pm = Bc + RC * RC;            // RC*RC eigenvectors: column l = Pm[l*RC + i]
   double* lam = Pm + RC * RC;           // RC
@@ -366,6 +368,15 @@ __global__ void __launch_bounds__(DD_THREADS) k_small_adv1(Problem P, PhaseBufs 
     }
   }
   __syncthreads();
+  // one FP64 refinement step of P and lambda (C itself, symmetrised, in Bc): the split's
+  // sensitivity to P is |C| / (the gap between positive and negative eigenvalues), and
+  // the double-float Jacobi alone left splits ~1e-13 |C| / gap off the FP64 ones
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    const int i = e / RC, j = e % RC;
+    Bc[e] = (i < rt && j < rt) ? 0.5 * (Csrc[i * RC + j] + Csrc[j * RC + i]) : 0.0;
+  }
+  __syncthreads();
+  refine_sym_eig(Bc, Pm, lam, rt, RC, X);
   // C+ = P diag(max(l,0)) P^T, C- = P diag(min(l,0)) P^T
   double* Cp = SMB(B, P, k, SM_CP);
   double* Cn = SMB(B, P, k, SM_CM);
