@@ -318,7 +318,7 @@ def pin_brute_force(cls, wl, nsteps=3, seed=50):
 @pytest.mark.parametrize("integrator", ["euler", "rk4"])
 @pytest.mark.parametrize("ragged", [False, True])
 def test_brute_force_tiny_grid(integrator, ragged):
-    """P12: the oracle's Algorithm 6 equals the dense restatement to roundoff (8 x 8
+    """The oracle's Algorithm 6 equals the dense restatement to roundoff (8 x 8
     cells, 8 directions, rank 2, r_t <= 6; a 2 x 2 tiling and a ragged 3 x 2 one)."""
     err, ranks_ok = pin_brute_force(dd_dlra.DDDLRA, tiny_problem(integrator, ragged))
     assert ranks_ok
@@ -327,7 +327,7 @@ def test_brute_force_tiny_grid(integrator, ragged):
 
 @pytest.mark.parametrize("integrator", ["euler", "rk4"])
 def test_brute_force_tolerance_mode(integrator):
-    """P12 with the tolerance rules of Algorithms 4 and 5 (tol 0.08, ranks 2..4)."""
+    """Brute force with the tolerance rules of Algorithms 4 and 5 (tol 0.08, ranks 2..4)."""
     wl = tiny_problem(integrator, True, tol_mode=True)
     err, ranks_ok = pin_brute_force(dd_dlra.DDDLRA, wl)
     assert ranks_ok
@@ -335,7 +335,7 @@ def test_brute_force_tolerance_mode(integrator):
 
 
 def test_brute_force_with_inflow_tolerance_mode():
-    """P12 with inflow in tolerance mode, where the augmentation column's norm
+    """Brute force with inflow in tolerance mode, where the augmentation column's norm
     |g|_x = (hx hy len sum g^2)^1/2 (R22) enters the rank decisions."""
     err, ranks_ok = pin_brute_force(dd_dlra.DDDLRA, inflow_tol_problem())
     assert ranks_ok
@@ -343,7 +343,7 @@ def test_brute_force_with_inflow_tolerance_mode():
 
 
 def test_brute_force_with_inflow():
-    """P12 with physical inflow on all four sides (random g, h; R22): the inflow acts
+    """Brute force with physical inflow on all four sides (random g, h; R22): the inflow acts
     as a neighbour in the ghost rows and in Algorithm 4."""
     wl = tiny_problem("rk4", False)
     rng = np.random.default_rng(12)
@@ -460,7 +460,7 @@ def pin_one_by_one(cls, integrator, nsteps=3):
 
 @pytest.mark.parametrize("integrator", ["euler", "rk4"])
 def test_one_by_one_tiling_is_classic_dlra(integrator):
-    """P8: a 1 x 1 tiling reduces Algorithm 6 to the classic projector-splitting DLRA
+    """A 1 x 1 tiling reduces Algorithm 6 to the classic projector-splitting DLRA
     (Algorithm 4 only rotates V; the fixed rank keeps r_t = r; the truncation only
     rotates the factors)."""
     err, ranks_ok = pin_one_by_one(dd_dlra.DDDLRA, integrator)
