@@ -193,10 +193,11 @@ def per_kernel_roofline(prof, nsteps, fp64_peak, fp32_peak, tc_peak, bf16_peak=N
     return out
 
 
-# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum)
-# from the ncu capture in profiles/k_tall_lognormal_subset.md (a 2x2 subset of the same
-# subdomains, scaled by the subdomain count; None until a capture of the kernel as it stands)
-NCU_TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean over one warm
+# step's launches) of the kernels as they stand, from the ncu captures summarised in
+# profiles/ (k_gram: profiles/k_gram_lognormal_traffic.md, the lognormal workload with the
+# tensor-core products).  An entry must be dropped when its kernel changes.
+NCU_TRAFFIC = {"k_gram": 63.1e6}
 
 
 def timed_steps(s, steps, warmup, flush, stream, torch):
