@@ -135,16 +135,18 @@ typedef struct dd_options {
                       /* rank; not the paper's scheme at low rank; no eigendecomposition)    */
   int products;       /* the FP64 tall x small products (orthonormalisations, truncation,     */
                       /* K0 = X S <V, V_hat>): DD_PRODUCTS_FP64: FP64 CUDA-core arithmetic;    */
-                      /* DD_PRODUCTS_TENSOR: on the BF16 tensor cores with the error-free      */
+                      /* DD_PRODUCTS_TENSOR: these and the orthonormalisations' Grams on the  */
+                      /* BF16 tensor cores with the error-free                                 */
                       /* splitting of Ozaki et al. (seven 8-bit digits per value, exact FP32   */
                       /* accumulation, FP64-level error).  Results agree to FP64 rounding, not */
                       /* bits.  DD_PRODUCTS_AUTO: per row family (spatial rows, angular rows)  */
                       /* the faster of the two: timed when the solver is created if autotune  */
                       /* is set, else the tensor cores where the family has at least two      */
-                      /* 128-row tiles per SM.                                                 */
+                      /* 128-row tiles per SM (the Grams then stay on the CUDA cores).         */
   int autotune;       /* 1: when the solver is created, time the launch choices on its own    */
-                      /* workspace and keep the fastest: the products' engine per row family  */
-                      /* (with DD_PRODUCTS_AUTO) and the chunk counts of the chunked Gram     */
+                      /* workspace and keep the fastest: the products' and the               */
+                      /* orthonormalisations' Grams' engines per row family (with            */
+                      /* DD_PRODUCTS_AUTO) and the chunk counts of the chunked Gram          */
                       /* reductions (the heuristic's, a half and a quarter of it; every count */
                       /* keeps a fixed summation order).  Cached per problem shape in the     */
                       /* process.  0: fixed heuristics.  See dd_dlra_tuning.                   */
@@ -253,8 +255,9 @@ dd_status dd_dlra_profile_work(dd_dlra_t h, int nsteps, double* ms, int* launche
 
 /*
  * dd_dlra_tuning — the launch choices the solver runs with (host outputs, either may be
- * NULL): choice[4] = {tensor-core products for spatial rows (0/1), for angular rows (0/1),
- * Gram chunks per subdomain for spatial rows, for angular rows}; ms[8] = the autotuner's
+ * NULL): choice[6] = {tensor-core products for spatial rows (0/1), for angular rows (0/1),
+ * Gram chunks per subdomain for spatial rows, for angular rows, the orthonormalisations'
+ * Grams on the tensor cores for spatial rows (0/1), for angular rows (0/1)}; ms[8] = the autotuner's
  * timings per family (spatial, then angular): FP64 products, tensor-core products, the
  * best and the worst chunk count (ms for one trial Gram and reduction); -1 where nothing
  * was timed (autotune off, or a choice fixed by the options).

@@ -204,11 +204,12 @@ class Solver:
     def tuning(self):
         """The launch choices in use and the autotuner's timings (dd_dlra_tuning):
         ({"oz_spatial", "oz_angular", "chunks_spatial", "chunks_angular"}, ms[8])."""
-        ch = np.zeros(4, dtype=np.int32)
+        ch = np.zeros(6, dtype=np.int32)
         ms = np.zeros(8)
         _check(self.lib, self.lib.dd_dlra_tuning(self.h, ch.ctypes.data_as(_ip), _ptr(ms)))
         return ({"oz_spatial": int(ch[0]), "oz_angular": int(ch[1]),
-                 "chunks_spatial": int(ch[2]), "chunks_angular": int(ch[3])}, ms.tolist())
+                 "chunks_spatial": int(ch[2]), "chunks_angular": int(ch[3]),
+                 "oz_gram_spatial": int(ch[4]), "oz_gram_angular": int(ch[5])}, ms.tolist())
 
     def step(self, nsteps: int = 1):
         _check(self.lib, self.lib.dd_dlra_step(self.h, int(nsteps)))

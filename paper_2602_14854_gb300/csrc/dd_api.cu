@@ -597,6 +597,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
                                        : dd::PREC_FP64;
   P.Ntot = Nt;
   P.oz_sp = P.oz_ang = opt->products == DD_PRODUCTS_TENSOR ? 1 : 0;
+  P.ozg_sp = P.ozg_ang = P.oz_sp;
   P.mass_fix = opt->mass_fix;
   P.splitting = opt->splitting;
   P.kstep_split = opt->kstep_split;
@@ -844,6 +845,8 @@ dd_status dd_dlra_tuning(dd_dlra_t h, int* choice, double* ms) {
     choice[1] = h->P.oz_ang;
     choice[2] = h->P.nchunk_sp;
     choice[3] = h->P.nchunk_ang;
+    choice[4] = h->P.ozg_sp;
+    choice[5] = h->P.ozg_ang;
   }
   if (ms)
     for (int i = 0; i < 8; ++i) ms[i] = h->tune_ms[i];

@@ -13,7 +13,7 @@ enum KernelSlot {
   KS_GHOST, KS_KSTEP_ADV, KS_SP_COEFFS, KS_SSTEP_ADV, KS_LSTEP_ADV, KS_GRAM, KS_TRUNC,
   KS_COLL_RANK, KS_COLL_A, KS_COLL_KSTEP, KS_COLL_SMALL, KS_COLL_LSTEP, KS_COLL_FINAL,
   KS_FLUX, KS_COPY, KS_GEIG, KS_CHOL, KS_COMPLETE, KS_MASS, KS_KC_W, KS_KC_SEL, KS_KC_APPLY,
-  KS_TC_TALL, KS_TC_GRAM, KS_TC_LSTEP, KS_OZ_TALL, NSLOT
+  KS_TC_TALL, KS_TC_GRAM, KS_TC_LSTEP, KS_OZ_TALL, KS_OZ_GRAM, NSLOT
 };
 extern const char* const kSlotNames[NSLOT];
 
@@ -130,6 +130,7 @@ struct Problem {
   int kstep_split;        // C+/C- of the advection K-step: 0 eigen-split, 1 direction split
   int oz_sp, oz_ang;      // FP64 tall products on the tensor cores (Ozaki splitting), for
                           // the spatial / the angular row family
+  int ozg_sp, ozg_ang;    // the orthonormalisations' Grams likewise
   // physical inflow (null without): per subdomain and side (x-lo, x-hi, y-lo, y-hi) an
   // on flag, face values sqrt(hx hy) g per line (maxlines), the angular column
   // sqrt(w) m_in h (n) and its augmentation scale |g|_x
@@ -189,6 +190,10 @@ bool tc_gram(const Problem& P, cudaStream_t st, const TcGram& a);
 bool oz_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
              int lda, const int* ninner, int ninner_fix, const double* Bm, int bsmall,
              const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy);
+// The chunk partials of the symmetric Gram A^T A (the layout and chunk exponents of k_gram)
+// FP64-accurate on the BF16 tensor cores; false when the capacity does not fit.
+bool oz_gram(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
+             int lda, const int* acnt, double* part, int nchunk, int* cexp);
 
 void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st);
 void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st);

@@ -1495,7 +1495,7 @@ const char* const kSlotNames[NSLOT] = {
     "k_ghost", "k_kstep_adv", "k_sp_coeffs", "k_sstep_adv", "k_lstep_adv", "k_gram", "k_trunc",
     "k_coll_rank", "k_coll_a", "k_coll_kstep", "k_coll_small", "k_coll_lstep", "k_coll_final",
     "k_flux", "memcpy", "k_geig", "k_chol_inv", "k_complete", "k_mass_fix", "k_kc_w", "k_kc_sel",
-    "k_kc_apply", "k_tc_tall", "k_tc_gram", "k_tc_lstep", "k_oz_tall"};
+    "k_kc_apply", "k_tc_tall", "k_tc_gram", "k_tc_lstep", "k_oz_tall", "k_oz_gram"};
 thread_local Prof* g_prof = nullptr;
 
 size_t part_elems(const Problem& P) {
@@ -1582,6 +1582,9 @@ static int gram_partials(const Problem& P, const PhaseBufs& B, cudaStream_t st, 
   a.wrow = nullptr; a.part = B.part; a.nchunk = spatial ? P.nchunk_sp : P.nchunk_ang;
   a.cexp = cexp;
   a.sym = 1;
+  if ((spatial ? P.ozg_sp : P.ozg_ang) &&
+      oz_gram(P, B.status, st, spatial, A, lda, acnt, B.part, a.nchunk, cexp))
+    return a.nchunk;
   pbeg(st, KS_GRAM);
   k_gram<<<dim3(a.nchunk, P.g.nsub), DD_THREADS, sizeof(double) * P.g.RC * P.g.RC, st>>>(P.g, a);
   pend(st);
@@ -1656,7 +1659,7 @@ __global__ void k_trial_fill(double* a, long n) {
 
 namespace {
 struct TuneChoice {
-  int oz_sp, oz_ang, nch_sp, nch_ang;
+  int oz_sp, oz_ang, nch_sp, nch_ang, ozg_sp, ozg_ang;
   double ms[8];
 };
 std::mutex g_tune_mu;
@@ -1692,7 +1695,9 @@ cudaError_t autotune(Problem& P, const PhaseBufs& B, cudaStream_t st, int tune_p
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
       const TuneChoice& c = it->second;
-      if (tune_products) { P.oz_sp = c.oz_sp; P.oz_ang = c.oz_ang; }
+      if (tune_products) {
+        P.oz_sp = c.oz_sp; P.oz_ang = c.oz_ang; P.ozg_sp = c.ozg_sp; P.ozg_ang = c.ozg_ang;
+      }
       if (tune_chunks) { P.nchunk_sp = c.nch_sp; P.nchunk_ang = c.nch_ang; }
       for (int i = 0; i < 8; ++i) ms[i] = c.ms[i];
       return cudaSuccess;
@@ -1720,15 +1725,26 @@ cudaError_t autotune(Problem& P, const PhaseBufs& B, cudaStream_t st, int tune_p
       // forms the Gram of its output from the same tiles in the orthonormalisation (one of
       // its two products there): the tensor-core side is charged half a separate Gram
       // reduction per product.
+      // The orthonormalisation's Gram engine (k_gram or k_oz_gram) is timed the same way
+      // and the faster one kept (by 3%; k_gram on a tie).
       const int half = std::max(2, (RC / 2) & ~1);
       Problem Q = P;
       Q.oz_sp = Q.oz_ang = 0;
-      const double tg = time_on(st, REPS, [&] {
-        const int n = gram_partials(P, B, st, sp, A, RC, B.keep, nullptr);
-        Dst d;
-        for (int i = 0; i < 8; ++i) d.idx[i] = SM_QM;
-        reduce_to(P, B, st, n, 1, d);
-      });
+      Q.ozg_sp = Q.ozg_ang = 0;
+      Problem Qg = Q;
+      Qg.ozg_sp = Qg.ozg_ang = 1;
+      auto gram_trial = [&](const Problem& R) {
+        return time_on(st, REPS, [&] {
+          const int n = gram_partials(R, B, st, sp, A, RC, B.keep, nullptr);
+          Dst d;
+          for (int i = 0; i < 8; ++i) d.idx[i] = SM_QM;
+          reduce_to(R, B, st, n, 1, d);
+        });
+      };
+      const double tg64 = gram_trial(Q), tgoz = gram_trial(Qg);
+      const int gpick = tgoz > 0.0 && tg64 > 0.0 && tgoz < 0.97 * tg64 ? 1 : 0;
+      if (sp) P.ozg_sp = gpick; else P.ozg_ang = gpick;
+      const double tg = gpick ? tgoz : tg64;
       double t64 = 0.0, toz = tg > 0.0 ? tg : 0.0;
       bool oz_ok = true;
       for (int c : {half, RC}) {
@@ -1778,6 +1794,7 @@ cudaError_t autotune(Problem& P, const PhaseBufs& B, cudaStream_t st, int tune_p
     std::lock_guard<std::mutex> lk(g_tune_mu);
     TuneChoice c;
     c.oz_sp = P.oz_sp; c.oz_ang = P.oz_ang; c.nch_sp = P.nchunk_sp; c.nch_ang = P.nchunk_ang;
+    c.ozg_sp = P.ozg_sp; c.ozg_ang = P.ozg_ang;
     for (int i = 0; i < 8; ++i) c.ms[i] = ms[i];
     g_tune_cache[key] = c;
   }
