@@ -634,8 +634,15 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
 // dt sum_s b_s R~_s is rotated back with P^T and added to the FP64 state.  P and lambda
 // come from k_small_adv1 (small slots S3T and VB, free until the S-step).  Same lines-
 // per-CTA layout as k_kstep_adv; the entry indices are decoded once.
+// y += x over n contiguous FP64 entries (the K-step's rotated increment)
+__global__ void k_add_flat(double* __restrict__ y, const double* __restrict__ x, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
 template <typename TC>
-__global__ void __launch_bounds__(DD_THREADS) k_kstep_eig(Problem P, PhaseBufs B, int axis, int lpb) {
+__global__ void __launch_bounds__(DD_THREADS) k_kstep_eig(Problem P, PhaseBufs B, int axis, int lpb,
+                                                      int ebasis) {
   extern __shared__ double sh_raw[];
   TC* sh = reinterpret_cast<TC*>(sh_raw);
   const int k = blockIdx.y, RC = P.g.RC;
@@ -648,7 +655,12 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_eig(Problem P, PhaseBufs B
   // a tile larger than the register tile (only with lpb = 1: a line longer than
   // 256 KE_EPT / r_t) is left to k_kstep_adv, launched after this kernel for exactly these
   if ((long)nl * len * rt > (long)DD_THREADS * KE_EPT) return;
-  count_work(P.g, KS_KSTEP_ADV, (double)nl * len * rt * (4.0 * rt + 8.0 * (P.integrator == 1 ? 4 : 1)));
+  count_work(P.g, KS_KSTEP_ADV,
+             (double)nl * len * rt * ((ebasis ? 0.0 : 4.0 * rt) + 8.0 * (P.integrator == 1 ? 4 : 1)));
+  // ebasis: K~ = K P was formed outside (in X1, by the tall products); the stages run on it
+  // and the increment dt sum_s b_s R~_s is written back there (rotated back and added to K
+  // outside)
+  const double* Ksrc = ebasis ? B.X1 : B.K;
   TC* Pm = sh;                     // Pm[u * RC + j]: component u of eigenvector j
   TC* lp = Pm + RC * RC;           // max(lambda, 0)
   TC* ln = lp + RC;                // min(lambda, 0)
@@ -672,7 +684,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_eig(Problem P, PhaseBufs B
     if (e < tot) {
       const int li = e / (len * rt), pos = (e / rt) % len, t = e % rt;
       code[i] = (li << 20) | (pos << 8) | t;
-      Kst[e] = (TC)B.K[((long)P.g.rowoff[k] + cell_of(L, l0 + li, pos)) * RC + t];
+      Kst[e] = (TC)Ksrc[((long)P.g.rowoff[k] + cell_of(L, l0 + li, pos)) * RC + t];
     }
   }
   __syncthreads();
@@ -690,17 +702,23 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_eig(Problem P, PhaseBufs B
     const int e = threadIdx.x + i * blockDim.x;
     k0[i] = 0; acc[i] = 0;
     if (e < tot) {
-      const int t = code[i] & 255, rowe = e - t;   // entry of column 0 of this cell
-      TC x = 0;
-      for (int u = 0; u < rt; ++u) x += Kst[rowe + u] * Pm[u * RC + t];
-      k0[i] = x;
+      if (ebasis) {
+        k0[i] = Kst[e];
+      } else {
+        const int t = code[i] & 255, rowe = e - t;   // entry of column 0 of this cell
+        TC x = 0;
+        for (int u = 0; u < rt; ++u) x += Kst[rowe + u] * Pm[u * RC + t];
+        k0[i] = x;
+      }
     }
   }
   __syncthreads();
+  if (!ebasis) {
 #pragma unroll
-  for (int i = 0; i < KE_EPT; ++i) {
-    const int e = threadIdx.x + i * blockDim.x;
-    if (e < tot) Kst[e] = k0[i];
+    for (int i = 0; i < KE_EPT; ++i) {
+      const int e = threadIdx.x + i * blockDim.x;
+      if (e < tot) Kst[e] = k0[i];
+    }
   }
   __syncthreads();
   const TC coef = (TC)(-P.c_adv / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]));
@@ -732,6 +750,17 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_eig(Problem P, PhaseBufs B
       }
     }
     __syncthreads();
+  }
+  if (ebasis) {                     // the increment dt acc~, in the eigenbasis
+#pragma unroll
+    for (int i = 0; i < KE_EPT; ++i) {
+      const int e = threadIdx.x + i * blockDim.x;
+      if (e < tot) {
+        const int li = code[i] >> 20, pos = (code[i] >> 8) & 4095, t = code[i] & 255;
+        B.X1[((long)P.g.rowoff[k] + cell_of(L, l0 + li, pos)) * RC + t] = (double)(dt * Kst[e]);
+      }
+    }
+    return;
   }
   // back to the original basis: increment_t = dt sum_j acc~_j P_tj, added in FP64
 #pragma unroll
@@ -1926,6 +1955,27 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   // 6. K-step
   {
     const int len = P.maxlines;
+    // with the spatial tall products on the tensor cores and every line within the
+    // eigenbasis tile: the two basis changes as tall products (K~ = K P into X1, free until
+    // the QR; the increment's P^T into Hw, free until the orthonormalisation), the stages in
+    // the eigenbasis kernel, and K += the rotated increment in FP64 (rotating the whole K back
+    // would put rounding of K's size on entries whose increment is tiny)
+    const bool ebasis = P.kstep_split == 0 && P.oz_sp && (long)len * g.RC <= (long)DD_THREADS * KE_EPT;
+    if (ebasis && oz_tall(P, B.status, st, 1, B.K, RC, B.rt, 0, nullptr, SM_S3T, B.sm, B.rt, 0,
+                          B.X1, RC, 0)) {
+      const int lpb = kstep_eig_lpb(P, len);
+      dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
+      pbeg(st, KS_KSTEP_ADV);
+      k_kstep_eig<double><<<grid, DD_THREADS, kstep_eig_smem(P, lpb, len), st>>>(P, B, axis, lpb, 1);
+      pend(st);
+      // the same shape as the first product: it cannot be refused where that one was not
+      (void)oz_tall(P, B.status, st, 1, B.X1, RC, B.rt, 0, nullptr, SM_S3T, B.sm, B.rt, 0, B.Hw, RC, 1);
+      const long nel = P.Ntot * RC;
+      pbeg(st, KS_KSTEP_ADV);
+      k_add_flat<<<(int)std::min<long>((nel + DD_THREADS - 1) / DD_THREADS, 4L * P.nsm), DD_THREADS, 0, st>>>(
+          B.K, B.Hw, nel);
+      pend(st);
+    } else {
     pbeg(st, KS_KSTEP_ADV);
     if (P.kstep_split == 0 && len < 4096) {
       // FP64 eigen-split in the eigenbasis, in the mixed form too: the FP32 matrix
@@ -1933,7 +1983,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
       // increment, and its error grew to 1e-4..1e-3 of the flux on narrow sources
       const int lpb = kstep_eig_lpb(P, len);
       dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
-      k_kstep_eig<double><<<grid, DD_THREADS, kstep_eig_smem(P, lpb, len), st>>>(P, B, axis, lpb);
+      k_kstep_eig<double><<<grid, DD_THREADS, kstep_eig_smem(P, lpb, len), st>>>(P, B, axis, lpb, 0);
       if ((long)len * g.RC > (long)DD_THREADS * KE_EPT) {
         // subdomains whose line exceeds the eigenbasis kernel's tile: the FP64 matrix
         // stencil (the same discrete operator)
@@ -1950,6 +2000,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
         k_kstep_adv<double><<<grid, DD_THREADS, kstep_smem(P, lpb, len), st>>>(P, B, axis, lpb, 0);
     }
     pend(st);
+    }
   }
   if (P.mass_fix) mass_acc(P, B, st, B.K, B.Vh, nullptr, B.rt, 1.0);
   // 7. QR of K

@@ -103,6 +103,7 @@ struct TcTall {
   int tps;                          // 128-row tiles per subdomain (of the largest)
   unsigned* status;
   const double* A;                  // A itself (the kernels that load it without a tensor map)
+  int mtrans;                       // M read transposed (the Ozaki kernel)
 };
 
 #define TT_ROWS 128
@@ -761,7 +762,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
 #pragma unroll
       for (int i = 0; i < DD_MAXC * DD_MAXC / OZ_WORKERS; ++i) {
         const int e = tid + OZ_WORKERS * i, kk = e >> 6, n = e & (DD_MAXC - 1);
-        if (worker && kk < KP) Ms[e] = (kk < t.ni && n < t.nc) ? __ldg(Mk + (long)kk * RC + n) : 0.0;
+        if (worker && kk < KP)
+          Ms[e] = (kk < t.ni && n < t.nc)
+                      ? __ldg(Mk + (a.mtrans ? (long)n * RC + kk : (long)kk * RC + n)) : 0.0;
       }
       __syncthreads();
       for (int kk = worker ? warp : KP; kk < KP; kk += OZ_WARPS) {   // mu_k: warp per row
@@ -1182,7 +1185,8 @@ bool tc_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, c
 
 bool oz_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
              int lda, const int* ninner, int ninner_fix, const double* Bm, int bsmall,
-             const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy) {
+             const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy,
+             int mtrans) {
   if (lda > DD_MAXC || (lda & 1)) return false;
   const OzPlan pl = oz_plan(lda, OZ_SMEM_LIMIT);
   if (pl.total > OZ_SMEM_LIMIT) return false;
@@ -1191,6 +1195,7 @@ bool oz_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, c
   a.Bm = Bm; a.bsmall = bsmall; a.smbase = smbase; a.ncols = ncols; a.ncols_fix = ncols_fix;
   a.Y = Y; a.ldy = ldy; a.alpha = 1.0; a.accumulate = 0; a.status = status;
   a.A = A;
+  a.mtrans = mtrans;
   a.tps = ((spatial ? P.maxN : P.g.n) + TT_ROWS - 1) / TT_ROWS;
   const long ntot = (long)P.g.nsub * a.tps;
   const int grid = (int)std::min<long>(ntot, P.nsm);
