@@ -156,7 +156,7 @@ def fp64_gemm_peak(torch):
 FP64_SLOTS = ["k_tall", "k_gram", "k_ang_coeffs", "k_sp_coeffs", "k_kstep_adv", "k_lstep_adv",
               "k_coll_kstep", "k_coll_lstep"]
 TC_SLOTS = ["k_tc_tall", "k_tc_gram"]
-OZ_SLOTS = ["k_oz_tall"]          # FP64-accurate products on the BF16 tensor cores (Ozaki)
+OZ_SLOTS = ["k_oz_tall", "k_oz_gram"]   # FP64-accurate products and Grams on the BF16 tensor cores (Ozaki)
 OZ_PAIRS = 28                     # digit-pair products per FP64 product (7 digits, order <= 6)
 LATENCY = ["k_geig", "k_geig(aug)", "k_trunc", "k_small_adv1", "k_chol_inv", "k_sstep_adv",
            "k_coll_small", "k_kc_w", "k_kc_sel", "k_kc_apply", "k_complete", "k_reduce"]
