@@ -256,8 +256,9 @@ dd_status dd_dlra_profile_work(dd_dlra_t h, int nsteps, double* ms, int* launche
 /*
  * dd_dlra_tuning — the launch choices the solver runs with (host outputs, either may be
  * NULL): choice[6] = {tensor-core products for spatial rows (0/1), for angular rows (0/1),
- * Gram chunks per subdomain for spatial rows, for angular rows, the orthonormalisations'
- * Grams on the tensor cores for spatial rows (0/1), for angular rows (0/1)}; ms[8] = the autotuner's
+ * chunks per subdomain of the orthonormalisations' Grams for spatial rows, for angular rows
+ * (the Galerkin products keep the heuristic's count), the orthonormalisations' Grams on the
+ * tensor cores for spatial rows (0/1), for angular rows (0/1)}; ms[8] = the autotuner's
  * timings per family (spatial, then angular): FP64 products, tensor-core products, the
  * best and the worst chunk count (ms for one trial Gram and reduction); -1 where nothing
  * was timed (autotune off, or a choice fixed by the options).

@@ -552,7 +552,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   }
   ok &= dalloc(&h->d_L0, (long)nsub * n * MC) == cudaSuccess;
   const int WC = RC;
-  ok &= dalloc(&h->d_Hw, Nt * WC) == cudaSuccess;
+  ok &= dalloc(&h->d_Hw, std::max(Nt, (long)nsub * n) * WC) == cudaSuccess;   // also the L-step's Y_-
   ok &= dalloc(&h->d_Hwa, (long)nsub * n * WC) == cudaSuccess;
   ok &= dalloc(&h->d_Vh, (long)nsub * n * RC) == cudaSuccess;
   ok &= dalloc(&h->d_K, Nt * RC) == cudaSuccess;
@@ -617,6 +617,8 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
     P.nsm = nsm;
   }
   P.nchunk_ang = std::max(1, std::min(16, n / 64));
+  P.ochunk_sp = P.nchunk_sp;
+  P.ochunk_ang = P.nchunk_ang;
   if (dalloc(&h->d_part, dd::part_elems(P)) != cudaSuccess)
     return bail(DD_ERR_CUDA, "device allocation failed");
   if (dd::orth_init() != cudaSuccess || dd::phase_init() != cudaSuccess)
@@ -843,8 +845,8 @@ dd_status dd_dlra_tuning(dd_dlra_t h, int* choice, double* ms) {
   if (choice) {
     choice[0] = h->P.oz_sp;
     choice[1] = h->P.oz_ang;
-    choice[2] = h->P.nchunk_sp;
-    choice[3] = h->P.nchunk_ang;
+    choice[2] = h->P.ochunk_sp;
+    choice[3] = h->P.ochunk_ang;
     choice[4] = h->P.ozg_sp;
     choice[5] = h->P.ozg_ang;
   }

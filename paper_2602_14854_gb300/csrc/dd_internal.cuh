@@ -795,16 +795,8 @@ __device__ __forceinline__ void jacobi_df_cols(float2* Bd, float2* Jd, int nr, i
 }
 
 // ---------------------------------------------------------------------------
-// Column-per-lane sweeps for 33..64 columns: lane j holds columns j and j + 32 (slots 0
-// and 1), rows interleaved over the warps as above.  A sweep is 63 rounds: 31 rounds pair
-// the columns of each slot among themselves by the circle method (both slots at once, the
-// same partner lane), then 32 rounds pair column j of slot 0 with column (j + r) mod 32 of
-// slot 1.  Every column meets every other once per sweep; each round costs one shuffle per
-// held entry, as with one column per lane, and both lanes of a pair again form their dot
-// product from the same operands.
+// Column-pair sweeps for 33..64 columns (see jacobi_f32_pairs below).
 // ---------------------------------------------------------------------------
-#define JW_JROWS2 ((64 + JW_WARPS - 1) / JW_WARPS)   // rows of J per warp (nc <= 64)
-
 __device__ __forceinline__ float4* jw_buffer4() {
   __shared__ float4 jwb4[2 * JW_WARPS * 32];
   return jwb4;
@@ -820,109 +812,113 @@ struct JwAddDF2 {
   }
 };
 
-// Partner lane of the round: within-slot rounds (r < 31) by the circle method over the 32
-// lanes (same partner for both slots); cross rounds: slot 0 meets lane (lane + c) & 31 in
-// slot 1, slot 1 meets lane (lane - c) & 31 in slot 0, c = r - 31.
-__device__ __forceinline__ void jw2_partners(int lane, int r, int* p0, int* p1, bool* cross) {
-  if (r < 31) {
-    const int p = jw_partner(lane, r, 32);
-    *p0 = p; *p1 = p; *cross = false;
-  } else {
-    const int c = r - 31;
-    *p0 = (lane + c) & 31; *p1 = (lane - c) & 31; *cross = true;
-  }
-}
+// Column pairs per lane (nc <= 64): lane l < np = mm / 2 (mm = nc rounded up to even) holds
+// the pair (top_l, bot_l) of columns, rows interleaved over the warps as in the other
+// column sweeps.  A sweep is mm - 1 rounds of the circle method: each round every lane
+// rotates its own pair (one dot product, one rotation for both columns), then the columns
+// move one place around the circle with top_0 fixed: top_l <- top_(l-1) (l >= 2),
+// top_1 <- bot_0, bot_l <- bot_(l+1), bot_(np-1) <- top_(np-1); over mm - 1 rounds every
+// pair of columns meets once.  The column indices travel with the data (a column index
+// >= nc is the empty partner of odd nc), and the columns return to their places at the
+// end.  Same contract as jacobi_f32_cols.
+#define JW_PROWS (64 / JW_WARPS)          // rows per warp for nr <= 64 (B and J alike)
 
-template <int ROWS, bool WJ>
-__device__ __forceinline__ void jacobi_f32_cols2(float* Bf, float* Jf, int nr, int nc, int ld,
+template <bool WJ>
+__device__ __forceinline__ void jacobi_f32_pairs(float* Bf, float* Jf, int nr, int nc, int ld,
                                                  float tol, float stop, int max_sweeps) {
   float2* xb = jw_buffer();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mm = nc + (nc & 1), np = mm >> 1;
   int ph = 0;
-  float b[2][ROWS], v[2][JW_JROWS2];
+  int it = lane, ib = lane + np;                  // column indices of top and bottom
+  float bt[JW_PROWS], bb[JW_PROWS], vt[JW_PROWS], vb[JW_PROWS];
 #pragma unroll
-  for (int sl = 0; sl < 2; ++sl) {
-    const int c = lane + 32 * sl;
-#pragma unroll
-    for (int k = 0; k < ROWS; ++k) {
-      const int i = warp + JW_WARPS * k;
-      b[sl][k] = (c < nc && i < nr) ? Bf[c * ld + i] : 0.f;
-    }
-#pragma unroll
-    for (int k = 0; k < JW_JROWS2; ++k) {
-      const int i = warp + JW_WARPS * k;
-      v[sl][k] = (WJ && c < nc && i < nc) ? Jf[c * ld + i] : 0.f;
-    }
+  for (int k = 0; k < JW_PROWS; ++k) {
+    const int i = warp + JW_WARPS * k;
+    const bool on = lane < np;
+    bt[k] = (on && it < nc && i < nr) ? Bf[it * ld + i] : 0.f;
+    bb[k] = (on && ib < nc && i < nr) ? Bf[ib * ld + i] : 0.f;
+    vt[k] = (WJ && on && it < nc && i < nc) ? Jf[it * ld + i] : 0.f;
+    vb[k] = (WJ && on && ib < nc && i < nc) ? Jf[ib * ld + i] : 0.f;
   }
-  __syncthreads();
-  float al[2] = {0.f, 0.f};
-  float abs_thr = 0.f;
+  __syncthreads();                                 // Bf, Jf are rewritten at the end
+  float at = 0.f, ab = 0.f, abs_thr = 0.f;
   for (int sweep = 0; sweep < max_sweeps && nc > 1; ++sweep) {
-    {
+    {                                              // squared norms afresh every sweep
       float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < ROWS; ++k) {
-        t.x = __fmaf_rn(b[0][k], b[0][k], t.x);
-        t.y = __fmaf_rn(b[1][k], b[1][k], t.y);
+      for (int k = 0; k < JW_PROWS; ++k) {
+        t.x = __fmaf_rn(bt[k], bt[k], t.x);
+        t.y = __fmaf_rn(bb[k], bb[k], t.y);
       }
       t = jw_sum(t, xb, &ph, JwAddF2());
-      al[0] = t.x; al[1] = t.y;
-      if (sweep == 0) abs_thr = 1e-30f * warp_sum_t(al[0] + al[1]);
+      at = t.x; ab = t.y;
+      if (sweep == 0) abs_thr = 1e-30f * warp_sum_t(lane < np ? at + ab : 0.f);
     }
     float lmax = 0.f;
-    for (int r = 0; r < 63; ++r) {
-      int p0, p1;
-      bool cross;
-      jw2_partners(lane, r, &p0, &p1, &cross);
-      // partner entries: slot 0 takes slot (cross ? 1 : 0) of lane p0, slot 1 takes slot
-      // (cross ? 0 : 1) of lane p1
-      float pb[2][ROWS], be[2];
+    for (int r = 0; r < mm - 1; ++r) {
+      float g = 0.f;
 #pragma unroll
-      for (int k = 0; k < ROWS; ++k) {
-        pb[0][k] = __shfl_sync(0xffffffffu, cross ? b[1][k] : b[0][k], p0);
-        pb[1][k] = __shfl_sync(0xffffffffu, cross ? b[0][k] : b[1][k], p1);
+      for (int k = 0; k < JW_PROWS; ++k) g = __fmaf_rn(bt[k], bb[k], g);
+      g = jw_sum(make_float2(g, 0.f), xb, &ph, JwAddF2()).x;
+      const float pr = at * ab;
+      const bool ok = lane < np && it < nc && ib < nc && fabsf(g) > abs_thr && pr > 0.f;
+      const float rel = ok ? fabsf(g) * rsqrtf(pr) : 0.f;
+      lmax = fmaxf(lmax, rel);
+      const bool lo = it < ib;                     // top is the pair's lower column
+      float c, s, t;
+      jw_rotation(lo ? at : ab, lo ? ab : at, g, &c, &s, &t);
+      if (rel > tol) {
+        // b_lo' = c b_lo - s b_hi, b_hi' = s b_lo + c b_hi; |b_lo'|^2 = a - t g, |b_hi'|^2 = b + t g
+        const float st = lo ? -s : s, tg = t * g;
+#pragma unroll
+        for (int k = 0; k < JW_PROWS; ++k) {
+          const float x = bt[k], y = bb[k];
+          bt[k] = c * x + st * y;
+          bb[k] = c * y - st * x;
+        }
+        if (WJ) {
+#pragma unroll
+          for (int k = 0; k < JW_PROWS; ++k) {
+            const float x = vt[k], y = vb[k];
+            vt[k] = c * x + st * y;
+            vb[k] = c * y - st * x;
+          }
+        }
+        at += lo ? -tg : tg;
+        ab += lo ? tg : -tg;
       }
-      be[0] = __shfl_sync(0xffffffffu, cross ? al[1] : al[0], p0);
-      be[1] = __shfl_sync(0xffffffffu, cross ? al[0] : al[1], p1);
-      float2 g = make_float2(0.f, 0.f);
+      if (np > 1) {                                // one place around the circle
+        const int sp = lane > 0 ? lane - 1 : 0, sn = lane + 1 < np ? lane + 1 : lane;
 #pragma unroll
-      for (int k = 0; k < ROWS; ++k) {
-        g.x = __fmaf_rn(b[0][k], pb[0][k], g.x);
-        g.y = __fmaf_rn(b[1][k], pb[1][k], g.y);
-      }
-      g = jw_sum(g, xb, &ph, JwAddF2());
-      float c[2], sn[2], tg[2];
+        for (int k = 0; k < JW_PROWS; ++k) {
+          const float pt = __shfl_sync(0xffffffffu, lane == 0 ? bb[k] : bt[k], sp);
+          const float pb = __shfl_sync(0xffffffffu, bb[k], sn);
+          const float own = bt[k];
+          bt[k] = lane == 0 ? own : pt;
+          bb[k] = lane == np - 1 ? own : pb;
+        }
+        if (WJ) {
 #pragma unroll
-      for (int sl = 0; sl < 2; ++sl) {
-        const int col = lane + 32 * sl;
-        const int pcol = cross ? (sl ? p1 : p0 + 32) : ((sl ? p1 : p0) + 32 * sl);
-        const float gg = sl ? g.y : g.x;
-        const float pr = al[sl] * be[sl];
-        const bool ok = pcol != col && pcol < nc && col < nc && fabsf(gg) > abs_thr && pr > 0.f;
-        const float rel = ok ? fabsf(gg) * rsqrtf(pr) : 0.f;
-        lmax = fmaxf(lmax, rel);
-        const bool lo = col < pcol;
-        float cc, ss, tt;
-        jw_rotation(lo ? al[sl] : be[sl], lo ? be[sl] : al[sl], gg, &cc, &ss, &tt);
-        const bool rot = rel > tol;
-        c[sl] = rot ? cc : 1.f;
-        sn[sl] = rot ? (lo ? -ss : ss) : 0.f;
-        tg[sl] = rot ? (lo ? -(tt * gg) : tt * gg) : 0.f;
-      }
-#pragma unroll
-      for (int k = 0; k < ROWS; ++k) {
-        b[0][k] = c[0] * b[0][k] + sn[0] * pb[0][k];
-        b[1][k] = c[1] * b[1][k] + sn[1] * pb[1][k];
-      }
-      al[0] += tg[0];
-      al[1] += tg[1];
-      if (WJ) {
-#pragma unroll
-        for (int k = 0; k < JW_JROWS2; ++k) {
-          const float q0 = __shfl_sync(0xffffffffu, cross ? v[1][k] : v[0][k], p0);
-          const float q1 = __shfl_sync(0xffffffffu, cross ? v[0][k] : v[1][k], p1);
-          v[0][k] = c[0] * v[0][k] + sn[0] * q0;
-          v[1][k] = c[1] * v[1][k] + sn[1] * q1;
+          for (int k = 0; k < JW_PROWS; ++k) {
+            const float pt = __shfl_sync(0xffffffffu, lane == 0 ? vb[k] : vt[k], sp);
+            const float pb = __shfl_sync(0xffffffffu, vb[k], sn);
+            const float own = vt[k];
+            vt[k] = lane == 0 ? own : pt;
+            vb[k] = lane == np - 1 ? own : pb;
+          }
+        }
+        {
+          const float pt = __shfl_sync(0xffffffffu, lane == 0 ? ab : at, sp);
+          const float pb = __shfl_sync(0xffffffffu, ab, sn);
+          const int qt = __shfl_sync(0xffffffffu, lane == 0 ? ib : it, sp);
+          const int qb = __shfl_sync(0xffffffffu, ib, sn);
+          const float oa = at;
+          const int oi = it;
+          at = lane == 0 ? oa : pt;
+          ab = lane == np - 1 ? oa : pb;
+          it = lane == 0 ? oi : qt;
+          ib = lane == np - 1 ? oi : qb;
         }
       }
     }
@@ -930,122 +926,135 @@ __device__ __forceinline__ void jacobi_f32_cols2(float* Bf, float* Jf, int nr, i
     if (mrel <= tol || mrel < stop) break;
   }
 #pragma unroll
-  for (int sl = 0; sl < 2; ++sl) {
-    const int c = lane + 32 * sl;
-#pragma unroll
-    for (int k = 0; k < ROWS; ++k) {
-      const int i = warp + JW_WARPS * k;
-      if (c < nc && i < nr) Bf[c * ld + i] = b[sl][k];
+  for (int k = 0; k < JW_PROWS; ++k) {
+    const int i = warp + JW_WARPS * k;
+    if (lane < np && i < nr) {
+      if (it < nc) Bf[it * ld + i] = bt[k];
+      if (ib < nc) Bf[ib * ld + i] = bb[k];
     }
-    if (WJ) {
-#pragma unroll
-      for (int k = 0; k < JW_JROWS2; ++k) {
-        const int i = warp + JW_WARPS * k;
-        if (c < nc && i < nc) Jf[c * ld + i] = v[sl][k];
-      }
+    if (WJ && lane < np && i < nc) {
+      if (it < nc) Jf[it * ld + i] = vt[k];
+      if (ib < nc) Jf[ib * ld + i] = vb[k];
     }
   }
   __syncthreads();
 }
 
-template <int ROWS, bool WJ>
-__device__ __forceinline__ void jacobi_df_cols2(float2* Bd, float2* Jd, int nr, int nc, int ld,
+// Double-float sweeps on column pairs (same layout and schedule as jacobi_f32_pairs; same
+// contract as jacobi_df_cols): the tangent from the hi parts in FP32, c = (1 + t^2)^-1/2
+// refined by one Newton step in double-float.
+template <bool WJ>
+__device__ __forceinline__ void jacobi_df_pairs(float2* Bd, float2* Jd, int nr, int nc, int ld,
                                                 float tol, float stop, int max_sweeps,
                                                 float2* nrm_out = nullptr) {
   float4* xd = jw_buffer4();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mm = nc + (nc & 1), np = mm >> 1;
   int ph = 0;
   const float2 z2 = make_float2(0.f, 0.f);
-  float2 b[2][ROWS], v[2][WJ ? JW_JROWS2 : 1];
+  int it = lane, ib = lane + np;
+  float2 bt[JW_PROWS], bb[JW_PROWS], vt[WJ ? JW_PROWS : 1], vb[WJ ? JW_PROWS : 1];
 #pragma unroll
-  for (int sl = 0; sl < 2; ++sl) {
-    const int c = lane + 32 * sl;
+  for (int k = 0; k < JW_PROWS; ++k) {
+    const int i = warp + JW_WARPS * k;
+    const bool on = lane < np;
+    bt[k] = (on && it < nc && i < nr) ? Bd[it * ld + i] : z2;
+    bb[k] = (on && ib < nc && i < nr) ? Bd[ib * ld + i] : z2;
+  }
+  if (WJ) {
 #pragma unroll
-    for (int k = 0; k < ROWS; ++k) {
+    for (int k = 0; k < (WJ ? JW_PROWS : 1); ++k) {
       const int i = warp + JW_WARPS * k;
-      b[sl][k] = (c < nc && i < nr) ? Bd[c * ld + i] : z2;
-    }
-    if (WJ) {
-#pragma unroll
-      for (int k = 0; k < (WJ ? JW_JROWS2 : 1); ++k) {
-        const int i = warp + JW_WARPS * k;
-        v[sl][k] = (c < nc && i < nc) ? Jd[c * ld + i] : z2;
-      }
+      const bool on = lane < np && i < nc;
+      vt[k] = (on && it < nc) ? Jd[it * ld + i] : z2;
+      vb[k] = (on && ib < nc) ? Jd[ib * ld + i] : z2;
     }
   }
   __syncthreads();
-  float2 al[2] = {z2, z2};
+  float2 at = z2, ab = z2;
   float abs_thr = 0.f;
   for (int sweep = 0; sweep < max_sweeps && nc > 1; ++sweep) {
     {
       float2 t0 = z2, t1 = z2;
 #pragma unroll
-      for (int k = 0; k < ROWS; ++k) {
-        t0 = df_add(t0, df_mul_sym(b[0][k], b[0][k]));
-        t1 = df_add(t1, df_mul_sym(b[1][k], b[1][k]));
+      for (int k = 0; k < JW_PROWS; ++k) {
+        t0 = df_add(t0, df_mul_sym(bt[k], bt[k]));
+        t1 = df_add(t1, df_mul_sym(bb[k], bb[k]));
       }
       const float4 t = jw_sum(make_float4(t0.x, t0.y, t1.x, t1.y), xd, &ph, JwAddDF2());
-      al[0] = make_float2(t.x, t.y); al[1] = make_float2(t.z, t.w);
-      if (sweep == 0) abs_thr = 1e-30f * warp_sum_t(al[0].x + al[1].x);
+      at = make_float2(t.x, t.y); ab = make_float2(t.z, t.w);
+      if (sweep == 0) abs_thr = 1e-30f * warp_sum_t(lane < np ? at.x + ab.x : 0.f);
     }
     float lmax = 0.f;
-    for (int r = 0; r < 63; ++r) {
-      int p0, p1;
-      bool cross;
-      jw2_partners(lane, r, &p0, &p1, &cross);
-      float2 pb[2][ROWS], be[2];
+    for (int r = 0; r < mm - 1; ++r) {
+      float2 g0 = z2;
 #pragma unroll
-      for (int k = 0; k < ROWS; ++k) {
-        pb[0][k] = df_shfl(0xffffffffu, cross ? b[1][k] : b[0][k], p0);
-        pb[1][k] = df_shfl(0xffffffffu, cross ? b[0][k] : b[1][k], p1);
-      }
-      be[0] = df_shfl(0xffffffffu, cross ? al[1] : al[0], p0);
-      be[1] = df_shfl(0xffffffffu, cross ? al[0] : al[1], p1);
-      float2 g0 = z2, g1 = z2;
-#pragma unroll
-      for (int k = 0; k < ROWS; ++k) {
-        g0 = df_add(g0, df_mul_sym(b[0][k], pb[0][k]));
-        g1 = df_add(g1, df_mul_sym(b[1][k], pb[1][k]));
-      }
-      const float4 gs = jw_sum(make_float4(g0.x, g0.y, g1.x, g1.y), xd, &ph, JwAddDF2());
-      const float2 g[2] = {make_float2(gs.x, gs.y), make_float2(gs.z, gs.w)};
-      float2 c[2], sn[2], tg[2];
-#pragma unroll
-      for (int sl = 0; sl < 2; ++sl) {
-        const int col = lane + 32 * sl;
-        const int pcol = cross ? (sl ? p1 : p0 + 32) : ((sl ? p1 : p0) + 32 * sl);
-        const float pr = al[sl].x * be[sl].x;
-        const bool ok = pcol != col && pcol < nc && col < nc && fabsf(g[sl].x) > abs_thr && pr > 0.f;
-        const float rel = ok ? fabsf(g[sl].x) * rsqrtf(pr) : 0.f;
-        lmax = fmaxf(lmax, rel);
-        const bool lo = col < pcol;
-        const float2 a_lo = lo ? al[sl] : be[sl], a_hi = lo ? be[sl] : al[sl];
+      for (int k = 0; k < JW_PROWS; ++k) g0 = df_add(g0, df_mul_sym(bt[k], bb[k]));
+      const float4 gs = jw_sum(make_float4(g0.x, g0.y, 0.f, 0.f), xd, &ph, JwAddDF2());
+      const float2 g = make_float2(gs.x, gs.y);
+      const float pr = at.x * ab.x;
+      const bool ok = lane < np && it < nc && ib < nc && fabsf(g.x) > abs_thr && pr > 0.f;
+      const float rel = ok ? fabsf(g.x) * rsqrtf(pr) : 0.f;
+      lmax = fmaxf(lmax, rel);
+      const bool lo = it < ib;
+      if (rel > tol) {
+        const float2 a_lo = lo ? at : ab, a_hi = lo ? ab : at;
         float c32, s32, t;
-        jw_rotation(0.f, df_add(a_hi, df_neg(a_lo)).x, g[sl].x, &c32, &s32, &t);
-        const bool rot = rel > tol;
+        jw_rotation(0.f, df_add(a_hi, df_neg(a_lo)).x, g.x, &c32, &s32, &t);
         const float2 w = df_add(make_float2(1.f, 0.f), df_mulf(make_float2(t, 0.f), t));
         const float y0 = rsqrtf(w.x);
         const float2 h = df_add(make_float2(1.f, 0.f), df_neg(df_mulf(df_mulf(w, y0), y0)));
-        float2 cc = df_add(make_float2(y0, 0.f), df_mulf(h, 0.5f * y0));
-        const float2 ss = df_mulf(cc, t), gt = df_mulf(g[sl], t);
-        c[sl] = rot ? cc : make_float2(1.f, 0.f);
-        sn[sl] = rot ? (lo ? df_neg(ss) : ss) : z2;
-        tg[sl] = rot ? (lo ? df_neg(gt) : gt) : z2;
-      }
+        const float2 cc = df_add(make_float2(y0, 0.f), df_mulf(h, 0.5f * y0));
+        const float2 ss = df_mulf(cc, t), gt = df_mulf(g, t);
+        const float2 st = lo ? df_neg(ss) : ss;    // top' = c top + st bot, bot' = c bot - st top
 #pragma unroll
-      for (int k = 0; k < ROWS; ++k) {
-        b[0][k] = df_add(df_mul(c[0], b[0][k]), df_mul(sn[0], pb[0][k]));
-        b[1][k] = df_add(df_mul(c[1], b[1][k]), df_mul(sn[1], pb[1][k]));
-      }
-      al[0] = df_add(al[0], tg[0]);
-      al[1] = df_add(al[1], tg[1]);
-      if (WJ) {
+        for (int k = 0; k < JW_PROWS; ++k) {
+          const float2 x = bt[k], y = bb[k];
+          bt[k] = df_add(df_mul(cc, x), df_mul(st, y));
+          bb[k] = df_add(df_mul(cc, y), df_neg(df_mul(st, x)));
+        }
+        if (WJ) {
 #pragma unroll
-        for (int k = 0; k < (WJ ? JW_JROWS2 : 1); ++k) {
-          const float2 q0 = df_shfl(0xffffffffu, cross ? v[1][k] : v[0][k], p0);
-          const float2 q1 = df_shfl(0xffffffffu, cross ? v[0][k] : v[1][k], p1);
-          v[0][k] = df_add(df_mul(c[0], v[0][k]), df_mul(sn[0], q0));
-          v[1][k] = df_add(df_mul(c[1], v[1][k]), df_mul(sn[1], q1));
+          for (int k = 0; k < (WJ ? JW_PROWS : 1); ++k) {
+            const float2 x = vt[k], y = vb[k];
+            vt[k] = df_add(df_mul(cc, x), df_mul(st, y));
+            vb[k] = df_add(df_mul(cc, y), df_neg(df_mul(st, x)));
+          }
+        }
+        at = df_add(at, lo ? df_neg(gt) : gt);
+        ab = df_add(ab, lo ? gt : df_neg(gt));
+      }
+      if (np > 1) {
+        const int sp = lane > 0 ? lane - 1 : 0, sn = lane + 1 < np ? lane + 1 : lane;
+#pragma unroll
+        for (int k = 0; k < JW_PROWS; ++k) {
+          const float2 pt = df_shfl(0xffffffffu, lane == 0 ? bb[k] : bt[k], sp);
+          const float2 pb = df_shfl(0xffffffffu, bb[k], sn);
+          const float2 own = bt[k];
+          bt[k] = lane == 0 ? own : pt;
+          bb[k] = lane == np - 1 ? own : pb;
+        }
+        if (WJ) {
+#pragma unroll
+          for (int k = 0; k < (WJ ? JW_PROWS : 1); ++k) {
+            const float2 pt = df_shfl(0xffffffffu, lane == 0 ? vb[k] : vt[k], sp);
+            const float2 pb = df_shfl(0xffffffffu, vb[k], sn);
+            const float2 own = vt[k];
+            vt[k] = lane == 0 ? own : pt;
+            vb[k] = lane == np - 1 ? own : pb;
+          }
+        }
+        {
+          const float2 pt = df_shfl(0xffffffffu, lane == 0 ? ab : at, sp);
+          const float2 pb = df_shfl(0xffffffffu, ab, sn);
+          const int qt = __shfl_sync(0xffffffffu, lane == 0 ? ib : it, sp);
+          const int qb = __shfl_sync(0xffffffffu, ib, sn);
+          const float2 oa = at;
+          const int oi = it;
+          at = lane == 0 ? oa : pt;
+          ab = lane == np - 1 ? oa : pb;
+          it = lane == 0 ? oi : qt;
+          ib = lane == np - 1 ? oi : qb;
         }
       }
     }
@@ -1055,29 +1064,31 @@ __device__ __forceinline__ void jacobi_df_cols2(float2* Bd, float2* Jd, int nr, 
   if (nrm_out) {
     float2 t0 = z2, t1 = z2;
 #pragma unroll
-    for (int k = 0; k < ROWS; ++k) {
-      t0 = df_add(t0, df_mul_sym(b[0][k], b[0][k]));
-      t1 = df_add(t1, df_mul_sym(b[1][k], b[1][k]));
+    for (int k = 0; k < JW_PROWS; ++k) {
+      t0 = df_add(t0, df_mul_sym(bt[k], bt[k]));
+      t1 = df_add(t1, df_mul_sym(bb[k], bb[k]));
     }
     const float4 t = jw_sum(make_float4(t0.x, t0.y, t1.x, t1.y), xd, &ph, JwAddDF2());
-    if (warp == 0) {
-      if (lane < nc) nrm_out[lane] = make_float2(t.x, t.y);
-      if (lane + 32 < nc) nrm_out[lane + 32] = make_float2(t.z, t.w);
+    if (warp == 0 && lane < np) {
+      if (it < nc) nrm_out[it] = make_float2(t.x, t.y);
+      if (ib < nc) nrm_out[ib] = make_float2(t.z, t.w);
     }
   }
 #pragma unroll
-  for (int sl = 0; sl < 2; ++sl) {
-    const int c = lane + 32 * sl;
-#pragma unroll
-    for (int k = 0; k < ROWS; ++k) {
-      const int i = warp + JW_WARPS * k;
-      if (c < nc && i < nr) Bd[c * ld + i] = b[sl][k];
+  for (int k = 0; k < JW_PROWS; ++k) {
+    const int i = warp + JW_WARPS * k;
+    if (lane < np && i < nr) {
+      if (it < nc) Bd[it * ld + i] = bt[k];
+      if (ib < nc) Bd[ib * ld + i] = bb[k];
     }
-    if (WJ) {
+  }
+  if (WJ) {
 #pragma unroll
-      for (int k = 0; k < (WJ ? JW_JROWS2 : 1); ++k) {
-        const int i = warp + JW_WARPS * k;
-        if (c < nc && i < nc) Jd[c * ld + i] = v[sl][k];
+    for (int k = 0; k < (WJ ? JW_PROWS : 1); ++k) {
+      const int i = warp + JW_WARPS * k;
+      if (lane < np && i < nc) {
+        if (it < nc) Jd[it * ld + i] = vt[k];
+        if (ib < nc) Jd[ib * ld + i] = vb[k];
       }
     }
   }
@@ -1256,7 +1267,7 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
   if (m <= 32 && blockDim.x == DD_THREADS)
     jacobi_f32_cols<JW_JROWS, true>(B32, J32, m, m, ld, 1e-6f, 1e-3f, 30);
   else if (m <= 64 && blockDim.x == DD_THREADS)
-    jacobi_f32_cols2<64 / JW_WARPS, true>(B32, J32, m, m, ld, 1e-6f, 1e-3f, 30);
+    jacobi_f32_pairs<true>(B32, J32, m, m, ld, 1e-6f, 1e-3f, 30);
   else
     jacobi_f32(B32, J32, m, ld, flag, n32, 1e-6f, 1e-3f, 30);
   for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) Jd[e] = make_float2(J32[e], 0.f);
@@ -1279,7 +1290,7 @@ __device__ __forceinline__ void jacobi_svd_mixed(double* Bc, double* Jc, int m, 
   if (m <= 32 && blockDim.x == DD_THREADS)
     jacobi_df_cols<JW_JROWS, true>(Bd, Jd, m, m, ld, 1e-13f, 3e-7f, 10);
   else if (m <= 64 && blockDim.x == DD_THREADS)
-    jacobi_df_cols2<64 / JW_WARPS, true>(Bd, Jd, m, m, ld, 1e-13f, 3e-7f, 10);
+    jacobi_df_pairs<true>(Bd, Jd, m, m, ld, 1e-13f, 3e-7f, 10);
   else
     jacobi_df(Bd, Jd, m, ld, flag, T, 1e-13f, 3e-7f, 10);
   for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
@@ -1331,7 +1342,7 @@ __device__ __forceinline__ void orth_cols_mixed(double* X, int nr, int nc, int l
   }
   __syncthreads();
   if (nc > 32)                                          // then nr >= nc > 32
-    jacobi_f32_cols2<64 / JW_WARPS, true>(B32, J32, nr, nc, ld, 1e-6f, 1e-3f, 30);
+    jacobi_f32_pairs<true>(B32, J32, nr, nc, ld, 1e-6f, 1e-3f, 30);
   else if (nr <= 32)
     jacobi_f32_cols<32 / JW_WARPS, true>(B32, J32, nr, nc, ld, 1e-6f, 1e-3f, 30);
   else
@@ -1351,7 +1362,7 @@ __device__ __forceinline__ void orth_cols_mixed(double* X, int nr, int nc, int l
     }
   __syncthreads();
   if (nc > 32)
-    jacobi_df_cols2<64 / JW_WARPS, false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10, nd);
+    jacobi_df_pairs<false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10, nd);
   else if (nr <= 32)
     jacobi_df_cols<32 / JW_WARPS, false>(Bd, nullptr, nr, nc, ld, 1e-13f, 3e-7f, 10, nd);
   else

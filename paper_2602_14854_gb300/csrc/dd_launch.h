@@ -13,7 +13,7 @@ enum KernelSlot {
   KS_GHOST, KS_KSTEP_ADV, KS_SP_COEFFS, KS_SSTEP_ADV, KS_LSTEP_ADV, KS_GRAM, KS_TRUNC,
   KS_COLL_RANK, KS_COLL_A, KS_COLL_KSTEP, KS_COLL_SMALL, KS_COLL_LSTEP, KS_COLL_FINAL,
   KS_FLUX, KS_COPY, KS_GEIG, KS_CHOL, KS_COMPLETE, KS_MASS, KS_KC_W, KS_KC_SEL, KS_KC_APPLY,
-  KS_TC_TALL, KS_TC_GRAM, KS_TC_LSTEP, KS_OZ_TALL, KS_OZ_GRAM, NSLOT
+  KS_TC_TALL, KS_TC_GRAM, KS_LSTEP_PROD, KS_OZ_TALL, KS_OZ_GRAM, NSLOT
 };
 extern const char* const kSlotNames[NSLOT];
 
@@ -77,7 +77,7 @@ struct PhaseBufs {
   double* Xo; double* Vo; double* So; int* ro;
   // workspace
   double* L0;      // angular rows, ld MC
-  double* Hw;      // orthonormalisation workspace, spatial rows, ld WC
+  double* Hw;      // orthonormalisation workspace, spatial rows (at least the direction rows), ld WC
   double* Hwa;     // orthonormalisation workspace, angular rows, ld WC
   double* Vh;      // angular rows, ld RC (augmented basis)
   double* K;       // spatial rows, ld RC
@@ -144,6 +144,7 @@ struct Problem {
   // f < nf[2k] and cos(pi f (j + 1/2) / n_y) for f < nf[2k + 1], from offset spoff[k]
   const double* sptab; const long long* spoff; const int* spnf;
   int nchunk_sp, nchunk_ang;   // chunks of the two-stage reductions
+  int ochunk_sp, ochunk_ang;   // chunks of the orthonormalisations' Grams (<= nchunk_*)
   int nsm;                     // streaming multiprocessors of the device
   long Ntot;                   // spatial rows of all subdomains
 };

@@ -914,6 +914,60 @@ __global__ void __launch_bounds__(DD_THREADS) k_sstep_adv(Problem P, PhaseBufs B
 }
 
 // ---------------------------------------------------------------------------
+// L-step of the advection with explicit Euler as products over all directions.  The
+// Euler step of direction q's ODE is L_q = S2 v_q + dt kappa_q (A_s S2 v_q + g_q), with s
+// the upwind side of Omega_q, g_q = -G_lo v_q (Omega_q > 0) or G_hi v_q (Omega_q < 0) and
+// kappa_q = -c Omega_q / h.  With W_+ = A_+ S2 - G_lo and W_- = A_- S2 + G_hi it is
+// L_q = S2 v_q + dt kappa_q W_s v_q: the tall products L = V S2^T, Y_+ = V W_+^T and
+// Y_- = V W_-^T over the direction rows (on the tensor cores, FP64-accurate, where the
+// angular family's products run there), then L_q += dt kappa_q Y_s,q.  The arithmetic is
+// that of k_lstep_adv's FP64 form but for the association ((A S2) v instead of A (S2 v));
+// the reduced-precision forms take it too (FP64-accurate, and faster than their FP32 stages).
+// k_lstep_w: blockIdx.x = 0 writes W_+^T (slot VB) and S2^T (slot UB), 1 writes W_-^T
+// (slot S3T); the three slots are free between the S-step and the truncation.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DD_THREADS) k_lstep_w(Problem P, PhaseBufs B) {
+  __shared__ double s2[DD_MAXC * DD_MAXC];
+  const int k = blockIdx.y, side = blockIdx.x, RC = P.g.RC, rt = B.rt[k];
+  const double* S2 = SMB(B, P, k, SM_S2);
+  for (int e = threadIdx.x; e < rt * RC; e += blockDim.x) s2[e] = S2[e];
+  __syncthreads();
+  const double* A = SMB(B, P, k, side ? SM_AM : SM_AP);
+  const double* G = SMB(B, P, k, side ? SM_G_HI : SM_G_LO);
+  const double gs = side ? 1.0 : -1.0;
+  double* Wt = SMB(B, P, k, side ? SM_S3T : SM_VB);
+  double* St = SMB(B, P, k, SM_UB);
+  for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
+    const int i = e / RC, j = e - i * RC;            // W[i][j] -> Wt[j][i]
+    double w = 0.0;
+    if (i < rt && j < rt) {
+      for (int l = 0; l < rt; ++l) w += A[i * RC + l] * s2[l * RC + j];
+      w += gs * G[i * RC + j];
+    }
+    Wt[j * RC + i] = w;
+    if (side == 0) St[j * RC + i] = (i < rt && j < rt) ? s2[i * RC + j] : 0.0;
+  }
+}
+
+// L += dt kappa_q Y_s on the first r_t columns of every direction row (Y_+ where
+// Omega_q > 0, Y_- where Omega_q < 0; nothing where Omega_q = 0); blockIdx.y = subdomain
+__global__ void __launch_bounds__(DD_THREADS) k_lstep_comb(Problem P, PhaseBufs B, int axis,
+                                                           const double* Yp, const double* Ym) {
+  const int k = blockIdx.y, RC = P.g.RC, n = P.g.n, rt = B.rt[k];
+  const double* om = axis == 0 ? P.ox : P.oy;
+  const double hinv = 1.0 / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]);
+  const double dt = P.g.dtk[k];
+  const long base = (long)k * n * RC;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * RC; e += gridDim.x * blockDim.x) {
+    const int q = e / RC, i = e - q * RC;
+    const double oq = om[q];
+    if (i >= rt || oq == 0.0) continue;
+    const double kap = -P.c_adv * oq * hinv;
+    B.L[base + e] += dt * (kap * (oq > 0.0 ? Yp[base + e] : Ym[base + e]));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // L-step of the advection: every direction is an independent r_t-dimensional
 // linear ODE; one warp per direction, all RK stages fused.  In FP32 (TC = float) the
 // first-stage right-hand side a0 = g + A L0 is formed in FP64 (the interior and ghost
@@ -1524,7 +1578,7 @@ const char* const kSlotNames[NSLOT] = {
     "k_ghost", "k_kstep_adv", "k_sp_coeffs", "k_sstep_adv", "k_lstep_adv", "k_gram", "k_trunc",
     "k_coll_rank", "k_coll_a", "k_coll_kstep", "k_coll_small", "k_coll_lstep", "k_coll_final",
     "k_flux", "memcpy", "k_geig", "k_chol_inv", "k_complete", "k_mass_fix", "k_kc_w", "k_kc_sel",
-    "k_kc_apply", "k_tc_tall", "k_tc_gram", "k_tc_lstep", "k_oz_tall", "k_oz_gram"};
+    "k_kc_apply", "k_tc_tall", "k_tc_gram", "k_lstep_prod", "k_oz_tall", "k_oz_gram"};
 thread_local Prof* g_prof = nullptr;
 
 size_t part_elems(const Problem& P) {
@@ -1608,7 +1662,7 @@ static int gram_partials(const Problem& P, const PhaseBufs& B, cudaStream_t st, 
   GramArgs a;
   a.spatial = spatial; a.A = A; a.lda = lda; a.acnt = acnt; a.afix = 0;
   a.Bm = A; a.ldb = lda; a.bcnt = acnt; a.bfix = 0; a.b_per_sub = 1;
-  a.wrow = nullptr; a.part = B.part; a.nchunk = spatial ? P.nchunk_sp : P.nchunk_ang;
+  a.wrow = nullptr; a.part = B.part; a.nchunk = spatial ? P.ochunk_sp : P.ochunk_ang;
   a.cexp = cexp;
   a.sym = 1;
   if ((spatial ? P.ozg_sp : P.ozg_ang) &&
@@ -1718,7 +1772,7 @@ cudaError_t autotune(Problem& P, const PhaseBufs& B, cudaStream_t st, int tune_p
   if (!tune_products && !tune_chunks) return cudaSuccess;
   const int RC = P.g.RC, nsub = P.g.nsub;
   const std::vector<long> key = {nsub, P.maxN, P.g.n, RC, P.prec, P.Ntot, tune_products,
-                                 tune_chunks, P.nchunk_sp, P.nchunk_ang};
+                                 tune_chunks, P.ochunk_sp, P.ochunk_ang};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -1727,7 +1781,7 @@ cudaError_t autotune(Problem& P, const PhaseBufs& B, cudaStream_t st, int tune_p
       if (tune_products) {
         P.oz_sp = c.oz_sp; P.oz_ang = c.oz_ang; P.ozg_sp = c.ozg_sp; P.ozg_ang = c.ozg_ang;
       }
-      if (tune_chunks) { P.nchunk_sp = c.nch_sp; P.nchunk_ang = c.nch_ang; }
+      if (tune_chunks) { P.ochunk_sp = c.nch_sp; P.ochunk_ang = c.nch_ang; }
       for (int i = 0; i < 8; ++i) ms[i] = c.ms[i];
       return cudaSuccess;
     }
@@ -1791,16 +1845,17 @@ cudaError_t autotune(Problem& P, const PhaseBufs& B, cudaStream_t st, int tune_p
       if (sp) P.oz_sp = pick; else P.oz_ang = pick;
     }
     if (tune_chunks) {
-      // the Gram A^T A with its fixed-order reduction, at the heuristic's chunk count and
-      // at a half and a quarter of it (the partials buffer is sized for the heuristic's)
-      int& nch = sp ? P.nchunk_sp : P.nchunk_ang;
+      // the orthonormalisations' Gram A^T A with its fixed-order reduction, at the
+      // heuristic's chunk count and at a half and a quarter of it (the partials buffer is
+      // sized for the heuristic's; the Galerkin products keep it)
+      int& nch = sp ? P.ochunk_sp : P.ochunk_ang;
       const int h = nch;
       double best = -1.0, worst = -1.0;
       int pick = h;
       for (int cand : {h, h / 2, h / 4}) {
         if (cand < 1 || (cand != h && cand == pick)) continue;
         Problem Q = P;
-        (sp ? Q.nchunk_sp : Q.nchunk_ang) = cand;
+        (sp ? Q.ochunk_sp : Q.ochunk_ang) = cand;
         const double t = time_on(st, REPS, [&] {
           const int n = gram_partials(Q, B, st, sp, A, RC, B.keep, nullptr);
           Dst d;
@@ -1822,7 +1877,7 @@ cudaError_t autotune(Problem& P, const PhaseBufs& B, cudaStream_t st, int tune_p
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     TuneChoice c;
-    c.oz_sp = P.oz_sp; c.oz_ang = P.oz_ang; c.nch_sp = P.nchunk_sp; c.nch_ang = P.nchunk_ang;
+    c.oz_sp = P.oz_sp; c.oz_ang = P.oz_ang; c.nch_sp = P.ochunk_sp; c.nch_ang = P.ochunk_ang;
     c.ozg_sp = P.ozg_sp; c.ozg_ang = P.ozg_ang;
     for (int i = 0; i < 8; ++i) c.ms[i] = ms[i];
     g_tune_cache[key] = c;
@@ -2046,15 +2101,29 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   }
   pend(st);
   // 9. L-step
-  pbeg(st, KS_LSTEP_ADV);
-  if (P.prec >= PREC_MIXED) {
-    k_lstep_adv<float><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, lstep_smem(RC),
-                  st>>>(P, B, axis);
+  if (P.integrator == 0 && P.oz_ang) {
+    // as three products over the direction rows (k_lstep_w), FP64-accurate in every form
+    pbeg(st, KS_LSTEP_PROD);
+    k_lstep_w<<<dim3(2, nsub), DD_THREADS, 0, st>>>(P, B);
+    pend(st);
+    tall(P, B, st, 0, B.Vh, RC, B.rt, 0, nullptr, SM_UB, B.rt, 0, B.L, RC);
+    tall(P, B, st, 0, B.Vh, RC, B.rt, 0, nullptr, SM_VB, B.rt, 0, B.Hwa, RC);
+    tall(P, B, st, 0, B.Vh, RC, B.rt, 0, nullptr, SM_S3T, B.rt, 0, B.Hw, RC);
+    pbeg(st, KS_LSTEP_PROD);
+    k_lstep_comb<<<dim3(std::max(1, 4 * P.nsm / nsub), nsub), DD_THREADS, 0, st>>>(P, B, axis,
+                                                                                   B.Hwa, B.Hw);
+    pend(st);
   } else {
-    k_lstep_adv<double><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, lstep_smem(RC),
-                  st>>>(P, B, axis);
+    pbeg(st, KS_LSTEP_ADV);
+    if (P.prec >= PREC_MIXED) {
+      k_lstep_adv<float><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, lstep_smem(RC),
+                    st>>>(P, B, axis);
+    } else {
+      k_lstep_adv<double><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, lstep_smem(RC),
+                    st>>>(P, B, axis);
+    }
+    pend(st);
   }
-  pend(st);
   // 10. QR of L
   {
     OrthArgs a = orth_args(P, B, 0, ORTH_QR);

@@ -880,17 +880,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
 // G_c = A_c^T A_c over a chunk of rows, with the chunks and the output of k_gram: one
 // RC x RC partial per (subdomain, chunk), zero outside the ma x ma block; with chunk
 // exponents, the Gram of 2^-e A_c (e = the chunk's scale when it is far from 1; INT_MIN for a
-// chunk below 2^-1000).  The chunk's rows are taken in stages of 64: in each stage every
-// column i is bounded by 2^c_i, the values become 7 balanced base-256 digits relative to their
-// column's bound (as for the tall products), and the digit products of orders s, t accumulate
-// exactly into TMEM accumulator s + t: the digit planes of A'^T (K = the stage's rows) serve
-// as both operands, and 64 terms of at most 7 pairs stay below 2^24.  Each stage is read out
-// (the upper triangle), combined in 64-bit integers, made FP64 with the stage's scales and
-// added into per-thread FP64 accumulators; a chunk's partial is written when its last stage
-// has been read out.  Stages alternate between two plane buffers so that a stage's MMAs
-// overlap the next stage's loads and conversion.  Persistent CTAs (one per SM: 16 worker
-// warps and one MMA-issue warp) walk the (subdomain, chunk) items.
+// chunk below 2^-1000).  A pre-pass over the chunk's rows bounds every column i by 2^c_i;
+// the values become 7 balanced base-256 digits relative to 2^(c_i + 1) (as for the tall
+// products, one bit higher, so that every digit, the leading one included, is in
+// [-128, 128]), and the chunk's rows are taken in stages of 64 (double-buffered digit
+// planes of A'^T, the K dimension of the stage's MMAs).
+// The M = 128 A operand of an MMA starting at plane s1 covers h = 128 / P consecutive
+// planes (P = the padded column count): lanes u P .. u P + P - 1 ("band" u) hold plane
+// s1 + u.  One MMA per s1 in {0, h, 2h, ..} with the B operand's planes t = 0 .. 6 - s1
+// stacked along N (accumulator column block s1 + t) therefore serves every band at once:
+// in band u, column block c accumulates the digit pairs (s, t) of order s + t = c + u.
+// At most 4 pairs of products <= 2^14 meet in one band's block, so 128 rows (two stages)
+// stay below 2^24 and exact in FP32: the accumulators are read out every two stages.  The
+// read-out combines each band's blocks in 64-bit integers (< 2^62), exchanges the bands
+// through the free plane buffer (rows padded to P + 1 entries), sums them in a fixed order and adds the result, made FP64
+// with the chunk's column scales, to per-thread FP64 accumulators (thread t owns the
+// upper-triangle entries t + 512 m of the P x P block); a chunk's partial is written after
+// its last read-out.  Persistent CTAs (one per SM: 16 worker warps, one MMA-issue warp)
+// walk the (subdomain, chunk) items.
 #define OG_KS 64                          // rows per stage (K of one stage's MMAs)
+#define OG_RO 2                           // stages per read-out (128 rows)
 #define OG_PAD (128 * 2 * OG_KS)          // the M = 128 A operand reads past the last plane
 
 struct OzGram {
@@ -903,9 +912,16 @@ struct OzGram {
   unsigned* status;
 };
 
-// what a stage's read-out needs to know
-struct OgStage {
-  int k, c, ma, P, ex, cb, last;
+// dynamic shared memory of k_oz_gram for a column capacity RC <= DD_MAXC: two plane buffers
+// (and the alignment slack); at most 147.6 KB, beside 5.2 KB of static shared memory
+static size_t og_smem(int RC) {
+  const int PMAX = (RC + 15) / 16 * 16;
+  return 128 + 2 * ((size_t)OZ_DIG * PMAX * 2 * OG_KS + OG_PAD);
+}
+
+// what a read-out needs to know
+struct OgGroup {
+  int k, c, ma, P, ex, last, cp;
 };
 
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gram(OzGram a) {
@@ -916,9 +932,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gram(OzGram a) {
   const uint32_t BUF = OZ_DIG * PMAX * 2 * OG_KS + OG_PAD;
   __shared__ uint64_t bar_mma[2];
   __shared__ uint32_t tmem_s;
-  __shared__ int cs[2][DD_MAXC];                 // column bound exponents of the stage (parity)
-  __shared__ int cred[8][DD_MAXC];
-  __shared__ long long mred[OZ_WARPS];
+  __shared__ int cs[2][DD_MAXC];                 // column bound exponents (item parity)
+  __shared__ long long cred[8][DD_MAXC];
+  __shared__ long long cmb[DD_MAXC];             // column maxima (bits) of the item
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool worker = warp < OZ_WARPS;
   const int nitems = a.g.nsub * a.nchunk;
@@ -928,96 +944,114 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gram(OzGram a) {
     tc::mbar_init(&bar_mma[1], 1);
     tc::mbar_init_fence();
   }
-  if (warp == 0) tc::tmem_alloc(&tmem_s, 512);   // OZ_DIG accumulators of up to 64 columns
+  if (warp == 0) tc::tmem_alloc(&tmem_s, 512);   // OZ_DIG column blocks of up to 64 columns
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_s;
   bool alive = true;
   int ns = 0;                                    // stages issued
-  bool pending = false;                          // a stage issued, not yet read out
-  OgStage prev{};
-  double acc[16];
+  int gs = 0;                                    // stages in the open read-out group
+  int cp = 0;                                    // item parity (cs)
+  bool pending = false;                          // a closed group not yet read out
+  OgGroup prev{};
+  double acc[8];
 #pragma unroll
-  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+  for (int m = 0; m < 8; ++m) acc[m] = 0.0;
   auto wait_stage = [&](int j) {
     alive = tc::mbar_wait(&bar_mma[j & 1], (j >> 1) & 1, kWait) && alive;
   };
-  // read out stage prev (its MMAs complete) into acc; write the chunk's partial after its
-  // last stage.  Worker warp w: TMEM lanes 32 (w % 4) .. (rows i < 64: w % 4 < 2), 4-column
-  // groups 4 (w / 4) + 16 t.
-  auto finish_prev = [&]() {
+  // read out the closed group prev (its MMAs complete) into acc; write the chunk's partial
+  // after its last group.  Scratch: the planes buffer of the group's last stage.
+  auto readout = [&]() {
     wait_stage(ns - 1);
     tc::fence_after_sync();
-    const int q4 = warp & 3, i = q4 * 32 + lane;
-    if (worker && q4 < 2) {
+    const int P = prev.P, h = 128 / P, nb = h < OZ_DIG ? h : OZ_DIG;
+    long long* X = reinterpret_cast<long long*>(buf0 + (size_t)((ns - 1) & 1) * BUF);
+    if (worker) {
+      // worker warp w: TMEM lanes 32 (w % 4) .. (band u = lane / P, row i), 4-column groups
+      // 4 (w / 4) + 16 t
+      const int q4 = warp & 3, L = q4 * 32 + lane, u = L / P, i = L - u * P;
+      const bool lv = u < nb && i < prev.ma;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int c0 = 4 * (warp >> 2) + 16 * t;
-        if (c0 >= prev.P || c0 + 3 < q4 * 32) continue;     // warp-uniform
+        if (c0 >= P) continue;                   // warp-uniform
         uint32_t D[OZ_DIG][4];
 #pragma unroll
-        for (int g = 0; g < OZ_DIG; ++g)
-          oz_tmem_ld4(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * prev.P + c0), D[g]);
+        for (int c = 0; c < OZ_DIG; ++c)
+          oz_tmem_ld4(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(c * P + c0), D[c]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int g = 0; g < OZ_DIG; ++g)
+        for (int c = 0; c < OZ_DIG; ++c)
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) asm volatile("" : "+r"(D[g][jj]));
+          for (int jj = 0; jj < 4; ++jj) asm volatile("" : "+r"(D[c][jj]));
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
           const int j = c0 + jj;
-          if (i < prev.ma && j < prev.ma && j >= i && alive) {
+          if (lv && j < prev.ma && j >= i) {
             long long J = 0;
 #pragma unroll
-            for (int g = 0; g < OZ_DIG - 1; ++g)
-              J += (long long)__float2int_rn(__uint_as_float(D[g][jj])) << (40 - 8 * g);
-            J += (long long)(__float2int_rn(__uint_as_float(D[OZ_DIG - 1][jj])) >> 8);
-            acc[4 * t + jj] += oz_to_f64(J, cs[prev.cb][i] + cs[prev.cb][j] - 56 - 2 * prev.ex);
+            for (int c = 0; c < OZ_DIG; ++c) {
+              const int g = c + u;                 // the digit order this block holds
+              const int d = __float2int_rn(__uint_as_float(D[c][jj]));
+              if (g < OZ_DIG - 1) J += (long long)d << (40 - 8 * g);
+              else if (g == OZ_DIG - 1) J += (long long)(d >> 8);
+            }
+            X[(u * P + i) * (P + 1) + j] = J;
           }
+        }
+      }
+    }
+    __syncthreads();
+    if (worker && alive) {
+      const int* csr = cs[prev.cp];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int e = tid + OZ_WORKERS * m, i = e / P, j = e - i * P;
+        if (e < P * P && i < prev.ma && j < prev.ma && j >= i) {
+          long long J = 0;
+          for (int u = 0; u < nb; ++u) J += X[(u * P + i) * (P + 1) + j];
+          acc[m] += oz_to_f64(J, csr[i] + csr[j] + 2 - 56 - 2 * prev.ex);
         }
       }
     }
     if (prev.last && worker) {
       double* out = a.part + ((long)prev.k * a.nchunk + prev.c) * RC * RC;
-      if (q4 < 2 && i < prev.ma) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const int j = 4 * (warp >> 2) + 16 * t + jj;
-            if (j < prev.ma && j >= i) {
-              out[i * RC + j] = acc[4 * t + jj];
-              out[j * RC + i] = acc[4 * t + jj];
-            }
-          }
+      for (int m = 0; m < 8; ++m) {
+        const int e = tid + OZ_WORKERS * m, i = e / P, j = e - i * P;
+        if (e < P * P && i < prev.ma && j < prev.ma && j >= i) {
+          out[i * RC + j] = acc[m];
+          out[j * RC + i] = acc[m];
+        }
+        acc[m] = 0.0;
       }
       for (int e = tid; e < RC * RC; e += OZ_WORKERS) {
         const int r = e / RC, cc = e - r * RC;
         if (r >= prev.ma || cc >= prev.ma) out[e] = 0.0;
       }
-#pragma unroll
-      for (int t = 0; t < 16; ++t) acc[t] = 0.0;
     }
     tc::fence_before_sync();
     alive = __syncthreads_and(alive) != 0;
     pending = false;
   };
-  // MMAs of one stage from plane buffer b (planes of P rows): accumulator g at TMEM columns
-  // g P; the M = 128 A operand is plane s1 (rows past P are junk and never read out), the B
-  // operand planes u0 .. u0 + nu - 1 stacked along N
-  auto issue = [&](int b, int P) {
+  // MMAs of one stage from plane buffer b (planes of P rows): for s1 = 0, h, 2h, .. the
+  // A operand is planes s1 .. s1 + h - 1 (one per band; past the last plane it reads junk
+  // into blocks never read out), the B operand planes u0 .. u0 + nu - 1 (u0 + nu <= 7 - s1)
+  // stacked along N into column blocks s1 + u0 ..
+  auto issue = [&](int b, int P, bool first) {
     tc::fence_after_sync();
-    const int nper = 256 / P;
+    const int nper = 256 / P, h = 128 / P;
     const uint32_t PL = (uint32_t)P * 2 * OG_KS;
     const uint64_t d0 = tc::sdesc(tc::smem_u32(buf0 + (size_t)b * BUF), 128, 16 * OG_KS);
     for (int j = 0; j < OG_KS / 16; ++j)
-      for (int s1 = 0; s1 < OZ_DIG; ++s1)
+      for (int s1 = 0; s1 < OZ_DIG; s1 += h)
         for (int u0 = 0; u0 < OZ_DIG - s1; u0 += nper) {
           const int nu = min(nper, OZ_DIG - s1 - u0);
           tc::mma_bf16(tmem + (uint32_t)((s1 + u0) * P), d0 + ((s1 * PL + 256 * j) >> 4),
                        d0 + ((u0 * PL + 256 * j) >> 4), tc::idesc(tc::FMT_BF16, 128, nu * P),
-                       (j > 0 || s1 > 0) ? 1u : 0u);
+                       (!first || j > 0 || s1 > 0) ? 1u : 0u);
         }
     tc::mma_commit(&bar_mma[b]);
   };
@@ -1029,26 +1063,36 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gram(OzGram a) {
     const int ch = (rows + a.nchunk - 1) / a.nchunk;
     const int i0 = min(rows, c * ch), i1 = min(rows, i0 + ch);
     const int ma = a.acnt[k], P = ma <= 16 ? 16 : (ma + 15) / 16 * 16;
-    // the chunk's scale (as k_gram: the largest |entry| on the integer order of the bits)
+    // ---- pre-pass: column bounds (largest |entry| of each column on the integer order of
+    // its bits; non-finite entries other than infinities are left out) and the chunk scale,
+    // into the parity cn of cs (a pending read-out of the previous item uses parity cp)
+    const int ci = tid & 63, rg = tid >> 6, cn = cp ^ 1;
+    {
+      long long mb = 0;
+      if (worker && ci < ma)
+        for (int row = i0 + rg; row < i1; row += 8) {
+          const long long bits =
+              __double_as_longlong(a.A[(rb + row) * a.lda + ci]) & 0x7fffffffffffffffll;
+          if (bits <= 0x7ff0000000000000ll) mb = max(mb, bits);
+        }
+      if (worker) cred[rg][ci] = mb;
+    }
+    __syncthreads();
+    if (tid < DD_MAXC) {
+      long long m2 = cred[0][tid];
+#pragma unroll
+      for (int r = 1; r < 8; ++r) m2 = max(m2, cred[r][tid]);
+      const int E = (int)((unsigned long long)m2 >> 52);
+      cs[cn][tid] = E ? E - 1022 : OZ_NONE;
+      cmb[tid] = tid < ma ? m2 : 0;
+    }
+    __syncthreads();                              // cred is read before the next item's writes
     int ex = 0;
     bool zero = ma == 0 || i1 <= i0;
     if (a.cexp) {
-      long long mb = 0;
-      if (worker)
-        for (int row = i0 + warp; row < i1; row += OZ_WARPS)
-          for (int l = lane; l < ma; l += 32) {
-            const long long bits =
-                __double_as_longlong(a.A[(rb + row) * a.lda + l]) & 0x7fffffffffffffffll;
-            if (bits <= 0x7ff0000000000000ll) mb = max(mb, bits);
-          }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-      if (worker && lane == 0) mred[warp] = mb;
-      __syncthreads();
-      mb = 0;
-      for (int q = 0; q < OZ_WARPS; ++q) mb = max(mb, mred[q]);
-      __syncthreads();                            // mred is read before the next item's writes
-      const double mx = __longlong_as_double(mb);
+      long long cmx = 0;                          // the chunk's largest |entry|
+      for (int q = 0; q < DD_MAXC; ++q) cmx = max(cmx, cmb[q]);
+      const double mx = __longlong_as_double(cmx);
       const int e0 = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) : 0;
       zero = zero || !(mx > 0.0) || e0 < -1000;
       ex = (!zero && (e0 < -400 || e0 > 400)) ? e0 : 0;
@@ -1059,47 +1103,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gram(OzGram a) {
       for (int e = tid; e < RC * RC; e += OZ_THREADS) out[e] = 0.0;
       continue;
     }
+    cp = cn;
     count_work(a.g, KS_OZ_GRAM, 2.0 * (i1 - i0) * (ma * (ma + 1) / 2));
     const int nst = (i1 - i0 + OG_KS - 1) / OG_KS;
+    const int e1 = cs[cp][ci] + 1;                // this thread's column: digits relative to 2^e1
     for (int sgi = 0; sgi < nst; ++sgi) {
       const int r0 = i0 + sgi * OG_KS, b = ns & 1;
-      // ---- loads: thread (column i = tid % 64, row pairs tid / 64 + 8 t)
-      const int ci = tid & 63;
+      // ---- loads: thread (column ci, row pairs tid / 64 + 8 t)
       double2 x[4];
-      int mx = OZ_NONE;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const int rp = (tid >> 6) + 8 * t, r = r0 + 2 * rp;
+        const int rp = rg + 8 * t, r = r0 + 2 * rp;
         x[t] = make_double2(0.0, 0.0);
         if (worker && ci < ma) {
           if (r < i1) x[t].x = __ldg(a.A + (rb + r) * a.lda + ci);
           if (r + 1 < i1) x[t].y = __ldg(a.A + (rb + r + 1) * a.lda + ci);
-          const int E0 = f64_bexp(x[t].x), E1 = f64_bexp(x[t].y);
-          if (E0) mx = max(mx, E0 - 1022);
-          if (E1) mx = max(mx, E1 - 1022);
         }
       }
-      if (ns >= 2) wait_stage(ns - 2);           // buffer b's previous stage is read
-      if (worker) cred[tid >> 6][ci] = mx;
-      __syncthreads();
-      if (tid < DD_MAXC) {
-        int m2 = cred[0][tid];
-#pragma unroll
-        for (int q = 1; q < 8; ++q) m2 = max(m2, cred[q][tid]);
-        cs[b][tid] = m2;
-      }
-      __syncthreads();
+      if (ns >= 2) wait_stage(ns - 2);           // buffer b's previous stage is done
       // ---- digit planes: element (i, r) of A'^T at op_off(i, 2 (r - r0), 2 OG_KS)
       if (worker && ci < ma) {
         uint8_t* pl = buf0 + (size_t)b * BUF;
         const uint32_t PL = (uint32_t)P * 2 * OG_KS;
-        const int e = cs[b][ci];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          const int rp = (tid >> 6) + 8 * t;
+          const int rp = rg + 8 * t;
           float d0[OZ_DIG], d1[OZ_DIG];
-          oz_digits(x[t].x, e, d0);
-          oz_digits(x[t].y, e, d1);
+          oz_digits(x[t].x, e1, d0);
+          oz_digits(x[t].y, e1, d1);
           const uint32_t off = tc::op_off(ci, rp * 4, 2 * OG_KS);
 #pragma unroll
           for (int s = 0; s < OZ_DIG; ++s)
@@ -1108,17 +1139,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gram(OzGram a) {
       }
       tc::fence_async_smem();
       alive = __syncthreads_and(alive) != 0;
-      if (alive && pending) finish_prev();        // overlapped with that stage's MMAs
+      if (alive && pending) readout();            // the closed group's MMAs, under this conversion
       if (!alive) break;
-      if (tid == OZ_WORKERS) issue(b, P);
+      if (tid == OZ_WORKERS) issue(b, P, gs == 0);
       ++ns;
-      pending = true;
-      prev.k = k; prev.c = c; prev.ma = ma; prev.P = P; prev.ex = ex; prev.cb = b;
-      prev.last = sgi == nst - 1;
+      ++gs;
+      if (gs == OG_RO || sgi == nst - 1) {       // close the group
+        pending = true;
+        prev.k = k; prev.c = c; prev.ma = ma; prev.P = P; prev.ex = ex; prev.cp = cp;
+        prev.last = sgi == nst - 1;
+        gs = 0;
+      }
       __syncwarp();
     }
   }
-  if (pending && alive) finish_prev();
+  if (pending && alive) readout();
   if (!alive) {
     if (tid == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
     if (ns > 0) tc::mbar_wait(&bar_mma[(ns - 1) & 1], ((ns - 1) >> 1) & 1, kWait);
@@ -1154,7 +1189,7 @@ cudaError_t tc_init() {
                            (int)OZ_SMEM_LIMIT);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_oz_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)OZ_SMEM_LIMIT);
+                           (int)og_smem(DD_MAXC));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_tc_gram<tc::FMT_BF16>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_gram_smem());
@@ -1237,9 +1272,7 @@ bool tc_gram(const Problem& P, cudaStream_t st, const TcGram& a0) {
 bool oz_gram(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
              int lda, const int* acnt, double* part, int nchunk, int* cexp) {
   if (P.g.RC > DD_MAXC) return false;
-  const int PMAX = (P.g.RC + 15) / 16 * 16;
-  const size_t smem = 128 + 2 * ((size_t)OZ_DIG * PMAX * 2 * OG_KS + OG_PAD);
-  if (smem > OZ_SMEM_LIMIT) return false;
+  const size_t smem = og_smem(P.g.RC);
   OzGram a;
   a.g = P.g; a.spatial = spatial; a.A = A; a.lda = lda; a.acnt = acnt; a.part = part;
   a.nchunk = nchunk; a.cexp = cexp; a.status = status;

@@ -136,8 +136,8 @@ def test_small_gaussian_euler(B):
         assert rel(rho, ref.scalar_flux()) < bound, prec
 
 
-def run_products(B, wl, products, nsteps=None):
-    s = B.Solver(wl, products=products, use_graph=True)
+def run_products(B, wl, products, nsteps=None, precision="fp64"):
+    s = B.Solver(wl, products=products, use_graph=True, precision=precision)
     s.step(wl.nsteps if nsteps is None else nsteps)
     rho = s.scalar_flux()
     ranks = list(s.ranks()[0])
@@ -159,6 +159,38 @@ def test_ozaki_products_small(B, seed, cuts):
     assert ranks == ref.ranks()
     assert rel(rho, ref.scalar_flux()) < 1e-9
     assert prof["k_oz_tall"][1] > 0
+
+
+@pytest.mark.parametrize("seed,cuts", [(1, None), (4, ([0, 3, 8, 16], [0, 5, 10]))])
+def test_ozaki_lstep_products_euler(B, seed, cuts):
+    """Explicit Euler with the Ozaki products: the advection L-step runs as three products
+    over the direction rows (with S2^T, W_+^T = (A_+ S2 - G_lo)^T, W_-^T = (A_- S2 + G_hi)^T)
+    and a per-direction combination, not as k_lstep_adv; FP64 bound 1e-9 and identical
+    ranks on even and ragged tilings."""
+    from paper_2602_14854_gb300 import inputs
+    kw = {} if cuts is None else {"nx": 16, "ny": 10, "xcuts": cuts[0], "ycuts": cuts[1]}
+    wl = inputs.random_small_problem(seed, **{"nx": 8, "ny": 8, **kw}, n_mu=2, n_phi=8, rank=3,
+                                     r_aug_max=7, integrator="euler", nsteps=4)
+    ref = dd_dlra.DDDLRA(wl).run()
+    rho, ranks, prof = run_products(B, wl, "tensor")
+    assert ranks == ref.ranks()
+    assert rel(rho, ref.scalar_flux()) < 1e-9
+    assert prof["k_lstep_prod"][1] > 0 and "k_lstep_adv" not in prof
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "mixed"])
+def test_ozaki_lstep_products_reduced_forms(B, prec):
+    """The reduced-precision forms with the Ozaki products take the same FP64-accurate
+    product L-step (in place of their FP32 stages) and stay within their bounds."""
+    from paper_2602_14854_gb300 import inputs
+    wl = inputs.random_small_problem(2, nx=16, ny=10, xcuts=[0, 3, 8, 16], ycuts=[0, 5, 10],
+                                     n_mu=2, n_phi=8, rank=3, r_aug_max=7, integrator="euler",
+                                     nsteps=4)
+    ref = dd_dlra.DDDLRA(wl).run()
+    rho, ranks, prof = run_products(B, wl, "tensor", precision=prec)
+    assert ranks == ref.ranks()
+    assert rel(rho, ref.scalar_flux()) < BOUND.get(prec, 1e-5)
+    assert prof["k_lstep_prod"][1] > 0 and "k_lstep_adv" not in prof
 
 
 def test_ozaki_products_pointsource(B):
