@@ -188,11 +188,12 @@ bool tc_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, c
 bool tc_gram(const Problem& P, cudaStream_t st, const TcGram& a);
 // Y = A M to FP64 accuracy on the BF16 tensor cores (Ozaki splitting); false when the
 // operands do not suit TMA, then nothing is launched
-// (mtrans: M is read transposed, Y = A M^T, M still the RC x RC block of its slot)
+// (mtrans: M is read transposed, Y = A M^T, M still the RC x RC block of its slot;
+// accumulate: Y += A M on the columns < ncols, the others untouched)
 bool oz_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
              int lda, const int* ninner, int ninner_fix, const double* Bm, int bsmall,
              const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy,
-             int mtrans = 0);
+             int mtrans = 0, int accumulate = 0);
 // The chunk partials of the symmetric Gram A^T A (the layout and chunk exponents of k_gram)
 // FP64-accurate on the BF16 tensor cores; false when the capacity does not fit.
 bool oz_gram(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,

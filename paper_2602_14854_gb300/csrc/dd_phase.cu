@@ -634,10 +634,57 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
 // dt sum_s b_s R~_s is rotated back with P^T and added to the FP64 state.  P and lambda
 // come from k_small_adv1 (small slots S3T and VB, free until the S-step).  Same lines-
 // per-CTA layout as k_kstep_adv; the entry indices are decoded once.
-// y += x over n contiguous FP64 entries (the K-step's rotated increment)
-__global__ void k_add_flat(double* __restrict__ y, const double* __restrict__ x, long n) {
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    y[i] += x[i];
+// The explicit-Euler K-step in the eigenbasis, the stencil alone: on K~ = K P (in X1, formed
+// by a tall product) along the lines of the sweep, with the ghosts K^b P at the line ends,
+// the increment dt coef (lambda+_j (K~_c - K~_p) + lambda-_j (K~_n - K~_c)) of column j
+// (Appendix A's per-eigenvector upwinding) into Hw (zero in the columns from r_t; rotated
+// back and added to K by the next tall product).  KE1_LINES lines per CTA, a warp per cell row (lanes over
+// the columns): the same arithmetic as k_kstep_eig's one-stage form.
+#define KE1_LINES 8
+__global__ void __launch_bounds__(DD_THREADS) k_kstep_eig1(Problem P, PhaseBufs B, int axis) {
+  __shared__ double lp[DD_MAXC], ln[DD_MAXC];
+  __shared__ double gh[2][KE1_LINES][DD_MAXC];
+  const int k = blockIdx.y, RC = P.g.RC;
+  const Lines L = lines_of(P.g, k, axis);
+  const int l0 = blockIdx.x * KE1_LINES;
+  if (l0 >= L.nlines) return;
+  const int nl = min(KE1_LINES, L.nlines - l0), len = L.len, rt = B.rt[k];
+  count_work(P.g, KS_KSTEP_ADV, (double)nl * len * rt * 8.0);
+  const double* Pg = SMB(B, P, k, SM_S3T);
+  const double* lam = SMB(B, P, k, SM_VB);
+  for (int j = threadIdx.x; j < RC; j += blockDim.x) {
+    const double l = j < rt ? lam[j] : 0.0;
+    lp[j] = l > 0.0 ? l : 0.0;
+    ln[j] = l < 0.0 ? l : 0.0;
+  }
+  for (int e = threadIdx.x; e < 2 * nl * rt; e += blockDim.x) {   // ghosts in the eigenbasis
+    const int side = e >= nl * rt, r = e - side * nl * rt, li = r / rt, j = r - li * rt;
+    const double* kb = B.Kb + (((long)k * 2 + side) * P.maxlines + l0 + li) * RC;
+    double x = 0.0;
+    for (int u = 0; u < rt; ++u) x += kb[u] * Pg[u * RC + j];
+    gh[side][li][j] = x;
+  }
+  __syncthreads();
+  const double coef = -P.c_adv / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]);
+  const double dt = P.g.dtk[k];
+  const long rb = P.g.rowoff[k];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int row = warp; row < nl * len; row += nw) {
+    const int li = row / len, pos = row - li * len;
+    const long c = rb + cell_of(L, l0 + li, pos);
+    const long cp = pos > 0 ? rb + cell_of(L, l0 + li, pos - 1) : -1;
+    const long cn = pos < len - 1 ? rb + cell_of(L, l0 + li, pos + 1) : -1;
+    for (int j = lane; j < RC; j += 32) {
+      double v = 0.0;                            // whole rows: the product reads pairs of columns
+      if (j < rt) {
+        const double kc = B.X1[c * RC + j];
+        const double kp = cp >= 0 ? B.X1[cp * RC + j] : gh[0][li][j];
+        const double kn = cn >= 0 ? B.X1[cn * RC + j] : gh[1][li][j];
+        v = dt * (coef * (lp[j] * (kc - kp) + ln[j] * (kn - kc)));
+      }
+      B.Hw[c * RC + j] = v;
+    }
+  }
 }
 
 template <typename TC>
@@ -2010,26 +2057,31 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   // 6. K-step
   {
     const int len = P.maxlines;
-    // with the spatial tall products on the tensor cores and every line within the
-    // eigenbasis tile: the two basis changes as tall products (K~ = K P into X1, free until
-    // the QR; the increment's P^T into Hw, free until the orthonormalisation), the stages in
-    // the eigenbasis kernel, and K += the rotated increment in FP64 (rotating the whole K back
-    // would put rounding of K's size on entries whose increment is tiny)
-    const bool ebasis = P.kstep_split == 0 && P.oz_sp && (long)len * g.RC <= (long)DD_THREADS * KE_EPT;
+    // with the spatial tall products on the tensor cores (and, for RK4, every line within
+    // the eigenbasis tile): the two basis changes as tall products (K~ = K P into X1, free
+    // until the QR; K += increment P^T, accumulated in FP64 by the product's epilogue:
+    // rotating the whole K back would put rounding of K's size on entries whose increment is
+    // tiny), the stages in the eigenbasis in between
+    const bool euler = P.integrator == 0;
+    const bool ebasis = P.kstep_split == 0 && P.oz_sp &&
+                        (euler || (long)len * g.RC <= (long)DD_THREADS * KE_EPT);
     if (ebasis && oz_tall(P, B.status, st, 1, B.K, RC, B.rt, 0, nullptr, SM_S3T, B.sm, B.rt, 0,
                           B.X1, RC, 0)) {
-      const int lpb = kstep_eig_lpb(P, len);
-      dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
+      // the stages on K~ (the increment into Hw with Euler, in place in X1 with RK4), then
+      // K += increment P^T by the second product (the same shape as the first: it cannot be
+      // refused where that one was not)
       pbeg(st, KS_KSTEP_ADV);
-      k_kstep_eig<double><<<grid, DD_THREADS, kstep_eig_smem(P, lpb, len), st>>>(P, B, axis, lpb, 1);
+      if (euler) {
+        dim3 grid((P.maxlines + KE1_LINES - 1) / KE1_LINES, nsub);
+        k_kstep_eig1<<<grid, DD_THREADS, 0, st>>>(P, B, axis);
+      } else {
+        const int lpb = kstep_eig_lpb(P, len);
+        dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
+        k_kstep_eig<double><<<grid, DD_THREADS, kstep_eig_smem(P, lpb, len), st>>>(P, B, axis, lpb, 1);
+      }
       pend(st);
-      // the same shape as the first product: it cannot be refused where that one was not
-      (void)oz_tall(P, B.status, st, 1, B.X1, RC, B.rt, 0, nullptr, SM_S3T, B.sm, B.rt, 0, B.Hw, RC, 1);
-      const long nel = P.Ntot * RC;
-      pbeg(st, KS_KSTEP_ADV);
-      k_add_flat<<<(int)std::min<long>((nel + DD_THREADS - 1) / DD_THREADS, 4L * P.nsm), DD_THREADS, 0, st>>>(
-          B.K, B.Hw, nel);
-      pend(st);
+      (void)oz_tall(P, B.status, st, 1, euler ? B.Hw : B.X1, RC, B.rt, 0, nullptr, SM_S3T, B.sm,
+                    B.rt, 0, B.K, RC, 1, 1);
     } else {
     pbeg(st, KS_KSTEP_ADV);
     if (P.kstep_split == 0 && len < 4096) {

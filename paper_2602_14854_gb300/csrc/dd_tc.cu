@@ -704,11 +704,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int rl = 8 * i + (lane >> 2), rr = q4 * 32 + rl;
-        if (rr < t.nrow && cc < a.ldy) ybase[(long)rr * a.ldy + cc] = ebuf[rl * 5 + (lane & 3)];
+        if (rr < t.nrow && cc < a.ldy) {
+          double* yp = ybase + (long)rr * a.ldy + cc;
+          if (!a.accumulate) *yp = ebuf[rl * 5 + (lane & 3)];
+          else if (cc < t.nc) *yp += ebuf[rl * 5 + (lane & 3)];
+        }
       }
       __syncwarp();
     }
-    if (warp < 4 && a.ldy > t.N)                        // columns N .. ldy - 1
+    if (warp < 4 && a.ldy > t.N && !a.accumulate)       // columns N .. ldy - 1
       for (int e = lane; e < 32 * (a.ldy - t.N); e += 32) {
         const int rr = q4 * 32 + e / (a.ldy - t.N), c = t.N + e % (a.ldy - t.N);
         if (rr < t.nrow) ybase[(long)rr * a.ldy + c] = 0.0;
@@ -1221,14 +1225,14 @@ bool tc_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, c
 bool oz_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
              int lda, const int* ninner, int ninner_fix, const double* Bm, int bsmall,
              const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy,
-             int mtrans) {
+             int mtrans, int accumulate) {
   if (lda > DD_MAXC || (lda & 1)) return false;
   const OzPlan pl = oz_plan(lda, OZ_SMEM_LIMIT);
   if (pl.total > OZ_SMEM_LIMIT) return false;
   TcTall a;
   a.g = P.g; a.spatial = spatial; a.lda = lda; a.ninner = ninner; a.ninner_fix = ninner_fix;
   a.Bm = Bm; a.bsmall = bsmall; a.smbase = smbase; a.ncols = ncols; a.ncols_fix = ncols_fix;
-  a.Y = Y; a.ldy = ldy; a.alpha = 1.0; a.accumulate = 0; a.status = status;
+  a.Y = Y; a.ldy = ldy; a.alpha = 1.0; a.accumulate = accumulate; a.status = status;
   a.A = A;
   a.mtrans = mtrans;
   a.tps = ((spatial ? P.maxN : P.g.n) + TT_ROWS - 1) / TT_ROWS;
