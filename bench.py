@@ -282,18 +282,22 @@ def run_ours(args, torch):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s3 = binding.Solver(wl, stream=sptr, use_graph=True, **OPT)
+    t1 = time.perf_counter()
     for _ in range(args.steps):
         s3.step(1)
         s3.scalar_flux()                 # device -> host read of the step's result
+    t2 = time.perf_counter()
     s3.close()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    e2e_parts = {"create_ms": 1e3 * (t1 - t0), "steps_ms": 1e3 * (t2 - t1),
+                 "destroy_ms": 1e3 * (time.perf_counter() - t2)}
     h2d = 8 * (4 * wl.ncells + 3 * wl.n) + 4 * (len(wl.xcuts) + len(wl.ycuts))
     e2e = {"value": units * args.steps * ws / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 8 * wl.ncells,
            "note": "create (problem data from host memory; the autotuner's choices cached "
                    "from the first solver of this shape) + per step: step + scalar flux to "
-                   "host + destroy, wall clock"}
+                   "host + destroy, wall clock", "parts": e2e_parts}
 
     # ---- roofline ------------------------------------------------------------------------
     peaks = measured_peaks()

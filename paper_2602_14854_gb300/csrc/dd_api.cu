@@ -188,14 +188,32 @@ void angular_family(const dd_quadrature* q, double ssum, std::vector<double>& ta
         }
         if (nn < 1e-12 * ssum) continue;
         ++total;
-        if (count < max_count) {
-          for (int i = 0; i < n; ++i) tab.push_back(std::sqrt(q->w[i]) * c[i]);
-          ++count;
+        if (count == max_count) {                  // a candidate past the table: not complete
+          *complete = 0;
+          return;
         }
+        for (int i = 0; i < n; ++i) tab.push_back(std::sqrt(q->w[i]) * c[i]);
+        ++count;
       }
     }
   }
   *complete = (count == total) ? 1 : 0;
+}
+
+// G = T T^T of the nc leading rows of the n-column table T (device), one thread per entry
+__global__ void k_tab_gram(const double* T, int nc, int n, double* G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nc * nc) return;
+  const int i = e / nc, j = e - i * nc;
+  double y = 0.0;
+  for (int q = 0; q < n; ++q) y += T[(size_t)i * n + q] * T[(size_t)j * n + q];
+  G[e] = y;
+}
+
+// dst[i * ld] = src[i], i < n (column 0 of a row-major matrix from a compact vector)
+__global__ void k_put_col0(double* dst, int ld, const double* src, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    dst[i * ld] = src[i];
 }
 
 void free_all(dd_dlra* h) {
@@ -457,8 +475,9 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   angular_family(quad, h->ssum, tab, 4 * RC + 16, &h->angcand_complete);
   h->n_angcand = (int)(tab.size() / n);
   // the longest leading part of the table whose candidates are mutually orthogonal (to
-  // 1e-12 in cosine): only those enter the coefficient-space completion
-  h->n_angorth = dd::orthogonal_prefix(tab.data(), h->n_angcand, n, 1e-12);
+  // 1e-12 in cosine): only those enter the coefficient-space completion, which examines at
+  // most kc_bmax(RC) of them (their Gram on the device, after the upload below)
+  const int n_chk = std::min(h->n_angcand, dd::kc_bmax(RC));
 #define UP_DBL(dst, ptr, count)                                                                 \
   if (dalloc(&dst, count) != cudaSuccess ||                                                      \
       cudaMemcpy(dst, ptr, sizeof(double) * (count), cudaMemcpyHostToDevice) != cudaSuccess)     \
@@ -471,6 +490,18 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   UP_DBL(h->d_sig_t, sig_t.data(), Nt);
   UP_DBL(h->d_sQ, sQ.data(), Nt);
   UP_DBL(h->d_angcand, tab.data(), tab.size());
+  {
+    double* d_g = nullptr;
+    std::vector<double> gh((size_t)n_chk * n_chk);
+    if (n_chk > 0) {
+      if (dalloc(&d_g, gh.size()) != cudaSuccess) return bail(DD_ERR_CUDA, "device allocation failed");
+      k_tab_gram<<<(n_chk * n_chk + 255) / 256, 256>>>(h->d_angcand, n_chk, n, d_g);
+      const cudaError_t e = cudaMemcpy(gh.data(), d_g, sizeof(double) * gh.size(), cudaMemcpyDeviceToHost);
+      cudaFree(d_g);
+      if (e != cudaSuccess) return bail(DD_ERR_CUDA, "angular table Gram");
+    }
+    h->n_angorth = dd::orthogonal_prefix_gram(gh.data(), n_chk, 1e-12);
+  }
   {
     // spatial completion family (R11): per subdomain the cosines cos(pi f (i + 1/2) / n)
     // of the x and y frequencies that its first kc_bmax(RC) candidates use
@@ -552,7 +583,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   }
   ok &= dalloc(&h->d_L0, (long)nsub * n * MC) == cudaSuccess;
   const int WC = RC;
-  ok &= dalloc(&h->d_Hw, std::max(Nt, (long)nsub * n) * WC) == cudaSuccess;   // also the L-step's Y_-
+  ok &= dalloc(&h->d_Hw, Nt * WC) == cudaSuccess;
   ok &= dalloc(&h->d_Hwa, (long)nsub * n * WC) == cudaSuccess;
   ok &= dalloc(&h->d_Vh, (long)nsub * n * RC) == cudaSuccess;
   ok &= dalloc(&h->d_K, Nt * RC) == cudaSuccess;
@@ -635,9 +666,11 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   if (dd::noalloc_scratch_address(&h->d_noalloc) != cudaSuccess)
     return bail(DD_ERR_CUDA, "scratch array lookup failed");
 
-  // isotropic initial data at rank 1 (rank 0 where g0 vanishes on the subdomain)
+  // isotropic initial data at rank 1 (rank 0 where g0 vanishes on the subdomain): only
+  // column 0 of X and V is nonzero; it is uploaded compactly (staged in the orthonormalisation
+  // workspaces) and scattered on the device into both state buffers, the rest cleared there
   {
-    std::vector<double> X((size_t)Nt * RC, 0.0), V((size_t)nsub * n * RC, 0.0),
+    std::vector<double> x0((size_t)Nt, 0.0), v0((size_t)nsub * n, 0.0),
         S((size_t)nsub * RC * RC, 0.0);
     std::vector<int> r(nsub, 0);
     for (int k = 0; k < nsub; ++k) {
@@ -652,17 +685,26 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
       if (!(nn > 0.0)) continue;
       r[k] = 1;
       for (int c = 0; c < s.N; ++c)
-        X[(size_t)(s.rowoff + c) * RC] = g0[(s.cy0 + c / s.nxk) * s.fnx + s.cx0 + c % s.nxk] / nn;
-      for (int q = 0; q < n; ++q) V[((size_t)k * n + q) * RC] = sw[q] / std::sqrt(h->ssum);
+        x0[(size_t)s.rowoff + c] = g0[(s.cy0 + c / s.nxk) * s.fnx + s.cx0 + c % s.nxk] / nn;
+      for (int q = 0; q < n; ++q) v0[(size_t)k * n + q] = sw[q] / std::sqrt(h->ssum);
       S[(size_t)k * RC * RC] = nn * s.sh * std::sqrt(h->ssum);
     }
+    if (cudaMemcpy(h->d_Hw, x0.data(), sizeof(double) * x0.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_Hwa, v0.data(), sizeof(double) * v0.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(DD_ERR_CUDA, "upload initial state");
     for (int b = 0; b < 2; ++b) {
-      if (cudaMemcpy(h->d_X[b], X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-          cudaMemcpy(h->d_V[b], V.data(), sizeof(double) * V.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      if (cudaMemset(h->d_X[b], 0, sizeof(double) * (size_t)Nt * RC) != cudaSuccess ||
+          cudaMemset(h->d_V[b], 0, sizeof(double) * (size_t)nsub * n * RC) != cudaSuccess)
+        return bail(DD_ERR_CUDA, "clear initial state");
+      k_put_col0<<<256, 256>>>(h->d_X[b], RC, h->d_Hw, (long)Nt);
+      k_put_col0<<<256, 256>>>(h->d_V[b], RC, h->d_Hwa, (long)nsub * n);
+      if (cudaGetLastError() != cudaSuccess ||
           cudaMemcpy(h->d_S[b], S.data(), sizeof(double) * S.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
           cudaMemcpy(h->d_r[b], r.data(), sizeof(int) * nsub, cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(DD_ERR_CUDA, "upload initial state");
     }
+    // the staging areas are the autotuner's trial outputs next, on the solver's stream
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(DD_ERR_CUDA, "upload initial state");
     if (cudaMemset(h->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(h->d_sm, 0, sizeof(double) * (size_t)nsub * dd::NSMALL * RC * RC) != cudaSuccess ||
         cudaMemset(h->d_rx, 0, sizeof(int) * 2 * nsub) != cudaSuccess ||

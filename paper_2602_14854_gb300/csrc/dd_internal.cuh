@@ -194,25 +194,20 @@ __host__ __device__ __forceinline__ int kc_bmax(int RC) { return RC + (4 * RC + 
 __host__ __device__ __forceinline__ size_t kc_region(int RC) {
   return (size_t)(kc_bmax(RC) + RC) * RC + (size_t)(RC + 1) * kc_bmax(RC);
 }
-// Length of the longest leading run of the nc candidates tab[i * n .. i * n + n) (host
-// memory) that are mutually orthogonal to rel_tol in cosine and non-zero: only those take
-// the coefficient-space completion (a product quadrature makes the whole angular table so).
-inline int orthogonal_prefix(const double* tab, int nc, int n, double rel_tol) {
-  double* nrm = new double[nc > 0 ? nc : 1];
+// Length of the longest leading run of nc candidates that are mutually orthogonal to rel_tol
+// in cosine and non-zero, from their Gram G (nc x nc, row-major, host memory): only those
+// take the coefficient-space completion (a product quadrature makes the whole angular table
+// so).
+inline int orthogonal_prefix_gram(const double* G, int nc, double rel_tol) {
   int po = 0;
   for (; po < nc; ++po) {
-    double x = 0.0;
-    for (int q = 0; q < n; ++q) x += tab[(size_t)po * n + q] * tab[(size_t)po * n + q];
-    nrm[po] = __builtin_sqrt(x);
-    bool ok = nrm[po] > 0.0;
-    for (int i = 0; i < po && ok; ++i) {
-      double y = 0.0;
-      for (int q = 0; q < n; ++q) y += tab[(size_t)i * n + q] * tab[(size_t)po * n + q];
-      ok = __builtin_fabs(y) <= rel_tol * nrm[i] * nrm[po];
-    }
+    const double np = __builtin_sqrt(G[(size_t)po * nc + po]);
+    bool ok = np > 0.0;
+    for (int i = 0; i < po && ok; ++i)
+      ok = __builtin_fabs(G[(size_t)i * nc + po]) <=
+           rel_tol * __builtin_sqrt(G[(size_t)i * nc + i]) * np;
     if (!ok) break;
   }
-  delete[] nrm;
   return po;
 }
 
@@ -1132,13 +1127,10 @@ __device__ __forceinline__ void ns_orthogonalize_df(float2* Jd, float2* T, float
 // r_ij / 2 within clusters and on the diagonal; the error of V maps to about its square.
 // G: m x m, row-major with stride RC; V: V_ij = V[j * RC + i] (refined in place); lam: the
 // refined eigenvalues (not sorted).  S and R are symmetric (upper triangles computed,
-// mirrored); the norms that set the cluster threshold and the quotients of E (a
-// first-order correction) are taken in FP32.  Scratch X: 3 RC^2 doubles.  Block-wide.
+// mirrored); the norms that set the cluster threshold, the quotients of E (a first-order
+// correction) and the product V E are taken in FP32.  Scratch X: 3 RC^2 doubles.  Block-wide.
 static __device__ __noinline__ void refine_sym_eig(const double* G, double* V, double* lam, int m,
                                                    int RC, double* X) {
-  // S and R are symmetric (upper triangles computed, mirrored); the norms that set the
-  // cluster threshold and the quotients of E (a first-order correction) are taken in
-  // FP32.
   double* T = X;
   double* S = T + RC * RC;
   double* R = S + RC * RC;
@@ -1175,21 +1167,31 @@ static __device__ __noinline__ void refine_sym_eig(const double* G, double* V, d
   const float delta = 2.f * (sqrtf(offn) + sqrtf(gn) * sqrtf(rn));   // cluster separation
   for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = S[i * RC + i] / (1.0 - R[i * RC + i]);
   __syncthreads();
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {            // E (into T)
+  float* Ef = reinterpret_cast<float*>(T);      // E in FP32 (T = G V is dead)
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e / m, j = e % m;
-    double x = 0.5 * R[i * RC + j];
+    float x = (float)(0.5 * R[i * RC + j]);
     if (i != j) {
       const float d = (float)(lam[j] - lam[i]);
-      if (fabsf(d) > delta) x = (double)__fdividef((float)(S[i * RC + j] + lam[j] * R[i * RC + j]), d);
+      if (fabsf(d) > delta) x = __fdividef((float)(S[i * RC + j] + lam[j] * R[i * RC + j]), d);
     }
-    T[i * RC + j] = x;
+    Ef[i * RC + j] = x;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {     // V (I + E) into S (dead)
+  float* Vf = reinterpret_cast<float*>(R);      // V in FP32 (R is dead)
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e / m, j = e % m;
-    double x = V[j * RC + i];
-    for (int l = 0; l < m; ++l) x += V[l * RC + i] * T[l * RC + j];
-    S[j * RC + i] = x;
+    Vf[j * RC + i] = (float)V[j * RC + i];
+  }
+  __syncthreads();
+  // V (I + E) into S (dead): V + V E with the correction V E in FP32 (E is itself a
+  // first-order FP32 quantity of the size of V's error, so FP32 rounding of V E lies far
+  // below FP64 rounding of V)
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    float x = 0.f;
+    for (int l = 0; l < m; ++l) x = __fmaf_rn(Vf[l * RC + i], Ef[l * RC + j], x);
+    S[j * RC + i] = V[j * RC + i] + (double)x;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {

@@ -77,7 +77,7 @@ struct PhaseBufs {
   double* Xo; double* Vo; double* So; int* ro;
   // workspace
   double* L0;      // angular rows, ld MC
-  double* Hw;      // orthonormalisation workspace, spatial rows (at least the direction rows), ld WC
+  double* Hw;      // orthonormalisation workspace, spatial rows, ld WC
   double* Hwa;     // orthonormalisation workspace, angular rows, ld WC
   double* Vh;      // angular rows, ld RC (augmented basis)
   double* K;       // spatial rows, ld RC
@@ -189,16 +189,16 @@ bool tc_gram(const Problem& P, cudaStream_t st, const TcGram& a);
 // Y = A M to FP64 accuracy on the BF16 tensor cores (Ozaki splitting); false when the
 // operands do not suit TMA, then nothing is launched
 // (mtrans: M is read transposed, Y = A M^T, M still the RC x RC block of its slot;
-// accumulate: Y += A M on the columns < ncols, the others untouched)
+// accumulate: Y += A M on the columns < ncols, the others untouched, each row r scaled by
+// rowscale[r] (global row index) when rowscale is not null)
 bool oz_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
              int lda, const int* ninner, int ninner_fix, const double* Bm, int bsmall,
              const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy,
-             int mtrans = 0, int accumulate = 0);
+             int mtrans = 0, int accumulate = 0, const double* rowscale = nullptr);
 // The chunk partials of the symmetric Gram A^T A (the layout and chunk exponents of k_gram)
 // FP64-accurate on the BF16 tensor cores; false when the capacity does not fit.
 bool oz_gram(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
              int lda, const int* acnt, double* part, int nchunk, int* cexp);
-
 void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_t st);
 void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st);
 void mass_fix_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st);

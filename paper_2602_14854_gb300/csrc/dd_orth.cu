@@ -141,9 +141,9 @@ __device__ int pchol_cols(double* A, double* X, int m, int ld, double thr_rel,
     done |= 1ull << bi;
     for (int j = warp; j < m; j += nw) {
       if ((done >> j) & 1ull) continue;
-      const double xj = A[bi * ld + j] * id;
+      const double f = (A[bi * ld + j] * id) * id;   // one FMA per entry of the update
       for (int i = lane; i < m; i += 32)
-        if (!((done >> i) & 1ull)) A[j * ld + i] -= (A[bi * ld + i] * id) * xj;
+        if (!((done >> i) & 1ull)) A[j * ld + i] = fma(-A[bi * ld + i], f, A[j * ld + i]);
     }
     __syncthreads();
   }

@@ -70,14 +70,14 @@ __global__ void k_build_L0(Geo g, const double* V, const double* S, const int* r
   const int src[3] = {k, lo, hi};
   int rr[3];
   for (int b = 0; b < 3; ++b) rr[b] = src[b] >= 0 ? r[src[b]] : 0;
+  const int sl = 2 * axis, shi = 2 * axis + 1;
+  const int il = (lo < 0 && infl_on && infl_on[k * 4 + sl]) ? 1 : 0;
+  const int ih = (hi < 0 && infl_on && infl_on[k * 4 + shi]) ? 1 : 0;
   // stage the three S blocks
   for (int b = 0; b < 3; ++b)
     for (int e = threadIdx.x; e < RC * RC; e += blockDim.x)
       sh[b * RC * RC + e] = src[b] >= 0 ? S[(long)src[b] * RC * RC + e] : 0.0;
   __syncthreads();
-  const int sl = 2 * axis, shi = 2 * axis + 1;
-  const int il = (lo < 0 && infl_on && infl_on[k * 4 + sl]) ? 1 : 0;
-  const int ih = (hi < 0 && infl_on && infl_on[k * 4 + shi]) ? 1 : 0;
   const int mn = rr[0] + rr[1] + rr[2], m = mn + il + ih;
   const int q0 = blockIdx.x * 32;
   for (int e = threadIdx.x; e < 32 * m; e += blockDim.x) {
@@ -381,16 +381,25 @@ __global__ void __launch_bounds__(DD_THREADS) k_small_adv1(Problem P, PhaseBufs 
   double* Cp = SMB(B, P, k, SM_CP);
   double* Cn = SMB(B, P, k, SM_CM);
   double* Ca = SMB(B, P, k, SM_CABS);
+  // (upper triangles, mirrored: the products P_li P_lj are symmetric bit for bit)
   for (int e = threadIdx.x; e < RC * RC; e += blockDim.x) {
-    int i = e / RC, j = e % RC;
+    const int i = e / RC, j = e - i * RC;
+    if (i >= rt || j >= rt) { Cp[e] = 0.0; Cn[e] = 0.0; Ca[e] = 0.0; }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rt * (rt + 1) / 2; e += blockDim.x) {
+    int j = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+    j += (j + 1) * (j + 2) / 2 <= e;
+    j -= j * (j + 1) / 2 > e;
+    const int i = e - j * (j + 1) / 2;              // i <= j
     double sp = 0.0, sm = 0.0;
-    if (i < rt && j < rt)
-      for (int l = 0; l < rt; ++l) {
-        const double pp = Pm[l * RC + i] * Pm[l * RC + j];
-        if (lam[l] > 0.0) sp += lam[l] * pp;
-        else if (lam[l] < 0.0) sm += lam[l] * pp;
-      }
-    Cp[e] = sp; Cn[e] = sm; Ca[e] = sp - sm;
+    for (int l = 0; l < rt; ++l) {
+      const double pp = Pm[l * RC + i] * Pm[l * RC + j];
+      if (lam[l] > 0.0) sp += lam[l] * pp;
+      else if (lam[l] < 0.0) sm += lam[l] * pp;
+    }
+    Cp[i * RC + j] = sp; Cn[i * RC + j] = sm; Ca[i * RC + j] = sp - sm;
+    Cp[j * RC + i] = sp; Cn[j * RC + i] = sm; Ca[j * RC + i] = sp - sm;
   }
   // P and lambda for the eigenbasis K-step (slots S3T and VB are free until the S-step)
   double* Pout = SMB(B, P, k, SM_S3T);
@@ -638,52 +647,48 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
 // by a tall product) along the lines of the sweep, with the ghosts K^b P at the line ends,
 // the increment dt coef (lambda+_j (K~_c - K~_p) + lambda-_j (K~_n - K~_c)) of column j
 // (Appendix A's per-eigenvector upwinding) into Hw (zero in the columns from r_t; rotated
-// back and added to K by the next tall product).  KE1_LINES lines per CTA, a warp per cell row (lanes over
-// the columns): the same arithmetic as k_kstep_eig's one-stage form.
-#define KE1_LINES 8
+// back and added to K by the next tall product).  One line per CTA: warp w takes the
+// columns 32 (w % 2) .. + 31 of the line's segment w / 2 (of KE1_SEGS), each thread walking
+// its column along the segment with the previous and current entries in registers: the
+// same arithmetic as k_kstep_eig's one-stage form.
+#define KE1_SEGS 4
+static_assert(DD_THREADS == 64 * KE1_SEGS, "k_kstep_eig1: two warps per segment");
 __global__ void __launch_bounds__(DD_THREADS) k_kstep_eig1(Problem P, PhaseBufs B, int axis) {
-  __shared__ double lp[DD_MAXC], ln[DD_MAXC];
-  __shared__ double gh[2][KE1_LINES][DD_MAXC];
-  const int k = blockIdx.y, RC = P.g.RC;
+  __shared__ double gh[2][DD_MAXC];
+  const int k = blockIdx.y, RC = P.g.RC, line = blockIdx.x;
   const Lines L = lines_of(P.g, k, axis);
-  const int l0 = blockIdx.x * KE1_LINES;
-  if (l0 >= L.nlines) return;
-  const int nl = min(KE1_LINES, L.nlines - l0), len = L.len, rt = B.rt[k];
-  count_work(P.g, KS_KSTEP_ADV, (double)nl * len * rt * 8.0);
+  if (line >= L.nlines) return;
+  const int len = L.len, rt = B.rt[k];
+  count_work(P.g, KS_KSTEP_ADV, (double)len * rt * 8.0);
   const double* Pg = SMB(B, P, k, SM_S3T);
   const double* lam = SMB(B, P, k, SM_VB);
-  for (int j = threadIdx.x; j < RC; j += blockDim.x) {
-    const double l = j < rt ? lam[j] : 0.0;
-    lp[j] = l > 0.0 ? l : 0.0;
-    ln[j] = l < 0.0 ? l : 0.0;
-  }
-  for (int e = threadIdx.x; e < 2 * nl * rt; e += blockDim.x) {   // ghosts in the eigenbasis
-    const int side = e >= nl * rt, r = e - side * nl * rt, li = r / rt, j = r - li * rt;
-    const double* kb = B.Kb + (((long)k * 2 + side) * P.maxlines + l0 + li) * RC;
+  for (int e = threadIdx.x; e < 2 * rt; e += blockDim.x) {     // ghosts in the eigenbasis
+    const int side = e >= rt, j = e - side * rt;
+    const double* kb = B.Kb + (((long)k * 2 + side) * P.maxlines + line) * RC;
     double x = 0.0;
     for (int u = 0; u < rt; ++u) x += kb[u] * Pg[u * RC + j];
-    gh[side][li][j] = x;
+    gh[side][j] = x;
   }
   __syncthreads();
+  const int warp = threadIdx.x >> 5, j = (warp & 1) * 32 + (threadIdx.x & 31);
+  const int sl = (len + KE1_SEGS - 1) / KE1_SEGS, p0 = (warp >> 1) * sl, p1 = min(len, p0 + sl);
+  if (j >= RC || p0 >= p1) return;
   const double coef = -P.c_adv / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]);
   const double dt = P.g.dtk[k];
-  const long rb = P.g.rowoff[k];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int row = warp; row < nl * len; row += nw) {
-    const int li = row / len, pos = row - li * len;
-    const long c = rb + cell_of(L, l0 + li, pos);
-    const long cp = pos > 0 ? rb + cell_of(L, l0 + li, pos - 1) : -1;
-    const long cn = pos < len - 1 ? rb + cell_of(L, l0 + li, pos + 1) : -1;
-    for (int j = lane; j < RC; j += 32) {
-      double v = 0.0;                            // whole rows: the product reads pairs of columns
-      if (j < rt) {
-        const double kc = B.X1[c * RC + j];
-        const double kp = cp >= 0 ? B.X1[cp * RC + j] : gh[0][li][j];
-        const double kn = cn >= 0 ? B.X1[cn * RC + j] : gh[1][li][j];
-        v = dt * (coef * (lp[j] * (kc - kp) + ln[j] * (kn - kc)));
-      }
-      B.Hw[c * RC + j] = v;
-    }
+  const long base = ((long)P.g.rowoff[k] + cell_of(L, line, 0)) * RC + j;
+  const long step = (long)L.stride_pos * RC;
+  if (j >= rt) {                                 // whole rows: the product reads pairs of columns
+    for (int pos = p0; pos < p1; ++pos) B.Hw[base + pos * step] = 0.0;
+    return;
+  }
+  const double l = lam[j], lp = l > 0.0 ? l : 0.0, ln = l < 0.0 ? l : 0.0;
+  double kp = p0 > 0 ? B.X1[base + (p0 - 1) * step] : gh[0][j], kc = B.X1[base + p0 * step];
+#pragma unroll 4
+  for (int pos = p0; pos < p1; ++pos) {
+    const double kn = pos < len - 1 ? B.X1[base + (pos + 1) * step] : gh[1][j];
+    B.Hw[base + pos * step] = dt * (coef * (lp * (kc - kp) + ln * (kn - kc)));
+    kp = kc;
+    kc = kn;
   }
 }
 
@@ -965,15 +970,17 @@ __global__ void __launch_bounds__(DD_THREADS) k_sstep_adv(Problem P, PhaseBufs B
 // Euler step of direction q's ODE is L_q = S2 v_q + dt kappa_q (A_s S2 v_q + g_q), with s
 // the upwind side of Omega_q, g_q = -G_lo v_q (Omega_q > 0) or G_hi v_q (Omega_q < 0) and
 // kappa_q = -c Omega_q / h.  With W_+ = A_+ S2 - G_lo and W_- = A_- S2 + G_hi it is
-// L_q = S2 v_q + dt kappa_q W_s v_q: the tall products L = V S2^T, Y_+ = V W_+^T and
-// Y_- = V W_-^T over the direction rows (on the tensor cores, FP64-accurate, where the
-// angular family's products run there), then L_q += dt kappa_q Y_s,q.  The arithmetic is
-// that of k_lstep_adv's FP64 form but for the association ((A S2) v instead of A (S2 v));
-// the reduced-precision forms take it too (FP64-accurate, and faster than their FP32 stages).
-// k_lstep_w: blockIdx.x = 0 writes W_+^T (slot VB) and S2^T (slot UB), 1 writes W_-^T
-// (slot S3T); the three slots are free between the S-step and the truncation.
+// L_q = S2 v_q + dt kappa_q W_s v_q: the tall product L = V S2^T over the direction rows,
+// then L += diag(rs_+) V W_+^T and L += diag(rs_-) V W_-^T with rs_s,q = dt kappa_q on the
+// directions of side s and 0 on the others (the Ozaki products' accumulating epilogue, FP64
+// accumulation).  The arithmetic is that of k_lstep_adv's FP64 form but for the association
+// ((A S2) v instead of A (S2 v), (dt kappa) y instead of dt (kappa y)); the reduced-precision
+// forms take it too (FP64-accurate, and faster than their FP32 stages).
+// k_lstep_w: blockIdx.x = 0 writes W_+^T (slot VB), S2^T (slot UB) and rs_+, 1 writes W_-^T
+// (slot S3T) and rs_-; the three slots are free between the S-step and the truncation.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(DD_THREADS) k_lstep_w(Problem P, PhaseBufs B) {
+__global__ void __launch_bounds__(DD_THREADS) k_lstep_w(Problem P, PhaseBufs B, int axis,
+                                                        double* rs) {
   __shared__ double s2[DD_MAXC * DD_MAXC];
   const int k = blockIdx.y, side = blockIdx.x, RC = P.g.RC, rt = B.rt[k];
   const double* S2 = SMB(B, P, k, SM_S2);
@@ -994,23 +1001,15 @@ __global__ void __launch_bounds__(DD_THREADS) k_lstep_w(Problem P, PhaseBufs B) 
     Wt[j * RC + i] = w;
     if (side == 0) St[j * RC + i] = (i < rt && j < rt) ? s2[i * RC + j] : 0.0;
   }
-}
-
-// L += dt kappa_q Y_s on the first r_t columns of every direction row (Y_+ where
-// Omega_q > 0, Y_- where Omega_q < 0; nothing where Omega_q = 0); blockIdx.y = subdomain
-__global__ void __launch_bounds__(DD_THREADS) k_lstep_comb(Problem P, PhaseBufs B, int axis,
-                                                           const double* Yp, const double* Ym) {
-  const int k = blockIdx.y, RC = P.g.RC, n = P.g.n, rt = B.rt[k];
+  // row scales dt kappa_q of this side's directions (kappa_q = -c Omega_q / h), 0 elsewhere
+  const int n = P.g.n;
   const double* om = axis == 0 ? P.ox : P.oy;
-  const double hinv = 1.0 / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]);
-  const double dt = P.g.dtk[k];
-  const long base = (long)k * n * RC;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * RC; e += gridDim.x * blockDim.x) {
-    const int q = e / RC, i = e - q * RC;
+  const double hinv = 1.0 / (axis == 0 ? P.g.hxk[k] : P.g.hyk[k]), dt = P.g.dtk[k];
+  double* r = rs + ((long)side * P.g.nsub + k) * n;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
     const double oq = om[q];
-    if (i >= rt || oq == 0.0) continue;
-    const double kap = -P.c_adv * oq * hinv;
-    B.L[base + e] += dt * (kap * (oq > 0.0 ? Yp[base + e] : Ym[base + e]));
+    const bool mine = side ? oq < 0.0 : oq > 0.0;
+    r[q] = mine ? dt * (-P.c_adv * oq * hinv) : 0.0;
   }
 }
 
@@ -1343,13 +1342,18 @@ __global__ void k_coll_kstep(Problem P, PhaseBufs B) {
       av[h] = t < rc ? a[t] : 0.0;
       ks[h] = k0[h];
     }
+    // the upper half of the columns only where r_c > 32 (FP64 instructions occupy the pipe
+    // whether or not their lanes are active)
+    const int nh = rc > 32 ? 2 : 1;
     for (int s = 0; s < nst; ++s) {
-      TC d = warp_sum_t<TC>(ks[0] * av[0] + ks[1] * av[1]);
-      TC kv[2];
-      for (int h = 0; h < 2; ++h) kv[h] = ss * d * av[h] - st * ks[h] + sq * av[h];
+      TC pd = ks[0] * av[0];
+      if (nh > 1) pd += ks[1] * av[1];
+      TC d = warp_sum_t<TC>(pd);
+      TC kv[2] = {0.0, 0.0};
+      for (int h = 0; h < nh; ++h) kv[h] = ss * d * av[h] - st * ks[h] + sq * av[h];
       const TC bs = (nst == 4) ? c_rk_b[s] : 1.0;
       const TC an = (s + 1 < nst) ? c_rk_a[s + 1] : 0.0;
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < nh; ++h) {
         acc[h] += bs * kv[h];
         ks[h] = k0[h] + an * dt * kv[h];
       }
@@ -2072,8 +2076,7 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
       // refused where that one was not)
       pbeg(st, KS_KSTEP_ADV);
       if (euler) {
-        dim3 grid((P.maxlines + KE1_LINES - 1) / KE1_LINES, nsub);
-        k_kstep_eig1<<<grid, DD_THREADS, 0, st>>>(P, B, axis);
+        k_kstep_eig1<<<dim3(P.maxlines, nsub), DD_THREADS, 0, st>>>(P, B, axis);
       } else {
         const int lpb = kstep_eig_lpb(P, len);
         dim3 grid((P.maxlines + lpb - 1) / lpb, nsub);
@@ -2153,19 +2156,24 @@ void advection_phase(const Problem& P, const PhaseBufs& B, int axis, cudaStream_
   }
   pend(st);
   // 9. L-step
+  bool lprod = false;
   if (P.integrator == 0 && P.oz_ang) {
-    // as three products over the direction rows (k_lstep_w), FP64-accurate in every form
+    // as three products over the direction rows, FP64-accurate in every form: L = V S2^T,
+    // then L += dt kappa_q (V W_s^T)_q by the products' accumulating epilogue, with the
+    // per-row scales of k_lstep_w (zero for the other upwind side)
+    double* rs = B.Hwa;                            // 2 x nsub x n row scales
     pbeg(st, KS_LSTEP_PROD);
-    k_lstep_w<<<dim3(2, nsub), DD_THREADS, 0, st>>>(P, B);
+    k_lstep_w<<<dim3(2, nsub), DD_THREADS, 0, st>>>(P, B, axis, rs);
     pend(st);
-    tall(P, B, st, 0, B.Vh, RC, B.rt, 0, nullptr, SM_UB, B.rt, 0, B.L, RC);
-    tall(P, B, st, 0, B.Vh, RC, B.rt, 0, nullptr, SM_VB, B.rt, 0, B.Hwa, RC);
-    tall(P, B, st, 0, B.Vh, RC, B.rt, 0, nullptr, SM_S3T, B.rt, 0, B.Hw, RC);
-    pbeg(st, KS_LSTEP_PROD);
-    k_lstep_comb<<<dim3(std::max(1, 4 * P.nsm / nsub), nsub), DD_THREADS, 0, st>>>(P, B, axis,
-                                                                                   B.Hwa, B.Hw);
-    pend(st);
-  } else {
+    lprod = oz_tall(P, B.status, st, 0, B.Vh, RC, B.rt, 0, nullptr, SM_UB, B.sm, B.rt, 0, B.L, RC);
+    if (lprod) {                                   // the same shape: not refused either
+      (void)oz_tall(P, B.status, st, 0, B.Vh, RC, B.rt, 0, nullptr, SM_VB, B.sm, B.rt, 0, B.L, RC,
+                    0, 1, rs);
+      (void)oz_tall(P, B.status, st, 0, B.Vh, RC, B.rt, 0, nullptr, SM_S3T, B.sm, B.rt, 0, B.L, RC,
+                    0, 1, rs + (long)nsub * g.n);
+    }
+  }
+  if (!lprod) {
     pbeg(st, KS_LSTEP_ADV);
     if (P.prec >= PREC_MIXED) {
       k_lstep_adv<float><<<dim3((g.n + 31) / 32, nsub), DD_THREADS, lstep_smem(RC),

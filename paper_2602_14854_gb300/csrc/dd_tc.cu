@@ -104,6 +104,7 @@ struct TcTall {
   unsigned* status;
   const double* A;                  // A itself (the kernels that load it without a tensor map)
   int mtrans;                       // M read transposed (the Ozaki kernel)
+  const double* rowscale;           // accumulate: Y_r += rowscale_r (A M)_r (the Ozaki kernel; null: 1)
 };
 
 #define TT_ROWS 128
@@ -707,7 +708,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_tall(TcTall a, int KP, int
         if (rr < t.nrow && cc < a.ldy) {
           double* yp = ybase + (long)rr * a.ldy + cc;
           if (!a.accumulate) *yp = ebuf[rl * 5 + (lane & 3)];
-          else if (cc < t.nc) *yp += ebuf[rl * 5 + (lane & 3)];
+          else if (cc < t.nc) *yp += (a.rowscale ? a.rowscale[t.row0 + rr] : 1.0) * ebuf[rl * 5 + (lane & 3)];
         }
       }
       __syncwarp();
@@ -1210,6 +1211,7 @@ bool tc_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, c
   a.g = P.g; a.spatial = spatial; a.lda = lda; a.ninner = ninner; a.ninner_fix = ninner_fix;
   a.Bm = Bm; a.bsmall = bsmall; a.smbase = smbase; a.ncols = ncols; a.ncols_fix = ncols_fix;
   a.Y = Y; a.ldy = ldy; a.alpha = alpha; a.accumulate = accumulate; a.status = status;
+  a.A = A; a.mtrans = 0; a.rowscale = nullptr;
   a.tps = ((spatial ? P.maxN : P.g.n) + TT_ROWS - 1) / TT_ROWS;
   const long ntot = (long)P.g.nsub * a.tps;
   const int grid = (int)std::min<long>(ntot, P.nsm);
@@ -1225,7 +1227,7 @@ bool tc_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, c
 bool oz_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,
              int lda, const int* ninner, int ninner_fix, const double* Bm, int bsmall,
              const double* smbase, const int* ncols, int ncols_fix, double* Y, int ldy,
-             int mtrans, int accumulate) {
+             int mtrans, int accumulate, const double* rowscale) {
   if (lda > DD_MAXC || (lda & 1)) return false;
   const OzPlan pl = oz_plan(lda, OZ_SMEM_LIMIT);
   if (pl.total > OZ_SMEM_LIMIT) return false;
@@ -1235,6 +1237,7 @@ bool oz_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, c
   a.Y = Y; a.ldy = ldy; a.alpha = 1.0; a.accumulate = accumulate; a.status = status;
   a.A = A;
   a.mtrans = mtrans;
+  a.rowscale = rowscale;
   a.tps = ((spatial ? P.maxN : P.g.n) + TT_ROWS - 1) / TT_ROWS;
   const long ntot = (long)P.g.nsub * a.tps;
   const int grid = (int)std::min<long>(ntot, P.nsm);

@@ -3,7 +3,7 @@ small host program:
 - the enumeration of the spatial completion family (kc_cand) follows R11's order: the same
   cosine products, in the same order, as the oracle's family, for square, thin and ragged
   subdomain shapes, and nothing past the family's end;
-- the guard on the angular table (orthogonal_prefix): the whole weighted table of a product
+- the guard on the angular table (orthogonal_prefix_gram): the whole weighted table of a product
   quadrature is mutually orthogonal, and a direction table whose angles are perturbed keeps
   only the leading part that still is."""
 import itertools
@@ -33,7 +33,15 @@ int main(int argc, char** argv) {
     for (size_t i = 0; i < (size_t)nc * n; ++i)
       if (fscanf(f, "%lf", &t[i]) != 1) return 3;
     fclose(f);
-    printf("%d\n", dd::orthogonal_prefix(t, nc, n, atof(argv[3])));
+    double* g = new double[(size_t)nc * nc];           // the table's Gram, as the library forms it
+    for (int i = 0; i < nc; ++i)
+      for (int j = 0; j < nc; ++j) {
+        double y = 0.0;
+        for (int q = 0; q < n; ++q) y += t[(size_t)i * n + q] * t[(size_t)j * n + q];
+        g[(size_t)i * nc + j] = y;
+      }
+    printf("%d\n", dd::orthogonal_prefix_gram(g, nc, atof(argv[3])));
+    delete[] g;
     delete[] t;
     return 0;
   }

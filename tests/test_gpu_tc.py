@@ -158,15 +158,16 @@ def test_ozaki_products_small(B, seed, cuts):
     rho, ranks, prof = run_products(B, wl, "tensor")
     assert ranks == ref.ranks()
     assert rel(rho, ref.scalar_flux()) < 1e-9
-    assert prof["k_oz_tall"][1] > 0
+    # the tall products and the orthonormalisations' Grams
+    assert prof["k_oz_tall"][1] > 0 and prof["k_oz_gram"][1] > 0
 
 
 @pytest.mark.parametrize("seed,cuts", [(1, None), (4, ([0, 3, 8, 16], [0, 5, 10]))])
 def test_ozaki_lstep_products_euler(B, seed, cuts):
     """Explicit Euler with the Ozaki products: the advection L-step runs as three products
-    over the direction rows (with S2^T, W_+^T = (A_+ S2 - G_lo)^T, W_-^T = (A_- S2 + G_hi)^T)
-    and a per-direction combination, not as k_lstep_adv; FP64 bound 1e-9 and identical
-    ranks on even and ragged tilings."""
+    over the direction rows (with S2^T, W_+^T = (A_+ S2 - G_lo)^T, W_-^T = (A_- S2 + G_hi)^T),
+    the last two accumulated row by row with the scales dt kappa_q of their upwind side, not
+    as k_lstep_adv; FP64 bound 1e-9 and identical ranks on even and ragged tilings."""
     from paper_2602_14854_gb300 import inputs
     kw = {} if cuts is None else {"nx": 16, "ny": 10, "xcuts": cuts[0], "ycuts": cuts[1]}
     wl = inputs.random_small_problem(seed, **{"nx": 8, "ny": 8, **kw}, n_mu=2, n_phi=8, rank=3,
@@ -191,6 +192,20 @@ def test_ozaki_lstep_products_reduced_forms(B, prec):
     assert ranks == ref.ranks()
     assert rel(rho, ref.scalar_flux()) < BOUND.get(prec, 1e-5)
     assert prof["k_lstep_prod"][1] > 0 and "k_lstep_adv" not in prof
+
+
+def test_ozaki_products_inflow(B):
+    """Ozaki products with a physical inflow side (the inflow column in the augmentation's L0,
+    neighbour blocks absent on the boundary) and explicit Euler; FP64 bound 1e-9."""
+    from paper_2602_14854_gb300 import inputs
+    wl = inputs.random_small_problem(5, nx=12, ny=12, tiles_x=3, tiles_y=3, n_mu=2, n_phi=8,
+                                     rank=3, r_aug_max=8, integrator="euler", nsteps=3)
+    wl = wl.with_(inflow={"x_lo": (np.linspace(0.5, 1.5, 12), np.linspace(0.1, 1.0, wl.n))})
+    ref = dd_dlra.DDDLRA(wl).run()
+    rho, ranks, prof = run_products(B, wl, "tensor")
+    assert ranks == ref.ranks()
+    assert rel(rho, ref.scalar_flux()) < 1e-9
+    assert prof["k_oz_tall"][1] > 0
 
 
 def test_ozaki_products_pointsource(B):
