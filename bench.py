@@ -195,9 +195,10 @@ def per_kernel_roofline(prof, nsteps, fp64_peak, fp32_peak, tc_peak, bf16_peak=N
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean over one warm
 # step's launches) of the kernels as they stand, from the ncu captures summarised in
-# profiles/ (k_gram: profiles/k_gram_lognormal_traffic.md, the lognormal workload with the
-# tensor-core products).  An entry must be dropped when its kernel changes.
-NCU_TRAFFIC = {"k_gram": 63.1e6}
+# profiles/ (k_gram: profiles/k_gram_lognormal_traffic.md; k_oz_tall: the 33 launches of a
+# step, profiles/k_oz_tall_lognormal.md; the lognormal workload with the tensor-core
+# products).  An entry must be dropped when its kernel changes.
+NCU_TRAFFIC = {"k_gram": 63.1e6, "k_oz_tall": 94.9e6}
 
 
 def timed_steps(s, steps, warmup, flush, stream, torch):
