@@ -649,8 +649,8 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_adv(Problem P, PhaseBufs B
 // (Appendix A's per-eigenvector upwinding) into Hw (zero in the columns from r_t; rotated
 // back and added to K by the next tall product).  One line per CTA: warp w takes the
 // columns 32 (w % 2) .. + 31 of the line's segment w / 2 (of KE1_SEGS), each thread walking
-// its column along the segment with the previous and current entries in registers: the
-// same arithmetic as k_kstep_eig's one-stage form.
+// its column along the segment with the previous and current entries in registers.  The
+// one-stage form of k_kstep_eig's stencil, expanded into one coefficient per neighbour.
 #define KE1_SEGS 4
 static_assert(DD_THREADS == 64 * KE1_SEGS, "k_kstep_eig1: two warps per segment");
 __global__ void __launch_bounds__(DD_THREADS) k_kstep_eig1(Problem P, PhaseBufs B, int axis) {
@@ -681,12 +681,16 @@ __global__ void __launch_bounds__(DD_THREADS) k_kstep_eig1(Problem P, PhaseBufs 
     for (int pos = p0; pos < p1; ++pos) B.Hw[base + pos * step] = 0.0;
     return;
   }
+  // inc = cc kc + cp kp + cn kn with the column's coefficients (three FP64 operations per
+  // entry: the kernel is bound by the FP64 pipe, whose warp instructions cost the same
+  // however many lanes are active)
   const double l = lam[j], lp = l > 0.0 ? l : 0.0, ln = l < 0.0 ? l : 0.0;
+  const double cpk = -dt * coef * lp, cnk = dt * coef * ln, cck = dt * coef * (lp - ln);
   double kp = p0 > 0 ? B.X1[base + (p0 - 1) * step] : gh[0][j], kc = B.X1[base + p0 * step];
 #pragma unroll 4
   for (int pos = p0; pos < p1; ++pos) {
     const double kn = pos < len - 1 ? B.X1[base + (pos + 1) * step] : gh[1][j];
-    B.Hw[base + pos * step] = dt * (coef * (lp * (kc - kp) + ln * (kn - kc)));
+    B.Hw[base + pos * step] = fma(cnk, kn, fma(cpk, kp, cck * kc));
     kp = kc;
     kc = kn;
   }
@@ -1362,6 +1366,33 @@ __global__ void k_coll_kstep(Problem P, PhaseBufs B) {
       int t = lane + 32 * h;
       if (t < RC) B.K[row * RC + t] = t < rc ? k0d[h] + (double)(dt * acc[h]) : 0.0;
     }
+  }
+}
+
+// The collision K-step with explicit Euler in FP64, a thread per cell (the warp form above
+// issues its FP64 instructions for one cell at a time, and a warp instruction holds the FP64
+// pipe however many of its lanes are active): K_c <- K_c + dt ((sig_s/|S|)(K_c . a) a
+// - sig_t K_c + sQ_c a) on the first r_c columns, zero beyond.
+__global__ void __launch_bounds__(DD_THREADS) k_coll_kstep1(Problem P, PhaseBufs B) {
+  __shared__ double av[DD_MAXC];
+  const int k = blockIdx.y, RC = P.g.RC, N = P.g.N[k], rc = B.rc[k];
+  const double* a = SMB(B, P, k, SM_VEC);
+  for (int t = threadIdx.x; t < RC; t += blockDim.x) av[t] = t < rc ? a[t] : 0.0;
+  __syncthreads();
+  const int c0 = blockIdx.x * blockDim.x;
+  if (c0 >= N) return;
+  count_work(P.g, KS_COLL_KSTEP, (double)min((int)blockDim.x, N - c0) * rc * 6.0);
+  const int cell = c0 + threadIdx.x;
+  if (cell >= N) return;
+  const long row = (long)P.g.rowoff[k] + cell;
+  const double ss = P.sig_s[row] / P.ssum, st = P.sig_t[row], sq = P.sQ[row];
+  const double dt = P.g.dtk[k];
+  double* Kr = B.K + row * RC;
+  double d = 0.0;
+  for (int t = 0; t < rc; ++t) d += Kr[t] * av[t];
+  for (int t = 0; t < RC; ++t) {
+    const double k0 = Kr[t];
+    Kr[t] = t < rc ? k0 + dt * (ss * d * av[t] - st * k0 + sq * av[t]) : 0.0;
   }
 }
 
@@ -2219,6 +2250,8 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   pbeg(st, KS_COLL_KSTEP);
   if (P.prec >= PREC_MIXED) {
     k_coll_kstep<float><<<dim3(64, nsub), DD_THREADS, 0, st>>>(P, B);
+  } else if (P.integrator == 0) {
+    k_coll_kstep1<<<dim3((P.maxN + DD_THREADS - 1) / DD_THREADS, nsub), DD_THREADS, 0, st>>>(P, B);
   } else {
     k_coll_kstep<double><<<dim3(64, nsub), DD_THREADS, 0, st>>>(P, B);
   }
