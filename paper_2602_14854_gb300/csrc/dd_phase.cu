@@ -1396,6 +1396,51 @@ __global__ void __launch_bounds__(DD_THREADS) k_coll_kstep1(Problem P, PhaseBufs
   }
 }
 
+// The collision L-step with explicit Euler in FP64, a thread per direction row (the warp
+// form below issues its FP64 instructions for one direction at a time, and a warp
+// instruction holds the FP64 pipe however many lanes are active): L0 = S2 v,
+// a = sw b_0 - Mt L0, L = L0 + dt a, every sum in the warp form's order (bitwise the same).
+// Dynamic shared memory: S2 and Mt (r_c rows each), b_0, and each thread's L0 (entry j of
+// thread t at j blockDim + t).
+size_t coll_lstep1_smem(int RC) { return sizeof(double) * (2 * RC * RC + RC + DD_THREADS * RC); }
+__global__ void __launch_bounds__(DD_THREADS) k_coll_lstep1(Problem P, PhaseBufs B) {
+  extern __shared__ double sc1[];
+  const int k = blockIdx.y, RC = P.g.RC, n = P.g.n, rc = B.rc[k], T = blockDim.x;
+  double* S2 = sc1;
+  double* Mt = S2 + rc * RC;
+  double* b0 = Mt + rc * RC;
+  double* L0 = b0 + RC;
+  for (int e = threadIdx.x; e < rc * RC; e += T) {
+    S2[e] = SMB(B, P, k, SM_S2)[e];
+    Mt[e] = SMB(B, P, k, SM_MT)[e];
+  }
+  for (int i = threadIdx.x; i < RC; i += T) b0[i] = SMB(B, P, k, SM_VEC)[2 * RC + i];
+  __syncthreads();
+  const int q0 = blockIdx.x * T;
+  if (q0 >= n) return;
+  count_work(P.g, KS_COLL_LSTEP, (double)min(T, n - q0) * rc * rc * 4.0);
+  const int q = q0 + threadIdx.x;
+  if (q >= n) return;
+  const double* Vq = B.Vh + ((long)k * n + q) * RC;
+  double* Lq = B.L + ((long)k * n + q) * RC;
+  double* l0 = L0 + threadIdx.x;
+  for (int i = 0; i < rc; ++i) l0[i * T] = 0.0;
+  for (int j = 0; j < rc; ++j) {                   // sd_i += S2_ij v_j, j ascending
+    const double vj = Vq[j];
+    for (int i = 0; i < rc; ++i) l0[i * T] += S2[i * RC + j] * vj;
+  }
+  const double swq = P.sw[q], dt = P.g.dtk[k];
+  for (int i = 0; i < RC; ++i) {
+    double out = 0.0;
+    if (i < rc) {
+      double a = swq * b0[i];
+      for (int j = 0; j < rc; ++j) a -= Mt[i * RC + j] * l0[j * T];
+      out = l0[i * T] + dt * a;
+    }
+    Lq[i] = out;
+  }
+}
+
 // collision S-step and the stage values b_s of the L-step's direction mean
 __global__ void k_coll_small(Problem P, PhaseBufs B) {
   extern __shared__ double sh[];
@@ -1701,6 +1746,9 @@ cudaError_t phase_init() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_coll_lstep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(coll_lstep_smem(RC)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_coll_lstep1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(coll_lstep1_smem(RC)));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_coll_lstep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(coll_lstep_smem(RC)));
@@ -2309,6 +2357,9 @@ void collision_phase(const Problem& P, const PhaseBufs& B, cudaStream_t st) {
   if (P.prec >= PREC_MIXED) {
     k_coll_lstep<float><<<dim3((g.n + 31) / 32, nsub), DD_THREADS,
                    coll_lstep_smem(RC), st>>>(P, B);
+  } else if (P.integrator == 0) {
+    k_coll_lstep1<<<dim3((g.n + DD_THREADS - 1) / DD_THREADS, nsub), DD_THREADS,
+                    coll_lstep1_smem(RC), st>>>(P, B);
   } else {
     k_coll_lstep<double><<<dim3((g.n + 31) / 32, nsub), DD_THREADS,
                    coll_lstep_smem(RC), st>>>(P, B);
