@@ -1330,29 +1330,38 @@ __global__ void k_coll_kstep(Problem P, PhaseBufs B) {
   const double* a = SMB(B, P, k, SM_VEC);
   const TC dt = (TC)P.g.dtk[k];
   const int nst = P.integrator == 1 ? 4 : 1;
+  // a cell per W lanes (W the power of two >= r_c, up to 32), G = 32 / W cells per warp: FP64
+  // instructions hold the pipe whether or not their lanes are active.  The dot product's
+  // butterfly over W lanes is the full warp's with the steps that add zero lanes left out.
+  int W = 1;
+  while (W < rc && W < 32) W <<= 1;
+  const int G = 32 / W, slot = lane / W, tl = lane - slot * W;
   {
-    const int cells = (N > (int)blockIdx.x * nw) ? ((N - (int)blockIdx.x * nw - 1) / ((int)gridDim.x * nw) + 1) * nw : 0;
-    count_work(P.g, KS_COLL_KSTEP, (double)min(cells, N) * rc * 6.0 * nst);
+    double cells = 0.0;
+    for (long c0 = (long)blockIdx.x * nw * G; c0 < N; c0 += (long)gridDim.x * nw * G)
+      cells += (double)min((long)nw * G, (long)N - c0);
+    count_work(P.g, KS_COLL_KSTEP, cells * rc * 6.0 * nst);
   }
-  for (int cell = blockIdx.x * nw + warp; cell < N; cell += gridDim.x * nw) {
-    const long row = (long)P.g.rowoff[k] + cell;
+  for (int c0 = (blockIdx.x * nw + warp) * G; c0 < N; c0 += gridDim.x * nw * G) {
+    const int cell = c0 + slot;
+    const bool valid = cell < N;
+    const long row = (long)P.g.rowoff[k] + (valid ? cell : c0);
     const TC ss = (TC)(P.sig_s[row] / P.ssum), st = (TC)P.sig_t[row], sq = (TC)P.sQ[row];
     TC k0[2], ks[2], acc[2] = {0.0, 0.0}, av[2];
     double k0d[2];
     for (int h = 0; h < 2; ++h) {
-      int t = lane + 32 * h;
-      k0d[h] = t < rc ? B.K[row * RC + t] : 0.0;
+      int t = tl + 32 * h;
+      k0d[h] = (valid && t < rc) ? B.K[row * RC + t] : 0.0;
       k0[h] = (TC)k0d[h];
       av[h] = t < rc ? a[t] : 0.0;
       ks[h] = k0[h];
     }
-    // the upper half of the columns only where r_c > 32 (FP64 instructions occupy the pipe
-    // whether or not their lanes are active)
+    // the upper half of the columns only where r_c > 32
     const int nh = rc > 32 ? 2 : 1;
     for (int s = 0; s < nst; ++s) {
-      TC pd = ks[0] * av[0];
-      if (nh > 1) pd += ks[1] * av[1];
-      TC d = warp_sum_t<TC>(pd);
+      TC d = ks[0] * av[0];
+      if (nh > 1) d += ks[1] * av[1];
+      for (int o = W >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
       TC kv[2] = {0.0, 0.0};
       for (int h = 0; h < nh; ++h) kv[h] = ss * d * av[h] - st * ks[h] + sq * av[h];
       const TC bs = (nst == 4) ? c_rk_b[s] : 1.0;
@@ -1362,10 +1371,11 @@ __global__ void k_coll_kstep(Problem P, PhaseBufs B) {
         ks[h] = k0[h] + an * dt * kv[h];
       }
     }
-    for (int h = 0; h < 2; ++h) {
-      int t = lane + 32 * h;
-      if (t < RC) B.K[row * RC + t] = t < rc ? k0d[h] + (double)(dt * acc[h]) : 0.0;
-    }
+    if (valid)
+      for (int t = tl; t < RC; t += W) {
+        const int h = t >> 5;
+        B.K[row * RC + t] = t < rc ? k0d[h] + (double)(dt * acc[h]) : 0.0;
+      }
   }
 }
 
