@@ -282,6 +282,9 @@ dd_status dd_dlra_tuning(dd_dlra_t h, int* choice, double* ms);
  * share the array and each overwrites every element it later reads, so nothing needs
  * clearing; calls that overlap on the GPU (other streams, other solvers) race on it.
  * Asynchronous on the solver's stream, like dd_dlra_scalar_flux with out_on_device != 0.
+ * The call can be recorded into a CUDA graph by stream capture when the capturing
+ * stream is the solver's own stream (the one given at create): it issues two kernel
+ * launches on that stream and nothing else.
  */
 dd_status dd_dlra_scalar_flux_noalloc(dd_dlra_t h, double* out);
 

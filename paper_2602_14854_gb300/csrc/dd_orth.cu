@@ -605,6 +605,7 @@ void launch_chol_inv(const OrthArgs& a, const double* part, int nchunk, double* 
 // ---------------------------------------------------------------------------------------
 #define KC_TR 128    // rows per tile of k_kca_w
 #define KC_TR3 32    // rows per CTA of k_kc_apply
+#define KCA_JC 4     // candidates per CTA of k_kca_w
 #define KC_JB 32     // grid rows per block of k_kc_w
 static_assert(DD_THREADS >= 160, "k_kc_w gives each of up to kc_bmax(DD_MAXC) candidates a thread");
 
@@ -629,7 +630,7 @@ __device__ __forceinline__ int kc_plan(const OrthArgs& a, const int* keep, int k
   return min(b, kc_bmax(RC));
 }
 
-size_t kca_w_smem(int RC) { return sizeof(double) * (KC_TR * (RC | 1) + KC_TR); }
+size_t kca_w_smem(int RC) { return sizeof(double) * KC_TR * ((RC | 1) + KCA_JC); }
 size_t kc_w_smem(int RC) { return sizeof(double) * KC_JB * kc_bmax(RC); }   // nfa <= b <= bmax
 size_t kc_sel_smem(int RC) { return sizeof(double) * ((size_t)(kc_bmax(RC) + RC) * RC + 2 * RC); }
 size_t kc_apply_smem(int RC) { return sizeof(double) * KC_TR3 * ((kc_bmax(RC) | 1) + (RC | 1)); }
@@ -702,52 +703,70 @@ __global__ void __launch_bounds__(DD_THREADS) k_kc_w(OrthArgs a, const double* t
   if (tid < b) W[(size_t)l * bm + tid] = acc;
 }
 
-// W for the angular table candidates: one CTA per (candidate j, subdomain), 128-row tiles
-// of Q0 staged in shared memory (odd pitch), lane = row, warp w accumulating columns
-// w + 8 q; warp 0 also sums |c_j|^2.
+// W for the angular table candidates: one CTA per (KCA_JC candidates, subdomain), 128-row
+// tiles of Q0 staged in shared memory once for all of them (odd pitch), lane = row, warp w
+// accumulating columns w + 8 q; warp 0 also sums |c_j|^2.  Every W[l][j] is summed over
+// the same rows in the same order as with one candidate per CTA.
 __global__ void __launch_bounds__(DD_THREADS) k_kca_w(OrthArgs a, const int* keep, double* part) {
   extern __shared__ double kq[];
-  const int k = blockIdx.y, j = blockIdx.x, RC = a.g.RC, bm = kc_bmax(RC);
+  const int k = blockIdx.y, j0 = blockIdx.x * KCA_JC, RC = a.g.RC, bm = kc_bmax(RC);
   int cur0 = 0, r_out = 0, rows = 0;
   const int b = kc_plan(a, keep, k, &cur0, &r_out, &rows);
-  if (j >= b) return;
-  const double* c = a.angcand + (size_t)j * a.g.n;
+  if (j0 >= b) return;
+  const int jn = min(KCA_JC, b - j0);
   const double* Q = a.Q + (size_t)k * a.g.n * a.ldq;
   const int pitch = cur0 | 1;
-  double* cv = kq + KC_TR * pitch;
+  double* cv = kq + KC_TR * pitch;                 // KCA_JC x KC_TR
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double acc[8];
+  double acc[8][KCA_JC], nn[KCA_JC];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-  double nn = 0.0;
+  for (int jj = 0; jj < KCA_JC; ++jj) {
+    nn[jj] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q][jj] = 0.0;
+  }
   for (int r0 = 0; r0 < rows; r0 += KC_TR) {
     const int nr = min(KC_TR, rows - r0);
-    for (int e = tid; e < nr * cur0; e += blockDim.x) {
-      const int r = e / cur0, l = e - r * cur0;
-      kq[r * pitch + l] = Q[(size_t)(r0 + r) * a.ldq + l];
+    for (int r = warp; r < nr; r += DD_THREADS / 32)
+      for (int l = lane; l < cur0; l += 32) kq[r * pitch + l] = Q[(size_t)(r0 + r) * a.ldq + l];
+    for (int e = tid; e < KCA_JC * KC_TR; e += DD_THREADS) {
+      const int jj = e / KC_TR, r = e - jj * KC_TR;
+      cv[e] = (jj < jn && r < nr) ? a.angcand[(size_t)(j0 + jj) * a.g.n + r0 + r] : 0.0;
     }
-    for (int r = tid; r < nr; r += blockDim.x) cv[r] = c[r0 + r];
     __syncthreads();
     for (int r = lane; r < nr; r += 32) {
-      const double x = cv[r];
+      double x[KCA_JC];
+#pragma unroll
+      for (int jj = 0; jj < KCA_JC; ++jj) x[jj] = cv[jj * KC_TR + r];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int l = warp + 8 * q;
-        if (l < cur0) acc[q] += kq[r * pitch + l] * x;
+        if (l < cur0) {
+          const double qv = kq[r * pitch + l];
+#pragma unroll
+          for (int jj = 0; jj < KCA_JC; ++jj) acc[q][jj] += qv * x[jj];
+        }
       }
-      if (warp == 0) nn += x * x;
+      if (warp == 0)
+#pragma unroll
+        for (int jj = 0; jj < KCA_JC; ++jj) nn[jj] += x[jj] * x[jj];
     }
     __syncthreads();
   }
   double* W = part + (size_t)k * kc_region(RC) + (size_t)(bm + RC) * RC;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const double x = warp_sum(acc[q]);
-    const int l = warp + 8 * q;
-    if (lane == 0 && l < cur0) W[(size_t)l * bm + j] = x;
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int jj = 0; jj < KCA_JC; ++jj) {
+      const double x = warp_sum(acc[q][jj]);
+      const int l = warp + 8 * q;
+      if (lane == 0 && l < cur0 && jj < jn) W[(size_t)l * bm + j0 + jj] = x;
+    }
+#pragma unroll
+  for (int jj = 0; jj < KCA_JC; ++jj) {
+    const double x = warp_sum(nn[jj]);
+    if (tid == 0 && jj < jn) W[(size_t)RC * bm + j0 + jj] = x;
   }
-  const double x = warp_sum(nn);
-  if (tid == 0) W[(size_t)RC * bm + j] = x;
 }
 
 // The selection in coefficient space (one CTA per subdomain): kcn = accepted count,
@@ -911,7 +930,8 @@ void launch_kc(const OrthArgs& a, const double* tab, const long long* off, const
   if (a.spatial)
     k_kc_w<<<dim3(RC + 1, nsub), DD_THREADS, kc_w_smem(RC), st>>>(a, tab, off, nf, keep, part);
   else
-    k_kca_w<<<dim3(kc_bmax(RC), nsub), DD_THREADS, kca_w_smem(RC), st>>>(a, keep, part);
+    k_kca_w<<<dim3((kc_bmax(RC) + KCA_JC - 1) / KCA_JC, nsub), DD_THREADS, kca_w_smem(RC), st>>>(
+        a, keep, part);
   pend(st);
   pbeg(st, KS_KC_SEL);
   k_kc_sel<<<nsub, DD_THREADS, kc_sel_smem(RC), st>>>(a, nf, keep, part, kcn, kcur);

@@ -147,13 +147,24 @@ __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* 
       j -= j * (j + 1) / 2 > w;
       const int i = w - j * (j + 1) / 2;
       double sc = 0.0, sl = 0.0, sh = 0.0, sp = 0.0, sm = 0.0;
-      for (int q = q0; q < q1; ++q) {
-        const double o = om[q];
-        const long long ob = __double_as_longlong(o);
-        const double t = Vhk[q * RC + i] * Vhk[q * RC + j];
-        sc += o * t;
-        if (ob < 0 && ob != (long long)0x8000000000000000ull) { sl += t; sm += o * t; }
-        else { sh += t; sp += o * t; }
+      if (nblk == 8) {
+        for (int q = q0; q < q1; ++q) {
+          const double o = om[q];
+          const long long ob = __double_as_longlong(o);
+          const double t = Vhk[q * RC + i] * Vhk[q * RC + j];
+          sc += o * t;
+          if (ob < 0 && ob != (long long)0x8000000000000000ull) { sl += t; sm += o * t; }
+          else { sh += t; sp += o * t; }
+        }
+      } else {                                     // C+ and C- not wanted: three FP64 ops a term
+        for (int q = q0; q < q1; ++q) {
+          const double o = om[q];
+          const long long ob = __double_as_longlong(o);
+          const double t = Vhk[q * RC + i] * Vhk[q * RC + j];
+          sc += o * t;
+          if (ob < 0 && ob != (long long)0x8000000000000000ull) sl += t;
+          else sh += t;
+        }
       }
       out[i * RC + j] = sc; out[j * RC + i] = sc;
       out[RC * RC + i * RC + j] = sl; out[RC * RC + j * RC + i] = sl;

@@ -56,3 +56,34 @@ def test_noalloc_flux_rejects_oversized_solver(B):
         s.scalar_flux_noalloc(out.data_ptr())
     assert e.value.status == 1 and "exceeds" in str(e.value)
     s.close()
+
+
+def test_noalloc_flux_is_capturable_on_the_solvers_stream(B):
+    """A solver created on a user stream: after one ordinary call, the readout is
+    captured on that stream in global capture mode (which refuses allocation and
+    synchronisation inside the capture), and replaying the graph reproduces the
+    regular readout of the state current at replay time."""
+    import torch
+    from paper_2602_14854_gb300 import inputs
+    wl = inputs.config_c0(nsteps=4)
+    st = torch.cuda.Stream()
+    s = B.Solver(wl, stream=st.cuda_stream)
+    out = torch.empty(wl.ncells, dtype=torch.float64, device="cuda")
+    s.step(2)
+    s.scalar_flux_noalloc(out.data_ptr())            # warm-up, outside any capture
+    s.sync()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st, capture_error_mode="global"):
+        s.scalar_flux_noalloc(out.data_ptr())
+    s.step(1)
+    s.sync()
+    ref = s.scalar_flux()
+    out.fill_(float("nan"))
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref)
+    del g
+    s.close()
