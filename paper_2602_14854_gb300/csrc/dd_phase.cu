@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* 
       const int i = w - j * (j + 1) / 2;
       double sc = 0.0, sl = 0.0, sh = 0.0, sp = 0.0, sm = 0.0;
       if (nblk == 8) {
+        #pragma unroll 8
         for (int q = q0; q < q1; ++q) {
           const double o = om[q];
           const long long ob = __double_as_longlong(o);
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* 
           else { sh += t; sp += o * t; }
         }
       } else {                                     // C+ and C- not wanted: three FP64 ops a term
+        #pragma unroll 8
         for (int q = q0; q < q1; ++q) {
           const double o = om[q];
           const long long ob = __double_as_longlong(o);
@@ -182,6 +184,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_ang_coeffs(Geo g, const double* 
       else { u -= n4; blk = 5; Va = Vhi; sel = 2; sa = shi; }
       const int i = u / rtk, j = u - i * rtk;
       double s = 0.0;
+      #pragma unroll 8
       for (int q = q0; q < q1; ++q) {
         const long long ob = __double_as_longlong(om[q]);
         const bool ng = ob < 0 && ob != (long long)0x8000000000000000ull;
