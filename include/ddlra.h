@@ -291,6 +291,20 @@ dd_status dd_dlra_scalar_flux_noalloc(dd_dlra_t h, double* out);
 /* Wait for the solver's stream and report any device-side error. */
 dd_status dd_dlra_sync(dd_dlra_t h);
 
+/*
+ * dd_selftest_wait — failure-detection self-test (no counterpart in the paper: a property of
+ * the library).  Runs, on the current device, one CTA that waits with the same bounded wait
+ * the tensor-core kernels use for their tile loads and MMAs on an mbarrier that nothing
+ * completes, for at most `polls` polls (1 .. 2^21; the production kernels allow 2^21, about a
+ * second).  The wait runs out, the kernel records the timeout bit in a device status word as
+ * the production kernels do (they then report DD_ERR_TIMEOUT from the next synchronising
+ * call) and returns; the call reads the word back and sets *timed_out = 1.  The CUDA context
+ * stays usable.  Synchronous (legacy default stream); allocates and frees one device word.
+ * Errors: DD_ERR_ARG for a null pointer or polls out of range, DD_ERR_CUDA for a failed CUDA
+ * call.
+ */
+dd_status dd_selftest_wait(unsigned polls, int* timed_out);
+
 /* Release all device and host memory of the solver.  NULL is ignored. */
 void dd_dlra_destroy(dd_dlra_t h);
 

@@ -30,7 +30,7 @@ EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scala
            "dd_dlra_sync", "dd_dlra_destroy", "dd_last_error", "dd_profile_slots",
            "dd_profile_slot_name", "dd_dlra_profile", "dd_dlra_profile_work",
            "dd_dlra_scalar_flux_noalloc", "dd_dlra_tuning",
-           "dd_dlra_create_batch", "dd_dlra_instance"]
+           "dd_dlra_create_batch", "dd_dlra_instance", "dd_selftest_wait"]
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -121,6 +121,16 @@ class DDError(RuntimeError):
 def _check(lib, st):
     if st != DD_OK:
         raise DDError(st, lib.dd_last_error().decode())
+
+
+def selftest_wait(polls: int) -> bool:
+    """dd_selftest_wait: run the tensor-core kernels' bounded wait on a barrier nothing
+    completes for at most ``polls`` polls; True when the timeout reached the host as the
+    status bit the production kernels set."""
+    lib = load()
+    out = C.c_int(0)
+    _check(lib, lib.dd_selftest_wait(C.c_uint(int(polls)), C.byref(out)))
+    return bool(out.value)
 
 
 def _d(a):

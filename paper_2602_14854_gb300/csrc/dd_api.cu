@@ -947,6 +947,24 @@ dd_status dd_dlra_profile_work(dd_dlra_t h, int nsteps, double* ms, int* launche
   return check_status(h);
 }
 
+dd_status dd_selftest_wait(unsigned polls, int* timed_out) {
+  g_err.clear();
+  if (!timed_out) return fail(DD_ERR_ARG, "null argument");
+  if (polls == 0 || polls > (1u << 21)) return fail(DD_ERR_ARG, "polls must be in 1 .. 2^21");
+  *timed_out = 0;
+  unsigned* d = nullptr;
+  DD_CUDA(cudaMalloc(&d, sizeof(unsigned)));
+  cudaError_t e = cudaMemset(d, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = dd::wait_selftest(d, polls, nullptr);
+  unsigned word = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&word, d, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  const cudaError_t ef = cudaFree(d);
+  if (e == cudaSuccess) e = ef;
+  if (e != cudaSuccess) return fail(DD_ERR_CUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+  *timed_out = (word & dd::ST_TIMEOUT) ? 1 : 0;
+  return DD_OK;
+}
+
 dd_status dd_dlra_sync(dd_dlra_t h) {
   if (!h) return fail(DD_ERR_ARG, "null handle");
   return check_status(h);

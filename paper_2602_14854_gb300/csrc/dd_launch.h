@@ -179,6 +179,8 @@ struct TcGram {
   unsigned* status;
 };
 cudaError_t tc_init();
+// the bounded-wait self-test (failure detection): ST_TIMEOUT into *status when it runs out
+cudaError_t wait_selftest(unsigned* status, unsigned polls, cudaStream_t st);
 // Y = alpha A M (accumulate: Y += alpha A M); false when the operands do not suit TMA
 // (odd leading dimension), then nothing is launched
 bool tc_tall(const Problem& P, unsigned* status, cudaStream_t st, int spatial, const double* A,

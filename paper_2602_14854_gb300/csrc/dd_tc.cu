@@ -1170,6 +1170,27 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gram(OzGram a) {
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
+// Failure-detection self-test of the bounded wait that every tensor-core kernel uses for its
+// tile loads and MMAs: one thread initialises an mbarrier expecting one arrival that nothing
+// makes and waits on its phase 0 for at most `polls` polls.  When the wait runs out it records
+// ST_TIMEOUT in *status, as the production kernels do, then makes the arrival itself so that
+// the barrier's phase is complete when the CTA exits.
+__global__ void k_wait_selftest(unsigned* status, uint32_t polls) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(&bar, 1);
+  tc::mbar_init_fence();
+  if (!tc::mbar_wait(&bar, 0, polls)) {
+    atomicOr(status, (unsigned)ST_TIMEOUT);
+    tc::mbar_arrive(&bar);
+  }
+}
+
+cudaError_t wait_selftest(unsigned* status, unsigned polls, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(status, polls);
+  return cudaGetLastError();
+}
+
 cudaError_t tc_init() {
   if (!g_encode) {
     void* fn = nullptr;

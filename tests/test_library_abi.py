@@ -34,3 +34,14 @@ def test_create_rejects_bad_arguments():
     h = C.c_void_p()
     st = lib.dd_dlra_create(None, None, None, None, None, None, None, C.byref(h))
     assert st == 1 and b"null" in lib.dd_last_error()
+
+
+def test_selftest_wait_rejects_bad_arguments():
+    """The wait self-test checks its arguments before any device call."""
+    import ctypes as C
+    lib = binding.load(build.build())
+    out = C.c_int(5)
+    assert lib.dd_selftest_wait(C.c_uint(0), C.byref(out)) == 1
+    assert lib.dd_selftest_wait(C.c_uint((1 << 21) + 1), C.byref(out)) == 1
+    assert lib.dd_selftest_wait(C.c_uint(16), None) == 1
+    assert b"polls" in lib.dd_last_error() or b"null" in lib.dd_last_error()
