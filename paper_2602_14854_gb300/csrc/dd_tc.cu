@@ -19,6 +19,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 
 #include "dd_internal.cuh"
@@ -33,19 +34,21 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiledFn g_encode = nullptr;
+// looked up once by tc_init; solvers may be created from several host threads
+std::atomic<EncodeTiledFn> g_encode{nullptr};
 
 // Tensor map of a row-major FP64 array (rows x ld) whose boxes are box_rows x ld
 // (ld even: rows start on 16-byte boundaries).  Rows outside the array read as zero.
 bool make_map(CUtensorMap* m, const double* ptr, int ld, long rows, int box_rows) {
-  if (!g_encode || (ld & 1) || ld > 256 || rows < 1) return false;
+  const EncodeTiledFn encode = g_encode.load(std::memory_order_acquire);
+  if (!encode || (ld & 1) || ld > 256 || rows < 1) return false;
   cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
   cuuint32_t box[2] = {(cuuint32_t)ld, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(ptr), dims, strides,
-                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(ptr), dims, strides,
+                box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
 
@@ -1192,14 +1195,14 @@ cudaError_t wait_selftest(unsigned* status, unsigned polls, cudaStream_t st) {
 }
 
 cudaError_t tc_init() {
-  if (!g_encode) {
+  if (!g_encode.load(std::memory_order_acquire)) {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                                      cudaEnableDefault, &q);
     if (e != cudaSuccess) return e;
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-    g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+    g_encode.store(reinterpret_cast<EncodeTiledFn>(fn), std::memory_order_release);
   }
   cudaError_t e;
   e = cudaFuncSetAttribute(k_tc_tall<tc::FMT_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
