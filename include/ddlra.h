@@ -26,7 +26,8 @@
  *  - Cells are numbered x-fastest over the global grid: c = j*nx + i.
  *    Within subdomain k cells are numbered x-fastest over the subdomain.
  *  - Subdomain k = J*tx + I for tile column I and tile row J.
- *  - Device memory is allocated by the library at create time and released by
+ *  - Device memory is allocated by the library at create time (by cudaMalloc, or
+ *    by the caller's allocator, see dd_set_allocator) and released by
  *    dd_dlra_destroy.  All device work is issued on the stream given at create.
  *  - Errors detected on the device (non-finite values, an exhausted basis
  *    completion family) are recorded in a device status word and reported by
@@ -310,6 +311,36 @@ void dd_dlra_destroy(dd_dlra_t h);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* dd_last_error(void);
+
+/* The same message, under the per-solver name: the message is kept per host thread, so h
+ * (which may be NULL, e.g. after a failed create) does not select it. */
+const char* dd_dlra_last_error(dd_dlra_t h);
+
+/*
+ * dd_allocator / dd_set_allocator — device memory from the caller's allocator, e.g. a
+ * framework's caching allocator, instead of cudaMalloc / cudaFree.  (No counterpart in the
+ * paper: a property of the library.)
+ *
+ * alloc(bytes, ctx) returns device memory of the current device of at least `bytes` bytes,
+ * 256-byte aligned, or NULL; release(ptr, ctx) gives back one pointer alloc returned.  The
+ * setter is process-wide and thread-safe; NULL, or both callbacks NULL, restores cudaMalloc /
+ * cudaFree.  Each solver copies the allocator in effect when it is created: every device
+ * buffer of its state and workspace is drawn through it during dd_dlra_create /
+ * dd_dlra_create_batch (on the creating thread) and released through the same copy by
+ * dd_dlra_destroy (on the destroying thread, after the solver's stream is synchronised), so
+ * changing the allocator later affects only solvers created later.  The memory must stay
+ * valid until release; it is used on the solver's stream.  Not drawn through it: the
+ * allocation-free readout's fixed array, the counters of dd_dlra_profile_work and the
+ * status word of dd_selftest_wait.  Errors: DD_ERR_ARG when exactly one callback is NULL; a NULL or
+ * misaligned block makes the create fail with DD_ERR_CUDA.
+ */
+typedef struct dd_allocator {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*release)(void* ptr, void* ctx);
+  void* ctx;
+} dd_allocator;
+
+dd_status dd_set_allocator(const dd_allocator* a);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,8 @@ EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scala
            "dd_dlra_sync", "dd_dlra_destroy", "dd_last_error", "dd_profile_slots",
            "dd_profile_slot_name", "dd_dlra_profile", "dd_dlra_profile_work",
            "dd_dlra_scalar_flux_noalloc", "dd_dlra_tuning",
-           "dd_dlra_create_batch", "dd_dlra_instance", "dd_selftest_wait"]
+           "dd_dlra_create_batch", "dd_dlra_instance", "dd_selftest_wait",
+           "dd_dlra_last_error", "dd_set_allocator"]
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -94,6 +95,9 @@ def load(path: str | None = None):
     lib.dd_dlra_destroy.argtypes = [vp]
     lib.dd_dlra_destroy.restype = None
     lib.dd_last_error.restype = C.c_char_p
+    lib.dd_dlra_last_error.argtypes = [vp]
+    lib.dd_dlra_last_error.restype = C.c_char_p
+    lib.dd_set_allocator.argtypes = [vp]
     lib.dd_profile_slots.argtypes = []
     lib.dd_profile_slot_name.argtypes = [C.c_int]
     lib.dd_profile_slot_name.restype = C.c_char_p
@@ -106,10 +110,50 @@ def load(path: str | None = None):
                                          C.POINTER(_dp), C.POINTER(Options), vp, C.POINTER(vp)]
     lib.dd_dlra_instance.argtypes = [vp, C.c_int, _ip, _ip, _ip, _ip, _ip]
     for name in EXPORTS:
-        if name not in ("dd_dlra_destroy", "dd_last_error", "dd_profile_slot_name"):
+        if name not in ("dd_dlra_destroy", "dd_last_error", "dd_dlra_last_error",
+                        "dd_profile_slot_name"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("release", _RELEASE_FN), ("ctx", C.c_void_p)]
+
+
+_allocator_keep = None    # the callbacks in effect (kept alive while the library may call them)
+
+
+def set_allocator(alloc=None, release=None):
+    """dd_set_allocator: ``alloc(nbytes) -> int`` device address (256-byte aligned) and
+    ``release(address)`` supply the device memory of solvers created from now on (e.g.
+    ``torch.cuda.caching_allocator_alloc`` / ``caching_allocator_delete``); no arguments
+    restores cudaMalloc / cudaFree.  A solver releases its memory through the callbacks in
+    effect when it was created, so keep them alive until those solvers are closed."""
+    global _allocator_keep
+    lib = load()
+    if alloc is None and release is None:
+        _check(lib, lib.dd_set_allocator(None))
+        return
+    if alloc is None or release is None:
+        raise ValueError("set_allocator needs both alloc and release")
+
+    def _a(nbytes, ctx):
+        try:
+            return int(alloc(int(nbytes)))
+        except Exception:           # noqa: BLE001 - a failed allocation is reported as NULL
+            return None
+
+    def _r(ptr, ctx):
+        release(int(ptr))
+
+    a = Allocator(_ALLOC_FN(_a), _RELEASE_FN(_r), None)
+    _check(lib, lib.dd_set_allocator(C.byref(a)))
+    _allocator_keep = (_allocator_keep or []) + [a]
 
 
 class DDError(RuntimeError):

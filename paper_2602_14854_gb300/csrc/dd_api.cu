@@ -6,7 +6,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -37,9 +39,34 @@ struct SubGeo {
   double hx, hy, dt, sh;
 };
 
+// The device allocator set by dd_set_allocator (both callbacks null: cudaMalloc / cudaFree).
+// A solver copies the one in effect when it is created and releases its memory through that
+// copy; t_alloc points at the copy of the solver being created on this thread.
+std::mutex g_alloc_mu;
+dd_allocator g_alloc = {nullptr, nullptr, nullptr};
+thread_local const dd_allocator* t_alloc = nullptr;
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
-  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(count, 1));
+  const size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
+  if (t_alloc && t_alloc->alloc) {
+    void* q = t_alloc->alloc(bytes, t_alloc->ctx);
+    *p = nullptr;
+    if (!q) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(q) & 255u) {     // the tile loads need aligned rows
+      t_alloc->release(q, t_alloc->ctx);
+      return cudaErrorInvalidValue;
+    }
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+  }
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+void dfree(const dd_allocator& a, void* p) {
+  if (!p) return;
+  if (a.alloc) a.release(p, a.ctx);
+  else cudaFree(p);
 }
 
 double legendre(int l, double x) {
@@ -69,6 +96,7 @@ struct dd_dlra {
   std::vector<SubGeo> geo;
   std::vector<double> sw_host;
   cudaStream_t stream;
+  dd_allocator alloc;   // the device allocator in effect at create
   int use_graph;
   cudaGraphExec_t graph_exec;
   bool graph_ready;
@@ -227,8 +255,7 @@ void free_all(dd_dlra* h) {
                   h->d_fnx, h->d_hxk, h->d_hyk, h->d_dtk, h->d_shk, h->d_dth, h->d_infl_on, h->d_infl_g,
                   h->d_infl_hw, h->d_infl_sc, h->d_kcn, h->d_kcur, h->d_sptab, h->d_spoff,
                   h->d_spnf};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) dfree(h->alloc, p);
   if (h->graph_ready) cudaGraphExecDestroy(h->graph_exec);
 }
 
@@ -262,6 +289,20 @@ dd_status noalloc_flux_impl(dd_dlra_t h, int scratch_doubles, double* out) {
 extern "C" {
 
 const char* dd_last_error(void) { return g_err.c_str(); }
+
+const char* dd_dlra_last_error(dd_dlra_t h) {
+  (void)h;   // the message is kept per host thread, not per solver
+  return g_err.c_str();
+}
+
+dd_status dd_set_allocator(const dd_allocator* a) {
+  g_err.clear();
+  if (a && (a->alloc == nullptr) != (a->release == nullptr))
+    return fail(DD_ERR_ARG, "an allocator needs both alloc and release, or neither");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = a ? *a : dd_allocator{nullptr, nullptr, nullptr};
+  return DD_OK;
+}
 
 static dd_status check_instance(const dd_grid* grid, const dd_tiling* tiling,
                                 const dd_fields* fields, const double* g0, const dd_options* opt) {
@@ -337,6 +378,14 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
   const dd_options* opt = &opts[0];
 
   dd_dlra* h = new dd_dlra();   // value-initialised: every device pointer starts null
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    h->alloc = g_alloc;
+  }
+  struct AllocScope {                // dalloc draws on this solver's allocator until create returns
+    explicit AllocScope(const dd_allocator* a) { t_alloc = a; }
+    ~AllocScope() { t_alloc = nullptr; }
+  } alloc_scope(&h->alloc);
   cudaGetDevice(&h->device);
   h->ninst = ninst;
   h->nx = grids[0].nx; h->ny = grids[0].ny; h->tx = tilings[0].tx; h->ty = tilings[0].ty;
@@ -497,7 +546,7 @@ static dd_status create_impl(int ninst, const dd_grid* grids, const dd_tiling* t
       if (dalloc(&d_g, gh.size()) != cudaSuccess) return bail(DD_ERR_CUDA, "device allocation failed");
       k_tab_gram<<<(n_chk * n_chk + 255) / 256, 256>>>(h->d_angcand, n_chk, n, d_g);
       const cudaError_t e = cudaMemcpy(gh.data(), d_g, sizeof(double) * gh.size(), cudaMemcpyDeviceToHost);
-      cudaFree(d_g);
+      dfree(h->alloc, d_g);
       if (e != cudaSuccess) return bail(DD_ERR_CUDA, "angular table Gram");
     }
     h->n_angorth = dd::orthogonal_prefix_gram(gh.data(), n_chk, 1e-12);

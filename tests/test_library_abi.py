@@ -45,3 +45,21 @@ def test_selftest_wait_rejects_bad_arguments():
     assert lib.dd_selftest_wait(C.c_uint((1 << 21) + 1), C.byref(out)) == 1
     assert lib.dd_selftest_wait(C.c_uint(16), None) == 1
     assert b"polls" in lib.dd_last_error() or b"null" in lib.dd_last_error()
+
+
+def test_allocator_setter_checks_its_callbacks():
+    """dd_set_allocator refuses an allocator with one callback missing, accepts a complete
+    one and NULL (both host-only: no device memory is touched), and dd_dlra_last_error
+    reports the thread's last message whatever the handle."""
+    import ctypes as C
+    lib = binding.load(build.build())
+    half = binding.Allocator(binding._ALLOC_FN(lambda n, ctx: None), binding._RELEASE_FN(), None)
+    assert lib.dd_set_allocator(C.byref(half)) == 1
+    assert b"both" in lib.dd_last_error()
+    assert lib.dd_dlra_last_error(None) == lib.dd_last_error()
+    binding.set_allocator(lambda n: 0, lambda p: None)
+    assert lib.dd_last_error() == b""
+    binding.set_allocator()
+    assert lib.dd_set_allocator(None) == 0
+    with pytest.raises(ValueError):
+        binding.set_allocator(lambda n: 0)
