@@ -214,6 +214,17 @@ dd_status dd_dlra_set_graph(dd_dlra_t h, int use_graph);
  */
 dd_status dd_dlra_scalar_flux(dd_dlra_t h, double* out, int out_on_device);
 
+/*
+ * dd_dlra_scalar_flux_instance — the density of problem inst of a batch alone (for a single
+ * problem, inst = 0 gives the same as dd_dlra_scalar_flux): its nx*ny cells (the grid size
+ * dd_dlra_instance reports), global x-fastest order of that problem.  The density of every
+ * problem is formed in the solver's workspace and problem inst's part copied to out; out is
+ * a device pointer when out_on_device != 0 (asynchronous on the solver's stream), else a
+ * host pointer (the call synchronises).  Errors: DD_ERR_ARG for a null handle or out, or inst
+ * outside 0 .. ninst-1; DD_ERR_CUDA.
+ */
+dd_status dd_dlra_scalar_flux_instance(dd_dlra_t h, int inst, double* out, int out_on_device);
+
 /* Stored ranks per subdomain after the last step (host, nsub ints), and the
  * intermediate ranks r_t of the last x- and y-augmentation (host, 2*nsub ints,
  * may be NULL).  Synchronises. */

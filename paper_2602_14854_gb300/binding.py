@@ -31,7 +31,7 @@ EXPORTS = ["dd_dlra_create", "dd_dlra_step", "dd_dlra_set_graph", "dd_dlra_scala
            "dd_profile_slot_name", "dd_dlra_profile", "dd_dlra_profile_work",
            "dd_dlra_scalar_flux_noalloc", "dd_dlra_tuning",
            "dd_dlra_create_batch", "dd_dlra_instance", "dd_selftest_wait",
-           "dd_dlra_last_error", "dd_set_allocator"]
+           "dd_dlra_last_error", "dd_set_allocator", "dd_dlra_scalar_flux_instance"]
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -87,6 +87,7 @@ def load(path: str | None = None):
     lib.dd_dlra_step.argtypes = [vp, C.c_int]
     lib.dd_dlra_set_graph.argtypes = [vp, C.c_int]
     lib.dd_dlra_scalar_flux.argtypes = [vp, vp, C.c_int]
+    lib.dd_dlra_scalar_flux_instance.argtypes = [vp, C.c_int, vp, C.c_int]
     lib.dd_dlra_ranks.argtypes = [vp, _ip, _ip]
     lib.dd_dlra_info.argtypes = [vp, _ip, _ip, _ip]
     lib.dd_dlra_get_factors.argtypes = [vp, C.c_int, _dp, _dp, _dp, _ip]
@@ -279,6 +280,18 @@ class Solver:
             return None
         rho = np.empty(self.ncells_out)
         _check(self.lib, self.lib.dd_dlra_scalar_flux(self.h, rho.ctypes.data_as(C.c_void_p), 0))
+        return rho
+
+    def scalar_flux_instance(self, i, out=None):
+        """Problem i's density alone (dd_dlra_scalar_flux_instance): a host numpy array
+        (synchronising), or written into the device pointer ``out``."""
+        if out is not None:
+            _check(self.lib, self.lib.dd_dlra_scalar_flux_instance(self.h, int(i), C.c_void_p(out), 1))
+            return None
+        _, _, _, nx, ny = self.layout[i]
+        rho = np.empty(nx * ny)
+        _check(self.lib, self.lib.dd_dlra_scalar_flux_instance(
+            self.h, int(i), rho.ctypes.data_as(C.c_void_p), 0))
         return rho
 
     def scalar_flux_noalloc(self, out):

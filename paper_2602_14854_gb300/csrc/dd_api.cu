@@ -851,6 +851,19 @@ dd_status dd_dlra_scalar_flux(dd_dlra_t h, double* out, int out_on_device) {
   return DD_OK;
 }
 
+dd_status dd_dlra_scalar_flux_instance(dd_dlra_t h, int inst, double* out, int out_on_device) {
+  g_err.clear();
+  if (!h || !out || inst < 0 || inst >= h->ninst) return fail(DD_ERR_ARG, "bad argument");
+  dd::scalar_flux(h->P, h->d_X[0], h->d_V[0], h->d_S[0], h->d_r[0], h->d_fluxw, h->d_rho, h->nx,
+                  h->stream);
+  DD_CUDA(cudaGetLastError());
+  const size_t cnt = (size_t)h->inst_nx[inst] * (size_t)h->inst_ny[inst];
+  DD_CUDA(cudaMemcpyAsync(out, h->d_rho + h->inst_fbase[inst], sizeof(double) * cnt,
+                          out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          h->stream));
+  return out_on_device ? DD_OK : check_status(h);
+}
+
 dd_status dd_dlra_ranks(dd_dlra_t h, int* stored, int* intermediate) {
   g_err.clear();
   if (!h || !stored) return fail(DD_ERR_ARG, "bad argument");
