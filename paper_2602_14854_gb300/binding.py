@@ -288,6 +288,8 @@ class Solver:
         if out is not None:
             _check(self.lib, self.lib.dd_dlra_scalar_flux_instance(self.h, int(i), C.c_void_p(out), 1))
             return None
+        if not 0 <= int(i) < len(self.layout):        # the library refuses it (DD_ERR_ARG)
+            _check(self.lib, self.lib.dd_dlra_scalar_flux_instance(self.h, int(i), None, 0))
         _, _, _, nx, ny = self.layout[i]
         rho = np.empty(nx * ny)
         _check(self.lib, self.lib.dd_dlra_scalar_flux_instance(

@@ -63,3 +63,12 @@ def test_allocator_setter_checks_its_callbacks():
     assert lib.dd_set_allocator(None) == 0
     with pytest.raises(ValueError):
         binding.set_allocator(lambda n: 0)
+
+
+def test_instance_flux_rejects_bad_arguments():
+    """dd_dlra_scalar_flux_instance checks its handle and output before any device call."""
+    import ctypes as C
+    lib = binding.load(build.build())
+    out = (C.c_double * 4)()
+    assert lib.dd_dlra_scalar_flux_instance(None, 0, out, 0) == 1
+    assert lib.dd_dlra_scalar_flux_instance(None, 0, None, 0) == 1
