@@ -178,6 +178,13 @@ def selftest_wait(polls: int) -> bool:
     return bool(out.value)
 
 
+def _choice(what, value, table):
+    """The library's code for an option value; an unknown value is refused here."""
+    if value not in table:
+        raise ValueError(f"{what} {value!r}: one of {sorted(table)}")
+    return table[value]
+
+
 def _d(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
@@ -222,12 +229,16 @@ class Solver:
                     ig[j], ih[j] = _ptr(gs), _ptr(hs)
             flds[i] = Fields(_ptr(ss), _ptr(sa), _ptr(q), ig, ih)
             fixed = w.rank_mode == "fixed"
+            if w.rank_mode not in ("fixed", "tol"):
+                raise ValueError(f"rank_mode {w.rank_mode!r}: 'fixed' or 'tol'")
             opts[i] = Options(DD_RANK_FIXED if fixed else DD_RANK_TOL, w.rank, w.tol, w.r_min,
-                              w.r_max, w.r_aug_max, DD_RK4 if w.integrator == "rk4" else DD_EULER,
-                              w.c_adv, w.dt, tau, PRECISIONS[precision],
-                              1 if w.mass_fix else 0, 1 if w.splitting == "strang" else 0,
-                              1 if w.kstep_split == "flux" else 0, PRODUCTS[products],
-                              1 if autotune else 0)
+                              w.r_max, w.r_aug_max,
+                              _choice("integrator", w.integrator, {"euler": DD_EULER, "rk4": DD_RK4}),
+                              w.c_adv, w.dt, tau, _choice("precision", precision, PRECISIONS),
+                              1 if w.mass_fix else 0,
+                              _choice("splitting", w.splitting, {"lie": 0, "strang": 1}),
+                              _choice("kstep_split", w.kstep_split, {"eigen": 0, "flux": 1}),
+                              _choice("products", products, PRODUCTS), 1 if autotune else 0)
             g0s[i] = _ptr(g0)
         w0 = wls[0]
         ox, oy, w = _d(w0.omega_x), _d(w0.omega_y), _d(w0.w)

@@ -24,6 +24,7 @@ def test_library_exports_every_symbol():
     lib = binding.load(path)
     for name in header_symbols():
         assert hasattr(lib, name), name
+    assert lib.dd_set_allocator(None) == 0          # a successful call clears the message
     assert lib.dd_last_error() == b""
 
 
