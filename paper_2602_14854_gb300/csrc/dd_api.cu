@@ -255,6 +255,9 @@ void free_all(dd_dlra* h) {
                   h->d_fnx, h->d_hxk, h->d_hyk, h->d_dtk, h->d_shk, h->d_dth, h->d_infl_on, h->d_infl_g,
                   h->d_infl_hw, h->d_infl_sc, h->d_kcn, h->d_kcur, h->d_sptab, h->d_spoff,
                   h->d_spnf};
+  // a caller's allocator may hand the blocks out again at once (cudaFree would wait for the
+  // device): nothing of this solver, a failed create's launches included, may still run
+  if (h->alloc.alloc) cudaDeviceSynchronize();
   for (void* p : ptrs) dfree(h->alloc, p);
   if (h->graph_ready) cudaGraphExecDestroy(h->graph_exec);
 }
