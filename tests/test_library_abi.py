@@ -73,3 +73,24 @@ def test_instance_flux_rejects_bad_arguments():
     out = (C.c_double * 4)()
     assert lib.dd_dlra_scalar_flux_instance(None, 0, out, 0) == 1
     assert lib.dd_dlra_scalar_flux_instance(None, 0, None, 0) == 1
+
+
+@pytest.mark.parametrize("block", [0, 0x1008])
+def test_allocator_failure_paths(block):
+    """A caller's allocator that returns NULL, or a block off the 256-byte alignment, makes the
+    create fail with DD_ERR_CUDA before anything runs on the device; a misaligned block goes
+    straight back through release, and nothing else is released."""
+    from paper_2602_14854_gb300 import inputs
+    calls = {"alloc": [], "release": []}
+    binding.set_allocator(lambda n: calls["alloc"].append(n) or block,
+                          lambda p: calls["release"].append(p))
+    try:
+        wl = inputs.random_small_problem(3, nx=8, ny=8, tiles_x=2, tiles_y=2, n_mu=2, n_phi=8,
+                                         rank=2, r_aug_max=4, nsteps=1)
+        with pytest.raises(binding.DDError) as e:
+            binding.Solver(wl)
+    finally:
+        binding.set_allocator()
+    assert e.value.status == 2
+    assert len(calls["alloc"]) == 1 and calls["alloc"][0] > 0
+    assert calls["release"] == ([block] if block else [])
