@@ -147,10 +147,10 @@ typedef struct dd_options {
   int autotune;       /* 1: when the solver is created, time the launch choices on its own    */
                       /* workspace and keep the fastest: the products' and the               */
                       /* orthonormalisations' Grams' engines per row family (with            */
-                      /* DD_PRODUCTS_AUTO) and the chunk counts of the chunked Gram          */
-                      /* reductions (the heuristic's, a half and a quarter of it; every count */
-                      /* keeps a fixed summation order).  Cached per problem shape in the     */
-                      /* process.  0: fixed heuristics.  See dd_dlra_tuning.                   */
+                      /* DD_PRODUCTS_AUTO) and the chunk counts of the orthonormalisations'  */
+                      /* chunked Gram reductions (the heuristic's, a half and a quarter of it; */
+                      /* every count keeps a fixed summation order).  Cached per problem     */
+                      /* shape in the process.  0: fixed heuristics.  See dd_dlra_tuning.      */
 } dd_options;
 
 enum { DD_SPLIT_LIE = 0, DD_SPLIT_STRANG = 1 };
