@@ -94,3 +94,10 @@ def test_allocator_failure_paths(block):
     assert e.value.status == 2
     assert len(calls["alloc"]) == 1 and calls["alloc"][0] > 0
     assert calls["release"] == ([block] if block else [])
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """Without the built CUDA library the binding raises; there is no fallback path."""
+    monkeypatch.setattr(binding, "_lib", None)
+    with pytest.raises(OSError, match="not built"):
+        binding.load(str(tmp_path / "libddlra.so"))
